@@ -1,0 +1,331 @@
+"""ctypes front end of the FP64 CPU oracle (oracle.h).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package; the CUDA library never
+links or calls it.  It shares no code with the CUDA path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+FLUX = {"tvdlf": 0, "hll": 1, "hllc": 2}
+LIMITER = {"minmod": 0, "vanleer": 1, "koren": 2, "none": 3}
+BC = {"periodic": 0, "outflow": 1}
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class OrcConfig(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int), ("block_nx", C.c_int), ("base", C.c_int * 3), ("max_level", C.c_int),
+        ("xmin", C.c_double * 3), ("xmax", C.c_double * 3), ("gamma", C.c_double), ("cfl", C.c_double),
+        ("flux", C.c_int), ("limiter", C.c_int), ("rk", C.c_int), ("bc", (C.c_int * 2) * 3),
+        ("refine_tol", C.c_double), ("coarsen_frac", C.c_double), ("wavefilter", C.c_double),
+        ("var_mask", C.c_uint),
+    ]
+
+
+class OrcMgConfig(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int), ("n", C.c_int), ("L", C.c_double), ("lam", C.c_double),
+        ("nu1", C.c_int), ("nu2", C.c_int), ("max_cycles", C.c_int), ("rtol", C.c_double),
+        ("coarse_max", C.c_int),
+    ]
+
+
+class OrcRdConfig(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int), ("n", C.c_int), ("L", C.c_double), ("Du", C.c_double), ("Dv", C.c_double),
+        ("F", C.c_double), ("k", C.c_double), ("dt", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
+        ("max_cycles", C.c_int), ("rtol", C.c_double), ("coarse_max", C.c_int),
+    ]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.orc_create.restype = C.c_void_p
+        L.orc_create.argtypes = [C.POINTER(OrcConfig)]
+        L.orc_destroy.argtypes = [C.c_void_p]
+        L.orc_num_leaves.argtypes = [C.c_void_p]
+        L.orc_leaves.argtypes = [C.c_void_p, _ip, _ip]
+        L.orc_set_leaves.argtypes = [C.c_void_p, C.c_int, _ip, _ip]
+        for f in ("orc_set_prim", "orc_set_cons", "orc_get_cons", "orc_totals", "orc_lohner"):
+            getattr(L, f).argtypes = [C.c_void_p, _dp]
+        L.orc_set_time.argtypes = [C.c_void_p, C.c_double]
+        L.orc_time.argtypes = [C.c_void_p]
+        L.orc_time.restype = C.c_double
+        L.orc_dt.argtypes = [C.c_void_p, C.c_double]
+        L.orc_dt.restype = C.c_double
+        L.orc_step.argtypes = [C.c_void_p, C.c_double]
+        L.orc_step.restype = C.c_double
+        L.orc_regrid.argtypes = [C.c_void_p]
+        L.orc_face_ghosts.argtypes = [C.c_void_p, C.c_int, _dp]
+        L.orc_prim_to_cons.argtypes = [C.c_int, C.c_double, _dp, _dp]
+        L.orc_cons_to_prim.argtypes = [C.c_int, C.c_double, _dp, _dp]
+        L.orc_phys_flux.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp]
+        L.orc_riemann_flux.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, _dp, _dp, _dp]
+        L.orc_limited_slopes.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp]
+        L.orc_exact_riemann.argtypes = [C.c_double, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp]
+        L.orc_mg_solve.argtypes = [C.POINTER(OrcMgConfig), _dp, _dp, _dp]
+        L.orc_mg_vcycle.argtypes = [C.POINTER(OrcMgConfig), _dp, _dp]
+        L.orc_mg_apply.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
+        L.orc_dense_solve.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
+        L.orc_rd_step.argtypes = [C.POINTER(OrcRdConfig), _dp, _dp, _ip]
+        L.orc_rd_reaction.argtypes = [C.c_double, C.c_double, C.c_int, _dp, _dp, _dp, _dp]
+        L.orc_laplacian.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp]
+        if hasattr(L, "orc_cnn_forward"):
+            _bind_cnn(L)
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    return a.ctypes.data_as(_ip)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_config(ndim, block_nx, base, max_level=1, xmin=(0, 0, 0), xmax=(1, 1, 1), gamma=1.4,
+                cfl=0.8, flux="hll", limiter="minmod", rk=2, bc="periodic", refine_tol=0.2,
+                coarsen_frac=0.5, wavefilter=0.01, var_mask=None):
+    c = OrcConfig()
+    c.ndim = ndim
+    c.block_nx = block_nx
+    base = list(base) + [1] * (3 - len(base))
+    for d in range(3):
+        c.base[d] = base[d]
+        c.xmin[d] = float(xmin[d]) if d < len(xmin) else 0.0
+        c.xmax[d] = float(xmax[d]) if d < len(xmax) else 1.0
+    c.max_level = max_level
+    c.gamma = gamma
+    c.cfl = cfl
+    c.flux = FLUX[flux] if isinstance(flux, str) else flux
+    c.limiter = LIMITER[limiter] if isinstance(limiter, str) else limiter
+    c.rk = rk
+    if isinstance(bc, str):
+        bc = [[bc, bc]] * 3
+    for d in range(3):
+        for s in range(2):
+            b = bc[d][s] if d < len(bc) else "periodic"
+            c.bc[d][s] = BC[b] if isinstance(b, str) else b
+    c.refine_tol = refine_tol
+    c.coarsen_frac = coarsen_frac
+    c.wavefilter = wavefilter
+    c.var_mask = var_mask if var_mask is not None else (1 | (1 << (ndim + 1)))
+    return c
+
+
+class Grid:
+    """A block tree held by the oracle."""
+
+    def __init__(self, **kw):
+        self.cfg = make_config(**kw)
+        self.ndim = self.cfg.ndim
+        self.nv = self.ndim + 2
+        self.ncell = self.cfg.block_nx ** self.ndim
+        self.h = lib().orc_create(C.byref(self.cfg))
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.orc_destroy(self.h)
+            self.h = None
+
+    @property
+    def nleaves(self):
+        return lib().orc_num_leaves(self.h)
+
+    def leaves(self):
+        n = self.nleaves
+        lev = np.zeros(n, dtype=np.int32)
+        crd = np.zeros((n, 3), dtype=np.int32)
+        lib().orc_leaves(self.h, _i(lev), _i(crd))
+        return lev, crd
+
+    def set_leaves(self, level, coords):
+        level = np.ascontiguousarray(level, dtype=np.int32)
+        coords = np.ascontiguousarray(coords, dtype=np.int32).reshape(-1, 3)
+        if lib().orc_set_leaves(self.h, len(level), _i(level), _i(coords)) != 0:
+            raise ValueError("duplicate leaves")
+
+    def set_prim(self, V):
+        V = _f64(V).reshape(self.nleaves, self.nv, self.ncell)
+        lib().orc_set_prim(self.h, _d(V))
+
+    def set_cons(self, U):
+        U = _f64(U).reshape(self.nleaves, self.nv, self.ncell)
+        lib().orc_set_cons(self.h, _d(U))
+
+    def get_cons(self):
+        U = np.zeros((self.nleaves, self.nv, self.ncell))
+        lib().orc_get_cons(self.h, _d(U))
+        return U
+
+    @property
+    def t(self):
+        return lib().orc_time(self.h)
+
+    @t.setter
+    def t(self, v):
+        lib().orc_set_time(self.h, v)
+
+    def dt(self, t_end=np.inf):
+        return lib().orc_dt(self.h, t_end)
+
+    def step(self, t_end=np.inf):
+        return lib().orc_step(self.h, t_end)
+
+    def run(self, nsteps=None, t_end=np.inf):
+        k = 0
+        while (nsteps is None or k < nsteps) and self.t < t_end:
+            if self.step(t_end) <= 0:
+                break
+            k += 1
+        return k
+
+    def totals(self):
+        t = np.zeros(self.nv)
+        lib().orc_totals(self.h, _d(t))
+        return t
+
+    def lohner(self):
+        e = np.zeros(self.nleaves)
+        lib().orc_lohner(self.h, _d(e))
+        return e
+
+    def regrid(self):
+        return lib().orc_regrid(self.h)
+
+    def face_ghosts(self, leaf):
+        nt = self.cfg.block_nx ** (self.ndim - 1)
+        out = np.zeros((self.nv, 2 * self.ndim, 2, nt))
+        lib().orc_face_ghosts(self.h, leaf, _d(out))
+        return out
+
+
+def prim_to_cons(ndim, gamma, V):
+    V = _f64(V)
+    U = np.zeros(ndim + 2)
+    lib().orc_prim_to_cons(ndim, gamma, _d(V), _d(U))
+    return U
+
+
+def cons_to_prim(ndim, gamma, U):
+    U = _f64(U)
+    V = np.zeros(ndim + 2)
+    lib().orc_cons_to_prim(ndim, gamma, _d(U), _d(V))
+    return V
+
+
+def phys_flux(ndim, direction, gamma, V):
+    V = _f64(V)
+    F = np.zeros(ndim + 2)
+    lib().orc_phys_flux(ndim, direction, gamma, _d(V), _d(F))
+    return F
+
+
+def riemann_flux(ndim, direction, flux, gamma, VL, VR):
+    VL, VR = _f64(VL), _f64(VR)
+    F = np.zeros(ndim + 2)
+    lib().orc_riemann_flux(ndim, direction, FLUX.get(flux, flux) if isinstance(flux, str) else flux,
+                           gamma, _d(VL), _d(VR), _d(F))
+    return F
+
+
+def limited_slopes(limiter, a, b):
+    sm, sp = C.c_double(), C.c_double()
+    lim = LIMITER[limiter] if isinstance(limiter, str) else limiter
+    lib().orc_limited_slopes(lim, float(a), float(b), C.byref(sm), C.byref(sp))
+    return sm.value, sp.value
+
+
+def exact_riemann(gamma, left, right, xi):
+    xi = _f64(xi)
+    out = np.zeros((len(xi), 3))
+    ps, us = C.c_double(), C.c_double()
+    rc = lib().orc_exact_riemann(gamma, _d(_f64(left)), _d(_f64(right)), len(xi), _d(xi), _d(out),
+                                 C.byref(ps), C.byref(us))
+    if rc != 0:
+        raise ValueError("vacuum")
+    return out, ps.value, us.value
+
+
+def mg_config(ndim, n, L, lam, nu1=2, nu2=2, max_cycles=50, rtol=1e-10, coarse_max=8):
+    return OrcMgConfig(ndim, n, L, lam, nu1, nu2, max_cycles, rtol, coarse_max)
+
+
+def mg_solve(b, x0, L, lam, **kw):
+    b = _f64(b)
+    x = _f64(x0).copy()
+    ndim, n = b.ndim, b.shape[0]
+    c = mg_config(ndim, n, L, lam, **kw)
+    rr = C.c_double()
+    cyc = lib().orc_mg_solve(C.byref(c), _d(b), _d(x), C.byref(rr))
+    return x, cyc, rr.value
+
+
+def mg_vcycle(r, L, lam, **kw):
+    r = _f64(r)
+    e = np.zeros_like(r)
+    c = mg_config(r.ndim, r.shape[0], L, lam, **kw)
+    lib().orc_mg_vcycle(C.byref(c), _d(r), _d(e))
+    return e
+
+
+def mg_apply(x, L, lam):
+    x = _f64(x)
+    out = np.zeros_like(x)
+    lib().orc_mg_apply(x.ndim, x.shape[0], L, lam, _d(x), _d(out))
+    return out
+
+
+def dense_solve(b, L, lam):
+    b = _f64(b)
+    x = np.zeros_like(b)
+    if lib().orc_dense_solve(b.ndim, b.shape[0], L, lam, _d(b), _d(x)) != 0:
+        raise ValueError("singular")
+    return x
+
+
+def laplacian(x, L):
+    x = _f64(x)
+    out = np.zeros_like(x)
+    lib().orc_laplacian(x.ndim, x.shape[0], L, _d(x), _d(out))
+    return out
+
+
+def rd_reaction(F, k, u, v):
+    u, v = _f64(u), _f64(v)
+    fu, fv = np.zeros_like(u), np.zeros_like(v)
+    lib().orc_rd_reaction(F, k, u.size, _d(u), _d(v), _d(fu), _d(fv))
+    return fu, fv
+
+
+def rd_step(u, v, L, Du, Dv, F, k, dt, nu1=2, nu2=2, max_cycles=50, rtol=1e-10, coarse_max=8):
+    u, v = _f64(u).copy(), _f64(v).copy()
+    c = OrcRdConfig(u.ndim, u.shape[0], L, Du, Dv, F, k, dt, nu1, nu2, max_cycles, rtol, coarse_max)
+    cyc = np.zeros(2, dtype=np.int32)
+    st = lib().orc_rd_step(C.byref(c), _d(u), _d(v), _i(cyc))
+    if st != 0:
+        raise RuntimeError("multigrid did not converge")
+    return u, v, cyc
+
+
+def _bind_cnn(L):  # filled in by the CNN part of the oracle
+    pass

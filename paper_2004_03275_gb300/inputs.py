@@ -1,0 +1,166 @@
+"""Seeded synthetic inputs for the finite-volume and reaction-diffusion workloads.
+
+This module only samples initial conditions (primitive variables at cell
+centres, species concentrations); it contains none of the method's arithmetic,
+so the CUDA path and the CPU oracle can both take their inputs from it.
+
+Random numbers come from a counter-based generator: splitmix64 (Steele, Lea,
+Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014) applied
+to ``seed + (counter + 1) * 0x9E3779B97F4A7C15``; the top 53 bits give a double
+in [0, 1).  Every value is a pure function of (seed, counter), so any subset of
+cells can be regenerated independently.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def uniform(seed: int, counter) -> np.ndarray:
+    """splitmix64 output for each counter, mapped to [0, 1)."""
+    c = np.asarray(counter, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (c + np.uint64(1)) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+# ------------------------------------------------------------ block geometry --
+def cell_centres(level, coords, ndim, block_nx, base, xmin, xmax):
+    """Cell-centre coordinates of every leaf cell.
+
+    Returns (x, gidx): x has shape [nleaf, 3, ncell] (unused dims 0), gidx the
+    global cell index on the leaf's own level, shape [nleaf, 3, ncell].  Cells
+    are ordered i fastest, then j, then k.
+    """
+    level = np.asarray(level)
+    coords = np.asarray(coords).reshape(-1, 3)
+    n = block_nx
+    ncell = n ** ndim
+    loc = np.zeros((3, ncell), dtype=np.int64)
+    ar = np.arange(ncell)
+    loc[0] = ar % n
+    if ndim > 1:
+        loc[1] = (ar // n) % n
+    if ndim > 2:
+        loc[2] = ar // (n * n)
+    nl = len(level)
+    x = np.zeros((nl, 3, ncell))
+    g = np.zeros((nl, 3, ncell), dtype=np.int64)
+    for d in range(ndim):
+        N = base[d] * n * (2 ** (level.astype(np.int64) - 1))  # cells on each leaf's level
+        dx = (xmax[d] - xmin[d]) / N
+        g[:, d, :] = coords[:, d, None].astype(np.int64) * n + loc[d][None, :]
+        x[:, d, :] = xmin[d] + (g[:, d, :] + 0.5) * dx[:, None]
+    return x, g
+
+
+def _prim(nl, ndim, ncell):
+    return np.zeros((nl, ndim + 2, ncell))
+
+
+def sod(x, ndim=1, x0=0.5, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.1)):
+    """Sod shock tube: (rho, v, p) = left for x < x0, right otherwise."""
+    nl, _, ncell = x.shape
+    V = _prim(nl, ndim, ncell)
+    L = x[:, 0, :] < x0
+    V[:, 0] = np.where(L, left[0], right[0])
+    V[:, 1] = np.where(L, left[1], right[1])
+    V[:, ndim + 1] = np.where(L, left[2], right[2])
+    return V
+
+
+def kelvin_helmholtz(x, gidx, base_cells, seed=2004, amp=0.01):
+    """2D shear layer: rho=2, vx=+0.5 for |y-0.5|<0.25, else rho=1, vx=-0.5; p=2.5;
+    vy = amp*(2U-1) with U drawn per cell from the global cell index j*Nx + i."""
+    nl, _, ncell = x.shape
+    V = _prim(nl, 2, ncell)
+    inner = np.abs(x[:, 1, :] - 0.5) < 0.25
+    V[:, 0] = np.where(inner, 2.0, 1.0)
+    V[:, 1] = np.where(inner, 0.5, -0.5)
+    cidx = gidx[:, 1, :] * base_cells + gidx[:, 0, :]
+    V[:, 2] = amp * (2.0 * uniform(seed, cidx) - 1.0)
+    V[:, 3] = 2.5
+    return V
+
+
+def blast(x, seed=7, radius=0.1, p_in=1000.0, p_out=1.0, jitter=0.02, ndim=3):
+    """Sphere of radius `radius` around (0.5,0.5,0.5) + uniform jitter in
+    [-jitter, jitter] per axis (counters 0..2 of `seed`), p_in inside, p_out
+    outside, rho = 1, v = 0."""
+    nl, _, ncell = x.shape
+    V = _prim(nl, ndim, ncell)
+    c = 0.5 + jitter * (2.0 * uniform(seed, np.arange(3)) - 1.0)
+    r2 = np.zeros((nl, ncell))
+    for d in range(ndim):
+        r2 += (x[:, d, :] - c[d]) ** 2
+    V[:, 0] = 1.0
+    V[:, ndim + 1] = np.where(r2 < radius * radius, p_in, p_out)
+    return V
+
+
+def blast_centre(seed=7, jitter=0.02):
+    return 0.5 + jitter * (2.0 * uniform(seed, np.arange(3)) - 1.0)
+
+
+def smooth_wave(x, ndim, t=0.0, amp=0.2, vel=None):
+    """rho = 1 + amp*sin(2 pi (sum_d x_d - t*sum_d v_d)), v = vel (default 1 along
+    every axis), p = 1 (advected density wave, exact solution = translation)."""
+    nl, _, ncell = x.shape
+    vel = [1.0] * ndim if vel is None else list(vel)
+    V = _prim(nl, ndim, ncell)
+    phase = np.zeros((nl, ncell))
+    for d in range(ndim):
+        phase += x[:, d, :] - vel[d] * t
+    V[:, 0] = 1.0 + amp * np.sin(2.0 * np.pi * phase)
+    for d in range(ndim):
+        V[:, 1 + d] = vel[d]
+    V[:, ndim + 1] = 1.0
+    return V
+
+
+# ---------------------------------------------------------- reaction-diffusion --
+def gray_scott_patches(n, ndim=2, L=2.5, seed=4000, npatch=20, side_frac=1.0 / 20.0,
+                       u_patch=0.5, v_patch=0.25, noise=0.01):
+    """u = 1, v = 0 plus `npatch` axis-aligned square (cube) patches of side
+    L*side_frac at uniform-random centres (periodic), where u = u_patch and
+    v = v_patch, each multiplied per cell by (1 + noise*(2U - 1)).
+
+    Counters: patch centres use 0 .. npatch*ndim-1; cell noise uses
+    2^32 + cell (u) and 2^33 + cell (v), cell = flat index of the n^ndim grid."""
+    shape = (n,) * ndim
+    u = np.ones(shape)
+    v = np.zeros(shape)
+    h = L / n
+    centres = uniform(seed, np.arange(npatch * ndim)).reshape(npatch, ndim) * L
+    axes = [(np.arange(n) + 0.5) * h for _ in range(ndim)]
+    mesh = np.meshgrid(*axes, indexing="ij")  # mesh[d][i0, i1, ...] with axis 0 = dim 0
+    half = 0.5 * L * side_frac
+    mask = np.zeros(shape, dtype=bool)
+    for p in range(npatch):
+        inside = np.ones(shape, dtype=bool)
+        for d in range(ndim):
+            dd = np.abs(mesh[d] - centres[p, d])
+            dd = np.minimum(dd, L - dd)
+            inside &= dd < half
+        mask |= inside
+    # storage order: x fastest -> transpose so that the flat index is i + n*(j + n*k)
+    mask = mask.transpose(tuple(range(ndim))[::-1])
+    flat = np.arange(n ** ndim, dtype=np.uint64).reshape((n,) * ndim)
+    nu = 1.0 + noise * (2.0 * uniform(seed, flat + np.uint64(1 << 32)) - 1.0)
+    nv = 1.0 + noise * (2.0 * uniform(seed, flat + np.uint64(1 << 33)) - 1.0)
+    u = np.where(mask, u_patch * nu, 1.0)
+    v = np.where(mask, v_patch * nv, 0.0)
+    return u, v
+
+
+def gray_scott_batch_sizes(count=16):
+    """Instance sides of the batched workload: 128*(i+2) for i = 0..14 plus a
+    second 2048 (16 instances, 256^2 .. 2048^2)."""
+    sizes = [128 * (i + 2) for i in range(15)]
+    return (sizes + [2048])[:count]

@@ -1,0 +1,237 @@
+"""Pins of the oracle's block-tree operations: ghost filling between levels,
+refluxing, Lohner estimator, regrid with 2:1 balance (no GPU)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2004_03275_gb300 import inputs
+from treeutil import random_balanced_tree, is_balanced, covers_domain, touching
+
+GAM = 1.4
+
+
+def grid_on_tree(ndim, bnx, base, max_level, lev, crd, **kw):
+    g = O.Grid(ndim=ndim, block_nx=bnx, base=base, max_level=max_level, gamma=kw.pop("gamma", GAM),
+               cfl=kw.pop("cfl", 0.5), flux=kw.pop("flux", "hllc"), limiter=kw.pop("limiter", "koren"),
+               rk=kw.pop("rk", 3), **kw)
+    g.set_leaves(lev, crd)
+    return g
+
+
+def centres(g, base):
+    lev, crd = g.leaves()
+    c = g.cfg
+    return inputs.cell_centres(lev, crd, g.ndim, c.block_nx, list(base) + [1] * (3 - len(base)),
+                               list(c.xmin), list(c.xmax))
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_random_trees_are_valid(ndim):
+    rng = np.random.default_rng(10 + ndim)
+    base = [2, 2, 2][:ndim] + [1] * (3 - ndim)
+    lev, crd = random_balanced_tree(ndim, base, 3, rng, 4)
+    leaves = list(zip(lev.tolist(), [tuple(c) for c in crd.tolist()]))
+    assert covers_domain(leaves, ndim, base, 3)
+    assert is_balanced(leaves, ndim, base, 3, (True, True, True))
+    g = grid_on_tree(ndim, 4, base, 3, lev, crd)
+    l2, c2 = g.leaves()
+    assert sorted(zip(l2.tolist(), map(tuple, c2.tolist()))) == sorted(leaves)
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_constant_state_exact_on_tree(ndim):
+    rng = np.random.default_rng(20 + ndim)
+    base = [2] * ndim + [1] * (3 - ndim)
+    lev, crd = random_balanced_tree(ndim, base, 3, rng, 3)
+    g = grid_on_tree(ndim, 4, base, 3, lev, crd)
+    V = np.zeros((g.nleaves, ndim + 2, g.ncell))
+    V[:, 0] = 1.7
+    V[:, 1] = 0.3
+    V[:, ndim + 1] = 0.9
+    g.set_prim(V)
+    U0 = g.get_cons()
+    for _ in range(2):
+        g.step()
+    assert np.allclose(g.get_cons(), U0, rtol=1e-14, atol=1e-15)
+
+
+def test_linear_data_ghosts_exact_1d():
+    """In 1D every ghost (copy, restriction, prolongation) of linear data is exact."""
+    # four level-1 blocks; block 1 split into a level-2 and two level-3 blocks
+    leaves = [(1, 0), (2, 2), (3, 6), (3, 7), (2, 4), (2, 5), (1, 3)]
+    lev = np.array([l for l, _ in leaves], dtype=np.int32)
+    crd = np.array([[c, 0, 0] for _, c in leaves], dtype=np.int32)
+    g = grid_on_tree(1, 4, [4, 1, 1], 3, lev, crd, bc="periodic")
+    x, _ = centres(g, [4])
+    V = np.zeros((g.nleaves, 3, g.ncell))
+    V[:, 0] = 2.0 + 0.5 * x[:, 0]   # linear, positive, no wrap jump inside the test leaves
+    V[:, 2] = 1.0
+    g.set_prim(V)
+    U = g.get_cons()
+    l2, c2 = g.leaves()
+    for b in range(g.nleaves):
+        lv, cx = l2[b], c2[b, 0]
+        if cx == 0 and lv == 1 or (lv == 1 and cx == 3):
+            continue  # blocks at the periodic seam see the wrap jump
+        gh = g.face_ghosts(b)  # [var][face][layer][1]
+        h = 1.0 / (4 * 4 * 2 ** (lv - 1))
+        x0 = cx * 4 * h
+        want_lo = [2.0 + 0.5 * (x0 - h / 2), 2.0 + 0.5 * (x0 - 3 * h / 2)]
+        want_hi = [2.0 + 0.5 * (x0 + 4 * h + h / 2), 2.0 + 0.5 * (x0 + 4 * h + 3 * h / 2)]
+        assert np.allclose(gh[0, 0, :, 0], want_lo, rtol=1e-14), (lv, cx)
+        assert np.allclose(gh[0, 1, :, 0], want_hi, rtol=1e-14), (lv, cx)
+
+
+def test_ghosts_exact_for_normal_linear_2d():
+    """Data linear in x only: ghosts across x-faces are exact at every level jump
+    (the tangential slope is zero), and likewise for y."""
+    rng = np.random.default_rng(31)
+    base = [3, 3]
+    lev, crd = random_balanced_tree(2, base + [1], 3, rng, 4, periodic=(False, False, False))
+    g = grid_on_tree(2, 4, base + [1], 3, lev, crd, bc="outflow")
+    x, _ = centres(g, base)
+    l2, c2 = g.leaves()
+    for dim in (0, 1):
+        V = np.zeros((g.nleaves, 4, g.ncell))
+        V[:, 0] = 2.0 + 0.7 * x[:, dim]
+        V[:, 3] = 1.0
+        g.set_prim(V)
+        for b in range(g.nleaves):
+            gh = g.face_ghosts(b)
+            lv = l2[b]
+            h = 1.0 / (3 * 4 * 2 ** (lv - 1))
+            lo = c2[b, dim] * 4 * h
+            for side in (0, 1):
+                at_edge = (side == 0 and c2[b, dim] == 0) or (side == 1 and (c2[b, dim] + 1) * 4 * h > 1 - 1e-12)
+                if at_edge:
+                    continue
+                for m in (0, 1):
+                    xg = lo - (m + 0.5) * h if side == 0 else lo + 4 * h + (m + 0.5) * h
+                    assert np.allclose(gh[0, 2 * dim + side, m], 2.0 + 0.7 * xg, rtol=1e-13), (b, dim, side, m)
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_conservation_on_periodic_tree(ndim):
+    """Refluxing keeps sum U dV constant to round-off across level jumps."""
+    rng = np.random.default_rng(40 + ndim)
+    base = [2] * ndim + [1] * (3 - ndim)
+    lev, crd = random_balanced_tree(ndim, base, 3, rng, 3)
+    g = grid_on_tree(ndim, 4, base, 3, lev, crd, flux="hllc", limiter="koren")
+    x, _ = centres(g, base)
+    V = np.zeros((g.nleaves, ndim + 2, g.ncell))
+    V[:, 0] = 1.0 + 0.3 * np.sin(2 * np.pi * x[:, 0]) * np.cos(2 * np.pi * x[:, 1])
+    V[:, 1] = 0.5 * np.cos(2 * np.pi * x[:, 1])
+    V[:, ndim + 1] = 1.0 + 0.2 * np.sin(2 * np.pi * (x[:, 0] + x[:, 1]))
+    g.set_prim(V)
+    t0 = g.totals()
+    for _ in range(4):
+        g.step()
+    t1 = g.totals()
+    assert np.all(np.abs(t1 - t0) <= 4e-14 * np.maximum(np.abs(t0), 1.0)), (t0, t1)
+
+
+def test_reflux_is_needed():
+    """Without the fine-flux mean on the coarse side, mass would not be conserved:
+    check that the coarse face flux actually changes at a level jump."""
+    lev = np.array([1, 2, 2, 2, 2], dtype=np.int32)
+    crd = np.array([[0, 0, 0], [2, 0, 0], [3, 0, 0], [2, 1, 0], [3, 1, 0]], dtype=np.int32)
+    g = grid_on_tree(2, 4, [2, 1, 1], 2, lev, crd, bc="periodic")
+    x, _ = centres(g, [2, 1])
+    V = np.zeros((g.nleaves, 4, g.ncell))
+    V[:, 0] = 1.0 + 0.5 * np.sin(2 * np.pi * x[:, 1]) + 0.2 * x[:, 0]
+    V[:, 1] = 0.7
+    V[:, 3] = 1.0
+    g.set_prim(V)
+    t0 = g.totals()
+    g.step()
+    assert abs(g.totals()[0] - t0[0]) < 1e-14 * abs(t0[0])
+
+
+def test_lohner_closed_form_sine():
+    """q = 1 + A sin(2 pi x), filter 0: E = 2 sin(pi h)|sin 2pi x| /
+    (|cos 2pi(x+h/2)| + |cos 2pi(x-h/2)|) per cell (trig identities), max per block."""
+    n, bnx = 64, 8
+    g = O.Grid(ndim=1, block_nx=bnx, base=[n // bnx], gamma=GAM, bc="periodic", wavefilter=0.0, var_mask=1)
+    x, _ = centres(g, [n // bnx])
+    V = np.zeros((g.nleaves, 3, bnx))
+    V[:, 0] = 1.0 + 0.4 * np.sin(2 * np.pi * x[:, 0])
+    V[:, 2] = 1.0
+    g.set_prim(V)
+    h = 1.0 / n
+    xc = x[:, 0]
+    E = 2 * np.sin(np.pi * h) * np.abs(np.sin(2 * np.pi * xc)) / (
+        np.abs(np.cos(2 * np.pi * (xc + h / 2))) + np.abs(np.cos(2 * np.pi * (xc - h / 2))))
+    assert np.allclose(g.lohner(), E.max(axis=1), rtol=1e-9)
+
+
+def test_lohner_step_and_filter():
+    """A jump gives E close to 1; the filter eps lowers it; linear data gives ~0."""
+    n, bnx = 64, 8
+    g = O.Grid(ndim=1, block_nx=bnx, base=[n // bnx], gamma=GAM, bc="periodic", wavefilter=0.01, var_mask=1)
+    x, _ = centres(g, [n // bnx])
+    V = np.zeros((g.nleaves, 3, bnx))
+    V[:, 0] = np.where(x[:, 0] < 0.5, 2.0, 1.0)
+    V[:, 2] = 1.0
+    g.set_prim(V)
+    e = g.lohner()
+    # at the jump: |d2| = 1, d1 = 1 + 0.01 (|2| + 2|2| + |1|) or (2 + 2 + 2*1... ) -> E = 1/(1+eps*s)
+    jump = 1.0 / (1.0 + 0.01 * 7.0)   # cell with q- = q0 = 2, q+ = 1: 2 + 4 + 1 = 7
+    assert e.max() == pytest.approx(max(jump, 1.0 / (1.0 + 0.01 * 5.0)), rel=1e-14)
+    assert np.sum(e > 0.5) == 4  # the two blocks at x = 0.5 and the two at the periodic seam
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_regrid_refine_then_coarsen_roundtrip(ndim):
+    base = [2] * ndim + [1] * (3 - ndim)
+    g = O.Grid(ndim=ndim, block_nx=4, base=base, max_level=2, gamma=GAM, refine_tol=-1.0, coarsen_frac=0.5)
+    x, _ = centres(g, base)
+    V = np.zeros((g.nleaves, ndim + 2, g.ncell))
+    V[:, 0] = 1.0 + 0.3 * np.sin(2 * np.pi * x[:, 0])
+    V[:, ndim + 1] = 1.0 + 0.1 * x[:, 1]
+    g.set_prim(V)
+    U0, t0 = g.get_cons(), g.totals()
+    n1 = g.regrid()
+    assert n1 == g.nleaves == (2 ** ndim) * int(np.prod(base[:ndim]))
+    assert np.allclose(g.totals(), t0, rtol=1e-14, atol=1e-15)
+    g2 = O.Grid(ndim=ndim, block_nx=4, base=base, max_level=2, gamma=GAM, refine_tol=1e30, coarsen_frac=0.5)
+    l2, c2 = g.leaves()
+    g2.set_leaves(l2, c2)
+    g2.set_cons(g.get_cons())
+    g2.regrid()
+    assert g2.nleaves == int(np.prod(base[:ndim]))
+    assert np.allclose(g2.get_cons(), U0, rtol=1e-14, atol=1e-15)
+
+
+def test_regrid_balance_and_levels():
+    """Regrid around a sharp 2D feature: 2:1 balanced, levels within [1, max_level],
+    domain covered, leaves at the feature reach max_level."""
+    base = [4, 4]
+    g = O.Grid(ndim=2, block_nx=8, base=base + [1], max_level=4, gamma=5 / 3, refine_tol=0.2,
+               coarsen_frac=0.5, var_mask=1 | 8)
+    for _ in range(3):
+        x, _ = centres(g, base)
+        r2 = (x[:, 0] - 0.3) ** 2 + (x[:, 1] - 0.6) ** 2
+        V = np.zeros((g.nleaves, 4, g.ncell))
+        V[:, 0] = 1.0
+        V[:, 3] = np.where(r2 < 0.01, 1000.0, 1.0)
+        g.set_prim(V)
+        g.regrid()
+    lev, crd = g.leaves()
+    leaves = list(zip(lev.tolist(), [tuple(c) for c in crd.tolist()]))
+    assert lev.max() == 4 and lev.min() >= 1
+    assert covers_domain(leaves, 2, base + [1], 4)
+    assert is_balanced(leaves, 2, base + [1], 4, (True, True, True))
+
+
+def test_regrid_coarsens_smooth_regions():
+    base = [2, 2]
+    lev, crd = random_balanced_tree(2, base + [1], 3, np.random.default_rng(5), 3)
+    g = grid_on_tree(2, 8, base + [1], 3, lev, crd, refine_tol=0.2, coarsen_frac=0.5)
+    V = np.zeros((g.nleaves, 4, g.ncell))
+    V[:, 0] = 1.0
+    V[:, 3] = 1.0
+    g.set_prim(V)
+    n0 = g.nleaves
+    for _ in range(3):
+        g.regrid()
+    assert g.nleaves == 4 and g.nleaves < n0

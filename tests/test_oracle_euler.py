@@ -1,0 +1,282 @@
+"""Pins of the FP64 oracle's finite-volume Euler update (no GPU).
+
+Each test ties the oracle to something outside itself: an exact Riemann
+solution, a textbook limiter function, conservation, a measured order of
+accuracy, an invariant of the tree algorithms.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2004_03275_gb300 import inputs
+from conftest import golden
+
+GAM = 1.4
+
+
+def rand_state(rng, ndim):
+    V = np.empty(ndim + 2)
+    V[0] = rng.uniform(0.2, 3.0)
+    V[1:ndim + 1] = rng.uniform(-1.5, 1.5, ndim)
+    V[ndim + 1] = rng.uniform(0.1, 4.0)
+    return V
+
+
+# ------------------------------------------------------------------ physics ---
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_prim_cons_closed_form(ndim):
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        V = rand_state(rng, ndim)
+        U = O.prim_to_cons(ndim, GAM, V)
+        assert U[0] == V[0]
+        assert np.allclose(U[1:ndim + 1], V[0] * V[1:ndim + 1], rtol=1e-15)
+        # E = rho v^2 / 2 + p / (gamma - 1)
+        E = 0.5 * V[0] * np.sum(V[1:ndim + 1] ** 2) + V[ndim + 1] / (GAM - 1)
+        assert abs(U[ndim + 1] - E) <= 1e-14 * E
+        assert np.allclose(O.cons_to_prim(ndim, GAM, U), V, rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("flux", ["tvdlf", "hll", "hllc"])
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_flux_consistency(flux, ndim):
+    """F(U, U) equals the physical flux (consistency of any Riemann solver)."""
+    rng = np.random.default_rng(2)
+    for _ in range(30):
+        V = rand_state(rng, ndim)
+        for d in range(ndim):
+            F = O.riemann_flux(ndim, d, flux, GAM, V, V)
+            Fp = O.phys_flux(ndim, d, GAM, V)
+            assert np.allclose(F, Fp, rtol=1e-13, atol=1e-13)
+
+
+def test_physical_flux_closed_form():
+    V = np.array([2.0, 0.3, -0.7, 1.5])  # 2D
+    F = O.phys_flux(2, 1, GAM, V)
+    E = 0.5 * 2.0 * (0.09 + 0.49) + 1.5 / 0.4
+    want = [2.0 * -0.7, 2.0 * 0.3 * -0.7, 2.0 * 0.49 + 1.5, (E + 1.5) * -0.7]
+    assert np.allclose(F, want, rtol=1e-14)
+
+
+@pytest.mark.parametrize("u", [0.0, 0.4, -0.3])
+def test_hllc_resolves_contact(u):
+    """An isolated contact (equal p and u, jump in rho and tangential v) is an
+    exact solution that HLLC reproduces: the flux is the upwind physical flux."""
+    VL = np.array([1.0, u, 0.2, 1.0])
+    VR = np.array([0.125, u, -0.5, 1.0])
+    F = O.riemann_flux(2, 0, "hllc", GAM, VL, VR)
+    up = VL if u >= 0 else VR
+    assert np.allclose(F, O.phys_flux(2, 0, GAM, up), rtol=1e-13, atol=1e-14)
+    # HLL smears it: mass flux differs from the upwind value
+    Fh = O.riemann_flux(2, 0, "hll", GAM, VL, VR)
+    assert abs(Fh[0] - O.phys_flux(2, 0, GAM, up)[0]) > 1e-3
+
+
+def test_supersonic_upwinding():
+    """When every wave moves right, HLL and HLLC return the left physical flux."""
+    VL = np.array([1.0, 5.0, 1.0])
+    VR = np.array([0.5, 5.0, 0.8])
+    for f in ("hll", "hllc"):
+        assert np.array_equal(O.riemann_flux(1, 0, f, GAM, VL, VR), O.phys_flux(1, 0, GAM, VL))
+
+
+def test_flux_mirror_symmetry():
+    """Reflecting x -> -x maps F(VL, VR) to -P F(P VR, P VL) with P flipping velocity."""
+    rng = np.random.default_rng(3)
+    for f in ("tvdlf", "hll", "hllc"):
+        for _ in range(20):
+            VL, VR = rand_state(rng, 1), rand_state(rng, 1)
+            F = O.riemann_flux(1, 0, f, GAM, VL, VR)
+            P = np.array([1.0, -1.0, 1.0])
+            Fm = O.riemann_flux(1, 0, f, GAM, P * VR, P * VL)
+            assert np.allclose(F, -P * Fm, rtol=1e-12, atol=1e-12)
+
+
+# ----------------------------------------------------------------- limiters ---
+def koren_phi(r):
+    return max(0.0, min(2 * r, (1 + 2 * r) / 3, 2.0))
+
+
+@pytest.mark.parametrize("lim", ["minmod", "vanleer", "koren"])
+def test_limiters_textbook(lim):
+    rng = np.random.default_rng(4)
+    for _ in range(200):
+        a, b = rng.normal(size=2)
+        sm, sp = O.limited_slopes(lim, a, b)
+        if a * b <= 0:
+            assert sm == 0 and sp == 0
+            continue
+        if lim == "minmod":
+            want_p = want_m = np.sign(a) * min(abs(a), abs(b))
+        elif lim == "vanleer":  # phi(r) = (r + |r|)/(1 + |r|), s = phi(a/b) b
+            r = a / b
+            want_p = want_m = (r + abs(r)) / (1 + abs(r)) * b
+        else:  # q_{i+1/2}^L = q_i + phi(a/b) b / 2 ; q_{i-1/2}^R = q_i - phi(b/a) a / 2
+            want_p = koren_phi(a / b) * b
+            want_m = koren_phi(b / a) * a
+        assert abs(sp - want_p) <= 1e-14 * max(1, abs(want_p))
+        assert abs(sm - want_m) <= 1e-14 * max(1, abs(want_m))
+
+
+@pytest.mark.parametrize("lim", ["minmod", "vanleer", "koren"])
+def test_limiters_reproduce_linear(lim):
+    for a in (0.3, -1.7, 2.5e-3):
+        sm, sp = O.limited_slopes(lim, a, a)
+        assert sm == pytest.approx(a, rel=1e-15) and sp == pytest.approx(a, rel=1e-15)
+
+
+# ----------------------------------------------------------- exact Riemann ---
+def read_golden(name):
+    vals = {}
+    for line in open(golden(name)):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, v = line.split()[:2]
+        vals[k] = float(v)
+    return vals
+
+
+def test_exact_riemann_sod_matches_toro_table():
+    gold = read_golden("sod_star_toro.txt")
+    out, ps, us = O.exact_riemann(GAM, [1, 0, 1], [0.125, 0, 0.1], np.array([0.5, 1.2]))
+    assert ps == pytest.approx(gold["p_star"], abs=6e-6)
+    assert us == pytest.approx(gold["u_star"], abs=6e-6)
+    assert out[0, 0] == pytest.approx(gold["rho_star_left"], abs=6e-6)  # xi=0.5 in star-left
+    assert out[1, 0] == pytest.approx(gold["rho_star_right"], abs=6e-6)  # xi=1.2 in star-right
+
+
+def test_exact_riemann_wave_positions():
+    """Rarefaction head moves at -c_L; tail at u* - c*L; shock speed from the
+    Rankine-Hugoniot condition (closed forms)."""
+    out, ps, us = O.exact_riemann(GAM, [1, 0, 1], [0.125, 0, 0.1], np.array([0.0]))
+    cL = np.sqrt(GAM)
+    head = -cL
+    tail = us - cL * (ps / 1.0) ** ((GAM - 1) / (2 * GAM))
+    rho_sR = 0.125 * (ps / 0.1 + (GAM - 1) / (GAM + 1)) / ((GAM - 1) / (GAM + 1) * ps / 0.1 + 1)
+    shock = us * rho_sR / (rho_sR - 0.125)  # mass conservation across the shock
+    eps = 1e-9
+    xi = np.array([head - eps, head + eps, tail - eps, tail + eps, us - eps, us + eps, shock - eps, shock + eps])
+    o, _, _ = O.exact_riemann(GAM, [1, 0, 1], [0.125, 0, 0.1], xi)
+    assert o[0, 0] == 1.0 and o[1, 0] < 1.0
+    assert o[3, 2] == pytest.approx(ps, rel=1e-12)
+    assert o[2, 2] > ps
+    assert o[4, 0] != pytest.approx(o[5, 0], rel=1e-3)  # contact: density jump
+    assert o[6, 0] == pytest.approx(rho_sR, rel=1e-12) and o[7, 0] == 0.125
+    # positions at t = 0.2 from x0 = 0.5
+    assert 0.5 + 0.2 * head == pytest.approx(0.2634, abs=1e-4)
+    assert 0.5 + 0.2 * tail == pytest.approx(0.4859, abs=1e-4)
+    assert 0.5 + 0.2 * us == pytest.approx(0.6855, abs=1e-4)
+    assert 0.5 + 0.2 * shock == pytest.approx(0.8504, abs=1e-4)
+
+
+# --------------------------------------------------------------- full runs ---
+def sod_grid(ncells, flux="hll", limiter="minmod", rk=2, bnx=16):
+    g = O.Grid(ndim=1, block_nx=bnx, base=[ncells // bnx], gamma=GAM, cfl=0.8, flux=flux,
+               limiter=limiter, rk=rk, bc="outflow")
+    lev, crd = g.leaves()
+    x, _ = inputs.cell_centres(lev, crd, 1, bnx, [ncells // bnx, 1, 1], [0, 0, 0], [1, 1, 1])
+    g.set_prim(inputs.sod(x))
+    return g, x
+
+
+def sod_l1(ncells, **kw):
+    g, x = sod_grid(ncells, **kw)
+    g.run(t_end=0.2)
+    assert g.t == 0.2
+    U = g.get_cons()
+    rho = U[:, 0, :].ravel()
+    xc = x[:, 0, :].ravel()
+    ex, _, _ = O.exact_riemann(GAM, [1, 0, 1], [0.125, 0, 0.1], (xc - 0.5) / 0.2)
+    return np.mean(np.abs(rho - ex[:, 0]))
+
+
+def test_sod_512_against_exact():
+    """Config: 512 cells as 32 blocks of 16, HLL + minmod, SSPRK2, CFL 0.8, t = 0.2."""
+    assert sod_l1(512) <= 1e-2
+
+
+def test_sod_convergence_first_order():
+    e = [sod_l1(n) for n in (128, 256, 512)]
+    orders = np.log2(np.array(e[:-1]) / np.array(e[1:]))
+    assert np.all(orders > 0.6) and np.all(orders < 1.3), (e, orders)
+
+
+@pytest.mark.parametrize("lim", ["vanleer", "koren"])
+def test_smooth_wave_second_order(lim):
+    """Advected density wave, periodic: L1 error order >= 1.8 (SSPRK3)."""
+    errs = []
+    for n in (64, 128, 256):
+        g = O.Grid(ndim=1, block_nx=16, base=[n // 16], gamma=GAM, cfl=0.4, flux="hllc",
+                   limiter=lim, rk=3, bc="periodic")
+        lev, crd = g.leaves()
+        x, _ = inputs.cell_centres(lev, crd, 1, 16, [n // 16, 1, 1], [0, 0, 0], [1, 1, 1])
+        g.set_prim(inputs.smooth_wave(x, 1))
+        g.run(t_end=1.0)
+        exact_rho = inputs.smooth_wave(x, 1, t=1.0)[:, 0]
+        # cell averages of the exact solution (second-order accurate midpoint is not enough)
+        h = 1.0 / n
+        xc = x[:, 0, :]
+        avg = 1.0 + 0.2 * (np.cos(2 * np.pi * (xc - 1.0 - h / 2)) - np.cos(2 * np.pi * (xc - 1.0 + h / 2))) / (2 * np.pi * h)
+        errs.append(np.mean(np.abs(g.get_cons()[:, 0, :] - avg)))
+        assert np.mean(np.abs(avg - exact_rho)) < 1e-3
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders >= 1.8), (errs, orders)
+
+
+def kh_grid(nside, bnx=16, seed=2004, **kw):
+    nb = nside // bnx
+    g = O.Grid(ndim=2, block_nx=bnx, base=[nb, nb], gamma=GAM, cfl=0.8, flux=kw.get("flux", "hllc"),
+               limiter=kw.get("limiter", "vanleer"), rk=3, bc="periodic")
+    lev, crd = g.leaves()
+    x, gi = inputs.cell_centres(lev, crd, 2, bnx, [nb, nb, 1], [0, 0, 0], [1, 1, 1])
+    g.set_prim(inputs.kelvin_helmholtz(x, gi, nside, seed=seed))
+    return g
+
+
+@pytest.mark.parametrize("flux", ["tvdlf", "hll", "hllc"])
+def test_periodic_conservation(flux):
+    g = kh_grid(32, bnx=8, flux=flux)
+    t0 = g.totals()
+    for _ in range(10):
+        g.step()
+        t1 = g.totals()
+        scale = np.maximum(np.abs(t0), 1.0)
+        assert np.all(np.abs(t1 - t0) <= 1e-13 * scale * 10), (t0, t1)
+
+
+def test_constant_state_stays_constant():
+    g = O.Grid(ndim=2, block_nx=8, base=[2, 3], gamma=GAM, cfl=0.8, flux="hllc", limiter="koren", rk=3)
+    V = np.zeros((g.nleaves, 4, 64))
+    V[:, 0], V[:, 1], V[:, 2], V[:, 3] = 1.3, 0.4, -0.2, 2.0
+    g.set_prim(V)
+    U0 = g.get_cons()
+    for _ in range(3):
+        g.step()
+    assert np.allclose(g.get_cons(), U0, rtol=1e-14, atol=1e-15)
+
+
+def test_x_y_symmetry():
+    """A state symmetric under x <-> y (with vx <-> vy) stays symmetric."""
+    n = 16
+    g = O.Grid(ndim=2, block_nx=8, base=[2, 2], gamma=GAM, cfl=0.8, flux="hllc", limiter="koren", rk=3)
+    lev, crd = g.leaves()
+    x, _ = inputs.cell_centres(lev, crd, 2, 8, [2, 2, 1], [0, 0, 0], [1, 1, 1])
+    r2 = (x[:, 0] - 0.5) ** 2 + (x[:, 1] - 0.5) ** 2
+    V = np.zeros((g.nleaves, 4, 64))
+    V[:, 0] = 1.0
+    V[:, 3] = np.where(r2 < 0.04, 10.0, 1.0)
+    g.set_prim(V)
+    for _ in range(5):
+        g.step()
+    U = g.get_cons()
+
+    def field(q):  # uniform 16x16 image [j, i]
+        img = np.zeros((n, n))
+        for b in range(g.nleaves):
+            cx, cy = crd[b, 0], crd[b, 1]
+            img[cy * 8:(cy + 1) * 8, cx * 8:(cx + 1) * 8] = q[b].reshape(8, 8)
+        return img
+
+    rho = field(U[:, 0])
+    assert np.allclose(rho, rho.T, rtol=1e-13, atol=1e-13)
+    assert np.allclose(field(U[:, 1]), field(U[:, 2]).T, rtol=1e-12, atol=1e-12)
