@@ -1,0 +1,229 @@
+/*
+ * amrvac_gb300 -- C ABI of the GB300 (sm_103a) implementation of the
+ * MPI-AMRVAC hot path (Keppens, Teunissen, Xia, Porth, arXiv:2004.03275):
+ * the conservative finite-volume Euler update on a block quadtree/octree and
+ * the geometric-multigrid implicit diffusion step of the reaction-diffusion
+ * module.
+ *
+ * Conventions for every call:
+ *  - returns an int status: AMR_OK (0) or a negative amr_status; no exception
+ *    or abort crosses the boundary; amr_last_error / mg_last_error give text.
+ *  - handles own all device memory they allocate; the caller owns host
+ *    buffers, device buffers it passes in, and the CUDA stream.
+ *  - state arrays that cross the boundary are float64, layout
+ *    [leaf][variable][cell] with leaves in Morton order and cells ordered
+ *    i fastest, then j, then k (i + nx*(j + nx*k)).
+ *  - `on_device` = 1 means the pointer is device memory readable/writable by
+ *    the handle's stream; 0 means host memory (pageable or pinned).
+ *  - calls on one handle are not thread safe; different handles are independent.
+ */
+#ifndef AMRVAC_GB300_H
+#define AMRVAC_GB300_H
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AMR_OK = 0,
+  AMR_ERR_INVALID_ARG = -1,   /* bad config or argument; nothing was changed */
+  AMR_ERR_OOM = -2,           /* device or host allocation failed */
+  AMR_ERR_CUDA = -3,          /* a CUDA runtime call failed (text in last_error) */
+  AMR_ERR_NONPHYSICAL = -4,   /* rho <= 0 or p <= 0 (or NaN) met on the device */
+  AMR_ERR_TIMEOUT = -5,       /* a bounded device wait gave up */
+  MG_ERR_NOT_CONVERGED = -6,  /* multigrid hit max_cycles before rtol */
+  AMR_ERR_CAPACITY = -7,      /* the tree would exceed max_blocks */
+  AMR_ERR_UNBALANCED = -8     /* a given leaf set is not a 2:1 balanced cover */
+} amr_status;
+
+enum { AMR_FLUX_TVDLF = 0, AMR_FLUX_HLL = 1, AMR_FLUX_HLLC = 2 };
+enum { AMR_LIM_MINMOD = 0, AMR_LIM_VANLEER = 1, AMR_LIM_KOREN = 2, AMR_LIM_NONE = 3 };
+enum { AMR_SSPRK2 = 2, AMR_SSPRK3 = 3 };
+enum { AMR_BC_PERIODIC = 0, AMR_BC_OUTFLOW = 1 };
+enum { AMR_FP64 = 0, AMR_FP32 = 1 };
+enum { AMR_NB_BOUNDARY = -1 };
+
+/* ------------------------------------------------------------------------
+ * Block-tree finite-volume Euler solver.
+ *
+ * Problem (Sec. 1.1, Eq. (eq) with S = 0): dU/dt + div F(U) = 0 for the HD
+ * variables U = (rho, rho v, E), E = rho v^2/2 + p/(gamma-1), primitive
+ * V = (rho, v, p).  Fluxes: TVDLF (local Lax-Friedrichs) and HLL from the
+ * signal-speed bounds (Sec. 1.2, phys_get_cmax / phys_get_cbounds), HLLC
+ * (Sec. 2.4); limited MUSCL reconstruction of V with minmod / van Leer / Koren
+ * (Koren: Sec. 2.3.1); SSP Runge-Kutta in two or three stages (Sec. 2.3.2,
+ * 2.4); CFL time step dt = cfl / max_cells sum_d (|v_d| + c)/dx_d (Sec. 1.2).
+ * Grid (Sec. 1.3): blocks of block_nx^ndim cells, base_nblocks blocks per
+ * dimension on level 1, refinement ratio 2 up to max_level, Lohner-type
+ * estimator of weighted second derivatives; refine if one cell exceeds
+ * refine_tol, coarsen if all cells of all siblings are below
+ * coarsen_frac*refine_tol; 2:1 balance across faces, edges and corners.
+ * ------------------------------------------------------------------------ */
+typedef struct amr_handle amr_handle;
+
+typedef struct {
+  int ndim;             /* 1, 2 or 3 */
+  int block_nx;         /* cells per block side: 8 or 16 (block_nx1.. of Sec. 1.3) */
+  int base_nblocks[3];  /* blocks per dimension on level 1 (domain_nx / block_nx) */
+  int max_level;        /* refine_max_level; 1 = uniform block grid */
+  double xmin[3], xmax[3];  /* xprobmin / xprobmax */
+  double gamma;
+  int flux;             /* AMR_FLUX_* */
+  int limiter;          /* AMR_LIM_* */
+  int rk;               /* AMR_SSPRK2 or AMR_SSPRK3 */
+  double cfl;
+  int bc[3][2];         /* [dim][low, high]: AMR_BC_PERIODIC (both sides) or AMR_BC_OUTFLOW */
+  int precision;        /* AMR_FP64 (plain) or AMR_FP32 (state, reconstruction, fluxes in float;
+                           conserved totals in float64) */
+  double refine_tol;    /* estimator threshold for refinement */
+  double coarsen_frac;  /* coarsen below coarsen_frac * refine_tol */
+  double wavefilter;    /* estimator filter epsilon (0.01 typical) */
+  unsigned refine_var_mask; /* primitive variables used by the estimator: bit 0 rho,
+                               bits 1..ndim velocity, bit ndim+1 p */
+  long long max_blocks; /* leaf capacity; a regrid that would exceed it fails with
+                           AMR_ERR_CAPACITY and leaves the tree unchanged */
+  void* stream;         /* cudaStream_t owned by the caller; NULL = legacy default stream */
+} amr_config;
+
+/* Creates the level-1 block grid (base_nblocks), state zero, t = 0.
+ * Errors: AMR_ERR_INVALID_ARG (unsupported ndim/block_nx/limits), AMR_ERR_OOM, AMR_ERR_CUDA. */
+int amr_create(const amr_config* cfg, amr_handle** out);
+int amr_destroy(amr_handle* h);
+const char* amr_last_error(const amr_handle* h);
+
+/* Number of leaves and their level / block coordinates (Morton order).
+ * coords has 3 ints per leaf; unused dimensions are 0.  cap = leaves the
+ * arrays can hold; AMR_ERR_INVALID_ARG if cap < number of leaves. */
+int amr_num_leaves(const amr_handle* h, long long* n);
+int amr_leaf_info(const amr_handle* h, int* level, int* coords, long long cap);
+
+/* Replaces the tree by the given leaves (any order; stored in Morton order).
+ * The leaves must cover the domain and be 2:1 balanced, else
+ * AMR_ERR_UNBALANCED and nothing changes.  State becomes zero. */
+int amr_set_leaves(amr_handle* h, long long n, const int* level, const int* coords);
+
+/* Sets the state of every leaf from a float64 array [leaf][var][cell]
+ * (n_values = leaves * (ndim+2) * block_nx^ndim).  primitive = 1: the values
+ * are (rho, v_1..v_ndim, p) and are converted on the device (Sec. 1.1,
+ * phys_to_conserved); 0: conserved (rho, m_1..m_ndim, E).  Recomputes the
+ * CFL step.  Synchronous. */
+int amr_set_state(amr_handle* h, const double* W, long long n_values, int on_device, int primitive);
+
+/* Copies the conserved state to a float64 array [leaf][var][cell] (converted
+ * on the device for the FP32 path).  cap_values = capacity in doubles.
+ * Synchronous. */
+int amr_read_state(amr_handle* h, double* U, long long cap_values, int on_device);
+
+int amr_set_time(amr_handle* h, double t);
+
+/* One SSPRK step with dt = min(cfl-step, t_end - t).  Synchronous; returns the
+ * dt taken (0 if t >= t_end) and the new time.  AMR_ERR_NONPHYSICAL if a
+ * non-positive density or pressure was met. */
+int amr_step(amr_handle* h, double t_end, double* dt_taken, double* t_now);
+
+/* nsteps SSPRK steps queued on the handle's stream as CUDA-graph launches
+ * (steps after t_end are no-ops on the device).  Asynchronous: call amr_sync
+ * to wait and to collect the status. */
+int amr_run(amr_handle* h, int nsteps, double t_end);
+int amr_sync(amr_handle* h, double* t_now, double* dt_last);
+
+/* Refinement estimator (max over each leaf's cells), computed on the device,
+ * copied to err[leaf]; cap = capacity.  Synchronous. */
+int amr_estimate(amr_handle* h, double* err, long long cap);
+
+/* Estimator -> flags -> refine / coarsen with 2:1 balance -> new leaves filled
+ * by limited prolongation (new children) or restriction (new parents).
+ * Synchronous.  Errors: AMR_ERR_CAPACITY (tree unchanged). */
+int amr_regrid(amr_handle* h);
+
+/* FP64 sum over leaves and cells of U dV, per conserved variable, as of the
+ * last step (or set_state / regrid).  totals has ndim+2 entries. */
+int amr_conserved_totals(amr_handle* h, double* totals);
+
+/* Face-neighbour table, for checks: for leaf i and face f = 2*d + side,
+ * kind[i*2*ndim + f] = 0 same level, 1 coarser, 2 finer, -1 domain boundary
+ * (outflow); nbr[...] = leaf index of the same-level or coarser neighbour, or
+ * of the first finer neighbour (tangential offset 0), -1 at a boundary.
+ * cap = entries the arrays can hold (leaves * 2 * ndim). */
+int amr_face_neighbors(const amr_handle* h, int* kind, int* nbr, long long cap);
+
+/* Face ghost values of one leaf after the device ghost fill, float64
+ * [var][face][layer 0..1][tangential cell]; for checks.  Synchronous. */
+int amr_face_ghosts(amr_handle* h, long long leaf, double* out, long long cap);
+
+/* Device launch counters: kernels launched by this handle since creation. */
+int amr_kernel_launches(const amr_handle* h, long long* n);
+
+/* ------------------------------------------------------------------------
+ * Batched Helmholtz multigrid (Sec. 2.5.1, Eq. (diff-helmholtz); Sec. 1.4).
+ * Solves (lambda_i - lap_h) x = b for n_inst independent periodic square
+ * (cube) grids of side n_cells[i] on [0, L]^ndim, cell-centred 5/7-point
+ * Laplacian.  Red-black Gauss-Seidel smoothing (nu1 pre, nu2 post),
+ * restriction = mean of 2^ndim children, cell-centred (bi/tri)linear
+ * prolongation, coarsening while the side is even and > coarse_max, exact
+ * solve on the coarsest grid.  Iterates until max|b - A x| <= rtol * max|b|
+ * per instance (the paper's max-residual rule, Sec. 2.5.2), or max_cycles.
+ * precision AMR_FP32: V-cycles in float on the correction, iterate, residual
+ * and norms in float64 (defect correction); AMR_FP64: everything float64.
+ * ------------------------------------------------------------------------ */
+typedef struct mg_handle mg_handle;
+
+typedef struct {
+  int ndim;             /* 2 or 3 */
+  int n_inst;           /* number of independent grids */
+  const int* n_cells;   /* [n_inst] cells per side (host pointer, copied) */
+  const double* lambda; /* [n_inst] Helmholtz constants > 0 (host pointer, copied) */
+  double L;             /* domain side */
+  int nu1, nu2, max_cycles;
+  double rtol;
+  int coarse_max;       /* 8 */
+  int precision;        /* AMR_FP32 or AMR_FP64 */
+  void* stream;
+} mg_config;
+
+int mg_create(const mg_config* cfg, mg_handle** out);
+int mg_destroy(mg_handle* h);
+const char* mg_last_error(const mg_handle* h);
+/* Total unknowns = sum_i n_cells[i]^ndim; b and x are packed instance after
+ * instance, each x-fastest.  x holds the initial guess on entry and the
+ * solution on return.  cycles[n_inst] (host, may be NULL) gets the V-cycles
+ * per instance, relres[n_inst] (host, may be NULL) the final max-norm
+ * relative residuals.  Synchronous.  MG_ERR_NOT_CONVERGED if an instance
+ * did not reach rtol (x then holds the last iterate). */
+int mg_solve(mg_handle* h, const double* b, double* x, int on_device, int* cycles, double* relres);
+int mg_num_unknowns(const mg_handle* h, long long* n);
+
+/* ------------------------------------------------------------------------
+ * Gray-Scott reaction-diffusion with the IMEX trapezoidal scheme (Sec. 2.5,
+ * Eq. (gray-scott), Eq. (imex)): reaction explicit, diffusion implicit through
+ * the batched multigrid above with lambda = 2/(dt D) per species; both species
+ * of all instances form one multigrid batch.  Initial guess: w_n.
+ * ------------------------------------------------------------------------ */
+typedef struct rd_handle rd_handle;
+
+typedef struct {
+  int ndim, n_inst;
+  const int* n_cells;   /* [n_inst] (host, copied) */
+  double L, Du, Dv, F, k, dt;
+  int nu1, nu2, max_cycles;
+  double rtol;
+  int coarse_max;
+  int precision;        /* AMR_FP32 (float smoothing) or AMR_FP64 */
+  void* stream;
+} rd_config;
+
+int rd_create(const rd_config* cfg, rd_handle** out);
+int rd_destroy(rd_handle* h);
+const char* rd_last_error(const rd_handle* h);
+/* u, v packed instance after instance (as mg_solve). Synchronous. */
+int rd_set_state(rd_handle* h, const double* u, const double* v, int on_device);
+int rd_read_state(rd_handle* h, double* u, double* v, int on_device);
+/* nsteps IMEX steps; cycles (host, may be NULL) receives [step][2*n_inst]
+ * V-cycles (species-major: u of every instance, then v).  Synchronous. */
+int rd_step(rd_handle* h, int nsteps, int* cycles);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,300 @@
+"""Python binding of the amrvac_gb300 C ABI (include/amrvac_gb300.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Loading fails loudly if the library has not been built; there is no CPU path.
+Arrays may be numpy (host) or torch CUDA tensors (device, float64, contiguous).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+AMR_OK = 0
+STATUS = {0: "AMR_OK", -1: "AMR_ERR_INVALID_ARG", -2: "AMR_ERR_OOM", -3: "AMR_ERR_CUDA",
+          -4: "AMR_ERR_NONPHYSICAL", -5: "AMR_ERR_TIMEOUT", -6: "MG_ERR_NOT_CONVERGED",
+          -7: "AMR_ERR_CAPACITY", -8: "AMR_ERR_UNBALANCED"}
+FLUX = {"tvdlf": 0, "hll": 1, "hllc": 2}
+LIMITER = {"minmod": 0, "vanleer": 1, "koren": 2, "none": 3}
+BC = {"periodic": 0, "outflow": 1}
+PRECISION = {"fp64": 0, "fp32": 1}
+
+
+class AmrError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+
+
+class AmrConfig(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int), ("block_nx", C.c_int), ("base_nblocks", C.c_int * 3), ("max_level", C.c_int),
+        ("xmin", C.c_double * 3), ("xmax", C.c_double * 3), ("gamma", C.c_double),
+        ("flux", C.c_int), ("limiter", C.c_int), ("rk", C.c_int), ("cfl", C.c_double),
+        ("bc", (C.c_int * 2) * 3), ("precision", C.c_int), ("refine_tol", C.c_double),
+        ("coarsen_frac", C.c_double), ("wavefilter", C.c_double), ("refine_var_mask", C.c_uint),
+        ("max_blocks", C.c_longlong), ("stream", C.c_void_p),
+    ]
+
+
+class MgConfig(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int), ("n_inst", C.c_int), ("n_cells", C.POINTER(C.c_int)),
+        ("lam", C.POINTER(C.c_double)), ("L", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
+        ("max_cycles", C.c_int), ("rtol", C.c_double), ("coarse_max", C.c_int), ("precision", C.c_int),
+        ("stream", C.c_void_p),
+    ]
+
+
+class RdConfig(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int), ("n_inst", C.c_int), ("n_cells", C.POINTER(C.c_int)), ("L", C.c_double),
+        ("Du", C.c_double), ("Dv", C.c_double), ("F", C.c_double), ("k", C.c_double), ("dt", C.c_double),
+        ("nu1", C.c_int), ("nu2", C.c_int), ("max_cycles", C.c_int), ("rtol", C.c_double),
+        ("coarse_max", C.c_int), ("precision", C.c_int), ("stream", C.c_void_p),
+    ]
+
+
+_vp, _dp, _ip, _llp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_longlong)
+
+_SIGS = {
+    "amr_create": ([C.POINTER(AmrConfig), C.POINTER(_vp)], C.c_int),
+    "amr_destroy": ([_vp], C.c_int),
+    "amr_last_error": ([_vp], C.c_char_p),
+    "amr_num_leaves": ([_vp, _llp], C.c_int),
+    "amr_leaf_info": ([_vp, _ip, _ip, C.c_longlong], C.c_int),
+    "amr_set_leaves": ([_vp, C.c_longlong, _ip, _ip], C.c_int),
+    "amr_set_state": ([_vp, _vp, C.c_longlong, C.c_int, C.c_int], C.c_int),
+    "amr_read_state": ([_vp, _vp, C.c_longlong, C.c_int], C.c_int),
+    "amr_set_time": ([_vp, C.c_double], C.c_int),
+    "amr_step": ([_vp, C.c_double, _dp, _dp], C.c_int),
+    "amr_run": ([_vp, C.c_int, C.c_double], C.c_int),
+    "amr_sync": ([_vp, _dp, _dp], C.c_int),
+    "amr_estimate": ([_vp, _dp, C.c_longlong], C.c_int),
+    "amr_regrid": ([_vp], C.c_int),
+    "amr_conserved_totals": ([_vp, _dp], C.c_int),
+    "amr_face_neighbors": ([_vp, _ip, _ip, C.c_longlong], C.c_int),
+    "amr_face_ghosts": ([_vp, C.c_longlong, _dp, C.c_longlong], C.c_int),
+    "amr_kernel_launches": ([_vp, _llp], C.c_int),
+    "mg_create": ([C.POINTER(MgConfig), C.POINTER(_vp)], C.c_int),
+    "mg_destroy": ([_vp], C.c_int),
+    "mg_last_error": ([_vp], C.c_char_p),
+    "mg_solve": ([_vp, _vp, _vp, C.c_int, _ip, _dp], C.c_int),
+    "mg_num_unknowns": ([_vp, _llp], C.c_int),
+    "rd_create": ([C.POINTER(RdConfig), C.POINTER(_vp)], C.c_int),
+    "rd_destroy": ([_vp], C.c_int),
+    "rd_last_error": ([_vp], C.c_char_p),
+    "rd_set_state": ([_vp, _vp, _vp, C.c_int], C.c_int),
+    "rd_read_state": ([_vp, _vp, _vp, C.c_int], C.c_int),
+    "rd_step": ([_vp, C.c_int, _ip], C.c_int),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load the CUDA library; raises if it is missing (no fallback)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+            _build.build()
+        L = C.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            if hasattr(L, name):
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(a):
+    """(address, on_device) of a numpy array or a torch tensor."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data, 0
+
+
+def _check(rc, h, errfn="amr_last_error"):
+    if rc != AMR_OK:
+        msg = ""
+        if h:
+            m = getattr(load(), errfn)(h)
+            msg = m.decode() if m else ""
+        raise AmrError(rc, msg)
+
+
+def make_amr_config(ndim, block_nx, base, max_level=1, xmin=(0, 0, 0), xmax=(1, 1, 1), gamma=1.4,
+                    flux="hllc", limiter="vanleer", rk=3, cfl=0.8, bc="periodic", precision="fp64",
+                    refine_tol=0.2, coarsen_frac=0.5, wavefilter=0.01, var_mask=None, max_blocks=None,
+                    stream=None):
+    c = AmrConfig()
+    c.ndim = ndim
+    c.block_nx = block_nx
+    base = list(base) + [1] * (3 - len(base))
+    for d in range(3):
+        c.base_nblocks[d] = base[d]
+        c.xmin[d] = float(xmin[d]) if d < len(xmin) else 0.0
+        c.xmax[d] = float(xmax[d]) if d < len(xmax) else 1.0
+    c.max_level = max_level
+    c.gamma = gamma
+    c.flux = FLUX[flux] if isinstance(flux, str) else flux
+    c.limiter = LIMITER[limiter] if isinstance(limiter, str) else limiter
+    c.rk = rk
+    c.cfl = cfl
+    if isinstance(bc, str):
+        bc = [[bc, bc]] * 3
+    for d in range(3):
+        for s in range(2):
+            b = bc[d][s] if d < len(bc) else "periodic"
+            c.bc[d][s] = BC[b] if isinstance(b, str) else b
+    c.precision = PRECISION[precision] if isinstance(precision, str) else precision
+    c.refine_tol = refine_tol
+    c.coarsen_frac = coarsen_frac
+    c.wavefilter = wavefilter
+    c.refine_var_mask = var_mask if var_mask is not None else (1 | (1 << (ndim + 1)))
+    nbase = int(np.prod(base[:ndim]))
+    c.max_blocks = max_blocks if max_blocks is not None else nbase * (2 ** ndim) ** (max_level - 1)
+    c.stream = stream
+    return c
+
+
+class AmrSolver:
+    """Owns one amr_handle.  Methods map one to one onto the C calls."""
+
+    def __init__(self, **kw):
+        self.lib = load()
+        self.cfg = make_amr_config(**kw)
+        self.ndim = self.cfg.ndim
+        self.nv = self.ndim + 2
+        self.ncell = self.cfg.block_nx ** self.ndim
+        h = _vp()
+        rc = self.lib.amr_create(C.byref(self.cfg), C.byref(h))
+        if rc != AMR_OK:
+            raise AmrError(rc, "amr_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.amr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nleaves(self):
+        n = C.c_longlong()
+        _check(self.lib.amr_num_leaves(self.h, C.byref(n)), self.h)
+        return n.value
+
+    def leaves(self):
+        n = self.nleaves
+        lev = np.zeros(n, dtype=np.int32)
+        crd = np.zeros((n, 3), dtype=np.int32)
+        _check(self.lib.amr_leaf_info(self.h, lev.ctypes.data_as(_ip), crd.ctypes.data_as(_ip), n), self.h)
+        return lev, crd
+
+    def set_leaves(self, level, coords):
+        level = np.ascontiguousarray(level, dtype=np.int32)
+        coords = np.ascontiguousarray(coords, dtype=np.int32).reshape(-1, 3)
+        _check(self.lib.amr_set_leaves(self.h, len(level), level.ctypes.data_as(_ip), coords.ctypes.data_as(_ip)),
+               self.h)
+
+    def set_state(self, W, primitive=True):
+        if not hasattr(W, "data_ptr"):
+            W = np.ascontiguousarray(W, dtype=np.float64)
+        p, dev = _ptr(W)
+        n = W.numel() if hasattr(W, "numel") else W.size
+        _check(self.lib.amr_set_state(self.h, p, n, dev, 1 if primitive else 0), self.h)
+
+    def set_prim(self, V):
+        self.set_state(V, primitive=True)
+
+    def set_cons(self, U):
+        self.set_state(U, primitive=False)
+
+    def read_state(self, out=None):
+        n = self.nleaves * self.nv * self.ncell
+        if out is None:
+            out = np.zeros((self.nleaves, self.nv, self.ncell))
+        p, dev = _ptr(out)
+        _check(self.lib.amr_read_state(self.h, p, n, dev), self.h)
+        return out
+
+    get_cons = read_state
+
+    def set_time(self, t):
+        _check(self.lib.amr_set_time(self.h, t), self.h)
+
+    def step(self, t_end=1e300):
+        dt, t = C.c_double(), C.c_double()
+        _check(self.lib.amr_step(self.h, t_end, C.byref(dt), C.byref(t)), self.h)
+        return dt.value
+
+    def run(self, nsteps, t_end=1e300):
+        _check(self.lib.amr_run(self.h, nsteps, t_end), self.h)
+
+    def sync(self):
+        t, dt = C.c_double(), C.c_double()
+        _check(self.lib.amr_sync(self.h, C.byref(t), C.byref(dt)), self.h)
+        return t.value, dt.value
+
+    @property
+    def t(self):
+        return self.sync()[0]
+
+    def totals(self):
+        out = np.zeros(self.nv)
+        _check(self.lib.amr_conserved_totals(self.h, out.ctypes.data_as(_dp)), self.h)
+        return out
+
+    def estimate(self):
+        e = np.zeros(self.nleaves)
+        _check(self.lib.amr_estimate(self.h, e.ctypes.data_as(_dp), len(e)), self.h)
+        return e
+
+    lohner = estimate
+
+    def regrid(self):
+        _check(self.lib.amr_regrid(self.h), self.h)
+        return self.nleaves
+
+    def face_neighbors(self):
+        n = self.nleaves * 2 * self.ndim
+        kind = np.zeros(n, dtype=np.int32)
+        nbr = np.zeros(n, dtype=np.int32)
+        _check(self.lib.amr_face_neighbors(self.h, kind.ctypes.data_as(_ip), nbr.ctypes.data_as(_ip), n), self.h)
+        return kind.reshape(-1, 2 * self.ndim), nbr.reshape(-1, 2 * self.ndim)
+
+    def face_ghosts(self, leaf):
+        nt = self.cfg.block_nx ** (self.ndim - 1)
+        out = np.zeros((self.nv, 2 * self.ndim, 2, nt))
+        _check(self.lib.amr_face_ghosts(self.h, leaf, out.ctypes.data_as(_dp), out.size), self.h)
+        return out
+
+    def kernel_launches(self):
+        n = C.c_longlong()
+        _check(self.lib.amr_kernel_launches(self.h, C.byref(n)), self.h)
+        return n.value

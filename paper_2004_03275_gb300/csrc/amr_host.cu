@@ -1,0 +1,906 @@
+// Host side of the block-tree Euler solver: the quadtree/octree of leaves
+// (Morton order, hash lookup), face-neighbour / ghost-slab / reflux tables,
+// refine-coarsen decisions with 2:1 balance, CUDA-graph step capture, and the
+// amr_* C ABI.
+//
+// Paper: Sec. 1.3 (block tree, refinement ratio 2, refine when one cell
+// exceeds the tolerance, coarsen when every cell is below a fraction of it);
+// Sec. 1.2 (CFL step); Sec. 2.3.2 / 2.4 (SSP Runge-Kutta stages).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstddef>
+#include <cstdint>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "../../include/amrvac_gb300.h"
+#include "euler_ops.h"
+
+using namespace amrgpu;
+
+namespace {
+
+// ------------------------------------------------------------------ tree --
+struct LeafH {
+  int level;
+  int c[3];
+};
+
+struct Tree {
+  int nd = 2, B = 16, maxlev = 1;
+  int base[3] = {1, 1, 1};
+  bool periodic[3] = {true, true, true};
+  std::vector<LeafH> leaves;
+  std::unordered_map<uint64_t, int> index;
+
+  static uint64_t key(int l, const int* c) {
+    return ((uint64_t)l << 59) | ((uint64_t)c[0] << 40) | ((uint64_t)c[1] << 20) | (uint64_t)c[2];
+  }
+  int nblk(int l, int d) const { return d < nd ? base[d] << (l - 1) : 1; }
+  int find(int l, const int* c) const {
+    if (l < 1 || l > maxlev) return -1;
+    for (int d = 0; d < nd; ++d)
+      if (c[d] < 0 || c[d] >= nblk(l, d)) return -1;
+    auto it = index.find(key(l, c));
+    return it == index.end() ? -1 : it->second;
+  }
+  // wrap block coordinates of level l into the domain; false if outside a non-periodic side
+  bool wrap(int l, int* c) const {
+    for (int d = 0; d < nd; ++d) {
+      int N = nblk(l, d);
+      if (c[d] < 0 || c[d] >= N) {
+        if (!periodic[d]) return false;
+        c[d] = ((c[d] % N) + N) % N;
+      }
+    }
+    return true;
+  }
+  uint64_t morton(const LeafH& L) const {
+    uint64_t X[3] = {0, 0, 0};
+    for (int d = 0; d < nd; ++d) X[d] = (uint64_t)L.c[d] << (maxlev - L.level);
+    uint64_t k = 0;
+    for (int b = 20; b >= 0; --b)
+      for (int d = nd - 1; d >= 0; --d) k = (k << 1) | ((X[d] >> b) & 1u);
+    return k;
+  }
+  // sorts leaves by Morton key; returns the permutation new -> old
+  std::vector<int> sort_and_index() {
+    std::vector<std::pair<uint64_t, int>> ks(leaves.size());
+    for (size_t i = 0; i < leaves.size(); ++i) ks[i] = {morton(leaves[i]), (int)i};
+    std::sort(ks.begin(), ks.end());
+    std::vector<LeafH> sorted(leaves.size());
+    std::vector<int> perm(leaves.size());
+    for (size_t i = 0; i < ks.size(); ++i) {
+      sorted[i] = leaves[ks[i].second];
+      perm[i] = ks[i].second;
+    }
+    leaves.swap(sorted);
+    index.clear();
+    for (size_t i = 0; i < leaves.size(); ++i) index[key(leaves[i].level, leaves[i].c)] = (int)i;
+    return perm;
+  }
+
+  // leaves touching block (l, c) (closed boxes, periodic images), excluding the
+  // block itself; the block need not be a leaf.  Relies on 2:1 balance only to
+  // bound the search depth.
+  void cover(int l, const int* n, const int* delta, std::unordered_set<int>& out) const {
+    for (int L = l; L >= 1; --L) {
+      int a[3] = {0, 0, 0};
+      for (int d = 0; d < nd; ++d) a[d] = n[d] >> (l - L);
+      int j = find(L, a);
+      if (j >= 0) {
+        out.insert(j);
+        return;
+      }
+    }
+    if (l >= maxlev) return;
+    for (int o = 0; o < (1 << nd); ++o) {
+      bool ok = true;
+      int ch[3] = {0, 0, 0};
+      for (int d = 0; d < nd; ++d) {
+        int od = (o >> d) & 1;
+        if (delta[d] == 1 && od != 0) ok = false;
+        if (delta[d] == -1 && od != 1) ok = false;
+        ch[d] = 2 * n[d] + od;
+      }
+      if (ok) cover(l + 1, ch, delta, out);
+    }
+  }
+  void touching(int l, const int* c, std::unordered_set<int>& out, int self) const {
+    int tot = 1;
+    for (int d = 0; d < nd; ++d) tot *= 3;
+    for (int q = 0; q < tot; ++q) {
+      int delta[3] = {0, 0, 0}, r = q;
+      bool zero = true;
+      for (int d = 0; d < nd; ++d) {
+        delta[d] = r % 3 - 1;
+        r /= 3;
+        if (delta[d]) zero = false;
+      }
+      if (zero) continue;
+      int n[3] = {c[0], c[1], c[2]};
+      for (int d = 0; d < nd; ++d) n[d] += delta[d];
+      if (!wrap(l, n)) continue;
+      cover(l, n, delta, out);
+    }
+    out.erase(self);
+  }
+};
+
+struct Tables {
+  std::vector<int> nb, kind, nbr, ffx;
+  std::vector<SlabDesc> slabs;
+  std::vector<RefluxRec> rec;
+  int nslots = 0;
+};
+
+// Face-neighbour codes, ghost slabs at level jumps and reflux records.
+bool build_tables(const Tree& T, Tables& tb, std::string* err) {
+  const int nd = T.nd, B = T.B, nf = 2 * nd;
+  size_t n = T.leaves.size();
+  tb.nb.assign(n * nf, -1);
+  tb.kind.assign(n * nf, -1);
+  tb.nbr.assign(n * nf, -1);
+  tb.ffx.assign(n * nf, -1);
+  tb.slabs.clear();
+  tb.rec.clear();
+  tb.nslots = 0;
+  auto slot = [&](int leaf, int face) {
+    int& s = tb.ffx[(size_t)leaf * nf + face];
+    if (s < 0) s = tb.nslots++;
+    return s;
+  };
+  for (size_t i = 0; i < n; ++i) {
+    const LeafH& L = T.leaves[i];
+    for (int f = 0; f < nf; ++f) {
+      int d = f >> 1, side = f & 1;
+      int c[3] = {L.c[0], L.c[1], L.c[2]};
+      c[d] += side ? 1 : -1;
+      size_t o = i * nf + f;
+      if (!T.wrap(L.level, c)) continue;  // outflow boundary
+      int j = T.find(L.level, c);
+      if (j >= 0) {
+        tb.nb[o] = j;
+        tb.kind[o] = 0;
+        tb.nbr[o] = j;
+        continue;
+      }
+      int e1 = -1, e2 = -1;
+      for (int e = 0; e < nd; ++e)
+        if (e != d) {
+          if (e1 < 0) e1 = e; else e2 = e;
+        }
+      int pc[3] = {c[0] >> 1, c[1] >> 1, c[2] >> 1};
+      int jc = L.level > 1 ? T.find(L.level - 1, pc) : -1;
+      if (jc >= 0) {
+        SlabDesc D{};
+        D.target = (int)i;
+        D.face = f;
+        D.kind = 1;
+        D.src[0] = jc;
+        D.off[0] = e1 >= 0 ? (L.c[e1] & 1) * (B / 2) : 0;
+        D.off[1] = e2 >= 0 ? (L.c[e2] & 1) * (B / 2) : 0;
+        tb.nb[o] = -2 - (int)tb.slabs.size();
+        tb.slabs.push_back(D);
+        tb.kind[o] = 1;
+        tb.nbr[o] = jc;
+        slot((int)i, f);
+        continue;
+      }
+      // finer neighbours
+      SlabDesc D{};
+      D.target = (int)i;
+      D.face = f;
+      D.kind = 0;
+      RefluxRec R{};
+      R.coarse = (int)i;
+      R.face = f;
+      int nq = 1 << (nd - 1);
+      for (int q = 0; q < nq; ++q) {
+        int ch[3] = {0, 0, 0};
+        ch[d] = 2 * c[d] + (side ? 0 : 1);
+        if (e1 >= 0) ch[e1] = 2 * c[e1] + (q & 1);
+        if (e2 >= 0) ch[e2] = 2 * c[e2] + ((q >> 1) & 1);
+        int jf = T.find(L.level + 1, ch);
+        if (jf < 0) {
+          if (err) *err = "tree is not 2:1 balanced or does not cover the domain";
+          return false;
+        }
+        D.src[q] = jf;
+        R.fslot[q] = slot(jf, f ^ 1);
+      }
+      R.cslot = slot((int)i, f);
+      tb.nb[o] = -2 - (int)tb.slabs.size();
+      tb.slabs.push_back(D);
+      tb.rec.push_back(R);
+      tb.kind[o] = 2;
+      tb.nbr[o] = D.src[0];
+    }
+  }
+  return true;
+}
+
+// ------------------------------------------------------------ device buf --
+struct DBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) cap = bytes;
+    return e;
+  }
+  template <typename T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+#define CK(call)                                             \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return h->fail_cuda(e_, #call);   \
+  } while (0)
+
+}  // namespace
+
+// ================================================================ handle ==
+struct amr_handle {
+  amr_config cfg{};
+  std::string err;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int nd = 2, B = 16, nv = 4, nc = 256, nt = 16;
+  size_t wbytes = 4;
+  Tree tree;
+  Tables tb;
+  Geometry G{};
+  // device state
+  DBuf U0, Ua, Ub, Unew, stagebuf, partials, ctl, nb, level, ffx, slabdesc, slabbuf, rec, fflux, ops, errbuf;
+  DevCtl* h_ctl = nullptr;  // pinned mirror
+  long long steps_seen = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_kernels = 0;
+  long long launches = 0;
+
+  int fail(int code, const std::string& m) {
+    err = m;
+    return code;
+  }
+  int fail_cuda(cudaError_t e, const char* what) {
+    err = std::string("CUDA error ") + cudaGetErrorString(e) + " in " + what;
+    return AMR_ERR_CUDA;
+  }
+  size_t state_bytes(size_t nleaves) const { return nleaves * nv * nc * wbytes; }
+
+  void drop_graph() {
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+  }
+
+  template <typename real, int ND>
+  int dispatch_stage(const StageArgs<real>& a) {
+    amr_handle* h = this;
+    CK((EulerOps<real, ND>::stage(B, cfg.flux, a, G, stream)));
+    ++launches;
+    return AMR_OK;
+  }
+
+  // ---- the per-precision, per-dimension operations
+  template <typename real, int ND>
+  int enqueue_step() {
+    amr_handle* h = this;
+    const int nl = (int)tree.leaves.size();
+    const bool jumps = !tb.slabs.empty();
+    real* s0 = U0.as<real>();
+    real* sa = Ua.as<real>();
+    real* sb = Ub.as<real>();
+    const int nst = cfg.rk == AMR_SSPRK2 ? 2 : 3;
+    const real w2a[2] = {real(0.5), real(0.5)};
+    const real w3a[3][2] = {{real(0), real(1)}, {real(0.75), real(0.25)}, {real(1.0 / 3.0), real(2.0 / 3.0)}};
+    for (int s = 0; s < nst; ++s) {
+      const real* Us = s == 0 ? s0 : (s == 1 ? sa : sb);
+      real* out = s == 0 ? sa : (s == 1 ? (nst == 3 ? sb : s0) : s0);
+      real alpha = s == 0 ? real(0) : (nst == 2 ? w2a[0] : w3a[s][0]);
+      real beta = s == 0 ? real(1) : (nst == 2 ? w2a[1] : w3a[s][1]);
+      if (jumps) {
+        CK((EulerOps<real, ND>::ghost_fill(B, Us, slabbuf.as<real>(), slabdesc.as<SlabDesc>(),
+                                           (int)tb.slabs.size(), stream)));
+        ++launches;
+      }
+      StageArgs<real> a{};
+      a.Us = Us;
+      a.U0 = s0;
+      a.out = out;
+      a.nb = nb.as<int>();
+      a.slabs = slabbuf.as<real>();
+      a.level = level.as<int>();
+      a.ffx = ffx.as<int>();
+      a.fflux = fflux.as<real>();
+      a.ctl = ctl.as<DevCtl>();
+      a.partials = partials.as<double>();
+      a.alpha = alpha;
+      a.beta = beta;
+      a.stage1 = s == 0;
+      a.fuse_reduce = (s == nst - 1) && !jumps;
+      a.has_ffx = jumps;
+      a.limiter = cfg.limiter;
+      a.nleaves = nl;
+      int rc = dispatch_stage<real, ND>(a);
+      if (rc) return rc;
+      if (jumps) {
+        CK((EulerOps<real, ND>::reflux(B, out, fflux.as<real>(), rec.as<RefluxRec>(), (int)tb.rec.size(),
+                                       level.as<int>(), G, ctl.as<DevCtl>(), beta, stream)));
+        ++launches;
+      }
+    }
+    if (jumps) {
+      CK((EulerOps<real, ND>::reduce(B, s0, level.as<int>(), G, ctl.as<DevCtl>(), partials.as<double>(), nl, 1,
+                                     stream)));
+      ++launches;
+    }
+    return AMR_OK;
+  }
+
+  template <typename real, int ND>
+  int ghost_fill_current(const real* U) {
+    amr_handle* h = this;
+    if (tb.slabs.empty()) return AMR_OK;
+    CK((EulerOps<real, ND>::ghost_fill(B, U, slabbuf.as<real>(), slabdesc.as<SlabDesc>(), (int)tb.slabs.size(),
+                                       stream)));
+    ++launches;
+    return AMR_OK;
+  }
+
+  int run_typed(const char* what);
+};
+
+namespace {
+
+template <typename F>
+int with_type(amr_handle* h, F&& f) {
+  if (h->cfg.precision == AMR_FP64) {
+    switch (h->nd) {
+      case 1: return f.template operator()<double, 1>();
+      case 2: return f.template operator()<double, 2>();
+      default: return f.template operator()<double, 3>();
+    }
+  }
+  switch (h->nd) {
+    case 1: return f.template operator()<float, 1>();
+    case 2: return f.template operator()<float, 2>();
+    default: return f.template operator()<float, 3>();
+  }
+}
+
+int upload_tables(amr_handle* h) {
+  auto& tb = h->tb;
+  auto& T = h->tree;
+  size_t n = T.leaves.size();
+  int nf = 2 * h->nd;
+  std::vector<int> lev(n);
+  for (size_t i = 0; i < n; ++i) lev[i] = T.leaves[i].level;
+#define CKH(call)                                               \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return h->fail_cuda(e_, #call);      \
+  } while (0)
+  CKH(h->nb.ensure(std::max<size_t>(1, n * nf) * sizeof(int)));
+  CKH(h->ffx.ensure(std::max<size_t>(1, n * nf) * sizeof(int)));
+  CKH(h->level.ensure(std::max<size_t>(1, n) * sizeof(int)));
+  CKH(h->slabdesc.ensure(std::max<size_t>(1, tb.slabs.size()) * sizeof(SlabDesc)));
+  CKH(h->slabbuf.ensure(std::max<size_t>(1, tb.slabs.size()) * h->nv * 2 * h->nt * h->wbytes));
+  CKH(h->rec.ensure(std::max<size_t>(1, tb.rec.size()) * sizeof(RefluxRec)));
+  CKH(h->fflux.ensure(std::max<size_t>(1, (size_t)tb.nslots) * h->nv * h->nt * h->wbytes));
+  CKH(h->partials.ensure(std::max<size_t>(1, n) * h->nv * sizeof(double)));
+  CKH(h->errbuf.ensure(std::max<size_t>(1, n) * sizeof(double)));
+  CKH(cudaMemcpyAsync(h->nb.p, tb.nb.data(), n * nf * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  CKH(cudaMemcpyAsync(h->ffx.p, tb.ffx.data(), n * nf * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  CKH(cudaMemcpyAsync(h->level.p, lev.data(), n * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  if (!tb.slabs.empty())
+    CKH(cudaMemcpyAsync(h->slabdesc.p, tb.slabs.data(), tb.slabs.size() * sizeof(SlabDesc), cudaMemcpyHostToDevice,
+                        h->stream));
+  if (!tb.rec.empty())
+    CKH(cudaMemcpyAsync(h->rec.p, tb.rec.data(), tb.rec.size() * sizeof(RefluxRec), cudaMemcpyHostToDevice,
+                        h->stream));
+  CKH(cudaStreamSynchronize(h->stream));
+  h->G.nleaves = (int)n;
+  h->drop_graph();
+  return AMR_OK;
+}
+
+int rebuild(amr_handle* h) {
+  std::string e;
+  if (!build_tables(h->tree, h->tb, &e)) return h->fail(AMR_ERR_UNBALANCED, e);
+  return upload_tables(h);
+}
+
+// recompute dt_cfl and totals of the current state (no time advance)
+int refresh_reduce(amr_handle* h) {
+  int nl = (int)h->tree.leaves.size();
+  return with_type(h, [&]<typename real, int ND>() -> int {
+    cudaError_t e = EulerOps<real, ND>::reduce(h->B, h->U0.as<real>(), h->level.as<int>(), h->G,
+                                               h->ctl.as<DevCtl>(), h->partials.as<double>(), nl, 0, h->stream);
+    if (e != cudaSuccess) return h->fail_cuda(e, "reduce");
+    ++h->launches;
+    return AMR_OK;
+  });
+}
+
+int sync_ctl(amr_handle* h) {
+  CKH(cudaMemcpyAsync(h->h_ctl, h->ctl.p, sizeof(DevCtl), cudaMemcpyDeviceToHost, h->stream));
+  CKH(cudaStreamSynchronize(h->stream));
+  if (h->h_ctl->status & 1) return h->fail(AMR_ERR_NONPHYSICAL, "non-positive density or pressure met");
+  return AMR_OK;
+}
+
+bool balanced_cover(const Tree& T, std::string* err) {
+  // volume check + pairwise 2:1 check through touching()
+  long double vol = 0, tot = 1;
+  for (int d = 0; d < T.nd; ++d) tot *= (long double)T.base[d] * (1 << (T.maxlev - 1));
+  for (auto& L : T.leaves) {
+    long double v = 1;
+    for (int d = 0; d < T.nd; ++d) v *= (long double)(1 << (T.maxlev - L.level));
+    vol += v;
+  }
+  if (vol != tot) {
+    *err = "leaves do not cover the domain exactly";
+    return false;
+  }
+  for (size_t i = 0; i < T.leaves.size(); ++i) {
+    std::unordered_set<int> t;
+    T.touching(T.leaves[i].level, T.leaves[i].c, t, (int)i);
+    for (int j : t)
+      if (std::abs(T.leaves[j].level - T.leaves[i].level) > 1) {
+        *err = "leaves are not 2:1 balanced";
+        return false;
+      }
+  }
+  return true;
+}
+
+}  // namespace
+
+// ================================================================== ABI ==
+extern "C" {
+
+int amr_create(const amr_config* cfg, amr_handle** out) {
+  if (!cfg || !out) return AMR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (cfg->ndim < 1 || cfg->ndim > 3) return AMR_ERR_INVALID_ARG;
+  if (cfg->block_nx != 8 && cfg->block_nx != 16) return AMR_ERR_INVALID_ARG;
+  if (cfg->max_level < 1 || cfg->max_level > kMaxLevel) return AMR_ERR_INVALID_ARG;
+  if (cfg->flux < 0 || cfg->flux > 2 || cfg->limiter < 0 || cfg->limiter > 3) return AMR_ERR_INVALID_ARG;
+  if (cfg->rk != AMR_SSPRK2 && cfg->rk != AMR_SSPRK3) return AMR_ERR_INVALID_ARG;
+  if (cfg->precision != AMR_FP64 && cfg->precision != AMR_FP32) return AMR_ERR_INVALID_ARG;
+  if (!(cfg->gamma > 1.0) || !(cfg->cfl > 0.0)) return AMR_ERR_INVALID_ARG;
+  long long nbase = 1;
+  for (int d = 0; d < cfg->ndim; ++d) {
+    if (cfg->base_nblocks[d] < 1 || !(cfg->xmax[d] > cfg->xmin[d])) return AMR_ERR_INVALID_ARG;
+    if ((long long)cfg->base_nblocks[d] << (cfg->max_level - 1) >= (1LL << 19)) return AMR_ERR_INVALID_ARG;
+    if ((cfg->bc[d][0] == AMR_BC_PERIODIC) != (cfg->bc[d][1] == AMR_BC_PERIODIC)) return AMR_ERR_INVALID_ARG;
+    nbase *= cfg->base_nblocks[d];
+  }
+  if (cfg->max_blocks < nbase) return AMR_ERR_CAPACITY;
+  std::unique_ptr<amr_handle> h(new amr_handle());
+  h->cfg = *cfg;
+  h->stream = (cudaStream_t)cfg->stream;
+  if (!h->stream) {  // graph capture needs a non-legacy stream
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) return AMR_ERR_CUDA;
+    h->own_stream = true;
+  }
+  h->nd = cfg->ndim;
+  h->B = cfg->block_nx;
+  h->nv = cfg->ndim + 2;
+  h->nc = 1;
+  for (int d = 0; d < h->nd; ++d) h->nc *= h->B;
+  h->nt = h->nc / h->B;
+  h->wbytes = cfg->precision == AMR_FP64 ? 8 : 4;
+  Tree& T = h->tree;
+  T.nd = h->nd;
+  T.B = h->B;
+  T.maxlev = cfg->max_level;
+  for (int d = 0; d < 3; ++d) {
+    T.base[d] = d < h->nd ? cfg->base_nblocks[d] : 1;
+    T.periodic[d] = d < h->nd ? cfg->bc[d][0] == AMR_BC_PERIODIC : true;
+  }
+  for (int z = 0; z < T.nblk(1, 2); ++z)
+    for (int y = 0; y < T.nblk(1, 1); ++y)
+      for (int x = 0; x < T.nblk(1, 0); ++x) T.leaves.push_back(LeafH{1, {x, y, z}});
+  T.sort_and_index();
+  // geometry
+  Geometry& G = h->G;
+  G.ndim = h->nd;
+  G.bnx = h->B;
+  G.gamma = cfg->gamma;
+  G.cfl = cfg->cfl;
+  for (int l = 1; l <= kMaxLevel; ++l) {
+    double dV = 1.0;
+    for (int d = 0; d < 3; ++d) {
+      double n = d < h->nd ? (double)cfg->base_nblocks[d] * h->B * (double)(1LL << (l - 1)) : 1.0;
+      G.dx[l][d] = d < h->nd ? (cfg->xmax[d] - cfg->xmin[d]) / n : 1.0;
+      if (d < h->nd) dV = dV * G.dx[l][d];
+    }
+    G.dV[l] = dV;
+  }
+  size_t sb = h->state_bytes((size_t)cfg->max_blocks);
+  cudaError_t e;
+  if ((e = h->U0.ensure(sb)) != cudaSuccess || (e = h->Ua.ensure(sb)) != cudaSuccess ||
+      (e = h->Ub.ensure(sb)) != cudaSuccess || (e = h->ctl.ensure(sizeof(DevCtl))) != cudaSuccess ||
+      (e = cudaMallocHost(&h->h_ctl, sizeof(DevCtl))) != cudaSuccess)
+    return e == cudaErrorMemoryAllocation ? AMR_ERR_OOM : AMR_ERR_CUDA;
+  DevCtl c0{};
+  c0.cfl = cfg->cfl;
+  c0.t_end = 1e300;
+  if (cudaMemcpy(h->ctl.p, &c0, sizeof(DevCtl), cudaMemcpyHostToDevice) != cudaSuccess) return AMR_ERR_CUDA;
+  if (cudaMemset(h->U0.p, 0, h->state_bytes(T.leaves.size())) != cudaSuccess) return AMR_ERR_CUDA;
+  int rc = rebuild(h.get());
+  if (rc) return rc;
+  amr_handle* hp = h.get();
+  rc = with_type(hp, [&]<typename real, int ND>() -> int {
+    cudaError_t e2 = EulerOps<real, ND>::prepare(hp->B, hp->cfg.flux);
+    return e2 == cudaSuccess ? AMR_OK : hp->fail_cuda(e2, "prepare");
+  });
+  if (rc) return rc;
+  *out = h.release();
+  return AMR_OK;
+}
+
+int amr_destroy(amr_handle* h) {
+  if (!h) return AMR_ERR_INVALID_ARG;
+  h->drop_graph();
+  for (DBuf* b : {&h->U0, &h->Ua, &h->Ub, &h->Unew, &h->stagebuf, &h->partials, &h->ctl, &h->nb, &h->level,
+                  &h->ffx, &h->slabdesc, &h->slabbuf, &h->rec, &h->fflux, &h->ops, &h->errbuf})
+    b->release();
+  if (h->h_ctl) cudaFreeHost(h->h_ctl);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return AMR_OK;
+}
+
+const char* amr_last_error(const amr_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+int amr_num_leaves(const amr_handle* h, long long* n) {
+  if (!h || !n) return AMR_ERR_INVALID_ARG;
+  *n = (long long)h->tree.leaves.size();
+  return AMR_OK;
+}
+
+int amr_leaf_info(const amr_handle* h, int* level, int* coords, long long cap) {
+  if (!h || cap < (long long)h->tree.leaves.size()) return AMR_ERR_INVALID_ARG;
+  for (size_t i = 0; i < h->tree.leaves.size(); ++i) {
+    if (level) level[i] = h->tree.leaves[i].level;
+    if (coords)
+      for (int d = 0; d < 3; ++d) coords[3 * i + d] = h->tree.leaves[i].c[d];
+  }
+  return AMR_OK;
+}
+
+int amr_set_leaves(amr_handle* h, long long n, const int* level, const int* coords) {
+  if (!h || n < 1 || !level || !coords) return AMR_ERR_INVALID_ARG;
+  if (n > h->cfg.max_blocks) return h->fail(AMR_ERR_CAPACITY, "more leaves than max_blocks");
+  Tree T = h->tree;
+  T.leaves.clear();
+  for (long long i = 0; i < n; ++i) {
+    LeafH L{level[i], {coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]}};
+    if (L.level < 1 || L.level > T.maxlev) return h->fail(AMR_ERR_INVALID_ARG, "leaf level out of range");
+    for (int d = 0; d < 3; ++d) {
+      if (d >= T.nd) L.c[d] = 0;
+      else if (L.c[d] < 0 || L.c[d] >= T.nblk(L.level, d)) return h->fail(AMR_ERR_INVALID_ARG, "leaf outside domain");
+    }
+    T.leaves.push_back(L);
+  }
+  T.sort_and_index();
+  if (T.index.size() != T.leaves.size()) return h->fail(AMR_ERR_UNBALANCED, "duplicate leaves");
+  std::string e;
+  if (!balanced_cover(T, &e)) return h->fail(AMR_ERR_UNBALANCED, e);
+  h->tree = T;
+  int rc = rebuild(h);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(h->U0.p, 0, h->state_bytes(n), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return AMR_OK;
+}
+
+int amr_set_state(amr_handle* h, const double* W, long long n_values, int on_device, int primitive) {
+  if (!h || !W) return AMR_ERR_INVALID_ARG;
+  long long nl = (long long)h->tree.leaves.size();
+  long long need = nl * h->nv * h->nc;
+  if (n_values != need) return h->fail(AMR_ERR_INVALID_ARG, "n_values does not match leaves*(ndim+2)*cells");
+  const double* src = W;
+  if (!on_device) {
+    CK(h->stagebuf.ensure(need * sizeof(double)));
+    CK(cudaMemcpyAsync(h->stagebuf.p, W, need * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    src = h->stagebuf.as<double>();
+  }
+  int rc = with_type(h, [&]<typename real, int ND>() -> int {
+    cudaError_t e = EulerOps<real, ND>::set_state(h->B, src, h->U0.as<real>(), nl, primitive, h->cfg.gamma, h->stream);
+    if (e != cudaSuccess) return h->fail_cuda(e, "set_state");
+    ++h->launches;
+    return AMR_OK;
+  });
+  if (rc) return rc;
+  // clear the status word, then recompute dt and totals
+  CK(cudaMemsetAsync((char*)h->ctl.p + offsetof(DevCtl, status), 0, sizeof(int), h->stream));
+  rc = refresh_reduce(h);
+  if (rc) return rc;
+  return sync_ctl(h);
+}
+
+int amr_read_state(amr_handle* h, double* U, long long cap_values, int on_device) {
+  if (!h || !U) return AMR_ERR_INVALID_ARG;
+  long long nl = (long long)h->tree.leaves.size();
+  long long need = nl * h->nv * h->nc;
+  if (cap_values < need) return h->fail(AMR_ERR_INVALID_ARG, "output buffer too small");
+  double* dst = U;
+  if (!on_device) {
+    CK(h->stagebuf.ensure(need * sizeof(double)));
+    dst = h->stagebuf.as<double>();
+  }
+  int rc = with_type(h, [&]<typename real, int ND>() -> int {
+    cudaError_t e = EulerOps<real, ND>::read_state(h->U0.as<real>(), dst, need, h->stream);
+    if (e != cudaSuccess) return h->fail_cuda(e, "read_state");
+    ++h->launches;
+    return AMR_OK;
+  });
+  if (rc) return rc;
+  if (!on_device) CK(cudaMemcpyAsync(U, dst, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return AMR_OK;
+}
+
+int amr_set_time(amr_handle* h, double t) {
+  if (!h) return AMR_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync((char*)h->ctl.p + offsetof(DevCtl, t), &t, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return AMR_OK;
+}
+
+static int ensure_graph(amr_handle* h) {
+  if (h->graph) return AMR_OK;
+  cudaGraph_t g;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  long long before = h->launches;
+  int rc = with_type(h, [&]<typename real, int ND>() -> int { return h->enqueue_step<real, ND>(); });
+  cudaError_t ec = cudaStreamEndCapture(h->stream, &g);
+  if (rc) return rc;
+  if (ec != cudaSuccess) return h->fail_cuda(ec, "cudaStreamEndCapture");
+  h->graph_kernels = (int)(h->launches - before);
+  h->launches = before;
+  cudaError_t ei = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    h->graph = nullptr;
+    return h->fail_cuda(ei, "cudaGraphInstantiate");
+  }
+  return AMR_OK;
+}
+
+int amr_run(amr_handle* h, int nsteps, double t_end) {
+  if (!h || nsteps < 0) return AMR_ERR_INVALID_ARG;
+  int rc = ensure_graph(h);
+  if (rc) return rc;
+  CK(ctl_set_t_end(h->ctl.as<DevCtl>(), t_end, h->stream));
+  ++h->launches;
+  for (int i = 0; i < nsteps; ++i) {
+    CK(cudaGraphLaunch(h->graph, h->stream));
+    h->launches += h->graph_kernels;
+  }
+  return AMR_OK;
+}
+
+int amr_sync(amr_handle* h, double* t_now, double* dt_last) {
+  if (!h) return AMR_ERR_INVALID_ARG;
+  int rc = sync_ctl(h);
+  if (t_now) *t_now = h->h_ctl->t;
+  if (dt_last) *dt_last = h->h_ctl->dt_last;
+  h->steps_seen = h->h_ctl->steps;
+  return rc;
+}
+
+int amr_step(amr_handle* h, double t_end, double* dt_taken, double* t_now) {
+  if (!h) return AMR_ERR_INVALID_ARG;
+  long long before = h->steps_seen;
+  int rc = amr_run(h, 1, t_end);
+  if (rc) return rc;
+  double t, dtl;
+  rc = amr_sync(h, &t, &dtl);
+  if (t_now) *t_now = t;
+  if (dt_taken) *dt_taken = h->steps_seen > before ? dtl : 0.0;
+  return rc;
+}
+
+int amr_conserved_totals(amr_handle* h, double* totals) {
+  if (!h || !totals) return AMR_ERR_INVALID_ARG;
+  int rc = sync_ctl(h);
+  for (int v = 0; v < h->nv; ++v) totals[v] = h->h_ctl->totals[v];
+  return rc;
+}
+
+int amr_estimate(amr_handle* h, double* err, long long cap) {
+  long long nl = h ? (long long)h->tree.leaves.size() : 0;
+  if (!h || !err || cap < nl) return AMR_ERR_INVALID_ARG;
+  int rc = with_type(h, [&]<typename real, int ND>() -> int {
+    int r = h->ghost_fill_current<real, ND>(h->U0.as<real>());
+    if (r) return r;
+    cudaError_t e = EulerOps<real, ND>::lohner(h->B, h->U0.as<real>(), h->slabbuf.as<real>(), h->nb.as<int>(),
+                                               h->cfg.gamma, h->cfg.wavefilter, h->cfg.refine_var_mask,
+                                               h->errbuf.as<double>(), (int)nl, h->stream);
+    if (e != cudaSuccess) return h->fail_cuda(e, "lohner");
+    ++h->launches;
+    return AMR_OK;
+  });
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(err, h->errbuf.p, nl * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return AMR_OK;
+}
+
+// Refine / coarsen with 2:1 balance (Sec. 1.3); see the header for the rules.
+int amr_regrid(amr_handle* h) {
+  if (!h) return AMR_ERR_INVALID_ARG;
+  Tree& T = h->tree;
+  const int nd = T.nd;
+  size_t nl = T.leaves.size();
+  std::vector<double> err(nl);
+  int rc = amr_estimate(h, err.data(), (long long)nl);
+  if (rc) return rc;
+  std::vector<char> ref(nl, 0), crs(nl, 0);
+  for (size_t i = 0; i < nl; ++i) {
+    int lev = T.leaves[i].level;
+    if (lev < T.maxlev && err[i] > h->cfg.refine_tol) ref[i] = 1;
+    if (lev > 1 && err[i] < h->cfg.coarsen_frac * h->cfg.refine_tol) crs[i] = 1;
+  }
+  // refinement closes over coarser touching leaves
+  std::vector<int> work;
+  for (size_t i = 0; i < nl; ++i)
+    if (ref[i]) work.push_back((int)i);
+  while (!work.empty()) {
+    int i = work.back();
+    work.pop_back();
+    std::unordered_set<int> t;
+    T.touching(T.leaves[i].level, T.leaves[i].c, t, i);
+    for (int j : t)
+      if (!ref[j] && T.leaves[j].level < T.leaves[i].level) {
+        ref[j] = 1;
+        work.push_back(j);
+      }
+  }
+  // coarsening groups
+  int nch = 1 << nd;
+  std::vector<char> merged(nl, 0);
+  std::vector<std::vector<int>> groups;
+  for (size_t i = 0; i < nl; ++i) {
+    const LeafH& A = T.leaves[i];
+    if (A.level == 1) continue;
+    bool first = true;
+    for (int d = 0; d < nd; ++d)
+      if (A.c[d] & 1) first = false;
+    if (!first) continue;
+    std::vector<int> kids;
+    bool ok = true;
+    for (int o = 0; o < nch && ok; ++o) {
+      int c[3] = {A.c[0] + (o & 1), nd > 1 ? A.c[1] + ((o >> 1) & 1) : 0, nd > 2 ? A.c[2] + ((o >> 2) & 1) : 0};
+      int j = T.find(A.level, c);
+      if (j < 0 || ref[j] || !crs[j]) ok = false;
+      kids.push_back(j);
+    }
+    if (!ok) continue;
+    int pc[3] = {A.c[0] >> 1, A.c[1] >> 1, A.c[2] >> 1};
+    std::unordered_set<int> t;
+    T.touching(A.level - 1, pc, t, -1);
+    for (int j : t)
+      if (T.leaves[j].level + (ref[j] ? 1 : 0) > A.level) ok = false;
+    if (!ok) continue;
+    for (int k : kids) merged[k] = 1;
+    groups.push_back(kids);
+  }
+  // new leaves and the ops that fill them
+  Tree NT = T;
+  NT.leaves.clear();
+  std::vector<RegridOp> ops;
+  for (size_t i = 0; i < nl; ++i) {
+    const LeafH& L = T.leaves[i];
+    if (ref[i]) {
+      for (int o = 0; o < nch; ++o) {
+        LeafH C{L.level + 1, {0, 0, 0}};
+        for (int d = 0; d < nd; ++d) C.c[d] = 2 * L.c[d] + ((o >> d) & 1);
+        NT.leaves.push_back(C);
+        RegridOp op{};
+        op.kind = 1;
+        op.src[0] = (int)i;
+        op.child = o;
+        ops.push_back(op);
+      }
+    } else if (!merged[i]) {
+      NT.leaves.push_back(L);
+      RegridOp op{};
+      op.kind = 0;
+      op.src[0] = (int)i;
+      ops.push_back(op);
+    }
+  }
+  for (auto& g : groups) {
+    const LeafH& A = T.leaves[g[0]];
+    LeafH P{A.level - 1, {A.c[0] >> 1, A.c[1] >> 1, A.c[2] >> 1}};
+    NT.leaves.push_back(P);
+    RegridOp op{};
+    op.kind = 2;
+    for (int o = 0; o < nch; ++o) op.src[o] = g[o];
+    ops.push_back(op);
+  }
+  if ((long long)NT.leaves.size() > h->cfg.max_blocks)
+    return h->fail(AMR_ERR_CAPACITY, "regrid would exceed max_blocks");
+  std::vector<int> perm = NT.sort_and_index();
+  std::vector<RegridOp> sops(ops.size());
+  for (size_t i = 0; i < perm.size(); ++i) sops[i] = ops[perm[i]];
+  // device: ghosts of the old tree (parents' edge slopes), then build the new state
+  CK(h->ops.ensure(std::max<size_t>(1, sops.size()) * sizeof(RegridOp)));
+  CK(cudaMemcpyAsync(h->ops.p, sops.data(), sops.size() * sizeof(RegridOp), cudaMemcpyHostToDevice, h->stream));
+  rc = with_type(h, [&]<typename real, int ND>() -> int {
+    int r = h->ghost_fill_current<real, ND>(h->U0.as<real>());
+    if (r) return r;
+    cudaError_t e = EulerOps<real, ND>::regrid(h->B, h->U0.as<real>(), h->Ua.as<real>(), h->slabbuf.as<real>(),
+                                               h->nb.as<int>(), h->ops.as<RegridOp>(), (int)sops.size(), h->stream);
+    if (e != cudaSuccess) return h->fail_cuda(e, "regrid");
+    ++h->launches;
+    return AMR_OK;
+  });
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  std::swap(h->U0, h->Ua);
+  h->tree = NT;
+  rc = rebuild(h);
+  if (rc) return rc;
+  rc = refresh_reduce(h);
+  if (rc) return rc;
+  return sync_ctl(h);
+}
+
+int amr_face_neighbors(const amr_handle* h, int* kind, int* nbr, long long cap) {
+  if (!h) return AMR_ERR_INVALID_ARG;
+  size_t n = h->tb.kind.size();
+  if (cap < (long long)n) return AMR_ERR_INVALID_ARG;
+  if (kind) std::memcpy(kind, h->tb.kind.data(), n * sizeof(int));
+  if (nbr) std::memcpy(nbr, h->tb.nbr.data(), n * sizeof(int));
+  return AMR_OK;
+}
+
+int amr_face_ghosts(amr_handle* h, long long leaf, double* out, long long cap) {
+  if (!h || !out || leaf < 0 || leaf >= (long long)h->tree.leaves.size()) return AMR_ERR_INVALID_ARG;
+  long long need = (long long)h->nv * 2 * h->nd * 2 * h->nt;
+  if (cap < need) return AMR_ERR_INVALID_ARG;
+  CK(h->stagebuf.ensure(std::max<size_t>(h->stagebuf.cap, need * sizeof(double))));
+  int rc = with_type(h, [&]<typename real, int ND>() -> int {
+    int r = h->ghost_fill_current<real, ND>(h->U0.as<real>());
+    if (r) return r;
+    cudaError_t e = EulerOps<real, ND>::face_ghosts(h->B, h->U0.as<real>(), h->slabbuf.as<real>(), h->nb.as<int>(),
+                                                    (int)leaf, h->stagebuf.as<double>(), h->stream);
+    if (e != cudaSuccess) return h->fail_cuda(e, "face_ghosts");
+    ++h->launches;
+    return AMR_OK;
+  });
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(out, h->stagebuf.p, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return AMR_OK;
+}
+
+int amr_kernel_launches(const amr_handle* h, long long* n) {
+  if (!h || !n) return AMR_ERR_INVALID_ARG;
+  *n = h->launches;
+  return AMR_OK;
+}
+
+}  // extern "C"

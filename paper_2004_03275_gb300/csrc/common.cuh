@@ -1,0 +1,77 @@
+// Shared device-side types of the amrvac_gb300 library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace amrgpu {
+
+constexpr int kMaxLevel = 16;
+
+// Device control block of one solver: time, CFL step, reductions.  Written only
+// by the last CTA of a reduction pass (no spin waits anywhere).
+struct DevCtl {
+  double t;          // current time
+  double t_end;      // end time of the current run
+  double dt_cfl;     // cfl / max signal rate of the current state
+  double dt_last;    // dt of the last completed step
+  double cfl;
+  unsigned long long smax_bits;  // running max of the signal rate (bit pattern, >= 0)
+  unsigned int done;             // CTAs finished in the current reduction pass
+  int status;                    // bit 0: non-physical state met
+  long long steps;
+  double totals[5];
+};
+
+// Ghost slab of one leaf face at a level jump.
+struct SlabDesc {
+  int target;   // leaf owning the ghosts
+  int face;     // 2*dim + side
+  int kind;     // 0: restriction from finer leaves, 1: prolongation from a coarser leaf
+  int src[4];   // kind 0: fine leaf per tangential quadrant (q1 + 2 q2); kind 1: src[0] coarse leaf
+  int off[2];   // kind 1: tangential offset of the target inside the coarse face (coarse cells)
+};
+
+// Coarse side of a level jump: replace the coarse face flux by the mean of the fine ones.
+struct RefluxRec {
+  int coarse;   // coarse leaf
+  int face;     // its face
+  int cslot;    // face-flux slot written by the coarse leaf
+  int fslot[4]; // face-flux slots of the fine leaves per tangential quadrant
+};
+
+// New leaf after a regrid.
+struct RegridOp {
+  int kind;     // 0 copy, 1 prolong from parent, 2 restrict from children
+  int src[8];   // copy/prolong: src[0] old leaf; restrict: children in x-fastest order
+  int child;    // prolong: child offset bits (x | y<<1 | z<<2)
+};
+
+struct Geometry {
+  int ndim, bnx, nleaves;
+  double gamma, cfl;
+  double dx[kMaxLevel + 1][3];
+  double dV[kMaxLevel + 1];
+};
+
+// ------------------------------------------------------------ stage args --
+template <typename real>
+struct StageArgs {
+  const real* Us;      // U^(s), read with halos
+  const real* U0;      // U^n, read pointwise
+  real* out;           // U^(s+1)
+  const int* nb;       // [leaf][2*ndim] neighbour codes
+  const real* slabs;   // [slab][var][2][nt]
+  const int* level;    // [leaf]
+  const int* ffx;      // [leaf][2*ndim] face-flux slot or -1
+  real* fflux;         // [slot][var][nt]
+  DevCtl* ctl;
+  double* partials;    // [leaf][var]
+  real alpha, beta;    // out = alpha*U0 + beta*(Us - dt*div); alpha == 0: out = Us - dt*div
+  int stage1;
+  int fuse_reduce;     // fold max rate / totals / time update into this pass
+  int has_ffx;
+  int limiter;
+  int nleaves;
+};
+
+}  // namespace amrgpu

@@ -1,0 +1,5 @@
+// Explicit instantiation of the Euler device code for double, 1D.
+#include "euler_kernels.cuh"
+#include "euler_dispatch.cuh"
+
+template struct amrgpu::EulerOps<double, 1>;

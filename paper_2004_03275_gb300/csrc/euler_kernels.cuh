@@ -1,0 +1,1028 @@
+// Device code of the block-tree finite-volume Euler update, templated on the
+// arithmetic type.  Included by one translation unit per (type, dimension);
+// float units are compiled with fast division/sqrt, double units without FMA
+// contraction so that every rounding follows the written order.
+//
+// Paper (arXiv:2004.03275): Sec. 1.1 variables and flux split; Sec. 1.2 signal
+// speeds (phys_get_cmax/cbounds), TVDLF and HLL; Sec. 2.4 HLLC; Sec. 2.3.1
+// limited reconstruction (Koren); Sec. 2.3.2 / 2.4 SSP Runge-Kutta; Sec. 1.3
+// block tree with refinement ratio 2 and a Lohner-type estimator.
+//
+// State layout: U[leaf][var][cell], cell = i + B*(j + B*k), leaves in Morton
+// order.  A leaf's face ghosts (two layers) come from a same-level neighbour's
+// interior, from a ghost slab filled at a level jump, or from the leaf itself
+// (zero-gradient outflow).
+#pragma once
+#include "common.cuh"
+
+namespace amrgpu {
+
+enum { FLUX_TVDLF = 0, FLUX_HLL = 1, FLUX_HLLC = 2 };
+enum { LIM_MINMOD = 0, LIM_VANLEER = 1, LIM_KOREN = 2, LIM_NONE = 3 };
+
+// ------------------------------------------------------------------ physics --
+template <typename real, int ND>
+__device__ __forceinline__ void cons_to_prim(const real* U, real* V, real gm1) {
+  real rho = U[0];
+  real msq = real(0);
+#pragma unroll
+  for (int d = 0; d < ND; ++d) msq = msq + U[1 + d] * U[1 + d];
+  V[0] = rho;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) V[1 + d] = U[1 + d] / rho;
+  V[ND + 1] = gm1 * (U[ND + 1] - (real(0.5) * msq) / rho);
+}
+
+template <typename real, int ND>
+__device__ __forceinline__ void prim_to_cons(const real* V, real* U, real gm1) {
+  real rho = V[0];
+  real vsq = real(0);
+#pragma unroll
+  for (int d = 0; d < ND; ++d) vsq = vsq + V[1 + d] * V[1 + d];
+  U[0] = rho;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) U[1 + d] = rho * V[1 + d];
+  U[ND + 1] = V[ND + 1] / gm1 + (real(0.5) * rho) * vsq;
+}
+
+template <typename real>
+__device__ __forceinline__ real dsqrt(real x) { return sqrt(x); }
+
+// flux of the state V (conserved U precomputed) normal to `dir`
+template <typename real, int ND>
+__device__ __forceinline__ void phys_flux(int dir, const real* V, const real* U, real* F) {
+  real un = V[1 + dir];
+  real p = V[ND + 1];
+  F[0] = U[1 + dir];
+#pragma unroll
+  for (int e = 0; e < ND; ++e) {
+    F[1 + e] = U[1 + e] * un;
+    if (e == dir) F[1 + e] = F[1 + e] + p;
+  }
+  F[ND + 1] = (U[ND + 1] + p) * un;
+}
+
+// Approximate Riemann fluxes.  Wave-speed bounds: Davis estimates
+// S_L = min(u_L - c_L, u_R - c_R), S_R = max(u_L + c_L, u_R + c_R); HLLC with
+// Toro's contact speed S*; TVDLF with c_max = max(|u| + c).
+template <typename real, int ND, int FLUX>
+__device__ __forceinline__ void riemann(int dir, const real* VL, const real* VR, real gam, real gm1, real* F) {
+  constexpr int NV = ND + 2;
+  real UL[NV], UR[NV], FL[NV], FR[NV];
+  prim_to_cons<real, ND>(VL, UL, gm1);
+  prim_to_cons<real, ND>(VR, UR, gm1);
+  phys_flux<real, ND>(dir, VL, UL, FL);
+  phys_flux<real, ND>(dir, VR, UR, FR);
+  real uL = VL[1 + dir], uR = VR[1 + dir];
+  real cL = dsqrt(gam * VL[ND + 1] / VL[0]);
+  real cR = dsqrt(gam * VR[ND + 1] / VR[0]);
+  if (FLUX == FLUX_TVDLF) {
+    real cmax = fmax(fabs(uL) + cL, fabs(uR) + cR);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = real(0.5) * (FL[v] + FR[v]) - (real(0.5) * cmax) * (UR[v] - UL[v]);
+    return;
+  }
+  real SL = fmin(uL - cL, uR - cR);
+  real SR = fmax(uL + cL, uR + cR);
+  if (SL >= real(0)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = FL[v];
+    return;
+  }
+  if (SR <= real(0)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = FR[v];
+    return;
+  }
+  if (FLUX == FLUX_HLL) {
+    real inv = real(1) / (SR - SL);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = (SR * FL[v] - SL * FR[v] + (SL * SR) * (UR[v] - UL[v])) * inv;
+    return;
+  }
+  real rL = VL[0], rR = VR[0], pL = VL[ND + 1], pR = VR[ND + 1];
+  real aL = rL * (SL - uL), aR = rR * (SR - uR);
+  real Sstar = (pR - pL + aL * uL - aR * uR) / (aL - aR);
+  bool left = Sstar >= real(0);
+  real Vk[NV], Uk[NV], Fk[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    Vk[v] = left ? VL[v] : VR[v];
+    Uk[v] = left ? UL[v] : UR[v];
+    Fk[v] = left ? FL[v] : FR[v];
+  }
+  real Sk = left ? SL : SR;
+  real ak = left ? aL : aR;
+  real uk = Vk[1 + dir], pk = Vk[ND + 1], rk = Vk[0];
+  real fac = ak / (Sk - Sstar);
+  real Us[NV];
+  Us[0] = fac;
+#pragma unroll
+  for (int e = 0; e < ND; ++e) Us[1 + e] = fac * (e == dir ? Sstar : Vk[1 + e]);
+  Us[ND + 1] = fac * (Uk[ND + 1] / rk + (Sstar - uk) * (Sstar + pk / ak));
+#pragma unroll
+  for (int v = 0; v < NV; ++v) F[v] = Fk[v] + Sk * (Us[v] - Uk[v]);
+}
+
+// Limited slopes of a cell from a = q_i - q_{i-1}, b = q_{i+1} - q_i:
+// s- towards i-1/2, s+ towards i+1/2 (minmod, van Leer, Koren phi(r) =
+// max(0, min(2r, (1+2r)/3, 2)) on each side).
+template <typename real>
+__device__ __forceinline__ void limited_slopes(int lim, real a, real b, real& sm, real& sp) {
+  bool same = (a > real(0) && b > real(0)) || (a < real(0) && b < real(0));
+  if (lim == LIM_NONE || !same) {
+    sm = real(0);
+    sp = real(0);
+    return;
+  }
+  if (lim == LIM_MINMOD) {
+    real s = (a > real(0)) ? fmin(a, b) : fmax(a, b);
+    sm = s;
+    sp = s;
+  } else if (lim == LIM_VANLEER) {
+    real s = (real(2) * a * b) / (a + b);
+    sm = s;
+    sp = s;
+  } else {
+    real A = fabs(a), Bb = fabs(b);
+    real up = fmin(fmin(real(2) * A, (real(2) * A + Bb) / real(3)), real(2) * Bb);
+    real dn = fmin(fmin(real(2) * Bb, (A + real(2) * Bb) / real(3)), real(2) * A);
+    sp = (b > real(0)) ? up : -up;
+    sm = (a > real(0)) ? dn : -dn;
+  }
+}
+
+template <typename real>
+__device__ __forceinline__ real minmod2(real a, real b) {
+  if (a > real(0) && b > real(0)) return fmin(a, b);
+  if (a < real(0) && b < real(0)) return fmax(a, b);
+  return real(0);
+}
+
+// Face state pair from the primitive values of cells f-2, f-1, f, f+1 along a line;
+// first-order fallback when a reconstructed density or pressure is not positive.
+template <typename real, int ND>
+__device__ __forceinline__ void face_states(int lim, const real (*W)[ND + 2], real* VL, real* VR) {
+  constexpr int NV = ND + 2;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    real smL, spL, smR, spR;
+    limited_slopes<real>(lim, W[1][v] - W[0][v], W[2][v] - W[1][v], smL, spL);
+    limited_slopes<real>(lim, W[2][v] - W[1][v], W[3][v] - W[2][v], smR, spR);
+    VL[v] = W[1][v] + real(0.5) * spL;
+    VR[v] = W[2][v] - real(0.5) * smR;
+  }
+  if (!(VL[0] > real(0)) || !(VR[0] > real(0)) || !(VL[ND + 1] > real(0)) || !(VR[ND + 1] > real(0))) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      VL[v] = W[1][v];
+      VR[v] = W[2][v];
+    }
+  }
+}
+
+// ------------------------------------------------------------- reductions --
+template <typename real>
+struct MaxKey;
+template <>
+struct MaxKey<double> {
+  static __device__ unsigned long long enc(double s) { return (unsigned long long)__double_as_longlong(s); }
+  static __device__ double dec(unsigned long long b) { return __longlong_as_double((long long)b); }
+};
+template <>
+struct MaxKey<float> {
+  static __device__ unsigned long long enc(float s) { return (unsigned long long)__float_as_uint(s); }
+  static __device__ double dec(unsigned long long b) { return (double)__uint_as_float((unsigned int)b); }
+};
+
+// dt of the current step: the CFL step clipped to t_end (same on every CTA)
+__device__ __forceinline__ double stage_dt(const DevCtl* ctl) {
+  double t = ctl->t, dt = ctl->dt_cfl;
+  if (t + dt > ctl->t_end) dt = ctl->t_end - t;
+  return dt;
+}
+
+// Signal rate sum_d (|v_d| + c)/dx_d of one cell (Sec. 1.2, phys_get_cmax);
+// marks non-physical states.
+template <typename real, int ND>
+__device__ __forceinline__ real cell_rate(const real* U, real gam, real gm1, const real* dx, int* bad) {
+  real V[ND + 2];
+  cons_to_prim<real, ND>(U, V, gm1);
+  if (!(V[0] > real(0)) || !(V[ND + 1] > real(0))) *bad = 1;
+  real cs = dsqrt(gam * V[ND + 1] / V[0]);
+  real s = real(0);
+#pragma unroll
+  for (int d = 0; d < ND; ++d) s = s + (fabs(V[1 + d]) + cs) / dx[d];
+  return s;
+}
+
+// Block-wide reduction of (max rate, per-variable FP64 sums) and the last-CTA
+// finalisation: totals = fixed-order sum of per-leaf partials, dt_cfl = cfl/smax,
+// and, when `advance`, t += dt of the step just taken.  Deterministic for any
+// CTA schedule; no CTA ever waits on another.
+template <typename real, int NV, int NTHREADS>
+__device__ void block_reduce_finish(real rate, const double* sums, int leaf_first, int nleaf_cta,
+                                    int leaf_of_thread, const Geometry& G, DevCtl* ctl, double* partials,
+                                    int nleaves, bool advance, double dt, int bad) {
+  __shared__ double red[NTHREADS / 32][4][NV];  // per warp, per local leaf (<= 4), per var
+  __shared__ real wmax[NTHREADS / 32];
+  __shared__ int sbad;
+  __shared__ bool is_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) sbad = 0;
+  __syncthreads();
+  if (bad) sbad = 1;
+  // max rate
+  real m = rate;
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) wmax[warp] = m;
+  // sums per local leaf: a warp covers one leaf when leaves have >= 32 cells per CTA slot
+  double s[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) s[v] = sums[v];
+  // leaves of a CTA are contiguous groups of threads of equal size >= 16 cells; reduce within
+  // groups of width gw = NTHREADS / nleaf_cta (power of two) by butterflies limited to the group
+  int gw = NTHREADS / nleaf_cta;
+  int lim = gw < 32 ? gw : 32;
+  for (int o = lim / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s[v] += __shfl_xor_sync(0xffffffffu, s[v], o);
+  if (gw >= 32) {
+    if (lane == 0)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) red[warp][0][v] = s[v];
+  } else {
+    if ((threadIdx.x % gw) == 0)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) red[warp][(threadIdx.x % 32) / gw][v] = s[v];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    real mm = wmax[0];
+    for (int w = 1; w < NTHREADS / 32; ++w) mm = fmax(mm, wmax[w]);
+    atomicMax(&ctl->smax_bits, MaxKey<real>::enc(mm));
+    if (sbad) atomicOr(&ctl->status, 1);
+  }
+  if (threadIdx.x < nleaf_cta) {
+    int l = leaf_first + threadIdx.x;
+    if (l < nleaves) {
+      double acc[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+      if (gw >= 32) {
+        int wpl = gw / 32;
+        for (int w = 0; w < wpl; ++w)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) acc[v] += red[threadIdx.x * wpl + w][0][v];
+      } else {
+        int lpw = 32 / gw;
+        int w = threadIdx.x / lpw, q = threadIdx.x % lpw;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] = red[w][q][v];
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) partials[(size_t)l * NV + v] = acc[v];
+    }
+  }
+  __threadfence();
+  __syncthreads();  // partials written and red[] consumed before it is reused below
+  if (threadIdx.x == 0) {
+    unsigned int ticket = atomicAdd(&ctl->done, 1u);
+    is_last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // last CTA: fixed-order totals over leaves (strided per thread, butterfly per
+  // warp, warps in order)
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  for (int l = threadIdx.x; l < nleaves; l += NTHREADS)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] += __ldcg(&partials[(size_t)l * NV + v]);
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+  if (lane == 0)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) red[warp][0][v] = acc[v];
+  __syncthreads();
+  double tot[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) tot[v] = red[0][0][v];
+  for (int w = 1; w < NTHREADS / 32; ++w)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) tot[v] += red[w][0][v];
+  if (threadIdx.x == 0) {
+    volatile DevCtl* c = ctl;
+    for (int v = 0; v < NV; ++v) c->totals[v] = tot[v];
+    unsigned long long bits = atomicAdd(&ctl->smax_bits, 0ull);
+    double smax = MaxKey<real>::dec(bits);
+    if (advance) {
+      c->t = c->t + dt;
+      c->dt_last = dt;
+      c->steps = c->steps + 1;
+    }
+    c->dt_cfl = c->cfl / smax;
+    c->smax_bits = 0ull;
+    c->done = 0u;
+  }
+}
+
+// ------------------------------------------------------------ ghost fetch --
+template <int ND, int B>
+__device__ __forceinline__ int compose_cell(int d, int n, int t) {
+  if (ND == 1) return n;
+  if (ND == 2) return d == 0 ? n + B * t : t + B * n;
+  int t1 = t % B, t2 = t / B;
+  if (d == 0) return n + B * (t1 + B * t2);
+  if (d == 1) return t1 + B * (n + B * t2);
+  return t1 + B * (t2 + B * n);
+}
+
+template <int ND, int B>
+struct Tile {
+  static constexpr int NV = ND + 2;
+  static constexpr int NC = ND == 1 ? B : (ND == 2 ? B * B : B * B * B);
+  static constexpr int NT = ND == 1 ? 1 : (ND == 2 ? B : B * B);
+};
+
+// conserved value of ghost (face f = 2d+side, layer m, tangential t, var v) of leaf b
+template <typename real, int ND, int B>
+__device__ __forceinline__ real fetch_ghost(const real* __restrict__ U, const real* __restrict__ slabs,
+                                            const int* __restrict__ nb, int b, int f, int m, int t, int v) {
+  constexpr int NV = ND + 2, NC = Tile<ND, B>::NC, NT = Tile<ND, B>::NT;
+  int code = __ldg(&nb[b * 2 * ND + f]);
+  int d = f >> 1, side = f & 1;
+  if (code >= 0) {
+    int n = side == 0 ? B - 1 - m : m;
+    return U[((size_t)code * NV + v) * NC + compose_cell<ND, B>(d, n, t)];
+  }
+  if (code == -1) {
+    int n = side == 0 ? 0 : B - 1;
+    return U[((size_t)b * NV + v) * NC + compose_cell<ND, B>(d, n, t)];
+  }
+  int s = -2 - code;
+  return slabs[(((size_t)s * NV + v) * 2 + m) * NT + t];
+}
+
+// ======================================================= 1D and 2D stages ==
+// One thread per cell; a CTA takes LPB leaves.  Primitive values of each leaf
+// plus its face ghosts are staged in shared memory, every face flux is computed
+// once, then each cell forms its flux difference and the SSPRK combination.
+template <typename real, int ND, int B, int FLUX>
+__global__ void __launch_bounds__(ND == 1 ? 128 : 256)
+stage_kernel_12(StageArgs<real> a, Geometry G) {
+  constexpr int THREADS = ND == 1 ? 128 : 256;
+  constexpr int NV = ND + 2, NC = Tile<ND, B>::NC, NT = Tile<ND, B>::NT;
+  constexpr int LPB = THREADS / NC;
+  constexpr int P = B + 4;
+  constexpr int PP = ND == 1 ? P : P * P;
+  constexpr int NFX = ND == 1 ? (B + 1) : B * (B + 1);  // faces per direction per leaf
+  __shared__ real W[LPB][NV][PP];
+  __shared__ real FXs[LPB][ND][NV][NFX];
+
+  const double dt = stage_dt(a.ctl);
+  if (!(dt > 0.0)) return;
+  const real dtr = (real)dt;
+  const real gam = (real)G.gamma, gm1 = gam - real(1);
+  const int lb = threadIdx.x / NC, tc = threadIdx.x % NC;
+  const int leaf = blockIdx.x * LPB + lb;
+  const bool active = leaf < a.nleaves;
+  const int ic = tc % B, jc = ND == 2 ? tc / B : 0;
+
+  real Uc[NV];
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Uc[v] = a.Us[((size_t)leaf * NV + v) * NC + tc];
+    real Vc[NV];
+    cons_to_prim<real, ND>(Uc, Vc, gm1);
+    int pidx = ND == 1 ? ic + 2 : (jc + 2) * P + (ic + 2);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) W[lb][v][pidx] = Vc[v];
+    // face ghosts: 2*ND faces x 2 layers x NT cells
+    constexpr int NH = 2 * ND * 2 * NT;
+    for (int h = tc; h < NH; h += NC) {
+      int f = h / (2 * NT), m = (h / NT) % 2, t = h % NT;
+      real Ug[NV], Vg[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Ug[v] = fetch_ghost<real, ND, B>(a.Us, a.slabs, a.nb, leaf, f, m, t, v);
+      cons_to_prim<real, ND>(Ug, Vg, gm1);
+      int d = f >> 1, side = f & 1;
+      int n = side == 0 ? -1 - m : B + m;
+      int pi, pj;
+      if (d == 0) { pi = n; pj = t; } else { pi = t; pj = n; }
+      int q = ND == 1 ? pi + 2 : (pj + 2) * P + (pi + 2);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) W[lb][v][q] = Vg[v];
+    }
+  }
+  __syncthreads();
+  const int lim = a.limiter;
+  if (active) {
+    for (int idx = tc; idx < ND * NFX; idx += NC) {
+      int dim = idx / NFX, fl = idx % NFX;
+      int fi, fj;  // face index along dim, row
+      if (ND == 1) { fi = fl; fj = 0; }
+      else if (dim == 0) { fi = fl % (B + 1); fj = fl / (B + 1); }
+      else { fi = fl % (B + 1); fj = fl / (B + 1); }
+      real Wl[4][NV];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        int c = fi - 2 + s;
+        int q = ND == 1 ? c + 2 : (dim == 0 ? (fj + 2) * P + (c + 2) : (c + 2) * P + (fj + 2));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Wl[s][v] = W[lb][v][q];
+      }
+      real VL[NV], VR[NV], F[NV];
+      face_states<real, ND>(lim, Wl, VL, VR);
+      riemann<real, ND, FLUX>(dim, VL, VR, gam, gm1, F);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) FXs[lb][dim][v][fl] = F[v];
+      if (a.has_ffx && (fi == 0 || fi == B)) {
+        int face = 2 * dim + (fi == 0 ? 0 : 1);
+        int slot = a.ffx[leaf * 2 * ND + face];
+        if (slot >= 0) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) a.fflux[((size_t)slot * NV + v) * NT + fj] = F[v];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  real rate = real(0);
+  double sums[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) sums[v] = 0.0;
+  int bad = 0;
+  if (active) {
+    const int lev = a.level[leaf];
+    real dx[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dx[d] = (real)G.dx[lev][d];
+    real Un[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      real div = real(0);
+      {
+        int lo = ND == 1 ? ic : jc * (B + 1) + ic;
+        div = div + (FXs[lb][0][v][lo + 1] - FXs[lb][0][v][lo]) / dx[0];
+      }
+      if (ND == 2)  // y faces are stored per column: (face index jc, column ic)
+        div = div + (FXs[lb][ND - 1][v][ic * (B + 1) + jc + 1] - FXs[lb][ND - 1][v][ic * (B + 1) + jc]) / dx[1];
+      real tmp = Uc[v] - dtr * div;
+      Un[v] = a.stage1 ? tmp : a.alpha * a.U0[((size_t)leaf * NV + v) * NC + tc] + a.beta * tmp;
+      a.out[((size_t)leaf * NV + v) * NC + tc] = Un[v];
+    }
+    if (a.fuse_reduce) {
+      rate = cell_rate<real, ND>(Un, gam, gm1, dx, &bad);
+      double dV = G.dV[lev];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sums[v] = (double)Un[v] * dV;
+    }
+  }
+  if (a.fuse_reduce)
+    block_reduce_finish<real, NV, THREADS>(rate, sums, blockIdx.x * LPB, LPB, lb, G, a.ctl, a.partials,
+                                           a.nleaves, true, dt, bad);
+}
+
+// ============================================================ 3D stage ==
+// One thread per (i, j) column of a leaf, marching in k.  Shared memory holds a
+// ring of four primitive planes (k-1 .. k+2, with x/y face ghosts for interior
+// planes), the x and y face fluxes of plane k and the z flux of face k-1/2.
+template <typename real, int B>
+struct Stage3DSmem {
+  static constexpr int NV = 5, P = B + 4, LPB = 256 / (B * B);
+  real W[LPB][4][NV][P * P];
+  real FX[LPB][2][NV][B * (B + 1)];
+  real FZ[LPB][NV][B * B];
+};
+
+template <typename real, int B, int FLUX>
+__global__ void __launch_bounds__(256) stage_kernel_3d(StageArgs<real> a, Geometry G) {
+  constexpr int ND = 3, NV = 5, NC = B * B * B, NT = B * B, P = B + 4, COLS = B * B;
+  constexpr int LPB = 256 / COLS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Stage3DSmem<real, B>& S = *reinterpret_cast<Stage3DSmem<real, B>*>(smem_raw);
+
+  const double dt = stage_dt(a.ctl);
+  if (!(dt > 0.0)) return;
+  const real dtr = (real)dt;
+  const real gam = (real)G.gamma, gm1 = gam - real(1);
+  const int lb = threadIdx.x / COLS, tc = threadIdx.x % COLS;
+  const int leaf = blockIdx.x * LPB + lb;
+  const bool active = leaf < a.nleaves;
+  const int ic = tc % B, jc = tc / B;
+  const int lim = a.limiter;
+  const int lev = active ? a.level[leaf] : 1;
+  real dx[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) dx[d] = (real)G.dx[lev][d];
+
+  // load plane z (-2 .. B+1) of this leaf into ring slot; interior planes get x/y ghosts
+  auto load_plane = [&](int z, real (&Ucol)[NV], bool keep) {
+    real* Wp = &S.W[lb][(z + 4) & 3][0][0];
+    real Uv[NV], Vv[NV];
+    if (z >= 0 && z < B) {
+      int cell = tc + COLS * z;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Uv[v] = a.Us[((size_t)leaf * NV + v) * NC + cell];
+      if (keep)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Ucol[v] = Uv[v];
+    } else {
+      int f = z < 0 ? 4 : 5;
+      int m = z < 0 ? -1 - z : z - B;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Uv[v] = fetch_ghost<real, 3, B>(a.Us, a.slabs, a.nb, leaf, f, m, tc, v);
+    }
+    cons_to_prim<real, 3>(Uv, Vv, gm1);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Wp[v * P * P + (jc + 2) * P + (ic + 2)] = Vv[v];
+    if (z >= 0 && z < B) {
+      // x/y ghosts of this plane: faces 0..3, 2 layers, B cells along the other in-plane axis
+      for (int h = tc; h < 4 * 2 * B; h += COLS) {
+        int f = h / (2 * B), m = (h / B) % 2, s = h % B;
+        int d = f >> 1, side = f & 1;
+        int t = d == 0 ? s + B * z : s + B * z;  // tangential (t1 = other in-plane axis, t2 = z)
+        real Ug[NV], Vg[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Ug[v] = fetch_ghost<real, 3, B>(a.Us, a.slabs, a.nb, leaf, f, m, t, v);
+        cons_to_prim<real, 3>(Ug, Vg, gm1);
+        int n = side == 0 ? -1 - m : B + m;
+        int pi = d == 0 ? n : s, pj = d == 0 ? s : n;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Wp[v * P * P + (pj + 2) * P + (pi + 2)] = Vg[v];
+      }
+    }
+  };
+
+  auto zflux = [&](int kface, real* F) {  // face between cells kface-1 and kface
+    real Wl[4][NV];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const real* Wp = &S.W[lb][(kface - 2 + s + 4) & 3][0][0];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Wl[s][v] = Wp[v * P * P + (jc + 2) * P + (ic + 2)];
+    }
+    real VL[NV], VR[NV];
+    face_states<real, 3>(lim, Wl, VL, VR);
+    riemann<real, 3, FLUX>(2, VL, VR, gam, gm1, F);
+  };
+
+  real Uk0[NV], Uk1[NV], Uk2[NV];  // conserved values of planes k, k+1, k+2 of this column
+  real rate = real(0);
+  double sums[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) sums[v] = 0.0;
+  int bad = 0;
+
+  if (active) {
+    load_plane(-2, Uk2, false);
+    load_plane(-1, Uk2, false);
+    load_plane(0, Uk0, true);
+    load_plane(1, Uk1, true);
+  }
+  __syncthreads();
+  if (active) {
+    real F[NV];
+    zflux(0, F);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) S.FZ[lb][v][tc] = F[v];
+    if (a.has_ffx) {
+      int slot = a.ffx[leaf * 6 + 4];
+      if (slot >= 0)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) a.fflux[((size_t)slot * NV + v) * NT + tc] = F[v];
+    }
+  }
+  for (int k = 0; k < B; ++k) {
+    // ring: slot of plane k-2 is reused for plane k+2
+    __syncthreads();
+    if (active) load_plane(k + 2, Uk2, k + 2 < B);
+    __syncthreads();
+    real Fz[NV];
+    if (active) {
+      zflux(k + 1, Fz);
+      if (a.has_ffx && k == B - 1) {
+        int slot = a.ffx[leaf * 6 + 5];
+        if (slot >= 0)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) a.fflux[((size_t)slot * NV + v) * NT + tc] = Fz[v];
+      }
+      // x and y faces of plane k
+      const real* Wp = &S.W[lb][(k + 4) & 3][0][0];
+      for (int idx = tc; idx < 2 * B * (B + 1); idx += COLS) {
+        int dim = idx / (B * (B + 1)), fl = idx % (B * (B + 1));
+        int fi = fl % (B + 1), fj = fl / (B + 1);
+        real Wl[4][NV];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          int c = fi - 2 + s;
+          int q = dim == 0 ? (fj + 2) * P + (c + 2) : (c + 2) * P + (fj + 2);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) Wl[s][v] = Wp[v * P * P + q];
+        }
+        real VL[NV], VR[NV], F[NV];
+        face_states<real, 3>(lim, Wl, VL, VR);
+        riemann<real, 3, FLUX>(dim, VL, VR, gam, gm1, F);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) S.FX[lb][dim][v][fl] = F[v];
+        if (a.has_ffx && (fi == 0 || fi == B)) {
+          int slot = a.ffx[leaf * 6 + 2 * dim + (fi == 0 ? 0 : 1)];
+          if (slot >= 0)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) a.fflux[((size_t)slot * NV + v) * NT + fj + B * k] = F[v];
+        }
+      }
+    }
+    __syncthreads();
+    if (active) {
+      const real* Uk = Uk0;
+      int cell = tc + COLS * k;
+      real Un[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        real div = real(0);
+        div = div + (S.FX[lb][0][v][jc * (B + 1) + ic + 1] - S.FX[lb][0][v][jc * (B + 1) + ic]) / dx[0];
+        div = div + (S.FX[lb][1][v][ic * (B + 1) + jc + 1] - S.FX[lb][1][v][ic * (B + 1) + jc]) / dx[1];
+        div = div + (Fz[v] - S.FZ[lb][v][tc]) / dx[2];
+        real tmp = Uk[v] - dtr * div;
+        Un[v] = a.stage1 ? tmp : a.alpha * a.U0[((size_t)leaf * NV + v) * NC + cell] + a.beta * tmp;
+        a.out[((size_t)leaf * NV + v) * NC + cell] = Un[v];
+        S.FZ[lb][v][tc] = Fz[v];
+      }
+      if (a.fuse_reduce) {
+        rate = fmax(rate, cell_rate<real, 3>(Un, gam, gm1, dx, &bad));
+        double dV = G.dV[lev];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sums[v] += (double)Un[v] * dV;
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        Uk0[v] = Uk1[v];
+        Uk1[v] = Uk2[v];
+      }
+    }
+  }
+  if (a.fuse_reduce)
+    block_reduce_finish<real, NV, 256>(rate, sums, blockIdx.x * LPB, LPB, lb, G, a.ctl, a.partials, a.nleaves,
+                                       true, dt, bad);
+}
+
+// ========================================================= reduce kernel ==
+// Max signal rate and FP64 totals of the current state (after set_state, a
+// regrid, or the refluxed last stage of a step on a tree with level jumps).
+template <typename real, int ND, int B>
+__global__ void __launch_bounds__(256) reduce_kernel(const real* __restrict__ U, const int* __restrict__ level,
+                                                     Geometry G, DevCtl* ctl, double* partials, int nleaves,
+                                                     int advance) {
+  constexpr int NV = ND + 2, NC = Tile<ND, B>::NC;
+  constexpr int CPT = NC >= 256 ? NC / 256 : 1;       // cells per thread
+  constexpr int LPB = NC >= 256 ? 1 : 256 / NC;
+  const int lb = threadIdx.x / (NC / CPT), tc = threadIdx.x % (NC / CPT);
+  const int leaf = blockIdx.x * LPB + lb;
+  const real gam = (real)G.gamma, gm1 = gam - real(1);
+  real rate = real(0);
+  double sums[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) sums[v] = 0.0;
+  int bad = 0;
+  double dt = 0.0;
+  if (advance) dt = stage_dt(ctl);
+  if (leaf < nleaves) {
+    int lev = level[leaf];
+    real dx[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dx[d] = (real)G.dx[lev][d];
+    for (int c = tc; c < NC; c += NC / CPT) {
+      real Uc[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Uc[v] = U[((size_t)leaf * NV + v) * NC + c];
+      rate = fmax(rate, cell_rate<real, ND>(Uc, gam, gm1, dx, &bad));
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sums[v] += (double)Uc[v] * G.dV[lev];
+    }
+  }
+  block_reduce_finish<real, NV, 256>(rate, sums, blockIdx.x * LPB, LPB, lb, G, ctl, partials, nleaves,
+                                     advance != 0, dt, bad);
+}
+
+// ====================================================== ghost slab fill ==
+// One thread per (slab, var, layer, tangential cell).  Restriction: mean of the
+// 2^ndim fine cells (x-fastest sum).  Prolongation: q_p + 1/4 sum_e sigma_e s_e,
+// minmod slopes; normal inner neighbour = restriction of the target leaf;
+// tangential neighbours outside the coarse leaf give s_e = 0.
+template <typename real, int ND, int B>
+__global__ void ghost_fill_kernel(const real* __restrict__ U, real* __restrict__ slabs,
+                                  const SlabDesc* __restrict__ desc, int nslabs) {
+  constexpr int NV = ND + 2, NC = Tile<ND, B>::NC, NT = Tile<ND, B>::NT;
+  long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long total = (long long)nslabs * NV * 2 * NT;
+  if (gid >= total) return;
+  int t = gid % NT;
+  int m = (gid / NT) % 2;
+  int v = (gid / (2 * NT)) % NV;
+  int s = gid / (2 * NT * NV);
+  SlabDesc D = desc[s];
+  int d = D.face >> 1, side = D.face & 1;
+  int e1 = -1, e2 = -1;
+  for (int e = 0; e < ND; ++e)
+    if (e != d) {
+      if (e1 < 0) e1 = e; else e2 = e;
+    }
+  int tl[3] = {0, 0, 0};
+  if (e1 >= 0) tl[e1] = t % B;
+  if (e2 >= 0) tl[e2] = t / B;
+  const real inv = real(1) / real(1 << ND);
+  real val;
+  if (D.kind == 0) {
+    int q1 = e1 >= 0 ? tl[e1] / (B / 2) : 0, q2 = e2 >= 0 ? tl[e2] / (B / 2) : 0;
+    int F = D.src[q1 + 2 * q2];
+    real sum = real(0);
+    for (int o = 0; o < (1 << ND); ++o) {
+      int loc[3] = {0, 0, 0};
+      for (int e = 0; e < ND; ++e) {
+        int oe = (o >> e) & 1;
+        if (e == d) loc[e] = (side == 0 ? B - 2 - 2 * m : 2 * m) + oe;
+        else loc[e] = 2 * tl[e] + oe - (e == e1 ? q1 : q2) * B;
+      }
+      sum = sum + U[((size_t)F * NV + v) * NC + loc[0] + B * (loc[1] + B * loc[2])];
+    }
+    val = sum * inv;
+  } else {
+    int Cl = D.src[0];
+    int p[3] = {0, 0, 0};
+    real sg[3];
+    for (int e = 0; e < ND; ++e) {
+      if (e == d) {
+        p[e] = side == 0 ? B - 1 : 0;
+        sg[e] = (side == 0) == (m == 0) ? real(1) : real(-1);
+      } else {
+        int off = (e == e1) ? D.off[0] : D.off[1];
+        p[e] = off + tl[e] / 2;
+        sg[e] = (tl[e] & 1) ? real(1) : real(-1);
+      }
+    }
+    auto cval = [&](const int* c) { return U[((size_t)Cl * NV + v) * NC + c[0] + B * (c[1] + B * c[2])]; };
+    real qp = cval(p);
+    // restriction of the target's fine cells next to the face (normal inner neighbour)
+    real inner;
+    {
+      real sum = real(0);
+      for (int o = 0; o < (1 << ND); ++o) {
+        int loc[3] = {0, 0, 0};
+        for (int e = 0; e < ND; ++e) {
+          int oe = (o >> e) & 1;
+          if (e == d) loc[e] = (side == 0 ? 0 : B - 2) + oe;
+          else loc[e] = 2 * (tl[e] / 2) + oe;
+        }
+        sum = sum + U[((size_t)D.target * NV + v) * NC + loc[0] + B * (loc[1] + B * loc[2])];
+      }
+      inner = sum * inv;
+    }
+    real acc = real(0);
+    for (int e = 0; e < ND; ++e) {
+      real qm, qq;
+      bool ok = true;
+      int c[3] = {p[0], p[1], p[2]};
+      if (e == d) {
+        c[e] = side == 0 ? p[e] - 1 : p[e] + 1;
+        real away = cval(c);
+        if (side == 0) { qm = away; qq = inner; } else { qm = inner; qq = away; }
+      } else {
+        int cm[3] = {p[0], p[1], p[2]}, cp[3] = {p[0], p[1], p[2]};
+        cm[e] -= 1;
+        cp[e] += 1;
+        ok = cm[e] >= 0 && cp[e] < B;
+        qm = ok ? cval(cm) : real(0);
+        qq = ok ? cval(cp) : real(0);
+      }
+      real sl = ok ? minmod2(qp - qm, qq - qp) : real(0);
+      acc = acc + sg[e] * sl;
+    }
+    val = qp + real(0.25) * acc;
+  }
+  slabs[(((size_t)s * NV + v) * 2 + m) * NT + t] = val;
+}
+
+// ================================================================ reflux ==
+// Coarse cell next to a level jump: out += +-beta*dt/dx_c*(mean fine flux - coarse flux).
+template <typename real, int ND, int B>
+__global__ void reflux_kernel(real* __restrict__ out, const real* __restrict__ fflux, const RefluxRec* __restrict__ rec,
+                              int nrec, const int* __restrict__ level, Geometry G, const DevCtl* ctl, real beta) {
+  constexpr int NV = ND + 2, NC = Tile<ND, B>::NC, NT = Tile<ND, B>::NT;
+  long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)nrec * NV * NT) return;
+  double dt = stage_dt(ctl);
+  if (!(dt > 0.0)) return;
+  int t = gid % NT, v = (gid / NT) % NV, r = gid / (NT * NV);
+  RefluxRec R = rec[r];
+  int d = R.face >> 1, side = R.face & 1;
+  int e1 = -1, e2 = -1;
+  for (int e = 0; e < ND; ++e)
+    if (e != d) {
+      if (e1 < 0) e1 = e; else e2 = e;
+    }
+  int t1 = e1 >= 0 ? t % B : 0, t2 = e2 >= 0 ? t / B : 0;
+  int q1 = t1 / (B / 2), q2 = t2 / (B / 2);
+  int fs = R.fslot[q1 + 2 * q2];
+  real sum = real(0);
+  int n2 = ND > 2 ? 2 : 1, n1 = ND > 1 ? 2 : 1;
+  for (int o2 = 0; o2 < n2; ++o2)
+    for (int o1 = 0; o1 < n1; ++o1) {
+      int f1 = 2 * t1 + o1 - q1 * B, f2 = 2 * t2 + o2 - q2 * B;
+      int tf = ND == 1 ? 0 : (ND == 2 ? f1 : f1 + B * f2);
+      sum = sum + fflux[((size_t)fs * NV + v) * NT + tf];
+    }
+  real mean = sum * (real(1) / real(1 << (ND - 1)));
+  real Fc = fflux[((size_t)R.cslot * NV + v) * NT + t];
+  int lev = level[R.coarse];
+  real dxc = (real)G.dx[lev][d];
+  real corr = beta * (real)dt * (mean - Fc) / dxc;
+  int n = side == 0 ? 0 : B - 1;
+  int cell = compose_cell<ND, B>(d, n, t);
+  size_t o = ((size_t)R.coarse * NV + v) * NC + cell;
+  out[o] = side == 0 ? out[o] + corr : out[o] - corr;
+}
+
+// ============================================================ estimator ==
+// Lohner-type estimator per direction: |q+ - 2 q0 + q-| over |q+ - q0| + |q0 - q-|
+// + eps (|q+| + 2|q0| + |q-|), squares summed over directions, sqrt; max over the
+// selected primitive variables and the leaf's cells.  Evaluated in float64.
+template <typename real, int ND, int B>
+__global__ void __launch_bounds__(256) lohner_kernel(const real* __restrict__ U, const real* __restrict__ slabs,
+                                                     const int* __restrict__ nb, double gamma, double eps,
+                                                     unsigned mask, double* err, int nleaves) {
+  constexpr int NV = ND + 2, NC = Tile<ND, B>::NC;
+  constexpr int TPL = NC >= 256 ? 256 : NC;  // threads per leaf
+  constexpr int LPB = 256 / TPL;
+  const int lb = threadIdx.x / TPL, tc = threadIdx.x % TPL;
+  const int leaf = blockIdx.x * LPB + lb;
+  double emax = 0.0;
+  const double gm1 = gamma - 1.0;
+  if (leaf < nleaves) {
+    for (int c = tc; c < NC; c += TPL) {
+      int ci[3] = {c % B, ND > 1 ? (c / B) % B : 0, ND > 2 ? c / (B * B) : 0};
+      double Uq[NV], Vc[NV], Vm[3][NV], Vp[3][NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Uq[v] = (double)U[((size_t)leaf * NV + v) * NC + c];
+      cons_to_prim<double, ND>(Uq, Vc, gm1);
+      for (int d = 0; d < ND; ++d) {
+        for (int s = 0; s < 2; ++s) {
+          int cc[3] = {ci[0], ci[1], ci[2]};
+          cc[d] += s == 0 ? -1 : 1;
+          double Un[NV];
+          if (cc[d] < 0 || cc[d] >= B) {
+            int f = 2 * d + (cc[d] < 0 ? 0 : 1);
+            int t = 0, k = 0;
+            for (int e = 0; e < ND; ++e)
+              if (e != d) {
+                t += ci[e] * (k == 0 ? 1 : B);
+                ++k;
+              }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Un[v] = (double)fetch_ghost<real, ND, B>(U, slabs, nb, leaf, f, 0, t, v);
+          } else {
+            int cn = cc[0] + B * (cc[1] + B * cc[2]);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Un[v] = (double)U[((size_t)leaf * NV + v) * NC + cn];
+          }
+          cons_to_prim<double, ND>(Un, s == 0 ? Vm[d] : Vp[d], gm1);
+        }
+      }
+      double ecell = 0.0;
+      for (int v = 0; v < NV; ++v) {
+        if (!((mask >> v) & 1u)) continue;
+        double num = 0.0, den = 0.0;
+        for (int d = 0; d < ND; ++d) {
+          double qm = Vm[d][v], q0 = Vc[v], qp = Vp[d][v];
+          double d2 = qp - 2.0 * q0 + qm;
+          double d1 = fabs(qp - q0) + fabs(q0 - qm) + eps * (fabs(qp) + 2.0 * fabs(q0) + fabs(qm));
+          num = num + d2 * d2;
+          den = den + d1 * d1;
+        }
+        double e = den > 0.0 ? sqrt(num / den) : 0.0;
+        ecell = fmax(ecell, e);
+      }
+      emax = fmax(emax, ecell);
+    }
+  }
+  // max within the leaf's threads
+  __shared__ double sm[256];
+  sm[threadIdx.x] = emax;
+  __syncthreads();
+  for (int w = TPL / 2; w > 0; w >>= 1) {
+    if (tc < w) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (tc == 0 && leaf < nleaves) err[leaf] = sm[threadIdx.x];
+}
+
+// =============================================================== regrid ==
+// New leaf state: copy, limited prolongation from the old parent (its face
+// ghosts give the slopes at its edges), or restriction from the old children.
+template <typename real, int ND, int B>
+__global__ void regrid_kernel(const real* __restrict__ Uold, real* __restrict__ Unew, const real* __restrict__ slabs,
+                              const int* __restrict__ nb, const RegridOp* __restrict__ ops, int nnew) {
+  constexpr int NV = ND + 2, NC = Tile<ND, B>::NC;
+  long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)nnew * NC) return;
+  int c = gid % NC;
+  int nl = gid / NC;
+  RegridOp op = ops[nl];
+  int ci[3] = {c % B, ND > 1 ? (c / B) % B : 0, ND > 2 ? c / (B * B) : 0};
+  for (int v = 0; v < NV; ++v) {
+    real val;
+    if (op.kind == 0) {
+      val = Uold[((size_t)op.src[0] * NV + v) * NC + c];
+    } else if (op.kind == 1) {
+      int P = op.src[0];
+      int pc[3] = {0, 0, 0};
+      real sg[3];
+      for (int e = 0; e < ND; ++e) {
+        int oe = (op.child >> e) & 1;
+        int f = oe * B + ci[e];
+        pc[e] = f >> 1;
+        sg[e] = (f & 1) ? real(1) : real(-1);
+      }
+      auto pval = [&](const int* q) -> real {
+        for (int e = 0; e < ND; ++e) {
+          if (q[e] < 0 || q[e] >= B) {
+            int face = 2 * e + (q[e] < 0 ? 0 : 1);
+            int t = 0, k = 0;
+            for (int g = 0; g < ND; ++g)
+              if (g != e) {
+                t += q[g] * (k == 0 ? 1 : B);
+                ++k;
+              }
+            return fetch_ghost<real, ND, B>(Uold, slabs, nb, P, face, 0, t, v);
+          }
+        }
+        return Uold[((size_t)P * NV + v) * NC + q[0] + B * (q[1] + B * q[2])];
+      };
+      real qp = pval(pc);
+      real acc = real(0);
+      for (int e = 0; e < ND; ++e) {
+        int m[3] = {pc[0], pc[1], pc[2]}, p[3] = {pc[0], pc[1], pc[2]};
+        m[e] -= 1;
+        p[e] += 1;
+        real s = minmod2(qp - pval(m), pval(p) - qp);
+        acc = acc + sg[e] * s;
+      }
+      val = qp + real(0.25) * acc;
+    } else {
+      int o[3] = {0, 0, 0};
+      for (int e = 0; e < ND; ++e) o[e] = (2 * ci[e]) / B;
+      int child = op.src[o[0] | (o[1] << 1) | (o[2] << 2)];
+      real sum = real(0);
+      for (int q = 0; q < (1 << ND); ++q) {
+        int f[3] = {0, 0, 0};
+        for (int e = 0; e < ND; ++e) f[e] = 2 * ci[e] - o[e] * B + ((q >> e) & 1);
+        sum = sum + Uold[((size_t)child * NV + v) * NC + f[0] + B * (f[1] + B * f[2])];
+      }
+      val = sum * (real(1) / real(1 << ND));
+    }
+    Unew[((size_t)nl * NV + v) * NC + c] = val;
+  }
+}
+
+// ============================================================ state I/O ==
+template <typename real, int ND>
+__global__ void set_state_kernel(const double* __restrict__ W, real* __restrict__ U, long long ncells_total, int nc,
+                                 int primitive, double gamma) {
+  constexpr int NV = ND + 2;
+  long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= ncells_total) return;
+  long long leaf = gid / nc;
+  int c = gid % nc;
+  double in[NV], o[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) in[v] = W[(leaf * NV + v) * nc + c];
+  if (primitive) prim_to_cons<double, ND>(in, o, gamma - 1.0);
+  else
+#pragma unroll
+    for (int v = 0; v < NV; ++v) o[v] = in[v];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) U[(leaf * NV + v) * nc + c] = (real)o[v];
+}
+
+template <typename real>
+__global__ void read_state_kernel(const real* __restrict__ U, double* __restrict__ out, long long n) {
+  long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid < n) out[gid] = (double)U[gid];
+}
+
+template <typename real, int ND, int B>
+__global__ void face_ghost_dump_kernel(const real* __restrict__ U, const real* __restrict__ slabs,
+                                       const int* __restrict__ nb, int leaf, double* out) {
+  constexpr int NV = ND + 2, NT = Tile<ND, B>::NT;
+  int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  int total = NV * 2 * ND * 2 * NT;
+  if (gid >= total) return;
+  int t = gid % NT, m = (gid / NT) % 2, f = (gid / (2 * NT)) % (2 * ND), v = gid / (2 * NT * 2 * ND);
+  out[gid] = (double)fetch_ghost<real, ND, B>(U, slabs, nb, leaf, f, m, t, v);
+}
+
+}  // namespace amrgpu
