@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark of the finite-volume stage update (and the multigrid step) on GB300.
+
+Headline: cell-updates/s per RK stage of the 2D Kelvin-Helmholtz workload
+(2048^2 cells as 128x128 blocks of 16^2, HLLC + van Leer, SSPRK3, CFL 0.8,
+periodic), FP32 batched path; the FP64 plain path is reported beside it.
+A step = one SSPRK3 step = 3 stage launches (ghost gather, MUSCL, HLLC, flux
+difference, SSPRK combination; the last one also does the CFL max-reduction
+and the FP64 conserved totals), CUDA-graph launched.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the method runs all blocks on one GPU (no sharding, no collective);
+N > 1 runs N independent replicas (weak scaling), value = sum over ranks.
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per RK stage (KH 2048^2, FP32 batched)"
+UNIT = "cell-stages/s"
+NSIDE, BNX = 2048, 16
+WORKLOAD = "2D Euler Kelvin-Helmholtz 2048^2, 128x128 blocks of 16^2, HLLC + van Leer, SSPRK3, CFL 0.8, periodic"
+
+
+def kh_kwargs(nside=NSIDE, precision="fp32", stream=None):
+    nb = nside // BNX
+    return dict(ndim=2, block_nx=BNX, base=[nb, nb], gamma=1.4, cfl=0.8, flux="hllc", limiter="vanleer",
+                rk=3, bc="periodic", precision=precision, stream=stream)
+
+
+def kh_state(lev, crd, nside=NSIDE, seed=2004):
+    from paper_2004_03275_gb300 import inputs
+    nb = nside // BNX
+    x, gi = inputs.cell_centres(lev, crd, 2, BNX, [nb, nb, 1], [0, 0, 0], [1, 1, 1])
+    return inputs.kelvin_helmholtz(x, gi, nside, seed=seed)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except FileNotFoundError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        loaded = [s for s in sm if s > 0.5 * (max(mx) if mx else 1)] or sm
+        return {"sm_mhz": float(np.median(loaded)) if loaded else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def time_steps(torch, solver, stream, steps):
+    """K graph-launched steps bracketed by synchronize, timed with CUDA events on the solver's stream."""
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    solver.run(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    solver.sync()
+    return ev0.elapsed_time(ev1) / steps
+
+
+def stage_roofline(solver, nsteps, nv, wbytes, ncells, hbm_gbs):
+    """Average stage-kernel duration from per-kernel CUDA events, algorithmic bytes per launch:
+    stage 1 reads U^n and writes U^1 (2 nv w per cell), stages 2-3 read U^(s), U^n and write (3 nv w)."""
+    ms_total, bytes_total, nlaunch = 0.0, 0.0, 0
+    for _ in range(nsteps):
+        prof = solver.profile_step()
+        stages = [ms for kind, ms in prof if kind == 0]
+        for s, ms in enumerate(stages):
+            ms_total += ms
+            bytes_total += (2 if s == 0 else 3) * nv * wbytes * ncells
+            nlaunch += 1
+    achieved = bytes_total / (ms_total * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_gbs, "unit": "GB/s",
+            "frac": round(achieved / hbm_gbs, 4), "traffic": None,
+            "kernel": "stage2d_f32_kernel<16,HLLC,VANLEER>", "launches_timed": nlaunch,
+            "avg_launch_us": round(ms_total / nlaunch * 1e3, 2),
+            "bytes_per_launch_avg": int(bytes_total / nlaunch), "frac_of_8TBs_nameplate": round(achieved / 8000, 4)}
+
+
+def oracle_cpu_baseline(budget_s=12.0, max_side=512):
+    """The FP64 oracle as it stands (single thread) on a bounded KH sample."""
+    import oracle as O
+    side = max_side
+    nb = side // BNX
+    kw = kh_kwargs(side)
+    kw.pop("precision")
+    kw.pop("stream")
+    g = O.Grid(**kw)
+    lev, crd = g.leaves()
+    g.set_prim(kh_state(lev, crd, side))
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        g.step()
+        n += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    cells = side * side
+    return {"value": cells * 3 * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"KH {side}^2 ({nb * nb} blocks of 16^2), {n} SSPRK3 steps, FP64, single thread, {el:.1f} s"}
+
+
+def run_reference(args, ws, rank):
+    """--impl reference: the oracle on the host cores, each step a bounded sample of the workload."""
+    if rank != 0:
+        return 0
+    import oracle as O
+    total = args.steps + args.warmup
+    budget = 150.0 / max(total, 1)  # seconds per step so that the run stays within a few minutes
+    side = 32
+    for s in (64, 96, 128, 192, 256, 384, 512, 768, 1024):
+        if s * s * 3 * 1.0e-6 <= budget:  # ~1 us per cell-stage on one core
+            side = s
+    kw = kh_kwargs(side)
+    kw.pop("precision")
+    kw.pop("stream")
+    g = O.Grid(**kw)
+    lev, crd = g.leaves()
+    g.set_prim(kh_state(lev, crd, side))
+    for _ in range(args.warmup):
+        g.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        g.step()
+    el = time.perf_counter() - t0
+    ms = el / args.steps * 1e3
+    value = side * side * 3 / (ms * 1e-3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_side": side, "parallelism": "cpu oracle, 1 thread"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"KH {side}^2 per step (bounded sample of the 2048^2 workload)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    from paper_2004_03275_gb300 import amrvac
+
+    amrvac.load()  # fails loudly if the CUDA library is missing
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # a real (non-legacy) stream shared by the library and the timing events
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    hbm, peak_src = peaks()
+    ncells = NSIDE * NSIDE
+
+    # ---------------------------------------------------------------- FP32 headline
+    s32 = amrvac.AmrSolver(**kh_kwargs(precision="fp32", stream=stream.cuda_stream))
+    lev, crd = s32.leaves()
+    V = kh_state(lev, crd)
+    s32.set_prim(V)
+    s32.run(args.warmup)
+    s32.sync()
+    clk = Clocks(local)
+    if rank == 0:
+        clk.start()
+    barrier()
+    l0 = s32.kernel_launches()
+    ms32 = time_steps(torch, s32, stream, args.steps)
+    launches = s32.kernel_launches() - l0
+    barrier()
+    clocks = clk.stop() if rank == 0 else None
+    ms32 = max_over_ranks(ms32)
+    value = ws * ncells * 3 / (ms32 * 1e-3)
+    roof = stage_roofline(s32, 5, 4, 4, ncells, hbm)
+    roof["peak_source"] = peak_src
+
+    # ---------------------------------------------------------------- FP64 plain
+    fp64 = None
+    if not args.skip_fp64:
+        s64 = amrvac.AmrSolver(**kh_kwargs(precision="fp64", stream=stream.cuda_stream))
+        s64.set_prim(V)
+        s64.run(3)
+        s64.sync()
+        k64 = max(3, min(200, args.steps // 20))
+        barrier()
+        ms64 = max_over_ranks(time_steps(torch, s64, stream, k64))
+        r64 = stage_roofline(s64, 2, 4, 8, ncells, hbm)
+        fp64 = {"value": ws * ncells * 3 / (ms64 * 1e-3), "ms_per_step": ms64, "steps": k64,
+                "stage_achieved_gbs": r64["achieved"], "stage_frac_hbm": r64["frac"],
+                "fp32_over_fp64": (ms64 / ms32)}
+        s64.close()
+
+    # ---------------------------------------------------------------- end to end
+    e2e = None
+    if not args.skip_e2e:
+        U = s32.read_state()
+        nbytes = U.size * 8
+        hin = torch.from_numpy(U.reshape(-1).copy()).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        k = max(3, min(20, args.steps // 100))
+        s32.set_state(hin, primitive=False)
+        s32.run(1)
+        s32.read_state(hout.view(U.shape))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k):
+            s32.set_state(hin, primitive=False)  # H2D of the step's input (pinned, float64)
+            s32.run(1)
+            s32.read_state(hout.view(U.shape))   # D2H of the step's result (float64)
+        torch.cuda.synchronize()
+        el = max_over_ranks((time.perf_counter() - t0) / k)
+        e2e = {"value": ws * ncells * 3 / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "ms_per_step": el * 1e3,
+               "path": "amr_set_state(host) + amr_run(1) + amr_read_state(host), float64 conserved state"}
+
+    totals = s32.totals().tolist()
+    s32.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        cpu = oracle_cpu_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": ncells, "stages_per_step": 3, "seed": 2004,
+                       "l2": "no flush: per-stage working set 201 MB (3 float32 state arrays) > 129 MB L2",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU, all blocks resident"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches, "fp64_plain": fp64, "totals_fp64": totals,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -152,6 +152,13 @@ int amr_face_neighbors(const amr_handle* h, int* kind, int* nbr, long long cap);
  * [var][face][layer 0..1][tangential cell]; for checks.  Synchronous. */
 int amr_face_ghosts(amr_handle* h, long long leaf, double* out, long long cap);
 
+/* One step like amr_step, launched kernel by kernel (no graph) with a CUDA
+ * event recorded on the handle's stream after every kernel: ms[i] = duration
+ * of kernel i, kind[i] = 0 stage update, 1 ghost fill, 2 reflux, 3 reduction.
+ * cap = capacity of ms / kind; *nkernels = kernels of the step.  Synchronous.
+ * For measurement only (the events add a little launch overhead). */
+int amr_profile_step(amr_handle* h, double t_end, float* ms, int* kind, int cap, int* nkernels);
+
 /* Device launch counters: kernels launched by this handle since creation. */
 int amr_kernel_launches(const amr_handle* h, long long* n);
 

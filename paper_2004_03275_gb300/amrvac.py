@@ -81,6 +81,7 @@ _SIGS = {
     "amr_face_neighbors": ([_vp, _ip, _ip, C.c_longlong], C.c_int),
     "amr_face_ghosts": ([_vp, C.c_longlong, _dp, C.c_longlong], C.c_int),
     "amr_kernel_launches": ([_vp, _llp], C.c_int),
+    "amr_profile_step": ([_vp, C.c_double, C.POINTER(C.c_float), _ip, C.c_int, _ip], C.c_int),
     "mg_create": ([C.POINTER(MgConfig), C.POINTER(_vp)], C.c_int),
     "mg_destroy": ([_vp], C.c_int),
     "mg_last_error": ([_vp], C.c_char_p),
@@ -293,6 +294,15 @@ class AmrSolver:
         out = np.zeros((self.nv, 2 * self.ndim, 2, nt))
         _check(self.lib.amr_face_ghosts(self.h, leaf, out.ctypes.data_as(_dp), out.size), self.h)
         return out
+
+    def profile_step(self, t_end=1e300):
+        """One step kernel by kernel; returns [(kind, ms)] (kind 0 stage, 1 ghost, 2 reflux, 3 reduce)."""
+        cap = 64
+        ms = (C.c_float * cap)()
+        kind = (C.c_int * cap)()
+        n = C.c_int()
+        _check(self.lib.amr_profile_step(self.h, t_end, ms, kind, cap, C.byref(n)), self.h)
+        return [(kind[i], ms[i]) for i in range(n.value)]
 
     def kernel_launches(self):
         n = C.c_longlong()

@@ -267,13 +267,30 @@ struct amr_handle {
   Tables tb;
   Geometry G{};
   // device state
-  DBuf U0, Ua, Ub, Unew, stagebuf, partials, ctl, nb, level, ffx, slabdesc, slabbuf, rec, fflux, ops, errbuf;
+  DBuf U0, Ua, Ub, Unew, stagebuf, partials, gpart, gcount, ctl, nb, level, ffx, slabdesc, slabbuf, rec, fflux, ops, errbuf;
   DevCtl* h_ctl = nullptr;  // pinned mirror
   long long steps_seen = 0;
   cudaGraphExec_t graph = nullptr;
   int graph_kernels = 0;
   long long launches = 0;
-
+  // profiling: when prof_ev is set, events bracket every kernel of a step
+  std::vector<cudaEvent_t>* prof_ev = nullptr;  // pairs (before, after)
+  std::vector<int>* prof_kind = nullptr;        // 0 stage, 1 ghost fill, 2 reflux, 3 reduce
+  void mark_begin() {
+    if (!prof_ev) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, stream);
+    prof_ev->push_back(e);
+  }
+  void mark(int kind) {
+    if (!prof_ev) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, stream);
+    prof_ev->push_back(e);
+    prof_kind->push_back(kind);
+  }
   int fail(int code, const std::string& m) {
     err = m;
     return code;
@@ -292,8 +309,10 @@ struct amr_handle {
   template <typename real, int ND>
   int dispatch_stage(const StageArgs<real>& a) {
     amr_handle* h = this;
+    mark_begin();
     CK((EulerOps<real, ND>::stage(B, cfg.flux, a, G, stream)));
     ++launches;
+    mark(0);
     return AMR_OK;
   }
 
@@ -315,9 +334,11 @@ struct amr_handle {
       real alpha = s == 0 ? real(0) : (nst == 2 ? w2a[0] : w3a[s][0]);
       real beta = s == 0 ? real(1) : (nst == 2 ? w2a[1] : w3a[s][1]);
       if (jumps) {
+        mark_begin();
         CK((EulerOps<real, ND>::ghost_fill(B, Us, slabbuf.as<real>(), slabdesc.as<SlabDesc>(),
                                            (int)tb.slabs.size(), stream)));
         ++launches;
+        mark(1);
       }
       StageArgs<real> a{};
       a.Us = Us;
@@ -330,6 +351,8 @@ struct amr_handle {
       a.fflux = fflux.as<real>();
       a.ctl = ctl.as<DevCtl>();
       a.partials = partials.as<double>();
+      a.gpart = gpart.as<double>();
+      a.gcount = gcount.as<unsigned>();
       a.alpha = alpha;
       a.beta = beta;
       a.stage1 = s == 0;
@@ -340,15 +363,19 @@ struct amr_handle {
       int rc = dispatch_stage<real, ND>(a);
       if (rc) return rc;
       if (jumps) {
+        mark_begin();
         CK((EulerOps<real, ND>::reflux(B, out, fflux.as<real>(), rec.as<RefluxRec>(), (int)tb.rec.size(),
                                        level.as<int>(), G, ctl.as<DevCtl>(), beta, stream)));
         ++launches;
+        mark(2);
       }
     }
     if (jumps) {
-      CK((EulerOps<real, ND>::reduce(B, s0, level.as<int>(), G, ctl.as<DevCtl>(), partials.as<double>(), nl, 1,
-                                     stream)));
+      mark_begin();
+      CK((EulerOps<real, ND>::reduce(B, s0, level.as<int>(), G, ctl.as<DevCtl>(), partials.as<double>(),
+                                     gpart.as<double>(), gcount.as<unsigned>(), nl, 1, stream)));
       ++launches;
+      mark(3);
     }
     return AMR_OK;
   }
@@ -431,7 +458,8 @@ int refresh_reduce(amr_handle* h) {
   int nl = (int)h->tree.leaves.size();
   return with_type(h, [&]<typename real, int ND>() -> int {
     cudaError_t e = EulerOps<real, ND>::reduce(h->B, h->U0.as<real>(), h->level.as<int>(), h->G,
-                                               h->ctl.as<DevCtl>(), h->partials.as<double>(), nl, 0, h->stream);
+                                               h->ctl.as<DevCtl>(), h->partials.as<double>(), h->gpart.as<double>(),
+                                               h->gcount.as<unsigned>(), nl, 0, h->stream);
     if (e != cudaSuccess) return h->fail_cuda(e, "reduce");
     ++h->launches;
     return AMR_OK;
@@ -533,11 +561,18 @@ int amr_create(const amr_config* cfg, amr_handle** out) {
       if (d < h->nd) dV = dV * G.dx[l][d];
     }
     G.dV[l] = dV;
+    for (int d = 0; d < 3; ++d) {
+      G.dxf[l][d] = (float)G.dx[l][d];
+      G.idxf[l][d] = (float)(1.0 / G.dx[l][d]);
+    }
   }
+  G.gammaf = (float)cfg->gamma;
   size_t sb = h->state_bytes((size_t)cfg->max_blocks);
   cudaError_t e;
   if ((e = h->U0.ensure(sb)) != cudaSuccess || (e = h->Ua.ensure(sb)) != cudaSuccess ||
       (e = h->Ub.ensure(sb)) != cudaSuccess || (e = h->ctl.ensure(sizeof(DevCtl))) != cudaSuccess ||
+      (e = h->gpart.ensure(((size_t)cfg->max_blocks / kGroupCTAs + 2) * 5 * sizeof(double))) != cudaSuccess ||
+      (e = h->gcount.ensure(((size_t)cfg->max_blocks / kGroupCTAs + 2) * sizeof(unsigned))) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_ctl, sizeof(DevCtl))) != cudaSuccess)
     return e == cudaErrorMemoryAllocation ? AMR_ERR_OOM : AMR_ERR_CUDA;
   DevCtl c0{};
@@ -545,11 +580,12 @@ int amr_create(const amr_config* cfg, amr_handle** out) {
   c0.t_end = 1e300;
   if (cudaMemcpy(h->ctl.p, &c0, sizeof(DevCtl), cudaMemcpyHostToDevice) != cudaSuccess) return AMR_ERR_CUDA;
   if (cudaMemset(h->U0.p, 0, h->state_bytes(T.leaves.size())) != cudaSuccess) return AMR_ERR_CUDA;
+  if (cudaMemset(h->gcount.p, 0, h->gcount.cap) != cudaSuccess) return AMR_ERR_CUDA;
   int rc = rebuild(h.get());
   if (rc) return rc;
   amr_handle* hp = h.get();
   rc = with_type(hp, [&]<typename real, int ND>() -> int {
-    cudaError_t e2 = EulerOps<real, ND>::prepare(hp->B, hp->cfg.flux);
+    cudaError_t e2 = EulerOps<real, ND>::prepare(hp->B, hp->cfg.flux, hp->cfg.limiter);
     return e2 == cudaSuccess ? AMR_OK : hp->fail_cuda(e2, "prepare");
   });
   if (rc) return rc;
@@ -560,7 +596,7 @@ int amr_create(const amr_config* cfg, amr_handle** out) {
 int amr_destroy(amr_handle* h) {
   if (!h) return AMR_ERR_INVALID_ARG;
   h->drop_graph();
-  for (DBuf* b : {&h->U0, &h->Ua, &h->Ub, &h->Unew, &h->stagebuf, &h->partials, &h->ctl, &h->nb, &h->level,
+  for (DBuf* b : {&h->U0, &h->Ua, &h->Ub, &h->Unew, &h->stagebuf, &h->partials, &h->gpart, &h->gcount, &h->ctl, &h->nb, &h->level,
                   &h->ffx, &h->slabdesc, &h->slabbuf, &h->rec, &h->fflux, &h->ops, &h->errbuf})
     b->release();
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
@@ -895,6 +931,37 @@ int amr_face_ghosts(amr_handle* h, long long leaf, double* out, long long cap) {
   CK(cudaMemcpyAsync(out, h->stagebuf.p, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return AMR_OK;
+}
+
+int amr_profile_step(amr_handle* h, double t_end, float* ms, int* kind, int cap, int* nkernels) {
+  if (!h || !ms || !kind || !nkernels) return AMR_ERR_INVALID_ARG;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kd;
+  cudaEvent_t e0;
+  CK(cudaEventCreate(&e0));
+  CK(ctl_set_t_end(h->ctl.as<DevCtl>(), t_end, h->stream));
+  ++h->launches;
+  CK(cudaEventRecord(e0, h->stream));
+  h->prof_ev = &ev;
+  h->prof_kind = &kd;
+  int rc = with_type(h, [&]<typename real, int ND>() -> int { return h->enqueue_step<real, ND>(); });
+  h->prof_ev = nullptr;
+  h->prof_kind = nullptr;
+  cudaError_t es = cudaStreamSynchronize(h->stream);
+  int n = (int)kd.size();
+  *nkernels = n;
+  if (rc == AMR_OK && es == cudaSuccess && n <= cap && ev.size() == 2 * kd.size()) {
+    for (int i = 0; i < n; ++i) {
+      cudaEventElapsedTime(&ms[i], ev[2 * i], ev[2 * i + 1]);
+      kind[i] = kd[i];
+    }
+  }
+  for (auto e : ev) cudaEventDestroy(e);
+  cudaEventDestroy(e0);
+  if (rc) return rc;
+  if (es != cudaSuccess) return h->fail_cuda(es, "profile step");
+  if (n > cap) return AMR_ERR_INVALID_ARG;
+  return sync_ctl(h);
 }
 
 int amr_kernel_launches(const amr_handle* h, long long* n) {

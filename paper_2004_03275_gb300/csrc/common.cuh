@@ -6,6 +6,7 @@
 namespace amrgpu {
 
 constexpr int kMaxLevel = 16;
+constexpr int kGroupCTAs = 64;  // CTAs per first-level group of the two-level reduction finish
 
 // Device control block of one solver: time, CFL step, reductions.  Written only
 // by the last CTA of a reduction pass (no spin waits anywhere).
@@ -51,6 +52,10 @@ struct Geometry {
   double gamma, cfl;
   double dx[kMaxLevel + 1][3];
   double dV[kMaxLevel + 1];
+  // float copies for the float32 kernels (float32 code touches no float64 unit in the cell loop)
+  float gammaf;
+  float dxf[kMaxLevel + 1][3];
+  float idxf[kMaxLevel + 1][3];
 };
 
 // ------------------------------------------------------------ stage args --
@@ -66,6 +71,8 @@ struct StageArgs {
   real* fflux;         // [slot][var][nt]
   DevCtl* ctl;
   double* partials;    // [leaf][var]
+  double* gpart;       // [group of CTAs][var]
+  unsigned* gcount;    // [group of CTAs], zero between passes
   real alpha, beta;    // out = alpha*U0 + beta*(Us - dt*div); alpha == 0: out = Us - dt*div
   int stage1;
   int fuse_reduce;     // fold max rate / totals / time update into this pass

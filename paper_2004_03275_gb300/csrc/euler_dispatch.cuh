@@ -1,7 +1,10 @@
 // Kernel launch wrappers; included after euler_kernels.cuh by each
 // (type, dimension) translation unit.
 #pragma once
+#include <type_traits>
+
 #include "euler_ops.h"
+#include "stage2d_f32.cuh"
 
 namespace amrgpu {
 
@@ -28,9 +31,57 @@ cudaError_t stage_launch(const StageArgs<real>& a, const Geometry& G, cudaStream
   return cudaGetLastError();
 }
 
+// persistent grid: resident CTAs per SM x SMs, computed once per kernel outside any capture
+template <int B, int FLUX, int LIM>
+int& stage2d_f32_grid() {
+  static int g = 0;
+  return g;
+}
+
+template <int B, int FLUX, int LIM>
+cudaError_t stage2d_f32_prepare_one() {
+  int dev, sms, per;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stage2d_f32_kernel<B, FLUX, LIM>, 256, 0);
+  if (e == cudaSuccess) stage2d_f32_grid<B, FLUX, LIM>() = sms * (per > 0 ? per : 1);
+  return e;
+}
+
+template <int B, int FLUX>
+cudaError_t stage2d_f32_prepare(int lim) {
+  switch (lim) {
+    case LIM_MINMOD: return stage2d_f32_prepare_one<B, FLUX, LIM_MINMOD>();
+    case LIM_VANLEER: return stage2d_f32_prepare_one<B, FLUX, LIM_VANLEER>();
+    case LIM_KOREN: return stage2d_f32_prepare_one<B, FLUX, LIM_KOREN>();
+    default: return stage2d_f32_prepare_one<B, FLUX, LIM_NONE>();
+  }
+}
+
+template <int B, int FLUX, int LIM>
+void stage2d_f32_go(const StageArgs<float>& a, const Geometry& G, cudaStream_t s) {
+  constexpr int LPB = 256 / (B * B);
+  int nslots = (a.nleaves + LPB - 1) / LPB;
+  int cap = stage2d_f32_grid<B, FLUX, LIM>();
+  int grid = cap > 0 && cap < nslots ? cap : nslots;
+  stage2d_f32_kernel<B, FLUX, LIM><<<grid, 256, 0, s>>>(a, G);
+}
+
+template <int B, int FLUX>
+cudaError_t stage2d_f32_launch(const StageArgs<float>& a, const Geometry& G, cudaStream_t s) {
+  switch (a.limiter) {
+    case LIM_MINMOD: stage2d_f32_go<B, FLUX, LIM_MINMOD>(a, G, s); break;
+    case LIM_VANLEER: stage2d_f32_go<B, FLUX, LIM_VANLEER>(a, G, s); break;
+    case LIM_KOREN: stage2d_f32_go<B, FLUX, LIM_KOREN>(a, G, s); break;
+    default: stage2d_f32_go<B, FLUX, LIM_NONE>(a, G, s); break;
+  }
+  return cudaGetLastError();
+}
+
 // opt in to the 3D kernel's dynamic shared memory (outside any stream capture)
 template <typename real, int ND, int B, int FLUX>
-cudaError_t stage_prepare() {
+cudaError_t stage_prepare(int lim) {
+  if constexpr (std::is_same<real, float>::value && ND == 2) return stage2d_f32_prepare<B, FLUX>(lim);
   if constexpr (ND == 3)
     return cudaFuncSetAttribute(stage_kernel_3d<real, B, FLUX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(Stage3DSmem<real, B>));
@@ -39,6 +90,14 @@ cudaError_t stage_prepare() {
 
 template <typename real, int ND, int B>
 cudaError_t stage_b(int flux, const StageArgs<real>& a, const Geometry& G, cudaStream_t s) {
+  if constexpr (std::is_same<real, float>::value && ND == 2) {
+    if (a.nleaves == 0) return cudaSuccess;
+    switch (flux) {
+      case FLUX_TVDLF: return stage2d_f32_launch<B, FLUX_TVDLF>(a, G, s);
+      case FLUX_HLL: return stage2d_f32_launch<B, FLUX_HLL>(a, G, s);
+      default: return stage2d_f32_launch<B, FLUX_HLLC>(a, G, s);
+    }
+  }
   switch (flux) {
     case FLUX_TVDLF: return stage_launch<real, ND, B, FLUX_TVDLF>(a, G, s);
     case FLUX_HLL: return stage_launch<real, ND, B, FLUX_HLL>(a, G, s);
@@ -61,25 +120,26 @@ cudaError_t EulerOps<real, ND>::stage(int B, int flux, const StageArgs<real>& a,
 }
 
 template <typename real, int ND>
-cudaError_t EulerOps<real, ND>::prepare(int B, int flux) {
-#define CALL(BB)                                                                          \
-  (flux == FLUX_TVDLF ? detail::stage_prepare<real, ND, BB, FLUX_TVDLF>()                \
-                      : (flux == FLUX_HLL ? detail::stage_prepare<real, ND, BB, FLUX_HLL>() \
-                                          : detail::stage_prepare<real, ND, BB, FLUX_HLLC>()))
+cudaError_t EulerOps<real, ND>::prepare(int B, int flux, int lim) {
+#define CALL(BB)                                                                             \
+  (flux == FLUX_TVDLF ? detail::stage_prepare<real, ND, BB, FLUX_TVDLF>(lim)                \
+                      : (flux == FLUX_HLL ? detail::stage_prepare<real, ND, BB, FLUX_HLL>(lim) \
+                                          : detail::stage_prepare<real, ND, BB, FLUX_HLLC>(lim)))
   return AMRGPU_BSWITCH(B, CALL);
 #undef CALL
 }
 
 template <typename real, int ND>
 cudaError_t EulerOps<real, ND>::reduce(int B, const real* U, const int* level, const Geometry& G, DevCtl* ctl,
-                                       double* partials, int nleaves, int advance, cudaStream_t s) {
+                                       double* partials, double* gpart, unsigned* gcount, int nleaves,
+                                       int advance, cudaStream_t s) {
   if (nleaves == 0) return cudaSuccess;
 #define CALL(BB)                                                                                   \
   ([&]() {                                                                                         \
     constexpr int NC = Tile<ND, BB>::NC;                                                           \
     constexpr int LPB = NC >= 256 ? 1 : 256 / NC;                                                  \
     reduce_kernel<real, ND, BB><<<(nleaves + LPB - 1) / LPB, 256, 0, s>>>(U, level, G, ctl, partials, \
-                                                                         nleaves, advance);        \
+                                                                         gpart, gcount, nleaves, advance); \
     return cudaGetLastError();                                                                     \
   }())
   return AMRGPU_BSWITCH(B, CALL);

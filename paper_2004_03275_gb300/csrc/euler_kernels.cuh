@@ -202,6 +202,34 @@ __device__ __forceinline__ double stage_dt(const DevCtl* ctl) {
   return dt;
 }
 
+// dt of the current step computed once per CTA (thread 0) and shared: keeps
+// float64 arithmetic out of the per-cell path of the float32 kernels.
+__device__ __forceinline__ double cta_stage_dt(const DevCtl* ctl, float* dtf) {
+  __shared__ double s_dt;
+  __shared__ float s_dtf;
+  if (threadIdx.x == 0) {
+    double d = stage_dt(ctl);
+    s_dt = d;
+    s_dtf = (float)d;
+  }
+  __syncthreads();
+  if (dtf) *dtf = s_dtf;
+  return s_dt;
+}
+
+template <typename real>
+__device__ __forceinline__ real geo_dx(const Geometry& G, int lev, int d);
+template <>
+__device__ __forceinline__ double geo_dx<double>(const Geometry& G, int lev, int d) { return G.dx[lev][d]; }
+template <>
+__device__ __forceinline__ float geo_dx<float>(const Geometry& G, int lev, int d) { return G.dxf[lev][d]; }
+template <typename real>
+__device__ __forceinline__ real geo_gamma(const Geometry& G);
+template <>
+__device__ __forceinline__ double geo_gamma<double>(const Geometry& G) { return G.gamma; }
+template <>
+__device__ __forceinline__ float geo_gamma<float>(const Geometry& G) { return G.gammaf; }
+
 // Signal rate sum_d (|v_d| + c)/dx_d of one cell (Sec. 1.2, phys_get_cmax);
 // marks non-physical states.
 template <typename real, int ND>
@@ -216,6 +244,98 @@ __device__ __forceinline__ real cell_rate(const real* U, real gam, real gm1, con
   return s;
 }
 
+// Fixed-order block sum of NV doubles held by every thread (butterfly per warp,
+// warps in order); the result is valid in thread 0.
+template <int NV, int NTHREADS>
+__device__ __forceinline__ void block_sum_fixed(double* acc) {
+  __shared__ double wred[NTHREADS / 32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+  if (lane == 0)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) wred[warp][v] = acc[v];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = wred[0][v];
+    for (int w = 1; w < NTHREADS / 32; ++w)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] += wred[w][v];
+  }
+}
+
+// Two-level finish of a reduction pass.  The last CTA to finish in each group of
+// kGroupCTAs CTAs sums that group's per-leaf partials (fixed order) into gpart;
+// the last group to finish sums the group partials (fixed order), sets the
+// totals, dt_cfl = cfl/smax and, when `advance`, t += dt.  Every thread of every
+// CTA calls this after its CTA's partials and atomicMax are issued.  No CTA
+// waits on another; counters are reset by the CTA that consumed them.
+template <typename real, int NV, int NTHREADS>
+__device__ void last_cta_finish(DevCtl* ctl, const double* partials, double* gpart, unsigned* gcount,
+                                int nleaves, int lpb, bool advance, double dt) {
+  __shared__ bool flag;
+  const int g = blockIdx.x / kGroupCTAs;
+  const int ngroups = (gridDim.x + kGroupCTAs - 1) / kGroupCTAs;
+  const int gsize = min(kGroupCTAs, (int)gridDim.x - g * kGroupCTAs);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) flag = atomicAdd(&gcount[g], 1u) == (unsigned)(gsize - 1);
+  __syncthreads();
+  if (!flag) return;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  // the group's CTAs processed slots s = g*kGroupCTAs + i + k*gridDim (i < gsize, k >= 0),
+  // each slot holding lpb consecutive leaves; summed in a fixed order
+  const int nslots = (nleaves + lpb - 1) / lpb;
+  const int nj = gsize * ((nslots + (int)gridDim.x - 1) / (int)gridDim.x);
+  for (int j = threadIdx.x; j < nj; j += NTHREADS) {
+    int s = g * kGroupCTAs + (j % gsize) + (j / gsize) * (int)gridDim.x;
+    if (s >= nslots) continue;
+    for (int q = 0; q < lpb; ++q) {
+      int l = s * lpb + q;
+      if (l < nleaves)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] += __ldcg(&partials[(size_t)l * NV + v]);
+    }
+  }
+  block_sum_fixed<NV, NTHREADS>(acc);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) gpart[(size_t)g * NV + v] = acc[v];
+    gcount[g] = 0u;
+    __threadfence();
+    flag = atomicAdd(&ctl->done, 1u) == (unsigned)(ngroups - 1);
+  }
+  __syncthreads();
+  if (!flag) return;
+  __threadfence();
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  for (int q = threadIdx.x; q < ngroups; q += NTHREADS)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] += __ldcg(&gpart[(size_t)q * NV + v]);
+  __syncthreads();  // wred reuse
+  block_sum_fixed<NV, NTHREADS>(acc);
+  if (threadIdx.x == 0) {
+    volatile DevCtl* c = ctl;
+    for (int v = 0; v < NV; ++v) c->totals[v] = acc[v];
+    unsigned long long bits = atomicAdd(&ctl->smax_bits, 0ull);
+    double smax = MaxKey<real>::dec(bits);
+    if (advance) {
+      c->t = c->t + dt;
+      c->dt_last = dt;
+      c->steps = c->steps + 1;
+    }
+    c->dt_cfl = c->cfl / smax;
+    c->smax_bits = 0ull;
+    c->done = 0u;
+  }
+}
+
 // Block-wide reduction of (max rate, per-variable FP64 sums) and the last-CTA
 // finalisation: totals = fixed-order sum of per-leaf partials, dt_cfl = cfl/smax,
 // and, when `advance`, t += dt of the step just taken.  Deterministic for any
@@ -223,11 +343,11 @@ __device__ __forceinline__ real cell_rate(const real* U, real gam, real gm1, con
 template <typename real, int NV, int NTHREADS>
 __device__ void block_reduce_finish(real rate, const double* sums, int leaf_first, int nleaf_cta,
                                     int leaf_of_thread, const Geometry& G, DevCtl* ctl, double* partials,
-                                    int nleaves, bool advance, double dt, int bad) {
+                                    double* gpart, unsigned* gcount, int nleaves, bool advance, double dt,
+                                    int bad) {
   __shared__ double red[NTHREADS / 32][4][NV];  // per warp, per local leaf (<= 4), per var
   __shared__ real wmax[NTHREADS / 32];
   __shared__ int sbad;
-  __shared__ bool is_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) sbad = 0;
   __syncthreads();
@@ -286,48 +406,7 @@ __device__ void block_reduce_finish(real rate, const double* sums, int leaf_firs
   }
   __threadfence();
   __syncthreads();  // partials written and red[] consumed before it is reused below
-  if (threadIdx.x == 0) {
-    unsigned int ticket = atomicAdd(&ctl->done, 1u);
-    is_last = (ticket == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  // last CTA: fixed-order totals over leaves (strided per thread, butterfly per
-  // warp, warps in order)
-  double acc[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
-  for (int l = threadIdx.x; l < nleaves; l += NTHREADS)
-#pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] += __ldcg(&partials[(size_t)l * NV + v]);
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
-  if (lane == 0)
-#pragma unroll
-    for (int v = 0; v < NV; ++v) red[warp][0][v] = acc[v];
-  __syncthreads();
-  double tot[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) tot[v] = red[0][0][v];
-  for (int w = 1; w < NTHREADS / 32; ++w)
-#pragma unroll
-    for (int v = 0; v < NV; ++v) tot[v] += red[w][0][v];
-  if (threadIdx.x == 0) {
-    volatile DevCtl* c = ctl;
-    for (int v = 0; v < NV; ++v) c->totals[v] = tot[v];
-    unsigned long long bits = atomicAdd(&ctl->smax_bits, 0ull);
-    double smax = MaxKey<real>::dec(bits);
-    if (advance) {
-      c->t = c->t + dt;
-      c->dt_last = dt;
-      c->steps = c->steps + 1;
-    }
-    c->dt_cfl = c->cfl / smax;
-    c->smax_bits = 0ull;
-    c->done = 0u;
-  }
+  last_cta_finish<real, NV, NTHREADS>(ctl, partials, gpart, gcount, nleaves, nleaf_cta, advance, dt);
 }
 
 // ------------------------------------------------------------ ghost fetch --
@@ -383,10 +462,11 @@ stage_kernel_12(StageArgs<real> a, Geometry G) {
   __shared__ real W[LPB][NV][PP];
   __shared__ real FXs[LPB][ND][NV][NFX];
 
-  const double dt = stage_dt(a.ctl);
+  float dtf;
+  const double dt = cta_stage_dt(a.ctl, &dtf);
   if (!(dt > 0.0)) return;
-  const real dtr = (real)dt;
-  const real gam = (real)G.gamma, gm1 = gam - real(1);
+  const real dtr = sizeof(real) == 4 ? (real)dtf : (real)dt;
+  const real gam = geo_gamma<real>(G), gm1 = gam - real(1);
   const int lb = threadIdx.x / NC, tc = threadIdx.x % NC;
   const int leaf = blockIdx.x * LPB + lb;
   const bool active = leaf < a.nleaves;
@@ -460,7 +540,7 @@ stage_kernel_12(StageArgs<real> a, Geometry G) {
     const int lev = a.level[leaf];
     real dx[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) dx[d] = (real)G.dx[lev][d];
+    for (int d = 0; d < 3; ++d) dx[d] = geo_dx<real>(G, lev, d);
     real Un[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -484,7 +564,7 @@ stage_kernel_12(StageArgs<real> a, Geometry G) {
   }
   if (a.fuse_reduce)
     block_reduce_finish<real, NV, THREADS>(rate, sums, blockIdx.x * LPB, LPB, lb, G, a.ctl, a.partials,
-                                           a.nleaves, true, dt, bad);
+                                           a.gpart, a.gcount, a.nleaves, true, dt, bad);
 }
 
 // ============================================================ 3D stage ==
@@ -506,10 +586,11 @@ __global__ void __launch_bounds__(256) stage_kernel_3d(StageArgs<real> a, Geomet
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Stage3DSmem<real, B>& S = *reinterpret_cast<Stage3DSmem<real, B>*>(smem_raw);
 
-  const double dt = stage_dt(a.ctl);
+  float dtf;
+  const double dt = cta_stage_dt(a.ctl, &dtf);
   if (!(dt > 0.0)) return;
-  const real dtr = (real)dt;
-  const real gam = (real)G.gamma, gm1 = gam - real(1);
+  const real dtr = sizeof(real) == 4 ? (real)dtf : (real)dt;
+  const real gam = geo_gamma<real>(G), gm1 = gam - real(1);
   const int lb = threadIdx.x / COLS, tc = threadIdx.x % COLS;
   const int leaf = blockIdx.x * LPB + lb;
   const bool active = leaf < a.nleaves;
@@ -518,7 +599,7 @@ __global__ void __launch_bounds__(256) stage_kernel_3d(StageArgs<real> a, Geomet
   const int lev = active ? a.level[leaf] : 1;
   real dx[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) dx[d] = (real)G.dx[lev][d];
+  for (int d = 0; d < 3; ++d) dx[d] = geo_dx<real>(G, lev, d);
 
   // load plane z (-2 .. B+1) of this leaf into ring slot; interior planes get x/y ghosts
   auto load_plane = [&](int z, real (&Ucol)[NV], bool keep) {
@@ -667,8 +748,8 @@ __global__ void __launch_bounds__(256) stage_kernel_3d(StageArgs<real> a, Geomet
     }
   }
   if (a.fuse_reduce)
-    block_reduce_finish<real, NV, 256>(rate, sums, blockIdx.x * LPB, LPB, lb, G, a.ctl, a.partials, a.nleaves,
-                                       true, dt, bad);
+    block_reduce_finish<real, NV, 256>(rate, sums, blockIdx.x * LPB, LPB, lb, G, a.ctl, a.partials, a.gpart,
+                                       a.gcount, a.nleaves, true, dt, bad);
 }
 
 // ========================================================= reduce kernel ==
@@ -676,26 +757,25 @@ __global__ void __launch_bounds__(256) stage_kernel_3d(StageArgs<real> a, Geomet
 // regrid, or the refluxed last stage of a step on a tree with level jumps).
 template <typename real, int ND, int B>
 __global__ void __launch_bounds__(256) reduce_kernel(const real* __restrict__ U, const int* __restrict__ level,
-                                                     Geometry G, DevCtl* ctl, double* partials, int nleaves,
-                                                     int advance) {
+                                                     Geometry G, DevCtl* ctl, double* partials, double* gpart,
+                                                     unsigned* gcount, int nleaves, int advance) {
   constexpr int NV = ND + 2, NC = Tile<ND, B>::NC;
   constexpr int CPT = NC >= 256 ? NC / 256 : 1;       // cells per thread
   constexpr int LPB = NC >= 256 ? 1 : 256 / NC;
   const int lb = threadIdx.x / (NC / CPT), tc = threadIdx.x % (NC / CPT);
   const int leaf = blockIdx.x * LPB + lb;
-  const real gam = (real)G.gamma, gm1 = gam - real(1);
+  const real gam = geo_gamma<real>(G), gm1 = gam - real(1);
   real rate = real(0);
   double sums[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) sums[v] = 0.0;
   int bad = 0;
-  double dt = 0.0;
-  if (advance) dt = stage_dt(ctl);
+  double dt = cta_stage_dt(ctl, nullptr);
   if (leaf < nleaves) {
     int lev = level[leaf];
     real dx[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) dx[d] = (real)G.dx[lev][d];
+    for (int d = 0; d < 3; ++d) dx[d] = geo_dx<real>(G, lev, d);
     for (int c = tc; c < NC; c += NC / CPT) {
       real Uc[NV];
 #pragma unroll
@@ -705,8 +785,8 @@ __global__ void __launch_bounds__(256) reduce_kernel(const real* __restrict__ U,
       for (int v = 0; v < NV; ++v) sums[v] += (double)Uc[v] * G.dV[lev];
     }
   }
-  block_reduce_finish<real, NV, 256>(rate, sums, blockIdx.x * LPB, LPB, lb, G, ctl, partials, nleaves,
-                                     advance != 0, dt, bad);
+  block_reduce_finish<real, NV, 256>(rate, sums, blockIdx.x * LPB, LPB, lb, G, ctl, partials, gpart, gcount,
+                                     nleaves, advance != 0, dt, bad);
 }
 
 // ====================================================== ghost slab fill ==
@@ -814,8 +894,9 @@ __global__ void reflux_kernel(real* __restrict__ out, const real* __restrict__ f
                               int nrec, const int* __restrict__ level, Geometry G, const DevCtl* ctl, real beta) {
   constexpr int NV = ND + 2, NC = Tile<ND, B>::NC, NT = Tile<ND, B>::NT;
   long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float dtf;
+  double dt = cta_stage_dt(ctl, &dtf);
   if (gid >= (long long)nrec * NV * NT) return;
-  double dt = stage_dt(ctl);
   if (!(dt > 0.0)) return;
   int t = gid % NT, v = (gid / NT) % NV, r = gid / (NT * NV);
   RefluxRec R = rec[r];
@@ -839,8 +920,8 @@ __global__ void reflux_kernel(real* __restrict__ out, const real* __restrict__ f
   real mean = sum * (real(1) / real(1 << (ND - 1)));
   real Fc = fflux[((size_t)R.cslot * NV + v) * NT + t];
   int lev = level[R.coarse];
-  real dxc = (real)G.dx[lev][d];
-  real corr = beta * (real)dt * (mean - Fc) / dxc;
+  real dxc = geo_dx<real>(G, lev, d);
+  real corr = beta * (sizeof(real) == 4 ? (real)dtf : (real)dt) * (mean - Fc) / dxc;
   int n = side == 0 ? 0 : B - 1;
   int cell = compose_cell<ND, B>(d, n, t);
   size_t o = ((size_t)R.coarse * NV + v) * NC + cell;

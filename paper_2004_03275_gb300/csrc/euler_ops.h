@@ -7,10 +7,11 @@ namespace amrgpu {
 
 template <typename real, int ND>
 struct EulerOps {
-  static cudaError_t prepare(int B, int flux);
+  static cudaError_t prepare(int B, int flux, int limiter);
   static cudaError_t stage(int B, int flux, const StageArgs<real>& a, const Geometry& G, cudaStream_t s);
   static cudaError_t reduce(int B, const real* U, const int* level, const Geometry& G, DevCtl* ctl,
-                            double* partials, int nleaves, int advance, cudaStream_t s);
+                            double* partials, double* gpart, unsigned* gcount, int nleaves, int advance,
+                            cudaStream_t s);
   static cudaError_t ghost_fill(int B, const real* U, real* slabs, const SlabDesc* desc, int nslabs,
                                 cudaStream_t s);
   static cudaError_t reflux(int B, real* out, const real* fflux, const RefluxRec* rec, int nrec,
