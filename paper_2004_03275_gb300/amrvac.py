@@ -308,3 +308,116 @@ class AmrSolver:
         n = C.c_longlong()
         _check(self.lib.amr_kernel_launches(self.h, C.byref(n)), self.h)
         return n.value
+
+
+class MgSolver:
+    """Owns one mg_handle: batched Helmholtz multigrid (lambda_i - lap) x = b."""
+
+    def __init__(self, ndim, n_cells, lam, L, nu1=2, nu2=2, max_cycles=50, rtol=1e-10, coarse_max=8,
+                 precision="fp32", stream=None):
+        self.lib = load()
+        self.n_cells = np.ascontiguousarray(n_cells, dtype=np.int32)
+        self.lam = np.ascontiguousarray(np.broadcast_to(np.asarray(lam, dtype=np.float64), self.n_cells.shape))
+        c = MgConfig()
+        c.ndim = ndim
+        c.n_inst = len(self.n_cells)
+        c.n_cells = self.n_cells.ctypes.data_as(_ip)
+        c.lam = self.lam.ctypes.data_as(_dp)
+        c.L = L
+        c.nu1, c.nu2, c.max_cycles, c.rtol, c.coarse_max = nu1, nu2, max_cycles, rtol, coarse_max
+        c.precision = PRECISION[precision] if isinstance(precision, str) else precision
+        c.stream = stream
+        self.ndim = ndim
+        h = _vp()
+        rc = self.lib.mg_create(C.byref(c), C.byref(h))
+        if rc != AMR_OK:
+            raise AmrError(rc, "mg_create")
+        self.h = h
+        n = C.c_longlong()
+        _check(self.lib.mg_num_unknowns(self.h, C.byref(n)), self.h, "mg_last_error")
+        self.n = n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, b, x):
+        """b, x: packed float64 arrays (numpy host or torch CUDA); x is updated in place.
+        Returns (cycles per instance, relative residual per instance)."""
+        if not hasattr(b, "data_ptr"):
+            b = np.ascontiguousarray(b, dtype=np.float64)
+        pb, db = _ptr(b)
+        px, dx = _ptr(x)
+        if db != dx:
+            raise ValueError("b and x must both be host or both be device arrays")
+        cyc = np.zeros(len(self.n_cells), dtype=np.int32)
+        rr = np.zeros(len(self.n_cells))
+        rc = self.lib.mg_solve(self.h, pb, px, db, cyc.ctypes.data_as(_ip), rr.ctypes.data_as(_dp))
+        if rc != AMR_OK:
+            e = AmrError(rc, self.lib.mg_last_error(self.h).decode())
+            e.cycles, e.relres = cyc, rr
+            raise e
+        return cyc, rr
+
+
+class RdSolver:
+    """Owns one rd_handle: Gray-Scott IMEX steps for a batch of periodic instances."""
+
+    def __init__(self, ndim, n_cells, L, Du, Dv, F, k, dt, nu1=2, nu2=2, max_cycles=50, rtol=1e-10,
+                 coarse_max=8, precision="fp32", stream=None):
+        self.lib = load()
+        self.n_cells = np.ascontiguousarray(n_cells, dtype=np.int32)
+        c = RdConfig()
+        c.ndim, c.n_inst = ndim, len(self.n_cells)
+        c.n_cells = self.n_cells.ctypes.data_as(_ip)
+        c.L, c.Du, c.Dv, c.F, c.k, c.dt = L, Du, Dv, F, k, dt
+        c.nu1, c.nu2, c.max_cycles, c.rtol, c.coarse_max = nu1, nu2, max_cycles, rtol, coarse_max
+        c.precision = PRECISION[precision] if isinstance(precision, str) else precision
+        c.stream = stream
+        self.ndim = ndim
+        h = _vp()
+        rc = self.lib.rd_create(C.byref(c), C.byref(h))
+        if rc != AMR_OK:
+            raise AmrError(rc, "rd_create")
+        self.h = h
+        self.ncells = int(sum(int(n) ** ndim for n in self.n_cells))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, u, v):
+        if not hasattr(u, "data_ptr"):
+            u = np.ascontiguousarray(u, dtype=np.float64)
+            v = np.ascontiguousarray(v, dtype=np.float64)
+        pu, du = _ptr(u)
+        pv, dv = _ptr(v)
+        _check(self.lib.rd_set_state(self.h, pu, pv, du), self.h, "rd_last_error")
+
+    def read_state(self, u=None, v=None):
+        if u is None:
+            u, v = np.zeros(self.ncells), np.zeros(self.ncells)
+        pu, du = _ptr(u)
+        pv, dv = _ptr(v)
+        _check(self.lib.rd_read_state(self.h, pu, pv, du), self.h, "rd_last_error")
+        return u, v
+
+    def step(self, nsteps=1):
+        """Returns V-cycles per step, shape [nsteps, 2, n_inst] (species-major)."""
+        cyc = np.zeros((nsteps, 2, len(self.n_cells)), dtype=np.int32)
+        _check(self.lib.rd_step(self.h, nsteps, cyc.ctypes.data_as(_ip)), self.h, "rd_last_error")
+        return cyc

@@ -135,7 +135,8 @@ struct Tree {
 struct Tables {
   std::vector<int> nb, kind, nbr, ffx;
   std::vector<SlabDesc> slabs;
-  std::vector<RefluxRec> rec;
+  std::vector<RefluxRec> rec;  // sorted by face dimension
+  int rec_off[4] = {0, 0, 0, 0};
   int nslots = 0;
 };
 
@@ -221,6 +222,16 @@ bool build_tables(const Tree& T, Tables& tb, std::string* err) {
       tb.kind[o] = 2;
       tb.nbr[o] = D.src[0];
     }
+  }
+  // A coarse cell at a leaf corner may border level jumps in several directions:
+  // corrections are applied one direction per launch so that no two threads of a
+  // launch update the same cell, in the fixed order x, y, z.
+  std::stable_sort(tb.rec.begin(), tb.rec.end(),
+                   [](const RefluxRec& a, const RefluxRec& b) { return (a.face >> 1) < (b.face >> 1); });
+  for (int d = 0; d <= 3; ++d) {
+    tb.rec_off[d] = 0;
+    for (const RefluxRec& r : tb.rec)
+      if ((r.face >> 1) < d) ++tb.rec_off[d];
   }
   return true;
 }
@@ -363,11 +374,15 @@ struct amr_handle {
       int rc = dispatch_stage<real, ND>(a);
       if (rc) return rc;
       if (jumps) {
-        mark_begin();
-        CK((EulerOps<real, ND>::reflux(B, out, fflux.as<real>(), rec.as<RefluxRec>(), (int)tb.rec.size(),
-                                       level.as<int>(), G, ctl.as<DevCtl>(), beta, stream)));
-        ++launches;
-        mark(2);
+        for (int d = 0; d < ND; ++d) {
+          int r0 = tb.rec_off[d], nr = tb.rec_off[d + 1] - r0;
+          if (nr == 0) continue;
+          mark_begin();
+          CK((EulerOps<real, ND>::reflux(B, out, fflux.as<real>(), rec.as<RefluxRec>() + r0, nr, level.as<int>(),
+                                         G, ctl.as<DevCtl>(), beta, stream)));
+          ++launches;
+          mark(2);
+        }
       }
     }
     if (jumps) {

@@ -1,0 +1,889 @@
+// Batched geometric multigrid for (lambda - lap_h) x = b on periodic grids, and
+// the Gray-Scott IMEX step built on it.
+//
+// Paper: Sec. 2.5.1, Eq. (diff-helmholtz): the implicit diffusion stage is a
+// Helmholtz problem solved by geometric multigrid (Sec. 1.4, linear cost);
+// Eq. (imex): IMEX trapezoidal scheme; Eq. (gray-scott): reaction terms; Sec.
+// 2.5.2: iterate until the maximum residual is below a fraction of the
+// right-hand side.
+//
+// Layout: every multigrid instance owns a chain of levels (side n, n/2, ...,
+// coarsest when the side is odd or <= coarse_max); level arrays of all
+// instances are packed in one buffer per quantity.  Work is described by
+// per-depth chunk lists (instance, first index, count), so one launch per
+// sweep covers every instance deep enough for that depth.  The float64
+// iterate X and right-hand side B live on level 0; V-cycles run on the
+// correction in `real` (float or double): R = B - A X (float64) -> V-cycle on
+// A e = R -> X += e (defect correction).  The coarsest level is solved with a
+// precomputed dense inverse, applied in float64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/amrvac_gb300.h"
+
+namespace mggpu {
+
+constexpr int kMaxLev = 16;
+constexpr int kChunk = 256;
+
+struct Chunk {
+  int inst, lev;
+  long long start;
+  int count;
+};
+
+struct InstDev {
+  int nlev;
+  int n[kMaxLev];
+  long long off[kMaxLev];  // offsets into the level buffers
+  double ih2[kMaxLev];
+  float ih2f[kMaxLev];
+  double lam;
+  float lamf;
+  long long off0;          // offset into X / B
+  long long inv_off;       // offset into the coarsest inverse matrices
+};
+
+struct MgState {
+  const InstDev* inst;
+  double* X;
+  const double* B;
+  unsigned long long* rnorm;  // max |R| bits per instance
+  double* bnorm;              // max |B| per instance
+  double* lastres;            // last max |R| per instance
+  int* active;                // instance still iterating
+  int* cycles;
+  int* failed;
+  int* any;                   // any instance active (for the host)
+  const double* inv;          // dense inverses of the coarsest operators
+  int ndim;
+  double rtol;
+  int max_cycles;
+};
+
+template <typename real>
+struct Lvl {
+  real* x;
+  real* b;
+};
+
+__device__ __forceinline__ void cell_of(long long t, int n, int nd, int* c) {
+  c[0] = (int)(t % n);
+  t /= n;
+  c[1] = nd > 1 ? (int)(t % n) : 0;
+  c[2] = nd > 2 ? (int)(t / n) : 0;
+}
+
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+__device__ __forceinline__ long long lin(const int* c, int n) {
+  return (long long)c[0] + (long long)n * ((long long)c[1] + (long long)n * c[2]);
+}
+
+// sum of the 2 ndim neighbours, ordered x-, x+, y-, y+, z-, z+
+template <typename T>
+__device__ __forceinline__ T nbsum(const T* x, const int* c, int n, int nd) {
+  int q[3] = {c[0], c[1], c[2]};
+  q[0] = wrapi(c[0] - 1, n);
+  T s = x[lin(q, n)];
+  q[0] = wrapi(c[0] + 1, n);
+  s = s + x[lin(q, n)];
+  q[0] = c[0];
+  if (nd > 1) {
+    q[1] = wrapi(c[1] - 1, n);
+    s = s + x[lin(q, n)];
+    q[1] = wrapi(c[1] + 1, n);
+    s = s + x[lin(q, n)];
+    q[1] = c[1];
+  }
+  if (nd > 2) {
+    q[2] = wrapi(c[2] - 1, n);
+    s = s + x[lin(q, n)];
+    q[2] = wrapi(c[2] + 1, n);
+    s = s + x[lin(q, n)];
+  }
+  return s;
+}
+
+template <typename real>
+__device__ __forceinline__ real ih2_of(const InstDev& I, int l);
+template <>
+__device__ __forceinline__ double ih2_of<double>(const InstDev& I, int l) { return I.ih2[l]; }
+template <>
+__device__ __forceinline__ float ih2_of<float>(const InstDev& I, int l) { return I.ih2f[l]; }
+template <typename real>
+__device__ __forceinline__ real lam_of(const InstDev& I);
+template <>
+__device__ __forceinline__ double lam_of<double>(const InstDev& I) { return I.lam; }
+template <>
+__device__ __forceinline__ float lam_of<float>(const InstDev& I) { return I.lamf; }
+
+// ---------------------------------------------------------------- kernels --
+// max |B| per instance (level-0 chunks)
+__global__ void bnorm_kernel(MgState S, const Chunk* ch) {
+  Chunk C = ch[blockIdx.x];
+  double m = 0.0;
+  if (threadIdx.x < C.count) {
+    const InstDev& I = S.inst[C.inst];
+    m = fabs(S.B[I.off0 + C.start + threadIdx.x]);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(&S.rnorm[C.inst], (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void bnorm_finish_kernel(MgState S, int ninst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  S.bnorm[i] = __longlong_as_double((long long)S.rnorm[i]);
+  S.rnorm[i] = 0ull;
+  S.active[i] = 1;
+  S.cycles[i] = 0;
+  S.failed[i] = 0;
+}
+
+// float64 residual R = B - (lambda X - lap X) on level 0 -> rhs of the correction,
+// correction zeroed, per-instance max |R|
+template <typename real>
+__global__ void residual64_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
+  Chunk C = ch[blockIdx.x];
+  double m = 0.0;
+  const InstDev& I = S.inst[C.inst];
+  if (S.active[C.inst] && threadIdx.x < C.count) {
+    long long t = C.start + threadIdx.x;
+    int n = I.n[0];
+    int c[3];
+    cell_of(t, n, S.ndim, c);
+    const double* X = S.X + I.off0;
+    double x = X[t];
+    double lap = (nbsum(X, c, n, S.ndim) - (2.0 * S.ndim) * x) * I.ih2[0];
+    double r = S.B[I.off0 + t] - (I.lam * x - lap);
+    L.b[I.off[0] + t] = (real)r;
+    L.x[I.off[0] + t] = real(0);
+    m = fabs(r);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(&S.rnorm[C.inst], (unsigned long long)__double_as_longlong(m));
+}
+
+// convergence test per instance (the paper's max-residual rule)
+__global__ void check_kernel(MgState S, int ninst) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < ninst; i += blockDim.x) {
+    if (!S.active[i]) continue;
+    double rn = __longlong_as_double((long long)S.rnorm[i]);
+    S.rnorm[i] = 0ull;
+    S.lastres[i] = rn;
+    if (rn <= S.rtol * S.bnorm[i]) {
+      S.active[i] = 0;
+    } else if (S.cycles[i] >= S.max_cycles) {
+      S.active[i] = 0;
+      S.failed[i] = 1;
+    } else {
+      S.cycles[i] += 1;
+      atomicOr(&any, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *S.any = any;
+}
+
+// red-black Gauss-Seidel sweep of one colour: x = (b + nbsum * ih2) / (lambda + 2 ndim ih2)
+template <typename real>
+__global__ void smooth_kernel(MgState S, Lvl<real> L, const Chunk* ch, int colour) {
+  Chunk C = ch[blockIdx.x];
+  if (!S.active[C.inst] || threadIdx.x >= C.count) return;
+  const InstDev& I = S.inst[C.inst];
+  const int l = C.lev, n = I.n[l], nd = S.ndim;
+  long long t = C.start + threadIdx.x;  // index among the cells of this colour
+  int half = n / 2;
+  int c[3];
+  long long row = t / half;
+  int ii = (int)(t % half);
+  c[1] = nd > 1 ? (int)(row % n) : 0;
+  c[2] = nd > 2 ? (int)(row / n) : 0;
+  c[0] = 2 * ii + ((c[1] + c[2] + colour) & 1);
+  real* x = L.x + I.off[l];
+  const real* b = L.b + I.off[l];
+  real ih2 = ih2_of<real>(I, l);
+  real diag = lam_of<real>(I) + real(2 * nd) * ih2;
+  long long q = lin(c, n);
+  x[q] = (b[q] + nbsum(x, c, n, nd) * ih2) / diag;
+}
+
+// residual of level l restricted to level l+1 (mean of the 2^ndim children), x_{l+1} = 0
+template <typename real>
+__global__ void resrestrict_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
+  Chunk C = ch[blockIdx.x];
+  if (!S.active[C.inst] || threadIdx.x >= C.count) return;
+  const InstDev& I = S.inst[C.inst];
+  const int l = C.lev, nd = S.ndim;  // chunk enumerates cells of level l+1
+  const int nc = I.n[l + 1], nf = I.n[l];
+  long long t = C.start + threadIdx.x;
+  int cc[3];
+  cell_of(t, nc, nd, cc);
+  const real* x = L.x + I.off[l];
+  const real* b = L.b + I.off[l];
+  real ih2 = ih2_of<real>(I, l), lam = lam_of<real>(I);
+  real sum = real(0);
+  for (int o = 0; o < (1 << nd); ++o) {
+    int f[3] = {2 * cc[0] + (o & 1), nd > 1 ? 2 * cc[1] + ((o >> 1) & 1) : 0, nd > 2 ? 2 * cc[2] + ((o >> 2) & 1) : 0};
+    long long q = lin(f, nf);
+    real xv = x[q];
+    real lap = (nbsum(x, f, nf, nd) - real(2 * nd) * xv) * ih2;
+    sum = sum + (b[q] - (lam * xv - lap));
+  }
+  L.b[I.off[l + 1] + t] = sum * (real(1) / real(1 << nd));
+  L.x[I.off[l + 1] + t] = real(0);
+}
+
+// cell-centred (bi/tri)linear prolongation of level l+1 added to level l
+template <typename real>
+__global__ void prolong_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
+  Chunk C = ch[blockIdx.x];
+  if (!S.active[C.inst] || threadIdx.x >= C.count) return;
+  const InstDev& I = S.inst[C.inst];
+  const int l = C.lev, nd = S.ndim;
+  const int nf = I.n[l], nc = I.n[l + 1];
+  long long t = C.start + threadIdx.x;
+  int f[3];
+  cell_of(t, nf, nd, f);
+  int P[3] = {f[0] >> 1, f[1] >> 1, f[2] >> 1};
+  int sg[3] = {(f[0] & 1) ? 1 : -1, (f[1] & 1) ? 1 : -1, (f[2] & 1) ? 1 : -1};
+  const real* ec = L.x + I.off[l + 1];
+  real acc = real(0);
+  int cz = nd > 2 ? 2 : 1, cy = nd > 1 ? 2 : 1;
+  for (int z = 0; z < cz; ++z)
+    for (int y = 0; y < cy; ++y)
+      for (int xx = 0; xx < 2; ++xx) {
+        int q[3] = {wrapi(P[0] + xx * sg[0], nc), nd > 1 ? wrapi(P[1] + y * sg[1], nc) : 0,
+                    nd > 2 ? wrapi(P[2] + z * sg[2], nc) : 0};
+        real w = xx ? real(0.25) : real(0.75);
+        if (nd > 1) w = w * (y ? real(0.25) : real(0.75));
+        if (nd > 2) w = w * (z ? real(0.25) : real(0.75));
+        acc = acc + w * ec[lin(q, nc)];
+      }
+  real* x = L.x + I.off[l] + t;
+  *x = *x + acc;
+}
+
+// coarsest level: x = inverse(A) b, float64, a warp per row
+template <typename real>
+__global__ void coarse_kernel(MgState S, Lvl<real> L, const int* insts, const int* rows0, int nitems) {
+  int item = blockIdx.x;
+  if (item >= nitems) return;
+  int i = insts[item];
+  if (!S.active[i]) return;
+  const InstDev& I = S.inst[i];
+  int l = I.nlev - 1, n = I.n[l];
+  int m = n;
+  for (int d = 1; d < S.ndim; ++d) m *= n;
+  const real* b = L.b + I.off[l];
+  real* x = L.x + I.off[l];
+  const double* A = S.inv + I.inv_off;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = rows0[item] + warp; r < min(m, rows0[item] + 64); r += blockDim.x / 32) {
+    double acc = 0.0;
+    for (int c = lane; c < m; c += 32) acc += A[(size_t)r * m + c] * (double)b[c];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) x[r] = (real)acc;
+  }
+}
+
+template <typename real>
+__global__ void correct64_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
+  Chunk C = ch[blockIdx.x];
+  if (!S.active[C.inst] || threadIdx.x >= C.count) return;
+  const InstDev& I = S.inst[C.inst];
+  long long t = C.start + threadIdx.x;
+  S.X[I.off0 + t] = S.X[I.off0 + t] + (double)L.x[I.off[0] + t];
+}
+
+// ------------------------------------------------------- Gray-Scott IMEX --
+// Eq. (gray-scott): F0_u = -u v^2 + F(1-u), F0_v = u v^2 - (F+k) v.
+// Eq. (imex) stage 1: B = lambda g, g = w + dt F0(w) + dt/2 D lap w, X = w (guess);
+// Fn = F0(w) + D lap w kept for stage 2.
+struct RdArgs {
+  const InstDev* inst;  // multigrid instances: species s of instance i is s*ninst + i
+  int ninst, ndim;
+  double F, k, dt, D[2], lam[2];
+  double* u;
+  double* v;            // state, packed like level 0 of one species
+  double* X;            // multigrid iterate (2 species)
+  double* B;            // multigrid right-hand side
+  double* Fn;           // F(w_n) per species
+};
+
+__device__ __forceinline__ void reaction(double F, double k, double u, double v, double* fu, double* fv) {
+  double uvv = (u * v) * v;
+  *fu = -uvv + F * (1.0 - u);
+  *fv = uvv - (F + k) * v;
+}
+
+__global__ void rd_rhs_kernel(RdArgs A, const Chunk* ch) {
+  Chunk C = ch[blockIdx.x];  // chunks over level 0 of species-0 instances
+  if (threadIdx.x >= C.count) return;
+  const InstDev& I0 = A.inst[C.inst];
+  const InstDev& I1 = A.inst[C.inst + A.ninst];
+  long long t = C.start + threadIdx.x;
+  int n = I0.n[0], c[3];
+  cell_of(t, n, A.ndim, c);
+  long long o = I0.off0;  // species-0 offset equals the state offset
+  const double* u = A.u + o;
+  const double* v = A.v + o;
+  double fu, fv;
+  reaction(A.F, A.k, u[t], v[t], &fu, &fv);
+  double lu = (nbsum(u, c, n, A.ndim) - (2.0 * A.ndim) * u[t]) * I0.ih2[0];
+  double lv = (nbsum(v, c, n, A.ndim) - (2.0 * A.ndim) * v[t]) * I0.ih2[0];
+  double gu = (u[t] + A.dt * fu) + ((0.5 * A.dt) * A.D[0]) * lu;
+  double gv = (v[t] + A.dt * fv) + ((0.5 * A.dt) * A.D[1]) * lv;
+  A.B[I0.off0 + t] = A.lam[0] * gu;
+  A.B[I1.off0 + t] = A.lam[1] * gv;
+  A.X[I0.off0 + t] = u[t];
+  A.X[I1.off0 + t] = v[t];
+  A.Fn[I0.off0 + t] = fu + A.D[0] * lu;
+  A.Fn[I1.off0 + t] = fv + A.D[1] * lv;
+}
+
+// Eq. (imex) stage 2: w_{n+1} = w_n + dt/2 [F(w_n) + F(w*)]
+__global__ void rd_finish_kernel(RdArgs A, const Chunk* ch) {
+  Chunk C = ch[blockIdx.x];
+  if (threadIdx.x >= C.count) return;
+  const InstDev& I0 = A.inst[C.inst];
+  const InstDev& I1 = A.inst[C.inst + A.ninst];
+  long long t = C.start + threadIdx.x;
+  int n = I0.n[0], c[3];
+  cell_of(t, n, A.ndim, c);
+  const double* us = A.X + I0.off0;
+  const double* vs = A.X + I1.off0;
+  double fu, fv;
+  reaction(A.F, A.k, us[t], vs[t], &fu, &fv);
+  double lu = (nbsum(us, c, n, A.ndim) - (2.0 * A.ndim) * us[t]) * I0.ih2[0];
+  double lv = (nbsum(vs, c, n, A.ndim) - (2.0 * A.ndim) * vs[t]) * I0.ih2[0];
+  double Fu = fu + A.D[0] * lu, Fv = fv + A.D[1] * lv;
+  long long o = I0.off0;
+  A.u[o + t] = A.u[o + t] + (0.5 * A.dt) * (A.Fn[I0.off0 + t] + Fu);
+  A.v[o + t] = A.v[o + t] + (0.5 * A.dt) * (A.Fn[I1.off0 + t] + Fv);
+}
+
+// ------------------------------------------------------------------ host --
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t alloc(size_t bytes) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+    if (e == cudaSuccess) n = bytes;
+    return e;
+  }
+  template <typename T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// Dense inverse of the periodic operator (lambda - lap_h) by Gauss-Jordan with
+// partial pivoting (host, float64).
+bool dense_inverse(int nd, int n, double L, double lambda, std::vector<double>& inv) {
+  int m = 1;
+  for (int d = 0; d < nd; ++d) m *= n;
+  double h = L / n, ih2 = 1.0 / (h * h);
+  std::vector<double> A((size_t)m * m, 0.0);
+  inv.assign((size_t)m * m, 0.0);
+  for (int r = 0; r < m; ++r) {
+    int c[3] = {r % n, nd > 1 ? (r / n) % n : 0, nd > 2 ? r / (n * n) : 0};
+    A[(size_t)r * m + r] += lambda + 2.0 * nd * ih2;
+    for (int d = 0; d < nd; ++d)
+      for (int s = -1; s <= 1; s += 2) {
+        int q[3] = {c[0], c[1], c[2]};
+        q[d] = (q[d] + s + n) % n;
+        int cidx = q[0] + n * (q[1] + n * q[2]);
+        A[(size_t)r * m + cidx] -= ih2;
+      }
+    inv[(size_t)r * m + r] = 1.0;
+  }
+  for (int col = 0; col < m; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < m; ++r)
+      if (std::fabs(A[(size_t)r * m + col]) > std::fabs(A[(size_t)piv * m + col])) piv = r;
+    if (A[(size_t)piv * m + col] == 0.0) return false;
+    if (piv != col)
+      for (int k = 0; k < m; ++k) {
+        std::swap(A[(size_t)piv * m + k], A[(size_t)col * m + k]);
+        std::swap(inv[(size_t)piv * m + k], inv[(size_t)col * m + k]);
+      }
+    double d = 1.0 / A[(size_t)col * m + col];
+    for (int k = 0; k < m; ++k) {
+      A[(size_t)col * m + k] *= d;
+      inv[(size_t)col * m + k] *= d;
+    }
+    for (int r = 0; r < m; ++r) {
+      if (r == col) continue;
+      double f = A[(size_t)r * m + col];
+      if (f == 0.0) continue;
+      for (int k = 0; k < m; ++k) {
+        A[(size_t)r * m + k] -= f * A[(size_t)col * m + k];
+        inv[(size_t)r * m + k] -= f * inv[(size_t)col * m + k];
+      }
+    }
+  }
+  return true;
+}
+
+void add_chunks(std::vector<Chunk>& v, int inst, int lev, long long count) {
+  for (long long s = 0; s < count; s += kChunk) v.push_back(Chunk{inst, lev, s, (int)std::min<long long>(kChunk, count - s)});
+}
+
+struct Mg {
+  int nd = 2, ninst = 0, nu1 = 2, nu2 = 2, max_cycles = 50, precision = AMR_FP32;
+  double rtol = 1e-10, Lside = 1.0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  std::vector<InstDev> insts;
+  int maxdepth = 0;
+  long long n0 = 0, nlevtot = 0;
+  // chunk lists: level 0 cells; per depth: colour cells, coarse cells, fine cells
+  std::vector<Chunk> ch0;
+  std::vector<std::vector<Chunk>> ch_half, ch_coarse, ch_fine;
+  std::vector<int> coarse_inst, coarse_row0;
+  DevBuf d_inst, d_X, d_B, d_xl, d_bl, d_rnorm, d_bnorm, d_lastres, d_active, d_cycles, d_failed, d_any, d_inv;
+  DevBuf d_ch0, d_chall, d_cinst, d_crow0;
+  std::vector<size_t> off_half, off_coarse, off_fine;
+  int* h_any = nullptr;
+  cudaGraphExec_t vgraph = nullptr;
+  long long launches = 0;
+  int vcycle_kernels = 0;
+
+  ~Mg() {
+    if (vgraph) cudaGraphExecDestroy(vgraph);
+    if (h_any) cudaFreeHost(h_any);
+    if (own_stream) cudaStreamDestroy(stream);
+  }
+  int fail(int code, const std::string& m) {
+    err = m;
+    return code;
+  }
+  int cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return AMR_OK;
+    err = std::string("CUDA error ") + cudaGetErrorString(e) + " in " + what;
+    return e == cudaErrorMemoryAllocation ? AMR_ERR_OOM : AMR_ERR_CUDA;
+  }
+
+  MgState state() const {
+    MgState S{};
+    S.inst = d_inst.as<InstDev>();
+    S.X = d_X.as<double>();
+    S.B = d_B.as<double>();
+    S.rnorm = d_rnorm.as<unsigned long long>();
+    S.bnorm = d_bnorm.as<double>();
+    S.lastres = d_lastres.as<double>();
+    S.active = d_active.as<int>();
+    S.cycles = d_cycles.as<int>();
+    S.failed = d_failed.as<int>();
+    S.any = d_any.as<int>();
+    S.inv = d_inv.as<double>();
+    S.ndim = nd;
+    S.rtol = rtol;
+    S.max_cycles = max_cycles;
+    return S;
+  }
+
+  int setup(int ndim, int n_inst, const int* n_cells, const double* lambda, double L, int nu1_, int nu2_, int maxc,
+            double rtol_, int coarse_max, int prec, void* strm) {
+    if (ndim < 2 || ndim > 3 || n_inst < 1 || !n_cells || !lambda || !(L > 0) || nu1_ < 0 || nu2_ < 0 ||
+        maxc < 0 || !(rtol_ > 0) || coarse_max < 1 || (prec != AMR_FP32 && prec != AMR_FP64))
+      return fail(AMR_ERR_INVALID_ARG, "invalid multigrid configuration");
+    nd = ndim;
+    ninst = n_inst;
+    nu1 = nu1_;
+    nu2 = nu2_;
+    max_cycles = maxc;
+    rtol = rtol_;
+    Lside = L;
+    precision = prec;
+    stream = (cudaStream_t)strm;
+    if (!stream) {
+      if (int rc = cuda(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking), "stream")) return rc;
+      own_stream = true;
+    }
+    insts.resize(n_inst);
+    long long off = 0, off0 = 0, invoff = 0;
+    std::vector<std::vector<double>> invs(n_inst);
+    for (int i = 0; i < n_inst; ++i) {
+      int n = n_cells[i];
+      if (n < 1 || !(lambda[i] > 0)) return fail(AMR_ERR_INVALID_ARG, "instance size or lambda");
+      InstDev& I = insts[i];
+      std::memset(&I, 0, sizeof(I));
+      I.lam = lambda[i];
+      I.lamf = (float)lambda[i];
+      I.off0 = off0;
+      long long cells0 = 1;
+      for (int d = 0; d < nd; ++d) cells0 *= n;
+      off0 += cells0;
+      int l = 0, m = n;
+      while (true) {
+        if (l >= kMaxLev) return fail(AMR_ERR_INVALID_ARG, "too many levels");
+        I.n[l] = m;
+        I.off[l] = off;
+        long long cells = 1;
+        for (int d = 0; d < nd; ++d) cells *= m;
+        off += cells;
+        double h = L / m;
+        I.ih2[l] = 1.0 / (h * h);
+        I.ih2f[l] = (float)I.ih2[l];
+        ++l;
+        if ((m & 1) || m <= coarse_max) break;
+        m /= 2;
+      }
+      I.nlev = l;
+      maxdepth = std::max(maxdepth, l);
+      int mc = I.n[l - 1];
+      long long msz = 1;
+      for (int d = 0; d < nd; ++d) msz *= mc;
+      if (msz > 4096) return fail(AMR_ERR_INVALID_ARG, "coarsest grid too large (increase coarse_max or use sizes with more factors of 2)");
+      if (!dense_inverse(nd, mc, L, lambda[i], invs[i])) return fail(AMR_ERR_INVALID_ARG, "singular coarse operator");
+      I.inv_off = invoff;
+      invoff += msz * msz;
+    }
+    n0 = off0;
+    nlevtot = off;
+    // chunk lists
+    ch0.clear();
+    for (int i = 0; i < n_inst; ++i) {
+      long long c = 1;
+      for (int d = 0; d < nd; ++d) c *= insts[i].n[0];
+      add_chunks(ch0, i, 0, c);
+    }
+    ch_half.assign(maxdepth, {});
+    ch_coarse.assign(maxdepth, {});
+    ch_fine.assign(maxdepth, {});
+    coarse_inst.clear();
+    coarse_row0.clear();
+    for (int i = 0; i < n_inst; ++i) {
+      const InstDev& I = insts[i];
+      for (int l = 0; l + 1 < I.nlev; ++l) {
+        long long cf = 1, cc = 1;
+        for (int d = 0; d < nd; ++d) {
+          cf *= I.n[l];
+          cc *= I.n[l + 1];
+        }
+        add_chunks(ch_half[l], i, l, cf / 2);
+        add_chunks(ch_coarse[l], i, l, cc);
+        add_chunks(ch_fine[l], i, l, cf);
+      }
+      long long m = 1;
+      for (int d = 0; d < nd; ++d) m *= I.n[I.nlev - 1];
+      for (long long r = 0; r < m; r += 64) {
+        coarse_inst.push_back(i);
+        coarse_row0.push_back((int)r);
+      }
+    }
+    // device buffers
+    size_t wb = precision == AMR_FP64 ? 8 : 4;
+    int rc;
+    if ((rc = cuda(d_inst.alloc(insts.size() * sizeof(InstDev)), "alloc")) ||
+        (rc = cuda(d_X.alloc(n0 * 8), "alloc X")) || (rc = cuda(d_B.alloc(n0 * 8), "alloc B")) ||
+        (rc = cuda(d_xl.alloc(nlevtot * wb), "alloc levels")) || (rc = cuda(d_bl.alloc(nlevtot * wb), "alloc levels")) ||
+        (rc = cuda(d_rnorm.alloc(n_inst * 8), "alloc")) || (rc = cuda(d_bnorm.alloc(n_inst * 8), "alloc")) ||
+        (rc = cuda(d_lastres.alloc(n_inst * 8), "alloc")) || (rc = cuda(d_active.alloc(n_inst * 4), "alloc")) ||
+        (rc = cuda(d_cycles.alloc(n_inst * 4), "alloc")) || (rc = cuda(d_failed.alloc(n_inst * 4), "alloc")) ||
+        (rc = cuda(d_any.alloc(4), "alloc")) || (rc = cuda(d_inv.alloc(invoff * 8), "alloc inverse")))
+      return rc;
+    if ((rc = cuda(cudaMallocHost(&h_any, 4), "host alloc"))) return rc;
+    cudaMemcpy(d_inst.p, insts.data(), insts.size() * sizeof(InstDev), cudaMemcpyHostToDevice);
+    for (int i = 0; i < n_inst; ++i)
+      cudaMemcpy(d_inv.as<double>() + insts[i].inv_off, invs[i].data(), invs[i].size() * 8, cudaMemcpyHostToDevice);
+    cudaMemset(d_rnorm.p, 0, n_inst * 8);
+    std::vector<Chunk> all;
+    off_half.assign(maxdepth, 0);
+    off_coarse.assign(maxdepth, 0);
+    off_fine.assign(maxdepth, 0);
+    for (int l = 0; l < maxdepth; ++l) {
+      off_half[l] = all.size();
+      all.insert(all.end(), ch_half[l].begin(), ch_half[l].end());
+      off_coarse[l] = all.size();
+      all.insert(all.end(), ch_coarse[l].begin(), ch_coarse[l].end());
+      off_fine[l] = all.size();
+      all.insert(all.end(), ch_fine[l].begin(), ch_fine[l].end());
+    }
+    if ((rc = cuda(d_ch0.alloc(ch0.size() * sizeof(Chunk)), "alloc")) ||
+        (rc = cuda(d_chall.alloc(all.size() * sizeof(Chunk)), "alloc")) ||
+        (rc = cuda(d_cinst.alloc(coarse_inst.size() * 4), "alloc")) ||
+        (rc = cuda(d_crow0.alloc(coarse_row0.size() * 4), "alloc")))
+      return rc;
+    cudaMemcpy(d_ch0.p, ch0.data(), ch0.size() * sizeof(Chunk), cudaMemcpyHostToDevice);
+    if (!all.empty()) cudaMemcpy(d_chall.p, all.data(), all.size() * sizeof(Chunk), cudaMemcpyHostToDevice);
+    cudaMemcpy(d_cinst.p, coarse_inst.data(), coarse_inst.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_crow0.p, coarse_row0.data(), coarse_row0.size() * 4, cudaMemcpyHostToDevice);
+    return cuda(cudaDeviceSynchronize(), "setup");
+  }
+
+  template <typename real>
+  Lvl<real> lvl() const {
+    return Lvl<real>{d_xl.as<real>(), d_bl.as<real>()};
+  }
+
+  template <typename real>
+  int enqueue_vcycle() {
+    MgState S = state();
+    Lvl<real> Lv = lvl<real>();
+    const Chunk* all = d_chall.as<Chunk>();
+    auto launch_half = [&](int l, int colour) {
+      if (ch_half[l].empty()) return;
+      smooth_kernel<real><<<(unsigned)ch_half[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_half[l], colour);
+      ++launches;
+    };
+    for (int l = 0; l + 1 < maxdepth; ++l) {
+      for (int s = 0; s < nu1; ++s) {
+        launch_half(l, 0);
+        launch_half(l, 1);
+      }
+      if (!ch_coarse[l].empty()) {
+        resrestrict_kernel<real><<<(unsigned)ch_coarse[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
+        ++launches;
+      }
+    }
+    coarse_kernel<real><<<(unsigned)coarse_inst.size(), 256, 0, stream>>>(S, Lv, d_cinst.as<int>(), d_crow0.as<int>(),
+                                                                          (int)coarse_inst.size());
+    ++launches;
+    for (int l = maxdepth - 2; l >= 0; --l) {
+      if (!ch_fine[l].empty()) {
+        prolong_kernel<real><<<(unsigned)ch_fine[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_fine[l]);
+        ++launches;
+      }
+      for (int s = 0; s < nu2; ++s) {
+        launch_half(l, 0);
+        launch_half(l, 1);
+      }
+    }
+    correct64_kernel<real><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+    ++launches;
+    return cuda(cudaGetLastError(), "vcycle launch");
+  }
+
+  template <typename real>
+  int build_graph() {
+    if (vgraph) return AMR_OK;
+    cudaGraph_t g;
+    if (int rc = cuda(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "capture")) return rc;
+    long long before = launches;
+    int rc = enqueue_vcycle<real>();
+    cudaError_t ec = cudaStreamEndCapture(stream, &g);
+    if (rc) return rc;
+    if ((rc = cuda(ec, "end capture"))) return rc;
+    vcycle_kernels = (int)(launches - before);
+    launches = before;
+    rc = cuda(cudaGraphInstantiate(&vgraph, g, 0), "instantiate");
+    cudaGraphDestroy(g);
+    return rc;
+  }
+
+  // X (device, float64) holds the guess; B (device) the right-hand side; both at d_X / d_B
+  template <typename real>
+  int solve_device() {
+    MgState S = state();
+    Lvl<real> Lv = lvl<real>();
+    int rc = build_graph<real>();
+    if (rc) return rc;
+    bnorm_kernel<<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, d_ch0.as<Chunk>());
+    bnorm_finish_kernel<<<(ninst + 255) / 256, 256, 0, stream>>>(S, ninst);
+    launches += 2;
+    while (true) {
+      residual64_kernel<real><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+      check_kernel<<<1, 256, 0, stream>>>(S, ninst);
+      launches += 2;
+      if ((rc = cuda(cudaMemcpyAsync(h_any, d_any.p, 4, cudaMemcpyDeviceToHost, stream), "copy"))) return rc;
+      if ((rc = cuda(cudaStreamSynchronize(stream), "sync"))) return rc;
+      if (!*h_any) break;
+      if ((rc = cuda(cudaGraphLaunch(vgraph, stream), "graph launch"))) return rc;
+      launches += vcycle_kernels;
+    }
+    return AMR_OK;
+  }
+
+  int solve_device_any() { return precision == AMR_FP64 ? solve_device<double>() : solve_device<float>(); }
+
+  int results(int* cycles, double* relres, bool* all_ok) {
+    std::vector<int> cyc(ninst), fl(ninst);
+    std::vector<double> lr(ninst), bn(ninst);
+    cudaMemcpy(cyc.data(), d_cycles.p, ninst * 4, cudaMemcpyDeviceToHost);
+    cudaMemcpy(fl.data(), d_failed.p, ninst * 4, cudaMemcpyDeviceToHost);
+    cudaMemcpy(lr.data(), d_lastres.p, ninst * 8, cudaMemcpyDeviceToHost);
+    if (int rc = cuda(cudaMemcpy(bn.data(), d_bnorm.p, ninst * 8, cudaMemcpyDeviceToHost), "copy")) return rc;
+    *all_ok = true;
+    for (int i = 0; i < ninst; ++i) {
+      if (cycles) cycles[i] = cyc[i];
+      if (relres) relres[i] = bn[i] > 0 ? lr[i] / bn[i] : lr[i];
+      if (fl[i]) *all_ok = false;
+    }
+    return AMR_OK;
+  }
+};
+
+}  // namespace mggpu
+
+using namespace mggpu;
+
+struct mg_handle {
+  Mg mg;
+};
+
+struct rd_handle {
+  Mg mg;
+  rd_config cfg{};
+  std::vector<int> sizes;
+  DevBuf d_u, d_v, d_Fn;
+  std::string err;
+  long long cells = 0;
+};
+
+extern "C" {
+
+int mg_create(const mg_config* cfg, mg_handle** out) {
+  if (!cfg || !out) return AMR_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::unique_ptr<mg_handle> h(new mg_handle());
+  int rc = h->mg.setup(cfg->ndim, cfg->n_inst, cfg->n_cells, cfg->lambda, cfg->L, cfg->nu1, cfg->nu2, cfg->max_cycles,
+                       cfg->rtol, cfg->coarse_max, cfg->precision, cfg->stream);
+  if (rc) return rc;
+  *out = h.release();
+  return AMR_OK;
+}
+
+int mg_destroy(mg_handle* h) {
+  if (!h) return AMR_ERR_INVALID_ARG;
+  delete h;
+  return AMR_OK;
+}
+
+const char* mg_last_error(const mg_handle* h) { return h ? h->mg.err.c_str() : "null handle"; }
+
+int mg_num_unknowns(const mg_handle* h, long long* n) {
+  if (!h || !n) return AMR_ERR_INVALID_ARG;
+  *n = h->mg.n0;
+  return AMR_OK;
+}
+
+int mg_solve(mg_handle* h, const double* b, double* x, int on_device, int* cycles, double* relres) {
+  if (!h || !b || !x) return AMR_ERR_INVALID_ARG;
+  Mg& M = h->mg;
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (int rc = M.cuda(cudaMemcpyAsync(M.d_B.p, b, M.n0 * 8, k, M.stream), "copy b")) return rc;
+  if (int rc = M.cuda(cudaMemcpyAsync(M.d_X.p, x, M.n0 * 8, k, M.stream), "copy x")) return rc;
+  int rc = M.solve_device_any();
+  if (rc) return rc;
+  cudaMemcpyKind kb = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if ((rc = M.cuda(cudaMemcpyAsync(x, M.d_X.p, M.n0 * 8, kb, M.stream), "copy x back"))) return rc;
+  if ((rc = M.cuda(cudaStreamSynchronize(M.stream), "sync"))) return rc;
+  bool ok;
+  if ((rc = M.results(cycles, relres, &ok))) return rc;
+  if (!ok) return M.fail(MG_ERR_NOT_CONVERGED, "an instance did not reach rtol within max_cycles");
+  return AMR_OK;
+}
+
+int rd_create(const rd_config* cfg, rd_handle** out) {
+  if (!cfg || !out || cfg->n_inst < 1 || !cfg->n_cells) return AMR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!(cfg->dt > 0) || !(cfg->Du > 0) || !(cfg->Dv > 0)) return AMR_ERR_INVALID_ARG;
+  std::unique_ptr<rd_handle> h(new rd_handle());
+  h->cfg = *cfg;
+  h->sizes.assign(cfg->n_cells, cfg->n_cells + cfg->n_inst);
+  h->cfg.n_cells = h->sizes.data();
+  // multigrid batch: species-major (u of every instance, then v)
+  std::vector<int> n2(2 * cfg->n_inst);
+  std::vector<double> lam(2 * cfg->n_inst);
+  for (int s = 0; s < 2; ++s)
+    for (int i = 0; i < cfg->n_inst; ++i) {
+      n2[s * cfg->n_inst + i] = cfg->n_cells[i];
+      lam[s * cfg->n_inst + i] = 2.0 / (cfg->dt * (s == 0 ? cfg->Du : cfg->Dv));
+    }
+  int rc = h->mg.setup(cfg->ndim, 2 * cfg->n_inst, n2.data(), lam.data(), cfg->L, cfg->nu1, cfg->nu2, cfg->max_cycles,
+                       cfg->rtol, cfg->coarse_max, cfg->precision, cfg->stream);
+  if (rc) return rc;
+  h->cells = h->mg.insts[cfg->n_inst].off0;  // species-0 block size = cells of all instances
+  if ((rc = h->mg.cuda(h->d_u.alloc(h->cells * 8), "alloc u")) || (rc = h->mg.cuda(h->d_v.alloc(h->cells * 8), "alloc v")) ||
+      (rc = h->mg.cuda(h->d_Fn.alloc(2 * h->cells * 8), "alloc Fn")))
+    return rc;
+  *out = h.release();
+  return AMR_OK;
+}
+
+int rd_destroy(rd_handle* h) {
+  if (!h) return AMR_ERR_INVALID_ARG;
+  delete h;
+  return AMR_OK;
+}
+
+const char* rd_last_error(const rd_handle* h) { return h ? h->mg.err.c_str() : "null handle"; }
+
+int rd_set_state(rd_handle* h, const double* u, const double* v, int on_device) {
+  if (!h || !u || !v) return AMR_ERR_INVALID_ARG;
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  Mg& M = h->mg;
+  if (int rc = M.cuda(cudaMemcpyAsync(h->d_u.p, u, h->cells * 8, k, M.stream), "copy u")) return rc;
+  if (int rc = M.cuda(cudaMemcpyAsync(h->d_v.p, v, h->cells * 8, k, M.stream), "copy v")) return rc;
+  return M.cuda(cudaStreamSynchronize(M.stream), "sync");
+}
+
+int rd_read_state(rd_handle* h, double* u, double* v, int on_device) {
+  if (!h || !u || !v) return AMR_ERR_INVALID_ARG;
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  Mg& M = h->mg;
+  if (int rc = M.cuda(cudaMemcpyAsync(u, h->d_u.p, h->cells * 8, k, M.stream), "copy u")) return rc;
+  if (int rc = M.cuda(cudaMemcpyAsync(v, h->d_v.p, h->cells * 8, k, M.stream), "copy v")) return rc;
+  return M.cuda(cudaStreamSynchronize(M.stream), "sync");
+}
+
+int rd_step(rd_handle* h, int nsteps, int* cycles) {
+  if (!h || nsteps < 0) return AMR_ERR_INVALID_ARG;
+  Mg& M = h->mg;
+  const int ni = h->cfg.n_inst;
+  RdArgs A{};
+  A.inst = M.d_inst.as<InstDev>();
+  A.ninst = ni;
+  A.ndim = h->cfg.ndim;
+  A.F = h->cfg.F;
+  A.k = h->cfg.k;
+  A.dt = h->cfg.dt;
+  A.D[0] = h->cfg.Du;
+  A.D[1] = h->cfg.Dv;
+  A.lam[0] = 2.0 / (h->cfg.dt * h->cfg.Du);
+  A.lam[1] = 2.0 / (h->cfg.dt * h->cfg.Dv);
+  A.u = h->d_u.as<double>();
+  A.v = h->d_v.as<double>();
+  A.X = M.d_X.as<double>();
+  A.B = M.d_B.as<double>();
+  A.Fn = h->d_Fn.as<double>();
+  // level-0 chunks of species 0 only
+  unsigned nch0 = 0;
+  for (const Chunk& c : M.ch0)
+    if (c.inst < ni) ++nch0;
+  for (int s = 0; s < nsteps; ++s) {
+    rd_rhs_kernel<<<nch0, kChunk, 0, M.stream>>>(A, M.d_ch0.as<Chunk>());
+    ++M.launches;
+    int rc = M.solve_device_any();
+    if (rc) return rc;
+    bool ok;
+    std::vector<int> cyc(2 * ni);
+    if ((rc = M.results(cyc.data(), nullptr, &ok))) return rc;
+    if (cycles) std::memcpy(cycles + (size_t)s * 2 * ni, cyc.data(), cyc.size() * sizeof(int));
+    if (!ok) return M.fail(MG_ERR_NOT_CONVERGED, "an instance did not reach rtol within max_cycles");
+    rd_finish_kernel<<<nch0, kChunk, 0, M.stream>>>(A, M.d_ch0.as<Chunk>());
+    ++M.launches;
+    if ((rc = M.cuda(cudaGetLastError(), "rd launch"))) return rc;
+  }
+  return M.cuda(cudaStreamSynchronize(M.stream), "sync");
+}
+
+}  // extern "C"
