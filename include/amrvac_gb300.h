@@ -163,6 +163,39 @@ int amr_profile_step(amr_handle* h, double t_end, float* ms, int* kind, int cap,
 int amr_kernel_launches(const amr_handle* h, long long* n);
 
 /* ------------------------------------------------------------------------
+ * CFL step and conserved totals without any device allocation.
+ *
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory themselves -- code running while an enclosing
+ * framework forbids cudaMalloc (for example during CUDA-graph stream capture
+ * in that framework, or under a fixed memory budget owned by a pool
+ * allocator), or latency-critical loops that cannot afford cudaMalloc's
+ * implicit device synchronisation.
+ *
+ * Computes, for a uniform block grid (every leaf on level 1, leaves in Morton
+ * order as amr_leaf_info reports them for a fresh handle), the same two
+ * results that amr_set_state leaves behind: dt_cfl = cfl / max over cells of
+ * sum_d (|v_d| + c)/dx_d and totals[v] = sum of U dV (float64).
+ *  - cfg: geometry and gamma/cfl as for amr_create (precision, flux, limiter,
+ *    rk, refinement fields and max_blocks are ignored); cfg->stream is used.
+ *  - U: device pointer, float64 conserved state [leaf][var][cell],
+ *    nleaves = product of cfg->base_nblocks.  Not modified.
+ *  - dt_cfl (host, 1 double), totals (host, ndim+2 doubles): outputs.
+ * Errors: AMR_ERR_INVALID_ARG (bad config or nleaves not matching the grid),
+ * AMR_ERR_CAPACITY if nleaves > AMR_NOALLOC_MAX_LEAVES, AMR_ERR_NONPHYSICAL
+ * (outputs still written), AMR_ERR_CUDA.
+ * Memory: the scratch is one fixed array of about 0.7 MB in the library's
+ * device image, present on every GPU that loads the library until exit; no
+ * call allocates.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call on a device shares the array and keeps the previous
+ * call's contents (the call resets what must start at zero): calls that
+ * overlap on the GPU (different streams or threads) race.  Synchronous.
+ * ------------------------------------------------------------------------ */
+#define AMR_NOALLOC_MAX_LEAVES 16384
+int amr_reduce_noalloc(const amr_config* cfg, const double* U, long long nleaves, double* dt_cfl, double* totals);
+
+/* ------------------------------------------------------------------------
  * Batched Helmholtz multigrid (Sec. 2.5.1, Eq. (diff-helmholtz); Sec. 1.4).
  * Solves (lambda_i - lap_h) x = b for n_inst independent periodic square
  * (cube) grids of side n_cells[i] on [0, L]^ndim, cell-centred 5/7-point

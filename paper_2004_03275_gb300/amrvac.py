@@ -82,6 +82,7 @@ _SIGS = {
     "amr_face_ghosts": ([_vp, C.c_longlong, _dp, C.c_longlong], C.c_int),
     "amr_kernel_launches": ([_vp, _llp], C.c_int),
     "amr_profile_step": ([_vp, C.c_double, C.POINTER(C.c_float), _ip, C.c_int, _ip], C.c_int),
+    "amr_reduce_noalloc": ([C.POINTER(AmrConfig), _vp, C.c_longlong, _dp, _dp], C.c_int),
     "mg_create": ([C.POINTER(MgConfig), C.POINTER(_vp)], C.c_int),
     "mg_destroy": ([_vp], C.c_int),
     "mg_last_error": ([_vp], C.c_char_p),
@@ -308,6 +309,27 @@ class AmrSolver:
         n = C.c_longlong()
         _check(self.lib.amr_kernel_launches(self.h, C.byref(n)), self.h)
         return n.value
+
+
+NOALLOC_MAX_LEAVES = 16384
+
+
+def reduce_noalloc(U, stream=None, **kw):
+    """amr_reduce_noalloc: (dt_cfl, totals) of a uniform block grid whose float64
+    conserved state U ([leaf][var][cell], a CUDA tensor) is already on the device.
+    Allocates no device memory; see include/amrvac_gb300.h for the shared scratch."""
+    lib = load()
+    cfg = make_amr_config(stream=stream, **kw)
+    p, dev = _ptr(U)
+    if not dev:
+        raise ValueError("U must be device memory")
+    nleaves = int(np.prod(list(cfg.base_nblocks)[:cfg.ndim]))
+    dt = C.c_double()
+    tot = np.zeros(cfg.ndim + 2)
+    rc = lib.amr_reduce_noalloc(C.byref(cfg), p, nleaves, C.byref(dt), tot.ctypes.data_as(_dp))
+    if rc != AMR_OK:
+        raise AmrError(rc, "amr_reduce_noalloc")
+    return dt.value, tot
 
 
 class MgSolver:
