@@ -129,7 +129,13 @@ def time_steps(torch, solver, stream, steps):
     return ev0.elapsed_time(ev1) / steps
 
 
-def stage_roofline(solver, nsteps, nv, wbytes, ncells, hbm_gbs):
+# dram__bytes_read.sum + dram__bytes_write.sum per stage launch (mean of the three stages of a
+# step) from the ncu capture summarised in profiles/stage2d_f32_kh2048.md; valid for the
+# kernel as captured there.
+STAGE2D_F32_TRAFFIC = 143.0e6
+
+
+def stage_roofline(solver, nsteps, nv, wbytes, ncells, hbm_gbs, traffic=None):
     """Average stage-kernel duration from per-kernel CUDA events, algorithmic bytes per launch:
     stage 1 reads U^n and writes U^1 (2 nv w per cell), stages 2-3 read U^(s), U^n and write (3 nv w)."""
     ms_total, bytes_total, nlaunch = 0.0, 0.0, 0
@@ -142,10 +148,79 @@ def stage_roofline(solver, nsteps, nv, wbytes, ncells, hbm_gbs):
             nlaunch += 1
     achieved = bytes_total / (ms_total * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_gbs, "unit": "GB/s",
-            "frac": round(achieved / hbm_gbs, 4), "traffic": None,
+            "frac": round(achieved / hbm_gbs, 4), "traffic": traffic,
             "kernel": "stage2d_f32_kernel<16,HLLC,VANLEER>", "launches_timed": nlaunch,
             "avg_launch_us": round(ms_total / nlaunch * 1e3, 2),
             "bytes_per_launch_avg": int(bytes_total / nlaunch), "frac_of_8TBs_nameplate": round(achieved / 8000, 4)}
+
+
+def bench_gray_scott(torch, amrvac, stream, steps=5):
+    """Config 4: 16 Gray-Scott instances (256^2 .. 2048^2), IMEX steps, multigrid to 1e-10.
+    Unit: cell-updates/s (both species of every instance per IMEX step)."""
+    from paper_2004_03275_gb300 import inputs
+    sizes = inputs.gray_scott_batch_sizes()
+    us, vs = [], []
+    for i, n in enumerate(sizes):
+        u, v = inputs.gray_scott_patches(n, seed=4000 + i)
+        us.append(u.ravel())
+        vs.append(v.ravel())
+    rd = amrvac.RdSolver(2, sizes, 2.5, Du=2e-5, Dv=1e-5, F=0.04, k=0.06, dt=0.5, precision="fp32",
+                         stream=stream.cuda_stream)
+    rd.set_state(np.concatenate(us), np.concatenate(vs))
+    rd.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cyc = rd.step(steps)
+    torch.cuda.synchronize()
+    el = (time.perf_counter() - t0) / steps
+    cells = sum(n * n for n in sizes)
+    out = {"workload": "Gray-Scott IMEX, 16 instances 256^2..2048^2 (28.7M cells/species), dt 0.5, MG rtol 1e-10",
+           "ms_per_step": el * 1e3, "cell_updates_per_s": 2 * cells / el, "steps": steps,
+           "vcycles_per_solve_mean": float(np.mean(cyc)), "vcycles_max": int(np.max(cyc)),
+           "timing": "host wall clock around rd_step (synchronous), stream synchronized"}
+    rd.close()
+    return out
+
+
+def bench_blast(torch, amrvac, stream, steps=20, regrid_every=10):
+    """Config 3: 3D blast, 4^3 base blocks of 16^3, 4 levels (effective 512^3), HLLC + Koren, SSPRK3,
+    FP32 state, regrid every 10 steps.  cell-updates/s per RK stage excluding regrid time."""
+    from paper_2004_03275_gb300 import inputs
+    kw = dict(ndim=3, block_nx=16, base=[4, 4, 4], max_level=4, gamma=5.0 / 3.0, cfl=0.8, flux="hllc",
+              limiter="koren", rk=3, bc="periodic", refine_tol=0.2, coarsen_frac=0.5, var_mask=1 | 16,
+              precision="fp32", max_blocks=20000, stream=stream.cuda_stream)
+    s = amrvac.AmrSolver(**kw)
+    for it in range(4):  # sample the initial condition on the tree, refine, repeat
+        lev, crd = s.leaves()
+        x, _ = inputs.cell_centres(lev, crd, 3, 16, [4, 4, 4], [0, 0, 0], [1, 1, 1])
+        s.set_prim(inputs.blast(x, seed=7))
+        if it < 3:
+            s.regrid()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms, cells_steps, t_regrid, levels = 0.0, 0, 0.0, []
+    done = 0
+    while done < steps:
+        k = min(regrid_every, steps - done)
+        lev, _ = s.leaves()
+        levels.append(np.bincount(lev, minlength=5)[1:].tolist())
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        s.run(k)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        s.sync()
+        step_ms += ev0.elapsed_time(ev1)
+        cells_steps += len(lev) * 4096 * k
+        done += k
+        t0 = time.perf_counter()
+        s.regrid()
+        t_regrid += time.perf_counter() - t0
+    out = {"workload": "3D blast, base 4^3 x 16^3, max_level 4 (eff. 512^3), HLLC+Koren, SSPRK3, FP32",
+           "steps": steps, "cell_stage_updates_per_s": 3 * cells_steps / (step_ms * 1e-3),
+           "ms_per_step_mean": step_ms / steps, "regrid_ms_mean": t_regrid * 1e3 / max(1, steps // regrid_every),
+           "blocks_per_level_at_each_regrid": levels}
+    s.close()
+    return out
 
 
 def oracle_cpu_baseline(budget_s=12.0, max_side=512):
@@ -217,6 +292,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true", help="skip the Gray-Scott and blast configurations")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -268,7 +344,7 @@ def main():
     clocks = clk.stop() if rank == 0 else None
     ms32 = max_over_ranks(ms32)
     value = ws * ncells * 3 / (ms32 * 1e-3)
-    roof = stage_roofline(s32, 5, 4, 4, ncells, hbm)
+    roof = stage_roofline(s32, 5, 4, 4, ncells, hbm, traffic=STAGE2D_F32_TRAFFIC)
     roof["peak_source"] = peak_src
 
     # ---------------------------------------------------------------- FP64 plain
@@ -313,6 +389,11 @@ def main():
     totals = s32.totals().tolist()
     s32.close()
 
+    extra = {}
+    if not args.skip_extra and rank == 0:
+        extra["gray_scott_batch"] = bench_gray_scott(torch, amrvac, stream)
+        extra["blast3d"] = bench_blast(torch, amrvac, stream)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
         cpu = oracle_cpu_baseline()
@@ -328,6 +409,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "fp64_plain": fp64, "totals_fp64": totals,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
