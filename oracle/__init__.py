@@ -327,5 +327,70 @@ def rd_step(u, v, L, Du, Dv, F, k, dt, nu1=2, nu2=2, max_cycles=50, rtol=1e-10, 
     return u, v, cyc
 
 
-def _bind_cnn(L):  # filled in by the CNN part of the oracle
-    pass
+def _bind_cnn(L):
+    L.orc_cnn_num_params.argtypes = [C.c_int]
+    L.orc_cnn_num_params.restype = C.c_longlong
+    L.orc_cnn_forward.argtypes = [C.c_int, _dp, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp]
+    L.orc_cnn_loss_grad.argtypes = [C.c_int, _dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp]
+    L.orc_cnn_loss_grad.restype = C.c_double
+    L.orc_cnn_adam.argtypes = [C.c_longlong, _dp, _dp, _dp, _dp, C.c_int, C.c_double, C.c_double, C.c_double,
+                               C.c_double]
+    L.orc_gelu.argtypes = [C.c_double]
+    L.orc_gelu.restype = C.c_double
+    L.orc_gelu_d.argtypes = [C.c_double]
+    L.orc_gelu_d.restype = C.c_double
+
+
+CNN_CHANNELS = (5, 16, 16, 16, 2)
+
+
+def cnn_num_params(ndim):
+    return lib().orc_cnn_num_params(ndim)
+
+
+def _shape(x, ndim):
+    x = _f64(x)
+    N = x.shape[0]
+    if ndim == 2:
+        return x, N, 1, x.shape[2], x.shape[3]
+    return x, N, x.shape[2], x.shape[3], x.shape[4]
+
+
+def cnn_forward(params, x, ndim=2):
+    """x: [N][5][H][W] (2D) or [N][5][D][H][W]; returns [N][2][...]"""
+    x, N, D, H, W = _shape(x, ndim)
+    out = np.zeros((N, 2) + x.shape[2:])
+    lib().orc_cnn_forward(ndim, _d(_f64(params)), N, D, H, W, _d(x), _d(out))
+    return out
+
+
+def cnn_loss_grad(params, x, target, margin=0, ndim=2):
+    x, N, D, H, W = _shape(x, ndim)
+    target = _f64(target)
+    g = np.zeros(cnn_num_params(ndim))
+    loss = lib().orc_cnn_loss_grad(ndim, _d(_f64(params)), N, D, H, W, margin, _d(x), _d(target), _d(g))
+    return loss, g
+
+
+def cnn_adam(params, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """in place on params, m, v (float64 arrays)"""
+    lib().orc_cnn_adam(len(params), _d(params), _d(_f64(grad)), _d(m), _d(v), t, lr, b1, b2, eps)
+
+
+def gelu(z):
+    return lib().orc_gelu(float(z))
+
+
+def gelu_d(z):
+    return lib().orc_gelu_d(float(z))
+
+
+def cnn_layer_slices(ndim):
+    """(W slice, b slice, cin, cout) per layer in the flat parameter vector"""
+    T = 27 if ndim == 3 else 9
+    out, o = [], 0
+    for l in range(4):
+        ci, co = CNN_CHANNELS[l], CNN_CHANNELS[l + 1]
+        out.append((slice(o, o + co * ci * T), slice(o + co * ci * T, o + co * ci * T + co), ci, co))
+        o += co * ci * T + co
+    return out

@@ -123,6 +123,18 @@ void orc_rd_reaction(double F, double k, int n, const double* u, const double* v
                      double* fu, double* fv);
 void orc_laplacian(int ndim, int n, double L, const double* x, double* out);
 
+/* ---- learned multigrid guess: CNN 5->16->16->16->2, 3^ndim periodic convolutions ----
+ * params flat: per layer W[cout][cin][tap] then b[cout]; images [N][C][D][H][W] (D = 1 in 2D) */
+long long orc_cnn_num_params(int ndim);
+void orc_cnn_forward(int ndim, const double* params, int N, int D, int H, int W, const double* in, double* out);
+/* masked MSE (pixels at least `margin` from every edge) and its gradient; returns the loss */
+double orc_cnn_loss_grad(int ndim, const double* params, int N, int D, int H, int W, int margin, const double* in,
+                         const double* target, double* grad);
+void orc_cnn_adam(long long n, double* params, const double* grad, double* m, double* v, int t, double lr,
+                  double b1, double b2, double eps);
+double orc_gelu(double z);
+double orc_gelu_d(double z);
+
 #ifdef __cplusplus
 }
 #endif
