@@ -263,6 +263,40 @@ int rd_read_state(rd_handle* h, double* u, double* v, int on_device);
  * V-cycles (species-major: u of every instance, then v).  Synchronous. */
 int rd_step(rd_handle* h, int nsteps, int* cycles);
 
+/* ------------------------------------------------------------------------
+ * Learned multigrid initial guess (no counterpart in the paper; the project's
+ * addition to the implicit diffusion stage of Eq. (imex)).
+ *
+ * Network: 4 periodic convolutions with 3^ndim taps and bias, channels
+ * 5 -> 16 -> 16 -> 16 -> 2, GELU (erf form) after layers 1..3; bf16 weights and
+ * activations, fp32 accumulation on the tensor cores.  Parameters are float32,
+ * flat, per layer W[cout][cin][tap] (tap x fastest over offsets -1, 0, 1 per
+ * dimension) followed by b[cout]; training keeps float32 master weights (Adam,
+ * beta 0.9/0.999, eps 1e-8).  Images are device float32 [N][C][D][H][W]
+ * (D = 1 in 2D); H and W multiples of 16 (2D) or D of 4 and H, W of 8 (3D).
+ * Loss: mean over both output channels and over pixels at least `margin`
+ * cells from every image edge of (out - target)^2.
+ * ------------------------------------------------------------------------ */
+typedef struct cnn_handle cnn_handle;
+
+/* He-normal initial weights from `seed`, zero biases; stream NULL = own stream. */
+int cnn_create(int ndim, unsigned long long seed, void* stream, cnn_handle** out);
+int cnn_destroy(cnn_handle* h);
+const char* cnn_last_error(const cnn_handle* h);
+int cnn_num_params(const cnn_handle* h, long long* n);
+/* host float32 arrays of exactly cnn_num_params values; set also resets Adam */
+int cnn_set_params(cnn_handle* h, const float* params, long long n);
+int cnn_get_params(cnn_handle* h, float* params, long long n);
+/* in: device [N][5][...]; out: device [N][2][...].  Synchronous. */
+int cnn_forward(cnn_handle* h, const float* in, int N, int D, int H, int W, float* out);
+/* loss (host, may be NULL) and its gradient (host float32 [n params], may be NULL) */
+int cnn_gradient(cnn_handle* h, const float* in, const float* target, int N, int D, int H, int W, int margin,
+                 float* grad, float* loss);
+/* one Adam step on the batch; loss (host) if not NULL */
+int cnn_train_step(cnn_handle* h, const float* in, const float* target, int N, int D, int H, int W, int margin,
+                   float lr, float* loss);
+int cnn_kernel_launches(const cnn_handle* h, long long* n);
+
 #ifdef __cplusplus
 }
 #endif

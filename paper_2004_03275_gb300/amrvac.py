@@ -94,6 +94,18 @@ _SIGS = {
     "rd_set_state": ([_vp, _vp, _vp, C.c_int], C.c_int),
     "rd_read_state": ([_vp, _vp, _vp, C.c_int], C.c_int),
     "rd_step": ([_vp, C.c_int, _ip], C.c_int),
+    "cnn_create": ([C.c_int, C.c_ulonglong, _vp, C.POINTER(_vp)], C.c_int),
+    "cnn_destroy": ([_vp], C.c_int),
+    "cnn_last_error": ([_vp], C.c_char_p),
+    "cnn_num_params": ([_vp, _llp], C.c_int),
+    "cnn_set_params": ([_vp, C.POINTER(C.c_float), C.c_longlong], C.c_int),
+    "cnn_get_params": ([_vp, C.POINTER(C.c_float), C.c_longlong], C.c_int),
+    "cnn_forward": ([_vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp], C.c_int),
+    "cnn_gradient": ([_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_float),
+                      C.POINTER(C.c_float)], C.c_int),
+    "cnn_train_step": ([_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float,
+                        C.POINTER(C.c_float)], C.c_int),
+    "cnn_kernel_launches": ([_vp, _llp], C.c_int),
 }
 
 
@@ -443,3 +455,77 @@ class RdSolver:
         cyc = np.zeros((nsteps, 2, len(self.n_cells)), dtype=np.int32)
         _check(self.lib.rd_step(self.h, nsteps, cyc.ctypes.data_as(_ip)), self.h, "rd_last_error")
         return cyc
+
+
+class CnnNet:
+    """Owns one cnn_handle (learned multigrid guess).  Images are CUDA float32
+    tensors [N][C][H][W] (2D) or [N][C][D][H][W] (3D)."""
+
+    def __init__(self, ndim=2, seed=0, stream=None):
+        self.lib = load()
+        self.ndim = ndim
+        h = _vp()
+        rc = self.lib.cnn_create(ndim, seed, stream, C.byref(h))
+        if rc != AMR_OK:
+            raise AmrError(rc, "cnn_create")
+        self.h = h
+        n = C.c_longlong()
+        _check(self.lib.cnn_num_params(self.h, C.byref(n)), self.h, "cnn_last_error")
+        self.nparams = n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cnn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dims(self, x):
+        if self.ndim == 2:
+            N, _, H, W = x.shape
+            return N, 1, H, W
+        N, _, D, H, W = x.shape
+        return N, D, H, W
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(self.lib.cnn_set_params(self.h, p.ctypes.data_as(C.POINTER(C.c_float)), len(p)), self.h,
+               "cnn_last_error")
+
+    def get_params(self):
+        p = np.zeros(self.nparams, dtype=np.float32)
+        _check(self.lib.cnn_get_params(self.h, p.ctypes.data_as(C.POINTER(C.c_float)), len(p)), self.h,
+               "cnn_last_error")
+        return p
+
+    def forward(self, x, out=None):
+        import torch
+        N, D, H, W = self._dims(x)
+        if out is None:
+            out = torch.empty((x.shape[0], 2) + tuple(x.shape[2:]), dtype=torch.float32, device=x.device)
+        _check(self.lib.cnn_forward(self.h, x.data_ptr(), N, D, H, W, out.data_ptr()), self.h, "cnn_last_error")
+        return out
+
+    def gradient(self, x, target, margin=0):
+        N, D, H, W = self._dims(x)
+        g = np.zeros(self.nparams, dtype=np.float32)
+        loss = C.c_float()
+        _check(self.lib.cnn_gradient(self.h, x.data_ptr(), target.data_ptr(), N, D, H, W, margin,
+                                     g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss)), self.h, "cnn_last_error")
+        return loss.value, g
+
+    def train_step(self, x, target, lr=1e-3, margin=0, want_loss=True):
+        N, D, H, W = self._dims(x)
+        loss = C.c_float()
+        _check(self.lib.cnn_train_step(self.h, x.data_ptr(), target.data_ptr(), N, D, H, W, margin, lr,
+                                       C.byref(loss) if want_loss else None), self.h, "cnn_last_error")
+        return loss.value if want_loss else None
+
+    def kernel_launches(self):
+        n = C.c_longlong()
+        _check(self.lib.cnn_kernel_launches(self.h, C.byref(n)), self.h, "cnn_last_error")
+        return n.value
