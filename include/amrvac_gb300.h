@@ -297,6 +297,23 @@ int cnn_train_step(cnn_handle* h, const float* in, const float* target, int N, i
                    float lr, float* loss);
 int cnn_kernel_launches(const cnn_handle* h, long long* n);
 
+/* Multigrid initial guess of rd_step: net = NULL restores the previous-step
+ * guess w_n; otherwise X = w_n + scale * net(u_n, v_n, u*_prev, v*_prev, dt)
+ * per species (the network predicts the increment over the previous-step
+ * guess).  The multigrid still iterates to rtol.  The handle keeps a pointer to
+ * net (not owned).  Sides must be multiples of 16 (2D) or 8 (3D). */
+int rd_set_guess(rd_handle* h, cnn_handle* net, double scale);
+/* Max-norm relative residuals max|b - A x| / max|b| of the initial guess and of
+ * the final iterate of the last multigrid solve, per (species, instance):
+ * initial[2*n_inst], final[2*n_inst] (host, either may be NULL). */
+int rd_last_residuals(rd_handle* h, double* initial, double* final_);
+/* Training pairs from the last rd_step: for crop k of side `crop` with lowest
+ * corner corner[3k..3k+2] (periodic) in instance inst[k]: in[k] (device float
+ * [5][crop^ndim]) = (u_n, v_n, u*_prev, v*_prev, dt) and target[k] (device float
+ * [2][crop^ndim]) = (w* - w_n) / scale for u and v. */
+int rd_extract_crops(rd_handle* h, int ncrops, const int* inst, const int* corner, int crop, double scale, float* in,
+                     float* target);
+
 #ifdef __cplusplus
 }
 #endif

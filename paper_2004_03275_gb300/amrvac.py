@@ -106,6 +106,9 @@ _SIGS = {
     "cnn_train_step": ([_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float,
                         C.POINTER(C.c_float)], C.c_int),
     "cnn_kernel_launches": ([_vp, _llp], C.c_int),
+    "rd_set_guess": ([_vp, _vp, C.c_double], C.c_int),
+    "rd_last_residuals": ([_vp, _dp, _dp], C.c_int),
+    "rd_extract_crops": ([_vp, C.c_int, _ip, _ip, C.c_int, C.c_double, _vp, _vp], C.c_int),
 }
 
 
@@ -449,6 +452,27 @@ class RdSolver:
         pv, dv = _ptr(v)
         _check(self.lib.rd_read_state(self.h, pu, pv, du), self.h, "rd_last_error")
         return u, v
+
+    def set_guess(self, net=None, scale=1.0):
+        """Multigrid initial guess: None -> previous-step guess w_n; a CnnNet -> g + scale * net(...)."""
+        _check(self.lib.rd_set_guess(self.h, net.h if net is not None else None, scale), self.h, "rd_last_error")
+        self._guess = net  # keep the network alive while the handle points to it
+
+    def last_residuals(self):
+        """(initial, final) max-norm relative residuals of the last solve, shape [2, n_inst]."""
+        a = np.zeros(2 * len(self.n_cells))
+        b = np.zeros(2 * len(self.n_cells))
+        _check(self.lib.rd_last_residuals(self.h, a.ctypes.data_as(_dp), b.ctypes.data_as(_dp)), self.h,
+               "rd_last_error")
+        return a.reshape(2, -1), b.reshape(2, -1)
+
+    def extract_crops(self, inst, corners, crop, scale, out_in, out_tgt):
+        """Training pairs of the last step into device float tensors [n][5][...], [n][2][...]."""
+        inst = np.ascontiguousarray(inst, dtype=np.int32)
+        corners = np.ascontiguousarray(corners, dtype=np.int32).reshape(-1, 3)
+        _check(self.lib.rd_extract_crops(self.h, len(inst), inst.ctypes.data_as(_ip), corners.ctypes.data_as(_ip),
+                                         crop, scale, out_in.data_ptr(), out_tgt.data_ptr()), self.h,
+               "rd_last_error")
 
     def step(self, nsteps=1):
         """Returns V-cycles per step, shape [nsteps, 2, n_inst] (species-major)."""

@@ -57,6 +57,7 @@ struct MgState {
   unsigned long long* rnorm;  // max |R| bits per instance
   double* bnorm;              // max |B| per instance
   double* lastres;            // last max |R| per instance
+  double* initres;            // max |R| of the initial guess per instance
   int* active;                // instance still iterating
   int* cycles;
   int* failed;
@@ -181,6 +182,7 @@ __global__ void check_kernel(MgState S, int ninst) {
     double rn = __longlong_as_double((long long)S.rnorm[i]);
     S.rnorm[i] = 0ull;
     S.lastres[i] = rn;
+    if (S.cycles[i] == 0) S.initres[i] = rn;
     if (rn <= S.rtol * S.bnorm[i]) {
       S.active[i] = 0;
     } else if (S.cycles[i] >= S.max_cycles) {
@@ -373,6 +375,77 @@ __global__ void rd_finish_kernel(RdArgs A, const Chunk* ch) {
   A.v[o + t] = A.v[o + t] + (0.5 * A.dt) * (A.Fn[I1.off0 + t] + Fv);
 }
 
+// ------------------------------------------------------- learned guess --
+// network input of one instance: (u_n, v_n, u*_prev, v*_prev, dt) as float [5][cells]
+__global__ void rd_cnn_input_kernel(const double* __restrict__ wn, const double* __restrict__ pin, long long cells,
+                                    long long off, long long n0, float dt, float* __restrict__ cin) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n0) return;
+  cin[0 * n0 + t] = (float)wn[off + t];
+  cin[1 * n0 + t] = (float)wn[cells + off + t];
+  cin[2 * n0 + t] = (float)pin[off + t];
+  cin[3 * n0 + t] = (float)pin[cells + off + t];
+  cin[4 * n0 + t] = dt;
+}
+
+// multigrid guess X = w_n + scale * network output (per species): the network
+// predicts the increment over the previous-step guess
+__global__ void rd_cnn_guess_kernel(const InstDev* __restrict__ inst, int iu, int iv, const float* __restrict__ cout,
+                                    long long n0, double scale, double* __restrict__ X, const double* __restrict__ wn,
+                                    long long cells) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n0) return;
+  const InstDev& Iu = inst[iu];
+  const InstDev& Iv = inst[iv];
+  X[Iu.off0 + t] = wn[Iu.off0 + t] + scale * (double)cout[t];
+  X[Iv.off0 + t] = wn[cells + Iu.off0 + t] + scale * (double)cout[n0 + t];
+}
+
+// training pairs: crops of (u_n, v_n, u*_prev, v*_prev, dt) and target (w* - w_n) / scale
+struct CropArgs {
+  const InstDev* inst;
+  const int* cinst;
+  const int* corner;  // [ncrops][3]
+  int ninst, ndim, crop, ncrops;
+  long long cells;
+  const double* wn;
+  const double* pin;
+  const double* X;
+  const double* B;
+  float dt;
+  double inv_scale;
+  float* in;
+  float* tgt;
+};
+
+__global__ void rd_crop_kernel(CropArgs A) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long cp = 1;
+  for (int d = 0; d < A.ndim; ++d) cp *= A.crop;
+  if (t >= cp * A.ncrops) return;
+  int k = (int)(t / cp);
+  long long q = t % cp;
+  int i = A.cinst[k];
+  const InstDev& Iu = A.inst[i];
+  const InstDev& Iv = A.inst[i + A.ninst];
+  int n = Iu.n[0];
+  int c[3] = {(int)(q % A.crop), A.ndim > 1 ? (int)((q / A.crop) % A.crop) : 0,
+              A.ndim > 2 ? (int)(q / ((long long)A.crop * A.crop)) : 0};
+  int g[3] = {0, 0, 0};
+  for (int d = 0; d < A.ndim; ++d) g[d] = (A.corner[3 * k + d] + c[d]) % n;
+  long long p = (long long)g[0] + (long long)n * ((long long)g[1] + (long long)n * g[2]);
+  long long off = Iu.off0;  // species-0 offset = state offset
+  float* in = A.in + (long long)k * 5 * cp;
+  in[0 * cp + q] = (float)A.wn[off + p];
+  in[1 * cp + q] = (float)A.wn[A.cells + off + p];
+  in[2 * cp + q] = (float)A.pin[off + p];
+  in[3 * cp + q] = (float)A.pin[A.cells + off + p];
+  in[4 * cp + q] = A.dt;
+  float* tg = A.tgt + (long long)k * 2 * cp;
+  tg[q] = (float)((A.X[Iu.off0 + p] - A.wn[off + p]) * A.inv_scale);
+  tg[cp + q] = (float)((A.X[Iv.off0 + p] - A.wn[A.cells + off + p]) * A.inv_scale);
+}
+
 // ------------------------------------------------------------------ host --
 struct DevBuf {
   void* p = nullptr;
@@ -457,7 +530,7 @@ struct Mg {
   std::vector<Chunk> ch0;
   std::vector<std::vector<Chunk>> ch_half, ch_coarse, ch_fine;
   std::vector<int> coarse_inst, coarse_row0;
-  DevBuf d_inst, d_X, d_B, d_xl, d_bl, d_rnorm, d_bnorm, d_lastres, d_active, d_cycles, d_failed, d_any, d_inv;
+  DevBuf d_inst, d_X, d_B, d_xl, d_bl, d_rnorm, d_bnorm, d_lastres, d_initres, d_active, d_cycles, d_failed, d_any, d_inv;
   DevBuf d_ch0, d_chall, d_cinst, d_crow0;
   std::vector<size_t> off_half, off_coarse, off_fine;
   int* h_any = nullptr;
@@ -488,6 +561,7 @@ struct Mg {
     S.rnorm = d_rnorm.as<unsigned long long>();
     S.bnorm = d_bnorm.as<double>();
     S.lastres = d_lastres.as<double>();
+    S.initres = d_initres.as<double>();
     S.active = d_active.as<int>();
     S.cycles = d_cycles.as<int>();
     S.failed = d_failed.as<int>();
@@ -596,7 +670,8 @@ struct Mg {
         (rc = cuda(d_X.alloc(n0 * 8), "alloc X")) || (rc = cuda(d_B.alloc(n0 * 8), "alloc B")) ||
         (rc = cuda(d_xl.alloc(nlevtot * wb), "alloc levels")) || (rc = cuda(d_bl.alloc(nlevtot * wb), "alloc levels")) ||
         (rc = cuda(d_rnorm.alloc(n_inst * 8), "alloc")) || (rc = cuda(d_bnorm.alloc(n_inst * 8), "alloc")) ||
-        (rc = cuda(d_lastres.alloc(n_inst * 8), "alloc")) || (rc = cuda(d_active.alloc(n_inst * 4), "alloc")) ||
+        (rc = cuda(d_lastres.alloc(n_inst * 8), "alloc")) || (rc = cuda(d_initres.alloc(n_inst * 8), "alloc")) ||
+        (rc = cuda(d_active.alloc(n_inst * 4), "alloc")) ||
         (rc = cuda(d_cycles.alloc(n_inst * 4), "alloc")) || (rc = cuda(d_failed.alloc(n_inst * 4), "alloc")) ||
         (rc = cuda(d_any.alloc(4), "alloc")) || (rc = cuda(d_inv.alloc(invoff * 8), "alloc inverse")))
       return rc;
@@ -744,8 +819,14 @@ struct rd_handle {
   rd_config cfg{};
   std::vector<int> sizes;
   DevBuf d_u, d_v, d_Fn;
+  DevBuf d_wn, d_prev, d_pin;  // state before the last step, last solution, solution before the last step
+  DevBuf d_cin, d_cout;        // network input / output of one instance (float)
+  bool have_prev = false;
+  cnn_handle* guess = nullptr;
+  double guess_scale = 1.0;
   std::string err;
   long long cells = 0;
+  long long maxcells = 0;
 };
 
 extern "C" {
@@ -812,8 +893,16 @@ int rd_create(const rd_config* cfg, rd_handle** out) {
                        cfg->rtol, cfg->coarse_max, cfg->precision, cfg->stream);
   if (rc) return rc;
   h->cells = h->mg.insts[cfg->n_inst].off0;  // species-0 block size = cells of all instances
+  for (int i = 0; i < cfg->n_inst; ++i) {
+    long long c = 1;
+    for (int d = 0; d < cfg->ndim; ++d) c *= cfg->n_cells[i];
+    h->maxcells = std::max(h->maxcells, c);
+  }
   if ((rc = h->mg.cuda(h->d_u.alloc(h->cells * 8), "alloc u")) || (rc = h->mg.cuda(h->d_v.alloc(h->cells * 8), "alloc v")) ||
-      (rc = h->mg.cuda(h->d_Fn.alloc(2 * h->cells * 8), "alloc Fn")))
+      (rc = h->mg.cuda(h->d_Fn.alloc(2 * h->cells * 8), "alloc Fn")) ||
+      (rc = h->mg.cuda(h->d_wn.alloc(2 * h->cells * 8), "alloc")) ||
+      (rc = h->mg.cuda(h->d_prev.alloc(2 * h->cells * 8), "alloc")) ||
+      (rc = h->mg.cuda(h->d_pin.alloc(2 * h->cells * 8), "alloc")))
     return rc;
   *out = h.release();
   return AMR_OK;
@@ -833,6 +922,7 @@ int rd_set_state(rd_handle* h, const double* u, const double* v, int on_device) 
   Mg& M = h->mg;
   if (int rc = M.cuda(cudaMemcpyAsync(h->d_u.p, u, h->cells * 8, k, M.stream), "copy u")) return rc;
   if (int rc = M.cuda(cudaMemcpyAsync(h->d_v.p, v, h->cells * 8, k, M.stream), "copy v")) return rc;
+  h->have_prev = false;
   return M.cuda(cudaStreamSynchronize(M.stream), "sync");
 }
 
@@ -869,11 +959,42 @@ int rd_step(rd_handle* h, int nsteps, int* cycles) {
   unsigned nch0 = 0;
   for (const Chunk& c : M.ch0)
     if (c.inst < ni) ++nch0;
+  const size_t cb = (size_t)h->cells * 8;
+  double* wn = h->d_wn.as<double>();
+  double* prev = h->d_prev.as<double>();
+  double* pin = h->d_pin.as<double>();
   for (int s = 0; s < nsteps; ++s) {
+    int rc;
+    // keep w_n and the previous solution (inputs of the learned guess and of training crops)
+    if ((rc = M.cuda(cudaMemcpyAsync(wn, h->d_u.p, cb, cudaMemcpyDeviceToDevice, M.stream), "copy")) ||
+        (rc = M.cuda(cudaMemcpyAsync(wn + h->cells, h->d_v.p, cb, cudaMemcpyDeviceToDevice, M.stream), "copy")) ||
+        (rc = M.cuda(cudaMemcpyAsync(pin, h->have_prev ? prev : wn, 2 * cb, cudaMemcpyDeviceToDevice, M.stream),
+                     "copy")))
+      return rc;
     rd_rhs_kernel<<<nch0, kChunk, 0, M.stream>>>(A, M.d_ch0.as<Chunk>());
     ++M.launches;
-    int rc = M.solve_device_any();
+    if (h->guess) {
+      if ((rc = M.cuda(cudaStreamSynchronize(M.stream), "sync"))) return rc;
+      for (int i = 0; i < ni; ++i) {
+        const InstDev& I = M.insts[i];
+        long long n0 = 1;
+        for (int d = 0; d < h->cfg.ndim; ++d) n0 *= I.n[0];
+        unsigned nb = (unsigned)((n0 + 255) / 256);
+        rd_cnn_input_kernel<<<nb, 256, 0, M.stream>>>(wn, pin, h->cells, I.off0, n0, (float)h->cfg.dt,
+                                                       h->d_cin.as<float>());
+        if ((rc = M.cuda(cudaStreamSynchronize(M.stream), "sync"))) return rc;
+        int n = I.n[0];
+        int crc = cnn_forward(h->guess, h->d_cin.as<float>(), 1, h->cfg.ndim == 3 ? n : 1, n, n, h->d_cout.as<float>());
+        if (crc) return M.fail(crc, std::string("learned guess: ") + cnn_last_error(h->guess));
+        rd_cnn_guess_kernel<<<nb, 256, 0, M.stream>>>(M.d_inst.as<InstDev>(), i, i + ni, h->d_cout.as<float>(), n0,
+                                                      h->guess_scale, M.d_X.as<double>(), wn, h->cells);
+        M.launches += 2;
+      }
+    }
+    rc = M.solve_device_any();
     if (rc) return rc;
+    if ((rc = M.cuda(cudaMemcpyAsync(prev, M.d_X.p, 2 * cb, cudaMemcpyDeviceToDevice, M.stream), "copy"))) return rc;
+    h->have_prev = true;
     bool ok;
     std::vector<int> cyc(2 * ni);
     if ((rc = M.results(cyc.data(), nullptr, &ok))) return rc;
@@ -883,6 +1004,76 @@ int rd_step(rd_handle* h, int nsteps, int* cycles) {
     ++M.launches;
     if ((rc = M.cuda(cudaGetLastError(), "rd launch"))) return rc;
   }
+  return M.cuda(cudaStreamSynchronize(M.stream), "sync");
+}
+
+int rd_last_residuals(rd_handle* h, double* initial, double* final_) {
+  if (!h) return AMR_ERR_INVALID_ARG;
+  Mg& M = h->mg;
+  std::vector<double> ir(M.ninst), lr(M.ninst), bn(M.ninst);
+  cudaMemcpy(ir.data(), M.d_initres.p, M.ninst * 8, cudaMemcpyDeviceToHost);
+  cudaMemcpy(lr.data(), M.d_lastres.p, M.ninst * 8, cudaMemcpyDeviceToHost);
+  if (int rc = M.cuda(cudaMemcpy(bn.data(), M.d_bnorm.p, M.ninst * 8, cudaMemcpyDeviceToHost), "copy")) return rc;
+  for (int i = 0; i < M.ninst; ++i) {
+    double b = bn[i] > 0 ? bn[i] : 1.0;
+    if (initial) initial[i] = ir[i] / b;
+    if (final_) final_[i] = lr[i] / b;
+  }
+  return AMR_OK;
+}
+
+int rd_set_guess(rd_handle* h, cnn_handle* net, double scale) {
+  if (!h || (net && !(scale > 0))) return AMR_ERR_INVALID_ARG;
+  if (net) {
+    for (int n : h->sizes) {
+      if (h->cfg.ndim == 2 && n % 16 != 0) return h->mg.fail(AMR_ERR_INVALID_ARG, "learned guess needs sides multiple of 16");
+      if (h->cfg.ndim == 3 && n % 8 != 0) return h->mg.fail(AMR_ERR_INVALID_ARG, "learned guess needs sides multiple of 8");
+    }
+    int rc;
+    if ((rc = h->mg.cuda(h->d_cin.alloc((size_t)h->maxcells * 5 * sizeof(float)), "alloc")) ||
+        (rc = h->mg.cuda(h->d_cout.alloc((size_t)h->maxcells * 2 * sizeof(float)), "alloc")))
+      return rc;
+  }
+  h->guess = net;
+  h->guess_scale = net ? scale : 1.0;
+  return AMR_OK;
+}
+
+int rd_extract_crops(rd_handle* h, int ncrops, const int* inst, const int* corner, int crop, double scale, float* in,
+                     float* target) {
+  if (!h || ncrops < 1 || !inst || !corner || crop < 1 || !(scale > 0) || !in || !target) return AMR_ERR_INVALID_ARG;
+  if (!h->have_prev) return h->mg.fail(AMR_ERR_INVALID_ARG, "no step taken yet");
+  Mg& M = h->mg;
+  for (int k = 0; k < ncrops; ++k)
+    if (inst[k] < 0 || inst[k] >= h->cfg.n_inst || crop > h->sizes[inst[k]]) return AMR_ERR_INVALID_ARG;
+  DevBuf dinst, dcorner;
+  int rc;
+  if ((rc = M.cuda(dinst.alloc(ncrops * sizeof(int)), "alloc")) || (rc = M.cuda(dcorner.alloc(ncrops * 3 * sizeof(int)), "alloc")))
+    return rc;
+  cudaMemcpy(dinst.p, inst, ncrops * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(dcorner.p, corner, ncrops * 3 * sizeof(int), cudaMemcpyHostToDevice);
+  CropArgs A{};
+  A.inst = M.d_inst.as<InstDev>();
+  A.cinst = dinst.as<int>();
+  A.corner = dcorner.as<int>();
+  A.ninst = h->cfg.n_inst;
+  A.ndim = h->cfg.ndim;
+  A.crop = crop;
+  A.ncrops = ncrops;
+  A.cells = h->cells;
+  A.wn = h->d_wn.as<double>();
+  A.pin = h->d_pin.as<double>();
+  A.X = M.d_X.as<double>();
+  A.B = M.d_B.as<double>();
+  A.dt = (float)h->cfg.dt;
+  A.inv_scale = 1.0 / scale;
+  A.in = in;
+  A.tgt = target;
+  long long cp = 1;
+  for (int d = 0; d < h->cfg.ndim; ++d) cp *= crop;
+  rd_crop_kernel<<<(unsigned)((cp * ncrops + 255) / 256), 256, 0, M.stream>>>(A);
+  ++M.launches;
+  if ((rc = M.cuda(cudaGetLastError(), "crops"))) return rc;
   return M.cuda(cudaStreamSynchronize(M.stream), "sync");
 }
 

@@ -1,0 +1,109 @@
+"""Training and evaluation of the learned multigrid initial guess.
+
+Orchestration only: the solver steps, the crop extraction, the network's
+forward/backward passes and the Adam updates all run in the CUDA library.
+
+Recipe (the project's own reading; the paper has no learned component):
+* training data: Gray-Scott IMEX runs of the plain solver (previous-step guess)
+  on training seeds, crops of side `crop` at seeded random positions after every
+  step, inputs (u_n, v_n, u*_prev, v*_prev, dt), target (w* - w_n) / scale (the
+  increment over the previous-step guess; a network that outputs zero gives
+  back that guess), where scale is the RMS of w* - w_n over the first
+  collected step;
+* loss: masked MSE (margin 4 = the network's receptive radius, so that the
+  periodic padding inside a crop never reaches a counted pixel);
+* Adam, lr 1e-3, batches of `batch` crops drawn uniformly with replacement;
+* evaluation on disjoint seeds: V-cycles per step and wall time per step with
+  the learned guess against the previous-step guess, both to the same rtol.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import amrvac, inputs
+
+GS = dict(Du=2e-5, Dv=1e-5, F=0.04, k=0.06, dt=0.5)
+
+
+def domain_for(n, ref_n=2048, ref_L=2.5):
+    """Domain side giving the same stiffness D dt / h^2 as the reference grid."""
+    return ref_L * n / ref_n
+
+
+def start_state(sizes, L, seeds):
+    us, vs = [], []
+    for n, sd in zip(sizes, seeds):
+        u, v = inputs.gray_scott_patches(n, L=L, seed=sd)
+        us.append(u.ravel())
+        vs.append(v.ravel())
+    return np.concatenate(us), np.concatenate(vs)
+
+
+def generate(torch, sizes, seeds, L, steps, crops_per_step, crop=64, warm=0, scale=None, seed=0, stream=None):
+    """Returns (inputs [M][5][c][c], targets [M][2][c][c], scale) as CUDA float tensors."""
+    rd = amrvac.RdSolver(2, sizes, L, precision="fp32", stream=stream, **GS)
+    rd.set_state(*start_state(sizes, L, seeds))
+    if warm:
+        rd.step(warm)
+    rng = np.random.default_rng(seed)
+    X, Y = [], []
+    for s in range(steps):
+        rd.step(1)
+        inst = rng.integers(0, len(sizes), crops_per_step)
+        corners = np.zeros((crops_per_step, 3), dtype=np.int32)
+        for k in range(crops_per_step):
+            n = sizes[inst[k]]
+            corners[k, :2] = rng.integers(0, n, 2)
+        if scale is None:  # RMS of w* - w_n over the first step's crops
+            xi = torch.empty((crops_per_step, 5, crop, crop), device="cuda")
+            yi = torch.empty((crops_per_step, 2, crop, crop), device="cuda")
+            rd.extract_crops(inst, corners, crop, 1.0, xi, yi)
+            scale = float(torch.sqrt(torch.mean(yi.double() ** 2)).item())
+        xi = torch.empty((crops_per_step, 5, crop, crop), device="cuda")
+        yi = torch.empty((crops_per_step, 2, crop, crop), device="cuda")
+        rd.extract_crops(inst, corners, crop, scale, xi, yi)
+        X.append(xi)
+        Y.append(yi)
+    rd.close()
+    return torch.cat(X), torch.cat(Y), scale
+
+
+def train(torch, net, X, Y, iters, batch=32, lr=1e-3, margin=4, seed=1):
+    rng = np.random.default_rng(seed)
+    losses = []
+    t0 = time.perf_counter()
+    for it in range(iters):
+        idx = torch.from_numpy(rng.integers(0, X.shape[0], batch)).cuda()
+        xb = X.index_select(0, idx).contiguous()
+        yb = Y.index_select(0, idx).contiguous()
+        want = it == 0 or it == iters - 1 or (it + 1) % 100 == 0
+        loss = net.train_step(xb, yb, lr=lr, margin=margin, want_loss=want)
+        if want:
+            losses.append((it + 1, loss))
+    torch.cuda.synchronize()
+    return losses, time.perf_counter() - t0
+
+
+def evaluate(torch, sizes, seeds, L, steps, net=None, scale=1.0, warm=0, stream=None):
+    """V-cycles per step (per species and instance) and wall time per step."""
+    rd = amrvac.RdSolver(2, sizes, L, precision="fp32", stream=stream, **GS)
+    rd.set_state(*start_state(sizes, L, seeds))
+    if warm:
+        rd.step(warm)
+    if net is not None:
+        rd.set_guess(net, scale)
+    rd.step(1)  # the guess needs one previous solution; not timed
+    torch.cuda.synchronize()
+    cyc, init = [], []
+    el = 0.0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        cyc.append(rd.step(1)[0])
+        torch.cuda.synchronize()
+        el += time.perf_counter() - t0
+        init.append(rd.last_residuals()[0])
+    u, v = rd.read_state()
+    rd.close()
+    return np.array(cyc), el / steps, (u, v), np.array(init)
