@@ -182,6 +182,33 @@ def bench_gray_scott(torch, amrvac, stream, steps=5):
     return out
 
 
+def bench_learned_guess(torch, amrvac, stream, eval_steps=6):
+    """Config 5 (2D): train the learned multigrid guess on 256^2 runs with the stiffness of the 2048^2
+    grid (seeds 0, 1), evaluate at 2048^2 on seed 10000 against the previous-step guess."""
+    from paper_2004_03275_gb300 import learned_guess as LG
+    n = 256
+    L = LG.domain_for(n)
+    t0 = time.perf_counter()
+    X, Y, scale = LG.generate(torch, [n, n], [0, 1], L, steps=24, crops_per_step=48, crop=64, warm=40)
+    net = amrvac.CnnNet(ndim=2, seed=3)
+    losses, train_s = LG.train(torch, net, X, Y, iters=1500, batch=64, lr=1e-3)
+    prep = time.perf_counter() - t0
+    c0, t0s, _, r0 = LG.evaluate(torch, [2048], [10000], 2.5, steps=eval_steps, warm=40)
+    c1, t1s, _, r1 = LG.evaluate(torch, [2048], [10000], 2.5, steps=eval_steps, warm=40, net=net, scale=scale)
+    out = {"workload": "Gray-Scott IMEX 2048^2 (seed 10000, after 40 warm-up steps), MG rtol 1e-10",
+           "training": f"{X.shape[0]} crops 64^2 from 256^2 runs (seeds 0,1, stiffness-matched domain), "
+                       f"1500 Adam steps, batch 64, {train_s:.1f}s; data+training {prep:.1f}s",
+           "loss_first_last": [losses[0][1], float(np.mean([l for _, l in losses[-5:]]))],
+           "vcycles_per_solve_previous_step_guess": float(np.mean(c0)),
+           "vcycles_per_solve_learned_guess": float(np.mean(c1)),
+           "initial_rel_residual_median_previous_step": float(np.median(r0)),
+           "initial_rel_residual_median_learned": float(np.median(r1)),
+           "ms_per_step_previous_step_guess": t0s * 1e3, "ms_per_step_learned_guess": t1s * 1e3,
+           "cnn_launches": net.kernel_launches()}
+    net.close()
+    return out
+
+
 def bench_blast(torch, amrvac, stream, steps=20, regrid_every=10):
     """Config 3: 3D blast, 4^3 base blocks of 16^3, 4 levels (effective 512^3), HLLC + Koren, SSPRK3,
     FP32 state, regrid every 10 steps.  cell-updates/s per RK stage excluding regrid time."""
@@ -393,6 +420,7 @@ def main():
     if not args.skip_extra and rank == 0:
         extra["gray_scott_batch"] = bench_gray_scott(torch, amrvac, stream)
         extra["blast3d"] = bench_blast(torch, amrvac, stream)
+        extra["learned_guess_2d"] = bench_learned_guess(torch, amrvac, stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:

@@ -212,7 +212,8 @@ typedef struct mg_handle mg_handle;
 typedef struct {
   int ndim;             /* 2 or 3 */
   int n_inst;           /* number of independent grids */
-  const int* n_cells;   /* [n_inst] cells per side (host pointer, copied) */
+  const int* n_cells;   /* [n_inst] cells per side, n_cells[i]^ndim < 2^31 (host pointer, copied);
+                           a larger instance fails with AMR_ERR_INVALID_ARG */
   const double* lambda; /* [n_inst] Helmholtz constants > 0 (host pointer, copied) */
   double L;             /* domain side */
   int nu1, nu2, max_cycles;

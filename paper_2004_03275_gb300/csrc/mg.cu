@@ -46,6 +46,7 @@ struct InstDev {
   float ih2f[kMaxLev];
   double lam;
   float lamf;
+  int ntx[kMaxLev];             // 2D sweep tiles along x on each level
   long long off0;          // offset into X / B
   long long inv_off;       // offset into the coarsest inverse matrices
 };
@@ -74,11 +75,36 @@ struct Lvl {
   real* b;
 };
 
+// cell coordinates of index t of an n^nd grid (setup keeps n^nd below 2^31, so the
+// divisions are 32-bit)
 __device__ __forceinline__ void cell_of(long long t, int n, int nd, int* c) {
-  c[0] = (int)(t % n);
-  t /= n;
-  c[1] = nd > 1 ? (int)(t % n) : 0;
-  c[2] = nd > 2 ? (int)(t / n) : 0;
+  unsigned u = (unsigned)t, un = (unsigned)n;
+  unsigned r = u / un;
+  c[0] = (int)(u - r * un);
+  if (nd > 2) {
+    unsigned z = r / un;
+    c[1] = (int)(r - z * un);
+    c[2] = (int)z;
+  } else {
+    c[1] = nd > 1 ? (int)r : 0;
+    c[2] = 0;
+  }
+}
+
+// max of a non-negative double over the block, as its bit pattern (the order of the
+// bit patterns of non-negative doubles is their numeric order), one atomic per block
+__device__ __forceinline__ void block_max_atomic(unsigned long long m, unsigned long long* dst) {
+  __shared__ unsigned long long wm[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
+    m = y > m ? y : m;
+  }
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = wm[w] > m ? wm[w] : m;
+    if (m) atomicMax(dst, m);
+  }
 }
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
@@ -129,13 +155,12 @@ __device__ __forceinline__ float lam_of<float>(const InstDev& I) { return I.lamf
 // max |B| per instance (level-0 chunks)
 __global__ void bnorm_kernel(MgState S, const Chunk* ch) {
   Chunk C = ch[blockIdx.x];
-  double m = 0.0;
+  unsigned long long m = 0ull;
   if (threadIdx.x < C.count) {
     const InstDev& I = S.inst[C.inst];
-    m = fabs(S.B[I.off0 + C.start + threadIdx.x]);
+    m = (unsigned long long)__double_as_longlong(fabs(S.B[I.off0 + C.start + threadIdx.x]));
   }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(&S.rnorm[C.inst], (unsigned long long)__double_as_longlong(m));
+  block_max_atomic(m, &S.rnorm[C.inst]);
 }
 
 __global__ void bnorm_finish_kernel(MgState S, int ninst) {
@@ -153,9 +178,10 @@ __global__ void bnorm_finish_kernel(MgState S, int ninst) {
 template <typename real>
 __global__ void residual64_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
   Chunk C = ch[blockIdx.x];
-  double m = 0.0;
+  if (!S.active[C.inst]) return;
+  unsigned long long m = 0ull;
   const InstDev& I = S.inst[C.inst];
-  if (S.active[C.inst] && threadIdx.x < C.count) {
+  if (threadIdx.x < C.count) {
     long long t = C.start + threadIdx.x;
     int n = I.n[0];
     int c[3];
@@ -166,10 +192,9 @@ __global__ void residual64_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
     double r = S.B[I.off0 + t] - (I.lam * x - lap);
     L.b[I.off[0] + t] = (real)r;
     L.x[I.off[0] + t] = real(0);
-    m = fabs(r);
+    m = (unsigned long long)__double_as_longlong(fabs(r));
   }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(&S.rnorm[C.inst], (unsigned long long)__double_as_longlong(m));
+  block_max_atomic(m, &S.rnorm[C.inst]);
 }
 
 // convergence test per instance (the paper's max-residual rule)
@@ -204,13 +229,14 @@ __global__ void smooth_kernel(MgState S, Lvl<real> L, const Chunk* ch, int colou
   if (!S.active[C.inst] || threadIdx.x >= C.count) return;
   const InstDev& I = S.inst[C.inst];
   const int l = C.lev, n = I.n[l], nd = S.ndim;
-  long long t = C.start + threadIdx.x;  // index among the cells of this colour
-  int half = n / 2;
+  unsigned t = (unsigned)(C.start + threadIdx.x);  // index among the cells of this colour
+  unsigned half = (unsigned)n / 2u;
   int c[3];
-  long long row = t / half;
-  int ii = (int)(t % half);
-  c[1] = nd > 1 ? (int)(row % n) : 0;
-  c[2] = nd > 2 ? (int)(row / n) : 0;
+  unsigned row = t / half;
+  int ii = (int)(t - row * half);
+  unsigned z = row / (unsigned)n;
+  c[1] = nd > 1 ? (int)(row - z * (unsigned)n) : 0;
+  c[2] = nd > 2 ? (int)z : 0;
   c[0] = 2 * ii + ((c[1] + c[2] + colour) & 1);
   real* x = L.x + I.off[l];
   const real* b = L.b + I.off[l];
@@ -218,6 +244,113 @@ __global__ void smooth_kernel(MgState S, Lvl<real> L, const Chunk* ch, int colou
   real diag = lam_of<real>(I) + real(2 * nd) * ih2;
   long long q = lin(c, n);
   x[q] = (b[q] + nbsum(x, c, n, nd) * ih2) / diag;
+}
+
+// One full red-black sweep of a 2D level on a TX x TY tile: x (halo 2) and b (halo 1)
+// staged in shared memory, red cells updated on the tile plus one ring, then black
+// cells on the tile, then the tile written to a second array (tiles never read what
+// another tile of the same launch writes).  Same updates, in the same order and the
+// same arithmetic, as two colour sweeps in place.
+constexpr int kSwTX = 64, kSwTY = 16;
+
+template <typename real>
+__global__ void __launch_bounds__(256)
+    sweep2d_kernel(MgState S, const real* __restrict__ xin, real* __restrict__ xout, const real* __restrict__ bl,
+                   const Chunk* ch) {
+  constexpr int PX = kSwTX + 4, PY = kSwTY + 4;
+  __shared__ real xs[PY][PX];
+  __shared__ real bs[PY - 2][PX - 2];
+  Chunk C = ch[blockIdx.x];
+  if (!S.active[C.inst]) return;
+  const InstDev& I = S.inst[C.inst];
+  const int l = C.lev, n = I.n[l];
+  const int tile = (int)C.start, ntx = I.ntx[l];
+  const int tx0 = (tile % ntx) * kSwTX, ty0 = (tile / ntx) * kSwTY;
+  const real* x = xin + I.off[l];
+  const real* b = bl + I.off[l];
+  for (int k = threadIdx.x; k < PX * PY; k += blockDim.x) {
+    int i = k % PX, j = k / PX;
+    int gi = tx0 - 2 + i, gj = ty0 - 2 + j;
+    gi = ((gi % n) + n) % n;
+    gj = ((gj % n) + n) % n;
+    xs[j][i] = x[(long long)gj * n + gi];
+    if (i >= 1 && i < PX - 1 && j >= 1 && j < PY - 1) bs[j - 1][i - 1] = b[(long long)gj * n + gi];
+  }
+  __syncthreads();
+  const real ih2 = ih2_of<real>(I, l);
+  const real diag = lam_of<real>(I) + real(2 * 2) * ih2;
+  // red (colour 0: even i+j in global coordinates, n even) on rows -1..TY, cols -1..TX
+  constexpr int RW = (kSwTX + 2) / 2;  // colour cells per row of the ring region
+  for (int k = threadIdx.x; k < (kSwTY + 2) * RW; k += blockDim.x) {
+    int jr = k / RW - 1, kk = k % RW;
+    int i0 = -1 + ((tx0 + ty0 + jr + 1) & 1);  // first ring column of colour 0 in this row
+    int ir = i0 + 2 * kk;
+    if (ir > kSwTX) continue;
+    int si = ir + 2, sj = jr + 2;
+    xs[sj][si] = (bs[sj - 1][si - 1] + (xs[sj][si - 1] + xs[sj][si + 1] + xs[sj - 1][si] + xs[sj + 1][si]) * ih2) / diag;
+  }
+  __syncthreads();
+  constexpr int BW = kSwTX / 2;
+  for (int k = threadIdx.x; k < kSwTY * BW; k += blockDim.x) {
+    int jb = k / BW, kk = k % BW;
+    int i0 = (tx0 + ty0 + jb + 1) & 1;  // first tile column of colour 1 in this row
+    int ib = i0 + 2 * kk;
+    int si = ib + 2, sj = jb + 2;
+    xs[sj][si] = (bs[sj - 1][si - 1] + (xs[sj][si - 1] + xs[sj][si + 1] + xs[sj - 1][si] + xs[sj + 1][si]) * ih2) / diag;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < kSwTX * kSwTY; k += blockDim.x) {
+    int i = k % kSwTX, j = k / kSwTX;
+    int gi = tx0 + i, gj = ty0 + j;
+    if (gi < n && gj < n) xout[I.off[l] + (long long)gj * n + gi] = xs[j + 2][i + 2];
+  }
+}
+
+// copy of one 2D level tile (after an odd number of sweeps)
+template <typename real>
+__global__ void copy2d_kernel(MgState S, const real* __restrict__ xin, real* __restrict__ xout, const Chunk* ch) {
+  Chunk C = ch[blockIdx.x];
+  if (!S.active[C.inst]) return;
+  const InstDev& I = S.inst[C.inst];
+  const int l = C.lev, n = I.n[l], ntx = I.ntx[l];
+  const int tx0 = ((int)C.start % ntx) * kSwTX, ty0 = ((int)C.start / ntx) * kSwTY;
+  for (int k = threadIdx.x; k < kSwTX * kSwTY; k += blockDim.x) {
+    int gi = tx0 + k % kSwTX, gj = ty0 + k / kSwTX;
+    if (gi < n && gj < n) xout[I.off[l] + (long long)gj * n + gi] = xin[I.off[l] + (long long)gj * n + gi];
+  }
+}
+
+// 2D prolongation, one thread per coarse cell writing its four fine children
+template <typename real>
+__global__ void prolong2d_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
+  Chunk C = ch[blockIdx.x];
+  if (!S.active[C.inst] || threadIdx.x >= C.count) return;
+  const InstDev& I = S.inst[C.inst];
+  const int l = C.lev;
+  const int nf = I.n[l], nc = I.n[l + 1];
+  unsigned t = (unsigned)(C.start + threadIdx.x);  // coarse cell
+  int cj = (int)(t / (unsigned)nc), ci = (int)(t - (unsigned)cj * (unsigned)nc);
+  const real* ec = L.x + I.off[l + 1];
+  real v[3][3];
+#pragma unroll
+  for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+    for (int di = -1; di <= 1; ++di) v[dj + 1][di + 1] = ec[(long long)wrapi(cj + dj, nc) * nc + wrapi(ci + di, nc)];
+  real* xf = L.x + I.off[l];
+#pragma unroll
+  for (int b2 = 0; b2 < 2; ++b2)
+#pragma unroll
+    for (int a2 = 0; a2 < 2; ++a2) {
+      int sx = a2 ? 1 : -1, sy = b2 ? 1 : -1;
+      // corners in the order (x, y) = (0,0), (1,0), (0,1), (1,1), weights 9/16, 3/16, 3/16, 1/16
+      real acc = real(0);
+      acc = acc + real(0.5625) * v[1][1];
+      acc = acc + real(0.1875) * v[1][1 + sx];
+      acc = acc + real(0.1875) * v[1 + sy][1];
+      acc = acc + real(0.0625) * v[1 + sy][1 + sx];
+      long long q = (long long)(2 * cj + b2) * nf + 2 * ci + a2;
+      xf[q] = xf[q] + acc;
+    }
 }
 
 // residual of level l restricted to level l+1 (mean of the 2^ndim children), x_{l+1} = 0
@@ -528,11 +661,12 @@ struct Mg {
   long long n0 = 0, nlevtot = 0;
   // chunk lists: level 0 cells; per depth: colour cells, coarse cells, fine cells
   std::vector<Chunk> ch0;
-  std::vector<std::vector<Chunk>> ch_half, ch_coarse, ch_fine;
+  std::vector<std::vector<Chunk>> ch_half, ch_coarse, ch_fine, ch_tile;
   std::vector<int> coarse_inst, coarse_row0;
+  DevBuf d_yl;  // 2D: second iterate array for the tiled sweeps
   DevBuf d_inst, d_X, d_B, d_xl, d_bl, d_rnorm, d_bnorm, d_lastres, d_initres, d_active, d_cycles, d_failed, d_any, d_inv;
   DevBuf d_ch0, d_chall, d_cinst, d_crow0;
-  std::vector<size_t> off_half, off_coarse, off_fine;
+  std::vector<size_t> off_half, off_coarse, off_fine, off_tile;
   int* h_any = nullptr;
   cudaGraphExec_t vgraph = nullptr;
   long long launches = 0;
@@ -597,6 +731,7 @@ struct Mg {
     for (int i = 0; i < n_inst; ++i) {
       int n = n_cells[i];
       if (n < 1 || !(lambda[i] > 0)) return fail(AMR_ERR_INVALID_ARG, "instance size or lambda");
+      if (std::pow((double)n, ndim) >= 2147483648.0) return fail(AMR_ERR_INVALID_ARG, "instance above 2^31 cells");
       InstDev& I = insts[i];
       std::memset(&I, 0, sizeof(I));
       I.lam = lambda[i];
@@ -616,6 +751,7 @@ struct Mg {
         double h = L / m;
         I.ih2[l] = 1.0 / (h * h);
         I.ih2f[l] = (float)I.ih2[l];
+        I.ntx[l] = (m + kSwTX - 1) / kSwTX;
         ++l;
         if ((m & 1) || m <= coarse_max) break;
         m /= 2;
@@ -642,6 +778,7 @@ struct Mg {
     ch_half.assign(maxdepth, {});
     ch_coarse.assign(maxdepth, {});
     ch_fine.assign(maxdepth, {});
+    ch_tile.assign(maxdepth, {});
     coarse_inst.clear();
     coarse_row0.clear();
     for (int i = 0; i < n_inst; ++i) {
@@ -655,6 +792,10 @@ struct Mg {
         add_chunks(ch_half[l], i, l, cf / 2);
         add_chunks(ch_coarse[l], i, l, cc);
         add_chunks(ch_fine[l], i, l, cf);
+        if (nd == 2) {
+          int nt = ((I.n[l] + kSwTX - 1) / kSwTX) * ((I.n[l] + kSwTY - 1) / kSwTY);
+          for (int k = 0; k < nt; ++k) ch_tile[l].push_back(Chunk{i, l, k, 1});
+        }
       }
       long long m = 1;
       for (int d = 0; d < nd; ++d) m *= I.n[I.nlev - 1];
@@ -669,6 +810,7 @@ struct Mg {
     if ((rc = cuda(d_inst.alloc(insts.size() * sizeof(InstDev)), "alloc")) ||
         (rc = cuda(d_X.alloc(n0 * 8), "alloc X")) || (rc = cuda(d_B.alloc(n0 * 8), "alloc B")) ||
         (rc = cuda(d_xl.alloc(nlevtot * wb), "alloc levels")) || (rc = cuda(d_bl.alloc(nlevtot * wb), "alloc levels")) ||
+        (nd == 2 && (rc = cuda(d_yl.alloc(nlevtot * wb), "alloc levels"))) ||
         (rc = cuda(d_rnorm.alloc(n_inst * 8), "alloc")) || (rc = cuda(d_bnorm.alloc(n_inst * 8), "alloc")) ||
         (rc = cuda(d_lastres.alloc(n_inst * 8), "alloc")) || (rc = cuda(d_initres.alloc(n_inst * 8), "alloc")) ||
         (rc = cuda(d_active.alloc(n_inst * 4), "alloc")) ||
@@ -684,7 +826,10 @@ struct Mg {
     off_half.assign(maxdepth, 0);
     off_coarse.assign(maxdepth, 0);
     off_fine.assign(maxdepth, 0);
+    off_tile.assign(maxdepth, 0);
     for (int l = 0; l < maxdepth; ++l) {
+      off_tile[l] = all.size();
+      all.insert(all.end(), ch_tile[l].begin(), ch_tile[l].end());
       off_half[l] = all.size();
       all.insert(all.end(), ch_half[l].begin(), ch_half[l].end());
       off_coarse[l] = all.size();
@@ -714,16 +859,32 @@ struct Mg {
     MgState S = state();
     Lvl<real> Lv = lvl<real>();
     const Chunk* all = d_chall.as<Chunk>();
-    auto launch_half = [&](int l, int colour) {
+    real* Y = d_yl.as<real>();
+    auto smooth = [&](int l, int sweeps) {  // `sweeps` red-black sweeps of depth l
+      if (nd == 2) {
+        if (ch_tile[l].empty()) return;
+        unsigned nb = (unsigned)ch_tile[l].size();
+        const Chunk* tl = all + off_tile[l];
+        for (int s = 0; s < sweeps; ++s) {
+          bool even = (s & 1) == 0;
+          sweep2d_kernel<real><<<nb, 256, 0, stream>>>(S, even ? Lv.x : Y, even ? Y : Lv.x, Lv.b, tl);
+          ++launches;
+        }
+        if (sweeps & 1) {
+          copy2d_kernel<real><<<nb, 256, 0, stream>>>(S, Y, Lv.x, tl);
+          ++launches;
+        }
+        return;
+      }
       if (ch_half[l].empty()) return;
-      smooth_kernel<real><<<(unsigned)ch_half[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_half[l], colour);
-      ++launches;
+      for (int s = 0; s < sweeps; ++s)
+        for (int colour = 0; colour < 2; ++colour) {
+          smooth_kernel<real><<<(unsigned)ch_half[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_half[l], colour);
+          ++launches;
+        }
     };
     for (int l = 0; l + 1 < maxdepth; ++l) {
-      for (int s = 0; s < nu1; ++s) {
-        launch_half(l, 0);
-        launch_half(l, 1);
-      }
+      smooth(l, nu1);
       if (!ch_coarse[l].empty()) {
         resrestrict_kernel<real><<<(unsigned)ch_coarse[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
         ++launches;
@@ -733,14 +894,14 @@ struct Mg {
                                                                           (int)coarse_inst.size());
     ++launches;
     for (int l = maxdepth - 2; l >= 0; --l) {
-      if (!ch_fine[l].empty()) {
+      if (nd == 2 && !ch_coarse[l].empty()) {
+        prolong2d_kernel<real><<<(unsigned)ch_coarse[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
+        ++launches;
+      } else if (nd != 2 && !ch_fine[l].empty()) {
         prolong_kernel<real><<<(unsigned)ch_fine[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_fine[l]);
         ++launches;
       }
-      for (int s = 0; s < nu2; ++s) {
-        launch_half(l, 0);
-        launch_half(l, 1);
-      }
+      smooth(l, nu2);
     }
     correct64_kernel<real><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
     ++launches;
@@ -784,7 +945,7 @@ struct Mg {
       if ((rc = cuda(cudaGraphLaunch(vgraph, stream), "graph launch"))) return rc;
       launches += vcycle_kernels;
     }
-    return AMR_OK;
+    return cuda(cudaGetLastError(), "solve");
   }
 
   int solve_device_any() { return precision == AMR_FP64 ? solve_device<double>() : solve_device<float>(); }

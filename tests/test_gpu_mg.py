@@ -53,6 +53,30 @@ def test_fp64_matches_oracle(ndim, sizes):
         assert np.max(np.abs(xs[i] - xo)) <= 1e-12 * np.max(np.abs(xo)), i
 
 
+@pytest.mark.parametrize("nu1,nu2", [(2, 2), (1, 3), (0, 1)])
+def test_fp64_tiled_sweeps_ragged_tiles(nu1, nu2):
+    """2D sides above one 64 x 16 sweep tile and not multiples of it (96, 80, 144:
+    coarsest 6, 5, 9), with even and odd sweep counts (an odd count ends in the
+    second iterate array and is copied back)."""
+    sizes, L = [96, 80, 144], 2.1
+    lam, bs = batch(sizes, 2, 11)
+    s = amrvac.MgSolver(2, sizes, lam, L, nu1=nu1, nu2=nu2, precision="fp64")
+    x = np.zeros(s.n)
+    cyc, rr = s.solve(pack(bs), x)
+    xs = unpack(x, sizes, 2)
+    for i, n in enumerate(sizes):
+        xo, co, ro = O.mg_solve(bs[i], np.zeros_like(bs[i]), L, lam[i], nu1=nu1, nu2=nu2)
+        assert rr[i] <= 1e-10
+        assert abs(int(cyc[i]) - co) <= 1, (i, cyc[i], co)
+        assert np.max(np.abs(xs[i] - xo)) <= 1e-12 * np.max(np.abs(xo)), i
+
+
+def test_instance_size_limit():
+    with pytest.raises(amrvac.AmrError) as ei:
+        amrvac.MgSolver(3, [2048], [1.0], 1.0)
+    assert ei.value.code == -1
+
+
 @pytest.mark.parametrize("ndim,sizes", [(2, SIZES_2D), (3, [16, 12, 24])])
 def test_fp32_defect_correction_within_bound(ndim, sizes):
     L, rtol = 2.5, 1e-10
