@@ -130,9 +130,9 @@ def time_steps(torch, solver, stream, steps):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per stage launch (mean of the three stages of a
-# step) from the ncu capture summarised in profiles/stage2d_f32_kh2048.md; valid for the
-# kernel as captured there.
-STAGE2D_F32_TRAFFIC = 143.0e6
+# step) from the ncu capture of the stage kernel summarised under profiles/; None until the
+# current kernel has been captured.
+STAGE2D_F32_TRAFFIC = None
 
 
 def stage_roofline(solver, nsteps, nv, wbytes, ncells, hbm_gbs, traffic=None):
@@ -149,7 +149,7 @@ def stage_roofline(solver, nsteps, nv, wbytes, ncells, hbm_gbs, traffic=None):
     achieved = bytes_total / (ms_total * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_gbs, "unit": "GB/s",
             "frac": round(achieved / hbm_gbs, 4), "traffic": traffic,
-            "kernel": "stage2d_f32_kernel<16,HLLC,VANLEER>", "launches_timed": nlaunch,
+            "kernel": "stage2d_march_kernel<HLLC,VANLEER>", "launches_timed": nlaunch,
             "avg_launch_us": round(ms_total / nlaunch * 1e3, 2),
             "bytes_per_launch_avg": int(bytes_total / nlaunch), "frac_of_8TBs_nameplate": round(achieved / 8000, 4)}
 

@@ -5,6 +5,7 @@
 
 #include "euler_ops.h"
 #include "stage2d_f32.cuh"
+#include "stage2d_march.cuh"
 
 namespace amrgpu {
 
@@ -40,6 +41,7 @@ int& stage2d_f32_grid() {
 
 template <int B, int FLUX, int LIM>
 cudaError_t stage2d_f32_prepare_one() {
+  if constexpr (B == 16) return cudaSuccess;  // one warp per leaf, no persistent grid
   int dev, sms, per;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -60,6 +62,11 @@ cudaError_t stage2d_f32_prepare(int lim) {
 
 template <int B, int FLUX, int LIM>
 void stage2d_f32_go(const StageArgs<float>& a, const Geometry& G, cudaStream_t s) {
+  if constexpr (B == 16) {
+    int grid = (a.nleaves + kMarchWarps - 1) / kMarchWarps;
+    stage2d_march_kernel<FLUX, LIM><<<grid, 32 * kMarchWarps, 0, s>>>(a, G);
+    return;
+  }
   constexpr int LPB = 256 / (B * B);
   int nslots = (a.nleaves + LPB - 1) / LPB;
   int cap = stage2d_f32_grid<B, FLUX, LIM>();

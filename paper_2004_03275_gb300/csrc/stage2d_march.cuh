@@ -1,0 +1,316 @@
+// Float32 2D stage kernel for 16^2 leaves: one warp per leaf, directional marches.
+//
+// Same method as the other stage kernels (limited MUSCL on primitive variables,
+// HLL/HLLC/TVDLF flux, SSPRK combination; Sec. 1.1, 1.2, 2.3-2.4), organised so
+// that the stencil work of each direction stays in registers:
+//   1. the warp loads the leaf (coalesced 16-byte loads) and its two-cell face
+//      ghosts, converts every cell to primitive values once and stores them as
+//      float4 in a shared tile T[20][21] (rows and columns -2..17, odd row stride);
+//   2. x march: lane (row j, half h) walks columns h*8-2 .. h*8+9 of row j keeping
+//      a three-cell window; at each step it forms the limited slope of one cell,
+//      its two face values, the flux through one face and, one step later, the
+//      flux difference of a cell, which goes to a shared array E[16][17];
+//   3. y march: lane (column i, half h) walks rows h*8-2 .. h*8+9 of column i the
+//      same way and finishes each cell: flux differences of both directions, the
+//      SSPRK combination with U^(s) and U^n (coalesced scalar loads), the store,
+//      and on the last stage the signal rate and the conserved totals.
+// Every lane does identical work in every phase (the leaf-boundary faces are the
+// first or last faces of a march), there is no block-wide barrier inside a leaf,
+// and the two access patterns of T and E hit distinct banks (strides 21 and 17).
+// Per cell: 1.5 primitive conversions (ghosts included), 1.25 slopes and 1.125
+// fluxes per direction.
+//
+// Conserved totals on the last stage: every thread accumulates its cells in
+// float-float (TwoSum), scaled by 4^-(level-1) so that all levels share one unit
+// (dV halves exactly per level and per dimension), the CTA adds its threads in a
+// fixed order into one float64 partial, and the two-level last-CTA finish sums
+// the partials in CTA order.  The result is deterministic for a given tree.
+#pragma once
+#include "stage2d_f32.cuh"
+
+namespace amrgpu {
+
+constexpr int kMarchWarps = 4;  // warps (= leaves) per CTA
+
+struct MarchSmem {
+  float4 T[20][21];  // primitive values, T[r+2][c+2], r, c in -2..17 (corners unused)
+  float4 E[16][17];  // x flux differences of the interior cells, E[j][i]
+};
+
+namespace march {
+
+__device__ __forceinline__ float4 prim(float r, float mx, float my, float e, float gm1) {
+  float ir = f32::rcp(r);
+  float vx = mx * ir, vy = my * ir;
+  return make_float4(r, vx, vy, gm1 * (e - 0.5f * (mx * vx + my * vy)));
+}
+
+// lower (toward -d) and upper (toward +d) face values of the cell w0 between wm and wp
+template <int LIM>
+__device__ __forceinline__ void faces(const float4& wm, const float4& w0, const float4& wp, float4& lo, float4& hi) {
+  float hm, hp;
+  f32::half_slopes<LIM>(w0.x - wm.x, wp.x - w0.x, hm, hp);
+  lo.x = w0.x - hm;
+  hi.x = w0.x + hp;
+  f32::half_slopes<LIM>(w0.y - wm.y, wp.y - w0.y, hm, hp);
+  lo.y = w0.y - hm;
+  hi.y = w0.y + hp;
+  f32::half_slopes<LIM>(w0.z - wm.z, wp.z - w0.z, hm, hp);
+  lo.z = w0.z - hm;
+  hi.z = w0.z + hp;
+  f32::half_slopes<LIM>(w0.w - wm.w, wp.w - w0.w, hm, hp);
+  lo.w = w0.w - hm;
+  hi.w = w0.w + hp;
+}
+
+// flux through the face between cells a (left) and b (right) from face states L, R;
+// first order (the cell values) if a reconstructed density or pressure is not
+// positive.  Result in variable order (rho, m_x, m_y, E).
+template <int FLUX, bool ISY>
+__device__ __forceinline__ void flux(float4 L, float4 R, const float4& a, const float4& b, float gam, float igm1,
+                                     float* F) {
+  if (!(L.x > 0.f) || !(R.x > 0.f) || !(L.w > 0.f) || !(R.w > 0.f)) {
+    L = a;
+    R = b;
+  }
+  float G[4];
+  if (ISY) {
+    f32::flux2<FLUX>(L.x, L.z, L.y, L.w, R.x, R.z, R.y, R.w, gam, igm1, G);
+    F[0] = G[0];
+    F[1] = G[2];
+    F[2] = G[1];
+    F[3] = G[3];
+  } else {
+    f32::flux2<FLUX>(L.x, L.y, L.z, L.w, R.x, R.y, R.z, R.w, gam, igm1, G);
+    F[0] = G[0];
+    F[1] = G[1];
+    F[2] = G[2];
+    F[3] = G[3];
+  }
+}
+
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
+  float s = hi + x, bb = s - hi;
+  lo += (hi - (s - bb)) + (x - bb);
+  hi = s;
+}
+
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float h2, float l2) {
+  float s = hi + h2, bb = s - hi;
+  float e = (hi - (s - bb)) + (h2 - bb);
+  lo = lo + l2 + e;
+  hi = s;
+}
+
+}  // namespace march
+
+template <int FLUX, int LIM>
+__global__ void __launch_bounds__(32 * kMarchWarps, 5) stage2d_march_kernel(StageArgs<float> a, Geometry G) {
+  constexpr int B = 16, NC = B * B, NV = 4;
+  __shared__ MarchSmem S[kMarchWarps];
+  __shared__ float red[kMarchWarps][2 * NV + 1];
+  __shared__ int sbad;
+  if (threadIdx.x == 0) sbad = 0;  // before the barrier inside cta_stage_dt
+  float dt;
+  const double dtd = cta_stage_dt(a.ctl, &dt);
+  if (!(dtd > 0.0)) return;
+  const float gam = G.gammaf, gm1 = gam - 1.f, igm1 = 1.f / gm1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int leaf = blockIdx.x * kMarchWarps + warp;
+  const bool active = leaf < a.nleaves;
+  const int lo16 = lane & 15, h = lane >> 4;
+  MarchSmem& M = S[warp];
+
+  float rate = 0.f;
+  int bad = 0;
+  float th[NV] = {0.f, 0.f, 0.f, 0.f}, tl[NV] = {0.f, 0.f, 0.f, 0.f};
+
+  if (active) {
+    const float* Ul = a.Us + (size_t)leaf * NV * NC;
+    // ---- 1. leaf cells (row lo16, columns h*8..h*8+7) and face ghosts -> primitive tile
+    {
+      float4 u[NV][2];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float4* p = reinterpret_cast<const float4*>(Ul + v * NC + lo16 * B + h * 8);
+        u[v][0] = __ldg(p);
+        u[v][1] = __ldg(p + 1);
+      }
+      float4* trow = &M.T[lo16 + 2][h * 8 + 2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        trow[4 * q + 0] = march::prim(u[0][q].x, u[1][q].x, u[2][q].x, u[3][q].x, gm1);
+        trow[4 * q + 1] = march::prim(u[0][q].y, u[1][q].y, u[2][q].y, u[3][q].y, gm1);
+        trow[4 * q + 2] = march::prim(u[0][q].z, u[1][q].z, u[2][q].z, u[3][q].z, gm1);
+        trow[4 * q + 3] = march::prim(u[0][q].w, u[1][q].w, u[2][q].w, u[3][q].w, gm1);
+      }
+      // ghosts: face f (x-, x+, y-, y+), layer m = h, tangential index t = lo16
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const int code = __ldg(&a.nb[leaf * 4 + f]);
+        const int d = f >> 1, side = f & 1, m = h, t = lo16;
+        const float* src;
+        int stride;
+        if (code >= -1) {
+          int n = code >= 0 ? (side == 0 ? B - 1 - m : m) : (side == 0 ? 0 : B - 1);
+          int cell = d == 0 ? n + B * t : t + B * n;
+          src = a.Us + (size_t)(code >= 0 ? code : leaf) * NV * NC + cell;
+          stride = NC;
+        } else {
+          src = a.slabs + ((size_t)(-2 - code) * NV * 2 + m) * B + t;
+          stride = 2 * B;
+        }
+        float4 w = march::prim(src[0], src[stride], src[2 * stride], src[3 * stride], gm1);
+        int r, c;
+        if (d == 0) {
+          r = t;
+          c = side == 0 ? -1 - m : B + m;
+        } else {
+          c = t;
+          r = side == 0 ? -1 - m : B + m;
+        }
+        M.T[r + 2][c + 2] = w;
+      }
+    }
+    __syncwarp();
+
+    const int lev = __ldg(&a.level[leaf]);
+    const float idx = G.idxf[lev][0], idy = G.idxf[lev][1];
+    const int c0 = h * 8;
+
+    // ---- 2. x march along row j = lo16: flux differences of columns c0..c0+7 -> E
+    {
+      const int j = lo16;
+      const float4* row = &M.T[j + 2][2];  // row[c] = W(c, j)
+      float4 wm = row[c0 - 2], w0 = row[c0 - 1], wp = row[c0];
+      float4 lo, hiPrev;
+      march::faces<LIM>(wm, w0, wp, lo, hiPrev);  // cell c0-1: its upper face value
+      wm = w0;
+      w0 = wp;
+      float Fp[NV];
+#pragma unroll
+      for (int k = 0; k <= 8; ++k) {
+        const int cc = c0 + k;  // cell whose slope is formed; face cc-1/2
+        wp = row[cc + 1];
+        float4 hi;
+        march::faces<LIM>(wm, w0, wp, lo, hi);
+        float F[NV];
+        march::flux<FLUX, false>(hiPrev, lo, wm, w0, gam, igm1, F);
+        if (a.has_ffx && ((h == 0 && k == 0) || (h == 1 && k == 8))) {
+          int slot = a.ffx[leaf * 4 + h];
+          if (slot >= 0)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) a.fflux[((size_t)slot * NV + v) * B + j] = F[v];
+        }
+        if (k > 0) M.E[j][cc - 1] = make_float4(F[0] - Fp[0], F[1] - Fp[1], F[2] - Fp[2], F[3] - Fp[3]);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Fp[v] = F[v];
+        hiPrev = hi;
+        wm = w0;
+        w0 = wp;
+      }
+    }
+    __syncwarp();
+
+    // ---- 3. y march along column i = lo16, then the cell update of rows c0..c0+7
+    {
+      const int i = lo16;
+      const float4* col = &M.T[2][i + 2];  // col[r * 21] = W(i, r)
+      constexpr int RS = 21;
+      float4 wm = col[(c0 - 2) * RS], w0 = col[(c0 - 1) * RS], wp = col[c0 * RS];
+      float4 lo, hiPrev;
+      march::faces<LIM>(wm, w0, wp, lo, hiPrev);
+      wm = w0;
+      w0 = wp;
+      float Fp[NV];
+      const float* U0l = a.U0 + (size_t)leaf * NV * NC;
+      float* Ol = a.out + (size_t)leaf * NV * NC;
+      const float vscale = __int_as_float((127 - 2 * (lev - 1)) << 23);  // 4^-(lev-1), exact
+#pragma unroll
+      for (int k = 0; k <= 8; ++k) {
+        const int rr = c0 + k;  // cell whose slope is formed; face rr-1/2
+        wp = col[(rr + 1) * RS];
+        float4 hi;
+        march::faces<LIM>(wm, w0, wp, lo, hi);
+        float F[NV];
+        march::flux<FLUX, true>(hiPrev, lo, wm, w0, gam, igm1, F);
+        if (a.has_ffx && ((h == 0 && k == 0) || (h == 1 && k == 8))) {
+          int slot = a.ffx[leaf * 4 + 2 + h];
+          if (slot >= 0)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) a.fflux[((size_t)slot * NV + v) * B + i] = F[v];
+        }
+        if (k > 0) {
+          const int r = rr - 1, q = r * B + i;
+          const float4 e = M.E[r][i];
+          const float ex[NV] = {e.x, e.y, e.z, e.w};
+          float Un[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            float div = ex[v] * idx + (F[v] - Fp[v]) * idy;
+            float tmp = __ldg(&Ul[v * NC + q]) - dt * div;
+            Un[v] = a.stage1 ? tmp : a.alpha * __ldg(&U0l[v * NC + q]) + a.beta * tmp;
+            Ol[v * NC + q] = Un[v];
+          }
+          if (a.fuse_reduce) {
+            float ir = f32::rcp(Un[0]);
+            float vx = Un[1] * ir, vy = Un[2] * ir;
+            float p = gm1 * (Un[3] - 0.5f * (Un[1] * vx + Un[2] * vy));
+            if (!(Un[0] > 0.f) || !(p > 0.f)) bad = 1;
+            float cs = sqrtf(gam * p * ir);
+            rate = fmaxf(rate, (fabsf(vx) + cs) * idx + (fabsf(vy) + cs) * idy);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) march::two_sum_add(th[v], tl[v], Un[v] * vscale);
+          }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Fp[v] = F[v];
+        hiPrev = hi;
+        wm = w0;
+        w0 = wp;
+      }
+    }
+  }
+  if (!a.fuse_reduce) return;
+
+  // ---- last stage: CTA max rate, CTA totals (fixed order), two-level finish
+  for (int o = 16; o > 0; o >>= 1) {
+    rate = fmaxf(rate, __shfl_xor_sync(0xffffffffu, rate, o));
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      float h2 = __shfl_xor_sync(0xffffffffu, th[v], o), l2 = __shfl_xor_sync(0xffffffffu, tl[v], o);
+      march::ff_add(th[v], tl[v], h2, l2);
+    }
+  }
+  if (lane == 0) {
+    red[warp][2 * NV] = rate;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      red[warp][v] = th[v];
+      red[warp][NV + v] = tl[v];
+    }
+  }
+  if (bad) sbad = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float mm = red[0][2 * NV];
+    float hh[NV], ll[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      hh[v] = red[0][v];
+      ll[v] = red[0][NV + v];
+    }
+    for (int w = 1; w < kMarchWarps; ++w) {
+      mm = fmaxf(mm, red[w][2 * NV]);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) march::ff_add(hh[v], ll[v], red[w][v], red[w][NV + v]);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) a.partials[(size_t)blockIdx.x * NV + v] = ((double)hh[v] + (double)ll[v]) * G.dV[1];
+    atomicMax(&a.ctl->smax_bits, MaxKey<float>::enc(mm));
+    if (sbad) atomicOr(&a.ctl->status, 1);
+  }
+  last_cta_finish<float, NV, 32 * kMarchWarps>(a.ctl, a.partials, a.gpart, a.gcount, (int)gridDim.x, 1, true, dtd);
+}
+
+}  // namespace amrgpu
