@@ -272,14 +272,16 @@ __device__ __forceinline__ void block_sum_fixed(double* acc) {
 // totals, dt_cfl = cfl/smax and, when `advance`, t += dt.  Every thread of every
 // CTA calls this after its CTA's partials and atomicMax are issued.  No CTA
 // waits on another; counters are reset by the CTA that consumed them.
+// fence_all = false: the threads that wrote the CTA's partials have already
+// issued their fence, so the others skip it.
 template <typename real, int NV, int NTHREADS>
 __device__ void last_cta_finish(DevCtl* ctl, const double* partials, double* gpart, unsigned* gcount,
-                                int nleaves, int lpb, bool advance, double dt) {
+                                int nleaves, int lpb, bool advance, double dt, bool fence_all = true) {
   __shared__ bool flag;
   const int g = blockIdx.x / kGroupCTAs;
   const int ngroups = (gridDim.x + kGroupCTAs - 1) / kGroupCTAs;
   const int gsize = min(kGroupCTAs, (int)gridDim.x - g * kGroupCTAs);
-  __threadfence();
+  if (fence_all) __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) flag = atomicAdd(&gcount[g], 1u) == (unsigned)(gsize - 1);
   __syncthreads();

@@ -22,9 +22,10 @@
 //
 // Conserved totals on the last stage: every thread accumulates its cells in
 // float-float (TwoSum), scaled by 4^-(level-1) so that all levels share one unit
-// (dV halves exactly per level and per dimension), the CTA adds its threads in a
-// fixed order into one float64 partial, and the two-level last-CTA finish sums
-// the partials in CTA order.  The result is deterministic for a given tree.
+// (dV halves exactly per level and per dimension); one warp adds the CTA's
+// threads in a fixed order into one float64 partial per variable, and the
+// two-level last-CTA finish sums the partials in CTA order.  The result is
+// deterministic for a given tree.
 #pragma once
 #include "stage2d_f32.cuh"
 
@@ -105,37 +106,64 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float h2, float l2)
 }  // namespace march
 
 template <int FLUX, int LIM>
-__global__ void __launch_bounds__(32 * kMarchWarps, 5) stage2d_march_kernel(StageArgs<float> a, Geometry G) {
+__global__ void __launch_bounds__(32 * kMarchWarps, 4) stage2d_march_kernel(StageArgs<float> a, Geometry G) {
   constexpr int B = 16, NC = B * B, NV = 4;
   __shared__ MarchSmem S[kMarchWarps];
-  __shared__ float red[kMarchWarps][2 * NV + 1];
+  __shared__ float wrate[kMarchWarps];
   __shared__ int sbad;
-  if (threadIdx.x == 0) sbad = 0;  // before the barrier inside cta_stage_dt
-  float dt;
-  const double dtd = cta_stage_dt(a.ctl, &dt);
-  if (!(dtd > 0.0)) return;
-  const float gam = G.gammaf, gm1 = gam - 1.f, igm1 = 1.f / gm1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int leaf = blockIdx.x * kMarchWarps + warp;
   const bool active = leaf < a.nleaves;
   const int lo16 = lane & 15, h = lane >> 4;
   MarchSmem& M = S[warp];
+  if (threadIdx.x == 0) sbad = 0;  // before the barrier inside cta_stage_dt
+
+  // ---- 1a. every global load of the leaf is issued before the CTA's dt barrier:
+  // the cells of row lo16, columns h*8..h*8+7, and one ghost cell per face
+  // (layer m = h, tangential index t = lo16; faces x-, x+, y-, y+)
+  const float* Ul = a.Us + (size_t)leaf * NV * NC;
+  float4 u[NV][2];
+  float gu[4][NV];
+  int lev = 1;
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const float4* p = reinterpret_cast<const float4*>(Ul + v * NC + lo16 * B + h * 8);
+      u[v][0] = __ldg(p);
+      u[v][1] = __ldg(p + 1);
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const int code = __ldg(&a.nb[leaf * 4 + f]);
+      const int d = f >> 1, side = f & 1, m = h, t = lo16;
+      const float* src;
+      int stride;
+      if (code >= -1) {
+        int n = code >= 0 ? (side == 0 ? B - 1 - m : m) : (side == 0 ? 0 : B - 1);
+        int cell = d == 0 ? n + B * t : t + B * n;
+        src = a.Us + (size_t)(code >= 0 ? code : leaf) * NV * NC + cell;
+        stride = NC;
+      } else {
+        src = a.slabs + ((size_t)(-2 - code) * NV * 2 + m) * B + t;
+        stride = 2 * B;
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) gu[f][v] = __ldg(&src[v * stride]);
+    }
+    lev = __ldg(&a.level[leaf]);
+  }
+  float dt;
+  const double dtd = cta_stage_dt(a.ctl, &dt);
+  if (!(dt > 0.f)) return;  // same decision as dtd > 0 (a positive dt never rounds to 0 here)
+  const float gam = G.gammaf, gm1 = gam - 1.f, igm1 = 1.f / gm1;
 
   float rate = 0.f;
   int bad = 0;
   float th[NV] = {0.f, 0.f, 0.f, 0.f}, tl[NV] = {0.f, 0.f, 0.f, 0.f};
 
   if (active) {
-    const float* Ul = a.Us + (size_t)leaf * NV * NC;
-    // ---- 1. leaf cells (row lo16, columns h*8..h*8+7) and face ghosts -> primitive tile
+    // ---- 1b. primitive tile
     {
-      float4 u[NV][2];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const float4* p = reinterpret_cast<const float4*>(Ul + v * NC + lo16 * B + h * 8);
-        u[v][0] = __ldg(p);
-        u[v][1] = __ldg(p + 1);
-      }
       float4* trow = &M.T[lo16 + 2][h * 8 + 2];
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
@@ -144,23 +172,9 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 5) stage2d_march_kernel(Stag
         trow[4 * q + 2] = march::prim(u[0][q].z, u[1][q].z, u[2][q].z, u[3][q].z, gm1);
         trow[4 * q + 3] = march::prim(u[0][q].w, u[1][q].w, u[2][q].w, u[3][q].w, gm1);
       }
-      // ghosts: face f (x-, x+, y-, y+), layer m = h, tangential index t = lo16
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
-        const int code = __ldg(&a.nb[leaf * 4 + f]);
         const int d = f >> 1, side = f & 1, m = h, t = lo16;
-        const float* src;
-        int stride;
-        if (code >= -1) {
-          int n = code >= 0 ? (side == 0 ? B - 1 - m : m) : (side == 0 ? 0 : B - 1);
-          int cell = d == 0 ? n + B * t : t + B * n;
-          src = a.Us + (size_t)(code >= 0 ? code : leaf) * NV * NC + cell;
-          stride = NC;
-        } else {
-          src = a.slabs + ((size_t)(-2 - code) * NV * 2 + m) * B + t;
-          stride = 2 * B;
-        }
-        float4 w = march::prim(src[0], src[stride], src[2 * stride], src[3 * stride], gm1);
         int r, c;
         if (d == 0) {
           r = t;
@@ -169,12 +183,11 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 5) stage2d_march_kernel(Stag
           c = t;
           r = side == 0 ? -1 - m : B + m;
         }
-        M.T[r + 2][c + 2] = w;
+        M.T[r + 2][c + 2] = march::prim(gu[f][0], gu[f][1], gu[f][2], gu[f][3], gm1);
       }
     }
     __syncwarp();
 
-    const int lev = __ldg(&a.level[leaf]);
     const float idx = G.idxf[lev][0], idy = G.idxf[lev][1];
     const int c0 = h * 8;
 
@@ -182,7 +195,7 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 5) stage2d_march_kernel(Stag
     {
       const int j = lo16;
       const float4* row = &M.T[j + 2][2];  // row[c] = W(c, j)
-      float4 wm = row[c0 - 2], w0 = row[c0 - 1], wp = row[c0];
+      float4 wm = row[c0 - 2], w0 = row[c0 - 1], wp = row[c0], wnext = row[c0 + 1];
       float4 lo, hiPrev;
       march::faces<LIM>(wm, w0, wp, lo, hiPrev);  // cell c0-1: its upper face value
       wm = w0;
@@ -191,7 +204,8 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 5) stage2d_march_kernel(Stag
 #pragma unroll
       for (int k = 0; k <= 8; ++k) {
         const int cc = c0 + k;  // cell whose slope is formed; face cc-1/2
-        wp = row[cc + 1];
+        wp = wnext;
+        if (k < 8) wnext = row[cc + 2];
         float4 hi;
         march::faces<LIM>(wm, w0, wp, lo, hi);
         float F[NV];
@@ -217,7 +231,7 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 5) stage2d_march_kernel(Stag
       const int i = lo16;
       const float4* col = &M.T[2][i + 2];  // col[r * 21] = W(i, r)
       constexpr int RS = 21;
-      float4 wm = col[(c0 - 2) * RS], w0 = col[(c0 - 1) * RS], wp = col[c0 * RS];
+      float4 wm = col[(c0 - 2) * RS], w0 = col[(c0 - 1) * RS], wp = col[c0 * RS], wnext = col[(c0 + 1) * RS];
       float4 lo, hiPrev;
       march::faces<LIM>(wm, w0, wp, lo, hiPrev);
       wm = w0;
@@ -226,10 +240,18 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 5) stage2d_march_kernel(Stag
       const float* U0l = a.U0 + (size_t)leaf * NV * NC;
       float* Ol = a.out + (size_t)leaf * NV * NC;
       const float vscale = __int_as_float((127 - 2 * (lev - 1)) << 23);  // 4^-(lev-1), exact
+      // U^(s) and U^n of the next cell to update, loaded one march step ahead
+      float un[NV], u0n[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        un[v] = __ldg(&Ul[v * NC + c0 * B + i]);
+        u0n[v] = a.stage1 ? 0.f : __ldg(&U0l[v * NC + c0 * B + i]);
+      }
 #pragma unroll
       for (int k = 0; k <= 8; ++k) {
         const int rr = c0 + k;  // cell whose slope is formed; face rr-1/2
-        wp = col[(rr + 1) * RS];
+        wp = wnext;
+        if (k < 8) wnext = col[(rr + 2) * RS];
         float4 hi;
         march::faces<LIM>(wm, w0, wp, lo, hi);
         float F[NV];
@@ -244,12 +266,24 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 5) stage2d_march_kernel(Stag
           const int r = rr - 1, q = r * B + i;
           const float4 e = M.E[r][i];
           const float ex[NV] = {e.x, e.y, e.z, e.w};
+          float uc[NV], u0c[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            uc[v] = un[v];
+            u0c[v] = u0n[v];
+          }
+          if (k < 8)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              un[v] = __ldg(&Ul[v * NC + q + B]);
+              u0n[v] = a.stage1 ? 0.f : __ldg(&U0l[v * NC + q + B]);
+            }
           float Un[NV];
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             float div = ex[v] * idx + (F[v] - Fp[v]) * idy;
-            float tmp = __ldg(&Ul[v * NC + q]) - dt * div;
-            Un[v] = a.stage1 ? tmp : a.alpha * __ldg(&U0l[v * NC + q]) + a.beta * tmp;
+            float tmp = uc[v] - dt * div;
+            Un[v] = a.stage1 ? tmp : a.alpha * u0c[v] + a.beta * tmp;
             Ol[v * NC + q] = Un[v];
           }
           if (a.fuse_reduce) {
@@ -274,43 +308,40 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 5) stage2d_march_kernel(Stag
   if (!a.fuse_reduce) return;
 
   // ---- last stage: CTA max rate, CTA totals (fixed order), two-level finish
-  for (int o = 16; o > 0; o >>= 1) {
-    rate = fmaxf(rate, __shfl_xor_sync(0xffffffffu, rate, o));
+  for (int o = 16; o > 0; o >>= 1) rate = fmaxf(rate, __shfl_xor_sync(0xffffffffu, rate, o));
+  if (lane == 0) wrate[warp] = rate;
+  // each warp parks its (hi, lo) pairs in its own E array, which its y march no longer reads
+  float* park = reinterpret_cast<float*>(&M.E[0][0]);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      float h2 = __shfl_xor_sync(0xffffffffu, th[v], o), l2 = __shfl_xor_sync(0xffffffffu, tl[v], o);
-      march::ff_add(th[v], tl[v], h2, l2);
-    }
-  }
-  if (lane == 0) {
-    red[warp][2 * NV] = rate;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      red[warp][v] = th[v];
-      red[warp][NV + v] = tl[v];
-    }
+  for (int v = 0; v < NV; ++v) {
+    park[v * 32 + lane] = th[v];
+    park[(NV + v) * 32 + lane] = tl[v];
   }
   if (bad) sbad = 1;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    float mm = red[0][2 * NV];
-    float hh[NV], ll[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      hh[v] = red[0][v];
-      ll[v] = red[0][NV + v];
+  if (warp == 0) {
+    // lane = 8 v + g: variable v, threads 16 g .. 16 g + 15 in order, then the 8 groups
+    constexpr int PER = 32 * kMarchWarps / 8;
+    const int v = lane >> 3, g = lane & 7;
+    auto hi_of = [&](int t) { return reinterpret_cast<const float*>(&S[t >> 5].E[0][0])[v * 32 + (t & 31)]; };
+    auto lo_of = [&](int t) { return reinterpret_cast<const float*>(&S[t >> 5].E[0][0])[(NV + v) * 32 + (t & 31)]; };
+    float hh = hi_of(g * PER), ll = lo_of(g * PER);
+    for (int t = 1; t < PER; ++t) march::ff_add(hh, ll, hi_of(g * PER + t), lo_of(g * PER + t));
+    for (int o = 4; o > 0; o >>= 1) {
+      float h2 = __shfl_down_sync(0xffffffffu, hh, o), l2 = __shfl_down_sync(0xffffffffu, ll, o);
+      if (g < o) march::ff_add(hh, ll, h2, l2);
     }
-    for (int w = 1; w < kMarchWarps; ++w) {
-      mm = fmaxf(mm, red[w][2 * NV]);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) march::ff_add(hh[v], ll[v], red[w][v], red[w][NV + v]);
+    if (g == 0) a.partials[(size_t)blockIdx.x * NV + v] = ((double)hh + (double)ll) * G.dV[1];
+    __threadfence();  // the partials are visible before the group counter counts this CTA
+    if (lane == 0) {
+      float mm = wrate[0];
+      for (int w = 1; w < kMarchWarps; ++w) mm = fmaxf(mm, wrate[w]);
+      atomicMax(&a.ctl->smax_bits, MaxKey<float>::enc(mm));
+      if (sbad) atomicOr(&a.ctl->status, 1);
     }
-#pragma unroll
-    for (int v = 0; v < NV; ++v) a.partials[(size_t)blockIdx.x * NV + v] = ((double)hh[v] + (double)ll[v]) * G.dV[1];
-    atomicMax(&a.ctl->smax_bits, MaxKey<float>::enc(mm));
-    if (sbad) atomicOr(&a.ctl->status, 1);
   }
-  last_cta_finish<float, NV, 32 * kMarchWarps>(a.ctl, a.partials, a.gpart, a.gcount, (int)gridDim.x, 1, true, dtd);
+  last_cta_finish<float, NV, 32 * kMarchWarps>(a.ctl, a.partials, a.gpart, a.gcount, (int)gridDim.x, 1, true, dtd,
+                                               false);
 }
 
 }  // namespace amrgpu
