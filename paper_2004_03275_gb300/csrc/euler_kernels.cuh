@@ -266,6 +266,23 @@ __device__ __forceinline__ void block_sum_fixed(double* acc) {
   }
 }
 
+// Totals, dt_cfl = cfl / smax and, when `advance`, t += dt (one thread).
+template <typename real, int NV>
+__device__ __forceinline__ void publish_reduction(DevCtl* ctl, const double* acc, bool advance, double dt) {
+  volatile DevCtl* c = ctl;
+  for (int v = 0; v < NV; ++v) c->totals[v] = acc[v];
+  unsigned long long bits = atomicAdd(&ctl->smax_bits, 0ull);
+  double smax = MaxKey<real>::dec(bits);
+  if (advance) {
+    c->t = c->t + dt;
+    c->dt_last = dt;
+    c->steps = c->steps + 1;
+  }
+  c->dt_cfl = c->cfl / smax;
+  c->smax_bits = 0ull;
+  c->done = 0u;
+}
+
 // Two-level finish of a reduction pass.  The last CTA to finish in each group of
 // kGroupCTAs CTAs sums that group's per-leaf partials (fixed order) into gpart;
 // the last group to finish sums the group partials (fixed order), sets the
@@ -322,20 +339,7 @@ __device__ void last_cta_finish(DevCtl* ctl, const double* partials, double* gpa
     for (int v = 0; v < NV; ++v) acc[v] += __ldcg(&gpart[(size_t)q * NV + v]);
   __syncthreads();  // wred reuse
   block_sum_fixed<NV, NTHREADS>(acc);
-  if (threadIdx.x == 0) {
-    volatile DevCtl* c = ctl;
-    for (int v = 0; v < NV; ++v) c->totals[v] = acc[v];
-    unsigned long long bits = atomicAdd(&ctl->smax_bits, 0ull);
-    double smax = MaxKey<real>::dec(bits);
-    if (advance) {
-      c->t = c->t + dt;
-      c->dt_last = dt;
-      c->steps = c->steps + 1;
-    }
-    c->dt_cfl = c->cfl / smax;
-    c->smax_bits = 0ull;
-    c->done = 0u;
-  }
+  if (threadIdx.x == 0) publish_reduction<real, NV>(ctl, acc, advance, dt);
 }
 
 // Block-wide reduction of (max rate, per-variable FP64 sums) and the last-CTA

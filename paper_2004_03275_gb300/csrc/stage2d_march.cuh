@@ -241,11 +241,13 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4) stage2d_march_kernel(Stag
       float* Ol = a.out + (size_t)leaf * NV * NC;
       const float vscale = __int_as_float((127 - 2 * (lev - 1)) << 23);  // 4^-(lev-1), exact
       // U^(s) and U^n of the next cell to update, loaded one march step ahead
-      float un[NV], u0n[NV];
+      float un[NV], u0n[NV], un2[NV], u0n2[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         un[v] = __ldg(&Ul[v * NC + c0 * B + i]);
         u0n[v] = a.stage1 ? 0.f : __ldg(&U0l[v * NC + c0 * B + i]);
+        un2[v] = __ldg(&Ul[v * NC + (c0 + 1) * B + i]);
+        u0n2[v] = a.stage1 ? 0.f : __ldg(&U0l[v * NC + (c0 + 1) * B + i]);
       }
 #pragma unroll
       for (int k = 0; k <= 8; ++k) {
@@ -272,11 +274,16 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4) stage2d_march_kernel(Stag
             uc[v] = un[v];
             u0c[v] = u0n[v];
           }
-          if (k < 8)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            un[v] = un2[v];
+            u0n[v] = u0n2[v];
+          }
+          if (k < 7)
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-              un[v] = __ldg(&Ul[v * NC + q + B]);
-              u0n[v] = a.stage1 ? 0.f : __ldg(&U0l[v * NC + q + B]);
+              un2[v] = __ldg(&Ul[v * NC + q + 2 * B]);
+              u0n2[v] = a.stage1 ? 0.f : __ldg(&U0l[v * NC + q + 2 * B]);
             }
           float Un[NV];
 #pragma unroll
