@@ -64,7 +64,12 @@ template <int B, int FLUX, int LIM>
 void stage2d_f32_go(const StageArgs<float>& a, const Geometry& G, cudaStream_t s) {
   if constexpr (B == 16) {
     int grid = (a.nleaves + kMarchWarps - 1) / kMarchWarps;
-    stage2d_march_kernel<FLUX, LIM><<<grid, 32 * kMarchWarps, 0, s>>>(a, G);
+    if (a.fuse_reduce)
+      stage2d_march_kernel<FLUX, LIM, kStageLast><<<grid, 32 * kMarchWarps, 0, s>>>(a, G);
+    else if (a.stage1)
+      stage2d_march_kernel<FLUX, LIM, kStageFirst><<<grid, 32 * kMarchWarps, 0, s>>>(a, G);
+    else
+      stage2d_march_kernel<FLUX, LIM, kStageMid><<<grid, 32 * kMarchWarps, 0, s>>>(a, G);
     return;
   }
   constexpr int LPB = 256 / (B * B);

@@ -105,9 +105,13 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float h2, float l2)
 
 }  // namespace march
 
-template <int FLUX, int LIM>
+// SK: stage kind, fixed at compile time so every kernel carries only its own path
+enum { kStageFirst = 0, kStageMid = 1, kStageLast = 2 };
+
+template <int FLUX, int LIM, int SK>
 __global__ void __launch_bounds__(32 * kMarchWarps, 4) stage2d_march_kernel(StageArgs<float> a, Geometry G) {
   constexpr int B = 16, NC = B * B, NV = 4;
+  constexpr bool FIRST = SK == kStageFirst, LAST = SK == kStageLast;
   __shared__ MarchSmem S[kMarchWarps];
   __shared__ float wrate[kMarchWarps];
   __shared__ int sbad;
@@ -245,9 +249,9 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4) stage2d_march_kernel(Stag
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         un[v] = __ldg(&Ul[v * NC + c0 * B + i]);
-        u0n[v] = a.stage1 ? 0.f : __ldg(&U0l[v * NC + c0 * B + i]);
+        u0n[v] = FIRST ? 0.f : __ldg(&U0l[v * NC + c0 * B + i]);
         un2[v] = __ldg(&Ul[v * NC + (c0 + 1) * B + i]);
-        u0n2[v] = a.stage1 ? 0.f : __ldg(&U0l[v * NC + (c0 + 1) * B + i]);
+        u0n2[v] = FIRST ? 0.f : __ldg(&U0l[v * NC + (c0 + 1) * B + i]);
       }
 #pragma unroll
       for (int k = 0; k <= 8; ++k) {
@@ -283,17 +287,17 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4) stage2d_march_kernel(Stag
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
               un2[v] = __ldg(&Ul[v * NC + q + 2 * B]);
-              u0n2[v] = a.stage1 ? 0.f : __ldg(&U0l[v * NC + q + 2 * B]);
+              u0n2[v] = FIRST ? 0.f : __ldg(&U0l[v * NC + q + 2 * B]);
             }
           float Un[NV];
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             float div = ex[v] * idx + (F[v] - Fp[v]) * idy;
             float tmp = uc[v] - dt * div;
-            Un[v] = a.stage1 ? tmp : a.alpha * u0c[v] + a.beta * tmp;
+            Un[v] = FIRST ? tmp : a.alpha * u0c[v] + a.beta * tmp;
             Ol[v * NC + q] = Un[v];
           }
-          if (a.fuse_reduce) {
+          if constexpr (LAST) {
             float ir = f32::rcp(Un[0]);
             float vx = Un[1] * ir, vy = Un[2] * ir;
             float p = gm1 * (Un[3] - 0.5f * (Un[1] * vx + Un[2] * vy));
@@ -312,7 +316,7 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4) stage2d_march_kernel(Stag
       }
     }
   }
-  if (!a.fuse_reduce) return;
+  if constexpr (!LAST) return;
 
   // ---- last stage: CTA max rate, CTA totals (fixed order), two-level finish
   for (int o = 16; o > 0; o >>= 1) rate = fmaxf(rate, __shfl_xor_sync(0xffffffffu, rate, o));
