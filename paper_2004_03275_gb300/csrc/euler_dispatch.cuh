@@ -41,11 +41,16 @@ int& stage2d_f32_grid() {
 
 template <int B, int FLUX, int LIM>
 cudaError_t stage2d_f32_prepare_one() {
-  if constexpr (B == 16) return cudaSuccess;  // one warp per leaf, no persistent grid
   int dev, sms, per;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stage2d_f32_kernel<B, FLUX, LIM>, 256, 0);
+  if constexpr (B == 16) {  // persistent grid of the march kernel's last stage
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stage2d_march_kernel<FLUX, LIM, kStageLast>,
+                                                        32 * kMarchWarps, 0);
+  } else if (e == cudaSuccess) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stage2d_f32_kernel<B, FLUX, LIM>, 256, 0);
+  }
   if (e == cudaSuccess) stage2d_f32_grid<B, FLUX, LIM>() = sms * (per > 0 ? per : 1);
   return e;
 }
@@ -64,8 +69,9 @@ template <int B, int FLUX, int LIM>
 void stage2d_f32_go(const StageArgs<float>& a, const Geometry& G, cudaStream_t s) {
   if constexpr (B == 16) {
     int grid = (a.nleaves + kMarchWarps - 1) / kMarchWarps;
+    int cap = stage2d_f32_grid<B, FLUX, LIM>();
     if (a.fuse_reduce)
-      stage2d_march_kernel<FLUX, LIM, kStageLast><<<grid, 32 * kMarchWarps, 0, s>>>(a, G);
+      stage2d_march_kernel<FLUX, LIM, kStageLast><<<cap > 0 && cap < grid ? cap : grid, 32 * kMarchWarps, 0, s>>>(a, G);
     else if (a.stage1)
       stage2d_march_kernel<FLUX, LIM, kStageFirst><<<grid, 32 * kMarchWarps, 0, s>>>(a, G);
     else

@@ -116,20 +116,26 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4) stage2d_march_kernel(Stag
   __shared__ float wrate[kMarchWarps];
   __shared__ int sbad;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int leaf = blockIdx.x * kMarchWarps + warp;
-  const bool active = leaf < a.nleaves;
   const int lo16 = lane & 15, h = lane >> 4;
   MarchSmem& M = S[warp];
   if (threadIdx.x == 0) sbad = 0;  // before the barrier inside cta_stage_dt
 
-  // ---- 1a. every global load of the leaf is issued before the CTA's dt barrier:
-  // the cells of row lo16, columns h*8..h*8+7, and one ghost cell per face
-  // (layer m = h, tangential index t = lo16; faces x-, x+, y-, y+)
-  const float* Ul = a.Us + (size_t)leaf * NV * NC;
+  // Leaf groups (kMarchWarps consecutive leaves, one per warp): the first and
+  // middle stages take one group per CTA; the last stage is persistent, CTA b
+  // taking groups b, b + gridDim.x, ... in that order, so that the per-thread
+  // totals are summed in a fixed order and the finish runs once per CTA.
+  const int ngroups = (a.nleaves + kMarchWarps - 1) / kMarchWarps;
+  int grp = blockIdx.x;
+  int leaf = grp * kMarchWarps + warp;
+  bool active = leaf < a.nleaves;
   float4 u[NV][2];
   float gu[4][NV];
   int lev = 1;
-  if (active) {
+  // ---- 1a. global loads of a leaf: the cells of row lo16, columns h*8..h*8+7,
+  // and one ghost cell per face (layer m = h, tangential index t = lo16; faces
+  // x-, x+, y-, y+).  Those of the first leaf are issued before the CTA's dt barrier.
+  auto load_leaf = [&]() {
+    const float* Ul = a.Us + (size_t)leaf * NV * NC;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const float4* p = reinterpret_cast<const float4*>(Ul + v * NC + lo16 * B + h * 8);
@@ -155,7 +161,8 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4) stage2d_march_kernel(Stag
       for (int v = 0; v < NV; ++v) gu[f][v] = __ldg(&src[v * stride]);
     }
     lev = __ldg(&a.level[leaf]);
-  }
+  };
+  if (active) load_leaf();
   float dt;
   const double dtd = cta_stage_dt(a.ctl, &dt);
   if (!(dt > 0.f)) return;  // same decision as dtd > 0 (a positive dt never rounds to 0 here)
@@ -165,158 +172,167 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4) stage2d_march_kernel(Stag
   int bad = 0;
   float th[NV] = {0.f, 0.f, 0.f, 0.f}, tl[NV] = {0.f, 0.f, 0.f, 0.f};
 
-  if (active) {
-    // ---- 1b. primitive tile
-    {
-      float4* trow = &M.T[lo16 + 2][h * 8 + 2];
+  while (true) {
+    if (active) {
+      const float* Ul = a.Us + (size_t)leaf * NV * NC;
+      // ---- 1b. primitive tile
+      {
+        float4* trow = &M.T[lo16 + 2][h * 8 + 2];
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        trow[4 * q + 0] = march::prim(u[0][q].x, u[1][q].x, u[2][q].x, u[3][q].x, gm1);
-        trow[4 * q + 1] = march::prim(u[0][q].y, u[1][q].y, u[2][q].y, u[3][q].y, gm1);
-        trow[4 * q + 2] = march::prim(u[0][q].z, u[1][q].z, u[2][q].z, u[3][q].z, gm1);
-        trow[4 * q + 3] = march::prim(u[0][q].w, u[1][q].w, u[2][q].w, u[3][q].w, gm1);
-      }
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        const int d = f >> 1, side = f & 1, m = h, t = lo16;
-        int r, c;
-        if (d == 0) {
-          r = t;
-          c = side == 0 ? -1 - m : B + m;
-        } else {
-          c = t;
-          r = side == 0 ? -1 - m : B + m;
+        for (int q = 0; q < 2; ++q) {
+          trow[4 * q + 0] = march::prim(u[0][q].x, u[1][q].x, u[2][q].x, u[3][q].x, gm1);
+          trow[4 * q + 1] = march::prim(u[0][q].y, u[1][q].y, u[2][q].y, u[3][q].y, gm1);
+          trow[4 * q + 2] = march::prim(u[0][q].z, u[1][q].z, u[2][q].z, u[3][q].z, gm1);
+          trow[4 * q + 3] = march::prim(u[0][q].w, u[1][q].w, u[2][q].w, u[3][q].w, gm1);
         }
-        M.T[r + 2][c + 2] = march::prim(gu[f][0], gu[f][1], gu[f][2], gu[f][3], gm1);
-      }
-    }
-    __syncwarp();
-
-    const float idx = G.idxf[lev][0], idy = G.idxf[lev][1];
-    const int c0 = h * 8;
-
-    // ---- 2. x march along row j = lo16: flux differences of columns c0..c0+7 -> E
-    {
-      const int j = lo16;
-      const float4* row = &M.T[j + 2][2];  // row[c] = W(c, j)
-      float4 wm = row[c0 - 2], w0 = row[c0 - 1], wp = row[c0], wnext = row[c0 + 1];
-      float4 lo, hiPrev;
-      march::faces<LIM>(wm, w0, wp, lo, hiPrev);  // cell c0-1: its upper face value
-      wm = w0;
-      w0 = wp;
-      float Fp[NV];
 #pragma unroll
-      for (int k = 0; k <= 8; ++k) {
-        const int cc = c0 + k;  // cell whose slope is formed; face cc-1/2
-        wp = wnext;
-        if (k < 8) wnext = row[cc + 2];
-        float4 hi;
-        march::faces<LIM>(wm, w0, wp, lo, hi);
-        float F[NV];
-        march::flux<FLUX, false>(hiPrev, lo, wm, w0, gam, igm1, F);
-        if (a.has_ffx && ((h == 0 && k == 0) || (h == 1 && k == 8))) {
-          int slot = a.ffx[leaf * 4 + h];
-          if (slot >= 0)
-#pragma unroll
-            for (int v = 0; v < NV; ++v) a.fflux[((size_t)slot * NV + v) * B + j] = F[v];
+        for (int f = 0; f < 4; ++f) {
+          const int d = f >> 1, side = f & 1, m = h, t = lo16;
+          int r, c;
+          if (d == 0) {
+            r = t;
+            c = side == 0 ? -1 - m : B + m;
+          } else {
+            c = t;
+            r = side == 0 ? -1 - m : B + m;
+          }
+          M.T[r + 2][c + 2] = march::prim(gu[f][0], gu[f][1], gu[f][2], gu[f][3], gm1);
         }
-        if (k > 0) M.E[j][cc - 1] = make_float4(F[0] - Fp[0], F[1] - Fp[1], F[2] - Fp[2], F[3] - Fp[3]);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) Fp[v] = F[v];
-        hiPrev = hi;
+      }
+      __syncwarp();
+
+      const float idx = G.idxf[lev][0], idy = G.idxf[lev][1];
+      const int c0 = h * 8;
+
+      // ---- 2. x march along row j = lo16: flux differences of columns c0..c0+7 -> E
+      {
+        const int j = lo16;
+        const float4* row = &M.T[j + 2][2];  // row[c] = W(c, j)
+        float4 wm = row[c0 - 2], w0 = row[c0 - 1], wp = row[c0], wnext = row[c0 + 1];
+        float4 lo, hiPrev;
+        march::faces<LIM>(wm, w0, wp, lo, hiPrev);  // cell c0-1: its upper face value
         wm = w0;
         w0 = wp;
-      }
-    }
-    __syncwarp();
-
-    // ---- 3. y march along column i = lo16, then the cell update of rows c0..c0+7
-    {
-      const int i = lo16;
-      const float4* col = &M.T[2][i + 2];  // col[r * 21] = W(i, r)
-      constexpr int RS = 21;
-      float4 wm = col[(c0 - 2) * RS], w0 = col[(c0 - 1) * RS], wp = col[c0 * RS], wnext = col[(c0 + 1) * RS];
-      float4 lo, hiPrev;
-      march::faces<LIM>(wm, w0, wp, lo, hiPrev);
-      wm = w0;
-      w0 = wp;
-      float Fp[NV];
-      const float* U0l = a.U0 + (size_t)leaf * NV * NC;
-      float* Ol = a.out + (size_t)leaf * NV * NC;
-      const float vscale = __int_as_float((127 - 2 * (lev - 1)) << 23);  // 4^-(lev-1), exact
-      // U^(s) and U^n of the next cell to update, loaded one march step ahead
-      float un[NV], u0n[NV], un2[NV], u0n2[NV];
+        float Fp[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        un[v] = __ldg(&Ul[v * NC + c0 * B + i]);
-        u0n[v] = FIRST ? 0.f : __ldg(&U0l[v * NC + c0 * B + i]);
-        un2[v] = __ldg(&Ul[v * NC + (c0 + 1) * B + i]);
-        u0n2[v] = FIRST ? 0.f : __ldg(&U0l[v * NC + (c0 + 1) * B + i]);
-      }
+        for (int k = 0; k <= 8; ++k) {
+          const int cc = c0 + k;  // cell whose slope is formed; face cc-1/2
+          wp = wnext;
+          if (k < 8) wnext = row[cc + 2];
+          float4 hi;
+          march::faces<LIM>(wm, w0, wp, lo, hi);
+          float F[NV];
+          march::flux<FLUX, false>(hiPrev, lo, wm, w0, gam, igm1, F);
+          if (a.has_ffx && ((h == 0 && k == 0) || (h == 1 && k == 8))) {
+            int slot = a.ffx[leaf * 4 + h];
+            if (slot >= 0)
 #pragma unroll
-      for (int k = 0; k <= 8; ++k) {
-        const int rr = c0 + k;  // cell whose slope is formed; face rr-1/2
-        wp = wnext;
-        if (k < 8) wnext = col[(rr + 2) * RS];
-        float4 hi;
-        march::faces<LIM>(wm, w0, wp, lo, hi);
-        float F[NV];
-        march::flux<FLUX, true>(hiPrev, lo, wm, w0, gam, igm1, F);
-        if (a.has_ffx && ((h == 0 && k == 0) || (h == 1 && k == 8))) {
-          int slot = a.ffx[leaf * 4 + 2 + h];
-          if (slot >= 0)
+              for (int v = 0; v < NV; ++v) a.fflux[((size_t)slot * NV + v) * B + j] = F[v];
+          }
+          if (k > 0) M.E[j][cc - 1] = make_float4(F[0] - Fp[0], F[1] - Fp[1], F[2] - Fp[2], F[3] - Fp[3]);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) a.fflux[((size_t)slot * NV + v) * B + i] = F[v];
+          for (int v = 0; v < NV; ++v) Fp[v] = F[v];
+          hiPrev = hi;
+          wm = w0;
+          w0 = wp;
         }
-        if (k > 0) {
-          const int r = rr - 1, q = r * B + i;
-          const float4 e = M.E[r][i];
-          const float ex[NV] = {e.x, e.y, e.z, e.w};
-          float uc[NV], u0c[NV];
+      }
+      __syncwarp();
+
+      // ---- 3. y march along column i = lo16, then the cell update of rows c0..c0+7
+      {
+        const int i = lo16;
+        const float4* col = &M.T[2][i + 2];  // col[r * 21] = W(i, r)
+        constexpr int RS = 21;
+        float4 wm = col[(c0 - 2) * RS], w0 = col[(c0 - 1) * RS], wp = col[c0 * RS], wnext = col[(c0 + 1) * RS];
+        float4 lo, hiPrev;
+        march::faces<LIM>(wm, w0, wp, lo, hiPrev);
+        wm = w0;
+        w0 = wp;
+        float Fp[NV];
+        const float* U0l = a.U0 + (size_t)leaf * NV * NC;
+        float* Ol = a.out + (size_t)leaf * NV * NC;
+        const float vscale = __int_as_float((127 - 2 * (lev - 1)) << 23);  // 4^-(lev-1), exact
+        // U^(s) and U^n of the next cell to update, loaded one march step ahead
+        float un[NV], u0n[NV], un2[NV], u0n2[NV];
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            uc[v] = un[v];
-            u0c[v] = u0n[v];
-          }
+        for (int v = 0; v < NV; ++v) {
+          un[v] = __ldg(&Ul[v * NC + c0 * B + i]);
+          u0n[v] = FIRST ? 0.f : __ldg(&U0l[v * NC + c0 * B + i]);
+          un2[v] = __ldg(&Ul[v * NC + (c0 + 1) * B + i]);
+          u0n2[v] = FIRST ? 0.f : __ldg(&U0l[v * NC + (c0 + 1) * B + i]);
+        }
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            un[v] = un2[v];
-            u0n[v] = u0n2[v];
+        for (int k = 0; k <= 8; ++k) {
+          const int rr = c0 + k;  // cell whose slope is formed; face rr-1/2
+          wp = wnext;
+          if (k < 8) wnext = col[(rr + 2) * RS];
+          float4 hi;
+          march::faces<LIM>(wm, w0, wp, lo, hi);
+          float F[NV];
+          march::flux<FLUX, true>(hiPrev, lo, wm, w0, gam, igm1, F);
+          if (a.has_ffx && ((h == 0 && k == 0) || (h == 1 && k == 8))) {
+            int slot = a.ffx[leaf * 4 + 2 + h];
+            if (slot >= 0)
+#pragma unroll
+              for (int v = 0; v < NV; ++v) a.fflux[((size_t)slot * NV + v) * B + i] = F[v];
           }
-          if (k < 7)
+          if (k > 0) {
+            const int r = rr - 1, q = r * B + i;
+            const float4 e = M.E[r][i];
+            const float ex[NV] = {e.x, e.y, e.z, e.w};
+            float uc[NV], u0c[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-              un2[v] = __ldg(&Ul[v * NC + q + 2 * B]);
-              u0n2[v] = FIRST ? 0.f : __ldg(&U0l[v * NC + q + 2 * B]);
+              uc[v] = un[v];
+              u0c[v] = u0n[v];
             }
-          float Un[NV];
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            float div = ex[v] * idx + (F[v] - Fp[v]) * idy;
-            float tmp = uc[v] - dt * div;
-            Un[v] = FIRST ? tmp : a.alpha * u0c[v] + a.beta * tmp;
-            Ol[v * NC + q] = Un[v];
-          }
-          if constexpr (LAST) {
-            float ir = f32::rcp(Un[0]);
-            float vx = Un[1] * ir, vy = Un[2] * ir;
-            float p = gm1 * (Un[3] - 0.5f * (Un[1] * vx + Un[2] * vy));
-            if (!(Un[0] > 0.f) || !(p > 0.f)) bad = 1;
-            float cs = sqrtf(gam * p * ir);
-            rate = fmaxf(rate, (fabsf(vx) + cs) * idx + (fabsf(vy) + cs) * idy);
+            for (int v = 0; v < NV; ++v) {
+              un[v] = un2[v];
+              u0n[v] = u0n2[v];
+            }
+            if (k < 7)
 #pragma unroll
-            for (int v = 0; v < NV; ++v) march::two_sum_add(th[v], tl[v], Un[v] * vscale);
+              for (int v = 0; v < NV; ++v) {
+                un2[v] = __ldg(&Ul[v * NC + q + 2 * B]);
+                u0n2[v] = FIRST ? 0.f : __ldg(&U0l[v * NC + q + 2 * B]);
+              }
+            float Un[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              float div = ex[v] * idx + (F[v] - Fp[v]) * idy;
+              float tmp = uc[v] - dt * div;
+              Un[v] = FIRST ? tmp : a.alpha * u0c[v] + a.beta * tmp;
+              Ol[v * NC + q] = Un[v];
+            }
+            if constexpr (LAST) {
+              float ir = f32::rcp(Un[0]);
+              float vx = Un[1] * ir, vy = Un[2] * ir;
+              float p = gm1 * (Un[3] - 0.5f * (Un[1] * vx + Un[2] * vy));
+              if (!(Un[0] > 0.f) || !(p > 0.f)) bad = 1;
+              float cs = sqrtf(gam * p * ir);
+              rate = fmaxf(rate, (fabsf(vx) + cs) * idx + (fabsf(vy) + cs) * idy);
+#pragma unroll
+              for (int v = 0; v < NV; ++v) march::two_sum_add(th[v], tl[v], Un[v] * vscale);
+            }
           }
+#pragma unroll
+          for (int v = 0; v < NV; ++v) Fp[v] = F[v];
+          hiPrev = hi;
+          wm = w0;
+          w0 = wp;
         }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) Fp[v] = F[v];
-        hiPrev = hi;
-        wm = w0;
-        w0 = wp;
       }
     }
+    if constexpr (!LAST) return;
+    grp += gridDim.x;
+    if (grp >= ngroups) break;
+    leaf = grp * kMarchWarps + warp;
+    active = leaf < a.nleaves;
+    __syncwarp();  // every lane of this warp is done with its tile and E before the next leaf
+    if (active) load_leaf();
   }
-  if constexpr (!LAST) return;
 
   // ---- last stage: CTA max rate, CTA totals (fixed order), two-level finish
   for (int o = 16; o > 0; o >>= 1) rate = fmaxf(rate, __shfl_xor_sync(0xffffffffu, rate, o));
