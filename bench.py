@@ -58,6 +58,15 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def bf16_peak():
+    """Dense bf16 burst peak (TFLOP/s) from MEASURED_PEAKS.json, else the fallback figure."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f).get("bf16_tflops", 1900.0))
+    return 1900.0
+
+
 class Clocks:
     """nvidia-smi sampling of SM clock and throttle reasons during a timed region."""
 
@@ -209,6 +218,80 @@ def bench_learned_guess(torch, amrvac, stream, eval_steps=6):
     return out
 
 
+# Algorithmic bytes per level-0 unknown per V-cycle of the float32 multigrid (nu1 = nu2 = 2, 2D):
+#   level 0: 4 sweeps x (read x, b; write x: 12 B) = 48; float64 residual (read X, B; write b0, x0 = 0)
+#   = 24; residual + restriction (read x0, b0; write 1/4 of b1, x1) = 10; prolongation (read 1/4 of x1,
+#   read + write x0) = 9; float64 correction (read X, x0; write X) = 20  -> 111 B;
+#   coarser levels: (48 + 10 + 9) B x (1/4 + 1/16 + ...) = 22 B  -> 133 B.
+MG_BYTES_PER_UNKNOWN_VCYCLE = 133.0
+
+
+def bench_mg_vcycle(torch, amrvac, stream, hbm_gbs):
+    """Time of one V-cycle of the batched float32 multigrid over the configuration-4 instance sizes
+    (16 grids 256^2..2048^2, 28.7M unknowns, lambda = 2/(dt Du) of Gray-Scott's u): two solves from a
+    zero guess to rtol 1e-4 and 1e-10, differenced, so the per-solve setup cancels."""
+    from paper_2004_03275_gb300 import inputs
+    sizes = inputs.gray_scott_batch_sizes()
+    n = sum(k * k for k in sizes)
+    lam = 2.0 / (0.5 * 2e-5)
+    b = torch.from_numpy(np.random.default_rng(7).normal(size=n)).cuda()
+    res = {}
+    for rtol in (1e-4, 1e-10):
+        s = amrvac.MgSolver(2, sizes, lam, 2.5, rtol=rtol, precision="fp32", stream=stream.cuda_stream)
+        x = torch.zeros_like(b)
+        s.solve(b, x)
+        best = None
+        for _ in range(3):
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cyc, _ = s.solve(b, x)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            best = el if best is None else min(best, el)
+        res[rtol] = (best, int(np.max(cyc)))
+        s.close()
+    (t_lo, c_lo), (t_hi, c_hi) = res[1e-4], res[1e-10]
+    tv = (t_hi - t_lo) / max(1, c_hi - c_lo)
+    gbs = MG_BYTES_PER_UNKNOWN_VCYCLE * n / tv / 1e9
+    return {"workload": "batched Helmholtz multigrid, 16 periodic grids 256^2..2048^2 (28.7M unknowns), "
+                        "float32 V-cycles on the float64 defect, nu1 = nu2 = 2",
+            "ms_per_vcycle": tv * 1e3, "unknown_vcycles_per_s": n / tv, "cycles_rtol_1e-4_1e-10": [c_lo, c_hi],
+            "roofline": {"bound": "hbm", "bytes_per_unknown": MG_BYTES_PER_UNKNOWN_VCYCLE,
+                         "achieved": round(gbs, 1), "peak": hbm_gbs, "unit": "GB/s", "frac": round(gbs / hbm_gbs, 4)},
+            "timing": "host wall clock around synchronous solves (includes the per-cycle residual check and "
+                      "host poll), best of 3, difference of two tolerances"}
+
+
+# 2 x 9 x (5*16 + 16*16 + 16*16 + 16*2) multiply-adds x 2 per pixel for the 4 layers
+CNN_FLOP_PER_PIXEL_2D = 11232.0
+
+
+def bench_cnn_forward(torch, amrvac, stream, peak_tflops):
+    """Inference of the learned-guess network on one 2048^2 grid (5 input channels), CUDA events."""
+    net = amrvac.CnnNet(ndim=2, seed=3, stream=stream.cuda_stream)
+    x = torch.from_numpy(np.random.default_rng(3).uniform(size=(1, 5, 2048, 2048)).astype(np.float32)).cuda()
+    out = torch.empty((1, 2, 2048, 2048), dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            net.forward(x, out)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            net.forward(x, out)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    tf = CNN_FLOP_PER_PIXEL_2D * 2048 * 2048 / (ms * 1e-3) / 1e12
+    net.close()
+    return {"workload": "learned-guess CNN inference, 2048^2, 5->16->16->16->2 channels, 3x3, bf16 mma.sync",
+            "ms_per_inference": ms, "roofline": {"bound": "tensor", "achieved": round(tf, 1), "peak": peak_tflops,
+                                                  "unit": "TFLOP/s", "frac": round(tf / peak_tflops, 4),
+                                                  "flop_per_pixel": CNN_FLOP_PER_PIXEL_2D}}
+
+
 def bench_blast(torch, amrvac, stream, steps=20, regrid_every=10):
     """Config 3: 3D blast, 4^3 base blocks of 16^3, 4 levels (effective 512^3), HLLC + Koren, SSPRK3,
     FP32 state, regrid every 10 steps.  cell-updates/s per RK stage excluding regrid time."""
@@ -320,6 +403,9 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-extra", action="store_true", help="skip the Gray-Scott and blast configurations")
+    ap.add_argument("--extras", default="all",
+                    help="comma list of extra workloads: gray_scott_batch, mg_vcycle, blast3d, learned_guess_2d, "
+                         "cnn_forward_2048 (default all; 'none' for none)")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -418,9 +504,15 @@ def main():
 
     extra = {}
     if not args.skip_extra and rank == 0:
-        extra["gray_scott_batch"] = bench_gray_scott(torch, amrvac, stream)
-        extra["blast3d"] = bench_blast(torch, amrvac, stream)
-        extra["learned_guess_2d"] = bench_learned_guess(torch, amrvac, stream)
+        names = ["gray_scott_batch", "mg_vcycle", "blast3d", "learned_guess_2d", "cnn_forward_2048"]
+        want = names if args.extras == "all" else [e for e in args.extras.split(",") if e in names]
+        runs = {"gray_scott_batch": lambda: bench_gray_scott(torch, amrvac, stream),
+                "mg_vcycle": lambda: bench_mg_vcycle(torch, amrvac, stream, hbm),
+                "blast3d": lambda: bench_blast(torch, amrvac, stream),
+                "learned_guess_2d": lambda: bench_learned_guess(torch, amrvac, stream),
+                "cnn_forward_2048": lambda: bench_cnn_forward(torch, amrvac, stream, bf16_peak())}
+        for name in want:
+            extra[name] = runs[name]()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:

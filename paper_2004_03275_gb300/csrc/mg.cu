@@ -46,6 +46,8 @@ struct InstDev {
   float ih2f[kMaxLev];
   double lam;
   float lamf;
+  double idiag[kMaxLev];        // 1 / (lambda + 2 ndim / h^2): the smoother multiplies by it
+  float idiagf[kMaxLev];
   int ntx[kMaxLev];             // 2D sweep tiles along x on each level
   long long off0;          // offset into X / B
   long long inv_off;       // offset into the coarsest inverse matrices
@@ -145,11 +147,57 @@ __device__ __forceinline__ double ih2_of<double>(const InstDev& I, int l) { retu
 template <>
 __device__ __forceinline__ float ih2_of<float>(const InstDev& I, int l) { return I.ih2f[l]; }
 template <typename real>
+__device__ __forceinline__ real idiag_of(const InstDev& I, int l);
+template <>
+__device__ __forceinline__ double idiag_of<double>(const InstDev& I, int l) { return I.idiag[l]; }
+template <>
+__device__ __forceinline__ float idiag_of<float>(const InstDev& I, int l) { return I.idiagf[l]; }
+template <typename real>
 __device__ __forceinline__ real lam_of(const InstDev& I);
 template <>
 __device__ __forceinline__ double lam_of<double>(const InstDev& I) { return I.lam; }
 template <>
 __device__ __forceinline__ float lam_of<float>(const InstDev& I) { return I.lamf; }
+
+// IEEE-754 widening and narrowing between float32 and float64 by bit manipulation, on the
+// integer units (GB300's float64 pipe is ~1/64 of its float32 rate and bounds the defect
+// correction).  Widening is exact, subnormals included.  Narrowing truncates the 29 dropped
+// mantissa bits and flushes values below the float normal range to zero, which is enough for
+// the right-hand side of a correction equation.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f), e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  unsigned long long bits;
+  if (e == 0u) {
+    if (m == 0u) {
+      bits = sign;  // signed zero
+    } else {        // subnormal: m 2^-149 = 2^(p-149) (m / 2^p), p = position of the leading one
+      const int p = 31 - __clz(m);
+      bits = sign | ((unsigned long long)(p + 874) << 52) | (((unsigned long long)m << (52 - p)) & 0xfffffffffffffull);
+    }
+  } else if (e == 0xffu) {
+    bits = sign | (0x7ffull << 52) | ((unsigned long long)m << 29);  // infinity, NaN (payload kept)
+  } else {
+    bits = sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+  }
+  return __longlong_as_double((long long)bits);
+}
+template <typename real>
+__device__ __forceinline__ real narrow(double d);
+template <>
+__device__ __forceinline__ double narrow<double>(double d) { return d; }
+template <>
+__device__ __forceinline__ float narrow<float>(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7ffu) - 896;  // float exponent field
+  const unsigned m = (unsigned)((b >> 29) & 0x7fffffull);
+  unsigned u;
+  if (e <= 0) u = sign;                                                             // below 2^-126: zero
+  else if (e >= 255) u = sign | 0x7f800000u | ((b & 0xfffffffffffffull) ? 0x400000u : 0u);  // overflow, inf, NaN
+  else u = sign | ((unsigned)e << 23) | m;
+  return __uint_as_float(u);
+}
 
 // ---------------------------------------------------------------- kernels --
 // max |B| per instance (level-0 chunks)
@@ -188,11 +236,14 @@ __global__ void residual64_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
     cell_of(t, n, S.ndim, c);
     const double* X = S.X + I.off0;
     double x = X[t];
-    double lap = (nbsum(X, c, n, S.ndim) - (2.0 * S.ndim) * x) * I.ih2[0];
-    double r = S.B[I.off0 + t] - (I.lam * x - lap);
-    L.b[I.off[0] + t] = (real)r;
+    // r = B + ih2 (nbsum - 2 ndim x) - lambda x in three fused multiply-adds: the float64
+    // unit is GB300's scarcest pipe, so the residual uses as few float64 operations as it can
+    const double m2nd = S.ndim == 3 ? -6.0 : -4.0;
+    double r = fma(fma(m2nd, x, nbsum(X, c, n, S.ndim)), I.ih2[0], S.B[I.off0 + t]);
+    r = fma(-I.lam, x, r);
+    L.b[I.off[0] + t] = narrow<real>(r);
     L.x[I.off[0] + t] = real(0);
-    m = (unsigned long long)__double_as_longlong(fabs(r));
+    m = (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;  // |r| as bits
   }
   block_max_atomic(m, &S.rnorm[C.inst]);
 }
@@ -241,9 +292,9 @@ __global__ void smooth_kernel(MgState S, Lvl<real> L, const Chunk* ch, int colou
   real* x = L.x + I.off[l];
   const real* b = L.b + I.off[l];
   real ih2 = ih2_of<real>(I, l);
-  real diag = lam_of<real>(I) + real(2 * nd) * ih2;
+  const real idg = idiag_of<real>(I, l);
   long long q = lin(c, n);
-  x[q] = (b[q] + nbsum(x, c, n, nd) * ih2) / diag;
+  x[q] = (b[q] + nbsum(x, c, n, nd) * ih2) * idg;
 }
 
 // One full red-black sweep of a 2D level on a TX x TY tile: x (halo 2) and b (halo 1)
@@ -268,17 +319,24 @@ __global__ void __launch_bounds__(256)
   const int tx0 = (tile % ntx) * kSwTX, ty0 = (tile / ntx) * kSwTY;
   const real* x = xin + I.off[l];
   const real* b = bl + I.off[l];
+  const bool one_wrap = n >= PX;  // every halo index is at most one period away
   for (int k = threadIdx.x; k < PX * PY; k += blockDim.x) {
     int i = k % PX, j = k / PX;
     int gi = tx0 - 2 + i, gj = ty0 - 2 + j;
-    gi = ((gi % n) + n) % n;
-    gj = ((gj % n) + n) % n;
-    xs[j][i] = x[(long long)gj * n + gi];
-    if (i >= 1 && i < PX - 1 && j >= 1 && j < PY - 1) bs[j - 1][i - 1] = b[(long long)gj * n + gi];
+    if (one_wrap) {
+      gi += gi < 0 ? n : (gi >= n ? -n : 0);
+      gj += gj < 0 ? n : (gj >= n ? -n : 0);
+    } else {
+      gi = ((gi % n) + n) % n;
+      gj = ((gj % n) + n) % n;
+    }
+    const int q = gj * n + gi;
+    xs[j][i] = x[q];
+    if (i >= 1 && i < PX - 1 && j >= 1 && j < PY - 1) bs[j - 1][i - 1] = b[q];
   }
   __syncthreads();
   const real ih2 = ih2_of<real>(I, l);
-  const real diag = lam_of<real>(I) + real(2 * 2) * ih2;
+  const real idg = idiag_of<real>(I, l);
   // red (colour 0: even i+j in global coordinates, n even) on rows -1..TY, cols -1..TX
   constexpr int RW = (kSwTX + 2) / 2;  // colour cells per row of the ring region
   for (int k = threadIdx.x; k < (kSwTY + 2) * RW; k += blockDim.x) {
@@ -287,7 +345,7 @@ __global__ void __launch_bounds__(256)
     int ir = i0 + 2 * kk;
     if (ir > kSwTX) continue;
     int si = ir + 2, sj = jr + 2;
-    xs[sj][si] = (bs[sj - 1][si - 1] + (xs[sj][si - 1] + xs[sj][si + 1] + xs[sj - 1][si] + xs[sj + 1][si]) * ih2) / diag;
+    xs[sj][si] = (bs[sj - 1][si - 1] + (xs[sj][si - 1] + xs[sj][si + 1] + xs[sj - 1][si] + xs[sj + 1][si]) * ih2) * idg;
   }
   __syncthreads();
   constexpr int BW = kSwTX / 2;
@@ -296,7 +354,7 @@ __global__ void __launch_bounds__(256)
     int i0 = (tx0 + ty0 + jb + 1) & 1;  // first tile column of colour 1 in this row
     int ib = i0 + 2 * kk;
     int si = ib + 2, sj = jb + 2;
-    xs[sj][si] = (bs[sj - 1][si - 1] + (xs[sj][si - 1] + xs[sj][si + 1] + xs[sj - 1][si] + xs[sj + 1][si]) * ih2) / diag;
+    xs[sj][si] = (bs[sj - 1][si - 1] + (xs[sj][si - 1] + xs[sj][si + 1] + xs[sj - 1][si] + xs[sj + 1][si]) * ih2) * idg;
   }
   __syncthreads();
   for (int k = threadIdx.x; k < kSwTX * kSwTY; k += blockDim.x) {
@@ -438,7 +496,11 @@ __global__ void correct64_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
   if (!S.active[C.inst] || threadIdx.x >= C.count) return;
   const InstDev& I = S.inst[C.inst];
   long long t = C.start + threadIdx.x;
-  S.X[I.off0 + t] = S.X[I.off0 + t] + (double)L.x[I.off[0] + t];
+  const real e = L.x[I.off[0] + t];
+  if constexpr (sizeof(real) == 4)
+    S.X[I.off0 + t] = S.X[I.off0 + t] + widen(e);
+  else
+    S.X[I.off0 + t] = S.X[I.off0 + t] + e;
 }
 
 // ------------------------------------------------------- Gray-Scott IMEX --
@@ -751,6 +813,8 @@ struct Mg {
         double h = L / m;
         I.ih2[l] = 1.0 / (h * h);
         I.ih2f[l] = (float)I.ih2[l];
+        I.idiag[l] = 1.0 / (lambda[i] + 2.0 * nd * I.ih2[l]);
+        I.idiagf[l] = (float)I.idiag[l];
         I.ntx[l] = (m + kSwTX - 1) / kSwTX;
         ++l;
         if ((m & 1) || m <= coarse_max) break;
