@@ -229,19 +229,19 @@ MG_BYTES_PER_UNKNOWN_VCYCLE = 133.0
 def bench_mg_vcycle(torch, amrvac, stream, hbm_gbs):
     """Time of one V-cycle of the batched float32 multigrid over the configuration-4 instance sizes
     (16 grids 256^2..2048^2, 28.7M unknowns, lambda = 2/(dt Du) of Gray-Scott's u): two solves from a
-    zero guess to rtol 1e-4 and 1e-10, differenced, so the per-solve setup cancels."""
+    zero guess to rtol 1e-3 and 1e-12 (best of 5 each), differenced, so the per-solve setup cancels."""
     from paper_2004_03275_gb300 import inputs
     sizes = inputs.gray_scott_batch_sizes()
     n = sum(k * k for k in sizes)
     lam = 2.0 / (0.5 * 2e-5)
     b = torch.from_numpy(np.random.default_rng(7).normal(size=n)).cuda()
     res = {}
-    for rtol in (1e-4, 1e-10):
+    for rtol in (1e-3, 1e-12):
         s = amrvac.MgSolver(2, sizes, lam, 2.5, rtol=rtol, precision="fp32", stream=stream.cuda_stream)
         x = torch.zeros_like(b)
         s.solve(b, x)
         best = None
-        for _ in range(3):
+        for _ in range(5):
             x.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -251,16 +251,16 @@ def bench_mg_vcycle(torch, amrvac, stream, hbm_gbs):
             best = el if best is None else min(best, el)
         res[rtol] = (best, int(np.max(cyc)))
         s.close()
-    (t_lo, c_lo), (t_hi, c_hi) = res[1e-4], res[1e-10]
+    (t_lo, c_lo), (t_hi, c_hi) = res[1e-3], res[1e-12]
     tv = (t_hi - t_lo) / max(1, c_hi - c_lo)
     gbs = MG_BYTES_PER_UNKNOWN_VCYCLE * n / tv / 1e9
     return {"workload": "batched Helmholtz multigrid, 16 periodic grids 256^2..2048^2 (28.7M unknowns), "
                         "float32 V-cycles on the float64 defect, nu1 = nu2 = 2",
-            "ms_per_vcycle": tv * 1e3, "unknown_vcycles_per_s": n / tv, "cycles_rtol_1e-4_1e-10": [c_lo, c_hi],
+            "ms_per_vcycle": tv * 1e3, "unknown_vcycles_per_s": n / tv, "cycles_rtol_1e-3_1e-12": [c_lo, c_hi],
             "roofline": {"bound": "hbm", "bytes_per_unknown": MG_BYTES_PER_UNKNOWN_VCYCLE,
                          "achieved": round(gbs, 1), "peak": hbm_gbs, "unit": "GB/s", "frac": round(gbs / hbm_gbs, 4)},
             "timing": "host wall clock around synchronous solves (includes the per-cycle residual check and "
-                      "host poll), best of 3, difference of two tolerances"}
+                      "host poll), best of 5, difference of two tolerances"}
 
 
 # 2 x 9 x (5*16 + 16*16 + 16*16 + 16*2) multiply-adds x 2 per pixel for the 4 layers

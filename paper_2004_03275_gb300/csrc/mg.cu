@@ -48,7 +48,6 @@ struct InstDev {
   float lamf;
   double idiag[kMaxLev];        // 1 / (lambda + 2 ndim / h^2): the smoother multiplies by it
   float idiagf[kMaxLev];
-  int ntx[kMaxLev];             // 2D sweep tiles along x on each level
   long long off0;          // offset into X / B
   long long inv_off;       // offset into the coarsest inverse matrices
 };
@@ -297,85 +296,124 @@ __global__ void smooth_kernel(MgState S, Lvl<real> L, const Chunk* ch, int colou
   x[q] = (b[q] + nbsum(x, c, n, nd) * ih2) * idg;
 }
 
-// One full red-black sweep of a 2D level on a TX x TY tile: x (halo 2) and b (halo 1)
-// staged in shared memory, red cells updated on the tile plus one ring, then black
-// cells on the tile, then the tile written to a second array (tiles never read what
-// another tile of the same launch writes).  Same updates, in the same order and the
-// same arithmetic, as two colour sweeps in place.
-constexpr int kSwTX = 64, kSwTY = 16;
+// One full red-black sweep of a 2D level, one warp per strip of kStripW columns and
+// H rows (H = clamp(n / 32, 8, 64) on a level of side n, carried in the chunk's count:
+// short strips on coarse levels keep the serial march short where there is little
+// parallelism).  Lane k holds column x0 - 2 + k (periodic); the two lanes at each edge
+// are halo.  Walking the strip's rows, a lane keeps three rows of old values and three
+// rows of red-updated values in registers (loads run kPre rows ahead): at row s it
+// updates the red cells of row s + 1 (old black neighbours: its own rows s and s + 2,
+// row s + 1 of the lanes beside it), then the black cells of row s (red-updated
+// neighbours: its own rows s - 1 and s + 1, row s of the lanes beside it), and stores
+// row s.  It reads one iterate array and writes the other, so no warp sees another's
+// writes; the updates and their arithmetic are those of two in-place colour sweeps.
+constexpr int kStripW = 28, kStripHMax = 64, kPre = 4;
+
+inline int strip_height(int n) { return std::min(kStripHMax, std::max(8, n / 32)); }
+constexpr unsigned kFull = 0xffffffffu;
+
+struct StripGeom {
+  int n, c, x0, y0, y1;
+  bool out_lane;
+};
+
+__device__ __forceinline__ StripGeom strip_geom(int n, long long start, int H, int lane) {
+  StripGeom g;
+  const int nsx = (n + kStripW - 1) / kStripW;
+  const int sx = (int)(start % nsx), sy = (int)(start / nsx);
+  g.n = n;
+  g.x0 = sx * kStripW;
+  g.y0 = sy * H;
+  g.y1 = min(g.y0 + H, n);
+  const int c = g.x0 - 2 + lane;
+  g.c = ((c % n) + n) % n;
+  g.out_lane = lane >= 2 && lane < 2 + kStripW && c < n;
+  return g;
+}
+
+__device__ __forceinline__ int wrap_row(int r, int n) { return r < 0 ? r + n : (r >= n ? r - n : r); }
 
 template <typename real>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
     sweep2d_kernel(MgState S, const real* __restrict__ xin, real* __restrict__ xout, const real* __restrict__ bl,
-                   const Chunk* ch) {
-  constexpr int PX = kSwTX + 4, PY = kSwTY + 4;
-  __shared__ real xs[PY][PX];
-  __shared__ real bs[PY - 2][PX - 2];
-  Chunk C = ch[blockIdx.x];
+                   const Chunk* ch, int nch) {
+  const int lane = threadIdx.x & 31;
+  const int wi = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (wi >= nch) return;
+  const Chunk C = ch[wi];
   if (!S.active[C.inst]) return;
   const InstDev& I = S.inst[C.inst];
-  const int l = C.lev, n = I.n[l];
-  const int tile = (int)C.start, ntx = I.ntx[l];
-  const int tx0 = (tile % ntx) * kSwTX, ty0 = (tile / ntx) * kSwTY;
+  const int l = C.lev;
+  const StripGeom g = strip_geom(I.n[l], C.start, C.count, lane);
+  const int n = g.n, c = g.c;
   const real* x = xin + I.off[l];
   const real* b = bl + I.off[l];
-  const bool one_wrap = n >= PX;  // every halo index is at most one period away
-  for (int k = threadIdx.x; k < PX * PY; k += blockDim.x) {
-    int i = k % PX, j = k / PX;
-    int gi = tx0 - 2 + i, gj = ty0 - 2 + j;
-    if (one_wrap) {
-      gi += gi < 0 ? n : (gi >= n ? -n : 0);
-      gj += gj < 0 ? n : (gj >= n ? -n : 0);
-    } else {
-      gi = ((gi % n) + n) % n;
-      gj = ((gj % n) + n) % n;
+  real* xo = xout + I.off[l];
+  const real ih2 = ih2_of<real>(I, l), idg = idiag_of<real>(I, l);
+  // rows stay within one period of [0, n) when n > H + kPre + 2; else a full modulo
+  const bool one_wrap = n > C.count + kPre + 2;
+  auto rowof = [&](int r) { return one_wrap ? wrap_row(r, n) : ((r % n) + n) % n; };
+  auto ldx = [&](int r) { return x[rowof(r) * n + c]; };
+  auto ldb = [&](int r) { return b[rowof(r) * n + c]; };
+  // red update of row r from old rows om, o0 (row r), op; black cells keep o0
+  auto red = [&](real om, real o0, real op, real bb, int r) {
+    const real lft = __shfl_up_sync(kFull, o0, 1), rgt = __shfl_down_sync(kFull, o0, 1);
+    const real v = (bb + (lft + rgt + om + op) * ih2) * idg;
+    return ((c + rowof(r)) & 1) == 0 ? v : o0;
+  };
+  const int y0 = g.y0, y1 = g.y1;
+  // old rows y0-2 .. y0+1, red rows y0-1 and y0
+  real o_a = ldx(y0 - 2), o_b = ldx(y0 - 1), o_c = ldx(y0), o_d = ldx(y0 + 1);
+  real b_c = ldb(y0 - 1), b_d = ldb(y0);
+  real r_m = red(o_a, o_b, o_c, b_c, y0 - 1);
+  real r_0 = red(o_b, o_c, o_d, b_d, y0);
+  real b_0 = b_d;
+  // prefetch ring: old rows s+2 .. s+1+kPre and right-hand sides of rows s+1 .. s+kPre
+  real px[kPre], pb[kPre];
+#pragma unroll
+  for (int k = 0; k < kPre; ++k) {
+    px[k] = y0 + 2 + k <= y1 + 1 ? ldx(y0 + 2 + k) : real(0);
+    pb[k] = y0 + 1 + k <= y1 ? ldb(y0 + 1 + k) : real(0);
+  }
+  real o_s = o_c, o_s1 = o_d;  // old rows s, s+1
+#pragma unroll 4
+  for (int s = y0; s < y1; ++s) {
+    const real o_s2 = px[0], b_s1 = pb[0];
+#pragma unroll
+    for (int k = 0; k + 1 < kPre; ++k) {
+      px[k] = px[k + 1];
+      pb[k] = pb[k + 1];
     }
-    const int q = gj * n + gi;
-    xs[j][i] = x[q];
-    if (i >= 1 && i < PX - 1 && j >= 1 && j < PY - 1) bs[j - 1][i - 1] = b[q];
-  }
-  __syncthreads();
-  const real ih2 = ih2_of<real>(I, l);
-  const real idg = idiag_of<real>(I, l);
-  // red (colour 0: even i+j in global coordinates, n even) on rows -1..TY, cols -1..TX
-  constexpr int RW = (kSwTX + 2) / 2;  // colour cells per row of the ring region
-  for (int k = threadIdx.x; k < (kSwTY + 2) * RW; k += blockDim.x) {
-    int jr = k / RW - 1, kk = k % RW;
-    int i0 = -1 + ((tx0 + ty0 + jr + 1) & 1);  // first ring column of colour 0 in this row
-    int ir = i0 + 2 * kk;
-    if (ir > kSwTX) continue;
-    int si = ir + 2, sj = jr + 2;
-    xs[sj][si] = (bs[sj - 1][si - 1] + (xs[sj][si - 1] + xs[sj][si + 1] + xs[sj - 1][si] + xs[sj + 1][si]) * ih2) * idg;
-  }
-  __syncthreads();
-  constexpr int BW = kSwTX / 2;
-  for (int k = threadIdx.x; k < kSwTY * BW; k += blockDim.x) {
-    int jb = k / BW, kk = k % BW;
-    int i0 = (tx0 + ty0 + jb + 1) & 1;  // first tile column of colour 1 in this row
-    int ib = i0 + 2 * kk;
-    int si = ib + 2, sj = jb + 2;
-    xs[sj][si] = (bs[sj - 1][si - 1] + (xs[sj][si - 1] + xs[sj][si + 1] + xs[sj - 1][si] + xs[sj + 1][si]) * ih2) * idg;
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < kSwTX * kSwTY; k += blockDim.x) {
-    int i = k % kSwTX, j = k / kSwTX;
-    int gi = tx0 + i, gj = ty0 + j;
-    if (gi < n && gj < n) xout[I.off[l] + (long long)gj * n + gi] = xs[j + 2][i + 2];
+    px[kPre - 1] = s + 2 + kPre <= y1 + 1 ? ldx(s + 2 + kPre) : real(0);
+    pb[kPre - 1] = s + 1 + kPre <= y1 ? ldb(s + 1 + kPre) : real(0);
+    const real r_p = red(o_s, o_s1, o_s2, b_s1, s + 1);
+    // black cells of row s
+    const real lft = __shfl_up_sync(kFull, r_0, 1), rgt = __shfl_down_sync(kFull, r_0, 1);
+    const real v = (b_0 + (lft + rgt + r_m + r_p) * ih2) * idg;
+    const real outv = ((c + rowof(s)) & 1) == 1 ? v : r_0;
+    if (g.out_lane) xo[s * n + c] = outv;
+    r_m = r_0;
+    r_0 = r_p;
+    b_0 = b_s1;
+    o_s = o_s1;
+    o_s1 = o_s2;
   }
 }
 
-// copy of one 2D level tile (after an odd number of sweeps)
+// copy of one strip (after an odd number of sweeps)
 template <typename real>
-__global__ void copy2d_kernel(MgState S, const real* __restrict__ xin, real* __restrict__ xout, const Chunk* ch) {
-  Chunk C = ch[blockIdx.x];
+__global__ void __launch_bounds__(128) copy2d_kernel(MgState S, const real* __restrict__ xin, real* __restrict__ xout,
+                                                     const Chunk* ch, int nch) {
+  const int lane = threadIdx.x & 31;
+  const int wi = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (wi >= nch) return;
+  const Chunk C = ch[wi];
   if (!S.active[C.inst]) return;
   const InstDev& I = S.inst[C.inst];
-  const int l = C.lev, n = I.n[l], ntx = I.ntx[l];
-  const int tx0 = ((int)C.start % ntx) * kSwTX, ty0 = ((int)C.start / ntx) * kSwTY;
-  for (int k = threadIdx.x; k < kSwTX * kSwTY; k += blockDim.x) {
-    int gi = tx0 + k % kSwTX, gj = ty0 + k / kSwTX;
-    if (gi < n && gj < n) xout[I.off[l] + (long long)gj * n + gi] = xin[I.off[l] + (long long)gj * n + gi];
-  }
+  const StripGeom g = strip_geom(I.n[C.lev], C.start, C.count, lane);
+  if (!g.out_lane) return;
+  const long long o = I.off[C.lev];
+  for (int s = g.y0; s < g.y1; ++s) xout[o + s * g.n + g.c] = xin[o + s * g.n + g.c];
 }
 
 // 2D prolongation, one thread per coarse cell writing its four fine children
@@ -815,7 +853,6 @@ struct Mg {
         I.ih2f[l] = (float)I.ih2[l];
         I.idiag[l] = 1.0 / (lambda[i] + 2.0 * nd * I.ih2[l]);
         I.idiagf[l] = (float)I.idiag[l];
-        I.ntx[l] = (m + kSwTX - 1) / kSwTX;
         ++l;
         if ((m & 1) || m <= coarse_max) break;
         m /= 2;
@@ -857,8 +894,9 @@ struct Mg {
         add_chunks(ch_coarse[l], i, l, cc);
         add_chunks(ch_fine[l], i, l, cf);
         if (nd == 2) {
-          int nt = ((I.n[l] + kSwTX - 1) / kSwTX) * ((I.n[l] + kSwTY - 1) / kSwTY);
-          for (int k = 0; k < nt; ++k) ch_tile[l].push_back(Chunk{i, l, k, 1});
+          const int H = strip_height(I.n[l]);
+          int nt = ((I.n[l] + kStripW - 1) / kStripW) * ((I.n[l] + H - 1) / H);
+          for (int k = 0; k < nt; ++k) ch_tile[l].push_back(Chunk{i, l, k, H});
         }
       }
       long long m = 1;
@@ -927,15 +965,16 @@ struct Mg {
     auto smooth = [&](int l, int sweeps) {  // `sweeps` red-black sweeps of depth l
       if (nd == 2) {
         if (ch_tile[l].empty()) return;
-        unsigned nb = (unsigned)ch_tile[l].size();
+        const int nch = (int)ch_tile[l].size();
+        const unsigned nb = (unsigned)((nch + 3) / 4);
         const Chunk* tl = all + off_tile[l];
         for (int s = 0; s < sweeps; ++s) {
           bool even = (s & 1) == 0;
-          sweep2d_kernel<real><<<nb, 256, 0, stream>>>(S, even ? Lv.x : Y, even ? Y : Lv.x, Lv.b, tl);
+          sweep2d_kernel<real><<<nb, 128, 0, stream>>>(S, even ? Lv.x : Y, even ? Y : Lv.x, Lv.b, tl, nch);
           ++launches;
         }
         if (sweeps & 1) {
-          copy2d_kernel<real><<<nb, 256, 0, stream>>>(S, Y, Lv.x, tl);
+          copy2d_kernel<real><<<nb, 128, 0, stream>>>(S, Y, Lv.x, tl, nch);
           ++launches;
         }
         return;
