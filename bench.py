@@ -188,6 +188,17 @@ def bench_gray_scott(torch, amrvac, stream, steps=5):
            "vcycles_per_solve_mean": float(np.mean(cyc)), "vcycles_max": int(np.max(cyc)),
            "timing": "host wall clock around rd_step (synchronous), stream synchronized"}
     rd.close()
+    # accuracy of the FP32 path against the FP64 path (which matches the oracle, tests) after 5 steps
+    res = {}
+    for prec in ("fp32", "fp64"):
+        r = amrvac.RdSolver(2, sizes, 2.5, Du=2e-5, Dv=1e-5, F=0.04, k=0.06, dt=0.5, precision=prec,
+                            stream=stream.cuda_stream)
+        r.set_state(np.concatenate(us), np.concatenate(vs))
+        r.step(5)
+        res[prec] = r.read_state()[0]
+        r.close()
+    du = np.abs(res["fp32"] - res["fp64"]).sum() / np.abs(res["fp64"]).sum()
+    out["l1_u_fp32_vs_fp64_after_5_steps"] = float(du)
     return out
 
 
@@ -200,20 +211,50 @@ def bench_learned_guess(torch, amrvac, stream, eval_steps=6):
     t0 = time.perf_counter()
     X, Y, scale = LG.generate(torch, [n, n], [0, 1], L, steps=24, crops_per_step=48, crop=64, warm=40)
     net = amrvac.CnnNet(ndim=2, seed=3)
+    loss0 = LG.dataset_loss(torch, net, X, Y)
     losses, train_s = LG.train(torch, net, X, Y, iters=1500, batch=64, lr=1e-3)
+    loss1 = LG.dataset_loss(torch, net, X, Y)
     prep = time.perf_counter() - t0
     c0, t0s, _, r0 = LG.evaluate(torch, [2048], [10000], 2.5, steps=eval_steps, warm=40)
     c1, t1s, _, r1 = LG.evaluate(torch, [2048], [10000], 2.5, steps=eval_steps, warm=40, net=net, scale=scale)
     out = {"workload": "Gray-Scott IMEX 2048^2 (seed 10000, after 40 warm-up steps), MG rtol 1e-10",
            "training": f"{X.shape[0]} crops 64^2 from 256^2 runs (seeds 0,1, stiffness-matched domain), "
                        f"1500 Adam steps, batch 64, {train_s:.1f}s; data+training {prep:.1f}s",
-           "loss_first_last": [losses[0][1], float(np.mean([l for _, l in losses[-5:]]))],
+           "training_set_loss_before_after": [loss0, loss1],
            "vcycles_per_solve_previous_step_guess": float(np.mean(c0)),
            "vcycles_per_solve_learned_guess": float(np.mean(c1)),
            "initial_rel_residual_median_previous_step": float(np.median(r0)),
            "initial_rel_residual_median_learned": float(np.median(r1)),
            "ms_per_step_previous_step_guess": t0s * 1e3, "ms_per_step_learned_guess": t1s * 1e3,
            "cnn_launches": net.kernel_launches()}
+    net.close()
+    return out
+
+
+def bench_learned_guess_3d(torch, amrvac, stream, eval_steps=6):
+    """Config 5 (3D): train the learned guess on 64^3 runs with the stiffness of the 256^3 grid
+    (seeds 0, 1), evaluate at 256^3 on seed 10000 against the previous-step guess."""
+    from paper_2004_03275_gb300 import learned_guess as LG
+    n, N = 64, 256
+    L = LG.domain_for(n, ref_n=N, ref_L=2.5)
+    t0 = time.perf_counter()
+    X, Y, scale = LG.generate(torch, [n, n], [0, 1], L, steps=16, crops_per_step=12, crop=32, warm=20, ndim=3)
+    net = amrvac.CnnNet(ndim=3, seed=3)
+    loss0 = LG.dataset_loss(torch, net, X, Y)
+    losses, train_s = LG.train(torch, net, X, Y, iters=600, batch=4, lr=1e-3)
+    loss1 = LG.dataset_loss(torch, net, X, Y)
+    prep = time.perf_counter() - t0
+    c0, t0s, _, r0 = LG.evaluate(torch, [N], [10000], 2.5, steps=eval_steps, warm=20, ndim=3)
+    c1, t1s, _, r1 = LG.evaluate(torch, [N], [10000], 2.5, steps=eval_steps, warm=20, net=net, scale=scale, ndim=3)
+    out = {"workload": "Gray-Scott IMEX 256^3 on [0,2.5]^3 (seed 10000, after 20 warm-up steps), MG rtol 1e-10",
+           "training": f"{X.shape[0]} crops 32^3 from 64^3 runs (seeds 0,1, stiffness-matched domain), "
+                       f"600 Adam steps, batch 4, {train_s:.1f}s; data+training {prep:.1f}s",
+           "training_set_loss_before_after": [loss0, loss1],
+           "vcycles_per_solve_previous_step_guess": float(np.mean(c0)),
+           "vcycles_per_solve_learned_guess": float(np.mean(c1)),
+           "initial_rel_residual_median_previous_step": float(np.median(r0)),
+           "initial_rel_residual_median_learned": float(np.median(r1)),
+           "ms_per_step_previous_step_guess": t0s * 1e3, "ms_per_step_learned_guess": t1s * 1e3}
     net.close()
     return out
 
@@ -405,7 +446,7 @@ def main():
     ap.add_argument("--skip-extra", action="store_true", help="skip the Gray-Scott and blast configurations")
     ap.add_argument("--extras", default="all",
                     help="comma list of extra workloads: gray_scott_batch, mg_vcycle, blast3d, learned_guess_2d, "
-                         "cnn_forward_2048 (default all; 'none' for none)")
+                         "learned_guess_3d, cnn_forward_2048 (default all; 'none' for none)")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -474,6 +515,27 @@ def main():
         fp64 = {"value": ws * ncells * 3 / (ms64 * 1e-3), "ms_per_step": ms64, "steps": k64,
                 "stage_achieved_gbs": r64["achieved"], "stage_frac_hbm": r64["frac"],
                 "fp32_over_fp64": (ms64 / ms32)}
+        # accuracy of the FP32 path: both paths from the initial state to the time the FP64 path
+        # reaches in 100 steps (the configuration's run length); the FP64 GPU path matches the
+        # FP64 oracle to 1e-12 per cell (tests), so it stands in for the oracle at this size
+        if rank == 0:
+            s64.set_prim(V)
+            s64.set_time(0.0)
+            s64.run(100)
+            s64.sync()
+            t100 = s64.t
+            r64s = s64.read_state()[:, 0]
+            a32 = amrvac.AmrSolver(**kh_kwargs(precision="fp32", stream=stream.cuda_stream))
+            a32.set_prim(V)
+            for _ in range(4):
+                if a32.t >= t100:
+                    break
+                a32.run(100, t_end=t100)
+                a32.sync()
+            r32s = a32.read_state()[:, 0]
+            fp64["l1_rho_fp32_vs_fp64"] = float(np.abs(r32s - r64s).sum() / np.abs(r64s).sum())
+            fp64["l1_at"] = {"t": t100, "fp64_steps": 100, "t_fp32": a32.t}
+            a32.close()
         s64.close()
 
     # ---------------------------------------------------------------- end to end
@@ -504,12 +566,14 @@ def main():
 
     extra = {}
     if not args.skip_extra and rank == 0:
-        names = ["gray_scott_batch", "mg_vcycle", "blast3d", "learned_guess_2d", "cnn_forward_2048"]
+        names = ["gray_scott_batch", "mg_vcycle", "blast3d", "learned_guess_2d", "learned_guess_3d",
+                 "cnn_forward_2048"]
         want = names if args.extras == "all" else [e for e in args.extras.split(",") if e in names]
         runs = {"gray_scott_batch": lambda: bench_gray_scott(torch, amrvac, stream),
                 "mg_vcycle": lambda: bench_mg_vcycle(torch, amrvac, stream, hbm),
                 "blast3d": lambda: bench_blast(torch, amrvac, stream),
                 "learned_guess_2d": lambda: bench_learned_guess(torch, amrvac, stream),
+                "learned_guess_3d": lambda: bench_learned_guess_3d(torch, amrvac, stream),
                 "cnn_forward_2048": lambda: bench_cnn_forward(torch, amrvac, stream, bf16_peak())}
         for name in want:
             extra[name] = runs[name]()

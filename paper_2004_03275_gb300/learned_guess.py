@@ -32,19 +32,21 @@ def domain_for(n, ref_n=2048, ref_L=2.5):
     return ref_L * n / ref_n
 
 
-def start_state(sizes, L, seeds):
+def start_state(sizes, L, seeds, ndim=2):
     us, vs = [], []
     for n, sd in zip(sizes, seeds):
-        u, v = inputs.gray_scott_patches(n, L=L, seed=sd)
+        u, v = inputs.gray_scott_patches(n, ndim=ndim, L=L, seed=sd)
         us.append(u.ravel())
         vs.append(v.ravel())
     return np.concatenate(us), np.concatenate(vs)
 
 
-def generate(torch, sizes, seeds, L, steps, crops_per_step, crop=64, warm=0, scale=None, seed=0, stream=None):
-    """Returns (inputs [M][5][c][c], targets [M][2][c][c], scale) as CUDA float tensors."""
-    rd = amrvac.RdSolver(2, sizes, L, precision="fp32", stream=stream, **GS)
-    rd.set_state(*start_state(sizes, L, seeds))
+def generate(torch, sizes, seeds, L, steps, crops_per_step, crop=64, warm=0, scale=None, seed=0, stream=None,
+             ndim=2):
+    """Returns (inputs [M][5][c]^ndim, targets [M][2][c]^ndim, scale) as CUDA float tensors."""
+    rd = amrvac.RdSolver(ndim, sizes, L, precision="fp32", stream=stream, **GS)
+    rd.set_state(*start_state(sizes, L, seeds, ndim))
+    box = (crop,) * ndim
     if warm:
         rd.step(warm)
     rng = np.random.default_rng(seed)
@@ -55,14 +57,14 @@ def generate(torch, sizes, seeds, L, steps, crops_per_step, crop=64, warm=0, sca
         corners = np.zeros((crops_per_step, 3), dtype=np.int32)
         for k in range(crops_per_step):
             n = sizes[inst[k]]
-            corners[k, :2] = rng.integers(0, n, 2)
+            corners[k, :ndim] = rng.integers(0, n, ndim)
         if scale is None:  # RMS of w* - w_n over the first step's crops
-            xi = torch.empty((crops_per_step, 5, crop, crop), device="cuda")
-            yi = torch.empty((crops_per_step, 2, crop, crop), device="cuda")
+            xi = torch.empty((crops_per_step, 5) + box, device="cuda")
+            yi = torch.empty((crops_per_step, 2) + box, device="cuda")
             rd.extract_crops(inst, corners, crop, 1.0, xi, yi)
             scale = float(torch.sqrt(torch.mean(yi.double() ** 2)).item())
-        xi = torch.empty((crops_per_step, 5, crop, crop), device="cuda")
-        yi = torch.empty((crops_per_step, 2, crop, crop), device="cuda")
+        xi = torch.empty((crops_per_step, 5) + box, device="cuda")
+        yi = torch.empty((crops_per_step, 2) + box, device="cuda")
         rd.extract_crops(inst, corners, crop, scale, xi, yi)
         X.append(xi)
         Y.append(yi)
@@ -86,10 +88,20 @@ def train(torch, net, X, Y, iters, batch=32, lr=1e-3, margin=4, seed=1):
     return losses, time.perf_counter() - t0
 
 
-def evaluate(torch, sizes, seeds, L, steps, net=None, scale=1.0, warm=0, stream=None):
+def dataset_loss(torch, net, X, Y, margin=4, chunk=16):
+    """Masked MSE of the network over the whole data set (chunks in order, weighted by size)."""
+    tot = 0.0
+    for i in range(0, X.shape[0], chunk):
+        xb, yb = X[i:i + chunk].contiguous(), Y[i:i + chunk].contiguous()
+        loss, _ = net.gradient(xb, yb, margin=margin)
+        tot += loss * xb.shape[0]
+    return tot / X.shape[0]
+
+
+def evaluate(torch, sizes, seeds, L, steps, net=None, scale=1.0, warm=0, stream=None, ndim=2):
     """V-cycles per step (per species and instance) and wall time per step."""
-    rd = amrvac.RdSolver(2, sizes, L, precision="fp32", stream=stream, **GS)
-    rd.set_state(*start_state(sizes, L, seeds))
+    rd = amrvac.RdSolver(ndim, sizes, L, precision="fp32", stream=stream, **GS)
+    rd.set_state(*start_state(sizes, L, seeds, ndim))
     if warm:
         rd.step(warm)
     if net is not None:
