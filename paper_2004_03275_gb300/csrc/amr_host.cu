@@ -280,6 +280,7 @@ struct amr_handle {
   Geometry G{};
   // device state
   DBuf U0, Ua, Ub, Unew, stagebuf, partials, gpart, gcount, ctl, nb, level, ffx, slabdesc, slabbuf, rec, fflux, ops, errbuf;
+  DBuf xyscr;  // float32 3D 16^3: x + y flux differences of the stage (like the state)
   DevCtl* h_ctl = nullptr;  // pinned mirror
   long long steps_seen = 0;
   cudaGraphExec_t graph = nullptr;
@@ -323,7 +324,7 @@ struct amr_handle {
     amr_handle* h = this;
     mark_begin();
     CK((EulerOps<real, ND>::stage(B, cfg.flux, a, G, stream)));
-    ++launches;
+    launches += (std::is_same<real, float>::value && ND == 3 && B == 16) ? 2 : 1;  // 3D: xy and z passes
     mark(0);
     return AMR_OK;
   }
@@ -361,6 +362,7 @@ struct amr_handle {
       a.level = level.as<int>();
       a.ffx = ffx.as<int>();
       a.fflux = fflux.as<real>();
+      a.scratch = xyscr.as<real>();
       a.ctl = ctl.as<DevCtl>();
       a.partials = partials.as<double>();
       a.gpart = gpart.as<double>();
@@ -446,7 +448,8 @@ int upload_tables(amr_handle* h) {
   CKH(h->slabbuf.ensure(std::max<size_t>(1, tb.slabs.size()) * h->nv * 2 * h->nt * h->wbytes));
   CKH(h->rec.ensure(std::max<size_t>(1, tb.rec.size()) * sizeof(RefluxRec)));
   CKH(h->fflux.ensure(std::max<size_t>(1, (size_t)tb.nslots) * h->nv * h->nt * h->wbytes));
-  CKH(h->partials.ensure(std::max<size_t>(1, n) * h->nv * sizeof(double)));
+  // one partial per leaf, or per CTA of a stage kernel (up to 4 CTAs per leaf)
+  CKH(h->partials.ensure(std::max<size_t>(1, 4 * n) * h->nv * sizeof(double)));
   CKH(h->errbuf.ensure(std::max<size_t>(1, n) * sizeof(double)));
   CKH(cudaMemcpyAsync(h->nb.p, tb.nb.data(), n * nf * sizeof(int), cudaMemcpyHostToDevice, h->stream));
   CKH(cudaMemcpyAsync(h->ffx.p, tb.ffx.data(), n * nf * sizeof(int), cudaMemcpyHostToDevice, h->stream));
@@ -587,8 +590,9 @@ int amr_create(const amr_config* cfg, amr_handle** out) {
   cudaError_t e;
   if ((e = h->U0.ensure(sb)) != cudaSuccess || (e = h->Ua.ensure(sb)) != cudaSuccess ||
       (e = h->Ub.ensure(sb)) != cudaSuccess || (e = h->ctl.ensure(sizeof(DevCtl))) != cudaSuccess ||
-      (e = h->gpart.ensure(((size_t)cfg->max_blocks / kGroupCTAs + 2) * 5 * sizeof(double))) != cudaSuccess ||
-      (e = h->gcount.ensure(((size_t)cfg->max_blocks / kGroupCTAs + 2) * sizeof(unsigned))) != cudaSuccess ||
+      (e = h->gpart.ensure((4 * (size_t)cfg->max_blocks / kGroupCTAs + 2) * 5 * sizeof(double))) != cudaSuccess ||
+      (e = h->gcount.ensure((4 * (size_t)cfg->max_blocks / kGroupCTAs + 2) * sizeof(unsigned))) != cudaSuccess ||
+      (h->nd == 3 && h->B == 16 && h->wbytes == 4 && (e = h->xyscr.ensure(sb)) != cudaSuccess) ||
       (e = cudaMallocHost(&h->h_ctl, sizeof(DevCtl))) != cudaSuccess)
     return e == cudaErrorMemoryAllocation ? AMR_ERR_OOM : AMR_ERR_CUDA;
   DevCtl c0{};
@@ -612,7 +616,7 @@ int amr_create(const amr_config* cfg, amr_handle** out) {
 int amr_destroy(amr_handle* h) {
   if (!h) return AMR_ERR_INVALID_ARG;
   h->drop_graph();
-  for (DBuf* b : {&h->U0, &h->Ua, &h->Ub, &h->Unew, &h->stagebuf, &h->partials, &h->gpart, &h->gcount, &h->ctl, &h->nb, &h->level,
+  for (DBuf* b : {&h->xyscr, &h->U0, &h->Ua, &h->Ub, &h->Unew, &h->stagebuf, &h->partials, &h->gpart, &h->gcount, &h->ctl, &h->nb, &h->level,
                   &h->ffx, &h->slabdesc, &h->slabbuf, &h->rec, &h->fflux, &h->ops, &h->errbuf})
     b->release();
   if (h->h_ctl) cudaFreeHost(h->h_ctl);

@@ -69,6 +69,7 @@ struct StageArgs {
   const int* level;    // [leaf]
   const int* ffx;      // [leaf][2*ndim] face-flux slot or -1
   real* fflux;         // [slot][var][nt]
+  real* scratch;       // float32 3D 16^3 leaves: x + y flux differences, laid out like the state
   DevCtl* ctl;
   double* partials;    // [leaf][var]
   double* gpart;       // [group of CTAs][var]

@@ -6,6 +6,7 @@
 #include "euler_ops.h"
 #include "stage2d_f32.cuh"
 #include "stage2d_march.cuh"
+#include "stage3d_march.cuh"
 
 namespace amrgpu {
 
@@ -96,13 +97,58 @@ cudaError_t stage2d_f32_launch(const StageArgs<float>& a, const Geometry& G, cud
   return cudaGetLastError();
 }
 
+// float32 3D, 16^3 leaves: xy pass then z pass (4 CTAs of 4 warps per leaf each)
+template <int FLUX, int LIM>
+void stage3d_f32_go(const StageArgs<float>& a, const Geometry& G, cudaStream_t s) {
+  const int grid = a.nleaves * 4;
+  stage3d_xy_kernel<FLUX, LIM><<<grid, 128, kXy3Smem, s>>>(a, G);
+  if (a.fuse_reduce)
+    stage3d_z_kernel<FLUX, LIM, true><<<grid, 128, 0, s>>>(a, G);
+  else
+    stage3d_z_kernel<FLUX, LIM, false><<<grid, 128, 0, s>>>(a, G);
+}
+
+template <int FLUX>
+cudaError_t stage3d_f32_launch(const StageArgs<float>& a, const Geometry& G, cudaStream_t s) {
+  switch (a.limiter) {
+    case LIM_MINMOD: stage3d_f32_go<FLUX, LIM_MINMOD>(a, G, s); break;
+    case LIM_VANLEER: stage3d_f32_go<FLUX, LIM_VANLEER>(a, G, s); break;
+    case LIM_KOREN: stage3d_f32_go<FLUX, LIM_KOREN>(a, G, s); break;
+    default: stage3d_f32_go<FLUX, LIM_NONE>(a, G, s); break;
+  }
+  return cudaGetLastError();
+}
+
+template <int FLUX>
+cudaError_t stage3d_f32_prepare(int lim) {
+  switch (lim) {
+    case LIM_MINMOD:
+      return cudaFuncSetAttribute(stage3d_xy_kernel<FLUX, LIM_MINMOD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kXy3Smem);
+    case LIM_VANLEER:
+      return cudaFuncSetAttribute(stage3d_xy_kernel<FLUX, LIM_VANLEER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kXy3Smem);
+    case LIM_KOREN:
+      return cudaFuncSetAttribute(stage3d_xy_kernel<FLUX, LIM_KOREN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kXy3Smem);
+    default:
+      return cudaFuncSetAttribute(stage3d_xy_kernel<FLUX, LIM_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kXy3Smem);
+  }
+}
+
 // opt in to the 3D kernel's dynamic shared memory (outside any stream capture)
 template <typename real, int ND, int B, int FLUX>
 cudaError_t stage_prepare(int lim) {
   if constexpr (std::is_same<real, float>::value && ND == 2) return stage2d_f32_prepare<B, FLUX>(lim);
-  if constexpr (ND == 3)
+  if constexpr (ND == 3) {
+    if constexpr (std::is_same<real, float>::value && B == 16) {
+      cudaError_t e = stage3d_f32_prepare<FLUX>(lim);
+      if (e != cudaSuccess) return e;
+    }
     return cudaFuncSetAttribute(stage_kernel_3d<real, B, FLUX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(Stage3DSmem<real, B>));
+  }
   return cudaSuccess;
 }
 
@@ -114,6 +160,14 @@ cudaError_t stage_b(int flux, const StageArgs<real>& a, const Geometry& G, cudaS
       case FLUX_TVDLF: return stage2d_f32_launch<B, FLUX_TVDLF>(a, G, s);
       case FLUX_HLL: return stage2d_f32_launch<B, FLUX_HLL>(a, G, s);
       default: return stage2d_f32_launch<B, FLUX_HLLC>(a, G, s);
+    }
+  }
+  if constexpr (std::is_same<real, float>::value && ND == 3 && B == 16) {
+    if (a.nleaves == 0) return cudaSuccess;
+    switch (flux) {
+      case FLUX_TVDLF: return stage3d_f32_launch<FLUX_TVDLF>(a, G, s);
+      case FLUX_HLL: return stage3d_f32_launch<FLUX_HLL>(a, G, s);
+      default: return stage3d_f32_launch<FLUX_HLLC>(a, G, s);
     }
   }
   switch (flux) {
