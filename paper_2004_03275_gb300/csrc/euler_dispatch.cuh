@@ -103,9 +103,9 @@ void stage3d_f32_go(const StageArgs<float>& a, const Geometry& G, cudaStream_t s
   const int grid = a.nleaves * 4;
   stage3d_xy_kernel<FLUX, LIM><<<grid, 128, kXy3Smem, s>>>(a, G);
   if (a.fuse_reduce)
-    stage3d_z_kernel<FLUX, LIM, true><<<grid, 128, 0, s>>>(a, G);
+    stage3d_z_kernel<FLUX, LIM, true><<<grid, 128, kZSmem, s>>>(a, G);
   else
-    stage3d_z_kernel<FLUX, LIM, false><<<grid, 128, 0, s>>>(a, G);
+    stage3d_z_kernel<FLUX, LIM, false><<<grid, 128, kZSmem, s>>>(a, G);
 }
 
 template <int FLUX>
@@ -119,8 +119,23 @@ cudaError_t stage3d_f32_launch(const StageArgs<float>& a, const Geometry& G, cud
   return cudaGetLastError();
 }
 
+template <int FLUX, int LIM>
+cudaError_t stage3d_z_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(stage3d_z_kernel<FLUX, LIM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kZSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(stage3d_z_kernel<FLUX, LIM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kZSmem);
+  return e;
+}
+
 template <int FLUX>
 cudaError_t stage3d_f32_prepare(int lim) {
+  cudaError_t e = lim == LIM_MINMOD    ? stage3d_z_prepare<FLUX, LIM_MINMOD>()
+                  : lim == LIM_VANLEER ? stage3d_z_prepare<FLUX, LIM_VANLEER>()
+                  : lim == LIM_KOREN   ? stage3d_z_prepare<FLUX, LIM_KOREN>()
+                                       : stage3d_z_prepare<FLUX, LIM_NONE>();
+  if (e != cudaSuccess) return e;
   switch (lim) {
     case LIM_MINMOD:
       return cudaFuncSetAttribute(stage3d_xy_kernel<FLUX, LIM_MINMOD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -224,7 +239,7 @@ cudaError_t EulerOps<real, ND>::ghost_fill(int B, const real* U, real* slabs, co
   if (nslabs == 0) return cudaSuccess;
 #define CALL(BB)                                                                                  \
   ([&]() {                                                                                        \
-    long long n = (long long)nslabs * (ND + 2) * 2 * Tile<ND, BB>::NT;                            \
+    long long n = (long long)nslabs * 2 * Tile<ND, BB>::NT;                                       \
     ghost_fill_kernel<real, ND, BB><<<detail::blocks_for(n, 256), 256, 0, s>>>(U, slabs, desc, nslabs); \
     return cudaGetLastError();                                                                    \
   }())

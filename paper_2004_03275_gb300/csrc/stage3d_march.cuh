@@ -308,20 +308,46 @@ __global__ void __launch_bounds__(128, 4) stage3d_xy_kernel(StageArgs<float> a, 
 }
 
 // ---- z pass: warp w of CTA b handles row j = (b & 3) * 4 + w of leaf b >> 2; lane (i, half)
+// z-pass staging: U^(s), D and U^n of the CTA's 4 rows of the leaf for all 16 planes,
+// [array][var][plane][row][i] with a plane stride of 66 floats, so that the two half-warps
+// (planes k and k + 8) fall on different banks
+constexpr int kZPlane = 66, kZVar = 16 * kZPlane;
+constexpr size_t kZSmem = 3 * 5 * kZVar * sizeof(float);  // 63.4 KB
+
 template <int FLUX, int LIM, bool LAST>
-__global__ void __launch_bounds__(128, 4) stage3d_z_kernel(StageArgs<float> a, Geometry G) {
+__global__ void __launch_bounds__(128, 3) stage3d_z_kernel(StageArgs<float> a, Geometry G) {
   constexpr int B = 16, NC = B * B * B, NV = 5, NT = B * B;
   __shared__ float red[4][2 * NV + 1];
   __shared__ int sbad;
+  extern __shared__ __align__(16) float zst[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int leaf = blockIdx.x >> 2, j = ((blockIdx.x & 3) << 2) + warp;
+  const int leaf = blockIdx.x >> 2, j0 = (blockIdx.x & 3) << 2, j = j0 + warp;
   const bool active = leaf < a.nleaves;
   const int i = lane & 15, h = lane >> 4, c0 = h * 8;
   if (threadIdx.x == 0) sbad = 0;
+  // ---- stage U^(s), D and U^n of rows j0..j0+3 (64 contiguous floats per variable and plane)
+  if (active) {
+    // thread t: 16-byte column q = t & 15 of planes k0 = t >> 4 and k0 + 8, every array and variable
+    const int q = threadIdx.x & 15, k0 = threadIdx.x >> 4;
+    const size_t lb = (size_t)leaf * NV * NC + j0 * B + k0 * NT;
+    const float* src3[3] = {a.Us, a.scratch, a.U0};
+#pragma unroll
+    for (int arr = 0; arr < 3; ++arr) {
+      if (arr == 2 && a.stage1) break;
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          const float4 x4 = __ldg(reinterpret_cast<const float4*>(src3[arr] + lb + (size_t)v * NC + p * 8 * NT) + q);
+          float2* dst = reinterpret_cast<float2*>(zst + (arr * NV + v) * kZVar + (k0 + 8 * p) * kZPlane + 4 * q);
+          dst[0] = make_float2(x4.x, x4.y);
+          dst[1] = make_float2(x4.z, x4.w);
+        }
+    }
+  }
   // ghost cells of the pencil beyond its z faces: h = 0 takes planes -2, -1 (face z-),
   // h = 1 planes 16, 17 (face z+); g[0] is the layer next to the leaf, g[1] the outer one
   float gz[2][NV];
-  const float* Ul = a.Us + (size_t)leaf * NV * NC;
   if (active) {
     const int f = 4 + h, code = __ldg(&a.nb[leaf * 6 + f]);
 #pragma unroll
@@ -341,7 +367,7 @@ __global__ void __launch_bounds__(128, 4) stage3d_z_kernel(StageArgs<float> a, G
     }
   }
   float dt;
-  const double dtd = cta_stage_dt(a.ctl, &dt);
+  const double dtd = cta_stage_dt(a.ctl, &dt);  // its barrier also publishes the staged arrays
   if (!(dt > 0.f)) return;
   const float gam = G.gammaf, gm1 = gam - 1.f, igm1 = 1.f / gm1;
   float rate = 0.f;
@@ -352,6 +378,9 @@ __global__ void __launch_bounds__(128, 4) stage3d_z_kernel(StageArgs<float> a, G
     const float idx = G.idxf[lev][0], idy = G.idxf[lev][1], idz = G.idxf[lev][2];
     const float vscale = __int_as_float((127 - 3 * (lev - 1)) << 23);  // 8^-(lev-1), exact
     const int col = i + B * j;
+    const float* sU = zst + 0 * NV * kZVar + warp * 16 + i;  // + v * kZVar + k * kZPlane
+    const float* sD = zst + 1 * NV * kZVar + warp * 16 + i;
+    const float* sU0 = zst + 2 * NV * kZVar + warp * 16 + i;
     // conserved cell of plane kk of the pencil (ghost planes from gz)
     auto cellU = [&](int kk, float* u) {
       if (kk < 0 || kk >= B) {
@@ -360,38 +389,31 @@ __global__ void __launch_bounds__(128, 4) stage3d_z_kernel(StageArgs<float> a, G
         for (int v = 0; v < NV; ++v) u[v] = outer ? gz[1][v] : gz[0][v];
       } else {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) u[v] = __ldg(&Ul[v * NC + kk * NT + col]);
+        for (int v = 0; v < NV; ++v) u[v] = sU[v * kZVar + kk * kZPlane];
       }
     };
-    const float* D = a.scratch + (size_t)leaf * NV * NC + col;
-    const float* U0l = a.U0 + (size_t)leaf * NV * NC + col;
     float* Ol = a.out + (size_t)leaf * NV * NC + col;
-    float um[NV], u0[NV], up[NV], wm[NV], w0[NV], wp[NV], lo[NV], hiPrev[NV], Fp[NV];
-    cellU(c0 - 2, um);
-    cellU(c0 - 1, u0);
+    float up[NV], wm[NV], w0[NV], wp[NV], lo[NV], hiPrev[NV], Fp[NV];
+    cellU(c0 - 2, up);
+    march3::prim5(up, gm1, wm);
+    cellU(c0 - 1, up);
+    march3::prim5(up, gm1, w0);
     cellU(c0, up);
-    march3::prim5(um, gm1, wm);
-    march3::prim5(u0, gm1, w0);
     march3::prim5(up, gm1, wp);
     march3::faces5<LIM>(wm, w0, wp, lo, hiPrev);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      um[v] = u0[v];
-      u0[v] = up[v];
       wm[v] = w0[v];
       w0[v] = wp[v];
     }
-    // D and U^n of the next cell to finish, loaded one step ahead
-    float dn[NV], u0n[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      dn[v] = __ldg(&D[v * NC + c0 * NT]);
-      u0n[v] = a.stage1 ? 0.f : __ldg(&U0l[v * NC + c0 * NT]);
-    }
+    float un[NV];
+    cellU(c0 + 1, un);
 #pragma unroll
     for (int kk = 0; kk <= 8; ++kk) {
       const int cc = c0 + kk;  // plane whose slope is formed; face cc-1/2
-      cellU(cc + 1, up);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) up[v] = un[v];
+      if (kk < 8) cellU(cc + 2, un);
       march3::prim5(up, gm1, wp);
       float hi[NV], F[NV];
       march3::faces5<LIM>(wm, w0, wp, lo, hi);
@@ -403,23 +425,18 @@ __global__ void __launch_bounds__(128, 4) stage3d_z_kernel(StageArgs<float> a, G
           for (int v = 0; v < NV; ++v) a.fflux[((size_t)slot * NV + v) * NT + col] = F[v];
       }
       if (kk > 0) {
-        const int r = cc - 1;  // plane of the cell finished now: its conserved value is um
-        float dc[NV], u0c[NV];
+        const int r = cc - 1;  // plane of the cell finished now
+        float uc[NV], dc[NV], u0c[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          dc[v] = dn[v];
-          u0c[v] = u0n[v];
+          uc[v] = sU[v * kZVar + r * kZPlane];
+          dc[v] = sD[v * kZVar + r * kZPlane];
+          u0c[v] = a.stage1 ? 0.f : sU0[v * kZVar + r * kZPlane];
         }
-        if (kk < 8)
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            dn[v] = __ldg(&D[v * NC + (r + 1) * NT]);
-            u0n[v] = a.stage1 ? 0.f : __ldg(&U0l[v * NC + (r + 1) * NT]);
-          }
         float Un[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          float tmp = um[v] - dt * (dc[v] + (F[v] - Fp[v]) * idz);
+          float tmp = uc[v] - dt * (dc[v] + (F[v] - Fp[v]) * idz);
           Un[v] = a.stage1 ? tmp : a.alpha * u0c[v] + a.beta * tmp;
           Ol[v * NC + r * NT] = Un[v];
         }
@@ -437,8 +454,6 @@ __global__ void __launch_bounds__(128, 4) stage3d_z_kernel(StageArgs<float> a, G
       for (int v = 0; v < NV; ++v) {
         Fp[v] = F[v];
         hiPrev[v] = hi[v];
-        um[v] = u0[v];
-        u0[v] = up[v];
         wm[v] = w0[v];
         w0[v] = wp[v];
       }
