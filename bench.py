@@ -118,6 +118,22 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_max(dist, x, device):
+    """Max of x over the ranks of the process group (identity without one); the timing of a
+    replica run is the slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank, ws, ms_max):
+    """Whole-job throughput of ws independent replicas: all ranks' units over the slowest time."""
+    return ws * units_per_rank / (ms_max * 1e-3)
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -468,11 +484,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(dist, x, "cuda")
 
     # a real (non-legacy) stream shared by the library and the timing events
     stream = torch.cuda.Stream()
@@ -497,7 +509,7 @@ def main():
     barrier()
     clocks = clk.stop() if rank == 0 else None
     ms32 = max_over_ranks(ms32)
-    value = ws * ncells * 3 / (ms32 * 1e-3)
+    value = replica_value(ncells * 3, ws, ms32)
     roof = stage_roofline(s32, 5, 4, 4, ncells, hbm, traffic=STAGE2D_F32_TRAFFIC)
     roof["peak_source"] = peak_src
 
