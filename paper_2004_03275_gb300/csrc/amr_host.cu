@@ -21,6 +21,7 @@
 
 #include "../../include/amrvac_gb300.h"
 #include "euler_ops.h"
+#include "tma.cuh"
 
 using namespace amrgpu;
 
@@ -281,6 +282,14 @@ struct amr_handle {
   // device state
   DBuf U0, Ua, Ub, Unew, stagebuf, partials, gpart, gcount, ctl, nb, level, ffx, slabdesc, slabbuf, rec, fflux, ops, errbuf;
   DBuf xyscr;  // float32 3D 16^3: x + y flux differences of the stage (like the state)
+  // float32 2D 16^2: TMA tensor maps of the three state buffers viewed as [leaf*4 + var][256]
+  CUtensorMap tmaps[3];
+  const void* tmap_base[3] = {nullptr, nullptr, nullptr};
+  const void* tmap_for(const void* p) const {
+    for (int k = 0; k < 3; ++k)
+      if (tmap_base[k] == p) return &tmaps[k];
+    return nullptr;
+  }
   DevCtl* h_ctl = nullptr;  // pinned mirror
   long long steps_seen = 0;
   cudaGraphExec_t graph = nullptr;
@@ -363,6 +372,7 @@ struct amr_handle {
       a.ffx = ffx.as<int>();
       a.fflux = fflux.as<real>();
       a.scratch = xyscr.as<real>();
+      a.tmap_us = tmap_for(Us);
       a.ctl = ctl.as<DevCtl>();
       a.partials = partials.as<double>();
       a.gpart = gpart.as<double>();
@@ -462,6 +472,13 @@ int upload_tables(amr_handle* h) {
                         h->stream));
   CKH(cudaStreamSynchronize(h->stream));
   h->G.nleaves = (int)n;
+  if (h->nd == 2 && h->B == 16 && h->wbytes == 4 && n > 0) {
+    const DBuf* bufs[3] = {&h->U0, &h->Ua, &h->Ub};
+    for (int k = 0; k < 3; ++k) {
+      CKH(encode_tmap_2d(&h->tmaps[k], bufs[k]->as<float>(), (uint64_t)n * 4, 256, 256, 4));
+      h->tmap_base[k] = bufs[k]->p;
+    }
+  }
   h->drop_graph();
   return AMR_OK;
 }
@@ -488,6 +505,7 @@ int refresh_reduce(amr_handle* h) {
 int sync_ctl(amr_handle* h) {
   CKH(cudaMemcpyAsync(h->h_ctl, h->ctl.p, sizeof(DevCtl), cudaMemcpyDeviceToHost, h->stream));
   CKH(cudaStreamSynchronize(h->stream));
+  if (h->h_ctl->status & 2) return h->fail(AMR_ERR_TIMEOUT, "a bounded wait for a TMA copy gave up");
   if (h->h_ctl->status & 1) return h->fail(AMR_ERR_NONPHYSICAL, "non-positive density or pressure met");
   return AMR_OK;
 }

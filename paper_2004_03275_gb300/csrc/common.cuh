@@ -70,6 +70,7 @@ struct StageArgs {
   const int* ffx;      // [leaf][2*ndim] face-flux slot or -1
   real* fflux;         // [slot][var][nt]
   real* scratch;       // float32 3D 16^3 leaves: x + y flux differences, laid out like the state
+  const void* tmap_us; // float32 2D 16^2 leaves: host pointer to the TMA tensor map of Us ([leaf*4+var][256])
   DevCtl* ctl;
   double* partials;    // [leaf][var]
   double* gpart;       // [group of CTAs][var]

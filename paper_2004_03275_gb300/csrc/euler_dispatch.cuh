@@ -71,12 +71,14 @@ void stage2d_f32_go(const StageArgs<float>& a, const Geometry& G, cudaStream_t s
   if constexpr (B == 16) {
     int grid = (a.nleaves + kMarchWarps - 1) / kMarchWarps;
     int cap = stage2d_f32_grid<B, FLUX, LIM>();
+    const CUtensorMap& tm = *static_cast<const CUtensorMap*>(a.tmap_us);
     if (a.fuse_reduce)
-      stage2d_march_kernel<FLUX, LIM, kStageLast><<<cap > 0 && cap < grid ? cap : grid, 32 * kMarchWarps, 0, s>>>(a, G);
+      stage2d_march_kernel<FLUX, LIM, kStageLast>
+          <<<cap > 0 && cap < grid ? cap : grid, 32 * kMarchWarps, 0, s>>>(a, G, tm);
     else if (a.stage1)
-      stage2d_march_kernel<FLUX, LIM, kStageFirst><<<grid, 32 * kMarchWarps, 0, s>>>(a, G);
+      stage2d_march_kernel<FLUX, LIM, kStageFirst><<<grid, 32 * kMarchWarps, 0, s>>>(a, G, tm);
     else
-      stage2d_march_kernel<FLUX, LIM, kStageMid><<<grid, 32 * kMarchWarps, 0, s>>>(a, G);
+      stage2d_march_kernel<FLUX, LIM, kStageMid><<<grid, 32 * kMarchWarps, 0, s>>>(a, G, tm);
     return;
   }
   constexpr int LPB = 256 / (B * B);
@@ -88,6 +90,7 @@ void stage2d_f32_go(const StageArgs<float>& a, const Geometry& G, cudaStream_t s
 
 template <int B, int FLUX>
 cudaError_t stage2d_f32_launch(const StageArgs<float>& a, const Geometry& G, cudaStream_t s) {
+  if (B == 16 && !a.tmap_us) return cudaErrorInvalidValue;  // the march kernel needs the state's tensor map
   switch (a.limiter) {
     case LIM_MINMOD: stage2d_f32_go<B, FLUX, LIM_MINMOD>(a, G, s); break;
     case LIM_VANLEER: stage2d_f32_go<B, FLUX, LIM_VANLEER>(a, G, s); break;
