@@ -349,7 +349,7 @@ def bench_cnn_forward(torch, amrvac, stream, peak_tflops):
                                                   "flop_per_pixel": CNN_FLOP_PER_PIXEL_2D}}
 
 
-def bench_blast(torch, amrvac, stream, steps=20, regrid_every=10):
+def bench_blast(torch, amrvac, stream, hbm_gbs, steps=20, regrid_every=10):
     """Config 3: 3D blast, 4^3 base blocks of 16^3, 4 levels (effective 512^3), HLLC + Koren, SSPRK3,
     FP32 state, regrid every 10 steps.  cell-updates/s per RK stage excluding regrid time."""
     from paper_2004_03275_gb300 import inputs
@@ -382,11 +382,42 @@ def bench_blast(torch, amrvac, stream, steps=20, regrid_every=10):
         t0 = time.perf_counter()
         s.regrid()
         t_regrid += time.perf_counter() - t0
+    rate = 3 * cells_steps / (step_ms * 1e-3)
+    # algorithmic bytes per cell-stage, SSPRK3 mean: (2 + 3 + 3) / 3 stages x 5 variables x 4 bytes
+    bps = 8.0 / 3.0 * 5 * 4
     out = {"workload": "3D blast, base 4^3 x 16^3, max_level 4 (eff. 512^3), HLLC+Koren, SSPRK3, FP32",
-           "steps": steps, "cell_stage_updates_per_s": 3 * cells_steps / (step_ms * 1e-3),
+           "steps": steps, "cell_stage_updates_per_s": rate,
            "ms_per_step_mean": step_ms / steps, "regrid_ms_mean": t_regrid * 1e3 / max(1, steps // regrid_every),
-           "blocks_per_level_at_each_regrid": levels}
+           "blocks_per_level_at_each_regrid": levels,
+           "roofline": {"bound": "hbm", "bytes_per_cell_stage": round(bps, 2), "achieved": round(rate * bps / 1e9, 1),
+                        "peak": hbm_gbs, "unit": "GB/s", "frac": round(rate * bps / 1e9 / hbm_gbs, 4),
+                        "scope": "whole step: stage passes, level-jump ghost fill, reflux, reductions; regrid excluded"}}
     s.close()
+    # accuracy of the FP32 path: both precisions on the same tree (built by the FP64 solver) and
+    # initial state, 10 steps without regrid; the FP64 GPU path matches the oracle (tests)
+    k64 = dict(kw, precision="fp64")
+    s64 = amrvac.AmrSolver(**k64)
+    for it in range(4):
+        lev, crd = s64.leaves()
+        x, _ = inputs.cell_centres(lev, crd, 3, 16, [4, 4, 4], [0, 0, 0], [1, 1, 1])
+        V = inputs.blast(x, seed=7)
+        s64.set_prim(V)
+        if it < 3:
+            s64.regrid()
+    s32 = amrvac.AmrSolver(**kw)
+    s32.set_leaves(lev, crd)
+    s32.set_prim(V)
+    s64.run(10)
+    s64.sync()
+    for _ in range(4):  # to the FP64 path's time (float32 dt may differ in the last digits)
+        if s32.t >= s64.t:
+            break
+        s32.run(10, t_end=s64.t)
+        s32.sync()
+    r64, r32 = s64.read_state()[:, 0], s32.read_state()[:, 0]
+    out["l1_rho_fp32_vs_fp64_10_steps"] = float(np.abs(r32 - r64).sum() / np.abs(r64).sum())
+    s64.close()
+    s32.close()
     return out
 
 
@@ -583,7 +614,7 @@ def main():
         want = names if args.extras == "all" else [e for e in args.extras.split(",") if e in names]
         runs = {"gray_scott_batch": lambda: bench_gray_scott(torch, amrvac, stream),
                 "mg_vcycle": lambda: bench_mg_vcycle(torch, amrvac, stream, hbm),
-                "blast3d": lambda: bench_blast(torch, amrvac, stream),
+                "blast3d": lambda: bench_blast(torch, amrvac, stream, hbm),
                 "learned_guess_2d": lambda: bench_learned_guess(torch, amrvac, stream),
                 "learned_guess_3d": lambda: bench_learned_guess_3d(torch, amrvac, stream),
                 "cnn_forward_2048": lambda: bench_cnn_forward(torch, amrvac, stream, bf16_peak())}

@@ -804,11 +804,13 @@ template <typename real, int ND, int B>
 __global__ void ghost_fill_kernel(const real* __restrict__ U, real* __restrict__ slabs,
                                   const SlabDesc* __restrict__ desc, int nslabs) {
   constexpr int NV = ND + 2, NC = Tile<ND, B>::NC, NT = Tile<ND, B>::NT;
-  // one thread per (slab, layer, tangential cell); the geometry is shared by the variables
+  // 2 NT threads per slab.  Restriction slabs: one thread per (layer, tangential cell).
+  // Prolongation slabs: the first NT / 2^(ND-1) threads, one per coarse face cell, each
+  // writing the 2 layers x 2^(ND-1) fine ghost cells that share its coarse value, inner
+  // restriction and slopes.  The geometry is shared by the variables.
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= nslabs * 2 * NT) return;
-  const int t = gid % NT;
-  const int m = (gid / NT) % 2;
+  const int q = gid % (2 * NT);
   const int s = gid / (2 * NT);
   SlabDesc D = desc[s];
   int d = D.face >> 1, side = D.face & 1;
@@ -817,16 +819,16 @@ __global__ void ghost_fill_kernel(const real* __restrict__ U, real* __restrict__
     if (e != d) {
       if (e1 < 0) e1 = e; else e2 = e;
     }
-  int tl[3] = {0, 0, 0};
-  if (e1 >= 0) tl[e1] = t % B;
-  if (e2 >= 0) tl[e2] = t / B;
   const real inv = real(1) / real(1 << ND);
+  if (D.kind == 0) {
+    const int t = q % NT, m = q / NT;
+    int tl[3] = {0, 0, 0};
+    if (e1 >= 0) tl[e1] = t % B;
+    if (e2 >= 0) tl[e2] = t / B;
+    int q1 = e1 >= 0 ? tl[e1] / (B / 2) : 0, q2 = e2 >= 0 ? tl[e2] / (B / 2) : 0;
+    int F = D.src[q1 + 2 * q2];
 #pragma unroll 1
-  for (int v = 0; v < NV; ++v) {
-    real val;
-    if (D.kind == 0) {
-      int q1 = e1 >= 0 ? tl[e1] / (B / 2) : 0, q2 = e2 >= 0 ? tl[e2] / (B / 2) : 0;
-      int F = D.src[q1 + 2 * q2];
+    for (int v = 0; v < NV; ++v) {
       real sum = real(0);
       for (int o = 0; o < (1 << ND); ++o) {
         int loc[3] = {0, 0, 0};
@@ -837,61 +839,74 @@ __global__ void ghost_fill_kernel(const real* __restrict__ U, real* __restrict__
         }
         sum = sum + U[((size_t)F * NV + v) * NC + loc[0] + B * (loc[1] + B * loc[2])];
       }
-      val = sum * inv;
-    } else {
-      int Cl = D.src[0];
-      int p[3] = {0, 0, 0};
-      real sg[3];
-      for (int e = 0; e < ND; ++e) {
-        if (e == d) {
-          p[e] = side == 0 ? B - 1 : 0;
-          sg[e] = (side == 0) == (m == 0) ? real(1) : real(-1);
-        } else {
-          int off = (e == e1) ? D.off[0] : D.off[1];
-          p[e] = off + tl[e] / 2;
-          sg[e] = (tl[e] & 1) ? real(1) : real(-1);
-        }
-      }
-      auto cval = [&](const int* c) { return U[((size_t)Cl * NV + v) * NC + c[0] + B * (c[1] + B * c[2])]; };
-      real qp = cval(p);
-      // restriction of the target's fine cells next to the face (normal inner neighbour)
-      real inner;
-      {
-        real sum = real(0);
-        for (int o = 0; o < (1 << ND); ++o) {
-          int loc[3] = {0, 0, 0};
-          for (int e = 0; e < ND; ++e) {
-            int oe = (o >> e) & 1;
-            if (e == d) loc[e] = (side == 0 ? 0 : B - 2) + oe;
-            else loc[e] = 2 * (tl[e] / 2) + oe;
-          }
-          sum = sum + U[((size_t)D.target * NV + v) * NC + loc[0] + B * (loc[1] + B * loc[2])];
-        }
-        inner = sum * inv;
-      }
-      real acc = real(0);
-      for (int e = 0; e < ND; ++e) {
-        real qm, qq;
-        bool ok = true;
-        int c[3] = {p[0], p[1], p[2]};
-        if (e == d) {
-          c[e] = side == 0 ? p[e] - 1 : p[e] + 1;
-          real away = cval(c);
-          if (side == 0) { qm = away; qq = inner; } else { qm = inner; qq = away; }
-        } else {
-          int cm[3] = {p[0], p[1], p[2]}, cp[3] = {p[0], p[1], p[2]};
-          cm[e] -= 1;
-          cp[e] += 1;
-          ok = cm[e] >= 0 && cp[e] < B;
-          qm = ok ? cval(cm) : real(0);
-          qq = ok ? cval(cp) : real(0);
-        }
-        real sl = ok ? minmod2(qp - qm, qq - qp) : real(0);
-        acc = acc + sg[e] * sl;
-      }
-      val = qp + real(0.25) * acc;
+      slabs[(((size_t)s * NV + v) * 2 + m) * NT + t] = sum * inv;
     }
-    slabs[(((size_t)s * NV + v) * 2 + m) * NT + t] = val;
+    return;
+  }
+  // prolongation: coarse face cell (c1, c2) in the target's tangential half-resolution grid
+  constexpr int HB = B / 2, NCC = ND == 1 ? 1 : (ND == 2 ? HB : HB * HB);
+  if (q >= NCC) return;
+  const int c1 = ND >= 2 ? q % HB : 0, c2 = ND == 3 ? q / HB : 0;
+  const int Cl = D.src[0];
+  int p[3] = {0, 0, 0}, cc[3] = {0, 0, 0};  // coarse cell; the target's coarse-cell index per direction
+  if (e1 >= 0) cc[e1] = c1;
+  if (e2 >= 0) cc[e2] = c2;
+  for (int e = 0; e < ND; ++e) {
+    if (e == d) p[e] = side == 0 ? B - 1 : 0;
+    else p[e] = ((e == e1) ? D.off[0] : D.off[1]) + cc[e];
+  }
+#pragma unroll 1
+  for (int v = 0; v < NV; ++v) {
+    auto cval = [&](const int* c) { return U[((size_t)Cl * NV + v) * NC + c[0] + B * (c[1] + B * c[2])]; };
+    const real qp = cval(p);
+    // restriction of the target's fine cells next to the face (normal inner neighbour)
+    real inner;
+    {
+      real sum = real(0);
+      for (int o = 0; o < (1 << ND); ++o) {
+        int loc[3] = {0, 0, 0};
+        for (int e = 0; e < ND; ++e) {
+          int oe = (o >> e) & 1;
+          if (e == d) loc[e] = (side == 0 ? 0 : B - 2) + oe;
+          else loc[e] = 2 * cc[e] + oe;
+        }
+        sum = sum + U[((size_t)D.target * NV + v) * NC + loc[0] + B * (loc[1] + B * loc[2])];
+      }
+      inner = sum * inv;
+    }
+    real sl[3] = {real(0), real(0), real(0)};
+    for (int e = 0; e < ND; ++e) {
+      real qm, qq;
+      bool ok = true;
+      int c[3] = {p[0], p[1], p[2]};
+      if (e == d) {
+        c[e] = side == 0 ? p[e] - 1 : p[e] + 1;
+        real away = cval(c);
+        if (side == 0) { qm = away; qq = inner; } else { qm = inner; qq = away; }
+      } else {
+        int cm[3] = {p[0], p[1], p[2]}, cp[3] = {p[0], p[1], p[2]};
+        cm[e] -= 1;
+        cp[e] += 1;
+        ok = cm[e] >= 0 && cp[e] < B;
+        qm = ok ? cval(cm) : real(0);
+        qq = ok ? cval(cp) : real(0);
+      }
+      sl[e] = ok ? minmod2(qp - qm, qq - qp) : real(0);
+    }
+    // the fine ghost cells of this coarse cell: layer m, fine offsets (a, b) along (e1, e2)
+    for (int m = 0; m < 2; ++m)
+      for (int b = 0; b < (ND == 3 ? 2 : 1); ++b)
+        for (int a = 0; a < (ND >= 2 ? 2 : 1); ++a) {
+          real acc = real(0);
+          for (int e = 0; e < ND; ++e) {
+            real sg;
+            if (e == d) sg = (side == 0) == (m == 0) ? real(1) : real(-1);
+            else sg = ((e == e1 ? a : b) == 1) ? real(1) : real(-1);
+            acc = acc + sg * sl[e];
+          }
+          const int t = ND == 1 ? 0 : (ND == 2 ? 2 * c1 + a : (2 * c1 + a) + B * (2 * c2 + b));
+          slabs[(((size_t)s * NV + v) * 2 + m) * NT + t] = qp + real(0.25) * acc;
+        }
   }
 }
 
