@@ -1,0 +1,76 @@
+"""GPU parity of the float32 march stage kernels (16^2 and 16^3 leaves) on the paths
+the uniform periodic tests do not reach: level jumps (slab ghosts and refluxed face
+fluxes) in 2D, and outflow boundaries (ghosts copied from the leaf's own edge) in 2D
+and 3D.  Tolerances as for the other float32 tests: per-cell difference <= 1e-5 of
+each variable's max norm after one step; normalised L1 of the density <= 1e-5 after
+a few; totals kept to float32 round-off on trees with jumps."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2004_03275_gb300 import amrvac
+from gpu_util import centres_for
+from treeutil import random_balanced_tree
+
+pytestmark = pytest.mark.gpu
+
+
+def scaled_err(a, b):
+    return float(np.max(np.abs(a - b) / np.max(np.abs(b), axis=(0, 2), keepdims=True)))
+
+
+def wave_state(x, ndim, nl, nc):
+    V = np.zeros((nl, ndim + 2, nc))
+    ph = sum(x[:, d] * (d + 1) for d in range(ndim))
+    V[:, 0] = 1.0 + 0.3 * np.sin(2 * np.pi * ph)
+    for d in range(ndim):
+        V[:, 1 + d] = 0.3 * np.cos(2 * np.pi * x[:, (d + 1) % ndim])
+    r2 = sum((x[:, d] - 0.4) ** 2 for d in range(ndim))
+    V[:, ndim + 1] = np.where(r2 < 0.02, 6.0, 1.0)
+    return V
+
+
+def run_pair(kw, lev=None, crd=None, steps=3):
+    s = amrvac.AmrSolver(precision="fp32", max_blocks=4096, **kw)
+    g = O.Grid(**kw)
+    if lev is not None:
+        s.set_leaves(lev, crd)
+        g.set_leaves(lev, crd)
+    l2, c2 = s.leaves()
+    x, _ = centres_for(l2, c2, kw)
+    nc = kw["block_nx"] ** kw["ndim"]
+    s.set_prim(wave_state(x, kw["ndim"], len(l2), nc))
+    g.set_cons(s.read_state())  # same (float-rounded) initial state on both sides
+    t0 = g.totals()
+    s.step()
+    g.step()
+    e1 = scaled_err(s.read_state(), g.get_cons())
+    for _ in range(steps - 1):
+        s.step()
+        g.step()
+    a, b = s.read_state()[:, 0], g.get_cons()[:, 0]
+    return e1, float(np.sum(np.abs(a - b)) / np.sum(np.abs(b))), t0, s.totals(), l2
+
+
+@pytest.mark.parametrize("flux", ["hll", "hllc"])
+@pytest.mark.parametrize("limiter", ["vanleer", "koren"])
+def test_2d_fp32_march_amr_tree(flux, limiter):
+    rng = np.random.default_rng(91)
+    base = [3, 2]
+    lev, crd = random_balanced_tree(2, base + [1], 3, rng, 4)
+    kw = dict(ndim=2, block_nx=16, base=base, max_level=3, gamma=1.4, cfl=0.6, flux=flux, limiter=limiter, rk=3,
+              bc="periodic", xmax=(1.0, 2.0 / 3.0, 1.0), refine_tol=0.2, coarsen_frac=0.5, wavefilter=0.01)
+    e1, l1, t0, t1, l2 = run_pair(kw, lev, crd)
+    assert len(np.unique(l2)) >= 2, "the tree must have level jumps"
+    assert e1 <= 1e-5, e1
+    assert l1 <= 1e-5, l1
+    assert np.all(np.abs(t1 - t0)[[0, 3]] <= 1e-6 * np.abs(t0)[[0, 3]]), (t0, t1)
+
+
+@pytest.mark.parametrize("ndim,base", [(2, [2, 3]), (3, [2, 1, 1])])
+def test_fp32_march_outflow(ndim, base):
+    kw = dict(ndim=ndim, block_nx=16, base=base, gamma=1.4, cfl=0.8, flux="hllc", limiter="koren", rk=3,
+              bc="outflow", xmax=tuple(b / max(base) for b in base) + (1.0,) * (3 - ndim))
+    e1, l1, _, _, _ = run_pair(kw)
+    assert e1 <= 1e-5, e1
+    assert l1 <= 1e-5, l1
