@@ -322,9 +322,14 @@ def bench_mg_vcycle(torch, amrvac, stream, hbm_gbs):
 
 # 2 x 9 x (5*16 + 16*16 + 16*16 + 16*2) multiply-adds x 2 per pixel for the 4 layers
 CNN_FLOP_PER_PIXEL_2D = 11232.0
+# HBM bytes per pixel of the layer-by-layer inference: layer 1 reads the float32 5-channel input
+# (20 B) and writes 16 bf16 channels (32 B); layers 2-3 read and write 32 B; layer 4 reads 32 B
+# and writes 2 float32 channels (8 B).  51 FLOP/B overall, below GB300's ~285 FLOP/B ridge
+# (measured bf16 peak / measured HBM bandwidth), so the attainable roofline is the HBM one.
+CNN_BYTES_PER_PIXEL_2D = 52.0 + 64.0 + 64.0 + 40.0
 
 
-def bench_cnn_forward(torch, amrvac, stream, peak_tflops):
+def bench_cnn_forward(torch, amrvac, stream, peak_tflops, hbm_gbs):
     """Inference of the learned-guess network on one 2048^2 grid (5 input channels), CUDA events."""
     net = amrvac.CnnNet(ndim=2, seed=3, stream=stream.cuda_stream)
     x = torch.from_numpy(np.random.default_rng(3).uniform(size=(1, 5, 2048, 2048)).astype(np.float32)).cuda()
@@ -341,12 +346,16 @@ def bench_cnn_forward(torch, amrvac, stream, peak_tflops):
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / reps
-    tf = CNN_FLOP_PER_PIXEL_2D * 2048 * 2048 / (ms * 1e-3) / 1e12
+    px = 2048 * 2048
+    tf = CNN_FLOP_PER_PIXEL_2D * px / (ms * 1e-3) / 1e12
+    gbs = CNN_BYTES_PER_PIXEL_2D * px / (ms * 1e-3) / 1e9
     net.close()
     return {"workload": "learned-guess CNN inference, 2048^2, 5->16->16->16->2 channels, 3x3, bf16 mma.sync",
-            "ms_per_inference": ms, "roofline": {"bound": "tensor", "achieved": round(tf, 1), "peak": peak_tflops,
-                                                  "unit": "TFLOP/s", "frac": round(tf / peak_tflops, 4),
-                                                  "flop_per_pixel": CNN_FLOP_PER_PIXEL_2D}}
+            "ms_per_inference": ms,
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_gbs, "unit": "GB/s",
+                         "frac": round(gbs / hbm_gbs, 4), "bytes_per_pixel": CNN_BYTES_PER_PIXEL_2D},
+            "tensor": {"achieved_tflops": round(tf, 1), "peak_tflops": peak_tflops, "frac": round(tf / peak_tflops, 4),
+                       "flop_per_pixel": CNN_FLOP_PER_PIXEL_2D}}
 
 
 def bench_blast(torch, amrvac, stream, hbm_gbs, steps=20, regrid_every=10):
@@ -617,7 +626,7 @@ def main():
                 "blast3d": lambda: bench_blast(torch, amrvac, stream, hbm),
                 "learned_guess_2d": lambda: bench_learned_guess(torch, amrvac, stream),
                 "learned_guess_3d": lambda: bench_learned_guess_3d(torch, amrvac, stream),
-                "cnn_forward_2048": lambda: bench_cnn_forward(torch, amrvac, stream, bf16_peak())}
+                "cnn_forward_2048": lambda: bench_cnn_forward(torch, amrvac, stream, bf16_peak(), hbm)}
         for name in want:
             extra[name] = runs[name]()
 
