@@ -16,7 +16,7 @@ from . import build as _build
 _lib = None
 
 FLUX = {"tvdlf": 0, "hll": 1, "hllc": 2}
-LIMITER = {"minmod": 0, "vanleer": 1, "koren": 2, "none": 3}
+LIMITER = {"minmod": 0, "vanleer": 1, "koren": 2, "none": 3, "mc": 4}
 BC = {"periodic": 0, "outflow": 1}
 
 _dp = C.POINTER(C.c_double)

@@ -158,6 +158,11 @@ void limited_slopes(int lim, double a, double b, double* sm, double* sp) {
     double s = (2.0 * a * b) / (a + b);
     *sm = s;
     *sp = s;
+  } else if (lim == ORC_LIM_MC) {  // monotonized central: minmod((a+b)/2, 2a, 2b)
+    double A = std::fabs(a), B = std::fabs(b);
+    double s = std::min(std::min(0.5 * (A + B), 2.0 * A), 2.0 * B);
+    *sm = (a > 0.0) ? s : -s;
+    *sp = *sm;
   } else {  // Koren, phi(r) = max(0, min(2r, (1+2r)/3, 2)) applied on each side
     double A = std::fabs(a), B = std::fabs(b);
     double up = std::min(std::min(2.0 * A, (2.0 * A + B) / 3.0), 2.0 * B);

@@ -58,6 +58,16 @@ struct Geometry {
   float idxf[kMaxLevel + 1][3];
 };
 
+// SSPRK stage combination alpha*U^n + beta*T, where T = U^(s) - dt div F and alpha + beta = 1
+// in every stage of SSPRK2/3 (Sec. 2.4).  Float: written T + alpha (U^n - T), so that the
+// rounded coefficients (1/3 and 2/3 round to floats whose sum is 1 + 3e-8) cannot scale the
+// state up a little every step; T == U^n gives U^n exactly.  Double: the plain form, in the
+// oracle's operation order (the double coefficients sum to 1 - 6e-17).
+__device__ __forceinline__ float ssp_combine(float alpha, float, float u0, float t) { return t + alpha * (u0 - t); }
+__device__ __forceinline__ double ssp_combine(double alpha, double beta, double u0, double t) {
+  return alpha * u0 + beta * t;
+}
+
 // ------------------------------------------------------------ stage args --
 template <typename real>
 struct StageArgs {
@@ -75,7 +85,7 @@ struct StageArgs {
   double* partials;    // [leaf][var]
   double* gpart;       // [group of CTAs][var]
   unsigned* gcount;    // [group of CTAs], zero between passes
-  real alpha, beta;    // out = alpha*U0 + beta*(Us - dt*div); alpha == 0: out = Us - dt*div
+  real alpha, beta;    // out = ssp_combine(alpha, beta, U0, Us - dt*div); stage1: out = Us - dt*div
   int stage1;
   int fuse_reduce;     // fold max rate / totals / time update into this pass
   int has_ffx;

@@ -62,6 +62,7 @@ cudaError_t stage2d_f32_prepare(int lim) {
     case LIM_MINMOD: return stage2d_f32_prepare_one<B, FLUX, LIM_MINMOD>();
     case LIM_VANLEER: return stage2d_f32_prepare_one<B, FLUX, LIM_VANLEER>();
     case LIM_KOREN: return stage2d_f32_prepare_one<B, FLUX, LIM_KOREN>();
+    case LIM_MC: return stage2d_f32_prepare_one<B, FLUX, LIM_MC>();
     default: return stage2d_f32_prepare_one<B, FLUX, LIM_NONE>();
   }
 }
@@ -95,6 +96,7 @@ cudaError_t stage2d_f32_launch(const StageArgs<float>& a, const Geometry& G, cud
     case LIM_MINMOD: stage2d_f32_go<B, FLUX, LIM_MINMOD>(a, G, s); break;
     case LIM_VANLEER: stage2d_f32_go<B, FLUX, LIM_VANLEER>(a, G, s); break;
     case LIM_KOREN: stage2d_f32_go<B, FLUX, LIM_KOREN>(a, G, s); break;
+    case LIM_MC: stage2d_f32_go<B, FLUX, LIM_MC>(a, G, s); break;
     default: stage2d_f32_go<B, FLUX, LIM_NONE>(a, G, s); break;
   }
   return cudaGetLastError();
@@ -117,6 +119,7 @@ cudaError_t stage3d_f32_launch(const StageArgs<float>& a, const Geometry& G, cud
     case LIM_MINMOD: stage3d_f32_go<FLUX, LIM_MINMOD>(a, G, s); break;
     case LIM_VANLEER: stage3d_f32_go<FLUX, LIM_VANLEER>(a, G, s); break;
     case LIM_KOREN: stage3d_f32_go<FLUX, LIM_KOREN>(a, G, s); break;
+    case LIM_MC: stage3d_f32_go<FLUX, LIM_MC>(a, G, s); break;
     default: stage3d_f32_go<FLUX, LIM_NONE>(a, G, s); break;
   }
   return cudaGetLastError();
@@ -137,6 +140,7 @@ cudaError_t stage3d_f32_prepare(int lim) {
   cudaError_t e = lim == LIM_MINMOD    ? stage3d_z_prepare<FLUX, LIM_MINMOD>()
                   : lim == LIM_VANLEER ? stage3d_z_prepare<FLUX, LIM_VANLEER>()
                   : lim == LIM_KOREN   ? stage3d_z_prepare<FLUX, LIM_KOREN>()
+                  : lim == LIM_MC      ? stage3d_z_prepare<FLUX, LIM_MC>()
                                        : stage3d_z_prepare<FLUX, LIM_NONE>();
   if (e != cudaSuccess) return e;
   switch (lim) {
@@ -148,6 +152,9 @@ cudaError_t stage3d_f32_prepare(int lim) {
                                   (int)kXy3Smem);
     case LIM_KOREN:
       return cudaFuncSetAttribute(stage3d_xy_kernel<FLUX, LIM_KOREN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kXy3Smem);
+    case LIM_MC:
+      return cudaFuncSetAttribute(stage3d_xy_kernel<FLUX, LIM_MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kXy3Smem);
     default:
       return cudaFuncSetAttribute(stage3d_xy_kernel<FLUX, LIM_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -18,7 +18,7 @@
 namespace amrgpu {
 
 enum { FLUX_TVDLF = 0, FLUX_HLL = 1, FLUX_HLLC = 2 };
-enum { LIM_MINMOD = 0, LIM_VANLEER = 1, LIM_KOREN = 2, LIM_NONE = 3 };
+enum { LIM_MINMOD = 0, LIM_VANLEER = 1, LIM_KOREN = 2, LIM_NONE = 3, LIM_MC = 4 };
 
 // ------------------------------------------------------------------ physics --
 template <typename real, int ND>
@@ -143,6 +143,11 @@ __device__ __forceinline__ void limited_slopes(int lim, real a, real b, real& sm
     real s = (real(2) * a * b) / (a + b);
     sm = s;
     sp = s;
+  } else if (lim == LIM_MC) {  // monotonized central: minmod((a+b)/2, 2a, 2b)
+    real A = fabs(a), Bb = fabs(b);
+    real s = fmin(fmin(real(0.5) * (A + Bb), real(2) * A), real(2) * Bb);
+    sm = (a > real(0)) ? s : -s;
+    sp = sm;
   } else {
     real A = fabs(a), Bb = fabs(b);
     real up = fmin(fmin(real(2) * A, (real(2) * A + Bb) / real(3)), real(2) * Bb);
@@ -558,7 +563,7 @@ stage_kernel_12(StageArgs<real> a, Geometry G) {
       if (ND == 2)  // y faces are stored per column: (face index jc, column ic)
         div = div + (FXs[lb][ND - 1][v][ic * (B + 1) + jc + 1] - FXs[lb][ND - 1][v][ic * (B + 1) + jc]) / dx[1];
       real tmp = Uc[v] - dtr * div;
-      Un[v] = a.stage1 ? tmp : a.alpha * a.U0[((size_t)leaf * NV + v) * NC + tc] + a.beta * tmp;
+      Un[v] = a.stage1 ? tmp : ssp_combine(a.alpha, a.beta, a.U0[((size_t)leaf * NV + v) * NC + tc], tmp);
       a.out[((size_t)leaf * NV + v) * NC + tc] = Un[v];
     }
     if (a.fuse_reduce) {
@@ -736,7 +741,7 @@ __global__ void __launch_bounds__(256) stage_kernel_3d(StageArgs<real> a, Geomet
         div = div + (S.FX[lb][1][v][ic * (B + 1) + jc + 1] - S.FX[lb][1][v][ic * (B + 1) + jc]) / dx[1];
         div = div + (Fz[v] - S.FZ[lb][v][tc]) / dx[2];
         real tmp = Uk[v] - dtr * div;
-        Un[v] = a.stage1 ? tmp : a.alpha * a.U0[((size_t)leaf * NV + v) * NC + cell] + a.beta * tmp;
+        Un[v] = a.stage1 ? tmp : ssp_combine(a.alpha, a.beta, a.U0[((size_t)leaf * NV + v) * NC + cell], tmp);
         a.out[((size_t)leaf * NV + v) * NC + cell] = Un[v];
         S.FZ[lb][v][tc] = Fz[v];
       }

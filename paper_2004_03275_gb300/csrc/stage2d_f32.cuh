@@ -40,6 +40,11 @@ __device__ __forceinline__ void half_slopes(float a, float b, float& hm, float& 
     s = (ab > 0.f) ? s : 0.f;
     hm = s;
     hp = s;
+  } else if (LIM == LIM_MC) {  // minmod((a+b)/2, 2a, 2b) / 2
+    float s = fminf(fminf(0.25f * fabsf(a + b), fabsf(a)), fabsf(b));
+    s = (a * b > 0.f) ? copysignf(s, a) : 0.f;
+    hm = s;
+    hp = s;
   } else {  // Koren
     float A = fabsf(a), B = fabsf(b);
     float up = fminf(fminf(A, (2.f * A + B) * (1.f / 6.f)), B);
@@ -317,7 +322,7 @@ __global__ void __launch_bounds__(256, 5) stage2d_f32_kernel(StageArgs<float> a,
         float div = (S.XL[lb][v][(ic + 1) * SS + jc] - S.XL[lb][v][ic * SS + jc]) * idx +
                     (S.YL[lb][v][ic * SS + jc + 1] - S.YL[lb][v][ic * SS + jc]) * idy;
         float tmp = Uc[v] - dt * div;
-        Un[v] = a.stage1 ? tmp : a.alpha * Un0[v] + a.beta * tmp;
+        Un[v] = a.stage1 ? tmp : ssp_combine(a.alpha, a.beta, Un0[v], tmp);
         a.out[((size_t)leaf * NV + v) * NC + tc] = Un[v];
       }
       if (a.fuse_reduce) {

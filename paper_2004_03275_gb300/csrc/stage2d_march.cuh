@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4)
             for (int v = 0; v < NV; ++v) {
               float div = ex[v] * idx + (F[v] - Fp[v]) * idy;
               float tmp = uc[v] - dt * div;
-              Un[v] = FIRST ? tmp : a.alpha * u0c[v] + a.beta * tmp;
+              Un[v] = FIRST ? tmp : ssp_combine(a.alpha, a.beta, u0c[v], tmp);
               Ol[v * NC + q] = Un[v];
             }
             if constexpr (LAST) {

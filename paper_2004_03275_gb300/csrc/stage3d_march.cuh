@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(128, 3) stage3d_z_kernel(StageArgs<float> a, G
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           float tmp = uc[v] - dt * (dc[v] + (F[v] - Fp[v]) * idz);
-          Un[v] = a.stage1 ? tmp : a.alpha * u0c[v] + a.beta * tmp;
+          Un[v] = a.stage1 ? tmp : ssp_combine(a.alpha, a.beta, u0c[v], tmp);
           Ol[v * NC + r * NT] = Un[v];
         }
         if constexpr (LAST) {

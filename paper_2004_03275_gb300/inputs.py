@@ -164,3 +164,27 @@ def gray_scott_batch_sizes(count=16):
     second 2048 (16 instances, 256^2 .. 2048^2)."""
     sizes = [128 * (i + 2) for i in range(15)]
     return (sizes + [2048])[:count]
+
+
+def gresho_chan(x, mach=3.0 ** 0.5 / 5.0, gamma=5.0 / 3.0):
+    """Gresho-Chan vortex (Sec. 2.2, Eqs. (gcp), (gcv)) on [-0.5, 0.5]^2: rho = 1, rotation
+    v_phi = 5r (r < 0.2), 2 - 5r (0.2 <= r < 0.4), 0 beyond; the pressure balances the
+    centrifugal force: p0 + 12.5 r^2 inside 0.2, p0 + 12.5 r^2 + 4(1 - 5r - ln 0.2 + ln r) up to
+    0.4, p0 - 2 + 4 ln 2 beyond, with p0 = 1/(gamma M^2).  A stationary solution of the Euler
+    equations.  gamma = 5/3 is the value the paper fixes for its hydrodynamic tests (Sec. 2.2).
+    x: cell centres [leaf][dim][cell]; returns primitive (rho, v_x, v_y, p)."""
+    nl, _, nc = x.shape
+    X, Y = x[:, 0], x[:, 1]
+    r = np.sqrt(X * X + Y * Y)
+    p0 = 1.0 / (gamma * mach * mach)
+    rs = np.maximum(r, 1e-300)
+    vphi = np.where(r < 0.2, 5.0 * r, np.where(r < 0.4, 2.0 - 5.0 * r, 0.0))
+    p = np.where(r < 0.2, p0 + 12.5 * r * r,
+                 np.where(r < 0.4, p0 + 12.5 * r * r + 4.0 * (1.0 - 5.0 * r - np.log(0.2) + np.log(rs)),
+                          p0 - 2.0 + 4.0 * np.log(2.0)))
+    V = np.zeros((nl, 4, nc))
+    V[:, 0] = 1.0
+    V[:, 1] = np.where(r > 0, -vphi * Y / rs, 0.0)
+    V[:, 2] = np.where(r > 0, vphi * X / rs, 0.0)
+    V[:, 3] = p
+    return V

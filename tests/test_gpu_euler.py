@@ -55,7 +55,7 @@ def test_sod_config_parity_and_exact():
 
 
 @pytest.mark.parametrize("flux", ["tvdlf", "hll", "hllc"])
-@pytest.mark.parametrize("limiter", ["minmod", "vanleer", "koren", "none"])
+@pytest.mark.parametrize("limiter", ["minmod", "vanleer", "koren", "none", "mc"])
 def test_2d_schemes_fp64_parity(flux, limiter):
     """Every flux x limiter pair, 15 leaves of 8^2 (ragged last CTA), 6 steps."""
     kw = dict(ndim=2, block_nx=8, base=[3, 5], gamma=1.4, cfl=0.8, flux=flux, limiter=limiter, rk=3,
@@ -222,7 +222,7 @@ def test_full_size_kh_one_step(precision):
 
 
 @pytest.mark.parametrize("flux", ["tvdlf", "hll", "hllc"])
-@pytest.mark.parametrize("limiter", ["minmod", "vanleer", "koren", "none"])
+@pytest.mark.parametrize("limiter", ["minmod", "vanleer", "koren", "none", "mc"])
 @pytest.mark.parametrize("bnx,base", [(8, [3, 5]), (16, [3, 2])])
 def test_2d_fp32_schemes(flux, limiter, bnx, base):
     """FP32 batched kernel: every flux x limiter, ragged last CTA for 8^2 leaves.

@@ -97,7 +97,11 @@ def koren_phi(r):
     return max(0.0, min(2 * r, (1 + 2 * r) / 3, 2.0))
 
 
-@pytest.mark.parametrize("lim", ["minmod", "vanleer", "koren"])
+def mc_phi(r):  # monotonized central (van Leer 1977): max(0, min(2r, (1+r)/2, 2))
+    return max(0.0, min(2 * r, (1 + r) / 2, 2.0))
+
+
+@pytest.mark.parametrize("lim", ["minmod", "vanleer", "koren", "mc"])
 def test_limiters_textbook(lim):
     rng = np.random.default_rng(4)
     for _ in range(200):
@@ -111,6 +115,8 @@ def test_limiters_textbook(lim):
         elif lim == "vanleer":  # phi(r) = (r + |r|)/(1 + |r|), s = phi(a/b) b
             r = a / b
             want_p = want_m = (r + abs(r)) / (1 + abs(r)) * b
+        elif lim == "mc":  # symmetric: s = phi(a/b) b
+            want_p = want_m = mc_phi(a / b) * b
         else:  # q_{i+1/2}^L = q_i + phi(a/b) b / 2 ; q_{i-1/2}^R = q_i - phi(b/a) a / 2
             want_p = koren_phi(a / b) * b
             want_m = koren_phi(b / a) * a
@@ -118,7 +124,7 @@ def test_limiters_textbook(lim):
         assert abs(sm - want_m) <= 1e-14 * max(1, abs(want_m))
 
 
-@pytest.mark.parametrize("lim", ["minmod", "vanleer", "koren"])
+@pytest.mark.parametrize("lim", ["minmod", "vanleer", "koren", "mc"])
 def test_limiters_reproduce_linear(lim):
     for a in (0.3, -1.7, 2.5e-3):
         sm, sp = O.limited_slopes(lim, a, a)
@@ -201,7 +207,7 @@ def test_sod_convergence_first_order():
     assert np.all(orders > 0.6) and np.all(orders < 1.3), (e, orders)
 
 
-@pytest.mark.parametrize("lim", ["vanleer", "koren"])
+@pytest.mark.parametrize("lim", ["vanleer", "koren", "mc"])
 def test_smooth_wave_second_order(lim):
     """Advected density wave, periodic: L1 error order >= 1.8 (SSPRK3)."""
     errs = []
@@ -280,3 +286,54 @@ def test_x_y_symmetry():
     rho = field(U[:, 0])
     assert np.allclose(rho, rho.T, rtol=1e-13, atol=1e-13)
     assert np.allclose(field(U[:, 1]), field(U[:, 2]).T, rtol=1e-12, atol=1e-12)
+
+
+# ----------------------------------------------------------- Gresho-Chan vortex ---
+GRESHO_GAMMA = 5.0 / 3.0  # the paper's value for its hydrodynamic tests (Sec. 2.2)
+
+
+def gresho_errors(n, t_end, lim="mc", make=None):
+    """L1 error of v_phi and L2 error of p against the stationary initial state."""
+    nb = n // 16
+    kw = dict(ndim=2, block_nx=16, base=[nb, nb], gamma=GRESHO_GAMMA, cfl=0.9, flux="hllc", limiter=lim, rk=3,
+              bc="periodic", xmin=(-0.5, -0.5, 0), xmax=(0.5, 0.5, 1))
+    g = (make or O.Grid)(**kw)
+    lev, crd = g.leaves()
+    x, _ = inputs.cell_centres(lev, crd, 2, 16, [nb, nb, 1], [-0.5, -0.5, 0], [0.5, 0.5, 1])
+    V0 = inputs.gresho_chan(x)
+    g.set_prim(V0)
+    g.run(t_end=t_end)
+    U = g.get_cons()
+    rho = U[:, 0]
+    vx, vy = U[:, 1] / rho, U[:, 2] / rho
+    p = (GRESHO_GAMMA - 1.0) * (U[:, 3] - 0.5 * rho * (vx ** 2 + vy ** 2))
+    X, Y = x[:, 0], x[:, 1]
+    r = np.sqrt(X ** 2 + Y ** 2) + 1e-300
+    vphi, vphi0 = (-vx * Y + vy * X) / r, (-V0[:, 1] * Y + V0[:, 2] * X) / r
+    return np.mean(np.abs(vphi - vphi0)), np.sqrt(np.mean((p - V0[:, 3]) ** 2))
+
+
+def test_gresho_chan_input_is_the_closed_form():
+    """The pressure profile is continuous at r = 0.2 and 0.4 and balances the centrifugal
+    force: dp/dr = rho v_phi^2 / r (checked by central differences along the x axis)."""
+    r = np.linspace(0.01, 0.49, 2001)
+    x = np.zeros((1, 2, r.size))
+    x[0, 0] = r
+    V = inputs.gresho_chan(x)
+    vphi, p = V[0, 2], V[0, 3]
+    dp = np.gradient(p, r)
+    inside = (np.abs(r - 0.2) > 2e-3) & (np.abs(r - 0.4) > 2e-3) & (r > r[1]) & (r < r[-2])  # central differences
+    assert np.max(np.abs(dp - vphi ** 2 / r)[inside]) < 1e-4
+    for rc in (0.2, 0.4):
+        lo = inputs.gresho_chan(np.array([[[rc - 1e-9], [0.0]]]))[0, 3, 0]
+        hi = inputs.gresho_chan(np.array([[[rc + 1e-9], [0.0]]]))[0, 3, 0]
+        assert abs(hi - lo) < 1e-7
+
+
+def test_gresho_chan_stays_and_converges():
+    """The vortex is stationary: at t = 0.2 the errors fall with resolution, faster than first
+    order for v_phi and close to second order for p (HLLC, MC limiter, SSPRK3, CFL 0.9)."""
+    e32, e64 = gresho_errors(32, 0.2), gresho_errors(64, 0.2)
+    ov, op = np.log2(e32[0] / e64[0]), np.log2(e32[1] / e64[1])
+    assert e64[0] < 5e-3 and e64[1] < 3e-3, (e32, e64)
+    assert ov > 1.2 and op > 1.6, (ov, op)
