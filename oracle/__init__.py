@@ -18,6 +18,9 @@ _lib = None
 FLUX = {"tvdlf": 0, "hll": 1, "hllc": 2}
 LIMITER = {"minmod": 0, "vanleer": 1, "koren": 2, "none": 3, "mc": 4}
 BC = {"periodic": 0, "outflow": 1}
+MG_BC = {"periodic": 0, "neumann": 1}
+RD_MODEL = {"gray-scott": 0, "schnakenberg": 1}
+RD_SCHEME = {"imex": 0, "split": 1, "explicit": 2}
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -37,7 +40,7 @@ class OrcMgConfig(C.Structure):
     _fields_ = [
         ("ndim", C.c_int), ("n", C.c_int), ("L", C.c_double), ("lam", C.c_double),
         ("nu1", C.c_int), ("nu2", C.c_int), ("max_cycles", C.c_int), ("rtol", C.c_double),
-        ("coarse_max", C.c_int),
+        ("coarse_max", C.c_int), ("bc", C.c_int),
     ]
 
 
@@ -46,6 +49,8 @@ class OrcRdConfig(C.Structure):
         ("ndim", C.c_int), ("n", C.c_int), ("L", C.c_double), ("Du", C.c_double), ("Dv", C.c_double),
         ("F", C.c_double), ("k", C.c_double), ("dt", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
         ("max_cycles", C.c_int), ("rtol", C.c_double), ("coarse_max", C.c_int),
+        ("model", C.c_int), ("kappa", C.c_double), ("a", C.c_double), ("b", C.c_double), ("scheme", C.c_int),
+        ("bc", C.c_int),
     ]
 
 
@@ -79,11 +84,12 @@ def lib():
         L.orc_exact_riemann.argtypes = [C.c_double, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp]
         L.orc_mg_solve.argtypes = [C.POINTER(OrcMgConfig), _dp, _dp, _dp]
         L.orc_mg_vcycle.argtypes = [C.POINTER(OrcMgConfig), _dp, _dp]
-        L.orc_mg_apply.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
-        L.orc_dense_solve.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
+        L.orc_mg_apply.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, _dp, _dp]
+        L.orc_dense_solve.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, _dp, _dp]
         L.orc_rd_step.argtypes = [C.POINTER(OrcRdConfig), _dp, _dp, _ip]
         L.orc_rd_reaction.argtypes = [C.c_double, C.c_double, C.c_int, _dp, _dp, _dp, _dp]
-        L.orc_laplacian.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp]
+        L.orc_rd_reaction_schnakenberg.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, _dp, _dp, _dp, _dp]
+        L.orc_laplacian.argtypes = [C.c_int, C.c_int, C.c_double, C.c_int, _dp, _dp]
         if hasattr(L, "orc_cnn_forward"):
             _bind_cnn(L)
         _lib = L
@@ -266,8 +272,8 @@ def exact_riemann(gamma, left, right, xi):
     return out, ps.value, us.value
 
 
-def mg_config(ndim, n, L, lam, nu1=2, nu2=2, max_cycles=50, rtol=1e-10, coarse_max=8):
-    return OrcMgConfig(ndim, n, L, lam, nu1, nu2, max_cycles, rtol, coarse_max)
+def mg_config(ndim, n, L, lam, nu1=2, nu2=2, max_cycles=50, rtol=1e-10, coarse_max=8, bc="periodic"):
+    return OrcMgConfig(ndim, n, L, lam, nu1, nu2, max_cycles, rtol, coarse_max, MG_BC[bc])
 
 
 def mg_solve(b, x0, L, lam, **kw):
@@ -288,25 +294,25 @@ def mg_vcycle(r, L, lam, **kw):
     return e
 
 
-def mg_apply(x, L, lam):
+def mg_apply(x, L, lam, bc="periodic"):
     x = _f64(x)
     out = np.zeros_like(x)
-    lib().orc_mg_apply(x.ndim, x.shape[0], L, lam, _d(x), _d(out))
+    lib().orc_mg_apply(x.ndim, x.shape[0], L, lam, MG_BC[bc], _d(x), _d(out))
     return out
 
 
-def dense_solve(b, L, lam):
+def dense_solve(b, L, lam, bc="periodic"):
     b = _f64(b)
     x = np.zeros_like(b)
-    if lib().orc_dense_solve(b.ndim, b.shape[0], L, lam, _d(b), _d(x)) != 0:
+    if lib().orc_dense_solve(b.ndim, b.shape[0], L, lam, MG_BC[bc], _d(b), _d(x)) != 0:
         raise ValueError("singular")
     return x
 
 
-def laplacian(x, L):
+def laplacian(x, L, bc="periodic"):
     x = _f64(x)
     out = np.zeros_like(x)
-    lib().orc_laplacian(x.ndim, x.shape[0], L, _d(x), _d(out))
+    lib().orc_laplacian(x.ndim, x.shape[0], L, MG_BC[bc], _d(x), _d(out))
     return out
 
 
@@ -317,9 +323,20 @@ def rd_reaction(F, k, u, v):
     return fu, fv
 
 
-def rd_step(u, v, L, Du, Dv, F, k, dt, nu1=2, nu2=2, max_cycles=50, rtol=1e-10, coarse_max=8):
+def rd_reaction_schnakenberg(kappa, a, b, u, v):
+    u, v = _f64(u), _f64(v)
+    fu, fv = np.zeros_like(u), np.zeros_like(v)
+    lib().orc_rd_reaction_schnakenberg(kappa, a, b, u.size, _d(u), _d(v), _d(fu), _d(fv))
+    return fu, fv
+
+
+def rd_step(u, v, L, Du, Dv, dt, F=0.0, k=0.0, nu1=2, nu2=2, max_cycles=50, rtol=1e-10, coarse_max=8,
+            model="gray-scott", kappa=0.0, a=0.0, b=0.0, scheme="imex", bc="periodic"):
+    """One reaction-diffusion step of `scheme` ("imex", "split", "explicit") for `model`
+    ("gray-scott": F, k; "schnakenberg": kappa, a, b) with `bc` ("periodic", "neumann")."""
     u, v = _f64(u).copy(), _f64(v).copy()
-    c = OrcRdConfig(u.ndim, u.shape[0], L, Du, Dv, F, k, dt, nu1, nu2, max_cycles, rtol, coarse_max)
+    c = OrcRdConfig(u.ndim, u.shape[0], L, Du, Dv, F, k, dt, nu1, nu2, max_cycles, rtol, coarse_max,
+                    RD_MODEL[model], kappa, a, b, RD_SCHEME[scheme], MG_BC[bc])
     cyc = np.zeros(2, dtype=np.int32)
     st = lib().orc_rd_step(C.byref(c), _d(u), _d(v), _i(cyc))
     if st != 0:

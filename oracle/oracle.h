@@ -94,34 +94,50 @@ int orc_exact_riemann(double gamma, const double* left, const double* right,
                       int n, const double* xi, double* out /* [n][3] rho,u,p */,
                       double* pstar, double* ustar);
 
-/* ---- multigrid: (lambda - lap_h) x = b on a periodic n^ndim grid of side L ---- */
+/* ---- multigrid: (lambda - lap_h) x = b on an n^ndim grid of side L ----
+ * Boundaries: periodic, or Neumann (zero flux: a face on the domain boundary carries no
+ * diffusive flux, so a boundary cell's Laplacian has only its in-domain neighbours). */
+enum { ORC_MG_PERIODIC = 0, ORC_MG_NEUMANN = 1 };
 typedef struct {
   int ndim, n;      /* cells per side */
   double L, lambda;
   int nu1, nu2, max_cycles;
   double rtol;      /* stop when max|b - A x| <= rtol * max|b| */
   int coarse_max;   /* coarsen while n is even and n > coarse_max */
+  int bc;           /* ORC_MG_PERIODIC or ORC_MG_NEUMANN */
 } orc_mg_config;
 /* x holds the initial guess on entry; returns V-cycles used (or -1 if not converged) */
 int orc_mg_solve(const orc_mg_config* c, const double* b, double* x, double* relres);
-void orc_mg_apply(int ndim, int n, double L, double lambda, const double* x, double* Ax);
+void orc_mg_apply(int ndim, int n, double L, double lambda, int bc, const double* x, double* Ax);
 /* one V-cycle on the correction equation A e = r, e zero on entry (test hook) */
 void orc_mg_vcycle(const orc_mg_config* c, const double* r, double* e);
 /* dense Gaussian elimination solve of the same system (tiny n only) */
-int orc_dense_solve(int ndim, int n, double L, double lambda, const double* b, double* x);
+int orc_dense_solve(int ndim, int n, double L, double lambda, int bc, const double* b, double* x);
 
-/* ---- Gray-Scott IMEX step, Eq. (imex) with F0 = reaction, F1 = diffusion ---- */
+/* ---- reaction-diffusion step (Sec. 2.5): w = (u, v), dw/dt = F0(w) + F1(w), F0 the
+ * reaction terms of Eq. (gray-scott) or Eq. (schnakenberg), F1 = D lap_h w ---- */
+enum { ORC_RD_GRAY_SCOTT = 0, ORC_RD_SCHNAKENBERG = 1 };
+enum { ORC_RD_IMEX = 0, ORC_RD_SPLIT = 1, ORC_RD_EXPLICIT = 2 };
 typedef struct {
   int ndim, n; double L;
   double Du, Dv, F, k, dt;
   int nu1, nu2, max_cycles; double rtol; int coarse_max;
+  int model;              /* ORC_RD_GRAY_SCOTT (F, k) or ORC_RD_SCHNAKENBERG (kappa, a, b) */
+  double kappa, a, b;
+  int scheme;             /* ORC_RD_IMEX: Eq. (imex); ORC_RD_SPLIT: explicit reaction then
+                             backward-Euler diffusion, Eqs. (splitting), (diff-helmholtz);
+                             ORC_RD_EXPLICIT: three-stage SSP Runge-Kutta on F0 + F1 */
+  int bc;                 /* ORC_MG_PERIODIC or ORC_MG_NEUMANN */
 } orc_rd_config;
-/* advances u, v (n^ndim each) by one step; cycles[2] receives V-cycles used per species */
+/* advances u, v (n^ndim each) by one step; cycles[2] receives V-cycles used per species
+ * (0 for the explicit scheme) */
 int orc_rd_step(const orc_rd_config* c, double* u, double* v, int* cycles);
 /* reaction terms F0 and the discrete Laplacian, for pins */
 void orc_rd_reaction(double F, double k, int n, const double* u, const double* v,
                      double* fu, double* fv);
-void orc_laplacian(int ndim, int n, double L, const double* x, double* out);
+void orc_rd_reaction_schnakenberg(double kappa, double a, double b, int n, const double* u, const double* v,
+                                  double* fu, double* fv);
+void orc_laplacian(int ndim, int n, double L, int bc, const double* x, double* out);
 
 /* ---- learned multigrid guess: CNN 5->16->16->16->2, 3^ndim periodic convolutions ----
  * params flat: per layer W[cout][cin][tap] then b[cout]; images [N][C][D][H][W] (D = 1 in 2D) */

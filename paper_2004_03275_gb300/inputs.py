@@ -188,3 +188,20 @@ def gresho_chan(x, mach=3.0 ** 0.5 / 5.0, gamma=5.0 / 3.0):
     V[:, 2] = np.where(r > 0, vphi * X / rs, 0.0)
     V[:, 3] = p
     return V
+
+
+SCHNAKENBERG = dict(Du=0.05, Dv=1.0, kappa=100.0, a=0.1305, b=0.7695)  # Sec. 2.5, Eq. (schnakenberg)
+
+
+def schnakenberg_initial(n, ndim=2, L=1.0, a=0.1305, b=0.7695):
+    """Initial state of the Schnakenberg runs (Sec. 2.5.2) on an n^ndim cell-centred grid of
+    [0, L]^ndim: v = b / (a + b)^2 and u = a + b + exp(-100 |r - r0|^2), with r0 = (1/3, 1/2)
+    in 2D and (1/3, 1/2, 1/2) in 3D.  Arrays of shape (n,)*ndim, x fastest (last axis)."""
+    r0 = [1.0 / 3.0, 0.5, 0.5][:ndim]
+    axes = [(np.arange(n) + 0.5) * (L / n) for _ in range(ndim)]
+    mesh = np.meshgrid(*axes, indexing="ij")  # mesh[d] varies along axis d
+    r2 = sum((mesh[d] - r0[d]) ** 2 for d in range(ndim))
+    u = (a + b) + np.exp(-100.0 * r2)
+    v = np.full(u.shape, b / (a + b) ** 2)
+    # storage order: x fastest, so the flat index is i + n*(j + n*k)
+    return np.ascontiguousarray(u.transpose(tuple(range(ndim))[::-1])), v
