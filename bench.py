@@ -320,6 +320,68 @@ def bench_mg_vcycle(torch, amrvac, stream, hbm_gbs):
                       "host poll), best of 5, difference of two tolerances"}
 
 
+def bench_schnakenberg(torch, amrvac, stream):
+    """Sec. 2.5.2's Schnakenberg study on the GPU: Eq. (schnakenberg) with D_u = 0.05, D_v = 1,
+    kappa = 100, a = 0.1305, b = 0.7695 on [0, 1]^d with zero-flux boundaries.
+    (1) Time per step of the explicit, IMEX and split schemes at 256^2 (the paper: 1.1, 7.7 and
+    7.2 ms on 4 CPU cores, multigrid to 1e-7 of the right-hand side) and at 128^3: explicit at
+    dt = 3e-6 (2D) / 1e-5 (3D), below h^2 / (2 ndim D_v); IMEX and split at dt = 1e-3.
+    (2) The paper's convergence study: 256^2 at t = 2 against an explicit run with dt = 3e-6
+    (666,667 steps), multigrid to 1e-10; IMEX at dt = 4e-3 .. 5e-4, split at dt = 1e-3 .. 1.25e-4
+    (its forward-Euler reaction step is unstable above dt ~ 1.1e-3: the reaction Jacobian at the
+    homogeneous steady state has eigenvalues -3.55 +- 80.4i)."""
+    from paper_2004_03275_gb300 import inputs
+    P = inputs.SCHNAKENBERG
+    kw = dict(Du=P["Du"], Dv=P["Dv"], kappa=P["kappa"], a=P["a"], b=P["b"], model="schnakenberg", bc="neumann",
+              precision="fp32", stream=stream.cuda_stream)
+
+    def solver(ndim, n, scheme, dt, rtol):
+        u0, v0 = inputs.schnakenberg_initial(n, ndim)
+        s = amrvac.RdSolver(ndim, [n], 1.0, dt=dt, scheme=scheme, rtol=rtol, **kw)
+        s.set_state(u0.ravel(), v0.ravel())
+        return s
+
+    timing = {}
+    for ndim, n in ((2, 256), (3, 128)):
+        for scheme, dt, steps in (("explicit", 3e-6 if ndim == 2 else 1e-5, 4000), ("imex", 1e-3, 100),
+                                  ("split", 1e-3, 100)):
+            s = solver(ndim, n, scheme, dt, 1e-7)
+            s.step(steps // 10)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cyc = s.step(steps)
+            el = (time.perf_counter() - t0) / steps
+            timing[f"{scheme}_{n}^{ndim}"] = {"dt": dt, "ms_per_step": round(el * 1e3, 5),
+                                              "vcycles_per_solve": round(float(np.mean(cyc)), 2)}
+            s.close()
+    T = 2.0
+    s = solver(2, 256, "explicit", 3e-6, 1e-10)
+    nref = int(round(T / 3e-6))
+    t0 = time.perf_counter()
+    s.step(nref)
+    t_ref = time.perf_counter() - t0
+    ur, vr = s.read_state()
+    s.close()
+    conv = {}
+    for scheme, dts in (("imex", (4e-3, 2e-3, 1e-3, 5e-4)), ("split", (1e-3, 5e-4, 2.5e-4, 1.25e-4))):
+        errs = []
+        for dt in dts:
+            s = solver(2, 256, scheme, dt, 1e-10)
+            s.step(int(round(T / dt)))
+            u, v = s.read_state()
+            errs.append(float(np.sqrt(np.mean((u - ur) ** 2 + (v - vr) ** 2))))
+            s.close()
+        e = np.array(errs)
+        conv[scheme] = {"dt": list(dts), "l2_error": errs,
+                        "orders": [round(float(x), 3) for x in np.log2(e[:-1] / e[1:])]}
+    return {"workload": "Schnakenberg (Sec. 2.5.2), Neumann, L = 1, 256^2 and 128^3, float32 multigrid on the "
+                        "float64 defect, state float64",
+            "per_step": timing,
+            "paper_per_step_ms_256^2_4_cpu_cores": {"explicit": 1.1, "imex": 7.7, "split": 7.2},
+            "convergence_t2_256^2": conv, "reference_explicit_steps": nref, "reference_seconds": round(t_ref, 2),
+            "timing": "host wall clock around synchronous rd_step calls"}
+
+
 # 2 x 9 x (5*16 + 16*16 + 16*16 + 16*2) multiply-adds x 2 per pixel for the 4 layers
 CNN_FLOP_PER_PIXEL_2D = 11232.0
 # HBM bytes per pixel of the layer-by-layer inference: layer 1 reads the float32 5-channel input
@@ -619,14 +681,15 @@ def main():
     extra = {}
     if not args.skip_extra and rank == 0:
         names = ["gray_scott_batch", "mg_vcycle", "blast3d", "learned_guess_2d", "learned_guess_3d",
-                 "cnn_forward_2048"]
+                 "cnn_forward_2048", "schnakenberg"]
         want = names if args.extras == "all" else [e for e in args.extras.split(",") if e in names]
         runs = {"gray_scott_batch": lambda: bench_gray_scott(torch, amrvac, stream),
                 "mg_vcycle": lambda: bench_mg_vcycle(torch, amrvac, stream, hbm),
                 "blast3d": lambda: bench_blast(torch, amrvac, stream, hbm),
                 "learned_guess_2d": lambda: bench_learned_guess(torch, amrvac, stream),
                 "learned_guess_3d": lambda: bench_learned_guess_3d(torch, amrvac, stream),
-                "cnn_forward_2048": lambda: bench_cnn_forward(torch, amrvac, stream, bf16_peak(), hbm)}
+                "cnn_forward_2048": lambda: bench_cnn_forward(torch, amrvac, stream, bf16_peak(), hbm),
+                "schnakenberg": lambda: bench_schnakenberg(torch, amrvac, stream)}
         for name in want:
             extra[name] = runs[name]()
 

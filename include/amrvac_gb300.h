@@ -43,6 +43,9 @@ enum { AMR_SSPRK2 = 2, AMR_SSPRK3 = 3 };
 enum { AMR_BC_PERIODIC = 0, AMR_BC_OUTFLOW = 1 };
 enum { AMR_FP64 = 0, AMR_FP32 = 1 };
 enum { AMR_NB_BOUNDARY = -1 };
+enum { MG_BC_PERIODIC = 0, MG_BC_NEUMANN = 1 };
+enum { RD_GRAY_SCOTT = 0, RD_SCHNAKENBERG = 1 };
+enum { RD_IMEX = 0, RD_SPLIT = 1, RD_EXPLICIT = 2 };
 
 /* ------------------------------------------------------------------------
  * Block-tree finite-volume Euler solver.
@@ -197,9 +200,10 @@ int amr_reduce_noalloc(const amr_config* cfg, const double* U, long long nleaves
 
 /* ------------------------------------------------------------------------
  * Batched Helmholtz multigrid (Sec. 2.5.1, Eq. (diff-helmholtz); Sec. 1.4).
- * Solves (lambda_i - lap_h) x = b for n_inst independent periodic square
- * (cube) grids of side n_cells[i] on [0, L]^ndim, cell-centred 5/7-point
- * Laplacian.  Red-black Gauss-Seidel smoothing (nu1 pre, nu2 post),
+ * Solves (lambda_i - lap_h) x = b for n_inst independent square (cube) grids
+ * of side n_cells[i] on [0, L]^ndim, cell-centred 5/7-point Laplacian, with
+ * periodic or zero-flux (Neumann, Sec. 2.5.2) boundaries: a Neumann boundary
+ * cell sums only its in-domain neighbours, (sum - count x) / h^2.  Red-black Gauss-Seidel smoothing (nu1 pre, nu2 post),
  * restriction = mean of 2^ndim children, cell-centred (bi/tri)linear
  * prolongation, coarsening while the side is even and > coarse_max, exact
  * solve on the coarsest grid.  Iterates until max|b - A x| <= rtol * max|b|
@@ -221,6 +225,7 @@ typedef struct {
   int coarse_max;       /* 8 */
   int precision;        /* AMR_FP32 or AMR_FP64 */
   void* stream;
+  int bc;               /* MG_BC_PERIODIC or MG_BC_NEUMANN */
 } mg_config;
 
 int mg_create(const mg_config* cfg, mg_handle** out);
@@ -236,10 +241,18 @@ int mg_solve(mg_handle* h, const double* b, double* x, int on_device, int* cycle
 int mg_num_unknowns(const mg_handle* h, long long* n);
 
 /* ------------------------------------------------------------------------
- * Gray-Scott reaction-diffusion with the IMEX trapezoidal scheme (Sec. 2.5,
- * Eq. (gray-scott), Eq. (imex)): reaction explicit, diffusion implicit through
- * the batched multigrid above with lambda = 2/(dt D) per species; both species
- * of all instances form one multigrid batch.  Initial guess: w_n.
+ * Reaction-diffusion steps (Sec. 2.5): w = (u, v), dw/dt = F0(w) + F1(w), with
+ * F0 the reaction terms of Eq. (gray-scott) (model RD_GRAY_SCOTT: F, k) or
+ * Eq. (schnakenberg) (RD_SCHNAKENBERG: kappa, a, b) and F1 = D lap_h w.
+ * Schemes:
+ *  RD_IMEX, Eq. (imex): reaction explicit, diffusion implicit through the
+ *    batched multigrid above with lambda = 2/(dt D) per species; guess w_n.
+ *  RD_SPLIT, Eqs. (splitting), (diff-helmholtz): w* = w_n + dt F0(w_n), then
+ *    (lambda - lap_h) w_{n+1} = lambda w* with lambda = 1/(dt D); guess w*.
+ *  RD_EXPLICIT: three-stage SSP Runge-Kutta on F0 + F1 (no multigrid); stable
+ *    for dt below about h^2 / (2 ndim max(Du, Dv)) (Sec. 2.5.1).
+ * Both species of all instances form one multigrid batch.  Boundaries: bc
+ * (MG_BC_PERIODIC or MG_BC_NEUMANN, zero flux).
  * ------------------------------------------------------------------------ */
 typedef struct rd_handle rd_handle;
 
@@ -252,6 +265,10 @@ typedef struct {
   int coarse_max;
   int precision;        /* AMR_FP32 (float smoothing) or AMR_FP64 */
   void* stream;
+  int model;            /* RD_GRAY_SCOTT or RD_SCHNAKENBERG */
+  double kappa, a, b;   /* Schnakenberg constants */
+  int scheme;           /* RD_IMEX, RD_SPLIT or RD_EXPLICIT */
+  int bc;               /* MG_BC_PERIODIC or MG_BC_NEUMANN */
 } rd_config;
 
 int rd_create(const rd_config* cfg, rd_handle** out);
@@ -260,8 +277,9 @@ const char* rd_last_error(const rd_handle* h);
 /* u, v packed instance after instance (as mg_solve). Synchronous. */
 int rd_set_state(rd_handle* h, const double* u, const double* v, int on_device);
 int rd_read_state(rd_handle* h, double* u, double* v, int on_device);
-/* nsteps IMEX steps; cycles (host, may be NULL) receives [step][2*n_inst]
- * V-cycles (species-major: u of every instance, then v).  Synchronous. */
+/* nsteps steps of the configured scheme; cycles (host, may be NULL) receives
+ * [step][2*n_inst] V-cycles (species-major: u of every instance, then v; 0 for
+ * RD_EXPLICIT).  Synchronous. */
 int rd_step(rd_handle* h, int nsteps, int* cycles);
 
 /* ------------------------------------------------------------------------

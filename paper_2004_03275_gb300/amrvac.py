@@ -47,8 +47,13 @@ class MgConfig(C.Structure):
         ("ndim", C.c_int), ("n_inst", C.c_int), ("n_cells", C.POINTER(C.c_int)),
         ("lam", C.POINTER(C.c_double)), ("L", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
         ("max_cycles", C.c_int), ("rtol", C.c_double), ("coarse_max", C.c_int), ("precision", C.c_int),
-        ("stream", C.c_void_p),
+        ("stream", C.c_void_p), ("bc", C.c_int),
     ]
+
+
+MG_BC = {"periodic": 0, "neumann": 1}
+RD_MODEL = {"gray-scott": 0, "schnakenberg": 1}
+RD_SCHEME = {"imex": 0, "split": 1, "explicit": 2}
 
 
 class RdConfig(C.Structure):
@@ -57,6 +62,8 @@ class RdConfig(C.Structure):
         ("Du", C.c_double), ("Dv", C.c_double), ("F", C.c_double), ("k", C.c_double), ("dt", C.c_double),
         ("nu1", C.c_int), ("nu2", C.c_int), ("max_cycles", C.c_int), ("rtol", C.c_double),
         ("coarse_max", C.c_int), ("precision", C.c_int), ("stream", C.c_void_p),
+        ("model", C.c_int), ("kappa", C.c_double), ("a", C.c_double), ("b", C.c_double), ("scheme", C.c_int),
+        ("bc", C.c_int),
     ]
 
 
@@ -351,7 +358,7 @@ class MgSolver:
     """Owns one mg_handle: batched Helmholtz multigrid (lambda_i - lap) x = b."""
 
     def __init__(self, ndim, n_cells, lam, L, nu1=2, nu2=2, max_cycles=50, rtol=1e-10, coarse_max=8,
-                 precision="fp32", stream=None):
+                 precision="fp32", stream=None, bc="periodic"):
         self.lib = load()
         self.n_cells = np.ascontiguousarray(n_cells, dtype=np.int32)
         self.lam = np.ascontiguousarray(np.broadcast_to(np.asarray(lam, dtype=np.float64), self.n_cells.shape))
@@ -364,6 +371,7 @@ class MgSolver:
         c.nu1, c.nu2, c.max_cycles, c.rtol, c.coarse_max = nu1, nu2, max_cycles, rtol, coarse_max
         c.precision = PRECISION[precision] if isinstance(precision, str) else precision
         c.stream = stream
+        c.bc = MG_BC[bc]
         self.ndim = ndim
         h = _vp()
         rc = self.lib.mg_create(C.byref(c), C.byref(h))
@@ -405,10 +413,13 @@ class MgSolver:
 
 
 class RdSolver:
-    """Owns one rd_handle: Gray-Scott IMEX steps for a batch of periodic instances."""
+    """Owns one rd_handle: reaction-diffusion steps for a batch of instances.  model
+    "gray-scott" (F, k) or "schnakenberg" (kappa, a, b); scheme "imex", "split" or "explicit";
+    bc "periodic" or "neumann"."""
 
-    def __init__(self, ndim, n_cells, L, Du, Dv, F, k, dt, nu1=2, nu2=2, max_cycles=50, rtol=1e-10,
-                 coarse_max=8, precision="fp32", stream=None):
+    def __init__(self, ndim, n_cells, L, Du, Dv, dt, F=0.0, k=0.0, nu1=2, nu2=2, max_cycles=50, rtol=1e-10,
+                 coarse_max=8, precision="fp32", stream=None, model="gray-scott", kappa=0.0, a=0.0, b=0.0,
+                 scheme="imex", bc="periodic"):
         self.lib = load()
         self.n_cells = np.ascontiguousarray(n_cells, dtype=np.int32)
         c = RdConfig()
@@ -418,6 +429,8 @@ class RdSolver:
         c.nu1, c.nu2, c.max_cycles, c.rtol, c.coarse_max = nu1, nu2, max_cycles, rtol, coarse_max
         c.precision = PRECISION[precision] if isinstance(precision, str) else precision
         c.stream = stream
+        c.model, c.kappa, c.a, c.b = RD_MODEL[model], kappa, a, b
+        c.scheme, c.bc = RD_SCHEME[scheme], MG_BC[bc]
         self.ndim = ndim
         h = _vp()
         rc = self.lib.rd_create(C.byref(c), C.byref(h))

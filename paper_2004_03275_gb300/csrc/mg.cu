@@ -1,11 +1,18 @@
-// Batched geometric multigrid for (lambda - lap_h) x = b on periodic grids, and
-// the Gray-Scott IMEX step built on it.
+// Batched geometric multigrid for (lambda - lap_h) x = b on periodic or zero-flux
+// (Neumann) grids, and the reaction-diffusion steps built on it.
 //
 // Paper: Sec. 2.5.1, Eq. (diff-helmholtz): the implicit diffusion stage is a
 // Helmholtz problem solved by geometric multigrid (Sec. 1.4, linear cost);
-// Eq. (imex): IMEX trapezoidal scheme; Eq. (gray-scott): reaction terms; Sec.
-// 2.5.2: iterate until the maximum residual is below a fraction of the
-// right-hand side.
+// Eq. (imex): IMEX trapezoidal scheme; Eq. (splitting): the split scheme;
+// Eqs. (gray-scott), (schnakenberg): reaction terms; Sec. 2.5.2: iterate until
+// the maximum residual is below a fraction of the right-hand side, Neumann
+// boundaries for the Schnakenberg runs.
+//
+// Neumann boundaries: a boundary face carries no flux, so a boundary cell sums
+// only its in-domain neighbours and its diagonal is lambda + count / h^2 (the
+// reciprocal diagonals are tabulated per level and per number of missing
+// neighbours); the prolongation puts the weight of a coarse neighbour beyond the
+// boundary on the parent.
 //
 // Layout: every multigrid instance owns a chain of levels (side n, n/2, ...,
 // coarsest when the side is odd or <= coarse_max); level arrays of all
@@ -46,8 +53,8 @@ struct InstDev {
   float ih2f[kMaxLev];
   double lam;
   float lamf;
-  double idiag[kMaxLev];        // 1 / (lambda + 2 ndim / h^2): the smoother multiplies by it
-  float idiagf[kMaxLev];
+  double idiag[kMaxLev][7];     // 1 / (lambda + (2 ndim - m) / h^2) for m neighbours beyond a
+  float idiagf[kMaxLev][7];     // Neumann boundary (m = 0 inside and on periodic grids)
   long long off0;          // offset into X / B
   long long inv_off;       // offset into the coarsest inverse matrices
 };
@@ -66,6 +73,7 @@ struct MgState {
   int* any;                   // any instance active (for the host)
   const double* inv;          // dense inverses of the coarsest operators
   int ndim;
+  int neu;                    // Neumann (zero-flux) boundaries, else periodic
   double rtol;
   int max_cycles;
 };
@@ -114,28 +122,33 @@ __device__ __forceinline__ long long lin(const int* c, int n) {
   return (long long)c[0] + (long long)n * ((long long)c[1] + (long long)n * c[2]);
 }
 
-// sum of the 2 ndim neighbours, ordered x-, x+, y-, y+, z-, z+
+// neighbour index i (at most one cell outside [0, n)): the periodic image, or the cell
+// itself (ci) beyond a Neumann boundary, where the prolongation uses the parent
+__device__ __forceinline__ int nbr_or_self(int i, int ci, int n, bool neu) {
+  return i < 0 ? (neu ? ci : i + n) : (i >= n ? (neu ? ci : i - n) : i);
+}
+
+// sum of the neighbours, ordered x-, x+, y-, y+, z-, z+: all 2 ndim on a periodic grid
+// (images across the boundary), only the in-domain ones on a Neumann grid; *miss gets the
+// number left out
 template <typename T>
-__device__ __forceinline__ T nbsum(const T* x, const int* c, int n, int nd) {
-  int q[3] = {c[0], c[1], c[2]};
-  q[0] = wrapi(c[0] - 1, n);
-  T s = x[lin(q, n)];
-  q[0] = wrapi(c[0] + 1, n);
-  s = s + x[lin(q, n)];
-  q[0] = c[0];
-  if (nd > 1) {
-    q[1] = wrapi(c[1] - 1, n);
-    s = s + x[lin(q, n)];
-    q[1] = wrapi(c[1] + 1, n);
-    s = s + x[lin(q, n)];
-    q[1] = c[1];
+__device__ __forceinline__ T nbsum(const T* x, const int* c, int n, int nd, bool neu, int* miss) {
+  T s = T(0);
+  int m = 0;
+  for (int d = 0; d < nd; ++d) {
+#pragma unroll
+    for (int side = -1; side <= 1; side += 2) {
+      int q[3] = {c[0], c[1], c[2]};
+      int t = c[d] + side;
+      if (neu && (t < 0 || t >= n)) {
+        ++m;
+        continue;
+      }
+      q[d] = wrapi(t, n);
+      s = s + x[lin(q, n)];
+    }
   }
-  if (nd > 2) {
-    q[2] = wrapi(c[2] - 1, n);
-    s = s + x[lin(q, n)];
-    q[2] = wrapi(c[2] + 1, n);
-    s = s + x[lin(q, n)];
-  }
+  *miss = m;
   return s;
 }
 
@@ -146,11 +159,11 @@ __device__ __forceinline__ double ih2_of<double>(const InstDev& I, int l) { retu
 template <>
 __device__ __forceinline__ float ih2_of<float>(const InstDev& I, int l) { return I.ih2f[l]; }
 template <typename real>
-__device__ __forceinline__ real idiag_of(const InstDev& I, int l);
+__device__ __forceinline__ real idiag_of(const InstDev& I, int l, int miss);
 template <>
-__device__ __forceinline__ double idiag_of<double>(const InstDev& I, int l) { return I.idiag[l]; }
+__device__ __forceinline__ double idiag_of<double>(const InstDev& I, int l, int miss) { return I.idiag[l][miss]; }
 template <>
-__device__ __forceinline__ float idiag_of<float>(const InstDev& I, int l) { return I.idiagf[l]; }
+__device__ __forceinline__ float idiag_of<float>(const InstDev& I, int l, int miss) { return I.idiagf[l][miss]; }
 template <typename real>
 __device__ __forceinline__ real lam_of(const InstDev& I);
 template <>
@@ -235,10 +248,12 @@ __global__ void residual64_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
     cell_of(t, n, S.ndim, c);
     const double* X = S.X + I.off0;
     double x = X[t];
-    // r = B + ih2 (nbsum - 2 ndim x) - lambda x in three fused multiply-adds: the float64
+    // r = B + ih2 (nbsum - count x) - lambda x in three fused multiply-adds: the float64
     // unit is GB300's scarcest pipe, so the residual uses as few float64 operations as it can
-    const double m2nd = S.ndim == 3 ? -6.0 : -4.0;
-    double r = fma(fma(m2nd, x, nbsum(X, c, n, S.ndim)), I.ih2[0], S.B[I.off0 + t]);
+    int miss;
+    const double s = nbsum(X, c, n, S.ndim, S.neu != 0, &miss);
+    const double mcount = (double)(miss - 2 * S.ndim);
+    double r = fma(fma(mcount, x, s), I.ih2[0], S.B[I.off0 + t]);
     r = fma(-I.lam, x, r);
     L.b[I.off[0] + t] = narrow<real>(r);
     L.x[I.off[0] + t] = real(0);
@@ -272,7 +287,7 @@ __global__ void check_kernel(MgState S, int ninst) {
   if (threadIdx.x == 0) *S.any = any;
 }
 
-// red-black Gauss-Seidel sweep of one colour: x = (b + nbsum * ih2) / (lambda + 2 ndim ih2)
+// red-black Gauss-Seidel sweep of one colour: x = (b + nbsum * ih2) / (lambda + count ih2)
 template <typename real>
 __global__ void smooth_kernel(MgState S, Lvl<real> L, const Chunk* ch, int colour) {
   Chunk C = ch[blockIdx.x];
@@ -291,9 +306,10 @@ __global__ void smooth_kernel(MgState S, Lvl<real> L, const Chunk* ch, int colou
   real* x = L.x + I.off[l];
   const real* b = L.b + I.off[l];
   real ih2 = ih2_of<real>(I, l);
-  const real idg = idiag_of<real>(I, l);
   long long q = lin(c, n);
-  x[q] = (b[q] + nbsum(x, c, n, nd) * ih2) * idg;
+  int miss;
+  const real sn = nbsum(x, c, n, nd, S.neu != 0, &miss);
+  x[q] = (b[q] + sn * ih2) * idiag_of<real>(I, l, miss);
 }
 
 // One full red-black sweep of a 2D level, one warp per strip of kStripW columns and
@@ -307,6 +323,9 @@ __global__ void smooth_kernel(MgState S, Lvl<real> L, const Chunk* ch, int colou
 // neighbours: its own rows s - 1 and s + 1, row s of the lanes beside it), and stores
 // row s.  It reads one iterate array and writes the other, so no warp sees another's
 // writes; the updates and their arithmetic are those of two in-place colour sweeps.
+// NEU (zero-flux boundaries): cells outside the domain read as 0 and are never
+// updated, so they add nothing to a neighbour sum, and a boundary cell divides by its
+// own diagonal lambda + count / h^2.
 constexpr int kStripW = 28, kStripHMax = 64, kPre = 4;
 
 inline int strip_height(int n) { return std::min(kStripHMax, std::max(8, n / 32)); }
@@ -333,7 +352,7 @@ __device__ __forceinline__ StripGeom strip_geom(int n, long long start, int H, i
 
 __device__ __forceinline__ int wrap_row(int r, int n) { return r < 0 ? r + n : (r >= n ? r - n : r); }
 
-template <typename real>
+template <typename real, bool NEU>
 __global__ void __launch_bounds__(128)
     sweep2d_kernel(MgState S, const real* __restrict__ xin, real* __restrict__ xout, const real* __restrict__ bl,
                    const Chunk* ch, int nch) {
@@ -349,17 +368,26 @@ __global__ void __launch_bounds__(128)
   const real* x = xin + I.off[l];
   const real* b = bl + I.off[l];
   real* xo = xout + I.off[l];
-  const real ih2 = ih2_of<real>(I, l), idg = idiag_of<real>(I, l);
+  const real ih2 = ih2_of<real>(I, l), idg = idiag_of<real>(I, l, 0);
   // rows stay within one period of [0, n) when n > H + kPre + 2; else a full modulo
   const bool one_wrap = n > C.count + kPre + 2;
   auto rowof = [&](int r) { return one_wrap ? wrap_row(r, n) : ((r % n) + n) % n; };
-  auto ldx = [&](int r) { return x[rowof(r) * n + c]; };
+  const int craw = g.x0 - 2 + lane;  // this lane's column before the periodic wrap
+  const bool colin = craw >= 0 && craw < n;
+  auto inside = [&](int r) { return !NEU || (colin && r >= 0 && r < n); };
+  auto ldx = [&](int r) { return inside(r) ? x[rowof(r) * n + c] : real(0); };
   auto ldb = [&](int r) { return b[rowof(r) * n + c]; };
+  // reciprocal diagonal of this lane's cell in row r
+  auto idg_at = [&](int r) {
+    if constexpr (!NEU) return idg;
+    const int m = (craw == 0) + (craw == n - 1) + (r == 0) + (r == n - 1);
+    return idiag_of<real>(I, l, m);
+  };
   // red update of row r from old rows om, o0 (row r), op; black cells keep o0
   auto red = [&](real om, real o0, real op, real bb, int r) {
     const real lft = __shfl_up_sync(kFull, o0, 1), rgt = __shfl_down_sync(kFull, o0, 1);
-    const real v = (bb + (lft + rgt + om + op) * ih2) * idg;
-    return ((c + rowof(r)) & 1) == 0 ? v : o0;
+    const real v = (bb + (lft + rgt + om + op) * ih2) * idg_at(r);
+    return inside(r) ? (((c + rowof(r)) & 1) == 0 ? v : o0) : real(0);
   };
   const int y0 = g.y0, y1 = g.y1;
   // old rows y0-2 .. y0+1, red rows y0-1 and y0
@@ -389,7 +417,7 @@ __global__ void __launch_bounds__(128)
     const real r_p = red(o_s, o_s1, o_s2, b_s1, s + 1);
     // black cells of row s
     const real lft = __shfl_up_sync(kFull, r_0, 1), rgt = __shfl_down_sync(kFull, r_0, 1);
-    const real v = (b_0 + (lft + rgt + r_m + r_p) * ih2) * idg;
+    const real v = (b_0 + (lft + rgt + r_m + r_p) * ih2) * idg_at(s);
     const real outv = ((c + rowof(s)) & 1) == 1 ? v : r_0;
     if (g.out_lane) xo[s * n + c] = outv;
     r_m = r_0;
@@ -427,11 +455,13 @@ __global__ void prolong2d_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
   unsigned t = (unsigned)(C.start + threadIdx.x);  // coarse cell
   int cj = (int)(t / (unsigned)nc), ci = (int)(t - (unsigned)cj * (unsigned)nc);
   const real* ec = L.x + I.off[l + 1];
+  const bool neu = S.neu != 0;
   real v[3][3];
 #pragma unroll
   for (int dj = -1; dj <= 1; ++dj)
 #pragma unroll
-    for (int di = -1; di <= 1; ++di) v[dj + 1][di + 1] = ec[(long long)wrapi(cj + dj, nc) * nc + wrapi(ci + di, nc)];
+    for (int di = -1; di <= 1; ++di)
+      v[dj + 1][di + 1] = ec[(long long)nbr_or_self(cj + dj, cj, nc, neu) * nc + nbr_or_self(ci + di, ci, nc, neu)];
   real* xf = L.x + I.off[l];
 #pragma unroll
   for (int b2 = 0; b2 < 2; ++b2)
@@ -468,7 +498,9 @@ __global__ void resrestrict_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
     int f[3] = {2 * cc[0] + (o & 1), nd > 1 ? 2 * cc[1] + ((o >> 1) & 1) : 0, nd > 2 ? 2 * cc[2] + ((o >> 2) & 1) : 0};
     long long q = lin(f, nf);
     real xv = x[q];
-    real lap = (nbsum(x, f, nf, nd) - real(2 * nd) * xv) * ih2;
+    int miss;
+    const real sn = nbsum(x, f, nf, nd, S.neu != 0, &miss);
+    real lap = (sn - real(2 * nd - miss) * xv) * ih2;
     sum = sum + (b[q] - (lam * xv - lap));
   }
   L.b[I.off[l + 1] + t] = sum * (real(1) / real(1 << nd));
@@ -494,8 +526,9 @@ __global__ void prolong_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
   for (int z = 0; z < cz; ++z)
     for (int y = 0; y < cy; ++y)
       for (int xx = 0; xx < 2; ++xx) {
-        int q[3] = {wrapi(P[0] + xx * sg[0], nc), nd > 1 ? wrapi(P[1] + y * sg[1], nc) : 0,
-                    nd > 2 ? wrapi(P[2] + z * sg[2], nc) : 0};
+        const bool neu = S.neu != 0;
+        int q[3] = {nbr_or_self(P[0] + xx * sg[0], P[0], nc, neu), nd > 1 ? nbr_or_self(P[1] + y * sg[1], P[1], nc, neu) : 0,
+                    nd > 2 ? nbr_or_self(P[2] + z * sg[2], P[2], nc, neu) : 0};
         real w = xx ? real(0.25) : real(0.75);
         if (nd > 1) w = w * (y ? real(0.25) : real(0.75));
         if (nd > 2) w = w * (z ? real(0.25) : real(0.75));
@@ -541,27 +574,46 @@ __global__ void correct64_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
     S.X[I.off0 + t] = S.X[I.off0 + t] + e;
 }
 
-// ------------------------------------------------------- Gray-Scott IMEX --
+// ------------------------------------------------------ reaction-diffusion --
 // Eq. (gray-scott): F0_u = -u v^2 + F(1-u), F0_v = u v^2 - (F+k) v.
-// Eq. (imex) stage 1: B = lambda g, g = w + dt F0(w) + dt/2 D lap w, X = w (guess);
-// Fn = F0(w) + D lap w kept for stage 2.
+// Eq. (schnakenberg): F0_u = kappa (a - u + u^2 v), F0_v = kappa (b - u^2 v).
+// IMEX, Eq. (imex): stage 1 B = lambda g, g = w + dt F0(w) + dt/2 D lap w, X = w (guess),
+//   Fn = F0(w) + D lap w kept for stage 2; after the solve w += dt/2 [Fn + F(w*)].
+// Split, Eqs. (splitting), (diff-helmholtz): B = lambda w*, X = w* = w + dt F0(w); after
+//   the solve w = X.
+// Explicit: three-stage SSP Runge-Kutta on F = F0 + D lap w, one kernel per stage.
 struct RdArgs {
   const InstDev* inst;  // multigrid instances: species s of instance i is s*ninst + i
-  int ninst, ndim;
-  double F, k, dt, D[2], lam[2];
+  int ninst, ndim, model, neu;
+  double F, k, kappa, a, b, dt, D[2], lam[2];
   double* u;
   double* v;            // state, packed like level 0 of one species
-  double* X;            // multigrid iterate (2 species)
-  double* B;            // multigrid right-hand side
+  double* X;            // multigrid iterate (2 species); explicit: stage 1 state
+  double* B;            // multigrid right-hand side; explicit: stage 2 state
   double* Fn;           // F(w_n) per species
 };
 
-__device__ __forceinline__ void reaction(double F, double k, double u, double v, double* fu, double* fv) {
-  double uvv = (u * v) * v;
-  *fu = -uvv + F * (1.0 - u);
-  *fv = uvv - (F + k) * v;
+__device__ __forceinline__ void reaction(const RdArgs& A, double u, double v, double* fu, double* fv) {
+  if (A.model == RD_SCHNAKENBERG) {
+    double uuv = (u * u) * v;
+    *fu = A.kappa * ((A.a - u) + uuv);
+    *fv = A.kappa * (A.b - uuv);
+  } else {
+    double uvv = (u * v) * v;
+    *fu = -uvv + A.F * (1.0 - u);
+    *fv = uvv - (A.F + A.k) * v;
+  }
 }
 
+// (sum of in-domain neighbours - count x) / h^2 on level 0
+__device__ __forceinline__ double rd_lap(const RdArgs& A, const double* x, const int* c, int n, long long t,
+                                         double ih2) {
+  int miss;
+  double s = nbsum(x, c, n, A.ndim, A.neu != 0, &miss);
+  return (s - (double)(2 * A.ndim - miss) * x[t]) * ih2;
+}
+
+template <int SCHEME>
 __global__ void rd_rhs_kernel(RdArgs A, const Chunk* ch) {
   Chunk C = ch[blockIdx.x];  // chunks over level 0 of species-0 instances
   if (threadIdx.x >= C.count) return;
@@ -574,21 +626,60 @@ __global__ void rd_rhs_kernel(RdArgs A, const Chunk* ch) {
   const double* u = A.u + o;
   const double* v = A.v + o;
   double fu, fv;
-  reaction(A.F, A.k, u[t], v[t], &fu, &fv);
-  double lu = (nbsum(u, c, n, A.ndim) - (2.0 * A.ndim) * u[t]) * I0.ih2[0];
-  double lv = (nbsum(v, c, n, A.ndim) - (2.0 * A.ndim) * v[t]) * I0.ih2[0];
-  double gu = (u[t] + A.dt * fu) + ((0.5 * A.dt) * A.D[0]) * lu;
-  double gv = (v[t] + A.dt * fv) + ((0.5 * A.dt) * A.D[1]) * lv;
-  A.B[I0.off0 + t] = A.lam[0] * gu;
-  A.B[I1.off0 + t] = A.lam[1] * gv;
-  A.X[I0.off0 + t] = u[t];
-  A.X[I1.off0 + t] = v[t];
-  A.Fn[I0.off0 + t] = fu + A.D[0] * lu;
-  A.Fn[I1.off0 + t] = fv + A.D[1] * lv;
+  reaction(A, u[t], v[t], &fu, &fv);
+  if constexpr (SCHEME == RD_SPLIT) {
+    double us = u[t] + A.dt * fu, vs = v[t] + A.dt * fv;
+    A.B[I0.off0 + t] = A.lam[0] * us;
+    A.B[I1.off0 + t] = A.lam[1] * vs;
+    A.X[I0.off0 + t] = us;
+    A.X[I1.off0 + t] = vs;
+  } else {
+    double lu = rd_lap(A, u, c, n, t, I0.ih2[0]);
+    double lv = rd_lap(A, v, c, n, t, I0.ih2[0]);
+    double gu = (u[t] + A.dt * fu) + ((0.5 * A.dt) * A.D[0]) * lu;
+    double gv = (v[t] + A.dt * fv) + ((0.5 * A.dt) * A.D[1]) * lv;
+    A.B[I0.off0 + t] = A.lam[0] * gu;
+    A.B[I1.off0 + t] = A.lam[1] * gv;
+    A.X[I0.off0 + t] = u[t];
+    A.X[I1.off0 + t] = v[t];
+    A.Fn[I0.off0 + t] = fu + A.D[0] * lu;
+    A.Fn[I1.off0 + t] = fv + A.D[1] * lv;
+  }
 }
 
-// Eq. (imex) stage 2: w_{n+1} = w_n + dt/2 [F(w_n) + F(w*)]
+// after the solve: IMEX w_{n+1} = w_n + dt/2 [F(w_n) + F(w*)]; split w_{n+1} = X
+template <int SCHEME>
 __global__ void rd_finish_kernel(RdArgs A, const Chunk* ch) {
+  Chunk C = ch[blockIdx.x];
+  if (threadIdx.x >= C.count) return;
+  const InstDev& I0 = A.inst[C.inst];
+  const InstDev& I1 = A.inst[C.inst + A.ninst];
+  long long t = C.start + threadIdx.x;
+  long long o = I0.off0;
+  const double* us = A.X + I0.off0;
+  const double* vs = A.X + I1.off0;
+  if constexpr (SCHEME == RD_SPLIT) {
+    A.u[o + t] = us[t];
+    A.v[o + t] = vs[t];
+  } else {
+    int n = I0.n[0], c[3];
+    cell_of(t, n, A.ndim, c);
+    double fu, fv;
+    reaction(A, us[t], vs[t], &fu, &fv);
+    double lu = rd_lap(A, us, c, n, t, I0.ih2[0]);
+    double lv = rd_lap(A, vs, c, n, t, I0.ih2[0]);
+    double Fu = fu + A.D[0] * lu, Fv = fv + A.D[1] * lv;
+    A.u[o + t] = A.u[o + t] + (0.5 * A.dt) * (A.Fn[I0.off0 + t] + Fu);
+    A.v[o + t] = A.v[o + t] + (0.5 * A.dt) * (A.Fn[I1.off0 + t] + Fv);
+  }
+}
+
+// Explicit step, stage S of the three-stage SSP Runge-Kutta scheme (w = state u, v):
+//   S = 0: X = w + dt F(w);  S = 1: B = 3/4 w + 1/4 (X + dt F(X));
+//   S = 2: w = 1/3 w + 2/3 (B + dt F(B)).
+// Stage 2 overwrites w in place: each cell reads only its own w and neighbours of B.
+template <int S>
+__global__ void rd_explicit_kernel(RdArgs A, const Chunk* ch) {
   Chunk C = ch[blockIdx.x];
   if (threadIdx.x >= C.count) return;
   const InstDev& I0 = A.inst[C.inst];
@@ -596,16 +687,24 @@ __global__ void rd_finish_kernel(RdArgs A, const Chunk* ch) {
   long long t = C.start + threadIdx.x;
   int n = I0.n[0], c[3];
   cell_of(t, n, A.ndim, c);
-  const double* us = A.X + I0.off0;
-  const double* vs = A.X + I1.off0;
+  const long long o = I0.off0;
+  const double* su = S == 0 ? A.u + o : (S == 1 ? A.X + I0.off0 : A.B + I0.off0);
+  const double* sv = S == 0 ? A.v + o : (S == 1 ? A.X + I1.off0 : A.B + I1.off0);
   double fu, fv;
-  reaction(A.F, A.k, us[t], vs[t], &fu, &fv);
-  double lu = (nbsum(us, c, n, A.ndim) - (2.0 * A.ndim) * us[t]) * I0.ih2[0];
-  double lv = (nbsum(vs, c, n, A.ndim) - (2.0 * A.ndim) * vs[t]) * I0.ih2[0];
-  double Fu = fu + A.D[0] * lu, Fv = fv + A.D[1] * lv;
-  long long o = I0.off0;
-  A.u[o + t] = A.u[o + t] + (0.5 * A.dt) * (A.Fn[I0.off0 + t] + Fu);
-  A.v[o + t] = A.v[o + t] + (0.5 * A.dt) * (A.Fn[I1.off0 + t] + Fv);
+  reaction(A, su[t], sv[t], &fu, &fv);
+  const double Fu = fu + A.D[0] * rd_lap(A, su, c, n, t, I0.ih2[0]);
+  const double Fv = fv + A.D[1] * rd_lap(A, sv, c, n, t, I0.ih2[0]);
+  const double eu = su[t] + A.dt * Fu, ev = sv[t] + A.dt * Fv;
+  if constexpr (S == 0) {
+    A.X[I0.off0 + t] = eu;
+    A.X[I1.off0 + t] = ev;
+  } else if constexpr (S == 1) {
+    A.B[I0.off0 + t] = 0.75 * A.u[o + t] + 0.25 * eu;
+    A.B[I1.off0 + t] = 0.75 * A.v[o + t] + 0.25 * ev;
+  } else {
+    A.u[o + t] = (1.0 / 3.0) * A.u[o + t] + (2.0 / 3.0) * eu;
+    A.v[o + t] = (1.0 / 3.0) * A.v[o + t] + (2.0 / 3.0) * ev;
+  }
 }
 
 // ------------------------------------------------------- learned guess --
@@ -698,9 +797,10 @@ struct DevBuf {
   T* as() const { return reinterpret_cast<T*>(p); }
 };
 
-// Dense inverse of the periodic operator (lambda - lap_h) by Gauss-Jordan with
+// Dense inverse of the operator (lambda - lap_h), periodic or Neumann (a neighbour beyond
+// the boundary is left out of the row and of its diagonal count), by Gauss-Jordan with
 // partial pivoting (host, float64).
-bool dense_inverse(int nd, int n, double L, double lambda, std::vector<double>& inv) {
+bool dense_inverse(int nd, int n, double L, double lambda, bool neu, std::vector<double>& inv) {
   int m = 1;
   for (int d = 0; d < nd; ++d) m *= n;
   double h = L / n, ih2 = 1.0 / (h * h);
@@ -708,14 +808,17 @@ bool dense_inverse(int nd, int n, double L, double lambda, std::vector<double>& 
   inv.assign((size_t)m * m, 0.0);
   for (int r = 0; r < m; ++r) {
     int c[3] = {r % n, nd > 1 ? (r / n) % n : 0, nd > 2 ? r / (n * n) : 0};
-    A[(size_t)r * m + r] += lambda + 2.0 * nd * ih2;
+    int count = 0;
     for (int d = 0; d < nd; ++d)
       for (int s = -1; s <= 1; s += 2) {
         int q[3] = {c[0], c[1], c[2]};
+        if (neu && (q[d] + s < 0 || q[d] + s >= n)) continue;
         q[d] = (q[d] + s + n) % n;
         int cidx = q[0] + n * (q[1] + n * q[2]);
         A[(size_t)r * m + cidx] -= ih2;
+        ++count;
       }
+    A[(size_t)r * m + r] += lambda + count * ih2;
     inv[(size_t)r * m + r] = 1.0;
   }
   for (int col = 0; col < m; ++col) {
@@ -752,6 +855,7 @@ void add_chunks(std::vector<Chunk>& v, int inst, int lev, long long count) {
 
 struct Mg {
   int nd = 2, ninst = 0, nu1 = 2, nu2 = 2, max_cycles = 50, precision = AMR_FP32;
+  bool neu = false;  // Neumann (zero-flux) boundaries, else periodic
   double rtol = 1e-10, Lside = 1.0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -802,17 +906,20 @@ struct Mg {
     S.any = d_any.as<int>();
     S.inv = d_inv.as<double>();
     S.ndim = nd;
+    S.neu = neu ? 1 : 0;
     S.rtol = rtol;
     S.max_cycles = max_cycles;
     return S;
   }
 
   int setup(int ndim, int n_inst, const int* n_cells, const double* lambda, double L, int nu1_, int nu2_, int maxc,
-            double rtol_, int coarse_max, int prec, void* strm) {
+            double rtol_, int coarse_max, int prec, int bc, void* strm) {
     if (ndim < 2 || ndim > 3 || n_inst < 1 || !n_cells || !lambda || !(L > 0) || nu1_ < 0 || nu2_ < 0 ||
-        maxc < 0 || !(rtol_ > 0) || coarse_max < 1 || (prec != AMR_FP32 && prec != AMR_FP64))
+        maxc < 0 || !(rtol_ > 0) || coarse_max < 1 || (prec != AMR_FP32 && prec != AMR_FP64) ||
+        (bc != MG_BC_PERIODIC && bc != MG_BC_NEUMANN))
       return fail(AMR_ERR_INVALID_ARG, "invalid multigrid configuration");
     nd = ndim;
+    neu = bc == MG_BC_NEUMANN;
     ninst = n_inst;
     nu1 = nu1_;
     nu2 = nu2_;
@@ -851,8 +958,11 @@ struct Mg {
         double h = L / m;
         I.ih2[l] = 1.0 / (h * h);
         I.ih2f[l] = (float)I.ih2[l];
-        I.idiag[l] = 1.0 / (lambda[i] + 2.0 * nd * I.ih2[l]);
-        I.idiagf[l] = (float)I.idiag[l];
+        for (int mm = 0; mm < 7; ++mm) {
+          const int count = std::max(0, 2 * nd - mm);
+          I.idiag[l][mm] = 1.0 / (lambda[i] + count * I.ih2[l]);
+          I.idiagf[l][mm] = (float)I.idiag[l][mm];
+        }
         ++l;
         if ((m & 1) || m <= coarse_max) break;
         m /= 2;
@@ -863,7 +973,7 @@ struct Mg {
       long long msz = 1;
       for (int d = 0; d < nd; ++d) msz *= mc;
       if (msz > 4096) return fail(AMR_ERR_INVALID_ARG, "coarsest grid too large (increase coarse_max or use sizes with more factors of 2)");
-      if (!dense_inverse(nd, mc, L, lambda[i], invs[i])) return fail(AMR_ERR_INVALID_ARG, "singular coarse operator");
+      if (!dense_inverse(nd, mc, L, lambda[i], neu, invs[i])) return fail(AMR_ERR_INVALID_ARG, "singular coarse operator");
       I.inv_off = invoff;
       invoff += msz * msz;
     }
@@ -970,7 +1080,10 @@ struct Mg {
         const Chunk* tl = all + off_tile[l];
         for (int s = 0; s < sweeps; ++s) {
           bool even = (s & 1) == 0;
-          sweep2d_kernel<real><<<nb, 128, 0, stream>>>(S, even ? Lv.x : Y, even ? Y : Lv.x, Lv.b, tl, nch);
+          if (neu)
+            sweep2d_kernel<real, true><<<nb, 128, 0, stream>>>(S, even ? Lv.x : Y, even ? Y : Lv.x, Lv.b, tl, nch);
+          else
+            sweep2d_kernel<real, false><<<nb, 128, 0, stream>>>(S, even ? Lv.x : Y, even ? Y : Lv.x, Lv.b, tl, nch);
           ++launches;
         }
         if (sweeps & 1) {
@@ -1078,8 +1191,18 @@ struct mg_handle {
   Mg mg;
 };
 
+// Helmholtz constant of species s: 2/(dt D) for the IMEX trapezoidal stage, 1/(dt D) for
+// the backward-Euler stage of the split scheme (the explicit scheme does not solve)
+inline double rd_lambda(const rd_config& c, int s) {
+  return (c.scheme == RD_SPLIT ? 1.0 : 2.0) / (c.dt * (s == 0 ? c.Du : c.Dv));
+}
+
 struct rd_handle {
   Mg mg;
+  cudaGraphExec_t egraph = nullptr;  // kExplicitGraphSteps explicit steps
+  ~rd_handle() {
+    if (egraph) cudaGraphExecDestroy(egraph);
+  }
   rd_config cfg{};
   std::vector<int> sizes;
   DevBuf d_u, d_v, d_Fn;
@@ -1100,7 +1223,7 @@ int mg_create(const mg_config* cfg, mg_handle** out) {
   *out = nullptr;
   std::unique_ptr<mg_handle> h(new mg_handle());
   int rc = h->mg.setup(cfg->ndim, cfg->n_inst, cfg->n_cells, cfg->lambda, cfg->L, cfg->nu1, cfg->nu2, cfg->max_cycles,
-                       cfg->rtol, cfg->coarse_max, cfg->precision, cfg->stream);
+                       cfg->rtol, cfg->coarse_max, cfg->precision, cfg->bc, cfg->stream);
   if (rc) return rc;
   *out = h.release();
   return AMR_OK;
@@ -1141,6 +1264,9 @@ int rd_create(const rd_config* cfg, rd_handle** out) {
   if (!cfg || !out || cfg->n_inst < 1 || !cfg->n_cells) return AMR_ERR_INVALID_ARG;
   *out = nullptr;
   if (!(cfg->dt > 0) || !(cfg->Du > 0) || !(cfg->Dv > 0)) return AMR_ERR_INVALID_ARG;
+  if ((cfg->model != RD_GRAY_SCOTT && cfg->model != RD_SCHNAKENBERG) ||
+      (cfg->scheme != RD_IMEX && cfg->scheme != RD_SPLIT && cfg->scheme != RD_EXPLICIT))
+    return AMR_ERR_INVALID_ARG;
   std::unique_ptr<rd_handle> h(new rd_handle());
   h->cfg = *cfg;
   h->sizes.assign(cfg->n_cells, cfg->n_cells + cfg->n_inst);
@@ -1151,10 +1277,10 @@ int rd_create(const rd_config* cfg, rd_handle** out) {
   for (int s = 0; s < 2; ++s)
     for (int i = 0; i < cfg->n_inst; ++i) {
       n2[s * cfg->n_inst + i] = cfg->n_cells[i];
-      lam[s * cfg->n_inst + i] = 2.0 / (cfg->dt * (s == 0 ? cfg->Du : cfg->Dv));
+      lam[s * cfg->n_inst + i] = rd_lambda(*cfg, s);
     }
   int rc = h->mg.setup(cfg->ndim, 2 * cfg->n_inst, n2.data(), lam.data(), cfg->L, cfg->nu1, cfg->nu2, cfg->max_cycles,
-                       cfg->rtol, cfg->coarse_max, cfg->precision, cfg->stream);
+                       cfg->rtol, cfg->coarse_max, cfg->precision, cfg->bc, cfg->stream);
   if (rc) return rc;
   h->cells = h->mg.insts[cfg->n_inst].off0;  // species-0 block size = cells of all instances
   for (int i = 0; i < cfg->n_inst; ++i) {
@@ -1199,21 +1325,29 @@ int rd_read_state(rd_handle* h, double* u, double* v, int on_device) {
   return M.cuda(cudaStreamSynchronize(M.stream), "sync");
 }
 
+constexpr int kExplicitGraphSteps = 32;
+
 int rd_step(rd_handle* h, int nsteps, int* cycles) {
   if (!h || nsteps < 0) return AMR_ERR_INVALID_ARG;
   Mg& M = h->mg;
   const int ni = h->cfg.n_inst;
+  const int scheme = h->cfg.scheme;
   RdArgs A{};
   A.inst = M.d_inst.as<InstDev>();
   A.ninst = ni;
   A.ndim = h->cfg.ndim;
+  A.model = h->cfg.model;
+  A.neu = h->cfg.bc == MG_BC_NEUMANN ? 1 : 0;
   A.F = h->cfg.F;
   A.k = h->cfg.k;
+  A.kappa = h->cfg.kappa;
+  A.a = h->cfg.a;
+  A.b = h->cfg.b;
   A.dt = h->cfg.dt;
   A.D[0] = h->cfg.Du;
   A.D[1] = h->cfg.Dv;
-  A.lam[0] = 2.0 / (h->cfg.dt * h->cfg.Du);
-  A.lam[1] = 2.0 / (h->cfg.dt * h->cfg.Dv);
+  A.lam[0] = rd_lambda(h->cfg, 0);
+  A.lam[1] = rd_lambda(h->cfg, 1);
   A.u = h->d_u.as<double>();
   A.v = h->d_v.as<double>();
   A.X = M.d_X.as<double>();
@@ -1223,19 +1357,53 @@ int rd_step(rd_handle* h, int nsteps, int* cycles) {
   unsigned nch0 = 0;
   for (const Chunk& c : M.ch0)
     if (c.inst < ni) ++nch0;
+  const Chunk* ch0 = M.d_ch0.as<Chunk>();
+  int rc;
+  if (scheme == RD_EXPLICIT) {
+    auto enqueue = [&](int k) {
+      for (int s = 0; s < k; ++s) {
+        rd_explicit_kernel<0><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
+        rd_explicit_kernel<1><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
+        rd_explicit_kernel<2><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
+      }
+    };
+    int left = nsteps;
+    if (nsteps >= kExplicitGraphSteps) {  // long runs: replay a captured graph of 32 steps
+      if (!h->egraph) {
+        cudaGraph_t g;
+        if ((rc = M.cuda(cudaStreamBeginCapture(M.stream, cudaStreamCaptureModeThreadLocal), "capture"))) return rc;
+        enqueue(kExplicitGraphSteps);
+        cudaError_t ec = cudaStreamEndCapture(M.stream, &g);
+        if ((rc = M.cuda(ec, "end capture"))) return rc;
+        rc = M.cuda(cudaGraphInstantiate(&h->egraph, g, 0), "instantiate");
+        cudaGraphDestroy(g);
+        if (rc) return rc;
+      }
+      for (; left >= kExplicitGraphSteps; left -= kExplicitGraphSteps)
+        if ((rc = M.cuda(cudaGraphLaunch(h->egraph, M.stream), "graph launch"))) return rc;
+    }
+    enqueue(left);
+    M.launches += 3LL * nsteps;
+    if (cycles) std::memset(cycles, 0, sizeof(int) * (size_t)nsteps * 2 * ni);
+    if ((rc = M.cuda(cudaGetLastError(), "rd launch"))) return rc;
+    return M.cuda(cudaStreamSynchronize(M.stream), "sync");
+  }
   const size_t cb = (size_t)h->cells * 8;
   double* wn = h->d_wn.as<double>();
   double* prev = h->d_prev.as<double>();
   double* pin = h->d_pin.as<double>();
   for (int s = 0; s < nsteps; ++s) {
-    int rc;
-    // keep w_n and the previous solution (inputs of the learned guess and of training crops)
-    if ((rc = M.cuda(cudaMemcpyAsync(wn, h->d_u.p, cb, cudaMemcpyDeviceToDevice, M.stream), "copy")) ||
-        (rc = M.cuda(cudaMemcpyAsync(wn + h->cells, h->d_v.p, cb, cudaMemcpyDeviceToDevice, M.stream), "copy")) ||
-        (rc = M.cuda(cudaMemcpyAsync(pin, h->have_prev ? prev : wn, 2 * cb, cudaMemcpyDeviceToDevice, M.stream),
-                     "copy")))
-      return rc;
-    rd_rhs_kernel<<<nch0, kChunk, 0, M.stream>>>(A, M.d_ch0.as<Chunk>());
+    if (scheme == RD_IMEX) {
+      // keep w_n and the previous solution (inputs of the learned guess and of training crops)
+      if ((rc = M.cuda(cudaMemcpyAsync(wn, h->d_u.p, cb, cudaMemcpyDeviceToDevice, M.stream), "copy")) ||
+          (rc = M.cuda(cudaMemcpyAsync(wn + h->cells, h->d_v.p, cb, cudaMemcpyDeviceToDevice, M.stream), "copy")) ||
+          (rc = M.cuda(cudaMemcpyAsync(pin, h->have_prev ? prev : wn, 2 * cb, cudaMemcpyDeviceToDevice, M.stream),
+                       "copy")))
+        return rc;
+      rd_rhs_kernel<RD_IMEX><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
+    } else {
+      rd_rhs_kernel<RD_SPLIT><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
+    }
     ++M.launches;
     if (h->guess) {
       if ((rc = M.cuda(cudaStreamSynchronize(M.stream), "sync"))) return rc;
@@ -1257,14 +1425,19 @@ int rd_step(rd_handle* h, int nsteps, int* cycles) {
     }
     rc = M.solve_device_any();
     if (rc) return rc;
-    if ((rc = M.cuda(cudaMemcpyAsync(prev, M.d_X.p, 2 * cb, cudaMemcpyDeviceToDevice, M.stream), "copy"))) return rc;
-    h->have_prev = true;
+    if (scheme == RD_IMEX) {
+      if ((rc = M.cuda(cudaMemcpyAsync(prev, M.d_X.p, 2 * cb, cudaMemcpyDeviceToDevice, M.stream), "copy"))) return rc;
+      h->have_prev = true;
+    }
     bool ok;
     std::vector<int> cyc(2 * ni);
     if ((rc = M.results(cyc.data(), nullptr, &ok))) return rc;
     if (cycles) std::memcpy(cycles + (size_t)s * 2 * ni, cyc.data(), cyc.size() * sizeof(int));
     if (!ok) return M.fail(MG_ERR_NOT_CONVERGED, "an instance did not reach rtol within max_cycles");
-    rd_finish_kernel<<<nch0, kChunk, 0, M.stream>>>(A, M.d_ch0.as<Chunk>());
+    if (scheme == RD_IMEX)
+      rd_finish_kernel<RD_IMEX><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
+    else
+      rd_finish_kernel<RD_SPLIT><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
     ++M.launches;
     if ((rc = M.cuda(cudaGetLastError(), "rd launch"))) return rc;
   }
@@ -1288,6 +1461,7 @@ int rd_last_residuals(rd_handle* h, double* initial, double* final_) {
 
 int rd_set_guess(rd_handle* h, cnn_handle* net, double scale) {
   if (!h || (net && !(scale > 0))) return AMR_ERR_INVALID_ARG;
+  if (net && h->cfg.scheme != RD_IMEX) return h->mg.fail(AMR_ERR_INVALID_ARG, "the learned guess is for the IMEX scheme");
   if (net) {
     for (int n : h->sizes) {
       if (h->cfg.ndim == 2 && n % 16 != 0) return h->mg.fail(AMR_ERR_INVALID_ARG, "learned guess needs sides multiple of 16");
@@ -1306,7 +1480,7 @@ int rd_set_guess(rd_handle* h, cnn_handle* net, double scale) {
 int rd_extract_crops(rd_handle* h, int ncrops, const int* inst, const int* corner, int crop, double scale, float* in,
                      float* target) {
   if (!h || ncrops < 1 || !inst || !corner || crop < 1 || !(scale > 0) || !in || !target) return AMR_ERR_INVALID_ARG;
-  if (!h->have_prev) return h->mg.fail(AMR_ERR_INVALID_ARG, "no step taken yet");
+  if (!h->have_prev) return h->mg.fail(AMR_ERR_INVALID_ARG, "no IMEX step taken yet");
   Mg& M = h->mg;
   for (int k = 0; k < ncrops; ++k)
     if (inst[k] < 0 || inst[k] >= h->cfg.n_inst || crop > h->sizes[inst[k]]) return AMR_ERR_INVALID_ARG;
