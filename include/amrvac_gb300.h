@@ -279,7 +279,10 @@ int rd_set_state(rd_handle* h, const double* u, const double* v, int on_device);
 int rd_read_state(rd_handle* h, double* u, double* v, int on_device);
 /* nsteps steps of the configured scheme; cycles (host, may be NULL) receives
  * [step][2*n_inst] V-cycles (species-major: u of every instance, then v; 0 for
- * RD_EXPLICIT).  Synchronous. */
+ * RD_EXPLICIT).  Synchronous.  Without a learned guess each implicit step is one
+ * graph launch whose multigrid convergence loop runs on the device (a graph
+ * conditional node), and the host waits once per 256 steps; MG_ERR_NOT_CONVERGED
+ * is then reported after those steps (the state has advanced through them). */
 int rd_step(rd_handle* h, int nsteps, int* cycles);
 
 /* ------------------------------------------------------------------------

@@ -71,6 +71,7 @@ struct MgState {
   int* cycles;
   int* failed;
   int* any;                   // any instance active (for the host)
+  int* iters;                 // loop iterations of the current solve (device-side loop cap)
   const double* inv;          // dense inverses of the coarsest operators
   int ndim;
   int neu;                    // Neumann (zero-flux) boundaries, else periodic
@@ -225,6 +226,7 @@ __global__ void bnorm_kernel(MgState S, const Chunk* ch) {
 
 __global__ void bnorm_finish_kernel(MgState S, int ninst) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *S.iters = 0;
   if (i >= ninst) return;
   S.bnorm[i] = __longlong_as_double((long long)S.rnorm[i]);
   S.rnorm[i] = 0ull;
@@ -263,7 +265,10 @@ __global__ void residual64_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
 }
 
 // convergence test per instance (the paper's max-residual rule)
-__global__ void check_kernel(MgState S, int ninst) {
+// cond != 0: the kernel runs inside a graph's device-side while loop and sets the loop
+// condition (some instance still iterating); the loop also stops after max_cycles + 1 checks
+// whatever the flags say, so it always ends.
+__global__ void check_kernel(MgState S, int ninst, cudaGraphConditionalHandle hc, int cond) {
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
@@ -284,7 +289,13 @@ __global__ void check_kernel(MgState S, int ninst) {
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) *S.any = any;
+  if (threadIdx.x == 0) {
+    *S.any = any;
+    if (cond) {
+      const int it = ++*S.iters;
+      cudaGraphSetConditional(hc, (any && it <= S.max_cycles + 1) ? 1u : 0u);
+    }
+  }
 }
 
 // red-black Gauss-Seidel sweep of one colour: x = (b + nbsum * ih2) / (lambda + count ih2)
@@ -572,6 +583,16 @@ __global__ void correct64_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
     S.X[I.off0 + t] = S.X[I.off0 + t] + widen(e);
   else
     S.X[I.off0 + t] = S.X[I.off0 + t] + e;
+}
+
+// per-step log of a device-side solve: entry [step % cap][instance] = V-cycles, or
+// -1 - cycles where the instance did not converge; then the step counter advances
+__global__ void log_kernel(MgState S, int ninst, int* log, int* step, int cap) {
+  const int row = *step % cap;
+  for (int i = threadIdx.x; i < ninst; i += blockDim.x)
+    log[(size_t)row * ninst + i] = S.failed[i] ? -1 - S.cycles[i] : S.cycles[i];
+  __syncthreads();
+  if (threadIdx.x == 0) *step = *step + 1;
 }
 
 // ------------------------------------------------------ reaction-diffusion --
@@ -869,6 +890,10 @@ struct Mg {
   std::vector<int> coarse_inst, coarse_row0;
   DevBuf d_yl;  // 2D: second iterate array for the tiled sweeps
   DevBuf d_inst, d_X, d_B, d_xl, d_bl, d_rnorm, d_bnorm, d_lastres, d_initres, d_active, d_cycles, d_failed, d_any, d_inv;
+  DevBuf d_iters;
+  cudaStream_t cstream = nullptr;   // captures the body of the device-side solve loop
+  cudaGraphExec_t sgraph = nullptr; // one whole solve (device-side convergence loop)
+  long long solve_loop_kernels = 0; // kernels per iteration of that loop
   DevBuf d_ch0, d_chall, d_cinst, d_crow0;
   std::vector<size_t> off_half, off_coarse, off_fine, off_tile;
   int* h_any = nullptr;
@@ -878,6 +903,8 @@ struct Mg {
 
   ~Mg() {
     if (vgraph) cudaGraphExecDestroy(vgraph);
+    if (sgraph) cudaGraphExecDestroy(sgraph);
+    if (cstream) cudaStreamDestroy(cstream);
     if (h_any) cudaFreeHost(h_any);
     if (own_stream) cudaStreamDestroy(stream);
   }
@@ -904,6 +931,7 @@ struct Mg {
     S.cycles = d_cycles.as<int>();
     S.failed = d_failed.as<int>();
     S.any = d_any.as<int>();
+    S.iters = d_iters.as<int>();
     S.inv = d_inv.as<double>();
     S.ndim = nd;
     S.neu = neu ? 1 : 0;
@@ -1027,7 +1055,8 @@ struct Mg {
         (rc = cuda(d_lastres.alloc(n_inst * 8), "alloc")) || (rc = cuda(d_initres.alloc(n_inst * 8), "alloc")) ||
         (rc = cuda(d_active.alloc(n_inst * 4), "alloc")) ||
         (rc = cuda(d_cycles.alloc(n_inst * 4), "alloc")) || (rc = cuda(d_failed.alloc(n_inst * 4), "alloc")) ||
-        (rc = cuda(d_any.alloc(4), "alloc")) || (rc = cuda(d_inv.alloc(invoff * 8), "alloc inverse")))
+        (rc = cuda(d_any.alloc(4), "alloc")) || (rc = cuda(d_iters.alloc(4), "alloc")) ||
+        (rc = cuda(d_inv.alloc(invoff * 8), "alloc inverse")))
       return rc;
     if ((rc = cuda(cudaMallocHost(&h_any, 4), "host alloc"))) return rc;
     cudaMemcpy(d_inst.p, insts.data(), insts.size() * sizeof(InstDev), cudaMemcpyHostToDevice);
@@ -1141,7 +1170,96 @@ struct Mg {
     return rc;
   }
 
+  // Enqueue one whole solve on `stream` while it is being captured into a graph: the norms,
+  // the first residual and check, then a conditional while node whose body (captured on
+  // cstream) is one V-cycle, the residual and the check.  The check kernel sets the loop
+  // condition, so the convergence loop runs on the device with no host round trip.
+  template <typename real>
+  int capture_solve() {
+    MgState S = state();
+    Lvl<real> Lv = lvl<real>();
+    if (!cstream) {
+      if (int rc = cuda(cudaStreamCreateWithFlags(&cstream, cudaStreamNonBlocking), "stream")) return rc;
+    }
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    if (int rc = cuda(cudaStreamGetCaptureInfo(stream, &st, nullptr, &g), "capture info")) return rc;
+    if (st != cudaStreamCaptureStatusActive || !g) return fail(AMR_ERR_CUDA, "solve capture outside a capture");
+    cudaGraphConditionalHandle hc;
+    if (int rc = cuda(cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault), "conditional handle"))
+      return rc;
+    bnorm_kernel<<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, d_ch0.as<Chunk>());
+    bnorm_finish_kernel<<<(ninst + 255) / 256, 256, 0, stream>>>(S, ninst);
+    residual64_kernel<real><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+    check_kernel<<<1, 256, 0, stream>>>(S, ninst, hc, 1);
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    if (int rc = cuda(cudaStreamGetCaptureInfo(stream, &st, nullptr, &g, &deps, nullptr, &ndeps), "capture info"))
+      return rc;
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (int rc = cuda(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp), "conditional node")) return rc;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (int rc = cuda(cudaStreamUpdateCaptureDependencies(stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies),
+                      "capture dependencies"))
+      return rc;
+    if (int rc = cuda(cudaStreamBeginCaptureToGraph(cstream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+                      "body capture"))
+      return rc;
+    cudaStream_t outer = stream;
+    stream = cstream;
+    long long before = launches;
+    int rc = enqueue_vcycle<real>();
+    residual64_kernel<real><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+    check_kernel<<<1, 256, 0, stream>>>(S, ninst, hc, 1);
+    solve_loop_kernels = launches - before + 2;
+    launches = before;
+    stream = outer;
+    cudaGraph_t got = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(cstream, &got);
+    if (rc) return rc;
+    return cuda(ec, "end body capture");
+  }
+
+  template <typename real>
+  int build_solve_graph() {
+    if (sgraph) return AMR_OK;
+    cudaGraph_t g;
+    if (int rc = cuda(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "capture")) return rc;
+    int rc = capture_solve<real>();
+    cudaError_t ec = cudaStreamEndCapture(stream, &g);
+    if (rc) {
+      if (ec == cudaSuccess) cudaGraphDestroy(g);
+      return rc;
+    }
+    if ((rc = cuda(ec, "end capture"))) return rc;
+    rc = cuda(cudaGraphInstantiate(&sgraph, g, 0), "instantiate");
+    cudaGraphDestroy(g);
+    return rc;
+  }
+
+  // kernels one device-side solve ran: prelude 4, then per loop iteration (max cycles of an
+  // instance) a V-cycle, a residual and a check
+  long long solve_kernels(int maxcyc) const { return 4 + (long long)maxcyc * solve_loop_kernels; }
+
+  // X (device, float64) holds the guess; B (device) the right-hand side; both at d_X / d_B.
+  // One launch of the solve graph; the host does not wait.
+  template <typename real>
+  int solve_graph_launch() {
+    if (int rc = build_solve_graph<real>()) return rc;
+    return cuda(cudaGraphLaunch(sgraph, stream), "solve graph launch");
+  }
+  int solve_graph_launch_any() {
+    return precision == AMR_FP64 ? solve_graph_launch<double>() : solve_graph_launch<float>();
+  }
+  int capture_solve_any() { return precision == AMR_FP64 ? capture_solve<double>() : capture_solve<float>(); }
+
   // X (device, float64) holds the guess; B (device) the right-hand side; both at d_X / d_B
+  // (host-polled loop: used with the learned guess, whose step syncs anyway)
   template <typename real>
   int solve_device() {
     MgState S = state();
@@ -1153,7 +1271,7 @@ struct Mg {
     launches += 2;
     while (true) {
       residual64_kernel<real><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
-      check_kernel<<<1, 256, 0, stream>>>(S, ninst);
+      check_kernel<<<1, 256, 0, stream>>>(S, ninst, 0, 0);
       launches += 2;
       if ((rc = cuda(cudaMemcpyAsync(h_any, d_any.p, 4, cudaMemcpyDeviceToHost, stream), "copy"))) return rc;
       if ((rc = cuda(cudaStreamSynchronize(stream), "sync"))) return rc;
@@ -1197,11 +1315,17 @@ inline double rd_lambda(const rd_config& c, int s) {
   return (c.scheme == RD_SPLIT ? 1.0 : 2.0) / (c.dt * (s == 0 ? c.Du : c.Dv));
 }
 
+constexpr int kExplicitGraphSteps = 32;  // explicit steps per captured graph
+constexpr int kLogSteps = 256;           // implicit steps per host wait (rows of the cycle log)
+
 struct rd_handle {
   Mg mg;
   cudaGraphExec_t egraph = nullptr;  // kExplicitGraphSteps explicit steps
+  cudaGraphExec_t stgraph = nullptr; // one implicit step with its device-side solve
+  DevBuf d_log, d_stepctr;           // per-step cycle log ([kLogSteps][2 n_inst]) and its counter
   ~rd_handle() {
     if (egraph) cudaGraphExecDestroy(egraph);
+    if (stgraph) cudaGraphExecDestroy(stgraph);
   }
   rd_config cfg{};
   std::vector<int> sizes;
@@ -1249,13 +1373,16 @@ int mg_solve(mg_handle* h, const double* b, double* x, int on_device, int* cycle
   cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (int rc = M.cuda(cudaMemcpyAsync(M.d_B.p, b, M.n0 * 8, k, M.stream), "copy b")) return rc;
   if (int rc = M.cuda(cudaMemcpyAsync(M.d_X.p, x, M.n0 * 8, k, M.stream), "copy x")) return rc;
-  int rc = M.solve_device_any();
+  int rc = M.solve_graph_launch_any();
   if (rc) return rc;
   cudaMemcpyKind kb = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if ((rc = M.cuda(cudaMemcpyAsync(x, M.d_X.p, M.n0 * 8, kb, M.stream), "copy x back"))) return rc;
   if ((rc = M.cuda(cudaStreamSynchronize(M.stream), "sync"))) return rc;
   bool ok;
-  if ((rc = M.results(cycles, relres, &ok))) return rc;
+  std::vector<int> cyc(M.ninst);
+  if ((rc = M.results(cyc.data(), relres, &ok))) return rc;
+  if (cycles) std::memcpy(cycles, cyc.data(), cyc.size() * sizeof(int));
+  M.launches += M.solve_kernels(*std::max_element(cyc.begin(), cyc.end()));
   if (!ok) return M.fail(MG_ERR_NOT_CONVERGED, "an instance did not reach rtol within max_cycles");
   return AMR_OK;
 }
@@ -1292,7 +1419,9 @@ int rd_create(const rd_config* cfg, rd_handle** out) {
       (rc = h->mg.cuda(h->d_Fn.alloc(2 * h->cells * 8), "alloc Fn")) ||
       (rc = h->mg.cuda(h->d_wn.alloc(2 * h->cells * 8), "alloc")) ||
       (rc = h->mg.cuda(h->d_prev.alloc(2 * h->cells * 8), "alloc")) ||
-      (rc = h->mg.cuda(h->d_pin.alloc(2 * h->cells * 8), "alloc")))
+      (rc = h->mg.cuda(h->d_pin.alloc(2 * h->cells * 8), "alloc")) ||
+      (rc = h->mg.cuda(h->d_log.alloc((size_t)kLogSteps * 2 * cfg->n_inst * sizeof(int)), "alloc")) ||
+      (rc = h->mg.cuda(h->d_stepctr.alloc(sizeof(int)), "alloc")))
     return rc;
   *out = h.release();
   return AMR_OK;
@@ -1312,6 +1441,12 @@ int rd_set_state(rd_handle* h, const double* u, const double* v, int on_device) 
   Mg& M = h->mg;
   if (int rc = M.cuda(cudaMemcpyAsync(h->d_u.p, u, h->cells * 8, k, M.stream), "copy u")) return rc;
   if (int rc = M.cuda(cudaMemcpyAsync(h->d_v.p, v, h->cells * 8, k, M.stream), "copy v")) return rc;
+  // the first step's "previous solution" is the state itself
+  if (int rc = M.cuda(cudaMemcpyAsync(h->d_prev.p, h->d_u.p, h->cells * 8, cudaMemcpyDeviceToDevice, M.stream), "copy"))
+    return rc;
+  if (int rc = M.cuda(cudaMemcpyAsync(h->d_prev.as<double>() + h->cells, h->d_v.p, h->cells * 8,
+                                      cudaMemcpyDeviceToDevice, M.stream), "copy"))
+    return rc;
   h->have_prev = false;
   return M.cuda(cudaStreamSynchronize(M.stream), "sync");
 }
@@ -1324,8 +1459,6 @@ int rd_read_state(rd_handle* h, double* u, double* v, int on_device) {
   if (int rc = M.cuda(cudaMemcpyAsync(v, h->d_v.p, h->cells * 8, k, M.stream), "copy v")) return rc;
   return M.cuda(cudaStreamSynchronize(M.stream), "sync");
 }
-
-constexpr int kExplicitGraphSteps = 32;
 
 int rd_step(rd_handle* h, int nsteps, int* cycles) {
   if (!h || nsteps < 0) return AMR_ERR_INVALID_ARG;
@@ -1392,6 +1525,69 @@ int rd_step(rd_handle* h, int nsteps, int* cycles) {
   double* wn = h->d_wn.as<double>();
   double* prev = h->d_prev.as<double>();
   double* pin = h->d_pin.as<double>();
+  if (!h->guess) {
+    // Each step is one graph launch: (IMEX: keep w_n and the previous solution) right-hand
+    // side, the solve with its device-side convergence loop, (IMEX: keep the solution)
+    // finish, and a row of the cycle log.  The host waits once per kLogSteps steps.
+    if (!h->stgraph) {
+      cudaGraph_t g;
+      if ((rc = M.cuda(cudaStreamBeginCapture(M.stream, cudaStreamCaptureModeThreadLocal), "capture"))) return rc;
+      int crc = AMR_OK;
+      if (scheme == RD_IMEX) {
+        cudaMemcpyAsync(wn, h->d_u.p, cb, cudaMemcpyDeviceToDevice, M.stream);
+        cudaMemcpyAsync(wn + h->cells, h->d_v.p, cb, cudaMemcpyDeviceToDevice, M.stream);
+        cudaMemcpyAsync(pin, prev, 2 * cb, cudaMemcpyDeviceToDevice, M.stream);
+        rd_rhs_kernel<RD_IMEX><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
+      } else {
+        rd_rhs_kernel<RD_SPLIT><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
+      }
+      crc = M.capture_solve_any();
+      if (scheme == RD_IMEX) {
+        cudaMemcpyAsync(prev, M.d_X.p, 2 * cb, cudaMemcpyDeviceToDevice, M.stream);
+        rd_finish_kernel<RD_IMEX><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
+      } else {
+        rd_finish_kernel<RD_SPLIT><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
+      }
+      log_kernel<<<1, 256, 0, M.stream>>>(M.state(), M.ninst, h->d_log.as<int>(), h->d_stepctr.as<int>(), kLogSteps);
+      cudaError_t ec = cudaStreamEndCapture(M.stream, &g);
+      if (crc) {
+        if (ec == cudaSuccess) cudaGraphDestroy(g);
+        return crc;
+      }
+      if ((rc = M.cuda(ec, "end capture"))) return rc;
+      rc = M.cuda(cudaGraphInstantiate(&h->stgraph, g, 0), "instantiate");
+      cudaGraphDestroy(g);
+      if (rc) return rc;
+    }
+    std::vector<int> log((size_t)kLogSteps * 2 * ni);
+    bool failed = false;
+    for (int s0 = 0; s0 < nsteps; s0 += kLogSteps) {
+      const int k = std::min(kLogSteps, nsteps - s0);
+      if ((rc = M.cuda(cudaMemsetAsync(h->d_stepctr.p, 0, sizeof(int), M.stream), "memset"))) return rc;
+      for (int s = 0; s < k; ++s)
+        if ((rc = M.cuda(cudaGraphLaunch(h->stgraph, M.stream), "step graph launch"))) return rc;
+      if ((rc = M.cuda(cudaMemcpyAsync(log.data(), h->d_log.p, (size_t)k * 2 * ni * sizeof(int),
+                                       cudaMemcpyDeviceToHost, M.stream), "copy log")))
+        return rc;
+      if ((rc = M.cuda(cudaStreamSynchronize(M.stream), "sync"))) return rc;
+      for (int s = 0; s < k; ++s) {
+        int maxc = 0;
+        for (int i = 0; i < 2 * ni; ++i) {
+          int e = log[(size_t)s * 2 * ni + i];
+          if (e < 0) {
+            failed = true;
+            e = -1 - e;
+          }
+          maxc = std::max(maxc, e);
+          if (cycles) cycles[(size_t)(s0 + s) * 2 * ni + i] = e;
+        }
+        M.launches += 3 + M.solve_kernels(maxc);
+      }
+    }
+    if (scheme == RD_IMEX && nsteps > 0) h->have_prev = true;
+    if (failed) return M.fail(MG_ERR_NOT_CONVERGED, "an instance did not reach rtol within max_cycles");
+    return M.cuda(cudaGetLastError(), "rd step");
+  }
   for (int s = 0; s < nsteps; ++s) {
     if (scheme == RD_IMEX) {
       // keep w_n and the previous solution (inputs of the learned guess and of training crops)
