@@ -54,6 +54,14 @@ class OrcRdConfig(C.Structure):
     ]
 
 
+class OrcAmgConfig(C.Structure):
+    _fields_ = [
+        ("nbx", C.c_int), ("nby", C.c_int), ("B", C.c_int), ("L", C.c_double), ("lam", C.c_double),
+        ("nu1", C.c_int), ("nu2", C.c_int), ("max_cycles", C.c_int), ("rtol", C.c_double),
+        ("base_rtol", C.c_double), ("coarse_max", C.c_int),
+    ]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -90,6 +98,9 @@ def lib():
         L.orc_rd_reaction.argtypes = [C.c_double, C.c_double, C.c_int, _dp, _dp, _dp, _dp]
         L.orc_rd_reaction_schnakenberg.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, _dp, _dp, _dp, _dp]
         L.orc_laplacian.argtypes = [C.c_int, C.c_int, C.c_double, C.c_int, _dp, _dp]
+        for f in ("orc_amg_apply", "orc_amg_face_ghosts"):
+            getattr(L, f).argtypes = [C.POINTER(OrcAmgConfig), C.c_int, _ip, _ip, _dp, _dp]
+        L.orc_amg_solve.argtypes = [C.POINTER(OrcAmgConfig), C.c_int, _ip, _ip, _dp, _dp, C.c_int, _dp]
         if hasattr(L, "orc_cnn_forward"):
             _bind_cnn(L)
         _lib = L
@@ -411,3 +422,48 @@ def cnn_layer_slices(ndim):
         out.append((slice(o, o + co * ci * T), slice(o + co * ci * T, o + co * ci * T + co), ci, co))
         o += co * ci * T + co
     return out
+
+
+# ------------------------------------------------------------------ AMR multigrid --
+def amg_config(nb, B, L, lam, nu1=2, nu2=2, max_cycles=50, rtol=1e-10, base_rtol=1e-12, coarse_max=8):
+    return OrcAmgConfig(nb, nb, B, L, lam, nu1, nu2, max_cycles, rtol, base_rtol, coarse_max)
+
+
+def _tree(level, coords):
+    level = np.ascontiguousarray(level, dtype=np.int32)
+    coords = np.ascontiguousarray(coords, dtype=np.int32).reshape(-1, 2)
+    return level, coords
+
+
+def amg_solve(level, coords, b, x0, nb, B, L, lam, fixed_cycles=0, **kw):
+    """Multigrid on a 2D block quadtree: leaves (level, (bx, by)); b, x0 [leaf][B*B].
+    Returns (x, cycles, relres); cycles -1 if rtol was not reached."""
+    level, coords = _tree(level, coords)
+    b = _f64(b)
+    x = _f64(x0).copy()
+    c = amg_config(nb, B, L, lam, **kw)
+    rr = C.c_double()
+    cyc = lib().orc_amg_solve(C.byref(c), len(level), _i(level), _i(coords), _d(b), _d(x), fixed_cycles,
+                              C.byref(rr))
+    if cyc == -2:
+        raise ValueError("invalid tree")
+    return x, cyc, rr.value
+
+
+def amg_apply(level, coords, x, nb, B, L, lam):
+    level, coords = _tree(level, coords)
+    x = _f64(x)
+    out = np.zeros_like(x)
+    if lib().orc_amg_apply(C.byref(amg_config(nb, B, L, lam)), len(level), _i(level), _i(coords), _d(x), _d(out)):
+        raise ValueError("invalid tree")
+    return out
+
+
+def amg_face_ghosts(level, coords, x, nb, B, L):
+    level, coords = _tree(level, coords)
+    x = _f64(x)
+    g = np.zeros((len(level), 4, B))
+    if lib().orc_amg_face_ghosts(C.byref(amg_config(nb, B, L, 1.0)), len(level), _i(level), _i(coords), _d(x),
+                                 _d(g)):
+        raise ValueError("invalid tree")
+    return g

@@ -13,7 +13,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["euler.cpp", "exact_riemann.cpp", "mg.cpp", "cnn.cpp"]
+SOURCES = ["euler.cpp", "exact_riemann.cpp", "mg.cpp", "amg.cpp", "cnn.cpp"]
 OUT = os.path.join(HERE, "_build", "liborc.so")
 
 

@@ -114,6 +114,29 @@ void orc_mg_vcycle(const orc_mg_config* c, const double* r, double* e);
 /* dense Gaussian elimination solve of the same system (tiny n only) */
 int orc_dense_solve(int ndim, int n, double L, double lambda, int bc, const double* b, double* x);
 
+/* ---- multigrid on a 2D block quadtree (Sec. 1.4, Sec. 2.5.2), periodic, square base of
+ * nbx x nby blocks of B^2 cells, level-1 cell size L / (nbx B).  Leaves: level[k] >= 1 and
+ * block coordinates coords[2k], coords[2k+1] at that level; the tree must tile the domain and
+ * be 2:1 balanced across faces and corners.  Leaf data [leaf][B*B], x fastest. ---- */
+typedef struct {
+  int nbx, nby, B;
+  double L, lambda;
+  int nu1, nu2, max_cycles;
+  double rtol;        /* max|b - A x| over leaf cells <= rtol max|b| */
+  double base_rtol;   /* level-1 solve by the uniform multigrid */
+  int coarse_max;
+} orc_amg_config;
+/* x: guess in, solution out.  fixed_cycles > 0 runs exactly that many V-cycles.  Returns
+ * the V-cycles used, -1 if rtol was not reached, -2 for an invalid tree. */
+int orc_amg_solve(const orc_amg_config* c, int nleaves, const int* level, const int* coords, const double* b,
+                  double* x, int fixed_cycles, double* relres);
+/* the composite operator on the leaves, and the face ghost values it uses ([leaf][4][B]:
+ * faces x-, x+, y-, y+, along the face in increasing order) */
+int orc_amg_apply(const orc_amg_config* c, int nleaves, const int* level, const int* coords, const double* x,
+                  double* Ax);
+int orc_amg_face_ghosts(const orc_amg_config* c, int nleaves, const int* level, const int* coords, const double* x,
+                        double* ghosts);
+
 /* ---- reaction-diffusion step (Sec. 2.5): w = (u, v), dw/dt = F0(w) + F1(w), F0 the
  * reaction terms of Eq. (gray-scott) or Eq. (schnakenberg), F1 = D lap_h w ---- */
 enum { ORC_RD_GRAY_SCOTT = 0, ORC_RD_SCHNAKENBERG = 1 };
