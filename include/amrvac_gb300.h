@@ -239,6 +239,8 @@ const char* mg_last_error(const mg_handle* h);
  * did not reach rtol (x then holds the last iterate). */
 int mg_solve(mg_handle* h, const double* b, double* x, int on_device, int* cycles, double* relres);
 int mg_num_unknowns(const mg_handle* h, long long* n);
+/* kernels this handle has launched so far (graph nodes included) */
+int mg_kernel_launches(const mg_handle* h, long long* n);
 
 /* ------------------------------------------------------------------------
  * Reaction-diffusion steps (Sec. 2.5): w = (u, v), dw/dt = F0(w) + F1(w), with
@@ -284,6 +286,50 @@ int rd_read_state(rd_handle* h, double* u, double* v, int on_device);
  * conditional node), and the host waits once per 256 steps; MG_ERR_NOT_CONVERGED
  * is then reported after those steps (the state has advanced through them). */
 int rd_step(rd_handle* h, int nsteps, int* cycles);
+int rd_kernel_launches(const rd_handle* h, long long* n);
+
+/* ------------------------------------------------------------------------
+ * Multigrid on a 2D block quadtree (Sec. 1.4: AMR-compatible multigrid; Sec.
+ * 2.5.2 runs it on a three-level mesh), float64: solves (lambda - lap_h) x = b
+ * on the leaf cells of a periodic, 2:1-balanced (faces and corners) quadtree
+ * over a square base of nbx x nby (nbx == nby) blocks of B^2 cells (B = 8 or
+ * 16), level-1 cell size L / (nbx B), level-l cell size halved per level.
+ * Composite operator: the 5-point stencil of each leaf cell's level; a coarser
+ * neighbour contributes (2/3) C^ + (1/3) f0 (C^: the coarse value moved along
+ * the face by a linear slope), a refined neighbour (4/3) m - (1/3) f0 (m: mean of
+ * the two finer cells on the face; flux matching, conservative).  Full
+ * approximation scheme over the tree levels with red-black Gauss-Seidel (nu1,
+ * nu2), the base level solved by the uniform multigrid above to base_rtol.
+ * Leaves: level[k] >= 1 and block coordinates (coords[2k], coords[2k+1]) at
+ * that level, any order; leaf data [leaf][B*B] in that order, x fastest.
+ * ------------------------------------------------------------------------ */
+typedef struct mgt_handle mgt_handle;
+
+typedef struct {
+  int nbx, nby, B;
+  double L, lambda;     /* lambda >= 0 */
+  int nu1, nu2, max_cycles;
+  double rtol;          /* stop when max|b - A x| over leaf cells <= rtol max|b| */
+  double base_rtol;     /* base-level solves */
+  int coarse_max;       /* the base multigrid's coarsest side */
+  void* stream;         /* NULL: the handle creates its own */
+} mgt_config;
+
+/* Copies the tree; AMR_ERR_INVALID_ARG if the leaves leave a gap, overlap, or break
+ * the 2:1 balance. */
+int mgt_create(const mgt_config* cfg, int nleaves, const int* level, const int* coords, mgt_handle** out);
+int mgt_destroy(mgt_handle* h);
+const char* mgt_last_error(const mgt_handle* h);
+int mgt_num_leaves(const mgt_handle* h, long long* n);
+/* x: guess in, solution out (host or device, as b).  fixed_cycles > 0 runs exactly
+ * that many V-cycles; 0 iterates to rtol (MG_ERR_NOT_CONVERGED after max_cycles).
+ * cycles, relres (host, may be NULL): V-cycles run, final relative residual.
+ * Synchronous. */
+int mgt_solve(mgt_handle* h, const double* b, double* x, int on_device, int fixed_cycles, int* cycles,
+              double* relres);
+/* the composite operator: Ax = (lambda - lap_h) x on the leaf cells.  Synchronous. */
+int mgt_apply(mgt_handle* h, const double* x, double* Ax, int on_device);
+int mgt_kernel_launches(const mgt_handle* h, long long* n);
 
 /* ------------------------------------------------------------------------
  * Learned multigrid initial guess (no counterpart in the paper; the project's

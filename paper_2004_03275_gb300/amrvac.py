@@ -51,6 +51,14 @@ class MgConfig(C.Structure):
     ]
 
 
+class MgtConfig(C.Structure):
+    _fields_ = [
+        ("nbx", C.c_int), ("nby", C.c_int), ("B", C.c_int), ("L", C.c_double), ("lam", C.c_double),
+        ("nu1", C.c_int), ("nu2", C.c_int), ("max_cycles", C.c_int), ("rtol", C.c_double),
+        ("base_rtol", C.c_double), ("coarse_max", C.c_int), ("stream", C.c_void_p),
+    ]
+
+
 MG_BC = {"periodic": 0, "neumann": 1}
 RD_MODEL = {"gray-scott": 0, "schnakenberg": 1}
 RD_SCHEME = {"imex": 0, "split": 1, "explicit": 2}
@@ -116,6 +124,15 @@ _SIGS = {
     "rd_set_guess": ([_vp, _vp, C.c_double], C.c_int),
     "rd_last_residuals": ([_vp, _dp, _dp], C.c_int),
     "rd_extract_crops": ([_vp, C.c_int, _ip, _ip, C.c_int, C.c_double, _vp, _vp], C.c_int),
+    "mg_kernel_launches": ([_vp, _llp], C.c_int),
+    "rd_kernel_launches": ([_vp, _llp], C.c_int),
+    "mgt_create": ([C.POINTER(MgtConfig), C.c_int, _ip, _ip, C.POINTER(_vp)], C.c_int),
+    "mgt_destroy": ([_vp], C.c_int),
+    "mgt_last_error": ([_vp], C.c_char_p),
+    "mgt_num_leaves": ([_vp, _llp], C.c_int),
+    "mgt_solve": ([_vp, _vp, _vp, C.c_int, C.c_int, _ip, _dp], C.c_int),
+    "mgt_apply": ([_vp, _vp, _vp, C.c_int], C.c_int),
+    "mgt_kernel_launches": ([_vp, _llp], C.c_int),
 }
 
 
@@ -492,6 +509,66 @@ class RdSolver:
         cyc = np.zeros((nsteps, 2, len(self.n_cells)), dtype=np.int32)
         _check(self.lib.rd_step(self.h, nsteps, cyc.ctypes.data_as(_ip)), self.h, "rd_last_error")
         return cyc
+
+
+class TreeMgSolver:
+    """Owns one mgt_handle: multigrid on the leaves of a 2D block quadtree (float64).
+    level[k] >= 1, coords[k] = (bx, by) block coordinates at that level; leaf data
+    [leaf][B*B] in the same order."""
+
+    def __init__(self, level, coords, nb, B, L, lam, nu1=2, nu2=2, max_cycles=50, rtol=1e-10, base_rtol=1e-12,
+                 coarse_max=8, stream=None):
+        self.lib = load()
+        self.level = np.ascontiguousarray(level, dtype=np.int32)
+        self.coords = np.ascontiguousarray(coords, dtype=np.int32).reshape(-1, 2)
+        c = MgtConfig(nb, nb, B, L, lam, nu1, nu2, max_cycles, rtol, base_rtol, coarse_max, stream)
+        h = _vp()
+        rc = self.lib.mgt_create(C.byref(c), len(self.level), self.level.ctypes.data_as(_ip),
+                                 self.coords.ctypes.data_as(_ip), C.byref(h))
+        if rc != AMR_OK:
+            raise AmrError(rc, "mgt_create")
+        self.h = h
+        self.B = B
+        self.n = len(self.level) * B * B
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mgt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, b, x, fixed_cycles=0):
+        """b, x: [leaf][B*B] float64 (numpy host or torch CUDA); x updated in place.
+        Returns (cycles, relative residual)."""
+        if not hasattr(b, "data_ptr"):
+            b = np.ascontiguousarray(b, dtype=np.float64)
+        pb, db = _ptr(b)
+        px, dx = _ptr(x)
+        if db != dx:
+            raise ValueError("b and x must both be host or both be device arrays")
+        cyc = C.c_int()
+        rr = C.c_double()
+        rc = self.lib.mgt_solve(self.h, pb, px, db, fixed_cycles, C.byref(cyc), C.byref(rr))
+        if rc != AMR_OK:
+            raise AmrError(rc, self.lib.mgt_last_error(self.h).decode())
+        return cyc.value, rr.value
+
+    def apply(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        out = np.zeros_like(x)
+        _check(self.lib.mgt_apply(self.h, x.ctypes.data_as(_vp), out.ctypes.data_as(_vp), 0), self.h,
+               "mgt_last_error")
+        return out
+
+    def kernel_launches(self):
+        n = C.c_longlong()
+        _check(self.lib.mgt_kernel_launches(self.h, C.byref(n)), self.h, "mgt_last_error")
+        return n.value
 
 
 class CnnNet:

@@ -1367,6 +1367,18 @@ int mg_num_unknowns(const mg_handle* h, long long* n) {
   return AMR_OK;
 }
 
+int mg_kernel_launches(const mg_handle* h, long long* n) {
+  if (!h || !n) return AMR_ERR_INVALID_ARG;
+  *n = h->mg.launches;
+  return AMR_OK;
+}
+
+int rd_kernel_launches(const rd_handle* h, long long* n) {
+  if (!h || !n) return AMR_ERR_INVALID_ARG;
+  *n = h->mg.launches;
+  return AMR_OK;
+}
+
 int mg_solve(mg_handle* h, const double* b, double* x, int on_device, int* cycles, double* relres) {
   if (!h || !b || !x) return AMR_ERR_INVALID_ARG;
   Mg& M = h->mg;

@@ -1,0 +1,694 @@
+// Multigrid for the Helmholtz problem (lambda - lap_h) x = b on the leaves of a 2D block
+// quadtree (Sec. 1.4: the multigrid is AMR-compatible; Sec. 2.5.2 runs it on a three-level
+// mesh), float64.
+//
+// Discretisation (the paper defers it to mg2019; these are the readings this file and the
+// test oracle share):
+//  * composite operator on leaf cells: 5-point stencil of the cell's level; a coarser
+//    neighbour contributes g = (2/3) C^ + (1/3) f0 with C^ = C + s (C_t+ - C_t-) / 8 (linear
+//    along the normal and along the face); a refined neighbour block contributes
+//    (4/3) m - (1/3) f0 with m the mean of the two finer cells touching the face (flux
+//    matching: the operator is conservative);
+//  * level operator: the same, except that a refined same-level block contributes its own
+//    level values (the means of its children);
+//  * full approximation scheme over the levels: red-black Gauss-Seidel of the level
+//    operator, the restriction of x and of the residual (means of 2x2 children), the
+//    composite residual for leaves of the coarser level, b = r + A x there, cell-centred
+//    bilinear prolongation (9/16, 3/16, 3/16, 1/16) of the coarse change, and the base grid
+//    (level 1, uniform) solved by the batched uniform multigrid of mg.cu through its C ABI.
+//
+// Layout: every block of every level (leaves and refined blocks) owns B*B values of x, b,
+// r, x_before and (leaves) the composite right-hand side, x fastest; a dense table per
+// level maps block coordinates to block indices (-1 where the level has no block), so a
+// stencil finds any neighbour cell by its global level indices.  One CTA of B*B threads per
+// block; the operations are level-by-level kernels in the order of the V-cycle.  This unit
+// is compiled without multiply-add contraction, so its arithmetic is the written one.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/amrvac_gb300.h"
+
+namespace mgtree {
+
+constexpr int kMaxLev = 12;
+
+struct TreeDev {
+  int B, lmax;
+  double lam;
+  const int* table[kMaxLev + 1];  // level l: [ny(l)][nx(l)] block index or -1
+  int nx[kMaxLev + 1], ny[kMaxLev + 1];
+  double ih2[kMaxLev + 1];
+  const int* leaf;  // [block] 1 for a leaf
+  double* x;
+  double* b;
+  double* r;
+  double* xold;
+  double* bo;       // composite right-hand side (leaves)
+};
+
+__device__ __forceinline__ int wrapc(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// block index of global level-l cell (I, J) (periodic) and the cell's offset in the block
+__device__ __forceinline__ int blk_at(const TreeDev& T, int l, int I, int J, int* off) {
+  if (l < 1 || l > T.lmax) return -1;
+  const int B = T.B;
+  I = wrapc(I, T.nx[l] * B);
+  J = wrapc(J, T.ny[l] * B);
+  *off = (J % B) * B + (I % B);
+  return T.table[l][(J / B) * T.nx[l] + I / B];
+}
+
+__device__ __forceinline__ bool cell(const TreeDev& T, const double* F, int l, int I, int J, double* v) {
+  int off;
+  const int k = blk_at(T, l, I, J, &off);
+  if (k < 0) return false;
+  *v = F[(size_t)k * T.B * T.B + off];
+  return true;
+}
+
+// the value the stencil of a level-l cell (value f0) reads for its neighbour cell (I, J)
+// across the face normal to d (side +1: the neighbour is in the + direction); leafcell:
+// the composite operator at a leaf cell
+__device__ double nbr(const TreeDev& T, const double* F, int l, int I, int J, int d, int side, double f0,
+                      bool leafcell) {
+  const int B = T.B;
+  I = wrapc(I, T.nx[l] * B);
+  J = wrapc(J, T.ny[l] * B);
+  const int k = T.table[l][(J / B) * T.nx[l] + I / B];
+  if (k >= 0) {
+    const double v = F[(size_t)k * B * B + (J % B) * B + (I % B)];
+    if (T.leaf[k] || !leafcell) return v;
+    const int n = side > 0 ? 0 : 1;  // the children's layer nearest the face
+    double a, c;
+    bool ok;
+    if (d == 0)
+      ok = cell(T, F, l + 1, 2 * I + n, 2 * J, &a) && cell(T, F, l + 1, 2 * I + n, 2 * J + 1, &c);
+    else
+      ok = cell(T, F, l + 1, 2 * I, 2 * J + n, &a) && cell(T, F, l + 1, 2 * I + 1, 2 * J + n, &c);
+    if (!ok) return nan("");
+    const double m = 0.5 * (a + c);
+    return (4.0 / 3.0) * m - (1.0 / 3.0) * f0;
+  }
+  const int Ic = I >> 1, Jc = J >> 1;
+  double C, Cp, Cm;
+  bool ok = cell(T, F, l - 1, Ic, Jc, &C);
+  if (d == 0)
+    ok = ok && cell(T, F, l - 1, Ic, Jc + 1, &Cp) && cell(T, F, l - 1, Ic, Jc - 1, &Cm);
+  else
+    ok = ok && cell(T, F, l - 1, Ic + 1, Jc, &Cp) && cell(T, F, l - 1, Ic - 1, Jc, &Cm);
+  if (!ok) return nan("");
+  const int t = d == 0 ? J : I;
+  const double s = (t & 1) ? 1.0 : -1.0;
+  const double Chat = C + (s * (Cp - Cm)) * 0.125;
+  return (2.0 / 3.0) * Chat + (1.0 / 3.0) * f0;
+}
+
+struct Cell {
+  int k, l, i, j, I, J;
+};
+
+__device__ __forceinline__ Cell cell_of_thread(const TreeDev& T, const int* list, int l, const int* bxy) {
+  Cell c;
+  c.k = list[blockIdx.x];
+  c.l = l;
+  c.i = threadIdx.x % T.B;
+  c.j = threadIdx.x / T.B;
+  c.I = bxy[2 * c.k] * T.B + c.i;
+  c.J = bxy[2 * c.k + 1] * T.B + c.j;
+  return c;
+}
+
+__device__ __forceinline__ double nbr_sum(const TreeDev& T, const double* F, const Cell& c, double x0, bool comp) {
+  const bool lf = comp && T.leaf[c.k];
+  double s = nbr(T, F, c.l, c.I - 1, c.J, 0, -1, x0, lf);
+  s = s + nbr(T, F, c.l, c.I + 1, c.J, 0, +1, x0, lf);
+  s = s + nbr(T, F, c.l, c.I, c.J - 1, 1, -1, x0, lf);
+  s = s + nbr(T, F, c.l, c.I, c.J + 1, 1, +1, x0, lf);
+  return s;
+}
+
+__device__ __forceinline__ double apply_at(const TreeDev& T, const double* F, const Cell& c, bool comp) {
+  const double x0 = F[(size_t)c.k * T.B * T.B + c.j * T.B + c.i];
+  const double s = nbr_sum(T, F, c, x0, comp);
+  return T.lam * x0 - (s - 4.0 * x0) * T.ih2[c.l];
+}
+
+// ---------------------------------------------------------------- kernels --
+// red-black Gauss-Seidel, one colour, every block of the list (level l)
+__global__ void gs_kernel(TreeDev T, const int* list, const int* bxy, int l, int colour) {
+  const Cell c = cell_of_thread(T, list, l, bxy);
+  if (((c.I + c.J) & 1) != colour) return;
+  const size_t q = (size_t)c.k * T.B * T.B + c.j * T.B + c.i;
+  const double x0 = T.x[q];
+  const double s = nbr_sum(T, T.x, c, x0, false);
+  const double ih2 = T.ih2[l];
+  T.x[q] = (T.b[q] + s * ih2) / (T.lam + 4.0 * ih2);
+}
+
+// r = b - A x (level operator) on the list
+__global__ void level_residual_kernel(TreeDev T, const int* list, const int* bxy, int l) {
+  const Cell c = cell_of_thread(T, list, l, bxy);
+  const size_t q = (size_t)c.k * T.B * T.B + c.j * T.B + c.i;
+  T.r[q] = T.b[q] - apply_at(T, T.x, c, false);
+}
+
+// leaves of the list: r = bo - A x (composite operator); then every block: b = r + A x
+// (level operator).  Two kernels: the second reads x only, so the order within a kernel
+// does not matter.
+__global__ void composite_residual_kernel(TreeDev T, const int* list, const int* bxy, int l) {
+  const Cell c = cell_of_thread(T, list, l, bxy);
+  if (!T.leaf[c.k]) return;
+  const size_t q = (size_t)c.k * T.B * T.B + c.j * T.B + c.i;
+  T.r[q] = T.bo[q] - apply_at(T, T.x, c, true);
+}
+
+__global__ void fas_rhs_kernel(TreeDev T, const int* list, const int* bxy, int l) {
+  const Cell c = cell_of_thread(T, list, l, bxy);
+  const size_t q = (size_t)c.k * T.B * T.B + c.j * T.B + c.i;
+  T.b[q] = T.r[q] + apply_at(T, T.x, c, false);
+}
+
+// refined blocks of the list: field = mean of the 2x2 children cells
+__global__ void restrict_kernel(TreeDev T, const int* list, const int* child, int which) {
+  const int k = list[blockIdx.x], B = T.B;
+  const int i = threadIdx.x % B, j = threadIdx.x / B;
+  double* F = which == 0 ? T.x : T.r;
+  const int quad = (2 * i >= B ? 1 : 0) + 2 * (2 * j >= B ? 1 : 0);
+  const int ck = child[4 * k + quad];
+  const int ci = (2 * i) % B, cj = (2 * j) % B;
+  const double* cf = F + (size_t)ck * B * B;
+  double s = cf[cj * B + ci];
+  s = s + cf[cj * B + ci + 1];
+  s = s + cf[(cj + 1) * B + ci];
+  s = s + cf[(cj + 1) * B + ci + 1];
+  F[(size_t)k * B * B + j * B + i] = 0.25 * s;
+}
+
+__global__ void save_kernel(TreeDev T, const int* list) {
+  const size_t q = (size_t)list[blockIdx.x] * T.B * T.B + threadIdx.x;
+  T.xold[q] = T.x[q];
+}
+
+// e = x - xold at level-l cell (Ic, Jc), or ep where the level has no block there
+__device__ __forceinline__ double corr(const TreeDev& T, int l, int Ic, int Jc, double ep) {
+  int off;
+  const int k = blk_at(T, l, Ic, Jc, &off);
+  if (k < 0) return ep;
+  const size_t q = (size_t)k * T.B * T.B + off;
+  return T.x[q] - T.xold[q];
+}
+
+// blocks of level l (children of refined level-(l-1) blocks): x += bilinear(e) of level l-1
+__global__ void prolong_kernel(TreeDev T, const int* list, const int* bxy, int l) {
+  const Cell c = cell_of_thread(T, list, l, bxy);
+  const int Ic = c.I >> 1, Jc = c.J >> 1;
+  const int sx = (c.I & 1) ? 1 : -1, sy = (c.J & 1) ? 1 : -1;
+  const double e0 = corr(T, l - 1, Ic, Jc, 0.0);
+  double acc = 0.5625 * e0;
+  acc = acc + 0.1875 * corr(T, l - 1, Ic + sx, Jc, e0);
+  acc = acc + 0.1875 * corr(T, l - 1, Ic, Jc + sy, e0);
+  acc = acc + 0.0625 * corr(T, l - 1, Ic + sx, Jc + sy, e0);
+  const size_t q = (size_t)c.k * T.B * T.B + c.j * T.B + c.i;
+  T.x[q] = T.x[q] + acc;
+}
+
+// level 1 <-> a uniform (nx B) x (ny B) array: dir 0 gathers x and b, dir 1 scatters x
+__global__ void base_copy_kernel(TreeDev T, const int* list, const int* bxy, double* ux, double* ub, int dir) {
+  const int k = list[blockIdx.x], B = T.B;
+  const int i = threadIdx.x % B, j = threadIdx.x / B;
+  const size_t g = (size_t)(bxy[2 * k + 1] * B + j) * (T.nx[1] * B) + bxy[2 * k] * B + i;
+  const size_t q = (size_t)k * B * B + j * B + i;
+  if (dir == 0) {
+    ux[g] = T.x[q];
+    ub[g] = T.b[q];
+  } else {
+    T.x[q] = ux[g];
+  }
+}
+
+// max |bo - A x| (composite) and max |bo| over the leaves of the list, as bit patterns
+__global__ void resmax_kernel(TreeDev T, const int* list, const int* bxy, int l, unsigned long long* out) {
+  const Cell c = cell_of_thread(T, list, l, bxy);
+  const size_t q = (size_t)c.k * T.B * T.B + c.j * T.B + c.i;
+  const double r = fabs(T.bo[q] - apply_at(T, T.x, c, true));
+  const double bm = fabs(T.bo[q]);
+  // NaN compares as the largest bit pattern, so it cannot pass the convergence test
+  unsigned long long rb = isnan(r) ? 0x7ff8000000000000ull : (unsigned long long)__double_as_longlong(r);
+  atomicMax(&out[0], rb);
+  atomicMax(&out[1], (unsigned long long)__double_as_longlong(bm));
+}
+
+__global__ void apply_kernel(TreeDev T, const int* list, const int* bxy, int l, double* out, const int* slot) {
+  const Cell c = cell_of_thread(T, list, l, bxy);
+  out[(size_t)slot[c.k] * T.B * T.B + c.j * T.B + c.i] = apply_at(T, T.x, c, true);
+}
+
+// leaf data [leaf][B*B] <-> block arrays: dir 0 loads x and bo (b too), dir 1 stores x
+__global__ void leaf_copy_kernel(TreeDev T, const int* leaf_blk, const double* bsrc, double* xio, int dir) {
+  const int s = blockIdx.x, k = leaf_blk[s], n = T.B * T.B;
+  const size_t q = (size_t)k * n + threadIdx.x, p = (size_t)s * n + threadIdx.x;
+  if (dir == 0) {
+    T.x[q] = xio[p];
+    if (bsrc) {
+      T.bo[q] = bsrc[p];
+      T.b[q] = bsrc[p];
+    }
+  } else {
+    xio[p] = T.x[q];
+  }
+}
+
+// ------------------------------------------------------------------ host --
+struct Buf {
+  void* p = nullptr;
+  ~Buf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t alloc(size_t n) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    return cudaMalloc(&p, n ? n : 16);
+  }
+  template <typename T>
+  T* as() const {
+    return reinterpret_cast<T*>(p);
+  }
+};
+
+struct Tree {
+  mgt_config cfg{};
+  int B = 8, lmax = 1;
+  std::string err;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // host tree
+  std::vector<int> lev, bx, by, isleaf, child;  // per block; child [4 per block]
+  std::vector<std::vector<int>> bylev, parents;  // per level: all blocks, refined blocks
+  std::vector<int> leaf_blk;                     // leaf order of the caller -> block
+  std::map<long long, int> at;
+  // device
+  TreeDev T{};
+  Buf d_x, d_b, d_r, d_xold, d_bo, d_leaf, d_bxy, d_child, d_leafblk, d_slot, d_lists, d_tables, d_red, d_ux, d_ub;
+  std::vector<size_t> off_all, off_par;  // offsets of the level lists inside d_lists
+  mg_handle* base = nullptr;
+  unsigned long long* h_red = nullptr;
+  long long launches = 0, base_launches = 0;
+
+  ~Tree() {
+    if (base) mg_destroy(base);
+    if (h_red) cudaFreeHost(h_red);
+    if (own_stream) cudaStreamDestroy(stream);
+  }
+  int fail(int code, const std::string& m) {
+    err = m;
+    return code;
+  }
+  int cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return AMR_OK;
+    err = std::string("CUDA error ") + cudaGetErrorString(e) + " in " + what;
+    return e == cudaErrorMemoryAllocation ? AMR_ERR_OOM : AMR_ERR_CUDA;
+  }
+  int nx(int l) const { return cfg.nbx << (l - 1); }
+  int ny(int l) const { return cfg.nby << (l - 1); }
+  static long long key(int l, int x, int y) { return ((long long)l << 48) | ((long long)y << 24) | x; }
+  int find(int l, int x, int y) const {
+    auto it = at.find(key(l, x, y));
+    return it == at.end() ? -1 : it->second;
+  }
+  int add(int l, int x, int y) {
+    int k = find(l, x, y);
+    if (k >= 0) return k;
+    k = (int)lev.size();
+    lev.push_back(l);
+    bx.push_back(x);
+    by.push_back(y);
+    isleaf.push_back(0);
+    for (int q = 0; q < 4; ++q) child.push_back(-1);
+    at[key(l, x, y)] = k;
+    return k;
+  }
+
+  int build(const mgt_config* c, int nleaves, const int* level, const int* coords) {
+    cfg = *c;
+    B = c->B;
+    if ((B != 8 && B != 16) || c->nbx < 1 || c->nbx != c->nby || !(c->L > 0) || !(c->lambda >= 0) || c->nu1 < 0 ||
+        c->nu2 < 0 || c->max_cycles < 0 || !(c->rtol > 0) || !(c->base_rtol > 0) || nleaves < 1 || !level || !coords)
+      return fail(AMR_ERR_INVALID_ARG, "invalid tree multigrid configuration");
+    lmax = 1;
+    for (int k = 0; k < nleaves; ++k) lmax = std::max(lmax, level[k]);
+    if (lmax > kMaxLev) return fail(AMR_ERR_INVALID_ARG, "too many levels");
+    for (int k = 0; k < nleaves; ++k) {
+      int l = level[k], x = coords[2 * k], y = coords[2 * k + 1];
+      if (l < 1 || x < 0 || y < 0 || x >= nx(l) || y >= ny(l) || find(l, x, y) >= 0)
+        return fail(AMR_ERR_INVALID_ARG, "leaf outside the domain or repeated");
+      int id = add(l, x, y);
+      isleaf[id] = 1;
+      leaf_blk.push_back(id);
+      while (l > 1) {
+        int p = add(l - 1, x >> 1, y >> 1);
+        if (isleaf[p]) return fail(AMR_ERR_INVALID_ARG, "leaves overlap");
+        child[4 * p + (x & 1) + 2 * (y & 1)] = find(l, x, y);
+        --l;
+        x >>= 1;
+        y >>= 1;
+      }
+    }
+    const int nblk = (int)lev.size();
+    for (int k = 0; k < nblk; ++k)
+      if (!isleaf[k])
+        for (int q = 0; q < 4; ++q)
+          if (child[4 * k + q] < 0) return fail(AMR_ERR_INVALID_ARG, "the leaves do not tile the domain");
+    // 2:1 balance across faces and corners: every block position next to a leaf is covered by
+    // a block of the leaf's level or by one of the level above it
+    for (int k : leaf_blk) {
+      const int l = lev[k];
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          if (!dx && !dy) continue;
+          const int X = (bx[k] + dx + nx(l)) % nx(l), Y = (by[k] + dy + ny(l)) % ny(l);
+          if (find(l, X, Y) < 0 && (l == 1 || find(l - 1, X >> 1, Y >> 1) < 0))
+            return fail(AMR_ERR_INVALID_ARG, "the tree is not 2:1 balanced");
+        }
+    }
+    bylev.assign(lmax + 1, {});
+    parents.assign(lmax + 1, {});
+    for (int k = 0; k < nblk; ++k) {
+      bylev[lev[k]].push_back(k);
+      if (!isleaf[k]) parents[lev[k]].push_back(k);
+    }
+    if ((int)bylev[1].size() != c->nbx * c->nby) return fail(AMR_ERR_INVALID_ARG, "incomplete base level");
+    return AMR_OK;
+  }
+
+  int setup(void* strm) {
+    stream = (cudaStream_t)strm;
+    if (!stream) {
+      if (int rc = cuda(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking), "stream")) return rc;
+      own_stream = true;
+    }
+    const int nblk = (int)lev.size();
+    const size_t cells = (size_t)nblk * B * B;
+    // level lists (all blocks, refined blocks) and tables
+    std::vector<int> lists;
+    off_all.assign(lmax + 1, 0);
+    off_par.assign(lmax + 1, 0);
+    for (int l = 1; l <= lmax; ++l) {
+      off_all[l] = lists.size();
+      lists.insert(lists.end(), bylev[l].begin(), bylev[l].end());
+      off_par[l] = lists.size();
+      lists.insert(lists.end(), parents[l].begin(), parents[l].end());
+    }
+    std::vector<int> tables;
+    std::vector<size_t> toff(lmax + 1, 0);
+    for (int l = 1; l <= lmax; ++l) {
+      toff[l] = tables.size();
+      std::vector<int> t((size_t)nx(l) * ny(l), -1);
+      for (int k : bylev[l]) t[(size_t)by[k] * nx(l) + bx[k]] = k;
+      tables.insert(tables.end(), t.begin(), t.end());
+    }
+    std::vector<int> bxy(2 * nblk), slot(nblk, -1);
+    for (int k = 0; k < nblk; ++k) {
+      bxy[2 * k] = bx[k];
+      bxy[2 * k + 1] = by[k];
+    }
+    for (size_t s = 0; s < leaf_blk.size(); ++s) slot[leaf_blk[s]] = (int)s;
+    const size_t nu = (size_t)nx(1) * B * ny(1) * B;
+    int rc;
+    if ((rc = cuda(d_x.alloc(cells * 8), "alloc")) || (rc = cuda(d_b.alloc(cells * 8), "alloc")) ||
+        (rc = cuda(d_r.alloc(cells * 8), "alloc")) || (rc = cuda(d_xold.alloc(cells * 8), "alloc")) ||
+        (rc = cuda(d_bo.alloc(cells * 8), "alloc")) || (rc = cuda(d_leaf.alloc(nblk * 4), "alloc")) ||
+        (rc = cuda(d_bxy.alloc(bxy.size() * 4), "alloc")) || (rc = cuda(d_child.alloc(child.size() * 4), "alloc")) ||
+        (rc = cuda(d_leafblk.alloc(leaf_blk.size() * 4), "alloc")) || (rc = cuda(d_slot.alloc(nblk * 4), "alloc")) ||
+        (rc = cuda(d_lists.alloc(lists.size() * 4), "alloc")) || (rc = cuda(d_tables.alloc(tables.size() * 4), "alloc")) ||
+        (rc = cuda(d_red.alloc(16), "alloc")) || (rc = cuda(d_ux.alloc(nu * 8), "alloc")) ||
+        (rc = cuda(d_ub.alloc(nu * 8), "alloc")) || (rc = cuda(cudaMallocHost(&h_red, 16), "host alloc")))
+      return rc;
+    cudaMemcpy(d_leaf.p, isleaf.data(), nblk * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_bxy.p, bxy.data(), bxy.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_child.p, child.data(), child.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_leafblk.p, leaf_blk.data(), leaf_blk.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_slot.p, slot.data(), nblk * 4, cudaMemcpyHostToDevice);
+    if (!lists.empty()) cudaMemcpy(d_lists.p, lists.data(), lists.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_tables.p, tables.data(), tables.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemset(d_x.p, 0, cells * 8);
+    cudaMemset(d_b.p, 0, cells * 8);
+    cudaMemset(d_r.p, 0, cells * 8);
+    cudaMemset(d_xold.p, 0, cells * 8);
+    cudaMemset(d_bo.p, 0, cells * 8);
+    T.B = B;
+    T.lmax = lmax;
+    T.lam = cfg.lambda;
+    const double h1 = cfg.L / (double)(cfg.nbx * B);
+    for (int l = 1; l <= lmax; ++l) {
+      T.table[l] = d_tables.as<int>() + toff[l];
+      T.nx[l] = nx(l);
+      T.ny[l] = ny(l);
+      const double h = h1 / (double)(1 << (l - 1));
+      T.ih2[l] = 1.0 / (h * h);
+    }
+    T.leaf = d_leaf.as<int>();
+    T.x = d_x.as<double>();
+    T.b = d_b.as<double>();
+    T.r = d_r.as<double>();
+    T.xold = d_xold.as<double>();
+    T.bo = d_bo.as<double>();
+    // the base grid's uniform multigrid (periodic, side nbx B)
+    const int nside = cfg.nbx * B;
+    const double lamb = cfg.lambda;
+    mg_config mc{};
+    mc.ndim = 2;
+    mc.n_inst = 1;
+    mc.n_cells = &nside;
+    mc.lambda = &lamb;
+    mc.L = cfg.L;
+    mc.nu1 = 2;
+    mc.nu2 = 2;
+    mc.max_cycles = 200;
+    mc.rtol = cfg.base_rtol;
+    mc.coarse_max = cfg.coarse_max;
+    mc.precision = AMR_FP64;
+    mc.stream = stream;
+    mc.bc = MG_BC_PERIODIC;
+    if ((rc = mg_create(&mc, &base))) return fail(rc, "base multigrid: could not create");
+    return cuda(cudaDeviceSynchronize(), "setup");
+  }
+
+  const int* all(int l) const { return d_lists.as<int>() + off_all[l]; }
+  const int* par(int l) const { return d_lists.as<int>() + off_par[l]; }
+  unsigned nall(int l) const { return (unsigned)bylev[l].size(); }
+  unsigned npar(int l) const { return (unsigned)parents[l].size(); }
+
+  void restrict_all() {
+    for (int l = lmax - 1; l >= 1; --l)
+      if (npar(l)) {
+        restrict_kernel<<<npar(l), B * B, 0, stream>>>(T, par(l), d_child.as<int>(), 0);
+        ++launches;
+      }
+  }
+
+  int base_solve() {
+    const int* bxy = d_bxy.as<int>();
+    base_copy_kernel<<<nall(1), B * B, 0, stream>>>(T, all(1), bxy, d_ux.as<double>(), d_ub.as<double>(), 0);
+    ++launches;
+    int cyc;
+    double rr;
+    int rc = mg_solve(base, d_ub.as<double>(), d_ux.as<double>(), 1, &cyc, &rr);
+    if (rc) return fail(rc, std::string("base multigrid: ") + mg_last_error(base));
+    long long bl = 0;
+    mg_kernel_launches(base, &bl);
+    launches += bl - base_launches;
+    base_launches = bl;
+    base_copy_kernel<<<nall(1), B * B, 0, stream>>>(T, all(1), bxy, d_ux.as<double>(), d_ub.as<double>(), 1);
+    ++launches;
+    return AMR_OK;
+  }
+
+  int vcycle(int l) {
+    if (l == 1) return base_solve();
+    const int* bxy = d_bxy.as<int>();
+    const unsigned nt = (unsigned)(B * B);
+    auto smooth = [&](int sweeps) {
+      for (int s = 0; s < sweeps; ++s)
+        for (int colour = 0; colour < 2; ++colour) {
+          gs_kernel<<<nall(l), nt, 0, stream>>>(T, all(l), bxy, l, colour);
+          ++launches;
+        }
+    };
+    smooth(cfg.nu1);
+    level_residual_kernel<<<nall(l), nt, 0, stream>>>(T, all(l), bxy, l);
+    ++launches;
+    if (npar(l - 1)) {
+      restrict_kernel<<<npar(l - 1), nt, 0, stream>>>(T, par(l - 1), d_child.as<int>(), 0);
+      ++launches;
+    }
+    save_kernel<<<nall(l - 1), nt, 0, stream>>>(T, all(l - 1));
+    ++launches;
+    if (npar(l - 1)) {
+      restrict_kernel<<<npar(l - 1), nt, 0, stream>>>(T, par(l - 1), d_child.as<int>(), 1);
+      ++launches;
+    }
+    composite_residual_kernel<<<nall(l - 1), nt, 0, stream>>>(T, all(l - 1), bxy, l - 1);
+    fas_rhs_kernel<<<nall(l - 1), nt, 0, stream>>>(T, all(l - 1), bxy, l - 1);
+    launches += 2;
+    if (int rc = vcycle(l - 1)) return rc;
+    prolong_kernel<<<nall(l), nt, 0, stream>>>(T, all(l), bxy, l);
+    ++launches;
+    smooth(cfg.nu2);
+    return cuda(cudaGetLastError(), "tree V-cycle");
+  }
+
+  // composite residual max and max |b| over the leaves (refined blocks restricted first)
+  int resmax(double* rm, double* bm) {
+    restrict_all();
+    if (int rc = cuda(cudaMemsetAsync(d_red.p, 0, 16, stream), "memset")) return rc;
+    const int* bxy = d_bxy.as<int>();
+    for (int l = 1; l <= lmax; ++l) {
+      // leaves of level l only: the kernel runs on all blocks of the level and skips none, so
+      // pass the leaf blocks through their own list
+      if (!leafl[l].empty()) {
+        resmax_kernel<<<(unsigned)leafl[l].size(), B * B, 0, stream>>>(T, d_leafl.as<int>() + leafl_off[l], bxy, l,
+                                                                        d_red.as<unsigned long long>());
+        ++launches;
+      }
+    }
+    if (int rc = cuda(cudaMemcpyAsync(h_red, d_red.p, 16, cudaMemcpyDeviceToHost, stream), "copy")) return rc;
+    if (int rc = cuda(cudaStreamSynchronize(stream), "sync")) return rc;
+    double a, b;
+    std::memcpy(&a, &h_red[0], 8);
+    std::memcpy(&b, &h_red[1], 8);
+    *rm = a;
+    *bm = b;
+    return AMR_OK;
+  }
+
+  std::vector<std::vector<int>> leafl;
+  std::vector<size_t> leafl_off;
+  Buf d_leafl;
+
+  int setup_leaf_lists() {
+    leafl.assign(lmax + 1, {});
+    for (int k : leaf_blk) leafl[lev[k]].push_back(k);
+    std::vector<int> flat;
+    leafl_off.assign(lmax + 1, 0);
+    for (int l = 1; l <= lmax; ++l) {
+      leafl_off[l] = flat.size();
+      flat.insert(flat.end(), leafl[l].begin(), leafl[l].end());
+    }
+    if (int rc = cuda(d_leafl.alloc(flat.size() * 4), "alloc")) return rc;
+    return cuda(cudaMemcpy(d_leafl.p, flat.data(), flat.size() * 4, cudaMemcpyHostToDevice), "copy");
+  }
+};
+
+}  // namespace mgtree
+
+using namespace mgtree;
+
+struct mgt_handle {
+  Tree t;
+};
+
+extern "C" {
+
+int mgt_create(const mgt_config* cfg, int nleaves, const int* level, const int* coords, mgt_handle** out) {
+  if (!cfg || !out) return AMR_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::unique_ptr<mgt_handle> h(new mgt_handle());
+  int rc = h->t.build(cfg, nleaves, level, coords);
+  if (!rc) rc = h->t.setup(cfg->stream);
+  if (!rc) rc = h->t.setup_leaf_lists();
+  if (rc) return rc;
+  *out = h.release();
+  return AMR_OK;
+}
+
+int mgt_destroy(mgt_handle* h) {
+  if (!h) return AMR_ERR_INVALID_ARG;
+  delete h;
+  return AMR_OK;
+}
+
+const char* mgt_last_error(const mgt_handle* h) { return h ? h->t.err.c_str() : "null handle"; }
+
+int mgt_num_leaves(const mgt_handle* h, long long* n) {
+  if (!h || !n) return AMR_ERR_INVALID_ARG;
+  *n = (long long)h->t.leaf_blk.size();
+  return AMR_OK;
+}
+
+int mgt_solve(mgt_handle* h, const double* b, double* x, int on_device, int fixed_cycles, int* cycles,
+              double* relres) {
+  if (!h || !b || !x || fixed_cycles < 0) return AMR_ERR_INVALID_ARG;
+  Tree& t = h->t;
+  const size_t n = t.leaf_blk.size() * (size_t)t.B * t.B;
+  double* db = const_cast<double*>(b);
+  double* dx = x;
+  Buf hb, hx;
+  int rc;
+  if (!on_device) {  // stage host arrays through device buffers
+    if ((rc = t.cuda(hb.alloc(n * 8), "alloc")) || (rc = t.cuda(hx.alloc(n * 8), "alloc"))) return rc;
+    cudaMemcpyAsync(hb.p, b, n * 8, cudaMemcpyHostToDevice, t.stream);
+    cudaMemcpyAsync(hx.p, x, n * 8, cudaMemcpyHostToDevice, t.stream);
+    db = hb.as<double>();
+    dx = hx.as<double>();
+  }
+  const unsigned nl = (unsigned)t.leaf_blk.size(), nt = (unsigned)(t.B * t.B);
+  leaf_copy_kernel<<<nl, nt, 0, t.stream>>>(t.T, t.d_leafblk.as<int>(), db, dx, 0);
+  ++t.launches;
+  double rm, bm;
+  if ((rc = t.resmax(&rm, &bm))) return rc;
+  int cyc = 0;
+  while (fixed_cycles > 0 ? cyc < fixed_cycles : (rm > t.cfg.rtol * bm && cyc < t.cfg.max_cycles)) {
+    if ((rc = t.vcycle(t.lmax))) return rc;
+    ++cyc;
+    if ((rc = t.resmax(&rm, &bm))) return rc;
+  }
+  leaf_copy_kernel<<<nl, nt, 0, t.stream>>>(t.T, t.d_leafblk.as<int>(), nullptr, dx, 1);
+  ++t.launches;
+  if (!on_device) cudaMemcpyAsync(x, hx.p, n * 8, cudaMemcpyDeviceToHost, t.stream);
+  if ((rc = t.cuda(cudaStreamSynchronize(t.stream), "sync"))) return rc;
+  if (cycles) *cycles = cyc;
+  if (relres) *relres = bm > 0 ? rm / bm : rm;
+  if (fixed_cycles == 0 && !(rm <= t.cfg.rtol * bm))
+    return t.fail(MG_ERR_NOT_CONVERGED, "the composite residual did not reach rtol within max_cycles");
+  return AMR_OK;
+}
+
+int mgt_apply(mgt_handle* h, const double* x, double* Ax, int on_device) {
+  if (!h || !x || !Ax) return AMR_ERR_INVALID_ARG;
+  Tree& t = h->t;
+  const size_t n = t.leaf_blk.size() * (size_t)t.B * t.B;
+  Buf hx, ha;
+  double* dx = const_cast<double*>(x);
+  double* da = Ax;
+  int rc;
+  if (!on_device) {
+    if ((rc = t.cuda(hx.alloc(n * 8), "alloc")) || (rc = t.cuda(ha.alloc(n * 8), "alloc"))) return rc;
+    cudaMemcpyAsync(hx.p, x, n * 8, cudaMemcpyHostToDevice, t.stream);
+    dx = hx.as<double>();
+    da = ha.as<double>();
+  }
+  const unsigned nt = (unsigned)(t.B * t.B);
+  leaf_copy_kernel<<<(unsigned)t.leaf_blk.size(), nt, 0, t.stream>>>(t.T, t.d_leafblk.as<int>(), nullptr, dx, 0);
+  t.restrict_all();
+  for (int l = 1; l <= t.lmax; ++l)
+    if (!t.leafl[l].empty())
+      apply_kernel<<<(unsigned)t.leafl[l].size(), nt, 0, t.stream>>>(t.T, t.d_leafl.as<int>() + t.leafl_off[l],
+                                                                    t.d_bxy.as<int>(), l, da, t.d_slot.as<int>());
+  if (!on_device) cudaMemcpyAsync(Ax, ha.p, n * 8, cudaMemcpyDeviceToHost, t.stream);
+  return t.cuda(cudaStreamSynchronize(t.stream), "sync");
+}
+
+int mgt_kernel_launches(const mgt_handle* h, long long* n) {
+  if (!h || !n) return AMR_ERR_INVALID_ARG;
+  *n = h->t.launches;
+  return AMR_OK;
+}
+
+}  // extern "C"
