@@ -101,6 +101,7 @@ def lib():
         for f in ("orc_amg_apply", "orc_amg_face_ghosts"):
             getattr(L, f).argtypes = [C.POINTER(OrcAmgConfig), C.c_int, _ip, _ip, _dp, _dp]
         L.orc_amg_solve.argtypes = [C.POINTER(OrcAmgConfig), C.c_int, _ip, _ip, _dp, _dp, C.c_int, _dp]
+        L.orc_amg_rd_step.argtypes = [C.POINTER(OrcAmgConfig), C.c_int, _ip, _ip] + [C.c_double] * 5 + [_dp, _dp, _ip]
         if hasattr(L, "orc_cnn_forward"):
             _bind_cnn(L)
         _lib = L
@@ -467,3 +468,17 @@ def amg_face_ghosts(level, coords, x, nb, B, L):
                                  _d(g)):
         raise ValueError("invalid tree")
     return g
+
+
+def amg_rd_step(level, coords, u, v, nb, B, L, Du, Dv, F, k, dt, **kw):
+    """Gray-Scott IMEX step on the quadtree leaves; returns (u, v, cycles[2])."""
+    level, coords = _tree(level, coords)
+    u, v = _f64(u).copy(), _f64(v).copy()
+    cyc = np.zeros(2, dtype=np.int32)
+    st = lib().orc_amg_rd_step(C.byref(amg_config(nb, B, L, 0.0, **kw)), len(level), _i(level), _i(coords),
+                               Du, Dv, F, k, dt, _d(u), _d(v), _i(cyc))
+    if st == -2:
+        raise ValueError("invalid tree")
+    if st != 0:
+        raise RuntimeError("tree multigrid did not converge")
+    return u, v, cyc

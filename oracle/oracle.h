@@ -136,6 +136,12 @@ int orc_amg_apply(const orc_amg_config* c, int nleaves, const int* level, const 
                   double* Ax);
 int orc_amg_face_ghosts(const orc_amg_config* c, int nleaves, const int* level, const int* coords, const double* x,
                         double* ghosts);
+/* Gray-Scott IMEX step (Eq. (imex), Eq. (gray-scott)) on the leaves: composite Laplacian
+ * for the explicit parts, the tree multigrid (lambda = 2/(dt D), guess w_n; c->lambda is
+ * ignored) for the implicit stage.  cycles[2]: V-cycles per species.  0, -1 (a solve did
+ * not reach rtol) or -2 (invalid tree). */
+int orc_amg_rd_step(const orc_amg_config* c, int nleaves, const int* level, const int* coords, double Du, double Dv,
+                    double F, double k, double dt, double* u, double* v, int* cycles);
 
 /* ---- reaction-diffusion step (Sec. 2.5): w = (u, v), dw/dt = F0(w) + F1(w), F0 the
  * reaction terms of Eq. (gray-scott) or Eq. (schnakenberg), F1 = D lap_h w ---- */

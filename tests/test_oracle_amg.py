@@ -140,3 +140,38 @@ def test_invalid_trees_are_rejected():
     crd = np.array([(0, 0), (1, 0), (0, 1)], np.int32)
     with pytest.raises(ValueError):
         O.amg_solve(lev, crd, np.zeros((3, B * B)), np.zeros((3, B * B)), nb, B, 1.0, 1.0)
+
+
+# ------------------------------------------------------------ Gray-Scott on the tree --
+GS = dict(Du=2e-5, Dv=1e-5, F=0.046, k=0.063)
+
+
+def test_rd_step_on_a_tree_refined_everywhere_is_the_uniform_step():
+    nb, B, L, dt = 2, 8, 0.25, 0.5
+    lev = np.full(4 * nb * nb, 2, np.int32)
+    crd = np.array([(x, y) for y in range(2 * nb) for x in range(2 * nb)], np.int32)
+    n = 2 * nb * B
+    rng = np.random.default_rng(4)
+    uu, vu = 1.0 - 0.3 * rng.random((n, n)), 0.25 * rng.random((n, n))
+    blk = lambda a: np.stack([a[y * B:(y + 1) * B, x * B:(x + 1) * B].ravel() for x, y in crd])
+    u1, v1, cyc = O.amg_rd_step(lev, crd, blk(uu), blk(vu), nb, B, L, dt=dt, rtol=1e-12, **GS)
+    uo, vo, _ = O.rd_step(uu, vu, L, dt=dt, rtol=1e-13, **GS)
+    assert np.max(np.abs(u1 - blk(uo))) <= 1e-10 and np.max(np.abs(v1 - blk(vo))) <= 1e-10
+
+
+def test_rd_step_on_a_tree_keeps_the_homogeneous_state_and_conserves():
+    nb, B, L, dt = 4, 8, 2.0, 0.5
+    lev, crd = patch_tree(nb)
+    n = len(lev) * B * B
+    u1, v1, cyc = O.amg_rd_step(lev, crd, np.ones(n), np.zeros(n), nb, B, L, dt=dt, **GS)
+    assert np.array_equal(u1, np.ones(n)) and np.array_equal(v1, np.zeros(n)) and np.all(cyc == 0)
+    # F = k = 0: the reactions exchange u and v, and the composite diffusion is conservative,
+    # so the area-weighted total of u + v is kept
+    X, Y, h = centres(lev, crd, nb, B, L)
+    u = (1.0 - 0.5 * np.exp(-25 * ((X - 1.0) ** 2 + (Y - 1.0) ** 2))).ravel()
+    v = (0.5 * np.exp(-25 * ((X - 1.0) ** 2 + (Y - 1.1) ** 2))).ravel()
+    area = np.repeat(h ** 2, B * B)
+    u1, v1, _ = O.amg_rd_step(lev, crd, u, v, nb, B, L, dt=dt, Du=2e-3, Dv=1e-3, F=0.0, k=0.0, rtol=1e-13)
+    t0, t1 = np.sum(area * (u + v)), np.sum(area * (u1 + v1))
+    assert abs(t1 - t0) <= 1e-12 * t0, (t0, t1)
+    assert np.max(np.abs(u1 - u)) > 1e-4  # the step did something
