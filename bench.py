@@ -382,6 +382,35 @@ def bench_schnakenberg(torch, amrvac, stream):
             "timing": "host wall clock around synchronous rd_step calls"}
 
 
+def bench_gray_scott_tree(torch, amrvac, stream, steps=20):
+    """Sec. 2.5.2's Gray-Scott run on a three-level block quadtree: F = 0.046, k = 0.063,
+    D_u = 2e-5, D_v = 1e-5, L = 2, 8^2 blocks, base 128^2, finest 512^2, dt = 0.5, two Gaussian
+    perturbations; IMEX steps with the float64 tree multigrid (rtol 1e-10).  The mesh is
+    fixed, refined around the perturbations (the paper adapts it as the pattern grows)."""
+    from paper_2004_03275_gb300 import inputs
+    p = inputs.GRAY_SCOTT_PAPER
+    nb, B = 16, 8
+    lev, crd = inputs.gray_scott_tree(nb=nb, L=p["L"])
+    X, Y = inputs.leaf_cell_centres(lev, crd, nb, B, p["L"])
+    u, v = inputs.gray_scott_gaussians(X, Y)
+    s = amrvac.TreeRdSolver(lev, crd, nb, B, p["L"], Du=p["Du"], Dv=p["Dv"], F=p["F"], k=p["k"], dt=p["dt"],
+                            stream=stream.cuda_stream)
+    s.set_state(u.ravel(), v.ravel())
+    s.step(2)
+    n0 = s.kernel_launches()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cyc = s.step(steps)
+    el = (time.perf_counter() - t0) / steps
+    out = {"workload": "Gray-Scott IMEX on a 3-level quadtree (8^2 blocks, 128^2..512^2), float64 tree multigrid",
+           "leaves_per_level": [int(c) for c in np.bincount(lev)[1:]], "cells": int(len(lev) * B * B),
+           "ms_per_step": round(el * 1e3, 3), "vcycles_per_solve": round(float(np.mean(cyc)), 2),
+           "kernels_per_step": round((s.kernel_launches() - n0) / steps, 1), "steps": steps,
+           "timing": "host wall clock around synchronous rdt_step calls (one host poll per V-cycle)"}
+    s.close()
+    return out
+
+
 # 2 x 9 x (5*16 + 16*16 + 16*16 + 16*2) multiply-adds x 2 per pixel for the 4 layers
 CNN_FLOP_PER_PIXEL_2D = 11232.0
 # HBM bytes per pixel of the layer-by-layer inference: layer 1 reads the float32 5-channel input
@@ -681,7 +710,7 @@ def main():
     extra = {}
     if not args.skip_extra and rank == 0:
         names = ["gray_scott_batch", "mg_vcycle", "blast3d", "learned_guess_2d", "learned_guess_3d",
-                 "cnn_forward_2048", "schnakenberg"]
+                 "cnn_forward_2048", "schnakenberg", "gray_scott_tree"]
         want = names if args.extras == "all" else [e for e in args.extras.split(",") if e in names]
         runs = {"gray_scott_batch": lambda: bench_gray_scott(torch, amrvac, stream),
                 "mg_vcycle": lambda: bench_mg_vcycle(torch, amrvac, stream, hbm),
@@ -689,7 +718,8 @@ def main():
                 "learned_guess_2d": lambda: bench_learned_guess(torch, amrvac, stream),
                 "learned_guess_3d": lambda: bench_learned_guess_3d(torch, amrvac, stream),
                 "cnn_forward_2048": lambda: bench_cnn_forward(torch, amrvac, stream, bf16_peak(), hbm),
-                "schnakenberg": lambda: bench_schnakenberg(torch, amrvac, stream)}
+                "schnakenberg": lambda: bench_schnakenberg(torch, amrvac, stream),
+                "gray_scott_tree": lambda: bench_gray_scott_tree(torch, amrvac, stream)}
         for name in want:
             extra[name] = runs[name]()
 

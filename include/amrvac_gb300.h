@@ -331,6 +331,26 @@ int mgt_solve(mgt_handle* h, const double* b, double* x, int on_device, int fixe
 int mgt_apply(mgt_handle* h, const double* x, double* Ax, int on_device);
 int mgt_kernel_launches(const mgt_handle* h, long long* n);
 
+/* Gray-Scott IMEX steps (Eq. (imex), Eq. (gray-scott)) on the leaves of the same kind
+ * of quadtree: the composite Laplacian above for the explicit parts, the tree multigrid
+ * (lambda = 2/(dt D) per species, guess w_n) for the implicit stage.  The tree is fixed
+ * (no regrid).  mg.lambda is ignored; state [leaf][B*B] per species, float64. */
+typedef struct rdt_handle rdt_handle;
+
+typedef struct {
+  mgt_config mg;
+  double Du, Dv, F, k, dt;
+} rdt_config;
+
+int rdt_create(const rdt_config* cfg, int nleaves, const int* level, const int* coords, rdt_handle** out);
+int rdt_destroy(rdt_handle* h);
+const char* rdt_last_error(const rdt_handle* h);
+int rdt_set_state(rdt_handle* h, const double* u, const double* v, int on_device);
+int rdt_read_state(rdt_handle* h, double* u, double* v, int on_device);
+/* cycles (host, may be NULL): [step][2] V-cycles (u, v).  Synchronous. */
+int rdt_step(rdt_handle* h, int nsteps, int* cycles);
+int rdt_kernel_launches(const rdt_handle* h, long long* n);
+
 /* ------------------------------------------------------------------------
  * Learned multigrid initial guess (no counterpart in the paper; the project's
  * addition to the implicit diffusion stage of Eq. (imex)).

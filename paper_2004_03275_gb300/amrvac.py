@@ -59,6 +59,11 @@ class MgtConfig(C.Structure):
     ]
 
 
+class RdtConfig(C.Structure):
+    _fields_ = [("mg", MgtConfig), ("Du", C.c_double), ("Dv", C.c_double), ("F", C.c_double), ("k", C.c_double),
+                ("dt", C.c_double)]
+
+
 MG_BC = {"periodic": 0, "neumann": 1}
 RD_MODEL = {"gray-scott": 0, "schnakenberg": 1}
 RD_SCHEME = {"imex": 0, "split": 1, "explicit": 2}
@@ -133,6 +138,13 @@ _SIGS = {
     "mgt_solve": ([_vp, _vp, _vp, C.c_int, C.c_int, _ip, _dp], C.c_int),
     "mgt_apply": ([_vp, _vp, _vp, C.c_int], C.c_int),
     "mgt_kernel_launches": ([_vp, _llp], C.c_int),
+    "rdt_create": ([C.POINTER(RdtConfig), C.c_int, _ip, _ip, C.POINTER(_vp)], C.c_int),
+    "rdt_destroy": ([_vp], C.c_int),
+    "rdt_last_error": ([_vp], C.c_char_p),
+    "rdt_set_state": ([_vp, _vp, _vp, C.c_int], C.c_int),
+    "rdt_read_state": ([_vp, _vp, _vp, C.c_int], C.c_int),
+    "rdt_step": ([_vp, C.c_int, _ip], C.c_int),
+    "rdt_kernel_launches": ([_vp, _llp], C.c_int),
 }
 
 
@@ -568,6 +580,58 @@ class TreeMgSolver:
     def kernel_launches(self):
         n = C.c_longlong()
         _check(self.lib.mgt_kernel_launches(self.h, C.byref(n)), self.h, "mgt_last_error")
+        return n.value
+
+
+class TreeRdSolver:
+    """Owns one rdt_handle: Gray-Scott IMEX steps on the leaves of a fixed 2D block quadtree."""
+
+    def __init__(self, level, coords, nb, B, L, Du, Dv, F, k, dt, nu1=2, nu2=2, max_cycles=50, rtol=1e-10,
+                 base_rtol=1e-12, coarse_max=8, stream=None):
+        self.lib = load()
+        self.level = np.ascontiguousarray(level, dtype=np.int32)
+        self.coords = np.ascontiguousarray(coords, dtype=np.int32).reshape(-1, 2)
+        mg = MgtConfig(nb, nb, B, L, 0.0, nu1, nu2, max_cycles, rtol, base_rtol, coarse_max, stream)
+        c = RdtConfig(mg, Du, Dv, F, k, dt)
+        h = _vp()
+        rc = self.lib.rdt_create(C.byref(c), len(self.level), self.level.ctypes.data_as(_ip),
+                                 self.coords.ctypes.data_as(_ip), C.byref(h))
+        if rc != AMR_OK:
+            raise AmrError(rc, "rdt_create")
+        self.h = h
+        self.n = len(self.level) * B * B
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rdt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, u, v):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        _check(self.lib.rdt_set_state(self.h, u.ctypes.data_as(_vp), v.ctypes.data_as(_vp), 0), self.h,
+               "rdt_last_error")
+
+    def read_state(self):
+        u, v = np.zeros(self.n), np.zeros(self.n)
+        _check(self.lib.rdt_read_state(self.h, u.ctypes.data_as(_vp), v.ctypes.data_as(_vp), 0), self.h,
+               "rdt_last_error")
+        return u, v
+
+    def step(self, nsteps=1):
+        cyc = np.zeros((nsteps, 2), dtype=np.int32)
+        _check(self.lib.rdt_step(self.h, nsteps, cyc.ctypes.data_as(_ip)), self.h, "rdt_last_error")
+        return cyc
+
+    def kernel_launches(self):
+        n = C.c_longlong()
+        _check(self.lib.rdt_kernel_launches(self.h, C.byref(n)), self.h, "rdt_last_error")
         return n.value
 
 

@@ -265,6 +265,59 @@ __global__ void leaf_copy_kernel(TreeDev T, const int* leaf_blk, const double* b
   }
 }
 
+// composite Laplacian (sum of neighbours - 4 x) / h^2 of the leaves of the list, into
+// leaf-major out[slot]
+__global__ void lap_kernel(TreeDev T, const int* list, const int* bxy, int l, double* out, const int* slot) {
+  const Cell c = cell_of_thread(T, list, l, bxy);
+  const double x0 = T.x[(size_t)c.k * T.B * T.B + c.j * T.B + c.i];
+  out[(size_t)slot[c.k] * T.B * T.B + c.j * T.B + c.i] = (nbr_sum(T, T.x, c, x0, true) - 4.0 * x0) * T.ih2[l];
+}
+
+// Gray-Scott on leaf-major arrays (Eq. (gray-scott)), IMEX stage 1 (Eq. (imex)):
+// b = lambda (w + dt F0 + dt/2 D lap w), Fn = F0 + D lap w, per species
+struct RdtArgs {
+  double Du, Dv, F, k, dt, lam_u, lam_v;
+  double* u;
+  double* v;
+  const double* lu;
+  const double* lv;
+  double* bu;
+  double* bv;
+  double* Fn;  // [2][n]
+  double* xu;  // solutions w* (guess w_n)
+  double* xv;
+  long long n;
+};
+
+__global__ void rdt_rhs_kernel(RdtArgs A) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  const double u = A.u[i], v = A.v[i];
+  const double uvv = (u * v) * v;
+  const double fu = -uvv + A.F * (1.0 - u);
+  const double fv = uvv - (A.F + A.k) * v;
+  const double gu = (u + A.dt * fu) + ((0.5 * A.dt) * A.Du) * A.lu[i];
+  const double gv = (v + A.dt * fv) + ((0.5 * A.dt) * A.Dv) * A.lv[i];
+  A.bu[i] = A.lam_u * gu;
+  A.bv[i] = A.lam_v * gv;
+  A.Fn[i] = fu + A.Du * A.lu[i];
+  A.Fn[A.n + i] = fv + A.Dv * A.lv[i];
+  A.xu[i] = u;
+  A.xv[i] = v;
+}
+
+// stage 2: w = w + dt/2 [F(w_n) + F(w*)], lu, lv the Laplacians of w*
+__global__ void rdt_finish_kernel(RdtArgs A) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  const double us = A.xu[i], vs = A.xv[i];
+  const double uvv = (us * vs) * vs;
+  const double fus = -uvv + A.F * (1.0 - us);
+  const double fvs = uvv - (A.F + A.k) * vs;
+  A.u[i] = A.u[i] + (0.5 * A.dt) * (A.Fn[i] + (fus + A.Du * A.lu[i]));
+  A.v[i] = A.v[i] + (0.5 * A.dt) * (A.Fn[A.n + i] + (fvs + A.Dv * A.lv[i]));
+}
+
 // ------------------------------------------------------------------ host --
 struct Buf {
   void* p = nullptr;
@@ -572,6 +625,44 @@ struct Tree {
   std::vector<size_t> leafl_off;
   Buf d_leafl;
 
+  // solve with device leaf-major b and x (x: guess in, solution out)
+  int solve_dev(const double* db, double* dx, int fixed_cycles, int* cycles, double* rmo, double* bmo) {
+    const unsigned nl = (unsigned)leaf_blk.size(), nt = (unsigned)(B * B);
+    leaf_copy_kernel<<<nl, nt, 0, stream>>>(T, d_leafblk.as<int>(), db, dx, 0);
+    ++launches;
+    double rm, bm;
+    int rc;
+    if ((rc = resmax(&rm, &bm))) return rc;
+    int cyc = 0;
+    while (fixed_cycles > 0 ? cyc < fixed_cycles : (rm > cfg.rtol * bm && cyc < cfg.max_cycles)) {
+      if ((rc = vcycle(lmax))) return rc;
+      ++cyc;
+      if ((rc = resmax(&rm, &bm))) return rc;
+    }
+    leaf_copy_kernel<<<nl, nt, 0, stream>>>(T, d_leafblk.as<int>(), nullptr, dx, 1);
+    ++launches;
+    *cycles = cyc;
+    *rmo = rm;
+    *bmo = bm;
+    return cuda(cudaGetLastError(), "tree solve");
+  }
+
+  // composite Laplacian of device leaf-major w into lap
+  int lap_leaves(const double* w, double* lap) {
+    const unsigned nt = (unsigned)(B * B);
+    leaf_copy_kernel<<<(unsigned)leaf_blk.size(), nt, 0, stream>>>(T, d_leafblk.as<int>(), nullptr,
+                                                                  const_cast<double*>(w), 0);
+    ++launches;
+    restrict_all();
+    for (int l = 1; l <= lmax; ++l)
+      if (!leafl[l].empty()) {
+        lap_kernel<<<(unsigned)leafl[l].size(), nt, 0, stream>>>(T, d_leafl.as<int>() + leafl_off[l], d_bxy.as<int>(),
+                                                                 l, lap, d_slot.as<int>());
+        ++launches;
+      }
+    return cuda(cudaGetLastError(), "laplacian");
+  }
+
   int setup_leaf_lists() {
     leafl.assign(lmax + 1, {});
     for (int k : leaf_blk) leafl[lev[k]].push_back(k);
@@ -638,19 +729,9 @@ int mgt_solve(mgt_handle* h, const double* b, double* x, int on_device, int fixe
     db = hb.as<double>();
     dx = hx.as<double>();
   }
-  const unsigned nl = (unsigned)t.leaf_blk.size(), nt = (unsigned)(t.B * t.B);
-  leaf_copy_kernel<<<nl, nt, 0, t.stream>>>(t.T, t.d_leafblk.as<int>(), db, dx, 0);
-  ++t.launches;
   double rm, bm;
-  if ((rc = t.resmax(&rm, &bm))) return rc;
-  int cyc = 0;
-  while (fixed_cycles > 0 ? cyc < fixed_cycles : (rm > t.cfg.rtol * bm && cyc < t.cfg.max_cycles)) {
-    if ((rc = t.vcycle(t.lmax))) return rc;
-    ++cyc;
-    if ((rc = t.resmax(&rm, &bm))) return rc;
-  }
-  leaf_copy_kernel<<<nl, nt, 0, t.stream>>>(t.T, t.d_leafblk.as<int>(), nullptr, dx, 1);
-  ++t.launches;
+  int cyc;
+  if ((rc = t.solve_dev(db, dx, fixed_cycles, &cyc, &rm, &bm))) return rc;
   if (!on_device) cudaMemcpyAsync(x, hx.p, n * 8, cudaMemcpyDeviceToHost, t.stream);
   if ((rc = t.cuda(cudaStreamSynchronize(t.stream), "sync"))) return rc;
   if (cycles) *cycles = cyc;
@@ -688,6 +769,147 @@ int mgt_apply(mgt_handle* h, const double* x, double* Ax, int on_device) {
 int mgt_kernel_launches(const mgt_handle* h, long long* n) {
   if (!h || !n) return AMR_ERR_INVALID_ARG;
   *n = h->t.launches;
+  return AMR_OK;
+}
+
+// ---------------------------------------------------- Gray-Scott on the tree --
+struct rdt_handle {
+  rdt_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::unique_ptr<Tree> tu, tv;  // the same leaves, lambda 2/(dt Du) and 2/(dt Dv)
+  Buf d_u, d_v, d_lu, d_lv, d_bu, d_bv, d_Fn, d_xu, d_xv;
+  long long n = 0;
+  std::string err;
+  ~rdt_handle() {
+    tu.reset();
+    tv.reset();
+    if (own_stream) cudaStreamDestroy(stream);
+  }
+  int fail(int code, const std::string& m) {
+    err = m;
+    return code;
+  }
+};
+
+int rdt_create(const rdt_config* cfg, int nleaves, const int* level, const int* coords, rdt_handle** out) {
+  if (!cfg || !out || !(cfg->dt > 0) || !(cfg->Du > 0) || !(cfg->Dv > 0)) return AMR_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::unique_ptr<rdt_handle> h(new rdt_handle());
+  h->cfg = *cfg;
+  h->stream = (cudaStream_t)cfg->mg.stream;
+  if (!h->stream) {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) return AMR_ERR_CUDA;
+    h->own_stream = true;
+  }
+  const double D[2] = {cfg->Du, cfg->Dv};
+  std::unique_ptr<Tree>* t[2] = {&h->tu, &h->tv};
+  for (int s = 0; s < 2; ++s) {
+    mgt_config mc = cfg->mg;
+    mc.lambda = 2.0 / (cfg->dt * D[s]);
+    mc.stream = h->stream;
+    t[s]->reset(new Tree());
+    Tree& tr = **t[s];
+    int rc = tr.build(&mc, nleaves, level, coords);
+    if (!rc) rc = tr.setup(h->stream);
+    if (!rc) rc = tr.setup_leaf_lists();
+    if (rc) {
+      *out = nullptr;
+      return rc;
+    }
+  }
+  h->n = (long long)nleaves * cfg->mg.B * cfg->mg.B;
+  const size_t bytes = (size_t)h->n * 8;
+  for (Buf* b : {&h->d_u, &h->d_v, &h->d_lu, &h->d_lv, &h->d_bu, &h->d_bv, &h->d_xu, &h->d_xv})
+    if (b->alloc(bytes) != cudaSuccess) return AMR_ERR_OOM;
+  if (h->d_Fn.alloc(2 * bytes) != cudaSuccess) return AMR_ERR_OOM;
+  *out = h.release();
+  return AMR_OK;
+}
+
+int rdt_destroy(rdt_handle* h) {
+  if (!h) return AMR_ERR_INVALID_ARG;
+  delete h;
+  return AMR_OK;
+}
+
+const char* rdt_last_error(const rdt_handle* h) {
+  if (!h) return "null handle";
+  if (!h->err.empty()) return h->err.c_str();
+  if (h->tu && !h->tu->err.empty()) return h->tu->err.c_str();
+  return h->tv ? h->tv->err.c_str() : "";
+}
+
+int rdt_set_state(rdt_handle* h, const double* u, const double* v, int on_device) {
+  if (!h || !u || !v) return AMR_ERR_INVALID_ARG;
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (cudaMemcpyAsync(h->d_u.p, u, h->n * 8, k, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(h->d_v.p, v, h->n * 8, k, h->stream) != cudaSuccess)
+    return AMR_ERR_CUDA;
+  return cudaStreamSynchronize(h->stream) == cudaSuccess ? AMR_OK : AMR_ERR_CUDA;
+}
+
+int rdt_read_state(rdt_handle* h, double* u, double* v, int on_device) {
+  if (!h || !u || !v) return AMR_ERR_INVALID_ARG;
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (cudaMemcpyAsync(u, h->d_u.p, h->n * 8, k, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(v, h->d_v.p, h->n * 8, k, h->stream) != cudaSuccess)
+    return AMR_ERR_CUDA;
+  return cudaStreamSynchronize(h->stream) == cudaSuccess ? AMR_OK : AMR_ERR_CUDA;
+}
+
+// nsteps IMEX steps: composite Laplacians, right-hand sides, the two tree solves, finish
+int rdt_step(rdt_handle* h, int nsteps, int* cycles) {
+  if (!h || nsteps < 0) return AMR_ERR_INVALID_ARG;
+  Tree& tu = *h->tu;
+  Tree& tv = *h->tv;
+  RdtArgs A{};
+  A.Du = h->cfg.Du;
+  A.Dv = h->cfg.Dv;
+  A.F = h->cfg.F;
+  A.k = h->cfg.k;
+  A.dt = h->cfg.dt;
+  A.lam_u = tu.cfg.lambda;
+  A.lam_v = tv.cfg.lambda;
+  A.u = h->d_u.as<double>();
+  A.v = h->d_v.as<double>();
+  A.lu = h->d_lu.as<double>();
+  A.lv = h->d_lv.as<double>();
+  A.bu = h->d_bu.as<double>();
+  A.bv = h->d_bv.as<double>();
+  A.Fn = h->d_Fn.as<double>();
+  A.xu = h->d_xu.as<double>();
+  A.xv = h->d_xv.as<double>();
+  A.n = h->n;
+  const unsigned nb = (unsigned)((h->n + 255) / 256);
+  for (int s = 0; s < nsteps; ++s) {
+    int rc;
+    if ((rc = tu.lap_leaves(A.u, h->d_lu.as<double>())) || (rc = tv.lap_leaves(A.v, h->d_lv.as<double>())))
+      return rc;
+    rdt_rhs_kernel<<<nb, 256, 0, h->stream>>>(A);
+    ++tu.launches;
+    int cu, cv;
+    double rm, bm, rm2, bm2;
+    if ((rc = tu.solve_dev(A.bu, A.xu, 0, &cu, &rm, &bm)) || (rc = tv.solve_dev(A.bv, A.xv, 0, &cv, &rm2, &bm2)))
+      return rc;
+    if (cycles) {
+      cycles[2 * s] = cu;
+      cycles[2 * s + 1] = cv;
+    }
+    if (!(rm <= tu.cfg.rtol * bm) || !(rm2 <= tv.cfg.rtol * bm2))
+      return h->fail(MG_ERR_NOT_CONVERGED, "a tree solve did not reach rtol within max_cycles");
+    if ((rc = tu.lap_leaves(A.xu, h->d_lu.as<double>())) || (rc = tv.lap_leaves(A.xv, h->d_lv.as<double>())))
+      return rc;
+    rdt_finish_kernel<<<nb, 256, 0, h->stream>>>(A);
+    ++tu.launches;
+    if (cudaGetLastError() != cudaSuccess) return h->fail(AMR_ERR_CUDA, "launch");
+  }
+  return cudaStreamSynchronize(h->stream) == cudaSuccess ? AMR_OK : AMR_ERR_CUDA;
+}
+
+int rdt_kernel_launches(const rdt_handle* h, long long* n) {
+  if (!h || !n) return AMR_ERR_INVALID_ARG;
+  *n = h->tu->launches + h->tv->launches;
   return AMR_OK;
 }
 

@@ -205,3 +205,74 @@ def schnakenberg_initial(n, ndim=2, L=1.0, a=0.1305, b=0.7695):
     v = np.full(u.shape, b / (a + b) ** 2)
     # storage order: x fastest, so the flat index is i + n*(j + n*k)
     return np.ascontiguousarray(u.transpose(tuple(range(ndim))[::-1])), v
+
+
+def quadtree_from_levels(want):
+    """Leaves (level, (bx, by)) of a periodic 2D block quadtree with three levels from a wanted
+    level per finest-level block position, want[by, bx] in {1, 2, 3} (shape (4 nb, 4 nb)).
+    The wish is raised until the tree exists and is 2:1 balanced across faces and corners:
+    every neighbour of a level-L position reaches L - 1, and a refined block refines all its
+    children.  Returns (level int32 [n], coords int32 [n, 2])."""
+    lv = np.array(want, dtype=np.int32)
+    ny, nx = lv.shape
+    while True:
+        old = lv.copy()
+        nbmax = lv.copy()
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                nbmax = np.maximum(nbmax, np.roll(np.roll(lv, dy, 0), dx, 1))
+        lv = np.maximum(lv, nbmax - 1)
+        g2 = lv.reshape(ny // 2, 2, nx // 2, 2).max(axis=(1, 3))  # level-2 blocks with a level-3 position
+        lv = np.where(np.repeat(np.repeat(g2 == 3, 2, 0), 2, 1), 3, lv)
+        g1 = lv.reshape(ny // 4, 4, nx // 4, 4).max(axis=(1, 3))  # level-1 blocks with a refined position
+        lv = np.where(np.repeat(np.repeat(g1 >= 2, 4, 0), 4, 1), np.maximum(lv, 2), lv)
+        if np.array_equal(lv, old):
+            break
+    leaves = []
+    for by in range(ny // 4):
+        for bx in range(nx // 4):
+            if lv[4 * by, 4 * bx] == 1:
+                leaves.append((1, bx, by))
+                continue
+            for q in range(4):
+                x2, y2 = 2 * bx + (q & 1), 2 * by + (q >> 1)
+                if lv[2 * y2, 2 * x2] == 2:
+                    leaves.append((2, x2, y2))
+                else:
+                    leaves += [(3, 2 * x2 + (r & 1), 2 * y2 + (r >> 1)) for r in range(4)]
+    arr = np.array(leaves, dtype=np.int32)
+    return arr[:, 0].copy(), arr[:, 1:].copy()
+
+
+GRAY_SCOTT_PAPER = dict(Du=2e-5, Dv=1e-5, F=0.046, k=0.063, dt=0.5, L=2.0)  # Sec. 2.5.2
+
+
+def gray_scott_tree(nb=16, L=2.0, centres=((0.5, 0.5), (0.55, 0.6)), radii=(0.5, 0.3)):
+    """The three-level mesh of Sec. 2.5.2's Gray-Scott run on [0, L]^2 (nb^2 base blocks):
+    level 3 within radii[1] of a perturbation centre, level 2 within radii[0], then
+    balanced.  (The paper adapts the mesh as the pattern grows; this mesh is fixed.)"""
+    n = 4 * nb
+    h = L / n
+    c = (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(c, c, indexing="xy")
+    d = np.min([np.hypot(X - cx, Y - cy) for cx, cy in centres], axis=0)
+    want = np.where(d < radii[1], 3, np.where(d < radii[0], 2, 1))
+    return quadtree_from_levels(want)
+
+
+def gray_scott_gaussians(X, Y, centres=((0.5, 0.5), (0.55, 0.6))):
+    """Sec. 2.5.2: u = 1, v = 0 with two perturbations (1/2) exp(-25 |r - r_i|^2) subtracted
+    from u and added to v."""
+    p = sum(0.5 * np.exp(-25.0 * ((X - cx) ** 2 + (Y - cy) ** 2)) for cx, cy in centres)
+    return 1.0 - p, p
+
+
+def leaf_cell_centres(level, coords, nb, B, L):
+    """Cell centres (X, Y), each [leaf][B*B] x fastest, of quadtree leaves on [0, L]^2."""
+    level = np.asarray(level)
+    coords = np.asarray(coords)
+    h = L / (nb * B) / 2.0 ** (level - 1)
+    i = np.arange(B)
+    X = (coords[:, :1] * B + i[None, :] + 0.5) * h[:, None]
+    Y = (coords[:, 1:2] * B + i[None, :] + 0.5) * h[:, None]
+    return np.tile(X, (1, B)), np.repeat(Y, B, axis=1)

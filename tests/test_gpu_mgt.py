@@ -94,3 +94,36 @@ def test_invalid_trees_are_rejected():
     with pytest.raises(amrvac.AmrError) as ei:
         amrvac.TreeMgSolver(np.array(lev), np.array(crd), 2, B, 1.0, 1.0)
     assert ei.value.code == -1
+
+
+# ------------------------------------------------------------ Gray-Scott on the tree --
+def test_gray_scott_steps_match_oracle():
+    from paper_2004_03275_gb300 import inputs
+    nb, B, L = 4, 8, 2.0
+    lev, crd = inputs.gray_scott_tree(nb=nb, L=L, radii=(0.5, 0.25))
+    assert set(np.unique(lev)) == {1, 2, 3}
+    X, Y = inputs.leaf_cell_centres(lev, crd, nb, B, L)
+    u, v = inputs.gray_scott_gaussians(X, Y)
+    p = dict(Du=2e-5, Dv=1e-5, F=0.046, k=0.063, dt=0.5)
+    s = amrvac.TreeRdSolver(lev, crd, nb, B, L, **p)
+    s.set_state(u.ravel(), v.ravel())
+    cyc = s.step(3)
+    ug, vg = s.read_state()
+    uo, vo = u.ravel(), v.ravel()
+    co = []
+    for _ in range(3):
+        uo, vo, c = O.amg_rd_step(lev, crd, uo, vo, nb, B, L, **p)
+        co.append(c)
+    assert np.all(np.abs(cyc - np.array(co)) <= 1), (cyc, co)
+    assert np.max(np.abs(ug - uo)) <= 1e-11 and np.max(np.abs(vg - vo)) <= 1e-11
+
+
+def test_gray_scott_tree_keeps_the_homogeneous_state():
+    from paper_2004_03275_gb300 import inputs
+    lev, crd = inputs.gray_scott_tree(nb=4, L=2.0, radii=(0.5, 0.25))
+    n = len(lev) * 64
+    s = amrvac.TreeRdSolver(lev, crd, 4, 8, 2.0, Du=2e-5, Dv=1e-5, F=0.046, k=0.063, dt=0.5)
+    s.set_state(np.ones(n), np.zeros(n))
+    cyc = s.step(2)
+    u, v = s.read_state()
+    assert np.array_equal(u, np.ones(n)) and np.array_equal(v, np.zeros(n)) and np.all(cyc == 0)

@@ -175,3 +175,13 @@ def test_rd_step_on_a_tree_keeps_the_homogeneous_state_and_conserves():
     t0, t1 = np.sum(area * (u + v)), np.sum(area * (u1 + v1))
     assert abs(t1 - t0) <= 1e-12 * t0, (t0, t1)
     assert np.max(np.abs(u1 - u)) > 1e-4  # the step did something
+
+
+def test_paper_gray_scott_tree_is_a_balanced_three_level_cover():
+    from paper_2004_03275_gb300 import inputs
+    from treeutil import covers_domain
+    lev, crd = inputs.gray_scott_tree()
+    assert set(np.unique(lev)) == {1, 2, 3}
+    leaves = [(int(l), (int(c[0]), int(c[1]), 0)) for l, c in zip(lev, crd)]
+    assert covers_domain(leaves, 2, [16, 16, 1], 3)
+    assert is_balanced(leaves, 2, [16, 16, 1], 3, (True, True, True))
