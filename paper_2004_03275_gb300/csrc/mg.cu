@@ -130,27 +130,51 @@ __device__ __forceinline__ int nbr_or_self(int i, int ci, int n, bool neu) {
 }
 
 // sum of the neighbours, ordered x-, x+, y-, y+, z-, z+: all 2 ndim on a periodic grid
-// (images across the boundary), only the in-domain ones on a Neumann grid; *miss gets the
-// number left out
-template <typename T>
-__device__ __forceinline__ T nbsum(const T* x, const int* c, int n, int nd, bool neu, int* miss) {
-  T s = T(0);
-  int m = 0;
-  for (int d = 0; d < nd; ++d) {
-#pragma unroll
-    for (int side = -1; side <= 1; side += 2) {
-      int q[3] = {c[0], c[1], c[2]};
-      int t = c[d] + side;
-      if (neu && (t < 0 || t >= n)) {
-        ++m;
-        continue;
-      }
-      q[d] = wrapi(t, n);
+// (images across the boundary), only the in-domain ones on a Neumann grid (NEU); *miss gets
+// the number left out
+template <bool NEU, typename T>
+__device__ __forceinline__ T nbsum(const T* x, const int* c, int n, int nd, int* miss) {
+  if constexpr (!NEU) {
+    *miss = 0;
+    int q[3] = {c[0], c[1], c[2]};
+    q[0] = wrapi(c[0] - 1, n);
+    T s = x[lin(q, n)];
+    q[0] = wrapi(c[0] + 1, n);
+    s = s + x[lin(q, n)];
+    q[0] = c[0];
+    if (nd > 1) {
+      q[1] = wrapi(c[1] - 1, n);
+      s = s + x[lin(q, n)];
+      q[1] = wrapi(c[1] + 1, n);
+      s = s + x[lin(q, n)];
+      q[1] = c[1];
+    }
+    if (nd > 2) {
+      q[2] = wrapi(c[2] - 1, n);
+      s = s + x[lin(q, n)];
+      q[2] = wrapi(c[2] + 1, n);
       s = s + x[lin(q, n)];
     }
+    return s;
+  } else {
+    T s = T(0);
+    int m = 0;
+    for (int d = 0; d < nd; ++d) {
+#pragma unroll
+      for (int side = -1; side <= 1; side += 2) {
+        int q[3] = {c[0], c[1], c[2]};
+        int t = c[d] + side;
+        if (t < 0 || t >= n) {
+          ++m;
+          continue;
+        }
+        q[d] = t;
+        s = s + x[lin(q, n)];
+      }
+    }
+    *miss = m;
+    return s;
   }
-  *miss = m;
-  return s;
 }
 
 template <typename real>
@@ -237,7 +261,7 @@ __global__ void bnorm_finish_kernel(MgState S, int ninst) {
 
 // float64 residual R = B - (lambda X - lap X) on level 0 -> rhs of the correction,
 // correction zeroed, per-instance max |R|
-template <typename real>
+template <typename real, bool NEU>
 __global__ void residual64_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
   Chunk C = ch[blockIdx.x];
   if (!S.active[C.inst]) return;
@@ -253,8 +277,8 @@ __global__ void residual64_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
     // r = B + ih2 (nbsum - count x) - lambda x in three fused multiply-adds: the float64
     // unit is GB300's scarcest pipe, so the residual uses as few float64 operations as it can
     int miss;
-    const double s = nbsum(X, c, n, S.ndim, S.neu != 0, &miss);
-    const double mcount = (double)(miss - 2 * S.ndim);
+    const double s = nbsum<NEU>(X, c, n, S.ndim, &miss);
+    const double mcount = NEU ? (double)(miss - 2 * S.ndim) : (S.ndim == 3 ? -6.0 : -4.0);
     double r = fma(fma(mcount, x, s), I.ih2[0], S.B[I.off0 + t]);
     r = fma(-I.lam, x, r);
     L.b[I.off[0] + t] = narrow<real>(r);
@@ -299,7 +323,7 @@ __global__ void check_kernel(MgState S, int ninst, cudaGraphConditionalHandle hc
 }
 
 // red-black Gauss-Seidel sweep of one colour: x = (b + nbsum * ih2) / (lambda + count ih2)
-template <typename real>
+template <typename real, bool NEU>
 __global__ void smooth_kernel(MgState S, Lvl<real> L, const Chunk* ch, int colour) {
   Chunk C = ch[blockIdx.x];
   if (!S.active[C.inst] || threadIdx.x >= C.count) return;
@@ -319,8 +343,8 @@ __global__ void smooth_kernel(MgState S, Lvl<real> L, const Chunk* ch, int colou
   real ih2 = ih2_of<real>(I, l);
   long long q = lin(c, n);
   int miss;
-  const real sn = nbsum(x, c, n, nd, S.neu != 0, &miss);
-  x[q] = (b[q] + sn * ih2) * idiag_of<real>(I, l, miss);
+  const real sn = nbsum<NEU>(x, c, n, nd, &miss);
+  x[q] = (b[q] + sn * ih2) * idiag_of<real>(I, l, NEU ? miss : 0);
 }
 
 // One full red-black sweep of a 2D level, one warp per strip of kStripW columns and
@@ -456,7 +480,7 @@ __global__ void __launch_bounds__(128) copy2d_kernel(MgState S, const real* __re
 }
 
 // 2D prolongation, one thread per coarse cell writing its four fine children
-template <typename real>
+template <typename real, bool NEU>
 __global__ void prolong2d_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
   Chunk C = ch[blockIdx.x];
   if (!S.active[C.inst] || threadIdx.x >= C.count) return;
@@ -466,7 +490,7 @@ __global__ void prolong2d_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
   unsigned t = (unsigned)(C.start + threadIdx.x);  // coarse cell
   int cj = (int)(t / (unsigned)nc), ci = (int)(t - (unsigned)cj * (unsigned)nc);
   const real* ec = L.x + I.off[l + 1];
-  const bool neu = S.neu != 0;
+  constexpr bool neu = NEU;
   real v[3][3];
 #pragma unroll
   for (int dj = -1; dj <= 1; ++dj)
@@ -491,7 +515,7 @@ __global__ void prolong2d_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
 }
 
 // residual of level l restricted to level l+1 (mean of the 2^ndim children), x_{l+1} = 0
-template <typename real>
+template <typename real, bool NEU>
 __global__ void resrestrict_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
   Chunk C = ch[blockIdx.x];
   if (!S.active[C.inst] || threadIdx.x >= C.count) return;
@@ -510,8 +534,8 @@ __global__ void resrestrict_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
     long long q = lin(f, nf);
     real xv = x[q];
     int miss;
-    const real sn = nbsum(x, f, nf, nd, S.neu != 0, &miss);
-    real lap = (sn - real(2 * nd - miss) * xv) * ih2;
+    const real sn = nbsum<NEU>(x, f, nf, nd, &miss);
+    real lap = (sn - real(2 * nd - (NEU ? miss : 0)) * xv) * ih2;
     sum = sum + (b[q] - (lam * xv - lap));
   }
   L.b[I.off[l + 1] + t] = sum * (real(1) / real(1 << nd));
@@ -519,7 +543,7 @@ __global__ void resrestrict_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
 }
 
 // cell-centred (bi/tri)linear prolongation of level l+1 added to level l
-template <typename real>
+template <typename real, bool NEU>
 __global__ void prolong_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
   Chunk C = ch[blockIdx.x];
   if (!S.active[C.inst] || threadIdx.x >= C.count) return;
@@ -537,7 +561,7 @@ __global__ void prolong_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
   for (int z = 0; z < cz; ++z)
     for (int y = 0; y < cy; ++y)
       for (int xx = 0; xx < 2; ++xx) {
-        const bool neu = S.neu != 0;
+        constexpr bool neu = NEU;
         int q[3] = {nbr_or_self(P[0] + xx * sg[0], P[0], nc, neu), nd > 1 ? nbr_or_self(P[1] + y * sg[1], P[1], nc, neu) : 0,
                     nd > 2 ? nbr_or_self(P[2] + z * sg[2], P[2], nc, neu) : 0};
         real w = xx ? real(0.25) : real(0.75);
@@ -630,7 +654,7 @@ __device__ __forceinline__ void reaction(const RdArgs& A, double u, double v, do
 __device__ __forceinline__ double rd_lap(const RdArgs& A, const double* x, const int* c, int n, long long t,
                                          double ih2) {
   int miss;
-  double s = nbsum(x, c, n, A.ndim, A.neu != 0, &miss);
+  double s = A.neu ? nbsum<true>(x, c, n, A.ndim, &miss) : nbsum<false>(x, c, n, A.ndim, &miss);
   return (s - (double)(2 * A.ndim - miss) * x[t]) * ih2;
 }
 
@@ -1124,14 +1148,20 @@ struct Mg {
       if (ch_half[l].empty()) return;
       for (int s = 0; s < sweeps; ++s)
         for (int colour = 0; colour < 2; ++colour) {
-          smooth_kernel<real><<<(unsigned)ch_half[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_half[l], colour);
+          if (neu)
+            smooth_kernel<real, true><<<(unsigned)ch_half[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_half[l], colour);
+          else
+            smooth_kernel<real, false><<<(unsigned)ch_half[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_half[l], colour);
           ++launches;
         }
     };
     for (int l = 0; l + 1 < maxdepth; ++l) {
       smooth(l, nu1);
       if (!ch_coarse[l].empty()) {
-        resrestrict_kernel<real><<<(unsigned)ch_coarse[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
+        if (neu)
+          resrestrict_kernel<real, true><<<(unsigned)ch_coarse[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
+        else
+          resrestrict_kernel<real, false><<<(unsigned)ch_coarse[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
         ++launches;
       }
     }
@@ -1140,10 +1170,16 @@ struct Mg {
     ++launches;
     for (int l = maxdepth - 2; l >= 0; --l) {
       if (nd == 2 && !ch_coarse[l].empty()) {
-        prolong2d_kernel<real><<<(unsigned)ch_coarse[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
+        if (neu)
+          prolong2d_kernel<real, true><<<(unsigned)ch_coarse[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
+        else
+          prolong2d_kernel<real, false><<<(unsigned)ch_coarse[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
         ++launches;
       } else if (nd != 2 && !ch_fine[l].empty()) {
-        prolong_kernel<real><<<(unsigned)ch_fine[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_fine[l]);
+        if (neu)
+          prolong_kernel<real, true><<<(unsigned)ch_fine[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_fine[l]);
+        else
+          prolong_kernel<real, false><<<(unsigned)ch_fine[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_fine[l]);
         ++launches;
       }
       smooth(l, nu2);
@@ -1190,7 +1226,10 @@ struct Mg {
       return rc;
     bnorm_kernel<<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, d_ch0.as<Chunk>());
     bnorm_finish_kernel<<<(ninst + 255) / 256, 256, 0, stream>>>(S, ninst);
-    residual64_kernel<real><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+    if (neu)
+      residual64_kernel<real, true><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+    else
+      residual64_kernel<real, false><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
     check_kernel<<<1, 256, 0, stream>>>(S, ninst, hc, 1);
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
@@ -1214,7 +1253,10 @@ struct Mg {
     stream = cstream;
     long long before = launches;
     int rc = enqueue_vcycle<real>();
-    residual64_kernel<real><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+    if (neu)
+      residual64_kernel<real, true><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+    else
+      residual64_kernel<real, false><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
     check_kernel<<<1, 256, 0, stream>>>(S, ninst, hc, 1);
     solve_loop_kernels = launches - before + 2;
     launches = before;
@@ -1270,7 +1312,10 @@ struct Mg {
     bnorm_finish_kernel<<<(ninst + 255) / 256, 256, 0, stream>>>(S, ninst);
     launches += 2;
     while (true) {
-      residual64_kernel<real><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+      if (neu)
+      residual64_kernel<real, true><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+    else
+      residual64_kernel<real, false><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
       check_kernel<<<1, 256, 0, stream>>>(S, ninst, 0, 0);
       launches += 2;
       if ((rc = cuda(cudaMemcpyAsync(h_any, d_any.p, 4, cudaMemcpyDeviceToHost, stream), "copy"))) return rc;
