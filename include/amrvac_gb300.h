@@ -110,12 +110,15 @@ int amr_set_leaves(amr_handle* h, long long n, const int* level, const int* coor
  * (n_values = leaves * (ndim+2) * block_nx^ndim).  primitive = 1: the values
  * are (rho, v_1..v_ndim, p) and are converted on the device (Sec. 1.1,
  * phys_to_conserved); 0: conserved (rho, m_1..m_ndim, E).  Recomputes the
- * CFL step.  Synchronous. */
+ * CFL step.  Synchronous.  A host array in page-locked (pinned) memory is read
+ * in place by the conversion kernel (zero copy); pageable host memory is staged
+ * through a device buffer. */
 int amr_set_state(amr_handle* h, const double* W, long long n_values, int on_device, int primitive);
 
 /* Copies the conserved state to a float64 array [leaf][var][cell] (converted
  * on the device for the FP32 path).  cap_values = capacity in doubles.
- * Synchronous. */
+ * Synchronous.  A pinned host array is written in place by the conversion
+ * kernel; pageable host memory is staged through a device buffer. */
 int amr_read_state(amr_handle* h, double* U, long long cap_values, int on_device);
 
 int amr_set_time(amr_handle* h, double t);

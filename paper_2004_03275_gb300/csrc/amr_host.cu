@@ -687,15 +687,31 @@ int amr_set_leaves(amr_handle* h, long long n, const int* level, const int* coor
   return AMR_OK;
 }
 
+// Device address of page-locked (pinned) host memory, which kernels read and write in place
+// (zero copy: one pass over the host buffer instead of a copy engine pass plus a pass over a
+// staging buffer); nullptr for pageable memory.
+static const void* pinned_device_ptr(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int amr_set_state(amr_handle* h, const double* W, long long n_values, int on_device, int primitive) {
   if (!h || !W) return AMR_ERR_INVALID_ARG;
   long long nl = (long long)h->tree.leaves.size();
   long long need = nl * h->nv * h->nc;
   if (n_values != need) return h->fail(AMR_ERR_INVALID_ARG, "n_values does not match leaves*(ndim+2)*cells");
+  // the conversion kernel reads two doubles per 16-byte load: an array that is not 16-byte
+  // aligned, or pageable host memory, goes through the (aligned) staging buffer
   const double* src = W;
-  if (!on_device) {
+  const void* pin = on_device ? nullptr : pinned_device_ptr(W);
+  if (pin) src = static_cast<const double*>(pin);
+  if ((!on_device && !pin) || (reinterpret_cast<uintptr_t>(src) & 15)) {
     CK(h->stagebuf.ensure(need * sizeof(double)));
-    CK(cudaMemcpyAsync(h->stagebuf.p, W, need * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->stagebuf.p, W, need * sizeof(double), cudaMemcpyDefault, h->stream));
     src = h->stagebuf.as<double>();
   }
   int rc = with_type(h, [&]<typename real, int ND>() -> int {
@@ -717,10 +733,15 @@ int amr_read_state(amr_handle* h, double* U, long long cap_values, int on_device
   long long nl = (long long)h->tree.leaves.size();
   long long need = nl * h->nv * h->nc;
   if (cap_values < need) return h->fail(AMR_ERR_INVALID_ARG, "output buffer too small");
+  // pageable host memory is written through the staging buffer
   double* dst = U;
-  if (!on_device) {
+  bool staged = false;
+  const void* pin = on_device ? nullptr : pinned_device_ptr(U);
+  if (pin) dst = static_cast<double*>(const_cast<void*>(pin));
+  if (!on_device && !pin) {
     CK(h->stagebuf.ensure(need * sizeof(double)));
     dst = h->stagebuf.as<double>();
+    staged = true;
   }
   int rc = with_type(h, [&]<typename real, int ND>() -> int {
     cudaError_t e = EulerOps<real, ND>::read_state(h->U0.as<real>(), dst, need, h->stream);
@@ -729,7 +750,7 @@ int amr_read_state(amr_handle* h, double* U, long long cap_values, int on_device
     return AMR_OK;
   });
   if (rc) return rc;
-  if (!on_device) CK(cudaMemcpyAsync(U, dst, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (staged) CK(cudaMemcpyAsync(U, dst, need * sizeof(double), cudaMemcpyDefault, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return AMR_OK;
 }

@@ -234,7 +234,7 @@ cudaError_t EulerOps<real, ND>::reduce(int B, const real* U, const int* level, c
 #define CALL(BB)                                                                                   \
   ([&]() {                                                                                         \
     constexpr int NC = Tile<ND, BB>::NC;                                                           \
-    constexpr int LPB = NC >= 256 ? 1 : 256 / NC;                                                  \
+    constexpr int LPB = ReduceShape<NC>::LPB;                                                      \
     reduce_kernel<real, ND, BB><<<(nleaves + LPB - 1) / LPB, 256, 0, s>>>(U, level, G, ctl, partials, \
                                                                          gpart, gcount, nleaves, advance); \
     return cudaGetLastError();                                                                     \
@@ -306,11 +306,12 @@ cudaError_t EulerOps<real, ND>::regrid(int B, const real* Uold, real* Unew, cons
 template <typename real, int ND>
 cudaError_t EulerOps<real, ND>::set_state(int B, const double* W, real* U, long long nleaves, int primitive,
                                           double gamma, cudaStream_t s) {
-  int nc = 1;
-  for (int d = 0; d < ND; ++d) nc *= B;
-  long long n = nleaves * nc;
+  int lognc = 0;
+  while ((1 << lognc) < B) ++lognc;  // block sizes are powers of two
+  lognc *= ND;
+  long long n = nleaves << lognc;
   if (n == 0) return cudaSuccess;
-  set_state_kernel<real, ND><<<detail::blocks_for(n, 256), 256, 0, s>>>(W, U, n, nc, primitive, gamma);
+  set_state_kernel<real, ND><<<detail::blocks_for(n / 2, 256), 256, 0, s>>>(W, U, n, lognc, primitive, gamma);
   return cudaGetLastError();
 }
 

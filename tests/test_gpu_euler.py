@@ -267,3 +267,37 @@ def test_fp32_totals_and_dt():
     g.t = s.t
     dt_next = s.step()
     assert dt_next == pytest.approx(g.dt(), rel=1e-5)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_state_io_through_every_buffer_kind(precision):
+    """Pageable host arrays (staged), pinned host arrays (read and written in place by the
+    conversion kernels), device arrays, and arrays that are not 16-byte aligned (staged) give
+    the same state."""
+    torch = pytest.importorskip("torch")
+    nb = 4
+    kw = dict(ndim=2, block_nx=16, base=[nb, nb], gamma=1.4, cfl=0.8, flux="hllc", limiter="vanleer", rk=3,
+              bc="periodic")
+    s = amrvac.AmrSolver(precision=precision, **kw)
+    lev, crd = s.leaves()
+    x, gidx = inputs.cell_centres(lev, crd, 2, 16, [nb, nb, 1], [0, 0, 0], [1, 1, 1])
+    s.set_prim(inputs.kelvin_helmholtz(x, gidx, nb * 16))
+    s.run(2)
+    s.sync()
+    ref = s.read_state()
+    n = ref.size
+    host = torch.from_numpy(ref.ravel().copy())
+    pinned = host.pin_memory()
+    pinned_off = torch.empty(n + 1, dtype=torch.float64).pin_memory()
+    pinned_off[1:] = host
+    dev = host.cuda()
+    dev_off = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    dev_off[1:] = dev
+    for src in (host.numpy(), pinned, pinned_off[1:], dev, dev_off[1:]):
+        s.set_state(src, primitive=False)
+        assert np.array_equal(s.read_state(), ref)
+    for out in (torch.empty(n, dtype=torch.float64).pin_memory(), torch.empty(n + 1, dtype=torch.float64).pin_memory()[1:],
+                torch.empty(n, dtype=torch.float64, device="cuda"),
+                torch.empty(n + 1, dtype=torch.float64, device="cuda")[1:]):
+        s.read_state(out.view(ref.shape))
+        assert np.array_equal(out.cpu().numpy(), ref.ravel())
