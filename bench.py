@@ -406,7 +406,7 @@ def bench_gray_scott_tree(torch, amrvac, stream, steps=20):
            "leaves_per_level": [int(c) for c in np.bincount(lev)[1:]], "cells": int(len(lev) * B * B),
            "ms_per_step": round(el * 1e3, 3), "vcycles_per_solve": round(float(np.mean(cyc)), 2),
            "kernels_per_step": round((s.kernel_launches() - n0) / steps, 1), "steps": steps,
-           "timing": "host wall clock around synchronous rdt_step calls (one host poll per V-cycle)"}
+           "timing": "host wall clock around synchronous rdt_step calls (each solve one graph with device-side loops)"}
     s.close()
     return out
 

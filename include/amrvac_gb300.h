@@ -302,7 +302,8 @@ int rd_kernel_launches(const rd_handle* h, long long* n);
  * the face by a linear slope), a refined neighbour (4/3) m - (1/3) f0 (m: mean of
  * the two finer cells on the face; flux matching, conservative).  Full
  * approximation scheme over the tree levels with red-black Gauss-Seidel (nu1,
- * nu2), the base level solved by the uniform multigrid above to base_rtol.
+ * nu2), the base level solved in correction form (A e = b - A x from e = 0) by the
+ * uniform multigrid above until its residual is below base_rtol of max|b - A x|.
  * Leaves: level[k] >= 1 and block coordinates (coords[2k], coords[2k+1]) at
  * that level, any order; leaf data [leaf][B*B] in that order, x fastest.
  * ------------------------------------------------------------------------ */
@@ -313,7 +314,7 @@ typedef struct {
   double L, lambda;     /* lambda >= 0 */
   int nu1, nu2, max_cycles;
   double rtol;          /* stop when max|b - A x| over leaf cells <= rtol max|b| */
-  double base_rtol;     /* base-level solves */
+  double base_rtol;     /* base-level solves: residual reduction factor (1e-3) */
   int coarse_max;       /* the base multigrid's coarsest side */
   void* stream;         /* NULL: the handle creates its own */
 } mgt_config;

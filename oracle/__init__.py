@@ -426,7 +426,7 @@ def cnn_layer_slices(ndim):
 
 
 # ------------------------------------------------------------------ AMR multigrid --
-def amg_config(nb, B, L, lam, nu1=2, nu2=2, max_cycles=50, rtol=1e-10, base_rtol=1e-12, coarse_max=8):
+def amg_config(nb, B, L, lam, nu1=2, nu2=2, max_cycles=50, rtol=1e-10, base_rtol=1e-3, coarse_max=8):
     return OrcAmgConfig(nb, nb, B, L, lam, nu1, nu2, max_cycles, rtol, base_rtol, coarse_max)
 
 

@@ -29,8 +29,11 @@
 //    children of refined blocks get the cell-centred bilinear prolongation (9/16, 3/16, 3/16,
 //    1/16) of e = x - x_before at level l-1 (a level-(l-1) cell that does not exist reads the
 //    parent cell's e); nu2 sweeps.  Level 1 (the base grid, uniform and periodic) is solved
-//    by the uniform multigrid of mg.cpp to base_rtol.  Gauss-Seidel colours by (I + J) parity
-//    of global level-l cell indices; a fine cell next to a coarser block reads its own old
+//    in correction form: A e = b - A x from e = 0 by the uniform multigrid of mg.cpp until
+//    the correction's residual is below base_rtol of max|b - A x| (a reduction factor, so
+//    every cycle reduces the base error; a tolerance relative to b would stall the
+//    iteration at that level), then x += e.  Gauss-Seidel colours by (I + J) parity of
+//    global level-l cell indices; a fine cell next to a coarser block reads its own old
 //    value through f0.
 //  * Outer iteration: refined blocks are set to the means of their children (bottom up)
 //    and V-cycles run from the finest level until the composite residual max|b - A x| over
@@ -254,7 +257,8 @@ void residual_level(Tree& T, int l) {
   }
 }
 
-// level 1 is a uniform periodic grid: gather it, solve with the uniform multigrid, scatter
+// level 1 is a uniform periodic grid: gather it, solve A e = b - A x from e = 0 with the
+// uniform multigrid (relative tolerance base_rtol), scatter x + e
 void base_solve(Tree& T, const orc_amg_config* c) {
   const int B = T.B, n = T.nbx * B;
   std::vector<double> x((size_t)n * n), b((size_t)n * n);
@@ -267,13 +271,20 @@ void base_solve(Tree& T, const orc_amg_config* c) {
         b[g] = blk.b[(size_t)j * B + i];
       }
   }
+  // correction form: A e = b - A x from e = 0, to base_rtol of the initial base residual
+  std::vector<double> r((size_t)n * n), e((size_t)n * n, 0.0);
+  orc_mg_apply(2, n, c->L, c->lambda, ORC_MG_PERIODIC, x.data(), r.data());
+  for (size_t i = 0; i < r.size(); ++i) r[i] = b[i] - r[i];
   orc_mg_config mc{2, n, c->L, c->lambda, 2, 2, 200, c->base_rtol, c->coarse_max, ORC_MG_PERIODIC};
   double rr;
-  orc_mg_solve(&mc, b.data(), x.data(), &rr);
+  orc_mg_solve(&mc, r.data(), e.data(), &rr);
   for (int k : T.bylev[1]) {
     Blk& blk = T.blk[k];
     for (int j = 0; j < B; ++j)
-      for (int i = 0; i < B; ++i) blk.x[(size_t)j * B + i] = x[(size_t)(blk.by * B + j) * n + blk.bx * B + i];
+      for (int i = 0; i < B; ++i) {
+        const size_t g = (size_t)(blk.by * B + j) * n + blk.bx * B + i;
+        blk.x[(size_t)j * B + i] = x[g] + e[g];
+      }
   }
 }
 

@@ -123,7 +123,7 @@ typedef struct {
   double L, lambda;
   int nu1, nu2, max_cycles;
   double rtol;        /* max|b - A x| over leaf cells <= rtol max|b| */
-  double base_rtol;   /* level-1 solve by the uniform multigrid */
+  double base_rtol;   /* level-1 correction solve by the uniform multigrid: residual reduction */
   int coarse_max;
 } orc_amg_config;
 /* x: guess in, solution out.  fixed_cycles > 0 runs exactly that many V-cycles.  Returns

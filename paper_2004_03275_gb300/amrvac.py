@@ -528,7 +528,7 @@ class TreeMgSolver:
     level[k] >= 1, coords[k] = (bx, by) block coordinates at that level; leaf data
     [leaf][B*B] in the same order."""
 
-    def __init__(self, level, coords, nb, B, L, lam, nu1=2, nu2=2, max_cycles=50, rtol=1e-10, base_rtol=1e-12,
+    def __init__(self, level, coords, nb, B, L, lam, nu1=2, nu2=2, max_cycles=50, rtol=1e-10, base_rtol=1e-3,
                  coarse_max=8, stream=None):
         self.lib = load()
         self.level = np.ascontiguousarray(level, dtype=np.int32)
@@ -587,7 +587,7 @@ class TreeRdSolver:
     """Owns one rdt_handle: Gray-Scott IMEX steps on the leaves of a fixed 2D block quadtree."""
 
     def __init__(self, level, coords, nb, B, L, Du, Dv, F, k, dt, nu1=2, nu2=2, max_cycles=50, rtol=1e-10,
-                 base_rtol=1e-12, coarse_max=8, stream=None):
+                 base_rtol=1e-3, coarse_max=8, stream=None):
         self.lib = load()
         self.level = np.ascontiguousarray(level, dtype=np.int32)
         self.coords = np.ascontiguousarray(coords, dtype=np.int32).reshape(-1, 2)

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "../../include/amrvac_gb300.h"
+#include "mg_internal.h"
 
 namespace mggpu {
 
@@ -1411,6 +1412,26 @@ int mg_num_unknowns(const mg_handle* h, long long* n) {
   *n = h->mg.n0;
   return AMR_OK;
 }
+
+}  // extern "C"
+
+int mg_capture_solve(mg_handle* h, const double* b, double* x, cudaStream_t s) {
+  Mg& M = h->mg;
+  cudaStream_t saved = M.stream;
+  M.stream = s;
+  int rc = M.cuda(cudaMemcpyAsync(M.d_B.p, b, M.n0 * 8, cudaMemcpyDeviceToDevice, s), "copy b");
+  if (!rc) rc = M.cuda(cudaMemcpyAsync(M.d_X.p, x, M.n0 * 8, cudaMemcpyDeviceToDevice, s), "copy x");
+  if (!rc) rc = M.capture_solve_any();
+  if (!rc) rc = M.cuda(cudaMemcpyAsync(x, M.d_X.p, M.n0 * 8, cudaMemcpyDeviceToDevice, s), "copy x back");
+  M.stream = saved;
+  return rc;
+}
+
+const int* mg_device_cycles(const mg_handle* h) { return h->mg.d_cycles.as<int>(); }
+
+long long mg_loop_kernels(const mg_handle* h) { return h->mg.solve_loop_kernels; }
+
+extern "C" {
 
 int mg_kernel_launches(const mg_handle* h, long long* n) {
   if (!h || !n) return AMR_ERR_INVALID_ARG;

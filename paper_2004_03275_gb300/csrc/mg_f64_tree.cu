@@ -15,7 +15,8 @@
 //    operator, the restriction of x and of the residual (means of 2x2 children), the
 //    composite residual for leaves of the coarser level, b = r + A x there, cell-centred
 //    bilinear prolongation (9/16, 3/16, 3/16, 1/16) of the coarse change, and the base grid
-//    (level 1, uniform) solved by the batched uniform multigrid of mg.cu through its C ABI.
+//    (level 1, uniform) solved in correction form, A e = b - A x from e = 0 to base_rtol of
+//    max|b - A x|, by the batched uniform multigrid of mg.cu.
 //
 // Layout: every block of every level (leaves and refined blocks) owns B*B values of x, b,
 // r, x_before and (leaves) the composite right-hand side, x fastest; a dense table per
@@ -34,6 +35,7 @@
 #include <vector>
 
 #include "../../include/amrvac_gb300.h"
+#include "mg_internal.h"
 
 namespace mgtree {
 
@@ -219,8 +221,9 @@ __global__ void prolong_kernel(TreeDev T, const int* list, const int* bxy, int l
   T.x[q] = T.x[q] + acc;
 }
 
-// level 1 <-> a uniform (nx B) x (ny B) array: dir 0 gathers x and b, dir 1 scatters x
-__global__ void base_copy_kernel(TreeDev T, const int* list, const int* bxy, double* ux, double* ub, int dir) {
+// level 1 <-> a uniform (nx B) x (ny B) array: dir 0 gathers x and b, dir 1 scatters x + e
+__global__ void base_copy_kernel(TreeDev T, const int* list, const int* bxy, double* ux, double* ub, const double* ue,
+                                 int dir) {
   const int k = list[blockIdx.x], B = T.B;
   const int i = threadIdx.x % B, j = threadIdx.x / B;
   const size_t g = (size_t)(bxy[2 * k + 1] * B + j) * (T.nx[1] * B) + bxy[2 * k] * B + i;
@@ -229,8 +232,24 @@ __global__ void base_copy_kernel(TreeDev T, const int* list, const int* bxy, dou
     ux[g] = T.x[q];
     ub[g] = T.b[q];
   } else {
-    T.x[q] = ux[g];
+    T.x[q] = ux[g] + ue[g];
   }
+}
+
+// base level in correction form: r = b - (lambda x - lap x) on the uniform periodic n x n
+// array (neighbours x-, x+, y-, y+), written over b; e = 0
+__global__ void base_residual_kernel(const double* __restrict__ ux, double* __restrict__ ub, double* __restrict__ ue,
+                                     int n, double lam, double ih2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= n) return;
+  const size_t g = (size_t)j * n + i;
+  const double x0 = ux[g];
+  double s = ux[(size_t)j * n + (i == 0 ? n - 1 : i - 1)];
+  s = s + ux[(size_t)j * n + (i == n - 1 ? 0 : i + 1)];
+  s = s + ux[(size_t)(j == 0 ? n - 1 : j - 1) * n + i];
+  s = s + ux[(size_t)(j == n - 1 ? 0 : j + 1) * n + i];
+  ub[g] = ub[g] - (lam * x0 - (s - 4.0 * x0) * ih2);
+  ue[g] = 0.0;
 }
 
 // max |bo - A x| (composite) and max |bo| over the leaves of the list, as bit patterns
@@ -263,6 +282,25 @@ __global__ void leaf_copy_kernel(TreeDev T, const int* leaf_blk, const double* b
   } else {
     xio[p] = T.x[q];
   }
+}
+
+// Convergence test of the device-side solve loop: max|r| and max|b| come as bit patterns in
+// red[0..1].  ctr[0] counts V-cycles and ctr[1] the base level's V-cycles (added from
+// base_cyc after each cycle); res[0..1] keep the last max|r| and max|b|.  The loop goes on
+// while max|r| > rtol max|b| and fewer than max_cycles cycles ran (a NaN residual stops it).
+__global__ void tree_check_kernel(const unsigned long long* red, int* ctr, double* res, const int* base_cyc,
+                                  double rtol, int max_cycles, int first, cudaGraphConditionalHandle hc) {
+  const double rm = __longlong_as_double((long long)red[0]), bm = __longlong_as_double((long long)red[1]);
+  if (first) {
+    ctr[0] = 0;
+    ctr[1] = 0;
+  } else {
+    ctr[0] += 1;
+    ctr[1] += base_cyc[0];
+  }
+  res[0] = rm;
+  res[1] = bm;
+  cudaGraphSetConditional(hc, (rm > rtol * bm && ctr[0] < max_cycles) ? 1u : 0u);
 }
 
 // composite Laplacian (sum of neighbours - 4 x) / h^2 of the leaves of the list, into
@@ -348,13 +386,25 @@ struct Tree {
   std::map<long long, int> at;
   // device
   TreeDev T{};
-  Buf d_x, d_b, d_r, d_xold, d_bo, d_leaf, d_bxy, d_child, d_leafblk, d_slot, d_lists, d_tables, d_red, d_ux, d_ub;
+  Buf d_x, d_b, d_r, d_xold, d_bo, d_leaf, d_bxy, d_child, d_leafblk, d_slot, d_lists, d_tables, d_red, d_ux, d_ub, d_ue;
   std::vector<size_t> off_all, off_par;  // offsets of the level lists inside d_lists
   mg_handle* base = nullptr;
   unsigned long long* h_red = nullptr;
   long long launches = 0, base_launches = 0;
+  // device-side solve loop (one graph per pair of b, x arrays)
+  cudaStream_t cstream = nullptr;
+  cudaGraphExec_t sgraph = nullptr;
+  const double* g_b = nullptr;
+  double* g_x = nullptr;
+  bool capturing = false;
+  long long pre_kernels = 0, body_kernels = 0;
+  Buf d_ctr, d_res, d_bin, d_xin;
+  double* h_res = nullptr;  // pinned: [rm, bm]
 
   ~Tree() {
+    if (sgraph) cudaGraphExecDestroy(sgraph);
+    if (cstream) cudaStreamDestroy(cstream);
+    if (h_res) cudaFreeHost(h_res);
     if (base) mg_destroy(base);
     if (h_red) cudaFreeHost(h_red);
     if (own_stream) cudaStreamDestroy(stream);
@@ -481,7 +531,8 @@ struct Tree {
         (rc = cuda(d_leafblk.alloc(leaf_blk.size() * 4), "alloc")) || (rc = cuda(d_slot.alloc(nblk * 4), "alloc")) ||
         (rc = cuda(d_lists.alloc(lists.size() * 4), "alloc")) || (rc = cuda(d_tables.alloc(tables.size() * 4), "alloc")) ||
         (rc = cuda(d_red.alloc(16), "alloc")) || (rc = cuda(d_ux.alloc(nu * 8), "alloc")) ||
-        (rc = cuda(d_ub.alloc(nu * 8), "alloc")) || (rc = cuda(cudaMallocHost(&h_red, 16), "host alloc")))
+        (rc = cuda(d_ub.alloc(nu * 8), "alloc")) || (rc = cuda(d_ue.alloc(nu * 8), "alloc")) ||
+        (rc = cuda(cudaMallocHost(&h_red, 16), "host alloc")))
       return rc;
     cudaMemcpy(d_leaf.p, isleaf.data(), nblk * 4, cudaMemcpyHostToDevice);
     cudaMemcpy(d_bxy.p, bxy.data(), bxy.size() * 4, cudaMemcpyHostToDevice);
@@ -548,17 +599,29 @@ struct Tree {
 
   int base_solve() {
     const int* bxy = d_bxy.as<int>();
-    base_copy_kernel<<<nall(1), B * B, 0, stream>>>(T, all(1), bxy, d_ux.as<double>(), d_ub.as<double>(), 0);
-    ++launches;
+    double* ux = d_ux.as<double>();
+    double* ub = d_ub.as<double>();
+    double* ue = d_ue.as<double>();
+    const int n = cfg.nbx * B;
+    base_copy_kernel<<<nall(1), B * B, 0, stream>>>(T, all(1), bxy, ux, ub, ue, 0);
+    base_residual_kernel<<<dim3((n + 127) / 128, n), 128, 0, stream>>>(ux, ub, ue, n, cfg.lambda, T.ih2[1]);
+    launches += 2;
+    if (capturing) {  // inside the graph of a device-side solve: the base solve is a nested loop
+      if (int rc = mg_capture_solve(base, ub, ue, stream))
+        return fail(rc, std::string("base multigrid: ") + mg_last_error(base));
+      base_copy_kernel<<<nall(1), B * B, 0, stream>>>(T, all(1), bxy, ux, ub, ue, 1);
+      ++launches;
+      return AMR_OK;
+    }
     int cyc;
     double rr;
-    int rc = mg_solve(base, d_ub.as<double>(), d_ux.as<double>(), 1, &cyc, &rr);
+    int rc = mg_solve(base, ub, ue, 1, &cyc, &rr);
     if (rc) return fail(rc, std::string("base multigrid: ") + mg_last_error(base));
     long long bl = 0;
     mg_kernel_launches(base, &bl);
     launches += bl - base_launches;
     base_launches = bl;
-    base_copy_kernel<<<nall(1), B * B, 0, stream>>>(T, all(1), bxy, d_ux.as<double>(), d_ub.as<double>(), 1);
+    base_copy_kernel<<<nall(1), B * B, 0, stream>>>(T, all(1), bxy, ux, ub, ue, 1);
     ++launches;
     return AMR_OK;
   }
@@ -595,6 +658,121 @@ struct Tree {
     ++launches;
     smooth(cfg.nu2);
     return cuda(cudaGetLastError(), "tree V-cycle");
+  }
+
+  // enqueue: refined blocks restricted, then max |b - A x| (composite) and max |b| over the
+  // leaves into d_red (bit patterns)
+  int enqueue_resmax() {
+    restrict_all();
+    if (int rc = cuda(cudaMemsetAsync(d_red.p, 0, 16, stream), "memset")) return rc;
+    const int* bxy = d_bxy.as<int>();
+    for (int l = 1; l <= lmax; ++l)
+      if (!leafl[l].empty()) {
+        resmax_kernel<<<(unsigned)leafl[l].size(), B * B, 0, stream>>>(T, d_leafl.as<int>() + leafl_off[l], bxy, l,
+                                                                        d_red.as<unsigned long long>());
+        ++launches;
+      }
+    return AMR_OK;
+  }
+
+  // Enqueue one whole solve of device leaf-major b, x onto `stream` while it is being
+  // captured: load, the first residual and check, a conditional while node whose body
+  // (captured on cstream) is a V-cycle (the base solve a nested device-side loop), the
+  // residual and the check, then the store of x.
+  int capture_solve(const double* db, double* dx) {
+    int rc;
+    if (!cstream && (rc = cuda(cudaStreamCreateWithFlags(&cstream, cudaStreamNonBlocking), "stream"))) return rc;
+    const unsigned nl = (unsigned)leaf_blk.size(), nt = (unsigned)(B * B);
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    if ((rc = cuda(cudaStreamGetCaptureInfo(stream, &st, nullptr, &g), "capture info"))) return rc;
+    cudaGraphConditionalHandle hc;
+    if ((rc = cuda(cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault), "conditional"))) return rc;
+    const long long start = launches;  // captured kernels are counted when a solve runs
+    long long l0 = launches;
+    leaf_copy_kernel<<<nl, nt, 0, stream>>>(T, d_leafblk.as<int>(), db, dx, 0);
+    ++launches;
+    if ((rc = enqueue_resmax())) return rc;
+    tree_check_kernel<<<1, 1, 0, stream>>>(d_red.as<unsigned long long>(), d_ctr.as<int>(), d_res.as<double>(),
+                                           mg_device_cycles(base), cfg.rtol, cfg.max_cycles, 1, hc);
+    ++launches;
+    pre_kernels = launches - l0 + 1;  // and the final store
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    if ((rc = cuda(cudaStreamGetCaptureInfo(stream, &st, nullptr, &g, &deps, nullptr, &ndeps), "capture info")))
+      return rc;
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((rc = cuda(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp), "conditional node"))) return rc;
+    if ((rc = cuda(cudaStreamUpdateCaptureDependencies(stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies),
+                   "capture dependencies")))
+      return rc;
+    if ((rc = cuda(cudaStreamBeginCaptureToGraph(cstream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                 cudaStreamCaptureModeThreadLocal),
+                   "body capture")))
+      return rc;
+    cudaStream_t outer = stream;
+    stream = cstream;
+    capturing = true;
+    l0 = launches;
+    rc = vcycle(lmax);
+    if (!rc) rc = enqueue_resmax();
+    if (!rc) {
+      tree_check_kernel<<<1, 1, 0, stream>>>(d_red.as<unsigned long long>(), d_ctr.as<int>(), d_res.as<double>(),
+                                             mg_device_cycles(base), cfg.rtol, cfg.max_cycles, 0, hc);
+      ++launches;
+    }
+    body_kernels = launches - l0 + 4;  // and the base solve's prelude
+    capturing = false;
+    stream = outer;
+    cudaGraph_t got = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(cstream, &got);
+    if (rc) return rc;
+    if ((rc = cuda(ec, "end body capture"))) return rc;
+    leaf_copy_kernel<<<nl, nt, 0, stream>>>(T, d_leafblk.as<int>(), nullptr, dx, 1);
+    launches = start;
+    return cuda(cudaGetLastError(), "solve capture");
+  }
+
+  // one device-side solve of device arrays db, dx (the graph is rebuilt when they change)
+  int solve_graph(const double* db, double* dx, int* cycles, double* rmo, double* bmo) {
+    int rc;
+    if (!sgraph || db != g_b || dx != g_x) {
+      if (sgraph) cudaGraphExecDestroy(sgraph);
+      sgraph = nullptr;
+      if (!d_ctr.p && ((rc = cuda(d_ctr.alloc(16), "alloc")) || (rc = cuda(d_res.alloc(16), "alloc")) ||
+                       (rc = cuda(cudaMallocHost(&h_res, 4 * sizeof(double)), "host alloc"))))
+        return rc;
+      cudaGraph_t g;
+      if ((rc = cuda(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "capture"))) return rc;
+      int crc = capture_solve(db, dx);
+      cudaError_t ec = cudaStreamEndCapture(stream, &g);
+      if (crc) {
+        if (ec == cudaSuccess) cudaGraphDestroy(g);
+        return crc;
+      }
+      if ((rc = cuda(ec, "end capture"))) return rc;
+      rc = cuda(cudaGraphInstantiate(&sgraph, g, 0), "instantiate");
+      cudaGraphDestroy(g);
+      if (rc) return rc;
+      g_b = db;
+      g_x = dx;
+    }
+    if ((rc = cuda(cudaGraphLaunch(sgraph, stream), "solve graph"))) return rc;
+    int ctr[2];
+    if ((rc = cuda(cudaMemcpyAsync(h_res, d_res.p, 16, cudaMemcpyDeviceToHost, stream), "copy")) ||
+        (rc = cuda(cudaMemcpyAsync(ctr, d_ctr.p, 8, cudaMemcpyDeviceToHost, stream), "copy")) ||
+        (rc = cuda(cudaStreamSynchronize(stream), "sync")))
+      return rc;
+    *cycles = ctr[0];
+    *rmo = h_res[0];
+    *bmo = h_res[1];
+    launches += pre_kernels + (long long)ctr[0] * body_kernels + (long long)ctr[1] * mg_loop_kernels(base);
+    return AMR_OK;
   }
 
   // composite residual max and max |b| over the leaves (refined blocks restricted first)
@@ -731,7 +909,16 @@ int mgt_solve(mgt_handle* h, const double* b, double* x, int on_device, int fixe
   }
   double rm, bm;
   int cyc;
-  if ((rc = t.solve_dev(db, dx, fixed_cycles, &cyc, &rm, &bm))) return rc;
+  if (fixed_cycles > 0) {  // a fixed number of cycles: the host-driven loop
+    if ((rc = t.solve_dev(db, dx, fixed_cycles, &cyc, &rm, &bm))) return rc;
+  } else {  // to rtol: the graph with the device-side loop, on the handle's own b, x arrays
+    if (!t.d_bin.p && ((rc = t.cuda(t.d_bin.alloc(n * 8), "alloc")) || (rc = t.cuda(t.d_xin.alloc(n * 8), "alloc"))))
+      return rc;
+    cudaMemcpyAsync(t.d_bin.p, db, n * 8, cudaMemcpyDeviceToDevice, t.stream);
+    cudaMemcpyAsync(t.d_xin.p, dx, n * 8, cudaMemcpyDeviceToDevice, t.stream);
+    if ((rc = t.solve_graph(t.d_bin.as<double>(), t.d_xin.as<double>(), &cyc, &rm, &bm))) return rc;
+    cudaMemcpyAsync(dx, t.d_xin.p, n * 8, cudaMemcpyDeviceToDevice, t.stream);
+  }
   if (!on_device) cudaMemcpyAsync(x, hx.p, n * 8, cudaMemcpyDeviceToHost, t.stream);
   if ((rc = t.cuda(cudaStreamSynchronize(t.stream), "sync"))) return rc;
   if (cycles) *cycles = cyc;
@@ -890,7 +1077,7 @@ int rdt_step(rdt_handle* h, int nsteps, int* cycles) {
     ++tu.launches;
     int cu, cv;
     double rm, bm, rm2, bm2;
-    if ((rc = tu.solve_dev(A.bu, A.xu, 0, &cu, &rm, &bm)) || (rc = tv.solve_dev(A.bv, A.xv, 0, &cv, &rm2, &bm2)))
+    if ((rc = tu.solve_graph(A.bu, A.xu, &cu, &rm, &bm)) || (rc = tv.solve_graph(A.bv, A.xv, &cv, &rm2, &bm2)))
       return rc;
     if (cycles) {
       cycles[2 * s] = cu;
