@@ -244,6 +244,13 @@ int mg_solve(mg_handle* h, const double* b, double* x, int on_device, int* cycle
 int mg_num_unknowns(const mg_handle* h, long long* n);
 /* kernels this handle has launched so far (graph nodes included) */
 int mg_kernel_launches(const mg_handle* h, long long* n);
+/* 2D: the strip height of the red-black sweep used for levels of side `side`, chosen by
+ * the autotuner at mg_create: per depth of the batch, the sweep of all instances' levels
+ * of that depth is timed with each candidate height (4..64, or the side-based default
+ * clamp(side/32, 8, 64)) and the fastest kept; cached per (sides, precision, boundary
+ * kind) for the process.  Every height gives the same iterate bit for bit.
+ * AMR_ERR_INVALID_ARG for a side that is not swept. */
+int mg_strip_height(const mg_handle* h, int side, int* height);
 
 /* ------------------------------------------------------------------------
  * Reaction-diffusion steps (Sec. 2.5): w = (u, v), dw/dt = F0(w) + F1(w), with

@@ -130,6 +130,7 @@ _SIGS = {
     "rd_last_residuals": ([_vp, _dp, _dp], C.c_int),
     "rd_extract_crops": ([_vp, C.c_int, _ip, _ip, C.c_int, C.c_double, _vp, _vp], C.c_int),
     "mg_kernel_launches": ([_vp, _llp], C.c_int),
+    "mg_strip_height": ([_vp, C.c_int, _ip], C.c_int),
     "rd_kernel_launches": ([_vp, _llp], C.c_int),
     "mgt_create": ([C.POINTER(MgtConfig), C.c_int, _ip, _ip, C.POINTER(_vp)], C.c_int),
     "mgt_destroy": ([_vp], C.c_int),
@@ -421,6 +422,12 @@ class MgSolver:
             self.close()
         except Exception:
             pass
+
+    def strip_height(self, side):
+        """2D: the autotuned strip height of the sweep for levels of this side."""
+        h = C.c_int()
+        _check(self.lib.mg_strip_height(self.h, side, C.byref(h)), self.h, "mg_last_error")
+        return h.value
 
     def solve(self, b, x):
         """b, x: packed float64 arrays (numpy host or torch CUDA); x is updated in place.

@@ -28,8 +28,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/amrvac_gb300.h"
@@ -365,6 +368,18 @@ __global__ void smooth_kernel(MgState S, Lvl<real> L, const Chunk* ch, int colou
 constexpr int kStripW = 28, kStripHMax = 64, kPre = 4;
 
 inline int strip_height(int n) { return std::min(kStripHMax, std::max(8, n / 32)); }
+
+// Autotuner of the strip height H of the 2D sweep, per depth of the batch: candidate heights,
+// and the process-wide cache of the measured choice keyed by (sides, precision, boundary kind).
+constexpr int kStripCandidates[] = {4, 8, 16, 32, 64};
+inline std::map<std::string, int>& strip_cache() {
+  static std::map<std::string, int> m;
+  return m;
+}
+inline std::mutex& strip_cache_mutex() {
+  static std::mutex m;
+  return m;
+}
 constexpr unsigned kFull = 0xffffffffu;
 
 struct StripGeom {
@@ -1056,11 +1071,6 @@ struct Mg {
         add_chunks(ch_half[l], i, l, cf / 2);
         add_chunks(ch_coarse[l], i, l, cc);
         add_chunks(ch_fine[l], i, l, cf);
-        if (nd == 2) {
-          const int H = strip_height(I.n[l]);
-          int nt = ((I.n[l] + kStripW - 1) / kStripW) * ((I.n[l] + H - 1) / H);
-          for (int k = 0; k < nt; ++k) ch_tile[l].push_back(Chunk{i, l, k, H});
-        }
       }
       long long m = 1;
       for (int d = 0; d < nd; ++d) m *= I.n[I.nlev - 1];
@@ -1088,6 +1098,16 @@ struct Mg {
     for (int i = 0; i < n_inst; ++i)
       cudaMemcpy(d_inv.as<double>() + insts[i].inv_off, invs[i].data(), invs[i].size() * 8, cudaMemcpyHostToDevice);
     cudaMemset(d_rnorm.p, 0, n_inst * 8);
+    if (nd == 2) {  // strip heights: measured per level side, then the tile lists
+      if ((rc = precision == AMR_FP64 ? tune_strips<double>() : tune_strips<float>())) return rc;
+      for (int i = 0; i < n_inst; ++i) {
+        const InstDev& I = insts[i];
+        for (int l = 0; l + 1 < I.nlev; ++l) {
+          const int H = height_for(l, I.n[l]);
+          for (int k = 0; k < tiles_of(I.n[l], H); ++k) ch_tile[l].push_back(Chunk{i, l, k, H});
+        }
+      }
+    }
     std::vector<Chunk> all;
     off_half.assign(maxdepth, 0);
     off_coarse.assign(maxdepth, 0);
@@ -1118,6 +1138,94 @@ struct Mg {
   template <typename real>
   Lvl<real> lvl() const {
     return Lvl<real>{d_xl.as<real>(), d_bl.as<real>()};
+  }
+
+  std::map<int, int> strip_h;  // level side -> strip height of the 2D sweep
+  std::vector<int> depth_h;     // per depth: the chosen candidate height, 0 = the side-based default
+  static int tiles_of(int n, int H) { return ((n + kStripW - 1) / kStripW) * ((n + H - 1) / H); }
+  int height_for(int depth, int n) const { return depth_h[depth] > 0 ? depth_h[depth] : strip_height(n); }
+
+  // Autotuner: for every depth of the batch, time the sweep of all the instances' levels of
+  // that depth together, as the V-cycle launches it, with each candidate strip height (one
+  // height for the whole depth, or the side-based default clamp(n/32, 8, 64)); 3 launches
+  // after a warm-up, CUDA events on the stream.  The kernel reads x and writes the second
+  // iterate array, so no data change, and every height gives the same iterate bit for bit:
+  // the choice changes time only.  Cached per (sides of the depth, precision, boundary kind).
+  template <typename real>
+  int tune_strips() {
+    std::vector<int> ones(ninst, 1);
+    if (int rc = cuda(cudaMemcpy(d_active.p, ones.data(), ninst * sizeof(int), cudaMemcpyHostToDevice), "copy"))
+      return rc;
+    MgState S = state();
+    Lvl<real> Lv = lvl<real>();
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DevBuf dch;
+    int rc = AMR_OK;
+    depth_h.assign(maxdepth, 0);
+    for (int l = 0; l + 1 < maxdepth && !rc; ++l) {
+      std::vector<int> sides;  // instances swept at this depth
+      std::vector<int> who;
+      for (int i = 0; i < ninst; ++i)
+        if (l + 1 < insts[i].nlev) {
+          sides.push_back(insts[i].n[l]);
+          who.push_back(i);
+        }
+      if (who.empty()) continue;
+      std::string key = std::to_string(precision) + (neu ? "n" : "p");
+      for (int n : sides) key += ":" + std::to_string(n);
+      {
+        std::lock_guard<std::mutex> g(strip_cache_mutex());
+        auto it = strip_cache().find(key);
+        if (it != strip_cache().end()) {
+          depth_h[l] = it->second;
+          continue;
+        }
+      }
+      if (!e0 && ((rc = cuda(cudaEventCreate(&e0), "event")) || (rc = cuda(cudaEventCreate(&e1), "event")))) break;
+      int best = 0;
+      float tbest = 1e30f;
+      for (int c = -1; c < (int)(sizeof(kStripCandidates) / sizeof(int)); ++c) {
+        const int H = c < 0 ? 0 : kStripCandidates[c];
+        std::vector<Chunk> t;
+        for (int i : who) {
+          const int n = insts[i].n[l], h = H > 0 ? H : strip_height(n);
+          for (int k = 0; k < tiles_of(n, h); ++k) t.push_back(Chunk{i, l, k, h});
+        }
+        const int nch = (int)t.size();
+        if ((rc = cuda(dch.alloc(t.size() * sizeof(Chunk)), "alloc")) ||
+            (rc = cuda(cudaMemcpy(dch.p, t.data(), t.size() * sizeof(Chunk), cudaMemcpyHostToDevice), "copy")))
+          break;
+        const unsigned nb = (unsigned)((nch + 3) / 4);
+        auto sweep = [&]() {
+          if (neu)
+            sweep2d_kernel<real, true><<<nb, 128, 0, stream>>>(S, Lv.x, d_yl.as<real>(), Lv.b, dch.as<Chunk>(), nch);
+          else
+            sweep2d_kernel<real, false><<<nb, 128, 0, stream>>>(S, Lv.x, d_yl.as<real>(), Lv.b, dch.as<Chunk>(), nch);
+        };
+        sweep();
+        cudaEventRecord(e0, stream);
+        for (int r = 0; r < 3; ++r) sweep();
+        cudaEventRecord(e1, stream);
+        if ((rc = cuda(cudaEventSynchronize(e1), "tuning"))) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < tbest) {
+          tbest = ms;
+          best = H;
+        }
+      }
+      depth_h[l] = best;
+      std::lock_guard<std::mutex> g(strip_cache_mutex());
+      strip_cache()[key] = best;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (!rc) rc = cuda(cudaGetLastError(), "tuning");
+    if (!rc)
+      for (int i = 0; i < ninst; ++i)
+        for (int l = 0; l + 1 < insts[i].nlev; ++l)
+          if (!strip_h.count(insts[i].n[l])) strip_h[insts[i].n[l]] = height_for(l, insts[i].n[l]);
+    return rc;
   }
 
   template <typename real>
@@ -1432,6 +1540,14 @@ const int* mg_device_cycles(const mg_handle* h) { return h->mg.d_cycles.as<int>(
 long long mg_loop_kernels(const mg_handle* h) { return h->mg.solve_loop_kernels; }
 
 extern "C" {
+
+int mg_strip_height(const mg_handle* h, int side, int* height) {
+  if (!h || !height) return AMR_ERR_INVALID_ARG;
+  auto it = h->mg.strip_h.find(side);
+  if (it == h->mg.strip_h.end()) return AMR_ERR_INVALID_ARG;
+  *height = it->second;
+  return AMR_OK;
+}
 
 int mg_kernel_launches(const mg_handle* h, long long* n) {
   if (!h || !n) return AMR_ERR_INVALID_ARG;

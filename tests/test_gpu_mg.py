@@ -227,3 +227,23 @@ def test_rd_uniform_state_is_heun():
     fus, fvs = f(0.6 + dt * fu, 0.3 + dt * fv)
     assert np.allclose(u1, 0.6 + dt / 2 * (fu + fus), rtol=1e-9)
     assert np.allclose(v1, 0.3 + dt / 2 * (fv + fvs), rtol=1e-9)
+
+
+def test_autotuned_strip_heights():
+    """mg_create times every candidate strip height of the 2D sweep per level side and keeps
+    the fastest; the heights are candidates, a side that is not swept has none, and the
+    solve reaches the oracle's solution whatever was chosen (every height gives the same
+    iterate)."""
+    sizes, L = [96, 80, 144], 2.1
+    lam, bs = batch(sizes, 2, 13)
+    s = amrvac.MgSolver(2, sizes, lam, L, precision="fp64")
+    for n in (96, 48, 24, 12, 80, 40, 20, 10, 144, 72, 36, 18):
+        assert s.strip_height(n) in (4, 8, 16, 32, 64), n
+    with pytest.raises(amrvac.AmrError):
+        s.strip_height(6)  # the coarsest side of 96: solved densely, never swept
+    x = np.zeros(s.n)
+    s.solve(pack(bs), x)
+    xs = unpack(x, sizes, 2)
+    for i in range(len(sizes)):
+        xo, _, _ = O.mg_solve(bs[i], np.zeros_like(bs[i]), L, lam[i])
+        assert np.max(np.abs(xs[i] - xo)) <= 1e-12 * np.max(np.abs(xo))
