@@ -101,6 +101,8 @@ def lib():
         for f in ("orc_amg_apply", "orc_amg_face_ghosts"):
             getattr(L, f).argtypes = [C.POINTER(OrcAmgConfig), C.c_int, _ip, _ip, _dp, _dp]
         L.orc_amg_solve.argtypes = [C.POINTER(OrcAmgConfig), C.c_int, _ip, _ip, _dp, _dp, C.c_int, _dp]
+        L.orc_amg_regrid.argtypes = [C.POINTER(OrcAmgConfig), C.c_int, _ip, _ip, _dp, _dp, C.c_double, C.c_double,
+                                     C.c_double, C.c_int, C.c_int, _ip, _ip, _dp, _dp, _dp]
         L.orc_amg_rd_step.argtypes = [C.POINTER(OrcAmgConfig), C.c_int, _ip, _ip] + [C.c_double] * 5 + [_dp, _dp, _ip]
         if hasattr(L, "orc_cnn_forward"):
             _bind_cnn(L)
@@ -482,3 +484,19 @@ def amg_rd_step(level, coords, u, v, nb, B, L, Du, Dv, F, k, dt, **kw):
     if st != 0:
         raise RuntimeError("tree multigrid did not converge")
     return u, v, cyc
+
+
+def amg_regrid(level, coords, u, v, nb, B, L, refine_tol, coarsen_frac=0.5, eps=0.01, max_level=3):
+    """Regrid of the reaction-diffusion quadtree; returns (level, coords, u, v, err_of_old_leaves)."""
+    level, coords = _tree(level, coords)
+    u, v = _f64(u), _f64(v)
+    n = len(level)
+    cap = 4 * n
+    nl, nc = np.zeros(cap, np.int32), np.zeros((cap, 2), np.int32)
+    nu, nv = np.zeros((cap, B * B)), np.zeros((cap, B * B))
+    err = np.zeros(n)
+    m = lib().orc_amg_regrid(C.byref(amg_config(nb, B, L, 0.0)), n, _i(level), _i(coords), _d(u), _d(v), refine_tol,
+                             coarsen_frac, eps, max_level, cap, _i(nl), _i(nc), _d(nu), _d(nv), _d(err))
+    if m < 0:
+        raise ValueError("invalid tree" if m == -2 else "capacity")
+    return nl[:m].copy(), nc[:m].copy(), nu[:m].copy(), nv[:m].copy(), err

@@ -38,6 +38,7 @@
 //  * Outer iteration: refined blocks are set to the means of their children (bottom up)
 //    and V-cycles run from the finest level until the composite residual max|b - A x| over
 //    the leaf cells is at most rtol max|b|, or a fixed number of cycles for parity tests.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -387,9 +388,195 @@ void composite_lap(Tree& T, const double* w, double* lap) {
   }
 }
 
+// ---------------------------------------------------------------- regrid ---
+// READING (the paper refines the Gray-Scott mesh adaptively but states no criterion; the
+// Lohner estimator of Sec. 1.3 is the method's default): per leaf, the Lohner estimator of u
+// and of v, per direction, second difference over the sum of the two first differences plus
+// a filter eps (|q+| + 2|q0| + |q-|), squares summed over the two directions, E = sqrt(num /
+// den) (0 where den = 0); neighbours through the level operator's values; max over cells and
+// both fields.
+double lohner_field(const Tree& T, int k, double eps) {
+  const Blk& b = T.blk[k];
+  const int B = T.B, l = b.lev;
+  double emax = 0.0;
+  for (int j = 0; j < B; ++j)
+    for (int i = 0; i < B; ++i) {
+      const int I = b.bx * B + i, J = b.by * B + j;
+      const double q0 = b.x[(size_t)j * B + i];
+      double num = 0.0, den = 0.0;
+      for (int d = 0; d < 2; ++d) {
+        const double qm = d == 0 ? nbr(T, l, I - 1, J, 0, -1, q0, &Blk::x, false) : nbr(T, l, I, J - 1, 1, -1, q0, &Blk::x, false);
+        const double qp = d == 0 ? nbr(T, l, I + 1, J, 0, +1, q0, &Blk::x, false) : nbr(T, l, I, J + 1, 1, +1, q0, &Blk::x, false);
+        const double d2 = qp - 2.0 * q0 + qm;
+        const double d1 = std::fabs(qp - q0) + std::fabs(q0 - qm) + eps * (std::fabs(qp) + 2.0 * std::fabs(q0) + std::fabs(qm));
+        num = num + d2 * d2;
+        den = den + d1 * d1;
+      }
+      const double e = den > 0.0 ? std::sqrt(num / den) : 0.0;
+      emax = std::fmax(emax, e);
+    }
+  return emax;
+}
+
+struct LeafKey {
+  int l, x, y;
+  bool operator<(const LeafKey& o) const { return l != o.l ? l < o.l : (x != o.x ? x < o.x : y < o.y); }
+  bool operator==(const LeafKey& o) const { return l == o.l && x == o.x && y == o.y; }
+};
+
+// closed boxes of two blocks overlap, periodic images included (nbx x nby base blocks)
+bool touches(const LeafKey& a, const LeafKey& b, int nbx, int nby, int lmax) {
+  const long sa = 1L << (lmax - a.l), sb = 1L << (lmax - b.l);
+  const long N[2] = {(long)nbx << (lmax - 1), (long)nby << (lmax - 1)};
+  const long lo_a[2] = {a.x * sa, a.y * sa}, lo_b[2] = {b.x * sb, b.y * sb};
+  for (int d = 0; d < 2; ++d) {
+    bool any = false;
+    for (long shift = -N[d]; shift <= N[d]; shift += N[d])
+      if (lo_a[d] <= lo_b[d] + sb + shift && lo_b[d] + shift <= lo_a[d] + sa) any = true;
+    if (!any) return false;
+  }
+  return true;
+}
+
+// Morton key of a block's lower corner at level lmax (x bits lowest): the order of new leaves
+unsigned long long morton(const LeafKey& k, int lmax) {
+  const unsigned long long x = (unsigned long long)k.x << (lmax - k.l), y = (unsigned long long)k.y << (lmax - k.l);
+  unsigned long long m = 0;
+  for (int b = 0; b < 24; ++b) m |= ((x >> b) & 1ull) << (2 * b) | ((y >> b) & 1ull) << (2 * b + 1);
+  return m;
+}
+
+double minmod(double a, double b) { return a * b > 0.0 ? (std::fabs(a) < std::fabs(b) ? a : b) : 0.0; }
+
 }  // namespace
 
 extern "C" {
+
+// Regrid of the reaction-diffusion quadtree (READING, see lohner_field above; the tree rules
+// are those of the hydrodynamic regrid): refine a leaf with E > refine_tol below max_level;
+// coarsen a group of four sibling leaves when each has E < coarsen_frac refine_tol and none
+// is refined; 2:1 balance across faces and corners (periodic images included) by refining
+// the coarser touching leaves of a refined leaf until none is left, and by dropping a
+// coarsening whose parent would touch a leaf more than one level finer.  Transfer: kept leaves
+// copy, a refined leaf's children take q + s_x/4 + s_y/4 with s the minmod of the parent's two
+// one-sided differences along each direction (parent-level neighbours, level operator),
+// signed by the child's half; a coarsened parent takes the means of its 2x2 children.  New
+// leaves in Morton order of their lower corner at max_level.
+int orc_amg_regrid(const orc_amg_config* c, int nleaves, const int* level, const int* coords, const double* u,
+                   const double* v, double refine_tol, double coarsen_frac, double eps, int max_level, int cap,
+                   int* new_level, int* new_coords, double* new_u, double* new_v, double* err) {
+  Tree Tu, Tv;
+  if (c->nbx != c->nby || build_tree(c, nleaves, level, coords, &Tu) || build_tree(c, nleaves, level, coords, &Tv))
+    return -2;
+  load(Tu, u, &Blk::x);
+  load(Tv, v, &Blk::x);
+  restrict_all(Tu);
+  restrict_all(Tv);
+  const int B = c->B, nb2 = B * B;
+  std::vector<double> E(nleaves);
+  std::vector<LeafKey> old(nleaves);
+  for (int k = 0; k < nleaves; ++k) {
+    E[k] = std::fmax(lohner_field(Tu, Tu.leaf_blk[k], eps), lohner_field(Tv, Tv.leaf_blk[k], eps));
+    if (err) err[k] = E[k];
+    old[k] = {level[k], coords[2 * k], coords[2 * k + 1]};
+  }
+  const int lmax = max_level > Tu.lmax ? max_level : Tu.lmax;
+  std::map<LeafKey, int> idx;  // old leaf -> index
+  for (int k = 0; k < nleaves; ++k) idx[old[k]] = k;
+  std::vector<char> refine(nleaves, 0);
+  for (int k = 0; k < nleaves; ++k) refine[k] = E[k] > refine_tol && old[k].l < max_level;
+  for (bool changed = true; changed;) {  // balance the refinement
+    changed = false;
+    for (int a = 0; a < nleaves; ++a) {
+      if (!refine[a]) continue;
+      for (int b = 0; b < nleaves; ++b)
+        if (!refine[b] && old[b].l < old[a].l && touches(old[a], old[b], c->nbx, c->nby, lmax)) {
+          refine[b] = 1;
+          changed = true;
+        }
+    }
+  }
+  std::vector<LeafKey> mid;  // the tree after refinement
+  for (int k = 0; k < nleaves; ++k) {
+    if (!refine[k]) {
+      mid.push_back(old[k]);
+      continue;
+    }
+    for (int q = 0; q < 4; ++q) mid.push_back({old[k].l + 1, 2 * old[k].x + (q & 1), 2 * old[k].y + (q >> 1)});
+  }
+  std::map<LeafKey, int> parents;  // candidate coarsenings: parent -> number of qualifying children
+  for (int k = 0; k < nleaves; ++k)
+    if (old[k].l > 1 && !refine[k] && E[k] < coarsen_frac * refine_tol)
+      parents[{old[k].l - 1, old[k].x >> 1, old[k].y >> 1}] += 1;
+  std::vector<LeafKey> coarsen;
+  for (const auto& pc : parents) {
+    if (pc.second != 4) continue;
+    bool ok = true;
+    for (const LeafKey& n : mid)
+      if (n.l > pc.first.l + 1 && touches(pc.first, n, c->nbx, c->nby, lmax)) {
+        ok = false;
+        break;
+      }
+    if (ok) coarsen.push_back(pc.first);
+  }
+  std::vector<LeafKey> out;
+  for (const LeafKey& n : mid) {
+    const LeafKey p{n.l - 1, n.x >> 1, n.y >> 1};
+    if (n.l > 1 && std::find(coarsen.begin(), coarsen.end(), p) != coarsen.end()) continue;
+    out.push_back(n);
+  }
+  for (const LeafKey& p : coarsen) out.push_back(p);
+  std::sort(out.begin(), out.end(),
+            [&](const LeafKey& a, const LeafKey& b) { return morton(a, lmax) < morton(b, lmax); });
+  if ((int)out.size() > cap) return -3;
+  for (size_t n = 0; n < out.size(); ++n) {
+    const LeafKey& K = out[n];
+    new_level[n] = K.l;
+    new_coords[2 * n] = K.x;
+    new_coords[2 * n + 1] = K.y;
+    for (int f = 0; f < 2; ++f) {
+      const Tree& T = f == 0 ? Tu : Tv;
+      double* dst = (f == 0 ? new_u : new_v) + n * nb2;
+      auto it = idx.find(K);
+      if (it != idx.end()) {  // kept
+        std::memcpy(dst, T.blk[T.leaf_blk[it->second]].x.data(), nb2 * sizeof(double));
+        continue;
+      }
+      const LeafKey P{K.l - 1, K.x >> 1, K.y >> 1};
+      if (K.l > 1 && idx.count(P)) {  // child of a refined leaf
+        const Blk& pb = T.blk[T.leaf_blk[idx[P]]];
+        for (int j = 0; j < B; ++j)
+          for (int i = 0; i < B; ++i) {
+            const int I = K.x * B + i, J = K.y * B + j;  // fine cell, level K.l
+            const int Ic = I >> 1, Jc = J >> 1;        // parent cell, level P.l
+            const int pi = Ic - pb.bx * B, pj = Jc - pb.by * B;
+            const double q = pb.x[(size_t)pj * B + pi];
+            const double qxm = nbr(T, P.l, Ic - 1, Jc, 0, -1, q, &Blk::x, false);
+            const double qxp = nbr(T, P.l, Ic + 1, Jc, 0, +1, q, &Blk::x, false);
+            const double qym = nbr(T, P.l, Ic, Jc - 1, 1, -1, q, &Blk::x, false);
+            const double qyp = nbr(T, P.l, Ic, Jc + 1, 1, +1, q, &Blk::x, false);
+            const double sx = (I & 1) ? 0.25 : -0.25, sy = (J & 1) ? 0.25 : -0.25;
+            dst[(size_t)j * B + i] = (q + sx * minmod(q - qxm, qxp - q)) + sy * minmod(q - qym, qyp - q);
+          }
+        continue;
+      }
+      // parent of coarsened leaves: means of the children
+      for (int j = 0; j < B; ++j)
+        for (int i = 0; i < B; ++i) {
+          const int quad = (2 * i >= B ? 1 : 0) + 2 * (2 * j >= B ? 1 : 0);
+          const LeafKey ch{K.l + 1, 2 * K.x + (quad & 1), 2 * K.y + (quad >> 1)};
+          const Blk& cb = T.blk[T.leaf_blk[idx.at(ch)]];
+          const int ci = (2 * i) % B, cj = (2 * j) % B;
+          double sum = cb.x[(size_t)cj * B + ci];
+          sum = sum + cb.x[(size_t)cj * B + ci + 1];
+          sum = sum + cb.x[(size_t)(cj + 1) * B + ci];
+          sum = sum + cb.x[(size_t)(cj + 1) * B + ci + 1];
+          dst[(size_t)j * B + i] = 0.25 * sum;
+        }
+    }
+  }
+  return (int)out.size();
+}
 
 // Gray-Scott IMEX step, Eq. (imex) with Eq. (gray-scott), on the leaves of the quadtree:
 // the composite Laplacian for the explicit parts and the tree multigrid for the implicit

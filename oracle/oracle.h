@@ -136,6 +136,14 @@ int orc_amg_apply(const orc_amg_config* c, int nleaves, const int* level, const 
                   double* Ax);
 int orc_amg_face_ghosts(const orc_amg_config* c, int nleaves, const int* level, const int* coords, const double* x,
                         double* ghosts);
+/* Regrid of the reaction-diffusion quadtree: Lohner estimator of u and v (eps filter), refine
+ * above refine_tol (up to max_level), coarsen sibling groups below coarsen_frac refine_tol, 2:1
+ * balance; fields copied, prolonged (minmod slopes) or restricted.  Writes the new leaves (Morton
+ * order of the lower corner at max_level), their u, v and the old leaves' estimator err[nleaves];
+ * returns the new leaf count, -2 for an invalid tree, -3 if it exceeds cap. */
+int orc_amg_regrid(const orc_amg_config* c, int nleaves, const int* level, const int* coords, const double* u,
+                   const double* v, double refine_tol, double coarsen_frac, double eps, int max_level, int cap,
+                   int* new_level, int* new_coords, double* new_u, double* new_v, double* err);
 /* Gray-Scott IMEX step (Eq. (imex), Eq. (gray-scott)) on the leaves: composite Laplacian
  * for the explicit parts, the tree multigrid (lambda = 2/(dt D), guess w_n; c->lambda is
  * ignored) for the implicit stage.  cycles[2]: V-cycles per species.  0, -1 (a solve did

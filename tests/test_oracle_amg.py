@@ -185,3 +185,66 @@ def test_paper_gray_scott_tree_is_a_balanced_three_level_cover():
     leaves = [(int(l), (int(c[0]), int(c[1]), 0)) for l, c in zip(lev, crd)]
     assert covers_domain(leaves, 2, [16, 16, 1], 3)
     assert is_balanced(leaves, 2, [16, 16, 1], 3, (True, True, True))
+
+
+# ------------------------------------------------------------ regrid of the RD tree --
+def _leaves(lev, crd):
+    return [(int(l), (int(c[0]), int(c[1]), 0)) for l, c in zip(lev, crd)]
+
+
+@pytest.mark.parametrize("seed", [7, 8])
+def test_regrid_keeps_a_balanced_cover_and_conserves(seed):
+    from treeutil import covers_domain
+    from paper_2004_03275_gb300 import inputs
+    nb, B, L = 4, 8, 2.0
+    lev, crd3 = random_balanced_tree(2, [nb, nb, 1], 3, np.random.default_rng(seed), 6)
+    crd = crd3[:, :2]
+    X, Y, h = centres(lev, crd, nb, B, L)
+    u, v = inputs.gray_scott_gaussians(X, Y, centres=((0.6, 1.3), (1.5, 0.4)))
+    nl, nc, nu, nv, err = O.amg_regrid(lev, crd, u, v, nb, B, L, refine_tol=0.05, coarsen_frac=0.5, max_level=3)
+    assert covers_domain(_leaves(nl, nc), 2, [nb, nb, 1], 3)
+    assert is_balanced(_leaves(nl, nc), 2, [nb, nb, 1], 3, (True, True, True))
+    assert np.max(nl) <= 3 and len(err) == len(lev)
+    assert not np.array_equal(np.sort(nl), np.sort(lev))  # the tree changed
+    _, _, h2 = centres(nl, nc, nb, B, L)
+    for a, b in ((u, nu), (v, nv)):
+        t0 = np.sum(a * (h ** 2)[:, None])
+        t1 = np.sum(b * (h2 ** 2)[:, None])
+        assert abs(t1 - t0) <= 1e-13 * abs(t0)
+
+
+def test_regrid_flags_follow_the_estimator():
+    """A constant field has estimator 0: every sibling group coarsens (one level per regrid) and
+    the values stay exact.  A linear field also has estimator 0 (no second differences)."""
+    nb, B, L = 4, 8, 1.0
+    lev, crd = patch_tree(nb)
+    n = len(lev)
+    u, v = np.full((n, B * B), 0.7), np.full((n, B * B), 0.2)
+    nl, nc, nu, nv, err = O.amg_regrid(lev, crd, u, v, nb, B, L, refine_tol=0.1)
+    assert np.all(err == 0.0)
+    assert np.max(nl) == 2 and np.all(nu == 0.7) and np.all(nv == 0.2)
+    X, Y, _ = centres(lev, crd, nb, B, L)
+    lin = 0.3 + 0.2 * X - 0.1 * Y
+    _, _, _, _, err = O.amg_regrid(lev, crd, lin, lin, nb, B, L, refine_tol=0.1)
+    interior = [k for k in range(n) if 0.3 < crd[k, 0] / (nb * 2 ** (lev[k] - 1)) < 0.7
+                and 0.3 < crd[k, 1] / (nb * 2 ** (lev[k] - 1)) < 0.7]
+    assert np.max(err[interior]) <= 1e-12
+
+
+def test_regrid_prolongation_is_exact_for_linear_data():
+    """Refining a leaf of linear data: its children's cells get the linear function at their
+    centres (minmod slopes of linear data are the exact one-sided differences)."""
+    nb, B, L = 4, 8, 1.0
+    lev = np.ones(nb * nb, np.int32)
+    crd = np.array([(x, y) for y in range(nb) for x in range(nb)], np.int32)
+    X, Y, _ = centres(lev, crd, nb, B, L)
+    f = lambda x, y: 0.5 + 0.3 * x + 0.2 * y
+    u = f(X, Y)
+    bump = np.exp(-400 * ((X - 0.6) ** 2 + (Y - 0.6) ** 2))  # refines the blocks around (0.6, 0.6)
+    nl, nc, nu, nv, err = O.amg_regrid(lev, crd, u, u + bump, nb, B, L, refine_tol=0.2)
+    assert np.any(nl == 2)
+    X2, Y2, _ = centres(nl, nc, nb, B, L)
+    for k in np.where(nl == 2)[0]:
+        xk, yk = X2[k], Y2[k]
+        if xk.min() > 0.3 and xk.max() < 0.9 and yk.min() > 0.3 and yk.max() < 0.9:
+            assert np.allclose(nu[k], f(xk, yk), rtol=0, atol=1e-14)
