@@ -382,11 +382,11 @@ def bench_schnakenberg(torch, amrvac, stream):
             "timing": "host wall clock around synchronous rd_step calls"}
 
 
-def bench_gray_scott_tree(torch, amrvac, stream, steps=20):
-    """Sec. 2.5.2's Gray-Scott run on a three-level block quadtree: F = 0.046, k = 0.063,
-    D_u = 2e-5, D_v = 1e-5, L = 2, 8^2 blocks, base 128^2, finest 512^2, dt = 0.5, two Gaussian
-    perturbations; IMEX steps with the float64 tree multigrid (rtol 1e-10).  The mesh is
-    fixed, refined around the perturbations (the paper adapts it as the pattern grows)."""
+def bench_gray_scott_tree(torch, amrvac, stream, steps=40, regrid_every=10):
+    """Sec. 2.5.2's Gray-Scott run on an adaptive three-level block quadtree: F = 0.046,
+    k = 0.063, D_u = 2e-5, D_v = 1e-5, L = 2, 8^2 blocks, base 128^2, finest 512^2, dt = 0.5, two
+    Gaussian perturbations; IMEX steps with the float64 tree multigrid (rtol 1e-10) and a regrid
+    (Lohner estimator of u, refine above 0.01, coarsen below 0.005) every 10 steps."""
     from paper_2004_03275_gb300 import inputs
     p = inputs.GRAY_SCOTT_PAPER
     nb, B = 16, 8
@@ -398,15 +398,25 @@ def bench_gray_scott_tree(torch, amrvac, stream, steps=20):
     s.set_state(u.ravel(), v.ravel())
     s.step(2)
     n0 = s.kernel_launches()
+    per_level, t_step, t_regrid, cyc = [], 0.0, 0.0, []
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    cyc = s.step(steps)
-    el = (time.perf_counter() - t0) / steps
-    out = {"workload": "Gray-Scott IMEX on a 3-level quadtree (8^2 blocks, 128^2..512^2), float64 tree multigrid",
-           "leaves_per_level": [int(c) for c in np.bincount(lev)[1:]], "cells": int(len(lev) * B * B),
-           "ms_per_step": round(el * 1e3, 3), "vcycles_per_solve": round(float(np.mean(cyc)), 2),
-           "kernels_per_step": round((s.kernel_launches() - n0) / steps, 1), "steps": steps,
-           "timing": "host wall clock around synchronous rdt_step calls (each solve one graph with device-side loops)"}
+    for k in range(steps // regrid_every):
+        t0 = time.perf_counter()
+        cyc.append(s.step(regrid_every))
+        t1 = time.perf_counter()
+        s.regrid(refine_tol=0.01, coarsen_frac=0.5, max_level=3)
+        t2 = time.perf_counter()
+        t_step += t1 - t0
+        t_regrid += t2 - t1
+        per_level.append([int(c) for c in np.bincount(s.leaves()[0], minlength=4)[1:]])
+    out = {"workload": "Gray-Scott IMEX on an adaptive 3-level quadtree (8^2 blocks, 128^2..512^2), float64 tree "
+                       "multigrid, regrid every 10 steps",
+           "initial_leaves_per_level": [int(c) for c in np.bincount(lev)[1:]], "leaves_per_level_after_each_regrid": per_level,
+           "ms_per_step": round(t_step / steps * 1e3, 3), "ms_per_regrid": round(t_regrid / (steps // regrid_every) * 1e3, 2),
+           "vcycles_per_solve": round(float(np.mean(np.concatenate(cyc))), 2),
+           "kernels_per_step_incl_regrids": round((s.kernel_launches() - n0) / steps, 1), "steps": steps,
+           "timing": "host wall clock around synchronous rdt_step / rdt_regrid calls (each solve one graph with "
+                     "device-side loops)"}
     s.close()
     return out
 

@@ -361,6 +361,18 @@ int rdt_read_state(rdt_handle* h, double* u, double* v, int on_device);
 /* cycles (host, may be NULL): [step][2] V-cycles (u, v).  Synchronous. */
 int rdt_step(rdt_handle* h, int nsteps, int* cycles);
 int rdt_kernel_launches(const rdt_handle* h, long long* n);
+int rdt_num_leaves(const rdt_handle* h, long long* n);
+/* the current leaves: level[n], coords[2n] (host, capacity cap leaves) */
+int rdt_leaves(const rdt_handle* h, int* level, int* coords, long long cap);
+/* Regrid (the paper adapts the Gray-Scott mesh; the criterion is a reading): Lohner
+ * estimator of u (per direction, filter eps, neighbours by the level values), refine
+ * leaves above refine_tol up to max_level, coarsen groups of four sibling leaves below
+ * coarsen_frac * refine_tol, 2:1 balance over faces and corners; fields copied, prolonged
+ * with minmod slopes, or restricted (means).  New leaves in Morton order of their lower
+ * corner at max_level; err_out (host, may be NULL) gets the old leaves' estimator and
+ * nleaves_out the new count.  The state keeps its float64 layout [leaf][B*B]. */
+int rdt_regrid(rdt_handle* h, double refine_tol, double coarsen_frac, double eps, int max_level, double* err_out,
+               long long* nleaves_out);
 
 /* ------------------------------------------------------------------------
  * Learned multigrid initial guess (no counterpart in the paper; the project's

@@ -391,10 +391,11 @@ void composite_lap(Tree& T, const double* w, double* lap) {
 // ---------------------------------------------------------------- regrid ---
 // READING (the paper refines the Gray-Scott mesh adaptively but states no criterion; the
 // Lohner estimator of Sec. 1.3 is the method's default): per leaf, the Lohner estimator of u
-// and of v, per direction, second difference over the sum of the two first differences plus
-// a filter eps (|q+| + 2|q0| + |q-|), squares summed over the two directions, E = sqrt(num /
-// den) (0 where den = 0); neighbours through the level operator's values; max over cells and
-// both fields.
+// (the field the paper's figure shows; v is near zero away from the pattern, where the
+// filter, relative to |q|, would flag round-off), per direction, second difference over the
+// sum of the two first differences plus a filter eps (|q+| + 2|q0| + |q-|), squares summed
+// over the two directions, E = sqrt(num / den) (0 where den = 0); neighbours through the
+// level operator's values; max over the leaf's cells.
 double lohner_field(const Tree& T, int k, double eps) {
   const Blk& b = T.blk[k];
   const int B = T.B, l = b.lev;
@@ -476,7 +477,7 @@ int orc_amg_regrid(const orc_amg_config* c, int nleaves, const int* level, const
   std::vector<double> E(nleaves);
   std::vector<LeafKey> old(nleaves);
   for (int k = 0; k < nleaves; ++k) {
-    E[k] = std::fmax(lohner_field(Tu, Tu.leaf_blk[k], eps), lohner_field(Tv, Tv.leaf_blk[k], eps));
+    E[k] = lohner_field(Tu, Tu.leaf_blk[k], eps);
     if (err) err[k] = E[k];
     old[k] = {level[k], coords[2 * k], coords[2 * k + 1]};
   }

@@ -136,7 +136,7 @@ int orc_amg_apply(const orc_amg_config* c, int nleaves, const int* level, const 
                   double* Ax);
 int orc_amg_face_ghosts(const orc_amg_config* c, int nleaves, const int* level, const int* coords, const double* x,
                         double* ghosts);
-/* Regrid of the reaction-diffusion quadtree: Lohner estimator of u and v (eps filter), refine
+/* Regrid of the reaction-diffusion quadtree: Lohner estimator of u (eps filter), refine
  * above refine_tol (up to max_level), coarsen sibling groups below coarsen_frac refine_tol, 2:1
  * balance; fields copied, prolonged (minmod slopes) or restricted.  Writes the new leaves (Morton
  * order of the lower corner at max_level), their u, v and the old leaves' estimator err[nleaves];

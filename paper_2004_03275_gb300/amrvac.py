@@ -146,6 +146,9 @@ _SIGS = {
     "rdt_read_state": ([_vp, _vp, _vp, C.c_int], C.c_int),
     "rdt_step": ([_vp, C.c_int, _ip], C.c_int),
     "rdt_kernel_launches": ([_vp, _llp], C.c_int),
+    "rdt_num_leaves": ([_vp, _llp], C.c_int),
+    "rdt_leaves": ([_vp, _ip, _ip, C.c_longlong], C.c_int),
+    "rdt_regrid": ([_vp, C.c_double, C.c_double, C.c_double, C.c_int, _dp, _llp], C.c_int),
 }
 
 
@@ -606,6 +609,7 @@ class TreeRdSolver:
         if rc != AMR_OK:
             raise AmrError(rc, "rdt_create")
         self.h = h
+        self.B2 = B * B
         self.n = len(self.level) * B * B
 
     def close(self):
@@ -635,6 +639,24 @@ class TreeRdSolver:
         cyc = np.zeros((nsteps, 2), dtype=np.int32)
         _check(self.lib.rdt_step(self.h, nsteps, cyc.ctypes.data_as(_ip)), self.h, "rdt_last_error")
         return cyc
+
+    def leaves(self):
+        n = C.c_longlong()
+        _check(self.lib.rdt_num_leaves(self.h, C.byref(n)), self.h, "rdt_last_error")
+        lev = np.zeros(n.value, np.int32)
+        crd = np.zeros((n.value, 2), np.int32)
+        _check(self.lib.rdt_leaves(self.h, lev.ctypes.data_as(_ip), crd.ctypes.data_as(_ip), n.value), self.h,
+               "rdt_last_error")
+        return lev, crd
+
+    def regrid(self, refine_tol, coarsen_frac=0.5, eps=0.01, max_level=3):
+        """Adapt the tree; returns the old leaves' estimator."""
+        err = np.zeros(self.n // self.B2)
+        n = C.c_longlong()
+        _check(self.lib.rdt_regrid(self.h, refine_tol, coarsen_frac, eps, max_level, err.ctypes.data_as(_dp),
+                                   C.byref(n)), self.h, "rdt_last_error")
+        self.n = n.value * self.B2
+        return err
 
     def kernel_launches(self):
         n = C.c_longlong()

@@ -32,6 +32,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/amrvac_gb300.h"
@@ -354,6 +355,80 @@ __global__ void rdt_finish_kernel(RdtArgs A) {
   const double fvs = uvv - (A.F + A.k) * vs;
   A.u[i] = A.u[i] + (0.5 * A.dt) * (A.Fn[i] + (fus + A.Du * A.lu[i]));
   A.v[i] = A.v[i] + (0.5 * A.dt) * (A.Fn[A.n + i] + (fvs + A.Dv * A.lv[i]));
+}
+
+// ------------------------------------------------------------------ regrid --
+// Lohner estimator of the field in x over the leaves of the list (level l): per cell and
+// direction, (q+ - 2 q0 + q-)^2 over (|q+ - q0| + |q0 - q-| + eps (|q+| + 2|q0| + |q-|))^2,
+// neighbours by the level operator, E = sqrt(num / den) (0 where den = 0); the max over the
+// leaf's cells goes to err[slot] as a bit pattern (non-negative doubles order like their bits)
+__global__ void lohner_kernel(TreeDev T, const int* list, const int* bxy, int l, const int* slot, double eps,
+                              unsigned long long* err) {
+  __shared__ unsigned long long wmax[8];
+  const Cell c = cell_of_thread(T, list, l, bxy);
+  const double q0 = T.x[(size_t)c.k * T.B * T.B + c.j * T.B + c.i];
+  double num = 0.0, den = 0.0;
+  for (int d = 0; d < 2; ++d) {
+    const double qm = d == 0 ? nbr(T, T.x, l, c.I - 1, c.J, 0, -1, q0, false) : nbr(T, T.x, l, c.I, c.J - 1, 1, -1, q0, false);
+    const double qp = d == 0 ? nbr(T, T.x, l, c.I + 1, c.J, 0, +1, q0, false) : nbr(T, T.x, l, c.I, c.J + 1, 1, +1, q0, false);
+    const double d2 = qp - 2.0 * q0 + qm;
+    const double d1 = fabs(qp - q0) + fabs(q0 - qm) + eps * (fabs(qp) + 2.0 * fabs(q0) + fabs(qm));
+    num = num + d2 * d2;
+    den = den + d1 * d1;
+  }
+  const double e = den > 0.0 ? sqrt(num / den) : 0.0;
+  unsigned long long m = (unsigned long long)__double_as_longlong(e);
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
+    m = y > m ? y : m;
+  }
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = wmax[w] > m ? wmax[w] : m;
+    atomicMax(&err[slot[c.k]], m);
+  }
+}
+
+__device__ __forceinline__ double minmod2(double a, double b) {
+  return a * b > 0.0 ? (fabs(a) < fabs(b) ? a : b) : 0.0;
+}
+
+// How new leaf n of a regrid gets its values from the old tree (block indices of the old tree)
+struct Xfer {
+  int kind;  // 0: the same leaf, 1: a child of refined leaf src[0], 2: the parent of leaves src[0..3]
+  int l, x, y;
+  int src[4];
+};
+
+// field of the new leaf blockIdx.x (old tree's x holds the field, refined blocks restricted)
+__global__ void transfer_kernel(TreeDev T, const Xfer* __restrict__ xf, double* __restrict__ out) {
+  const Xfer X = xf[blockIdx.x];
+  const int B = T.B, i = threadIdx.x % B, j = threadIdx.x / B;
+  double* dst = out + (size_t)blockIdx.x * B * B + j * B + i;
+  if (X.kind == 0) {
+    *dst = T.x[(size_t)X.src[0] * B * B + j * B + i];
+  } else if (X.kind == 1) {
+    const int I = X.x * B + i, J = X.y * B + j, Ic = I >> 1, Jc = J >> 1, pl = X.l - 1;
+    const int pk = X.src[0];
+    const int pi = Ic - (X.x >> 1) * B, pj = Jc - (X.y >> 1) * B;
+    const double q = T.x[(size_t)pk * B * B + pj * B + pi];
+    const double qxm = nbr(T, T.x, pl, Ic - 1, Jc, 0, -1, q, false);
+    const double qxp = nbr(T, T.x, pl, Ic + 1, Jc, 0, +1, q, false);
+    const double qym = nbr(T, T.x, pl, Ic, Jc - 1, 1, -1, q, false);
+    const double qyp = nbr(T, T.x, pl, Ic, Jc + 1, 1, +1, q, false);
+    const double sx = (I & 1) ? 0.25 : -0.25, sy = (J & 1) ? 0.25 : -0.25;
+    *dst = (q + sx * minmod2(q - qxm, qxp - q)) + sy * minmod2(q - qym, qyp - q);
+  } else {
+    const int quad = (2 * i >= B ? 1 : 0) + 2 * (2 * j >= B ? 1 : 0);
+    const double* cf = T.x + (size_t)X.src[quad] * B * B;
+    const int ci = (2 * i) % B, cj = (2 * j) % B;
+    double sum = cf[cj * B + ci];
+    sum = sum + cf[cj * B + ci + 1];
+    sum = sum + cf[(cj + 1) * B + ci];
+    sum = sum + cf[(cj + 1) * B + ci + 1];
+    *dst = 0.25 * sum;
+  }
 }
 
 // ------------------------------------------------------------------ host --
@@ -979,16 +1054,9 @@ struct rdt_handle {
   }
 };
 
-int rdt_create(const rdt_config* cfg, int nleaves, const int* level, const int* coords, rdt_handle** out) {
-  if (!cfg || !out || !(cfg->dt > 0) || !(cfg->Du > 0) || !(cfg->Dv > 0)) return AMR_ERR_INVALID_ARG;
-  *out = nullptr;
-  std::unique_ptr<rdt_handle> h(new rdt_handle());
-  h->cfg = *cfg;
-  h->stream = (cudaStream_t)cfg->mg.stream;
-  if (!h->stream) {
-    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) return AMR_ERR_CUDA;
-    h->own_stream = true;
-  }
+// (re)build the two trees and the state buffers of h for these leaves
+static int rdt_build(rdt_handle* h, int nleaves, const int* level, const int* coords) {
+  const rdt_config* cfg = &h->cfg;
   const double D[2] = {cfg->Du, cfg->Dv};
   std::unique_ptr<Tree>* t[2] = {&h->tu, &h->tv};
   for (int s = 0; s < 2; ++s) {
@@ -1000,16 +1068,27 @@ int rdt_create(const rdt_config* cfg, int nleaves, const int* level, const int* 
     int rc = tr.build(&mc, nleaves, level, coords);
     if (!rc) rc = tr.setup(h->stream);
     if (!rc) rc = tr.setup_leaf_lists();
-    if (rc) {
-      *out = nullptr;
-      return rc;
-    }
+    if (rc) return h->fail(rc, tr.err);
   }
   h->n = (long long)nleaves * cfg->mg.B * cfg->mg.B;
   const size_t bytes = (size_t)h->n * 8;
   for (Buf* b : {&h->d_u, &h->d_v, &h->d_lu, &h->d_lv, &h->d_bu, &h->d_bv, &h->d_xu, &h->d_xv})
-    if (b->alloc(bytes) != cudaSuccess) return AMR_ERR_OOM;
-  if (h->d_Fn.alloc(2 * bytes) != cudaSuccess) return AMR_ERR_OOM;
+    if (b->alloc(bytes) != cudaSuccess) return h->fail(AMR_ERR_OOM, "alloc");
+  if (h->d_Fn.alloc(2 * bytes) != cudaSuccess) return h->fail(AMR_ERR_OOM, "alloc");
+  return AMR_OK;
+}
+
+int rdt_create(const rdt_config* cfg, int nleaves, const int* level, const int* coords, rdt_handle** out) {
+  if (!cfg || !out || !(cfg->dt > 0) || !(cfg->Du > 0) || !(cfg->Dv > 0)) return AMR_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::unique_ptr<rdt_handle> h(new rdt_handle());
+  h->cfg = *cfg;
+  h->stream = (cudaStream_t)cfg->mg.stream;
+  if (!h->stream) {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) return AMR_ERR_CUDA;
+    h->own_stream = true;
+  }
+  if (int rc = rdt_build(h.get(), nleaves, level, coords)) return rc;
   *out = h.release();
   return AMR_OK;
 }
@@ -1092,6 +1171,194 @@ int rdt_step(rdt_handle* h, int nsteps, int* cycles) {
     if (cudaGetLastError() != cudaSuccess) return h->fail(AMR_ERR_CUDA, "launch");
   }
   return cudaStreamSynchronize(h->stream) == cudaSuccess ? AMR_OK : AMR_ERR_CUDA;
+}
+
+int rdt_num_leaves(const rdt_handle* h, long long* n) {
+  if (!h || !n) return AMR_ERR_INVALID_ARG;
+  *n = (long long)h->tu->leaf_blk.size();
+  return AMR_OK;
+}
+
+int rdt_leaves(const rdt_handle* h, int* level, int* coords, long long cap) {
+  if (!h || !level || !coords) return AMR_ERR_INVALID_ARG;
+  const Tree& t = *h->tu;
+  if (cap < (long long)t.leaf_blk.size()) return AMR_ERR_INVALID_ARG;
+  for (size_t s = 0; s < t.leaf_blk.size(); ++s) {
+    const int k = t.leaf_blk[s];
+    level[s] = t.lev[k];
+    coords[2 * s] = t.bx[k];
+    coords[2 * s + 1] = t.by[k];
+  }
+  return AMR_OK;
+}
+
+namespace {
+struct LeafId {
+  int l, x, y;
+};
+long long leaf_key(int l, int x, int y) { return ((long long)l << 48) | ((long long)y << 24) | x; }
+// do the closed boxes of two blocks meet (periodic images included)?  Box edges in units of a
+// level-lmax block.
+bool boxes_meet(const LeafId& a, const LeafId& b, int nbx, int nby, int lmax) {
+  const long long n[2] = {(long long)nbx << (lmax - 1), (long long)nby << (lmax - 1)};
+  const long long sa = 1LL << (lmax - a.l), sb = 1LL << (lmax - b.l);
+  const long long a0[2] = {a.x * sa, a.y * sa}, b0[2] = {b.x * sb, b.y * sb};
+  for (int d = 0; d < 2; ++d) {
+    bool hit = false;
+    for (int img = -1; img <= 1 && !hit; ++img) {
+      const long long off = img * n[d];
+      hit = a0[d] <= b0[d] + off + sb && b0[d] + off <= a0[d] + sa;
+    }
+    if (!hit) return false;
+  }
+  return true;
+}
+unsigned long long zorder(const LeafId& k, int lmax) {
+  unsigned long long x = (unsigned long long)k.x << (lmax - k.l), y = (unsigned long long)k.y << (lmax - k.l), z = 0;
+  for (int b = 0; b < 24; ++b) z |= (((x >> b) & 1ull) << (2 * b)) | (((y >> b) & 1ull) << (2 * b + 1));
+  return z;
+}
+}  // namespace
+
+// Regrid: Lohner estimator of u on the GPU, the new tree on the host (refine above
+// refine_tol up to max_level; coarsen sibling groups below coarsen_frac refine_tol; 2:1
+// balance over faces and corners), the fields moved on the GPU (copy, minmod-sloped
+// prolongation, mean restriction), then the trees rebuilt for the new leaves (Morton order).
+int rdt_regrid(rdt_handle* h, double refine_tol, double coarsen_frac, double eps, int max_level, double* err_out,
+               long long* nleaves_out) {
+  if (!h || !(refine_tol > 0) || !(coarsen_frac >= 0) || max_level < 1 || max_level > kMaxLev)
+    return AMR_ERR_INVALID_ARG;
+  Tree& tu = *h->tu;
+  Tree& tv = *h->tv;
+  const int nl = (int)tu.leaf_blk.size(), B = tu.B, nt = B * B;
+  Buf d_err;
+  if (d_err.alloc((size_t)nl * 8) != cudaSuccess) return h->fail(AMR_ERR_OOM, "alloc");
+  cudaMemsetAsync(d_err.p, 0, (size_t)nl * 8, h->stream);
+  // fields into the old trees' x (refined blocks restricted); the estimator on u
+  Tree* trees[2] = {&tu, &tv};
+  const double* fields[2] = {h->d_u.as<double>(), h->d_v.as<double>()};
+  long long extra = 2;  // the two transfers below
+  for (int f = 0; f < 2; ++f) {
+    Tree& t = *trees[f];
+    leaf_copy_kernel<<<(unsigned)nl, nt, 0, h->stream>>>(t.T, t.d_leafblk.as<int>(), nullptr,
+                                                        const_cast<double*>(fields[f]), 0);
+    ++extra;
+    t.restrict_all();
+    for (int l = 1; l <= t.lmax && f == 0; ++l)
+      if (!t.leafl[l].empty()) {
+        lohner_kernel<<<(unsigned)t.leafl[l].size(), nt, 0, h->stream>>>(t.T, t.d_leafl.as<int>() + t.leafl_off[l],
+                                                                        t.d_bxy.as<int>(), l, t.d_slot.as<int>(), eps,
+                                                                        d_err.as<unsigned long long>());
+        ++extra;
+      }
+  }
+  std::vector<unsigned long long> eb(nl);
+  if (cudaMemcpyAsync(eb.data(), d_err.p, (size_t)nl * 8, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return h->fail(AMR_ERR_CUDA, "estimator");
+  std::vector<double> E(nl);
+  for (int k = 0; k < nl; ++k) std::memcpy(&E[k], &eb[k], 8);
+  if (err_out) std::memcpy(err_out, E.data(), (size_t)nl * 8);
+  // the new tree
+  std::vector<LeafId> old(nl);
+  std::unordered_map<long long, int> where;  // old leaf -> its position in the caller's order
+  for (int k = 0; k < nl; ++k) {
+    const int b = tu.leaf_blk[k];
+    old[k] = {tu.lev[b], tu.bx[b], tu.by[b]};
+    where[leaf_key(old[k].l, old[k].x, old[k].y)] = k;
+  }
+  const int lmax = std::max(max_level, tu.lmax), nbx = h->cfg.mg.nbx, nby = h->cfg.mg.nby;
+  std::vector<char> ref(nl);
+  for (int k = 0; k < nl; ++k) ref[k] = E[k] > refine_tol && old[k].l < max_level;
+  bool grew = true;
+  while (grew) {  // a refined leaf's coarser neighbours are refined too
+    grew = false;
+    for (int a = 0; a < nl; ++a)
+      if (ref[a])
+        for (int b = 0; b < nl; ++b)
+          if (!ref[b] && old[b].l < old[a].l && boxes_meet(old[a], old[b], nbx, nby, lmax)) {
+            ref[b] = 1;
+            grew = true;
+          }
+  }
+  std::vector<LeafId> after;  // the tree once the refinements are applied
+  for (int k = 0; k < nl; ++k) {
+    if (!ref[k]) {
+      after.push_back(old[k]);
+    } else {
+      for (int q = 0; q < 4; ++q) after.push_back({old[k].l + 1, 2 * old[k].x + (q & 1), 2 * old[k].y + (q >> 1)});
+    }
+  }
+  std::unordered_map<long long, int> quiet;  // parent -> number of its children that may coarsen
+  for (int k = 0; k < nl; ++k)
+    if (old[k].l > 1 && !ref[k] && E[k] < coarsen_frac * refine_tol) ++quiet[leaf_key(old[k].l - 1, old[k].x >> 1, old[k].y >> 1)];
+  std::unordered_map<long long, char> merge;  // parents that replace their four children
+  for (const auto& kv : quiet) {
+    if (kv.second != 4) continue;
+    const LeafId p{(int)(kv.first >> 48), (int)(kv.first & 0xffffff), (int)((kv.first >> 24) & 0xffffff)};
+    bool ok = true;
+    for (const LeafId& n : after)
+      if (n.l > p.l + 1 && boxes_meet(p, n, nbx, nby, lmax)) {
+        ok = false;
+        break;
+      }
+    if (ok) merge[kv.first] = 1;
+  }
+  std::vector<LeafId> nw;
+  for (const LeafId& n : after)
+    if (!(n.l > 1 && merge.count(leaf_key(n.l - 1, n.x >> 1, n.y >> 1)))) nw.push_back(n);
+  for (const auto& kv : merge) nw.push_back({(int)(kv.first >> 48), (int)(kv.first & 0xffffff), (int)((kv.first >> 24) & 0xffffff)});
+  std::sort(nw.begin(), nw.end(), [&](const LeafId& a, const LeafId& b) { return zorder(a, lmax) < zorder(b, lmax); });
+  // how each new leaf gets its values (old blocks)
+  const int nn = (int)nw.size();
+  std::vector<Xfer> xf(nn);
+  for (int n = 0; n < nn; ++n) {
+    Xfer& X = xf[n];
+    X.l = nw[n].l;
+    X.x = nw[n].x;
+    X.y = nw[n].y;
+    auto it = where.find(leaf_key(X.l, X.x, X.y));
+    if (it != where.end()) {
+      X.kind = 0;
+      X.src[0] = tu.leaf_blk[it->second];
+      continue;
+    }
+    auto ip = X.l > 1 ? where.find(leaf_key(X.l - 1, X.x >> 1, X.y >> 1)) : where.end();
+    if (ip != where.end()) {
+      X.kind = 1;
+      X.src[0] = tu.leaf_blk[ip->second];
+      continue;
+    }
+    X.kind = 2;
+    for (int q = 0; q < 4; ++q) {
+      auto ic = where.find(leaf_key(X.l + 1, 2 * X.x + (q & 1), 2 * X.y + (q >> 1)));
+      if (ic == where.end()) return h->fail(AMR_ERR_CUDA, "regrid: a merged parent lost a child");
+      X.src[q] = tu.leaf_blk[ic->second];
+    }
+  }
+  Buf d_xf, nu, nv;
+  if (d_xf.alloc(nn * sizeof(Xfer)) != cudaSuccess || nu.alloc((size_t)nn * nt * 8) != cudaSuccess ||
+      nv.alloc((size_t)nn * nt * 8) != cudaSuccess)
+    return h->fail(AMR_ERR_OOM, "alloc");
+  cudaMemcpyAsync(d_xf.p, xf.data(), nn * sizeof(Xfer), cudaMemcpyHostToDevice, h->stream);
+  transfer_kernel<<<(unsigned)nn, nt, 0, h->stream>>>(tu.T, d_xf.as<Xfer>(), nu.as<double>());
+  transfer_kernel<<<(unsigned)nn, nt, 0, h->stream>>>(tv.T, d_xf.as<Xfer>(), nv.as<double>());
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return h->fail(AMR_ERR_CUDA, "transfer");
+  const long long kept = tu.launches + tv.launches + extra;
+  // rebuild the trees for the new leaves and move the fields in
+  std::vector<int> lv(nn), cd(2 * nn);
+  for (int n = 0; n < nn; ++n) {
+    lv[n] = nw[n].l;
+    cd[2 * n] = nw[n].x;
+    cd[2 * n + 1] = nw[n].y;
+  }
+  if (int rc = rdt_build(h, nn, lv.data(), cd.data())) return rc;
+  h->tu->launches = kept;  // the count carries over
+  cudaMemcpyAsync(h->d_u.p, nu.p, (size_t)nn * nt * 8, cudaMemcpyDeviceToDevice, h->stream);
+  cudaMemcpyAsync(h->d_v.p, nv.p, (size_t)nn * nt * 8, cudaMemcpyDeviceToDevice, h->stream);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return h->fail(AMR_ERR_CUDA, "regrid");
+  if (nleaves_out) *nleaves_out = nn;
+  return AMR_OK;
 }
 
 int rdt_kernel_launches(const rdt_handle* h, long long* n) {

@@ -128,3 +128,50 @@ def test_gray_scott_tree_keeps_the_homogeneous_state():
     cyc = s.step(2)
     u, v = s.read_state()
     assert np.array_equal(u, np.ones(n)) and np.array_equal(v, np.zeros(n)) and np.all(cyc == 0)
+
+
+# ------------------------------------------------------------- regrid of the RD tree --
+@pytest.mark.parametrize("seed", [7, 8])
+def test_regrid_matches_oracle(seed):
+    """Estimator, new tree and moved fields against the oracle: the tree bit for bit."""
+    from paper_2004_03275_gb300 import inputs
+    nb, B, L = 4, 8, 2.0
+    lev, crd3 = random_balanced_tree(2, [nb, nb, 1], 3, np.random.default_rng(seed), 6)
+    crd = crd3[:, :2]
+    X, Y = inputs.leaf_cell_centres(lev, crd, nb, B, L)
+    u, v = inputs.gray_scott_gaussians(X, Y, centres=((0.6, 1.3), (1.5, 0.4)))
+    s = amrvac.TreeRdSolver(lev, crd, nb, B, L, Du=2e-5, Dv=1e-5, F=0.046, k=0.063, dt=0.5)
+    s.set_state(u.ravel(), v.ravel())
+    err = s.regrid(refine_tol=0.05, coarsen_frac=0.5, max_level=3)
+    nl, nc, nu, nv, eo = O.amg_regrid(lev, crd, u, v, nb, B, L, refine_tol=0.05, coarsen_frac=0.5, max_level=3)
+    assert np.array_equal(err, eo)
+    gl, gc = s.leaves()
+    assert np.array_equal(gl, nl) and np.array_equal(gc, nc)
+    ug, vg = s.read_state()
+    assert np.max(np.abs(ug - nu.ravel())) <= 1e-15 and np.max(np.abs(vg - nv.ravel())) <= 1e-15
+
+
+def test_gray_scott_with_regrids_matches_oracle():
+    """Steps and regrids alternate on the paper's mesh (4^2 base blocks): leaves and fields
+    against the oracle after two rounds."""
+    from paper_2004_03275_gb300 import inputs
+    nb, B, L = 4, 8, 2.0
+    p = dict(Du=2e-5, Dv=1e-5, F=0.046, k=0.063, dt=0.5)
+    lev, crd = inputs.gray_scott_tree(nb=nb, L=L, radii=(0.5, 0.25))
+    X, Y = inputs.leaf_cell_centres(lev, crd, nb, B, L)
+    u, v = inputs.gray_scott_gaussians(X, Y)
+    s = amrvac.TreeRdSolver(lev, crd, nb, B, L, **p)
+    s.set_state(u.ravel(), v.ravel())
+    uo, vo, lo, co = u.ravel(), v.ravel(), lev, crd
+    for _ in range(2):
+        s.step(3)
+        for _ in range(3):
+            uo, vo, _ = O.amg_rd_step(lo, co, uo, vo, nb, B, L, **p)
+        s.regrid(refine_tol=0.02)
+        lo, co, uo, vo, _ = O.amg_regrid(lo, co, uo.reshape(len(lo), -1), vo.reshape(len(lo), -1), nb, B, L,
+                                         refine_tol=0.02)
+        uo, vo = uo.ravel(), vo.ravel()
+    gl, gc = s.leaves()
+    assert np.array_equal(gl, lo) and np.array_equal(gc, co)
+    ug, vg = s.read_state()
+    assert np.max(np.abs(ug - uo)) <= 1e-11 and np.max(np.abs(vg - vo)) <= 1e-11
