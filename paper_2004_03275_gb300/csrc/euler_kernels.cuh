@@ -776,6 +776,13 @@ struct ReduceShape {
   static constexpr int LPB = 256 / TPL;
 };
 
+// error-free sum a + b = s + e (TwoSum, Knuth), accumulated into the pair (hi, lo)
+__device__ __forceinline__ void twosum_acc(float& hi, float& lo, float x) {
+  const float s = hi + x, bb = s - hi;
+  lo += (hi - (s - bb)) + (x - bb);
+  hi = s;
+}
+
 template <typename real, int ND, int B>
 __global__ void __launch_bounds__(256) reduce_kernel(const real* __restrict__ U, const int* __restrict__ level,
                                                      Geometry G, DevCtl* ctl, double* partials, double* gpart,
@@ -796,16 +803,27 @@ __global__ void __launch_bounds__(256) reduce_kernel(const real* __restrict__ U,
     real dx[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) dx[d] = geo_dx<real>(G, lev, d);
+    // float32 state: per-thread sums as float-float pairs (TwoSum), widened once per thread,
+    // so the float64 pipe (GB300's scarcest) is not touched per cell; float64 state: plain sums
+    float hi[NV], lo[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) hi[v] = lo[v] = 0.f;
     for (int c = tc; c < NC; c += TPL) {
       real Uc[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) Uc[v] = U[((size_t)leaf * NV + v) * NC + c];
       rate = fmax(rate, cell_rate<real, ND>(Uc, gam, gm1, dx, &bad));
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sums[v] += (double)Uc[v];
+      for (int v = 0; v < NV; ++v) {
+        if constexpr (sizeof(real) == 4) twosum_acc(hi[v], lo[v], Uc[v]);
+        else sums[v] += (double)Uc[v];
+      }
     }
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sums[v] *= G.dV[lev];  // one cell volume per leaf
+    for (int v = 0; v < NV; ++v) {
+      if constexpr (sizeof(real) == 4) sums[v] = (double)hi[v] + (double)lo[v];
+      sums[v] *= G.dV[lev];  // one cell volume per leaf
+    }
   }
   block_reduce_finish<real, NV, 256>(rate, sums, blockIdx.x * LPB, LPB, lb, G, ctl, partials, gpart, gcount,
                                      nleaves, advance != 0, dt, bad);
@@ -820,10 +838,10 @@ template <typename real, int ND, int B>
 __global__ void ghost_fill_kernel(const real* __restrict__ U, real* __restrict__ slabs,
                                   const SlabDesc* __restrict__ desc, int nslabs) {
   constexpr int NV = ND + 2, NC = Tile<ND, B>::NC, NT = Tile<ND, B>::NT;
-  // 2 NT threads per slab.  Restriction slabs: one thread per (layer, tangential cell).
-  // Prolongation slabs: the first NT / 2^(ND-1) threads, one per coarse face cell, each
-  // writing the 2 layers x 2^(ND-1) fine ghost cells that share its coarse value, inner
-  // restriction and slopes.  The geometry is shared by the variables.
+  // 2 NT threads per slab.  Restriction slabs: one thread per (layer, tangential cell), the
+  // variables unrolled so that their loads are in flight together.  Prolongation slabs: one
+  // thread per (coarse face cell, variable), each writing the 2 layers x 2^(ND-1) fine ghost
+  // cells that share its coarse value, inner restriction and slopes.
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= nslabs * 2 * NT) return;
   const int q = gid % (2 * NT);
@@ -843,7 +861,7 @@ __global__ void ghost_fill_kernel(const real* __restrict__ U, real* __restrict__
     if (e2 >= 0) tl[e2] = t / B;
     int q1 = e1 >= 0 ? tl[e1] / (B / 2) : 0, q2 = e2 >= 0 ? tl[e2] / (B / 2) : 0;
     int F = D.src[q1 + 2 * q2];
-#pragma unroll 1
+#pragma unroll
     for (int v = 0; v < NV; ++v) {
       real sum = real(0);
       for (int o = 0; o < (1 << ND); ++o) {
@@ -861,8 +879,13 @@ __global__ void ghost_fill_kernel(const real* __restrict__ U, real* __restrict__
   }
   // prolongation: coarse face cell (c1, c2) in the target's tangential half-resolution grid
   constexpr int HB = B / 2, NCC = ND == 1 ? 1 : (ND == 2 ? HB : HB * HB);
-  if (q >= NCC) return;
-  const int c1 = ND >= 2 ? q % HB : 0, c2 = ND == 3 ? q / HB : 0;
+  // one thread per (coarse face cell, variable) where the slab's threads suffice (2D, 3D);
+  // in 1D one thread per coarse face cell loops over the variables
+  constexpr bool PERVAR = NCC * NV <= 2 * NT;
+  if (q >= (PERVAR ? NCC * NV : NCC)) return;
+  const int qc = q % NCC;
+  const int v0 = PERVAR ? q / NCC : 0, v1 = PERVAR ? v0 + 1 : NV;
+  const int c1 = ND >= 2 ? qc % HB : 0, c2 = ND == 3 ? qc / HB : 0;
   const int Cl = D.src[0];
   int p[3] = {0, 0, 0}, cc[3] = {0, 0, 0};  // coarse cell; the target's coarse-cell index per direction
   if (e1 >= 0) cc[e1] = c1;
@@ -871,8 +894,7 @@ __global__ void ghost_fill_kernel(const real* __restrict__ U, real* __restrict__
     if (e == d) p[e] = side == 0 ? B - 1 : 0;
     else p[e] = ((e == e1) ? D.off[0] : D.off[1]) + cc[e];
   }
-#pragma unroll 1
-  for (int v = 0; v < NV; ++v) {
+  for (int v = v0; v < v1; ++v) {
     auto cval = [&](const int* c) { return U[((size_t)Cl * NV + v) * NC + c[0] + B * (c[1] + B * c[2])]; };
     const real qp = cval(p);
     // restriction of the target's fine cells next to the face (normal inner neighbour)
