@@ -273,6 +273,21 @@ cudaError_t EulerOps<real, ND>::reflux(int B, real* out, const real* fflux, cons
 #undef CALL
 }
 
+// shared memory of the staged estimator for the selected variables, 0 where it does not apply
+// (1D, or more than 200 KB)
+template <int ND, int B>
+size_t lohner_tile_smem(unsigned mask) {
+  if constexpr (ND < 2) {
+    return 0;
+  } else {
+    int nsel = 0;
+    for (int v = 0; v < ND + 2; ++v) nsel += (mask >> v) & 1u;
+    size_t pt = ND == 2 ? (size_t)(B + 2) * (B + 2) : (size_t)(B + 2) * (B + 2) * (B + 2);
+    size_t bytes = (size_t)nsel * pt * sizeof(double);
+    return nsel > 0 && bytes <= 200 * 1024 ? bytes : 0;
+  }
+}
+
 template <typename real, int ND>
 cudaError_t EulerOps<real, ND>::lohner(int B, const real* U, const real* slabs, const int* nb, double gamma,
                                        double eps, unsigned mask, double* err, int nleaves, cudaStream_t s) {
@@ -281,6 +296,16 @@ cudaError_t EulerOps<real, ND>::lohner(int B, const real* U, const real* slabs, 
   ([&]() {                                                                                         \
     constexpr int NC = Tile<ND, BB>::NC;                                                           \
     constexpr int LPB = NC >= 256 ? 1 : 256 / NC;                                                  \
+    const size_t smem = lohner_tile_smem<ND, BB>(mask);                                            \
+    if constexpr (ND >= 2) if (smem > 0) {                                                         \
+      if (smem > 48 * 1024) {                                                                      \
+        cudaError_t e = cudaFuncSetAttribute(lohner_tile_kernel<real, ND, BB>,                     \
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                            \
+      }                                                                                            \
+      lohner_tile_kernel<real, ND, BB><<<nleaves, 256, smem, s>>>(U, slabs, nb, gamma, eps, mask, err, nleaves); \
+      return cudaGetLastError();                                                                   \
+    }                                                                                              \
     lohner_kernel<real, ND, BB><<<(nleaves + LPB - 1) / LPB, 256, 0, s>>>(U, slabs, nb, gamma, eps, mask, err, \
                                                                          nleaves);                 \
     return cudaGetLastError();                                                                     \

@@ -127,12 +127,16 @@ def test_amr_steps_parity_and_conservation(ndim, bnx, flux):
     assert np.all(np.abs(tg - t0) <= 5e-13 * np.maximum(np.abs(t0), 1.0)), (t0, tg)
 
 
-@pytest.mark.parametrize("ndim", [2, 3])
-def test_estimator_bit_exact(ndim):
+@pytest.mark.parametrize("ndim,bnx,allvars", [(2, 8, False), (3, 8, False), (3, 16, False), (2, 16, True),
+                                              (3, 8, True), (3, 16, True)])
+def test_estimator_bit_exact(ndim, bnx, allvars):
+    """The staged estimator (primitive values in a shared tile; 2D and 3D) and the per-cell one
+    (3D 16^3 with all five variables, whose tile would not fit) against the oracle."""
     rng = np.random.default_rng(60 + ndim)
     base = [2] * ndim + [1] * (3 - ndim)
     lev, crd = random_balanced_tree(ndim, base, 3, rng, 4)
-    s, g, kw = make_pair(ndim, 8, base, 3, lev, crd, var_mask=1 | (1 << (ndim + 1)))
+    mask = (1 << (ndim + 2)) - 1 if allvars else 1 | (1 << (ndim + 1))
+    s, g, kw = make_pair(ndim, bnx, base, 3, lev, crd, var_mask=mask)
     l2, c2 = s.leaves()
     x, _ = centres_for(l2, c2, kw)
     V = smooth_state(x, ndim, seed=2)
