@@ -364,6 +364,12 @@ def _bind_cnn(L):
     L.orc_cnn_forward.argtypes = [C.c_int, _dp, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp]
     L.orc_cnn_loss_grad.argtypes = [C.c_int, _dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp]
     L.orc_cnn_loss_grad.restype = C.c_double
+    L.orc_cnn_loss_grad_kind.argtypes = [C.c_int, _dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _dp,
+                                         _dp, _dp, _dp]
+    L.orc_cnn_loss_grad_kind.restype = C.c_double
+    L.orc_cnn_output_loss.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp,
+                                      _dp]
+    L.orc_cnn_output_loss.restype = C.c_double
     L.orc_cnn_adam.argtypes = [C.c_longlong, _dp, _dp, _dp, _dp, C.c_int, C.c_double, C.c_double, C.c_double,
                                C.c_double]
     L.orc_gelu.argtypes = [C.c_double]
@@ -395,12 +401,34 @@ def cnn_forward(params, x, ndim=2):
     return out
 
 
-def cnn_loss_grad(params, x, target, margin=0, ndim=2):
+CNN_LOSS = {"mse": 0, "operator": 1}
+
+
+def cnn_loss_grad(params, x, target, margin=0, ndim=2, loss="mse", kappa=(0.0, 0.0)):
+    """Loss and its gradient over the flat parameters.  loss="operator": the mean of q^2,
+    q = (1 + kappa_c) e - (1/(2 ndim)) sum_faces e, e = out - target (margin >= 1)."""
     x, N, D, H, W = _shape(x, ndim)
     target = _f64(target)
     g = np.zeros(cnn_num_params(ndim))
-    loss = lib().orc_cnn_loss_grad(ndim, _d(_f64(params)), N, D, H, W, margin, _d(x), _d(target), _d(g))
-    return loss, g
+    kap = _f64(np.asarray(kappa, dtype=np.float64).reshape(2))
+    val = lib().orc_cnn_loss_grad_kind(ndim, _d(_f64(params)), N, D, H, W, margin, CNN_LOSS[loss], _d(kap), _d(x),
+                                       _d(target), _d(g))
+    if val < 0:
+        raise ValueError("the operator-weighted loss needs margin >= 1")
+    return val, g
+
+
+def cnn_output_loss(out, target, margin=0, ndim=2, loss="mse", kappa=(0.0, 0.0)):
+    """The loss alone on network outputs [N][2][...]: (loss, dL/d(out))."""
+    out, N, D, H, W = _shape(out, ndim)
+    target = _f64(target)
+    dout = np.zeros_like(out)
+    kap = _f64(np.asarray(kappa, dtype=np.float64).reshape(2))
+    val = lib().orc_cnn_output_loss(ndim, N, D, H, W, margin, CNN_LOSS[loss], _d(kap), _d(out), _d(target),
+                                    _d(dout))
+    if val < 0:
+        raise ValueError("the operator-weighted loss needs margin >= 1")
+    return val, dout
 
 
 def cnn_adam(params, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):

@@ -10,6 +10,14 @@
 //    offsets -1, 0, 1 per dimension) followed by b[cout];
 //  * loss = mean over channels and over pixels at least `margin` cells away
 //    from every image edge of (out - target)^2;
+//  * or, the operator-weighted loss: the same mean of q^2 with
+//    q = (1 + kappa_c) e - (1/(2 ndim)) * (sum of e over the 2 ndim face
+//    neighbours), e = out - target, kappa_c per output channel.  This is the
+//    residual of the guess under the diagonal-normalised Helmholtz operator
+//    (lambda - lap_h) * h^2 / (2 ndim) of Eq. (diff-helmholtz) with kappa =
+//    lambda h^2 / (2 ndim): for a guess X = w_n + s * out and the converged
+//    solution w* = w_n + s * target, lambda g - A X = s (2 ndim / h^2) q.
+//    It needs margin >= 1 (the neighbours of counted pixels lie in the image);
 //  * Adam with bias correction.
 #include <cmath>
 #include <cstring>
@@ -101,34 +109,93 @@ void orc_cnn_forward(int ndim, const double* params, int N, int D, int H, int W,
   std::memcpy(out, A.x[4].data(), A.x[4].size() * sizeof(double));
 }
 
-// loss and gradient of the masked MSE with respect to every parameter
-double orc_cnn_loss_grad(int ndim, const double* params, int N, int D, int H, int W, int margin, const double* in,
-                         const double* target, double* grad) {
-  Shape s{ndim, N, ndim == 3 ? D : 1, H, W};
+}  // extern "C"
+
+namespace {
+
+// masked loss of the network output and its derivative dL/d(out); kind 0 = MSE,
+// kind 1 = operator-weighted (kappa[2] per output channel); margin >= 1 for kind 1
+double output_loss(const Shape& s, int margin, int kind, const double* kappa, const double* out,
+                   const double* target, double* dout) {
   long long P = s.npix();
-  int T = ntaps(ndim);
-  Acts A;
-  forward(s, params, in, A);
+  const int C = kCh[4];
   long long count = 0;
   for (int k = 0; k < s.D; ++k)
     for (int j = 0; j < s.H; ++j)
       for (int i = 0; i < s.W; ++i)
         if (in_mask(s, k, j, i, margin)) ++count;
-  count *= (long long)s.N * kCh[4];
+  count *= (long long)s.N * C;
+  size_t n_all = (size_t)s.N * C * P;
+  for (size_t o = 0; o < n_all; ++o) dout[o] = 0.0;
   double loss = 0.0;
-  std::vector<double> dz((size_t)s.N * kCh[4] * P, 0.0);  // dL/dz of the current layer
+  if (kind == 0) {
+    for (int n = 0; n < s.N; ++n)
+      for (int c = 0; c < C; ++c)
+        for (int k = 0; k < s.D; ++k)
+          for (int j = 0; j < s.H; ++j)
+            for (int i = 0; i < s.W; ++i) {
+              if (!in_mask(s, k, j, i, margin)) continue;
+              size_t o = ((size_t)n * C + c) * P + ((long long)k * s.H + j) * s.W + i;
+              double d = out[o] - target[o];
+              loss += d * d;
+              dout[o] = 2.0 * d / (double)count;
+            }
+    return loss / (double)count;
+  }
+  // operator-weighted: q on the counted pixels, then dL/d(out) = (2/count) A^T q
+  // (the normalised operator is symmetric), neighbours by plain index offsets
+  const double nb_w = 1.0 / (2.0 * s.nd);
+  auto e_at = [&](size_t base, int k, int j, int i) {
+    size_t o = base + ((long long)k * s.H + j) * s.W + i;
+    return out[o] - target[o];
+  };
+  std::vector<double> q(n_all, 0.0);
   for (int n = 0; n < s.N; ++n)
-    for (int c = 0; c < kCh[4]; ++c)
+    for (int c = 0; c < C; ++c) {
+      size_t base = ((size_t)n * C + c) * P;
       for (int k = 0; k < s.D; ++k)
         for (int j = 0; j < s.H; ++j)
           for (int i = 0; i < s.W; ++i) {
             if (!in_mask(s, k, j, i, margin)) continue;
-            size_t o = ((size_t)n * kCh[4] + c) * P + ((long long)k * s.H + j) * s.W + i;
-            double d = A.x[4][o] - target[o];
-            loss += d * d;
-            dz[o] = 2.0 * d / (double)count;
+            double nb = e_at(base, k, j, i - 1) + e_at(base, k, j, i + 1) + e_at(base, k, j - 1, i) +
+                        e_at(base, k, j + 1, i);
+            if (s.nd == 3) nb += e_at(base, k - 1, j, i) + e_at(base, k + 1, j, i);
+            double qv = (1.0 + kappa[c]) * e_at(base, k, j, i) - nb_w * nb;
+            q[base + ((long long)k * s.H + j) * s.W + i] = qv;
+            loss += qv * qv;
           }
-  loss /= (double)count;
+    }
+  for (int n = 0; n < s.N; ++n)
+    for (int c = 0; c < C; ++c) {
+      size_t base = ((size_t)n * C + c) * P;
+      for (int k = 0; k < s.D; ++k)
+        for (int j = 0; j < s.H; ++j)
+          for (int i = 0; i < s.W; ++i) {
+            size_t o = base + ((long long)k * s.H + j) * s.W + i;
+            // q is zero off the mask, and every pixel next to the mask lies in the image
+            double g = (1.0 + kappa[c]) * q[o];
+            if (i > 0) g -= nb_w * q[o - 1];
+            if (i < s.W - 1) g -= nb_w * q[o + 1];
+            if (j > 0) g -= nb_w * q[o - s.W];
+            if (j < s.H - 1) g -= nb_w * q[o + s.W];
+            if (s.nd == 3 && k > 0) g -= nb_w * q[o - (size_t)s.H * s.W];
+            if (s.nd == 3 && k < s.D - 1) g -= nb_w * q[o + (size_t)s.H * s.W];
+            dout[o] = 2.0 * g / (double)count;
+          }
+    }
+  return loss / (double)count;
+}
+
+// loss and gradient of the masked loss with respect to every parameter
+double loss_grad(int ndim, const double* params, int N, int D, int H, int W, int margin, int kind,
+                 const double* kappa, const double* in, const double* target, double* grad) {
+  Shape s{ndim, N, ndim == 3 ? D : 1, H, W};
+  long long P = s.npix();
+  int T = ntaps(ndim);
+  Acts A;
+  forward(s, params, in, A);
+  std::vector<double> dz((size_t)s.N * kCh[4] * P, 0.0);  // dL/dz of the current layer
+  double loss = output_loss(s, margin, kind, kappa, A.x[4].data(), target, dz.data());
   std::memset(grad, 0, sizeof(double) * layer_offset(ndim, 4));
   for (int l = 3; l >= 0; --l) {
     int cin = kCh[l], cout = kCh[l + 1];
@@ -160,6 +227,31 @@ double orc_cnn_loss_grad(int ndim, const double* params, int N, int D, int H, in
     dz.swap(dx);
   }
   return loss;
+}
+
+}  // namespace
+
+extern "C" {
+
+// loss and gradient of the masked MSE with respect to every parameter
+double orc_cnn_loss_grad(int ndim, const double* params, int N, int D, int H, int W, int margin, const double* in,
+                         const double* target, double* grad) {
+  return loss_grad(ndim, params, N, D, H, W, margin, 0, nullptr, in, target, grad);
+}
+
+// the same for a loss kind (0 = MSE, 1 = operator-weighted with kappa[2]); negative = invalid
+double orc_cnn_loss_grad_kind(int ndim, const double* params, int N, int D, int H, int W, int margin, int kind,
+                              const double* kappa, const double* in, const double* target, double* grad) {
+  if (kind == 1 && margin < 1) return -1.0;
+  return loss_grad(ndim, params, N, D, H, W, margin, kind, kappa, in, target, grad);
+}
+
+// the loss alone, on given network outputs: returns it and writes dL/d(out)
+double orc_cnn_output_loss(int ndim, int N, int D, int H, int W, int margin, int kind, const double* kappa,
+                           const double* out, const double* target, double* dout) {
+  if (kind == 1 && margin < 1) return -1.0;
+  Shape s{ndim, N, ndim == 3 ? D : 1, H, W};
+  return output_loss(s, margin, kind, kappa, out, target, dout);
 }
 
 // one Adam step (bias-corrected), t = step number starting at 1

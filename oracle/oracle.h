@@ -183,6 +183,12 @@ void orc_cnn_forward(int ndim, const double* params, int N, int D, int H, int W,
 /* masked MSE (pixels at least `margin` from every edge) and its gradient; returns the loss */
 double orc_cnn_loss_grad(int ndim, const double* params, int N, int D, int H, int W, int margin, const double* in,
                          const double* target, double* grad);
+// kind 0 = the masked MSE above; kind 1 = operator-weighted (kappa[2] per output channel,
+// margin >= 1, else -1 is returned)
+double orc_cnn_loss_grad_kind(int ndim, const double* params, int N, int D, int H, int W, int margin, int kind,
+                              const double* kappa, const double* in, const double* target, double* grad);
+double orc_cnn_output_loss(int ndim, int N, int D, int H, int W, int margin, int kind, const double* kappa,
+                           const double* out, const double* target, double* dout);
 void orc_cnn_adam(long long n, double* params, const double* grad, double* m, double* v, int t, double lr,
                   double b1, double b2, double eps);
 double orc_gelu(double z);

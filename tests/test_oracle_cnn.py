@@ -108,3 +108,103 @@ def test_training_reduces_loss():
         loss, g = O.cnn_loss_grad(p, x, tgt)
         O.cnn_adam(p, g, m, v, t, lr=3e-3)
     assert O.cnn_loss_grad(p, x, tgt)[0] < 0.5 * l0
+
+
+# ---- operator-weighted loss: q = (1 + kappa) e - (1/(2 ndim)) sum_faces e, e = out - target ----
+
+def test_operator_loss_of_a_fourier_mode_closed_form():
+    """For e = cos(theta i + phi) along x, every counted pixel has q = (kappa + (1 - cos theta)/ndim) e:
+    the symbol of the normalised 5/7-point operator."""
+    rng = np.random.default_rng(21)
+    for ndim, shape in ((2, (1, 2, 6, 20)), (3, (1, 2, 5, 4, 12))):
+        W = shape[-1]
+        m, phi = 3, 0.4
+        theta = 2 * np.pi * m / W
+        i = np.arange(W)
+        e = np.broadcast_to(np.cos(theta * i + phi), shape).copy()
+        tgt = rng.normal(size=shape)
+        kappa = (0.25, 0.0625)
+        margin = 1
+        loss, _ = O.cnn_output_loss(tgt + e, tgt, margin=margin, ndim=ndim, loss="operator", kappa=kappa)
+        sl = (slice(None),) + tuple(slice(margin, n - margin) for n in shape[2:])
+        want = []
+        for c in range(2):
+            q = (kappa[c] + (1 - np.cos(theta)) / ndim) * e[:, c]
+            want.append(q[sl] ** 2)
+        want = np.mean(np.stack(want))
+        assert loss == pytest.approx(want, rel=1e-12)
+
+
+@pytest.mark.parametrize("ndim,n", [(2, 16), (3, 8)])
+def test_operator_loss_is_the_scaled_residual_of_the_guess(ndim, n):
+    """With target = (w* - w_n)/s and the guess X = w_n + s out, the multigrid oracle's own
+    operator gives lambda g - A X = A (w* - X) = s (2 ndim / h^2) q on every counted pixel, for
+    kappa = lambda h^2 / (2 ndim) per species."""
+    rng = np.random.default_rng(7 + ndim)
+    L, s = 2.5, 0.01
+    h = L / n
+    lams = (2.0 / (0.5 * 2e-5), 2.0 / (0.5 * 1e-5))
+    shape = (n,) * ndim
+    wn = rng.uniform(0.2, 1.0, size=(2,) + shape)
+    ws = wn + s * rng.normal(size=(2,) + shape)
+    out = rng.normal(size=(2,) + shape)
+    tgt = (ws - wn) / s
+    kappa = [lam * h * h / (2 * ndim) for lam in lams]
+    margin = 1
+    loss, _ = O.cnn_output_loss(out[None], tgt[None], margin=margin, ndim=ndim, loss="operator", kappa=kappa)
+    sl = tuple(slice(margin, n - margin) for _ in range(ndim))
+    terms = []
+    for c in range(2):
+        X = wn[c] + s * out[c]
+        r = O.mg_apply(ws[c], L, lams[c]) - O.mg_apply(X, L, lams[c])
+        terms.append((r * h * h / (2 * ndim * s))[sl] ** 2)
+    assert loss == pytest.approx(np.mean(np.stack(terms)), rel=1e-9)
+
+
+def test_operator_loss_tends_to_mse_for_large_kappa():
+    rng = np.random.default_rng(4)
+    out, tgt = rng.normal(size=(2, 2, 9, 11)), rng.normal(size=(2, 2, 9, 11))
+    k = 1e7
+    lo, go = O.cnn_output_loss(out, tgt, margin=2, loss="operator", kappa=(k, k))
+    lm, gm = O.cnn_output_loss(out, tgt, margin=2, loss="mse")
+    assert lo / (1 + k) ** 2 == pytest.approx(lm, rel=1e-6)
+    assert np.max(np.abs(go / (1 + k) ** 2 - gm)) <= 1e-6 * np.max(np.abs(gm))
+    with pytest.raises(ValueError):
+        O.cnn_output_loss(out, tgt, margin=0, loss="operator", kappa=(k, k))
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_operator_loss_output_gradient_matches_finite_differences(ndim):
+    rng = np.random.default_rng(30 + ndim)
+    shape = (2, 2, 7, 9) if ndim == 2 else (1, 2, 5, 6, 7)
+    out, tgt = rng.normal(size=shape), rng.normal(size=shape)
+    kappa = (0.3, 0.07)
+    _, g = O.cnn_output_loss(out, tgt, margin=1, ndim=ndim, loss="operator", kappa=kappa)
+    flat = out.reshape(-1)
+    h = 1e-2  # the loss is quadratic in the outputs: central differences are exact up to rounding
+    for i in rng.choice(flat.size, size=60, replace=False).tolist() + [0, flat.size - 1]:
+        op, om = flat.copy(), flat.copy()
+        op[i] += h
+        om[i] -= h
+        fp = O.cnn_output_loss(op.reshape(shape), tgt, margin=1, ndim=ndim, loss="operator", kappa=kappa)[0]
+        fm = O.cnn_output_loss(om.reshape(shape), tgt, margin=1, ndim=ndim, loss="operator", kappa=kappa)[0]
+        fd = (fp - fm) / (2 * h)
+        assert abs(fd - g.reshape(-1)[i]) <= 1e-10, (i, fd, g.reshape(-1)[i])
+
+
+@pytest.mark.parametrize("ndim,shape", [(2, (1, 5, 10, 10)), (3, (1, 5, 6, 6, 6))])
+def test_operator_loss_parameter_gradient_matches_finite_differences(ndim, shape):
+    rng = np.random.default_rng(40 + ndim)
+    p = rand_params(ndim, rng)
+    x = rng.uniform(0, 1, size=shape)
+    tgt = rng.normal(size=(shape[0], 2) + shape[2:]) * 0.1
+    kw = dict(margin=2, ndim=ndim, loss="operator", kappa=(0.15, 0.075))
+    _, g = O.cnn_loss_grad(p, x, tgt, **kw)
+    idx = np.unique(np.concatenate([rng.choice(len(p), size=60, replace=False), np.arange(len(p) - 2, len(p))]))
+    h = 1e-6
+    for i in idx:
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (O.cnn_loss_grad(pp, x, tgt, **kw)[0] - O.cnn_loss_grad(pm, x, tgt, **kw)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(abs(fd), abs(g[i])) + 1e-11, (i, fd, g[i])
