@@ -218,61 +218,78 @@ def bench_gray_scott(torch, amrvac, stream, steps=5):
     return out
 
 
+def _train_guess(torch, amrvac, LG, X, Y, ndim, loss, kappa, iters, batch):
+    """One network trained with `loss`; the training-set loss of the zero output (the
+    previous-step guess), of the initial network and of the trained one."""
+    margin = LG.MARGIN[loss]
+    zero = amrvac.CnnNet(ndim=ndim, seed=3)
+    zero.set_params(np.zeros(zero.nparams, dtype=np.float32))
+    zero.set_loss(loss, kappa)
+    loss_zero = LG.dataset_loss(torch, zero, X, Y, margin=margin)
+    zero.close()
+    net = amrvac.CnnNet(ndim=ndim, seed=3)
+    net.set_loss(loss, kappa)
+    loss0 = LG.dataset_loss(torch, net, X, Y, margin=margin)
+    _, train_s = LG.train(torch, net, X, Y, iters=iters, batch=batch, lr=1e-3, margin=margin)
+    loss1 = LG.dataset_loss(torch, net, X, Y, margin=margin)
+    return net, {"training_set_loss_zero_output_initial_trained": [loss_zero, loss0, loss1],
+                 "train_s": round(train_s, 2)}
+
+
 def bench_learned_guess(torch, amrvac, stream, eval_steps=6):
-    """Config 5 (2D): train the learned multigrid guess on 256^2 runs with the stiffness of the 2048^2
-    grid (seeds 0, 1), evaluate at 2048^2 on seed 10000 against the previous-step guess."""
+    """Config 5 (2D): learned multigrid guesses trained on crops of 2048^2 runs (training seeds 0, 1),
+    evaluated at 2048^2 on seed 10000 against the previous-step guess.  Two networks:
+    * residual inputs (the normalised residual of the previous-step guess) trained on the
+      operator-weighted loss (the guess's own residual);
+    * (u*_prev, v*_prev) inputs trained on the masked MSE of the increment."""
     from paper_2004_03275_gb300 import learned_guess as LG
-    n = 256
-    L = LG.domain_for(n)
-    t0 = time.perf_counter()
-    X, Y, scale = LG.generate(torch, [n, n], [0, 1], L, steps=24, crops_per_step=48, crop=64, warm=40)
-    net = amrvac.CnnNet(ndim=2, seed=3)
-    loss0 = LG.dataset_loss(torch, net, X, Y)
-    losses, train_s = LG.train(torch, net, X, Y, iters=1500, batch=64, lr=1e-3)
-    loss1 = LG.dataset_loss(torch, net, X, Y)
-    prep = time.perf_counter() - t0
-    c0, t0s, _, r0 = LG.evaluate(torch, [2048], [10000], 2.5, steps=eval_steps, warm=40)
-    c1, t1s, _, r1 = LG.evaluate(torch, [2048], [10000], 2.5, steps=eval_steps, warm=40, net=net, scale=scale)
+    n, L = 2048, 2.5
+    kappa = LG.operator_kappa(n, L, ndim=2)
+    c0, t0s, _, r0 = LG.evaluate(torch, [n], [10000], L, steps=eval_steps, warm=40)
     out = {"workload": "Gray-Scott IMEX 2048^2 (seed 10000, after 40 warm-up steps), MG rtol 1e-10",
-           "training": f"{X.shape[0]} crops 64^2 from 256^2 runs (seeds 0,1, stiffness-matched domain), "
-                       f"1500 Adam steps, batch 64, {train_s:.1f}s; data+training {prep:.1f}s",
-           "training_set_loss_before_after": [loss0, loss1],
+           "training_data": "crops 64^2 after each of 24 steps of two 2048^2 runs (seeds 0, 1; 40 warm-up steps), "
+                            "48 crops per step",
            "vcycles_per_solve_previous_step_guess": float(np.mean(c0)),
-           "vcycles_per_solve_learned_guess": float(np.mean(c1)),
            "initial_rel_residual_median_previous_step": float(np.median(r0)),
-           "initial_rel_residual_median_learned": float(np.median(r1)),
-           "ms_per_step_previous_step_guess": t0s * 1e3, "ms_per_step_learned_guess": t1s * 1e3,
-           "cnn_launches": net.kernel_launches()}
-    net.close()
+           "ms_per_step_previous_step_guess": t0s * 1e3, "operator_kappa": [round(k, 5) for k in kappa]}
+    for inp, loss, iters in (("residual", "operator", 5000), ("prev", "mse", 1500)):
+        t0 = time.perf_counter()
+        X, Y, scale = LG.generate(torch, [n, n], [0, 1], L, steps=24, crops_per_step=48, crop=64, warm=40,
+                                  inputs=inp)
+        gen_s = time.perf_counter() - t0
+        net, info = _train_guess(torch, amrvac, LG, X, Y, 2, loss, kappa, iters=iters, batch=64)
+        c1, t1s, _, r1 = LG.evaluate(torch, [n], [10000], L, steps=eval_steps, warm=40, net=net, scale=scale,
+                                     inputs=inp)
+        info.update({"data_s": round(gen_s, 2), "adam_steps": iters, "batch": 64, "lr": 1e-3,
+                     "vcycles_per_solve": float(np.mean(c1)), "vcycles_per_solve_each": [int(x) for x in c1.ravel()],
+                     "initial_rel_residual_median": float(np.median(r1)), "ms_per_step": t1s * 1e3,
+                     "cnn_launches": net.kernel_launches()})
+        out[f"learned_{inp}_inputs_{loss}_loss"] = info
+        net.close()
+        del X, Y
     return out
 
 
 def bench_learned_guess_3d(torch, amrvac, stream, eval_steps=6):
-    """Config 5 (3D): train the learned guess on 64^3 runs with the stiffness of the 256^3 grid
-    (seeds 0, 1), evaluate at 256^3 on seed 10000 against the previous-step guess."""
+    """Config 5 (3D): the learned guess ((u*_prev, v*_prev) inputs, masked MSE) trained on crops of
+    256^3 runs (training seeds 0, 1), evaluated at 256^3 on seed 10000 against the previous-step guess."""
     from paper_2004_03275_gb300 import learned_guess as LG
-    n, N = 64, 256
-    L = LG.domain_for(n, ref_n=N, ref_L=2.5)
+    N, L = 256, 2.5
     t0 = time.perf_counter()
-    X, Y, scale = LG.generate(torch, [n, n], [0, 1], L, steps=16, crops_per_step=12, crop=32, warm=20, ndim=3)
-    net = amrvac.CnnNet(ndim=3, seed=3)
-    loss0 = LG.dataset_loss(torch, net, X, Y)
-    losses, train_s = LG.train(torch, net, X, Y, iters=600, batch=4, lr=1e-3)
-    loss1 = LG.dataset_loss(torch, net, X, Y)
-    prep = time.perf_counter() - t0
-    c0, t0s, _, r0 = LG.evaluate(torch, [N], [10000], 2.5, steps=eval_steps, warm=20, ndim=3)
-    c1, t1s, _, r1 = LG.evaluate(torch, [N], [10000], 2.5, steps=eval_steps, warm=20, net=net, scale=scale, ndim=3)
-    out = {"workload": "Gray-Scott IMEX 256^3 on [0,2.5]^3 (seed 10000, after 20 warm-up steps), MG rtol 1e-10",
-           "training": f"{X.shape[0]} crops 32^3 from 64^3 runs (seeds 0,1, stiffness-matched domain), "
-                       f"600 Adam steps, batch 4, {train_s:.1f}s; data+training {prep:.1f}s",
-           "training_set_loss_before_after": [loss0, loss1],
-           "vcycles_per_solve_previous_step_guess": float(np.mean(c0)),
-           "vcycles_per_solve_learned_guess": float(np.mean(c1)),
-           "initial_rel_residual_median_previous_step": float(np.median(r0)),
-           "initial_rel_residual_median_learned": float(np.median(r1)),
-           "ms_per_step_previous_step_guess": t0s * 1e3, "ms_per_step_learned_guess": t1s * 1e3}
+    X, Y, scale = LG.generate(torch, [N, N], [0, 1], L, steps=16, crops_per_step=12, crop=32, warm=20, ndim=3)
+    gen_s = time.perf_counter() - t0
+    c0, t0s, _, r0 = LG.evaluate(torch, [N], [10000], L, steps=eval_steps, warm=20, ndim=3)
+    net, info = _train_guess(torch, amrvac, LG, X, Y, 3, "mse", None, iters=600, batch=4)
+    c1, t1s, _, r1 = LG.evaluate(torch, [N], [10000], L, steps=eval_steps, warm=20, net=net, scale=scale, ndim=3)
     net.close()
-    return out
+    info.update({"vcycles_per_solve": float(np.mean(c1)), "initial_rel_residual_median": float(np.median(r1)),
+                 "ms_per_step": t1s * 1e3})
+    return {"workload": "Gray-Scott IMEX 256^3 on [0,2.5]^3 (seed 10000, after 20 warm-up steps), MG rtol 1e-10",
+            "training": f"{X.shape[0]} crops 32^3 after each of 16 steps of two 256^3 runs (seeds 0, 1), "
+                        f"{gen_s:.1f}s; 600 Adam steps, batch 4, lr 1e-3",
+            "vcycles_per_solve_previous_step_guess": float(np.mean(c0)),
+            "initial_rel_residual_median_previous_step": float(np.median(r0)),
+            "ms_per_step_previous_step_guess": t0s * 1e3, "learned_prev_inputs_mse_loss": info}
 
 
 # Algorithmic bytes per level-0 unknown per V-cycle of the float32 multigrid (nu1 = nu2 = 2, 2D):

@@ -385,9 +385,18 @@ int rdt_regrid(rdt_handle* h, double refine_tol, double coarsen_frac, double eps
  * dimension) followed by b[cout]; training keeps float32 master weights (Adam,
  * beta 0.9/0.999, eps 1e-8).  Images are device float32 [N][C][D][H][W]
  * (D = 1 in 2D); H and W multiples of 16 (2D) or D of 4 and H, W of 8 (3D).
- * Loss: mean over both output channels and over pixels at least `margin`
- * cells from every image edge of (out - target)^2.
+ * Loss (cnn_set_loss): mean over both output channels and over pixels at least
+ * `margin` cells from every image edge of (out - target)^2 (CNN_LOSS_MSE, the
+ * default), or of q^2 (CNN_LOSS_OPERATOR) with
+ *   q = (1 + kappa_c) e - (1/(2 ndim)) * sum of e over the 2 ndim face neighbours,
+ *   e = out - target.
+ * With target = (w* - w_n)/scale, q is the residual lambda g - A X of the guess
+ * X = w_n + scale * out under the Helmholtz operator A = lambda - lap_h of
+ * Eq. (diff-helmholtz), divided by scale * 2 ndim / h^2; kappa_c = lambda_c h^2 /
+ * (2 ndim) per species.  The operator loss needs margin >= 1.
  * ------------------------------------------------------------------------ */
+#define CNN_LOSS_MSE 0
+#define CNN_LOSS_OPERATOR 1
 typedef struct cnn_handle cnn_handle;
 
 /* He-normal initial weights from `seed`, zero biases; stream NULL = own stream. */
@@ -406,22 +415,37 @@ int cnn_gradient(cnn_handle* h, const float* in, const float* target, int N, int
 /* one Adam step on the batch; loss (host) if not NULL */
 int cnn_train_step(cnn_handle* h, const float* in, const float* target, int N, int D, int H, int W, int margin,
                    float lr, float* loss);
+/* Loss of the following cnn_gradient / cnn_train_step calls: kind CNN_LOSS_MSE or
+ * CNN_LOSS_OPERATOR; kappa (host, 2 values, finite, >= 0) is read for the operator
+ * loss only and may be NULL for MSE.  AMR_ERR_INVALID_ARG otherwise; a later
+ * gradient call with margin < 1 under the operator loss is AMR_ERR_INVALID_ARG. */
+int cnn_set_loss(cnn_handle* h, int kind, const double* kappa);
 int cnn_kernel_launches(const cnn_handle* h, long long* n);
 
 /* Multigrid initial guess of rd_step: net = NULL restores the previous-step
- * guess w_n; otherwise X = w_n + scale * net(u_n, v_n, u*_prev, v*_prev, dt)
- * per species (the network predicts the increment over the previous-step
+ * guess w_n; otherwise X = w_n + scale * net(u_n, v_n, c2, c3, dt) per species
+ * (c2, c3 as set by rd_set_guess_inputs) (the network predicts the increment over the previous-step
  * guess).  The multigrid still iterates to rtol.  The handle keeps a pointer to
  * net (not owned).  Sides must be multiples of 16 (2D) or 8 (3D). */
 int rd_set_guess(rd_handle* h, cnn_handle* net, double scale);
+/* Input channels 2 and 3 of the network, for rd_set_guess and rd_extract_crops:
+ * RD_GUESS_IN_PREV (default) = (u*_prev, v*_prev), the previous step's solution;
+ * RD_GUESS_IN_RESIDUAL = the residual of the previous-step guess, per species
+ * (lambda g - A w_n) * h^2 / (2 ndim) / scale, A = lambda - lap_h of
+ * Eq. (diff-helmholtz) with the handle's boundaries.  With target (w* - w_n)/scale
+ * the network's ideal map is then the local inverse of the normalised operator. */
+#define RD_GUESS_IN_PREV 0
+#define RD_GUESS_IN_RESIDUAL 1
+int rd_set_guess_inputs(rd_handle* h, int kind);
 /* Max-norm relative residuals max|b - A x| / max|b| of the initial guess and of
  * the final iterate of the last multigrid solve, per (species, instance):
  * initial[2*n_inst], final[2*n_inst] (host, either may be NULL). */
 int rd_last_residuals(rd_handle* h, double* initial, double* final_);
 /* Training pairs from the last rd_step: for crop k of side `crop` with lowest
  * corner corner[3k..3k+2] (periodic) in instance inst[k]: in[k] (device float
- * [5][crop^ndim]) = (u_n, v_n, u*_prev, v*_prev, dt) and target[k] (device float
- * [2][crop^ndim]) = (w* - w_n) / scale for u and v. */
+ * [5][crop^ndim]) = (u_n, v_n, c2, c3, dt), channels 2 and 3 as set by
+ * rd_set_guess_inputs, and target[k] (device float [2][crop^ndim]) =
+ * (w* - w_n) / scale for u and v. */
 int rd_extract_crops(rd_handle* h, int ncrops, const int* inst, const int* corner, int crop, double scale, float* in,
                      float* target);
 

@@ -125,8 +125,10 @@ _SIGS = {
                       C.POINTER(C.c_float)], C.c_int),
     "cnn_train_step": ([_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float,
                         C.POINTER(C.c_float)], C.c_int),
+    "cnn_set_loss": ([_vp, C.c_int, C.POINTER(C.c_double)], C.c_int),
     "cnn_kernel_launches": ([_vp, _llp], C.c_int),
     "rd_set_guess": ([_vp, _vp, C.c_double], C.c_int),
+    "rd_set_guess_inputs": ([_vp, C.c_int], C.c_int),
     "rd_last_residuals": ([_vp, _dp, _dp], C.c_int),
     "rd_extract_crops": ([_vp, C.c_int, _ip, _ip, C.c_int, C.c_double, _vp, _vp], C.c_int),
     "mg_kernel_launches": ([_vp, _llp], C.c_int),
@@ -505,8 +507,13 @@ class RdSolver:
         _check(self.lib.rd_read_state(self.h, pu, pv, du), self.h, "rd_last_error")
         return u, v
 
+    def set_guess_inputs(self, kind="prev"):
+        """Network input channels 2, 3: "prev" = (u*_prev, v*_prev); "residual" = the normalised
+        residual of the previous-step guess per species."""
+        _check(self.lib.rd_set_guess_inputs(self.h, {"prev": 0, "residual": 1}[kind]), self.h, "rd_last_error")
+
     def set_guess(self, net=None, scale=1.0):
-        """Multigrid initial guess: None -> previous-step guess w_n; a CnnNet -> g + scale * net(...)."""
+        """Multigrid initial guess: None -> previous-step guess w_n; a CnnNet -> w_n + scale * net(...)."""
         _check(self.lib.rd_set_guess(self.h, net.h if net is not None else None, scale), self.h, "rd_last_error")
         self._guess = net  # keep the network alive while the handle points to it
 
@@ -731,6 +738,14 @@ class CnnNet:
         _check(self.lib.cnn_train_step(self.h, x.data_ptr(), target.data_ptr(), N, D, H, W, margin, lr,
                                        C.byref(loss) if want_loss else None), self.h, "cnn_last_error")
         return loss.value if want_loss else None
+
+    def set_loss(self, kind="mse", kappa=None):
+        """kind "mse" or "operator" (kappa: two values, one per output channel)."""
+        k = {"mse": 0, "operator": 1}[kind]
+        arr = None
+        if kappa is not None:
+            arr = (C.c_double * 2)(*[float(v) for v in kappa])
+        _check(self.lib.cnn_set_loss(self.h, k, arr), self.h, "cnn_last_error")
 
     def kernel_launches(self):
         n = C.c_longlong()

@@ -262,6 +262,74 @@ __global__ void loss_grad_kernel(const float* __restrict__ out, const float* __r
   if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(loss, l * inv_count);
 }
 
+// operator-weighted loss, pass 1: q = (1 + kappa_c) e - (1/(2 ndim)) sum_faces e with
+// e = out - target on the counted pixels (zero elsewhere), and the loss sum of q^2.
+// The counted pixels lie at least one cell inside the image, so every neighbour exists.
+__global__ void op_q_kernel(const float* __restrict__ out, const float* __restrict__ target, float* __restrict__ q,
+                            float* loss, long long npix, int D, int H, int W, int margin, int ndim, float k0, float k1,
+                            float inv_count) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float l = 0.f;
+  if (i < npix) {
+    long long P = (long long)D * H * W;
+    long long n = i / P, p = i % P;
+    int x = (int)(p % W), y = (int)((p / W) % H), z = (int)(p / ((long long)W * H));
+    bool in = x >= margin && x < W - margin && y >= margin && y < H - margin &&
+              (ndim < 3 || (z >= margin && z < D - margin));
+    float qv[2] = {0.f, 0.f};
+    if (in) {
+      const long long HW = (long long)H * W;
+      const float nbw = ndim == 3 ? 1.f / 6.f : 0.25f;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const float* t = target + (n * 2 + c) * P;
+        auto e = [&](long long pp, long long ii) { return out[ii * 2 + c] - t[pp]; };
+        float nb = e(p - 1, i - 1) + e(p + 1, i + 1) + e(p - W, i - W) + e(p + W, i + W);
+        if (ndim == 3) nb += e(p - HW, i - HW) + e(p + HW, i + HW);
+        qv[c] = (1.f + (c ? k1 : k0)) * e(p, i) - nbw * nb;
+        l += qv[c] * qv[c];
+      }
+    }
+    reinterpret_cast<float2*>(q)[i] = make_float2(qv[0], qv[1]);
+  }
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(loss, l * inv_count);
+}
+
+// operator-weighted loss, pass 2: dL/dz of the output layer = (2 / count) A^T q, A the
+// normalised operator (symmetric); neighbours outside the image hold no q.
+__global__ void op_grad_kernel(const float* __restrict__ q, bf16* __restrict__ dz, long long npix, int D, int H, int W,
+                               int ndim, float k0, float k1, float inv_count) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npix) return;
+  long long P = (long long)D * H * W;
+  long long p = i % P;
+  int x = (int)(p % W), y = (int)((p / W) % H), z = (int)(p / ((long long)W * H));
+  const long long HW = (long long)H * W;
+  const float nbw = ndim == 3 ? 1.f / 6.f : 0.25f;
+  const float2* q2 = reinterpret_cast<const float2*>(q);
+  float2 c = q2[i];
+  float2 s = make_float2(0.f, 0.f);
+  auto add = [&](long long j) {
+    float2 v = q2[j];
+    s.x += v.x;
+    s.y += v.y;
+  };
+  if (x > 0) add(i - 1);
+  if (x < W - 1) add(i + 1);
+  if (y > 0) add(i - W);
+  if (y < H - 1) add(i + W);
+  if (ndim == 3 && z > 0) add(i - HW);
+  if (ndim == 3 && z < D - 1) add(i + HW);
+  __align__(16) bf16 v[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __float2bfloat16_rn(0.f);
+  v[0] = __float2bfloat16_rn(2.f * inv_count * ((1.f + k0) * c.x - nbw * s.x));
+  v[1] = __float2bfloat16_rn(2.f * inv_count * ((1.f + k1) * c.y - nbw * s.y));
+  reinterpret_cast<uint4*>(dz + i * 16)[0] = reinterpret_cast<uint4*>(v)[0];
+  reinterpret_cast<uint4*>(dz + i * 16)[1] = reinterpret_cast<uint4*>(v)[1];
+}
+
 // weight and bias gradient partials of one layer, one set per CTA (persistent over tiles):
 // dW[co][ci][tap] = sum_p dz[p][co] a[p + off(tap)][ci]; db[co] = sum_p dz[p][co]
 template <int ND>
@@ -388,9 +456,12 @@ struct cnn_handle {
   bool own_stream = false;
   Buf params, grad, m, v, wfwd[4], wbwd[4], loss;
   Buf x0, z[4], act[4], outp, dz[5], part, out_user;
+  Buf qres;  // q of the operator-weighted loss, float2 per pixel
   long long cap_pix = 0;
   int sms = 152;
   long long launches = 0;
+  int loss_kind = CNN_LOSS_MSE;
+  float kappa[2] = {0.f, 0.f};
 
   ~cnn_handle() {
     if (own_stream) cudaStreamDestroy(stream);
@@ -513,10 +584,11 @@ struct cnn_handle {
     return cuda(cudaGetLastError(), "pack input");
   }
 
-  // loss + gradient of the masked MSE into `grad`; returns via *loss_out (host)
+  // loss + gradient of the masked loss (MSE or operator-weighted) into `grad`; returns via *loss_out (host)
   int loss_and_grad(const float* in, const float* target, int N, int D, int H, int W, int margin, float* loss_out) {
     long long P = (long long)D * H * W, npix = (long long)N * P;
     int rc;
+    if (loss_kind == CNN_LOSS_OPERATOR && margin < 1) return fail(AMR_ERR_INVALID_ARG, "operator loss needs margin >= 1");
     if ((rc = ensure_acts(npix))) return rc;
     if ((rc = pack_input(in, npix, P)) || (rc = forward(N, D, H, W))) return rc;
     long long cnt = 0;
@@ -527,10 +599,19 @@ struct cnn_handle {
     }
     if (cnt == 0) return fail(AMR_ERR_INVALID_ARG, "margin leaves no pixel");
     if ((rc = cuda(cudaMemsetAsync(loss.p, 0, sizeof(float), stream), "memset"))) return rc;
-    loss_grad_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, stream>>>(outp.as<float>(), target, dz[4].as<bf16>(),
-                                                                         loss.as<float>(), npix, D, H, W, margin, nd,
-                                                                         1.f / (float)cnt);
-    ++launches;
+    unsigned grid = (unsigned)((npix + 255) / 256);
+    if (loss_kind == CNN_LOSS_OPERATOR) {
+      if ((rc = cuda(qres.ensure((size_t)npix * 2 * sizeof(float)), "alloc"))) return rc;
+      op_q_kernel<<<grid, 256, 0, stream>>>(outp.as<float>(), target, qres.as<float>(), loss.as<float>(), npix, D, H,
+                                            W, margin, nd, kappa[0], kappa[1], 1.f / (float)cnt);
+      op_grad_kernel<<<grid, 256, 0, stream>>>(qres.as<float>(), dz[4].as<bf16>(), npix, D, H, W, nd, kappa[0],
+                                               kappa[1], 1.f / (float)cnt);
+      launches += 2;
+    } else {
+      loss_grad_kernel<<<grid, 256, 0, stream>>>(outp.as<float>(), target, dz[4].as<bf16>(), loss.as<float>(), npix,
+                                                 D, H, W, margin, nd, 1.f / (float)cnt);
+      ++launches;
+    }
     if ((rc = backward(N, D, H, W))) return rc;
     if (loss_out) {
       if ((rc = cuda(cudaMemcpyAsync(loss_out, loss.p, sizeof(float), cudaMemcpyDeviceToHost, stream), "copy")))
@@ -667,6 +748,21 @@ int cnn_train_step(cnn_handle* h, const float* in, const float* target, int N, i
   if ((rc = h->repack())) return rc;
   if (loss) return h->cuda(cudaStreamSynchronize(h->stream), "sync");
   return h->cuda(cudaGetLastError(), "adam");
+}
+
+int cnn_set_loss(cnn_handle* h, int kind, const double* kappa) {
+  if (!h) return AMR_ERR_INVALID_ARG;
+  if (kind == CNN_LOSS_MSE) {
+    h->loss_kind = kind;
+    return AMR_OK;
+  }
+  if (kind != CNN_LOSS_OPERATOR || !kappa) return h->fail(AMR_ERR_INVALID_ARG, "cnn_set_loss: bad kind or kappa");
+  for (int c = 0; c < 2; ++c)
+    if (!(kappa[c] >= 0.0) || !std::isfinite(kappa[c])) return h->fail(AMR_ERR_INVALID_ARG, "cnn_set_loss: kappa");
+  h->loss_kind = kind;
+  h->kappa[0] = (float)kappa[0];
+  h->kappa[1] = (float)kappa[1];
+  return AMR_OK;
 }
 
 int cnn_kernel_launches(const cnn_handle* h, long long* n) {

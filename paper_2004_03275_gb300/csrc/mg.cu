@@ -769,15 +769,61 @@ __global__ void rd_explicit_kernel(RdArgs A, const Chunk* ch) {
 }
 
 // ------------------------------------------------------- learned guess --
-// network input of one instance: (u_n, v_n, u*_prev, v*_prev, dt) as float [5][cells]
-__global__ void rd_cnn_input_kernel(const double* __restrict__ wn, const double* __restrict__ pin, long long cells,
-                                    long long off, long long n0, float dt, float* __restrict__ cin) {
+// Residual of the previous-step guess at cell p of one instance-species, B - A w_n with
+// A = lambda - lap_h (Eq. (diff-helmholtz)), normalised by the operator's diagonal scale
+// 2 ndim / h^2 and by the target scale: with target t = (w* - w_n) / scale the network
+// then learns t = A_hat^-1 rho_hat, A_hat = A h^2 / (2 ndim).  Periodic wrap, or zero
+// flux (neighbours outside the domain dropped from the sum and from the diagonal).
+__device__ __forceinline__ double rd_guess_residual(const InstDev& I, const double* __restrict__ B,
+                                                    const double* __restrict__ w, long long p, int ndim, int neu,
+                                                    double inv_scale) {
+  const int n = I.n[0];
+  int c[3] = {(int)(p % n), ndim > 1 ? (int)((p / n) % n) : 0, ndim > 2 ? (int)(p / ((long long)n * n)) : 0};
+  long long stride = 1;
+  double nb = 0.0;
+  int cnt = 0;
+  for (int d = 0; d < ndim; ++d) {
+    if (c[d] > 0) {
+      nb += w[p - stride];
+      ++cnt;
+    } else if (!neu) {
+      nb += w[p + (long long)(n - 1) * stride];
+      ++cnt;
+    }
+    if (c[d] < n - 1) {
+      nb += w[p + stride];
+      ++cnt;
+    } else if (!neu) {
+      nb += w[p - (long long)(n - 1) * stride];
+      ++cnt;
+    }
+    stride *= n;
+  }
+  const double ih2 = I.ih2[0];
+  double Aw = I.lam * w[p] - (nb - cnt * w[p]) * ih2;
+  return (B[I.off0 + p] - Aw) * inv_scale / (2.0 * ndim * ih2);
+}
+
+// network input of one instance as float [5][cells]: (u_n, v_n, c2, c3, dt) with
+// (c2, c3) = (u*_prev, v*_prev) (RD_GUESS_IN_PREV) or the normalised residuals of the
+// previous-step guess (RD_GUESS_IN_RESIDUAL)
+__global__ void rd_cnn_input_kernel(const InstDev* __restrict__ inst, int iu, int iv, const double* __restrict__ B,
+                                    const double* __restrict__ wn, const double* __restrict__ pin, long long cells,
+                                    long long n0, float dt, int kind, int ndim, int neu, double inv_scale,
+                                    float* __restrict__ cin) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n0) return;
+  const InstDev& Iu = inst[iu];
+  const long long off = Iu.off0;
   cin[0 * n0 + t] = (float)wn[off + t];
   cin[1 * n0 + t] = (float)wn[cells + off + t];
-  cin[2 * n0 + t] = (float)pin[off + t];
-  cin[3 * n0 + t] = (float)pin[cells + off + t];
+  if (kind == RD_GUESS_IN_RESIDUAL) {
+    cin[2 * n0 + t] = (float)rd_guess_residual(Iu, B, wn + off, t, ndim, neu, inv_scale);
+    cin[3 * n0 + t] = (float)rd_guess_residual(inst[iv], B, wn + cells + off, t, ndim, neu, inv_scale);
+  } else {
+    cin[2 * n0 + t] = (float)pin[off + t];
+    cin[3 * n0 + t] = (float)pin[cells + off + t];
+  }
   cin[4 * n0 + t] = dt;
 }
 
@@ -794,7 +840,7 @@ __global__ void rd_cnn_guess_kernel(const InstDev* __restrict__ inst, int iu, in
   X[Iv.off0 + t] = wn[cells + Iu.off0 + t] + scale * (double)cout[n0 + t];
 }
 
-// training pairs: crops of (u_n, v_n, u*_prev, v*_prev, dt) and target (w* - w_n) / scale
+// training pairs: crops of the network input (as rd_cnn_input_kernel) and target (w* - w_n) / scale
 struct CropArgs {
   const InstDev* inst;
   const int* cinst;
@@ -807,6 +853,7 @@ struct CropArgs {
   const double* B;
   float dt;
   double inv_scale;
+  int kind, neu;
   float* in;
   float* tgt;
 };
@@ -831,8 +878,13 @@ __global__ void rd_crop_kernel(CropArgs A) {
   float* in = A.in + (long long)k * 5 * cp;
   in[0 * cp + q] = (float)A.wn[off + p];
   in[1 * cp + q] = (float)A.wn[A.cells + off + p];
-  in[2 * cp + q] = (float)A.pin[off + p];
-  in[3 * cp + q] = (float)A.pin[A.cells + off + p];
+  if (A.kind == RD_GUESS_IN_RESIDUAL) {
+    in[2 * cp + q] = (float)rd_guess_residual(Iu, A.B, A.wn + off, p, A.ndim, A.neu, A.inv_scale);
+    in[3 * cp + q] = (float)rd_guess_residual(Iv, A.B, A.wn + A.cells + off, p, A.ndim, A.neu, A.inv_scale);
+  } else {
+    in[2 * cp + q] = (float)A.pin[off + p];
+    in[3 * cp + q] = (float)A.pin[A.cells + off + p];
+  }
   in[4 * cp + q] = A.dt;
   float* tg = A.tgt + (long long)k * 2 * cp;
   tg[q] = (float)((A.X[Iu.off0 + p] - A.wn[off + p]) * A.inv_scale);
@@ -1489,6 +1541,7 @@ struct rd_handle {
   bool have_prev = false;
   cnn_handle* guess = nullptr;
   double guess_scale = 1.0;
+  int guess_inputs = RD_GUESS_IN_PREV;
   std::string err;
   long long cells = 0;
   long long maxcells = 0;
@@ -1802,8 +1855,10 @@ int rd_step(rd_handle* h, int nsteps, int* cycles) {
         long long n0 = 1;
         for (int d = 0; d < h->cfg.ndim; ++d) n0 *= I.n[0];
         unsigned nb = (unsigned)((n0 + 255) / 256);
-        rd_cnn_input_kernel<<<nb, 256, 0, M.stream>>>(wn, pin, h->cells, I.off0, n0, (float)h->cfg.dt,
-                                                       h->d_cin.as<float>());
+        rd_cnn_input_kernel<<<nb, 256, 0, M.stream>>>(M.d_inst.as<InstDev>(), i, i + ni, M.d_B.as<double>(), wn, pin,
+                                                       h->cells, n0, (float)h->cfg.dt, h->guess_inputs,
+                                                       h->cfg.ndim, h->cfg.bc == MG_BC_NEUMANN ? 1 : 0,
+                                                       1.0 / h->guess_scale, h->d_cin.as<float>());
         if ((rc = M.cuda(cudaStreamSynchronize(M.stream), "sync"))) return rc;
         int n = I.n[0];
         int crc = cnn_forward(h->guess, h->d_cin.as<float>(), 1, h->cfg.ndim == 3 ? n : 1, n, n, h->d_cout.as<float>());
@@ -1867,6 +1922,12 @@ int rd_set_guess(rd_handle* h, cnn_handle* net, double scale) {
   return AMR_OK;
 }
 
+int rd_set_guess_inputs(rd_handle* h, int kind) {
+  if (!h || (kind != RD_GUESS_IN_PREV && kind != RD_GUESS_IN_RESIDUAL)) return AMR_ERR_INVALID_ARG;
+  h->guess_inputs = kind;
+  return AMR_OK;
+}
+
 int rd_extract_crops(rd_handle* h, int ncrops, const int* inst, const int* corner, int crop, double scale, float* in,
                      float* target) {
   if (!h || ncrops < 1 || !inst || !corner || crop < 1 || !(scale > 0) || !in || !target) return AMR_ERR_INVALID_ARG;
@@ -1895,6 +1956,8 @@ int rd_extract_crops(rd_handle* h, int ncrops, const int* inst, const int* corne
   A.B = M.d_B.as<double>();
   A.dt = (float)h->cfg.dt;
   A.inv_scale = 1.0 / scale;
+  A.kind = h->guess_inputs;
+  A.neu = h->cfg.bc == MG_BC_NEUMANN ? 1 : 0;
   A.in = in;
   A.tgt = target;
   long long cp = 1;

@@ -6,12 +6,19 @@ forward/backward passes and the Adam updates all run in the CUDA library.
 Recipe (the project's own reading; the paper has no learned component):
 * training data: Gray-Scott IMEX runs of the plain solver (previous-step guess)
   on training seeds, crops of side `crop` at seeded random positions after every
-  step, inputs (u_n, v_n, u*_prev, v*_prev, dt), target (w* - w_n) / scale (the
+  step, inputs (u_n, v_n, u*_prev, v*_prev, dt), or (u_n, v_n, rho_u, rho_v, dt)
+  with rho the normalised residual of the previous-step guess (inputs="residual":
+  the increment is then the local inverse of the normalised operator applied to
+  rho), target (w* - w_n) / scale (the
   increment over the previous-step guess; a network that outputs zero gives
   back that guess), where scale is the RMS of w* - w_n over the first
   collected step;
 * loss: masked MSE (margin 4 = the network's receptive radius, so that the
-  periodic padding inside a crop never reaches a counted pixel);
+  periodic padding inside a crop never reaches a counted pixel), or the
+  operator-weighted loss: the mean square of the guess's residual under the
+  diagonal-normalised Helmholtz operator of Eq. (diff-helmholtz), kappa =
+  lambda h^2 / (2 ndim) per species (`operator_kappa`), margin 5 (the
+  operator's stencil adds one cell to the receptive radius);
 * Adam, lr 1e-3, batches of `batch` crops drawn uniformly with replacement;
 * evaluation on disjoint seeds: V-cycles per step and wall time per step with
   the learned guess against the previous-step guess, both to the same rtol.
@@ -32,6 +39,15 @@ def domain_for(n, ref_n=2048, ref_L=2.5):
     return ref_L * n / ref_n
 
 
+def operator_kappa(n, L, ndim=2, dt=GS["dt"], Du=GS["Du"], Dv=GS["Dv"]):
+    """kappa_c = lambda_c h^2 / (2 ndim), lambda_c = 2 / (dt D_c) (IMEX, Eq. (imex)), h = L / n."""
+    h = L / n
+    return tuple(2.0 / (dt * D) * h * h / (2 * ndim) for D in (Du, Dv))
+
+
+MARGIN = {"mse": 4, "operator": 5}
+
+
 def start_state(sizes, L, seeds, ndim=2):
     us, vs = [], []
     for n, sd in zip(sizes, seeds):
@@ -42,9 +58,11 @@ def start_state(sizes, L, seeds, ndim=2):
 
 
 def generate(torch, sizes, seeds, L, steps, crops_per_step, crop=64, warm=0, scale=None, seed=0, stream=None,
-             ndim=2):
-    """Returns (inputs [M][5][c]^ndim, targets [M][2][c]^ndim, scale) as CUDA float tensors."""
+             ndim=2, inputs="prev"):
+    """Returns (inputs [M][5][c]^ndim, targets [M][2][c]^ndim, scale) as CUDA float tensors;
+    `inputs` selects channels 2, 3 (RdSolver.set_guess_inputs)."""
     rd = amrvac.RdSolver(ndim, sizes, L, precision="fp32", stream=stream, **GS)
+    rd.set_guess_inputs(inputs)
     rd.set_state(*start_state(sizes, L, seeds, ndim))
     box = (crop,) * ndim
     if warm:
@@ -98,9 +116,10 @@ def dataset_loss(torch, net, X, Y, margin=4, chunk=16):
     return tot / X.shape[0]
 
 
-def evaluate(torch, sizes, seeds, L, steps, net=None, scale=1.0, warm=0, stream=None, ndim=2):
+def evaluate(torch, sizes, seeds, L, steps, net=None, scale=1.0, warm=0, stream=None, ndim=2, inputs="prev"):
     """V-cycles per step (per species and instance) and wall time per step."""
     rd = amrvac.RdSolver(ndim, sizes, L, precision="fp32", stream=stream, **GS)
+    rd.set_guess_inputs(inputs)
     rd.set_state(*start_state(sizes, L, seeds, ndim))
     if warm:
         rd.step(warm)

@@ -67,6 +67,42 @@ def test_gradient_matches_oracle(ndim, shape, margin):
             assert rel <= 5e-2 and cos >= 0.998, (sl, rel, cos)
 
 
+@pytest.mark.parametrize("ndim,shape,margin", [(2, (2, 5, 32, 32), 2), (3, (1, 5, 8, 8, 8), 1)])
+def test_operator_loss_gradient_matches_oracle(ndim, shape, margin):
+    """Operator-weighted loss (kappa of the 2048^2 Gray-Scott species): the loss of the GPU's
+    own outputs matches the oracle's loss of those outputs to float32 rounding; the parameter
+    gradient matches the oracle's within the bf16 tolerance of the MSE test."""
+    rng = np.random.default_rng(60 + ndim)
+    p = rand_params(ndim, rng)
+    x = bf16_round(rng.uniform(0, 1, size=shape)).astype(np.float64)
+    tgt = (0.05 * rng.normal(size=(shape[0], 2) + shape[2:])).astype(np.float32)
+    kappa = (0.0745, 0.149)
+    net = amrvac.CnnNet(ndim=ndim)
+    net.set_params(p)
+    net.set_loss("operator", kappa)
+    xt, tt = torch.from_numpy(x.astype(np.float32)).cuda(), torch.from_numpy(tgt).cuda()
+    loss, g = net.gradient(xt, tt, margin=margin)
+    out = net.forward(xt).double().cpu().numpy()
+    lo_own, _ = O.cnn_output_loss(out, tgt, margin=margin, ndim=ndim, loss="operator", kappa=kappa)
+    assert loss == pytest.approx(lo_own, rel=1e-4)
+    lo, go = O.cnn_loss_grad(p, x, tgt, margin=margin, ndim=ndim, loss="operator", kappa=kappa)
+    assert loss == pytest.approx(lo, rel=3e-2)
+    for ws, bs, ci, co in O.cnn_layer_slices(ndim):
+        for sl in (ws, bs):
+            a, b = g[sl].astype(np.float64), go[sl]
+            rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+            cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+            assert rel <= 5e-2 and cos >= 0.998, (sl, rel, cos)
+    # margin 0 has no neighbours at the edge; the loss kinds are validated
+    with pytest.raises(amrvac.AmrError):
+        net.gradient(xt, tt, margin=0)
+    with pytest.raises(amrvac.AmrError):
+        net.set_loss("operator", (-1.0, 0.0))
+    net.set_loss("mse")
+    l_mse, _ = net.gradient(xt, tt, margin=margin)
+    assert l_mse == pytest.approx(O.cnn_output_loss(out, tgt, margin=margin, ndim=ndim)[0], rel=1e-4)
+
+
 def test_training_reduces_loss_and_adam_moves_by_lr():
     rng = np.random.default_rng(3)
     x = torch.from_numpy(rng.uniform(0, 1, size=(8, 5, 32, 32)).astype(np.float32)).cuda()
