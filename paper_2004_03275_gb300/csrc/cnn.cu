@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "../../include/amrvac_gb300.h"
+#include "mg_internal.h"
 
 namespace cnngpu {
 
@@ -65,7 +66,8 @@ __device__ __forceinline__ float gelu_d(float z) {
   return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
 }
 
-enum { FWD_GELU = 0, FWD_OUT = 1, BWD_GELU = 2 };
+// FWD_INFER: FWD_GELU without the pre-activation store (inference has no backward pass)
+enum { FWD_GELU = 0, FWD_OUT = 1, BWD_GELU = 2, FWD_INFER = 3 };
 
 struct ConvArgs {
   const bf16* in;     // NHWC16
@@ -182,10 +184,11 @@ __global__ void __launch_bounds__(256) conv_kernel(ConvArgs a) {
       for (int nt = 0; nt < NT; ++nt) {
         int c = nt * 8 + 2 * t;
         float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
-        if (MODE == FWD_GELU) {
+        if (MODE == FWD_GELU || MODE == FWD_INFER) {
           v0 += a.bias[c];
           v1 += a.bias[c + 1];
-          *reinterpret_cast<__nv_bfloat162*>(a.z_out + gp * 16 + c) = __floats2bfloat162_rn(v0, v1);
+          if (MODE == FWD_GELU)
+            *reinterpret_cast<__nv_bfloat162*>(a.z_out + gp * 16 + c) = __floats2bfloat162_rn(v0, v1);
           *reinterpret_cast<__nv_bfloat162*>(a.a_out + gp * 16 + c) = __floats2bfloat162_rn(gelu(v0), gelu(v1));
         } else if (MODE == FWD_OUT) {
           if (c < 2) {
@@ -463,7 +466,10 @@ struct cnn_handle {
   int loss_kind = CNN_LOSS_MSE;
   float kappa[2] = {0.f, 0.f};
 
+  cudaEvent_t order_ev = nullptr;  // orders inference on a caller's stream against this stream
+
   ~cnn_handle() {
+    if (order_ev) cudaEventDestroy(order_ev);
     if (own_stream) cudaStreamDestroy(stream);
   }
   int fail(int code, const std::string& s) {
@@ -514,8 +520,9 @@ struct cnn_handle {
     return D % TD<3>::TZ == 0 && H % TD<3>::TY == 0 && W % TD<3>::TX == 0;
   }
 
+  // infer: no pre-activations are kept (no backward pass follows)
   template <int ND>
-  int forward_t(int N, int D, int H, int W) {
+  int forward_t(int N, int D, int H, int W, bool infer) {
     using T = TD<ND>;
     int tiles = N * (D / T::TZ) * (H / T::TY) * (W / T::TX);
     const bf16* in = x0.as<bf16>();
@@ -531,7 +538,10 @@ struct cnn_handle {
       if (l < 3) {
         a.z_out = z[l].as<bf16>();
         a.a_out = act[l].as<bf16>();
-        conv_kernel<ND, FWD_GELU><<<tiles, 256, conv_smem_bytes<ND, FWD_GELU>(), stream>>>(a);
+        if (infer)
+          conv_kernel<ND, FWD_INFER><<<tiles, 256, conv_smem_bytes<ND, FWD_INFER>(), stream>>>(a);
+        else
+          conv_kernel<ND, FWD_GELU><<<tiles, 256, conv_smem_bytes<ND, FWD_GELU>(), stream>>>(a);
         in = act[l].as<bf16>();
       } else {
         a.out = outp.as<float>();
@@ -575,7 +585,9 @@ struct cnn_handle {
     return cuda(cudaGetLastError(), "backward");
   }
 
-  int forward(int N, int D, int H, int W) { return nd == 2 ? forward_t<2>(N, D, H, W) : forward_t<3>(N, D, H, W); }
+  int forward(int N, int D, int H, int W, bool infer = false) {
+    return nd == 2 ? forward_t<2>(N, D, H, W, infer) : forward_t<3>(N, D, H, W, infer);
+  }
   int backward(int N, int D, int H, int W) { return nd == 2 ? backward_t<2>(N, D, H, W) : backward_t<3>(N, D, H, W); }
 
   int pack_input(const float* in, long long npix, long long P) {
@@ -622,6 +634,37 @@ struct cnn_handle {
   }
 };
 
+// inference on `stream` (NULL = the handle's own) without a final synchronisation
+int cnn_forward_async(cnn_handle* h, const float* in, int N, int D, int H, int W, float* out, cudaStream_t stream) {
+  if (!h || !in || !out || !h->shape_ok(N, D, H, W)) return AMR_ERR_INVALID_ARG;
+  long long P = (long long)D * H * W, npix = (long long)N * P;
+  cudaStream_t own = h->stream;
+  int rc;
+  const bool other = stream && stream != own;
+  if (other) {
+    // `stream` waits for the handle's pending work (weight repacks after Adam steps), and
+    // the handle's stream later waits for this inference (it reads the packed weights)
+    if (!h->order_ev && (rc = h->cuda(cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming), "event")))
+      return rc;
+    if ((rc = h->cuda(cudaEventRecord(h->order_ev, own), "event")) ||
+        (rc = h->cuda(cudaStreamWaitEvent(stream, h->order_ev, 0), "event")))
+      return rc;
+    h->stream = stream;
+  }
+  if (!(rc = h->ensure_acts(npix)) && !(rc = h->pack_input(in, npix, P)) && !(rc = h->forward(N, D, H, W, true))) {
+    unpack_output_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, h->stream>>>(h->outp.as<float>(), out, npix, P);
+    ++h->launches;
+    rc = h->cuda(cudaGetLastError(), "unpack");
+  }
+  h->stream = own;
+  if (other && !rc) {
+    if ((rc = h->cuda(cudaEventRecord(h->order_ev, stream), "event")) ||
+        (rc = h->cuda(cudaStreamWaitEvent(own, h->order_ev, 0), "event")))
+      return rc;
+  }
+  return rc;
+}
+
 extern "C" {
 
 int cnn_create(int ndim, unsigned long long seed, void* stream, cnn_handle** out) {
@@ -643,6 +686,8 @@ int cnn_create(int ndim, unsigned long long seed, void* stream, cnn_handle** out
                            (int)conv_smem_bytes<3, FWD_GELU>()) != cudaSuccess ||
       cudaFuncSetAttribute(conv_kernel<3, FWD_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)conv_smem_bytes<3, FWD_OUT>()) != cudaSuccess ||
+      cudaFuncSetAttribute(conv_kernel<3, FWD_INFER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)conv_smem_bytes<3, FWD_INFER>()) != cudaSuccess ||
       cudaFuncSetAttribute(conv_kernel<3, BWD_GELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)conv_smem_bytes<3, BWD_GELU>()) != cudaSuccess)
     return AMR_ERR_CUDA;
@@ -710,13 +755,8 @@ int cnn_get_params(cnn_handle* h, float* p, long long n) {
 }
 
 int cnn_forward(cnn_handle* h, const float* in, int N, int D, int H, int W, float* out) {
-  if (!h || !in || !out || !h->shape_ok(N, D, H, W)) return AMR_ERR_INVALID_ARG;
-  long long P = (long long)D * H * W, npix = (long long)N * P;
-  int rc;
-  if ((rc = h->ensure_acts(npix)) || (rc = h->pack_input(in, npix, P)) || (rc = h->forward(N, D, H, W))) return rc;
-  unpack_output_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, h->stream>>>(h->outp.as<float>(), out, npix, P);
-  ++h->launches;
-  if ((rc = h->cuda(cudaGetLastError(), "unpack"))) return rc;
+  int rc = cnn_forward_async(h, in, N, D, H, W, out, nullptr);
+  if (rc) return rc;
   return h->cuda(cudaStreamSynchronize(h->stream), "sync");
 }
 

@@ -1849,7 +1849,7 @@ int rd_step(rd_handle* h, int nsteps, int* cycles) {
     }
     ++M.launches;
     if (h->guess) {
-      if ((rc = M.cuda(cudaStreamSynchronize(M.stream), "sync"))) return rc;
+      // the network runs in order on the solver's stream (no host synchronisation)
       for (int i = 0; i < ni; ++i) {
         const InstDev& I = M.insts[i];
         long long n0 = 1;
@@ -1859,9 +1859,9 @@ int rd_step(rd_handle* h, int nsteps, int* cycles) {
                                                        h->cells, n0, (float)h->cfg.dt, h->guess_inputs,
                                                        h->cfg.ndim, h->cfg.bc == MG_BC_NEUMANN ? 1 : 0,
                                                        1.0 / h->guess_scale, h->d_cin.as<float>());
-        if ((rc = M.cuda(cudaStreamSynchronize(M.stream), "sync"))) return rc;
         int n = I.n[0];
-        int crc = cnn_forward(h->guess, h->d_cin.as<float>(), 1, h->cfg.ndim == 3 ? n : 1, n, n, h->d_cout.as<float>());
+        int crc = cnn_forward_async(h->guess, h->d_cin.as<float>(), 1, h->cfg.ndim == 3 ? n : 1, n, n,
+                                    h->d_cout.as<float>(), M.stream);
         if (crc) return M.fail(crc, std::string("learned guess: ") + cnn_last_error(h->guess));
         rd_cnn_guess_kernel<<<nb, 256, 0, M.stream>>>(M.d_inst.as<InstDev>(), i, i + ni, h->d_cout.as<float>(), n0,
                                                       h->guess_scale, M.d_X.as<double>(), wn, h->cells);

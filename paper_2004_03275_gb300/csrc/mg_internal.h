@@ -14,3 +14,8 @@ int mg_capture_solve(mg_handle* h, const double* b, double* x, cudaStream_t s);
 // of kernels one iteration of its device-side loop launches.
 const int* mg_device_cycles(const mg_handle* h);
 long long mg_loop_kernels(const mg_handle* h);
+
+// Inference of the learned-guess network (cnn.cu) on stream s without a final
+// synchronisation; the network's own pending work is ordered before it, and the network's
+// later work after it, by events.  Arguments as cnn_forward.
+int cnn_forward_async(cnn_handle* h, const float* in, int N, int D, int H, int W, float* out, cudaStream_t s);

@@ -19,7 +19,8 @@ Recipe (the project's own reading; the paper has no learned component):
   diagonal-normalised Helmholtz operator of Eq. (diff-helmholtz), kappa =
   lambda h^2 / (2 ndim) per species (`operator_kappa`), margin 5 (the
   operator's stencil adds one cell to the receptive radius);
-* Adam, lr 1e-3, batches of `batch` crops drawn uniformly with replacement;
+* Adam, lr 1e-3 over the first half of the steps, then a cosine decay to 5e-5
+  (`lr_at`), batches of `batch` crops drawn uniformly with replacement;
 * evaluation on disjoint seeds: V-cycles per step and wall time per step with
   the learned guess against the previous-step guess, both to the same rtol.
 """
@@ -90,6 +91,17 @@ def generate(torch, sizes, seeds, L, steps, crops_per_step, crop=64, warm=0, sca
     return torch.cat(X), torch.cat(Y), scale
 
 
+def lr_at(it, iters, lr, final_frac=0.05):
+    """Learning rate of Adam step `it` (0-based): constant over the first half, then a cosine
+    decay to final_frac * lr at the last step, so that training ends on a settled iterate
+    rather than on one of the fluctuating constant-rate iterates."""
+    half = iters // 2
+    if it < half or iters - half <= 1:
+        return lr
+    f = (it - half) / (iters - half - 1)
+    return lr * (final_frac + (1.0 - final_frac) * 0.5 * (1.0 + np.cos(np.pi * f)))
+
+
 def train(torch, net, X, Y, iters, batch=32, lr=1e-3, margin=4, seed=1):
     rng = np.random.default_rng(seed)
     losses = []
@@ -99,7 +111,7 @@ def train(torch, net, X, Y, iters, batch=32, lr=1e-3, margin=4, seed=1):
         xb = X.index_select(0, idx).contiguous()
         yb = Y.index_select(0, idx).contiguous()
         want = it == 0 or it == iters - 1 or (it + 1) % 100 == 0
-        loss = net.train_step(xb, yb, lr=lr, margin=margin, want_loss=want)
+        loss = net.train_step(xb, yb, lr=lr_at(it, iters, lr), margin=margin, want_loss=want)
         if want:
             losses.append((it + 1, loss))
     torch.cuda.synchronize()
