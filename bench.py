@@ -293,9 +293,9 @@ def bench_learned_guess_3d(torch, amrvac, stream, eval_steps=6):
 
 
 # Algorithmic bytes per level-0 unknown per V-cycle of the float32 multigrid (nu1 = nu2 = 2, 2D):
-#   level 0: 4 sweeps x (read x, b; write x: 12 B) = 48; float64 residual (read X, B; write b0, x0 = 0)
-#   = 24; residual + restriction (read x0, b0; write 1/4 of b1, x1) = 10; prolongation (read 1/4 of x1,
-#   read + write x0) = 9; float64 correction (read X, x0; write X) = 20  -> 111 B;
+#   level 0: 4 sweeps x (read x, b; write x: 12 B) = 48; residual + restriction (read x0, b0; write 1/4
+#   of b1, x1) = 10; prolongation (read 1/4 of x1, read + write x0) = 9; float64 correction and defect
+#   update (read x0, X, R; write X, R, b0) = 40; correction zeroed (write x0) = 4  -> 111 B;
 #   coarser levels: (48 + 10 + 9) B x (1/4 + 1/16 + ...) = 22 B  -> 133 B.
 MG_BYTES_PER_UNKNOWN_VCYCLE = 133.0
 

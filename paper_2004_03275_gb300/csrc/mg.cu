@@ -57,6 +57,8 @@ struct InstDev {
   float ih2f[kMaxLev];
   double lam;
   float lamf;
+  float lamlo;    // lambda - lamf (float-float lambda for the level-0 defect update)
+  float ih2lo0;   // ih2[0] - ih2f[0]
   double idiag[kMaxLev][7];     // 1 / (lambda + (2 ndim - m) / h^2) for m neighbours beyond a
   float idiagf[kMaxLev][7];     // Neumann boundary (m = 0 inside and on periodic grids)
   long long off0;          // offset into X / B
@@ -67,6 +69,7 @@ struct MgState {
   const InstDev* inst;
   double* X;
   const double* B;
+  double* R;                  // float32 V-cycles: level-0 float64 defect B - A X, kept up to date
   unsigned long long* rnorm;  // max |R| bits per instance
   double* bnorm;              // max |B| per instance
   double* lastres;            // last max |R| per instance
@@ -285,6 +288,7 @@ __global__ void residual64_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
     const double mcount = NEU ? (double)(miss - 2 * S.ndim) : (S.ndim == 3 ? -6.0 : -4.0);
     double r = fma(fma(mcount, x, s), I.ih2[0], S.B[I.off0 + t]);
     r = fma(-I.lam, x, r);
+    if constexpr (sizeof(real) == 4) S.R[I.off0 + t] = r;
     L.b[I.off[0] + t] = narrow<real>(r);
     L.x[I.off[0] + t] = real(0);
     m = (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;  // |r| as bits
@@ -623,6 +627,97 @@ __global__ void correct64_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
     S.X[I.off0 + t] = S.X[I.off0 + t] + widen(e);
   else
     S.X[I.off0 + t] = S.X[I.off0 + t] + e;
+}
+
+// float-float arithmetic (Dekker / Knuth error-free transformations) for the defect update.
+// The _rn intrinsics keep every product and sum rounded on its own: a multiply-add
+// contraction would break the exactness the transformations rely on.
+struct FF {
+  float hi, lo;
+};
+// a + b exactly as s + err (TwoSum), err folded into the low part, renormalised
+__device__ __forceinline__ FF ff_add(FF a, float b) {
+  const float s = __fadd_rn(a.hi, b);
+  const float bb = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  const float lo = __fadd_rn(a.lo, err);
+  const float hi = __fadd_rn(s, lo);
+  return {hi, __fsub_rn(lo, __fsub_rn(hi, s))};
+}
+__device__ __forceinline__ FF ff_sub(FF a, FF b) {
+  FF r = ff_add(a, -b.hi);
+  return ff_add(r, -b.lo);
+}
+// a (c.hi + c.lo) for a float-float a and a float-float constant c (TwoProd by fma)
+__device__ __forceinline__ FF ff_mul(FF a, float chi, float clo) {
+  const float p = __fmul_rn(a.hi, chi);
+  float e = __fmaf_rn(a.hi, chi, -p);
+  e = __fmaf_rn(a.hi, clo, e);
+  e = __fmaf_rn(a.lo, chi, e);
+  const float hi = __fadd_rn(p, e);
+  return {hi, __fsub_rn(e, __fsub_rn(hi, p))};
+}
+
+// Update of the float64 defect after a float32 V-cycle, fused with the correction:
+// X += e and R -= A e, with e the level-0 correction and A = lambda - lap_h.  Since A is
+// linear, R stays B - A X; A e is formed in float-float from the float values of e (error
+// ~2^-44 of its largest term, far below the stopping tolerance), so the only float64
+// operations per cell are the two updates and one widening add.  R replaces the float64
+// re-evaluation of the stencil of X, which kept GB300's float64 pipe busy.  e is not zeroed
+// here (its neighbours are still being read); zero0_kernel follows.
+template <bool NEU>
+__global__ void update64_kernel(MgState S, Lvl<float> L, const Chunk* ch) {
+  Chunk C = ch[blockIdx.x];
+  if (!S.active[C.inst]) return;
+  unsigned long long m = 0ull;
+  const InstDev& I = S.inst[C.inst];
+  if (threadIdx.x < C.count) {
+    const long long t = C.start + threadIdx.x;
+    const int n = I.n[0];
+    int c[3];
+    cell_of(t, n, S.ndim, c);
+    const float* E = L.x + I.off[0];
+    const float e = E[t];
+    // lap e * h^2 = sum of the neighbours - count e, in float-float
+    FF sum{0.f, 0.f};
+    int cnt = 0;
+    for (int d = 0; d < S.ndim; ++d) {
+#pragma unroll
+      for (int side = -1; side <= 1; side += 2) {
+        int q[3] = {c[0], c[1], c[2]};
+        int u = c[d] + side;
+        if (u < 0 || u >= n) {
+          if (NEU) continue;
+          u = u < 0 ? u + n : u - n;
+        }
+        q[d] = u;
+        sum = ff_add(sum, E[lin(q, n)]);
+        ++cnt;
+      }
+    }
+    const float ce = __fmul_rn((float)cnt, e);  // cnt e exactly as ce + ce_err
+    const float ce_err = __fmaf_rn((float)cnt, e, -ce);
+    sum = ff_add(sum, -ce);
+    sum = ff_add(sum, -ce_err);
+    const FF lap = ff_mul(sum, I.ih2f[0], I.ih2lo0);
+    const FF le = ff_mul(FF{e, 0.f}, I.lamf, I.lamlo);
+    const FF ae = ff_sub(le, lap);
+    double* X = S.X + I.off0;
+    double* R = S.R + I.off0;
+    X[t] = __dadd_rn(X[t], widen(e));
+    const double r = __dsub_rn(R[t], __dadd_rn(widen(ae.hi), widen(ae.lo)));
+    R[t] = r;
+    L.b[I.off[0] + t] = narrow<float>(r);
+    m = (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;  // |r| as bits
+  }
+  block_max_atomic(m, &S.rnorm[C.inst]);
+}
+
+// level-0 correction zeroed for the next V-cycle (after update64_kernel has read it)
+__global__ void zero0_kernel(MgState S, Lvl<float> L, const Chunk* ch) {
+  Chunk C = ch[blockIdx.x];
+  if (!S.active[C.inst] || threadIdx.x >= C.count) return;
+  L.x[S.inst[C.inst].off[0] + C.start + threadIdx.x] = 0.f;
 }
 
 // per-step log of a device-side solve: entry [step % cap][instance] = V-cycles, or
@@ -981,6 +1076,7 @@ struct Mg {
   std::vector<std::vector<Chunk>> ch_half, ch_coarse, ch_fine, ch_tile;
   std::vector<int> coarse_inst, coarse_row0;
   DevBuf d_yl;  // 2D: second iterate array for the tiled sweeps
+  DevBuf d_R;  // float32 V-cycles: level-0 float64 defect
   DevBuf d_inst, d_X, d_B, d_xl, d_bl, d_rnorm, d_bnorm, d_lastres, d_initres, d_active, d_cycles, d_failed, d_any, d_inv;
   DevBuf d_iters;
   cudaStream_t cstream = nullptr;   // captures the body of the device-side solve loop
@@ -1015,6 +1111,7 @@ struct Mg {
     S.inst = d_inst.as<InstDev>();
     S.X = d_X.as<double>();
     S.B = d_B.as<double>();
+    S.R = d_R.as<double>();
     S.rnorm = d_rnorm.as<unsigned long long>();
     S.bnorm = d_bnorm.as<double>();
     S.lastres = d_lastres.as<double>();
@@ -1063,6 +1160,7 @@ struct Mg {
       std::memset(&I, 0, sizeof(I));
       I.lam = lambda[i];
       I.lamf = (float)lambda[i];
+      I.lamlo = (float)(lambda[i] - (double)I.lamf);
       I.off0 = off0;
       long long cells0 = 1;
       for (int d = 0; d < nd; ++d) cells0 *= n;
@@ -1088,6 +1186,7 @@ struct Mg {
         m /= 2;
       }
       I.nlev = l;
+      I.ih2lo0 = (float)(I.ih2[0] - (double)I.ih2f[0]);
       maxdepth = std::max(maxdepth, l);
       int mc = I.n[l - 1];
       long long msz = 1;
@@ -1136,6 +1235,7 @@ struct Mg {
     int rc;
     if ((rc = cuda(d_inst.alloc(insts.size() * sizeof(InstDev)), "alloc")) ||
         (rc = cuda(d_X.alloc(n0 * 8), "alloc X")) || (rc = cuda(d_B.alloc(n0 * 8), "alloc B")) ||
+        (precision != AMR_FP64 && (rc = cuda(d_R.alloc(n0 * 8), "alloc R"))) ||
         (rc = cuda(d_xl.alloc(nlevtot * wb), "alloc levels")) || (rc = cuda(d_bl.alloc(nlevtot * wb), "alloc levels")) ||
         (nd == 2 && (rc = cuda(d_yl.alloc(nlevtot * wb), "alloc levels"))) ||
         (rc = cuda(d_rnorm.alloc(n_inst * 8), "alloc")) || (rc = cuda(d_bnorm.alloc(n_inst * 8), "alloc")) ||
@@ -1345,8 +1445,22 @@ struct Mg {
       }
       smooth(l, nu2);
     }
-    correct64_kernel<real><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
-    ++launches;
+    // the correction and the new level-0 defect: float32 cycles update R by A e; float64
+    // cycles correct X and re-evaluate the residual
+    if constexpr (sizeof(real) == 4) {
+      if (neu)
+        update64_kernel<true><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+      else
+        update64_kernel<false><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+      zero0_kernel<<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+    } else {
+      correct64_kernel<real><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+      if (neu)
+        residual64_kernel<real, true><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+      else
+        residual64_kernel<real, false><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+    }
+    launches += 2;
     return cuda(cudaGetLastError(), "vcycle launch");
   }
 
@@ -1413,13 +1527,9 @@ struct Mg {
     cudaStream_t outer = stream;
     stream = cstream;
     long long before = launches;
-    int rc = enqueue_vcycle<real>();
-    if (neu)
-      residual64_kernel<real, true><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
-    else
-      residual64_kernel<real, false><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+    int rc = enqueue_vcycle<real>();  // ends with the new defect
     check_kernel<<<1, 256, 0, stream>>>(S, ninst, hc, 1);
-    solve_loop_kernels = launches - before + 2;
+    solve_loop_kernels = launches - before + 1;
     launches = before;
     stream = outer;
     cudaGraph_t got = nullptr;
@@ -1445,8 +1555,8 @@ struct Mg {
     return rc;
   }
 
-  // kernels one device-side solve ran: prelude 4, then per loop iteration (max cycles of an
-  // instance) a V-cycle, a residual and a check
+  // kernels one device-side solve ran: prelude 4 (norms, first residual, check), then per loop
+  // iteration (max cycles of an instance) a V-cycle ending with the new defect, and a check
   long long solve_kernels(int maxcyc) const { return 4 + (long long)maxcyc * solve_loop_kernels; }
 
   // X (device, float64) holds the guess; B (device) the right-hand side; both at d_X / d_B.
@@ -1471,18 +1581,18 @@ struct Mg {
     if (rc) return rc;
     bnorm_kernel<<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, d_ch0.as<Chunk>());
     bnorm_finish_kernel<<<(ninst + 255) / 256, 256, 0, stream>>>(S, ninst);
-    launches += 2;
-    while (true) {
-      if (neu)
+    if (neu)
       residual64_kernel<real, true><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
     else
       residual64_kernel<real, false><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+    launches += 3;
+    while (true) {
       check_kernel<<<1, 256, 0, stream>>>(S, ninst, 0, 0);
-      launches += 2;
+      ++launches;
       if ((rc = cuda(cudaMemcpyAsync(h_any, d_any.p, 4, cudaMemcpyDeviceToHost, stream), "copy"))) return rc;
       if ((rc = cuda(cudaStreamSynchronize(stream), "sync"))) return rc;
       if (!*h_any) break;
-      if ((rc = cuda(cudaGraphLaunch(vgraph, stream), "graph launch"))) return rc;
+      if ((rc = cuda(cudaGraphLaunch(vgraph, stream), "graph launch"))) return rc;  // V-cycle + new defect
       launches += vcycle_kernels;
     }
     return cuda(cudaGetLastError(), "solve");
