@@ -235,3 +235,31 @@ def test_regrid_coarsens_smooth_regions():
     for _ in range(3):
         g.regrid()
     assert g.nleaves == 4 and g.nleaves < n0
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_cfl_dt_closed_form_on_a_tree(ndim):
+    """Sec. 1.2's Courant condition on a uniform state: every cell has the same signal speeds,
+    so the bound is set by the finest level present, dt = cfl / sum_d (|v_d| + c) / dx_d(finest)
+    with c = sqrt(gamma p / rho) in closed form; the last step is clipped to t_end."""
+    rng = np.random.default_rng(50 + ndim)
+    base = [2, 3, 2][:ndim]
+    lev, crd = random_balanced_tree(ndim, base + [1] * (3 - ndim), 3, rng, 2)
+    xmin, xmax = (0.0, -1.0, 0.5)[:ndim], (1.0, 2.0, 1.25)[:ndim]
+    cfl, bnx = 0.7, 4
+    g = grid_on_tree(ndim, bnx, base, 3, lev, crd, cfl=cfl, xmin=xmin, xmax=xmax)
+    rho, p = 1.3, 0.9
+    vel = np.array([0.4, -0.75, 0.2][:ndim])
+    V = np.zeros((g.nleaves, ndim + 2, bnx ** ndim))
+    V[:, 0], V[:, ndim + 1] = rho, p
+    for d in range(ndim):
+        V[:, 1 + d] = vel[d]
+    g.set_prim(V)
+    c = np.sqrt(GAM * p / rho)
+    fine = int(lev.max())
+    dx = [(xmax[d] - xmin[d]) / (base[d] * bnx * 2 ** (fine - 1)) for d in range(ndim)]
+    want = cfl / sum((abs(vel[d]) + c) / dx[d] for d in range(ndim))
+    assert g.dt() == pytest.approx(want, rel=1e-13)
+    g.t = 0.25
+    assert g.dt(t_end=0.25 + 0.1 * want) == pytest.approx(0.1 * want, rel=1e-9)
+    assert g.dt(t_end=1.0) == pytest.approx(want, rel=1e-13)

@@ -174,3 +174,40 @@ def test_gray_scott_patch_input_shape():
     assert v.min() == 0.0 and 0.24 < v.max() < 0.26
     frac = np.mean(v > 0)
     assert 0.01 < frac < 0.06  # 20 patches of (L/20)^2 cover at most 5% of the domain
+
+
+def test_gray_scott_reaction_steady_states_and_jacobian():
+    """Eq. (gray-scott)'s reaction terms vanish at its homogeneous steady states: (1, 0), and
+    where F^2 >= 4 F (F + k)^2 the two roots v = (F -+ sqrt(F^2 - 4 F (F + k)^2)) / (2 (F + k)),
+    u = (F + k) / v of v (F + k) = F (1 - u), u v = F + k.  At the configuration's F = 0.04,
+    k = 0.06 the discriminant is exactly zero: one double root (u, v) = (0.5, 0.2).  The
+    Jacobian at (1, 0), by central differences, is diag(-F, -(F + k)) (the autocatalytic
+    term is quadratic in v), and the autocatalytic terms cancel in the sum."""
+    def roots(F, k):
+        disc = F * F - 4 * F * (F + k) ** 2
+        if abs(disc) <= 1e-15:
+            disc = 0.0  # the configuration's double root (zero up to rounding)
+        out = [(1.0, 0.0)]
+        if disc >= 0:
+            for sgn in (-1, 1):
+                v = (F + sgn * np.sqrt(disc)) / (2 * (F + k))
+                out.append(((F + k) / v, v))
+        return out
+
+    for F, k in ((0.04, 0.06), (0.03, 0.05), (0.02, 0.03), (0.05, 0.04)):
+        for us, vs in roots(F, k):
+            fu, fv = O.rd_reaction(F, k, np.array([us]), np.array([vs]))
+            assert abs(fu[0]) <= 1e-15 and abs(fv[0]) <= 1e-15, (F, k, us, vs, fu, fv)
+    F, k = GS["F"], GS["k"]
+    assert roots(F, k)[1] == pytest.approx((0.5, 0.2), rel=1e-12)
+    eps = 1e-6
+    J = np.zeros((2, 2))
+    for j, (du, dv) in enumerate([(eps, 0.0), (0.0, eps)]):
+        p = O.rd_reaction(F, k, np.array([1.0 + du]), np.array([dv]))
+        m = O.rd_reaction(F, k, np.array([1.0 - du]), np.array([-dv]))
+        J[:, j] = [(p[0][0] - m[0][0]) / (2 * eps), (p[1][0] - m[1][0]) / (2 * eps)]
+    assert np.allclose(J, [[-F, 0.0], [0.0, -(F + k)]], rtol=1e-8, atol=1e-10)
+    rng = np.random.default_rng(8)
+    u, v = rng.uniform(0, 1, 64), rng.uniform(0, 1, 64)
+    fu, fv = O.rd_reaction(F, k, u, v)
+    assert np.allclose(fu + fv, F * (1 - u) - (F + k) * v, rtol=1e-13, atol=1e-15)
