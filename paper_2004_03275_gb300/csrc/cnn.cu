@@ -711,9 +711,9 @@ int cnn_create(int ndim, unsigned long long seed, void* stream, cnn_handle** out
     long long o = layer_off(ndim, l);
     for (long long i = 0; i < (long long)kCh[l + 1] * kCh[l] * ntaps(ndim); ++i) p[o + i] = nd_(rng);
   }
-  cudaMemcpy(h->params.p, p.data(), pb, cudaMemcpyHostToDevice);
-  cudaMemset(h->m.p, 0, pb);
-  cudaMemset(h->v.p, 0, pb);
+  if ((rc = h->cuda(cudaMemcpy(h->params.p, p.data(), pb, cudaMemcpyHostToDevice), "copy")) ||
+      (rc = h->cuda(cudaMemset(h->m.p, 0, pb), "memset")) || (rc = h->cuda(cudaMemset(h->v.p, 0, pb), "memset")))
+    return rc;
   if ((rc = h->repack())) return rc;
   if ((rc = h->cuda(cudaStreamSynchronize(h->stream), "sync"))) return rc;
   *out = h.release();
@@ -739,8 +739,9 @@ int cnn_set_params(cnn_handle* h, const float* p, long long n) {
   int rc;
   if ((rc = h->cuda(cudaMemcpyAsync(h->params.p, p, n * sizeof(float), cudaMemcpyHostToDevice, h->stream), "copy")))
     return rc;
-  cudaMemsetAsync(h->m.p, 0, n * sizeof(float), h->stream);
-  cudaMemsetAsync(h->v.p, 0, n * sizeof(float), h->stream);
+  if ((rc = h->cuda(cudaMemsetAsync(h->m.p, 0, n * sizeof(float), h->stream), "memset")) ||
+      (rc = h->cuda(cudaMemsetAsync(h->v.p, 0, n * sizeof(float), h->stream), "memset")))
+    return rc;
   h->step = 0;
   if ((rc = h->repack())) return rc;
   return h->cuda(cudaStreamSynchronize(h->stream), "sync");

@@ -1246,10 +1246,14 @@ struct Mg {
         (rc = cuda(d_inv.alloc(invoff * 8), "alloc inverse")))
       return rc;
     if ((rc = cuda(cudaMallocHost(&h_any, 4), "host alloc"))) return rc;
-    cudaMemcpy(d_inst.p, insts.data(), insts.size() * sizeof(InstDev), cudaMemcpyHostToDevice);
+    // host-to-device copy of a table (empty tables copy nothing)
+    auto upload = [&](void* dst, const void* src, size_t bytes) {
+      return bytes ? cuda(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice), "copy table") : AMR_OK;
+    };
+    if ((rc = upload(d_inst.p, insts.data(), insts.size() * sizeof(InstDev)))) return rc;
     for (int i = 0; i < n_inst; ++i)
-      cudaMemcpy(d_inv.as<double>() + insts[i].inv_off, invs[i].data(), invs[i].size() * 8, cudaMemcpyHostToDevice);
-    cudaMemset(d_rnorm.p, 0, n_inst * 8);
+      if ((rc = upload(d_inv.as<double>() + insts[i].inv_off, invs[i].data(), invs[i].size() * 8))) return rc;
+    if ((rc = cuda(cudaMemset(d_rnorm.p, 0, n_inst * 8), "memset"))) return rc;
     if (nd == 2) {  // strip heights: measured per level side, then the tile lists
       if ((rc = precision == AMR_FP64 ? tune_strips<double>() : tune_strips<float>())) return rc;
       for (int i = 0; i < n_inst; ++i) {
@@ -1280,10 +1284,11 @@ struct Mg {
         (rc = cuda(d_cinst.alloc(coarse_inst.size() * 4), "alloc")) ||
         (rc = cuda(d_crow0.alloc(coarse_row0.size() * 4), "alloc")))
       return rc;
-    cudaMemcpy(d_ch0.p, ch0.data(), ch0.size() * sizeof(Chunk), cudaMemcpyHostToDevice);
-    if (!all.empty()) cudaMemcpy(d_chall.p, all.data(), all.size() * sizeof(Chunk), cudaMemcpyHostToDevice);
-    cudaMemcpy(d_cinst.p, coarse_inst.data(), coarse_inst.size() * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(d_crow0.p, coarse_row0.data(), coarse_row0.size() * 4, cudaMemcpyHostToDevice);
+    if ((rc = upload(d_ch0.p, ch0.data(), ch0.size() * sizeof(Chunk))) ||
+        (rc = upload(d_chall.p, all.data(), all.size() * sizeof(Chunk))) ||
+        (rc = upload(d_cinst.p, coarse_inst.data(), coarse_inst.size() * 4)) ||
+        (rc = upload(d_crow0.p, coarse_row0.data(), coarse_row0.size() * 4)))
+      return rc;
     return cuda(cudaDeviceSynchronize(), "setup");
   }
 
@@ -1603,10 +1608,12 @@ struct Mg {
   int results(int* cycles, double* relres, bool* all_ok) {
     std::vector<int> cyc(ninst), fl(ninst);
     std::vector<double> lr(ninst), bn(ninst);
-    cudaMemcpy(cyc.data(), d_cycles.p, ninst * 4, cudaMemcpyDeviceToHost);
-    cudaMemcpy(fl.data(), d_failed.p, ninst * 4, cudaMemcpyDeviceToHost);
-    cudaMemcpy(lr.data(), d_lastres.p, ninst * 8, cudaMemcpyDeviceToHost);
-    if (int rc = cuda(cudaMemcpy(bn.data(), d_bnorm.p, ninst * 8, cudaMemcpyDeviceToHost), "copy")) return rc;
+    int rc;
+    if ((rc = cuda(cudaMemcpy(cyc.data(), d_cycles.p, ninst * 4, cudaMemcpyDeviceToHost), "copy")) ||
+        (rc = cuda(cudaMemcpy(fl.data(), d_failed.p, ninst * 4, cudaMemcpyDeviceToHost), "copy")) ||
+        (rc = cuda(cudaMemcpy(lr.data(), d_lastres.p, ninst * 8, cudaMemcpyDeviceToHost), "copy")) ||
+        (rc = cuda(cudaMemcpy(bn.data(), d_bnorm.p, ninst * 8, cudaMemcpyDeviceToHost), "copy")))
+      return rc;
     *all_ok = true;
     for (int i = 0; i < ninst; ++i) {
       if (cycles) cycles[i] = cyc[i];
@@ -2003,9 +2010,11 @@ int rd_last_residuals(rd_handle* h, double* initial, double* final_) {
   if (!h) return AMR_ERR_INVALID_ARG;
   Mg& M = h->mg;
   std::vector<double> ir(M.ninst), lr(M.ninst), bn(M.ninst);
-  cudaMemcpy(ir.data(), M.d_initres.p, M.ninst * 8, cudaMemcpyDeviceToHost);
-  cudaMemcpy(lr.data(), M.d_lastres.p, M.ninst * 8, cudaMemcpyDeviceToHost);
-  if (int rc = M.cuda(cudaMemcpy(bn.data(), M.d_bnorm.p, M.ninst * 8, cudaMemcpyDeviceToHost), "copy")) return rc;
+  int rc;
+  if ((rc = M.cuda(cudaMemcpy(ir.data(), M.d_initres.p, M.ninst * 8, cudaMemcpyDeviceToHost), "copy")) ||
+      (rc = M.cuda(cudaMemcpy(lr.data(), M.d_lastres.p, M.ninst * 8, cudaMemcpyDeviceToHost), "copy")) ||
+      (rc = M.cuda(cudaMemcpy(bn.data(), M.d_bnorm.p, M.ninst * 8, cudaMemcpyDeviceToHost), "copy")))
+    return rc;
   for (int i = 0; i < M.ninst; ++i) {
     double b = bn[i] > 0 ? bn[i] : 1.0;
     if (initial) initial[i] = ir[i] / b;
@@ -2049,8 +2058,9 @@ int rd_extract_crops(rd_handle* h, int ncrops, const int* inst, const int* corne
   int rc;
   if ((rc = M.cuda(dinst.alloc(ncrops * sizeof(int)), "alloc")) || (rc = M.cuda(dcorner.alloc(ncrops * 3 * sizeof(int)), "alloc")))
     return rc;
-  cudaMemcpy(dinst.p, inst, ncrops * sizeof(int), cudaMemcpyHostToDevice);
-  cudaMemcpy(dcorner.p, corner, ncrops * 3 * sizeof(int), cudaMemcpyHostToDevice);
+  if ((rc = M.cuda(cudaMemcpy(dinst.p, inst, ncrops * sizeof(int), cudaMemcpyHostToDevice), "copy")) ||
+      (rc = M.cuda(cudaMemcpy(dcorner.p, corner, ncrops * 3 * sizeof(int), cudaMemcpyHostToDevice), "copy")))
+    return rc;
   CropArgs A{};
   A.inst = M.d_inst.as<InstDev>();
   A.cinst = dinst.as<int>();

@@ -609,18 +609,18 @@ struct Tree {
         (rc = cuda(d_ub.alloc(nu * 8), "alloc")) || (rc = cuda(d_ue.alloc(nu * 8), "alloc")) ||
         (rc = cuda(cudaMallocHost(&h_red, 16), "host alloc")))
       return rc;
-    cudaMemcpy(d_leaf.p, isleaf.data(), nblk * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(d_bxy.p, bxy.data(), bxy.size() * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(d_child.p, child.data(), child.size() * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(d_leafblk.p, leaf_blk.data(), leaf_blk.size() * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(d_slot.p, slot.data(), nblk * 4, cudaMemcpyHostToDevice);
-    if (!lists.empty()) cudaMemcpy(d_lists.p, lists.data(), lists.size() * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(d_tables.p, tables.data(), tables.size() * 4, cudaMemcpyHostToDevice);
-    cudaMemset(d_x.p, 0, cells * 8);
-    cudaMemset(d_b.p, 0, cells * 8);
-    cudaMemset(d_r.p, 0, cells * 8);
-    cudaMemset(d_xold.p, 0, cells * 8);
-    cudaMemset(d_bo.p, 0, cells * 8);
+    // host-to-device copy of a table (empty tables copy nothing)
+    auto upload = [&](void* dst, const void* src, size_t bytes) {
+      return bytes ? cuda(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice), "copy table") : AMR_OK;
+    };
+    if ((rc = upload(d_leaf.p, isleaf.data(), (size_t)nblk * 4)) || (rc = upload(d_bxy.p, bxy.data(), bxy.size() * 4)) ||
+        (rc = upload(d_child.p, child.data(), child.size() * 4)) ||
+        (rc = upload(d_leafblk.p, leaf_blk.data(), leaf_blk.size() * 4)) ||
+        (rc = upload(d_slot.p, slot.data(), (size_t)nblk * 4)) || (rc = upload(d_lists.p, lists.data(), lists.size() * 4)) ||
+        (rc = upload(d_tables.p, tables.data(), tables.size() * 4)))
+      return rc;
+    for (Buf* z : {&d_x, &d_b, &d_r, &d_xold, &d_bo})
+      if ((rc = cuda(cudaMemset(z->p, 0, cells * 8), "memset"))) return rc;
     T.B = B;
     T.lmax = lmax;
     T.lam = cfg.lambda;
