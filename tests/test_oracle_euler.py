@@ -337,3 +337,27 @@ def test_gresho_chan_stays_and_converges():
     ov, op = np.log2(e32[0] / e64[0]), np.log2(e32[1] / e64[1])
     assert e64[0] < 5e-3 and e64[1] < 3e-3, (e32, e64)
     assert ov > 1.2 and op > 1.6, (ov, op)
+
+
+@pytest.mark.parametrize("rk,lo,hi", [(2, 1.8, 2.3), (3, 2.6, 3.3)])
+def test_ssprk_temporal_order(rk, lo, hi):
+    """Sec. 2.3-2.4's SSP Runge-Kutta schemes at their orders in time: on a fixed 64-cell grid
+    (smooth wave, van Leer, whose slopes are smooth functions of the data away from extrema)
+    the difference to a run at Courant number 0.02 falls by 2^order per halving of the
+    Courant number.  A wrong stage coefficient drops the order."""
+    n, T = 64, 0.5
+
+    def run(cfl):
+        g = O.Grid(ndim=1, block_nx=16, base=[n // 16], gamma=GAM, cfl=cfl, flux="hllc", limiter="vanleer", rk=rk,
+                   bc="periodic")
+        lev, crd = g.leaves()
+        x, _ = inputs.cell_centres(lev, crd, 1, 16, [n // 16, 1, 1], [0, 0, 0], [1, 1, 1])
+        g.set_prim(inputs.smooth_wave(x, 1))
+        g.run(t_end=T)
+        assert g.t == pytest.approx(T, abs=1e-14)
+        return g.get_cons()[:, 0, :].ravel()
+
+    ref = run(0.02)
+    e = np.array([np.max(np.abs(run(c) - ref)) for c in (0.8, 0.4, 0.2)])
+    orders = np.log2(e[:-1] / e[1:])
+    assert np.all((orders > lo) & (orders < hi)), (e, orders)
