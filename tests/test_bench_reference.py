@@ -1,0 +1,37 @@
+"""The reference arm of the benchmark (`bench.py --impl reference`) runs the float64 oracle on the
+host cores, so its JSON-line contract is checked here without a GPU: one line from rank 0 with the
+arm's metric, unit and cpu_baseline, zero host-device bytes, and nothing from other ranks."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def run_bench(env_extra, *args):
+    env = dict(os.environ)
+    env.update(env_extra)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", *args],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return [l for l in r.stdout.splitlines() if l.strip()]
+
+
+def test_reference_arm_prints_one_line_with_the_contract_keys():
+    # 12500 steps leave ~12 ms per step: the smallest (32^2) KH sample, a few seconds in all
+    lines = run_bench({"RANK": "0", "WORLD_SIZE": "1", "LOCAL_RANK": "0"}, "--steps", "12500", "--warmup", "0")
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["higher_is_better"] is True and d["value"] > 0
+    assert d["unit"] == "cell-stages/s" and d["steps"] == 12500 and d["warmup"] == 0
+    assert d["config"]["sample_side"] == 32
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and "32^2" in cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["ms_per_step"] > 0
+
+
+def test_reference_arm_other_ranks_print_nothing():
+    lines = run_bench({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, "--steps", "3", "--warmup", "0")
+    assert lines == []
