@@ -748,7 +748,11 @@ def main():
                 "schnakenberg": lambda: bench_schnakenberg(torch, amrvac, stream),
                 "gray_scott_tree": lambda: bench_gray_scott_tree(torch, amrvac, stream)}
         for name in want:
-            extra[name] = runs[name]()
+            # an extra workload that fails is reported as such; the headline line still prints
+            try:
+                extra[name] = runs[name]()
+            except Exception as e:  # noqa: BLE001
+                extra[name] = {"error": f"{type(e).__name__}: {e}"[:500]}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
