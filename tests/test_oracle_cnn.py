@@ -208,3 +208,27 @@ def test_operator_loss_parameter_gradient_matches_finite_differences(ndim, shape
         pm[i] -= h
         fd = (O.cnn_loss_grad(pp, x, tgt, **kw)[0] - O.cnn_loss_grad(pm, x, tgt, **kw)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(abs(fd), abs(g[i])) + 1e-11, (i, fd, g[i])
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_receptive_field_is_four_cells(ndim):
+    """Four layers of 3^ndim taps: an output depends on the inputs within Chebyshev distance 4
+    and on no input farther away; a crop with that margin reproduces the full image's output."""
+    rng = np.random.default_rng(70 + ndim)
+    p = rand_params(ndim, rng)
+    shape = (1, 5, 24, 24) if ndim == 2 else (1, 5, 12, 12, 12)
+    x = rng.uniform(0, 1, size=shape)
+    out = O.cnn_forward(p, x, ndim=ndim)
+    c = tuple(s // 2 for s in shape[2:])
+    for dist, changes in ((4, True), (5, False)):
+        xp = x.copy()
+        idx = (0, 1) + tuple(ci + (dist if d == 0 else 0) for d, ci in enumerate(c))
+        xp[idx] += 0.5
+        o2 = O.cnn_forward(p, xp, ndim=ndim)
+        diff = np.max(np.abs(o2[(0, slice(None)) + c] - out[(0, slice(None)) + c]))
+        assert (diff > 1e-9) == changes, (dist, diff)
+    # a crop of side 9 (radius 4) around a pixel gives the same output at its centre
+    sl = (slice(None), slice(None)) + tuple(slice(ci - 4, ci + 5) for ci in c)
+    oc = O.cnn_forward(p, x[sl], ndim=ndim)
+    centre = (0, slice(None)) + (4,) * ndim
+    assert np.max(np.abs(oc[centre] - out[(0, slice(None)) + c])) <= 1e-12
