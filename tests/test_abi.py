@@ -41,3 +41,20 @@ def test_load_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(amrvac, "_lib", None)
     with pytest.raises(RuntimeError):
         amrvac.load()
+
+
+def test_build_flags_keep_parity_and_target_sm103a():
+    """Every unit compiles for sm_103a only; the float64 units (compared with the oracle to
+    1e-12) are compiled without multiply-add contraction, the float32 stage units with fast math."""
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    srcs = build.sources()
+    assert srcs and all(s.endswith(".cu") for s in srcs)
+    for s in srcs:
+        flags = build.unit_flags(s)
+        if s.startswith(("euler_f64", "mg_f64")):
+            assert flags == ["--fmad=false"], s
+        elif s.startswith("euler_f32"):
+            assert flags == ["--use_fast_math"], s
+        else:
+            assert "--use_fast_math" not in flags, s
+    assert {"euler_f64_1d.cu", "euler_f64_2d.cu", "euler_f64_3d.cu", "mg_f64_tree.cu"} <= set(srcs)
