@@ -115,6 +115,14 @@ int amr_set_leaves(amr_handle* h, long long n, const int* level, const int* coor
  * through a device buffer. */
 int amr_set_state(amr_handle* h, const double* W, long long n_values, int on_device, int primitive);
 
+/* Initial condition from a host callback: prim_at(x, V, user) writes the primitive state
+ * V = (rho, v_1..v_ndim, p) at the cell centre x[3] (unused dimensions 0).  The current tree
+ * is sampled, then regridded (amr_regrid, the handle's estimator and thresholds) and resampled
+ * max_level - 1 times, so that the initial tree resolves the callback's features (Sec. 1.3);
+ * the state is the last sampling.  Synchronous; errors of amr_regrid / amr_set_state. */
+typedef void (*amr_prim_fn)(const double x[3], double* V, void* user);
+int amr_set_state_fn(amr_handle* h, amr_prim_fn prim_at, void* user);
+
 /* Copies the conserved state to a float64 array [leaf][var][cell] (converted
  * on the device for the FP32 path).  cap_values = capacity in doubles.
  * Synchronous.  A pinned host array is written in place by the conversion
@@ -420,6 +428,14 @@ int cnn_train_step(cnn_handle* h, const float* in, const float* target, int N, i
  * loss only and may be NULL for MSE.  AMR_ERR_INVALID_ARG otherwise; a later
  * gradient call with margin < 1 under the operator loss is AMR_ERR_INVALID_ARG. */
 int cnn_set_loss(cnn_handle* h, int kind, const double* kappa);
+/* cnn_forward under the name of the inference call. */
+int cnn_infer(cnn_handle* h, const float* in, int N, int D, int H, int W, float* out);
+/* Parameters to / from a file: 8-byte magic "AMRVCNN1", int32 ndim, int32 0, int64 count,
+ * count float32 values (host byte order).  cnn_load checks the magic, ndim and count
+ * (AMR_ERR_INVALID_ARG otherwise, handle unchanged) and resets Adam like cnn_set_params.
+ * File errors: AMR_ERR_INVALID_ARG with the path in cnn_last_error. */
+int cnn_save(cnn_handle* h, const char* path);
+int cnn_load(cnn_handle* h, const char* path);
 int cnn_kernel_launches(const cnn_handle* h, long long* n);
 
 /* Multigrid initial guess of rd_step: net = NULL restores the previous-step

@@ -81,6 +81,8 @@ class RdConfig(C.Structure):
 
 
 _vp, _dp, _ip, _llp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_longlong)
+# amr_prim_fn: void (*)(const double x[3], double* V, void* user)
+_PRIM_FN = C.CFUNCTYPE(None, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
 
 _SIGS = {
     "amr_create": ([C.POINTER(AmrConfig), C.POINTER(_vp)], C.c_int),
@@ -90,6 +92,7 @@ _SIGS = {
     "amr_leaf_info": ([_vp, _ip, _ip, C.c_longlong], C.c_int),
     "amr_set_leaves": ([_vp, C.c_longlong, _ip, _ip], C.c_int),
     "amr_set_state": ([_vp, _vp, C.c_longlong, C.c_int, C.c_int], C.c_int),
+    "amr_set_state_fn": ([_vp, _PRIM_FN, _vp], C.c_int),
     "amr_read_state": ([_vp, _vp, C.c_longlong, C.c_int], C.c_int),
     "amr_set_time": ([_vp, C.c_double], C.c_int),
     "amr_step": ([_vp, C.c_double, _dp, _dp], C.c_int),
@@ -126,6 +129,9 @@ _SIGS = {
     "cnn_train_step": ([_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float,
                         C.POINTER(C.c_float)], C.c_int),
     "cnn_set_loss": ([_vp, C.c_int, C.POINTER(C.c_double)], C.c_int),
+    "cnn_infer": ([_vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp], C.c_int),
+    "cnn_save": ([_vp, C.c_char_p], C.c_int),
+    "cnn_load": ([_vp, C.c_char_p], C.c_int),
     "cnn_kernel_launches": ([_vp, _llp], C.c_int),
     "rd_set_guess": ([_vp, _vp, C.c_double], C.c_int),
     "rd_set_guess_inputs": ([_vp, C.c_int], C.c_int),
@@ -287,6 +293,29 @@ class AmrSolver:
         p, dev = _ptr(W)
         n = W.numel() if hasattr(W, "numel") else W.size
         _check(self.lib.amr_set_state(self.h, p, n, dev, 1 if primitive else 0), self.h)
+
+    def set_state_fn(self, prim_at):
+        """Initial condition from a Python callable prim_at(x) -> ndim + 2 primitive values at the
+        cell centre x (3 floats; unused dimensions 0): the tree is sampled and regridded
+        max_level - 1 times (amr_set_state_fn).  One call per cell, so meant for moderate grids."""
+        nv, failure = self.nv, []
+
+        def cb(xp, vp, _user):
+            try:
+                vals = prim_at((xp[0], xp[1], xp[2]))
+                for k in range(nv):
+                    vp[k] = float(vals[k])
+            except Exception as e:  # noqa: BLE001 -- re-raised after the C call returns
+                if not failure:
+                    failure.append(e)
+                for k in range(nv):
+                    vp[k] = float("nan")
+
+        fn = _PRIM_FN(cb)
+        rc = self.lib.amr_set_state_fn(self.h, fn, None)
+        if failure:
+            raise failure[0]
+        _check(rc, self.h)
 
     def set_prim(self, V):
         self.set_state(V, primitive=True)
@@ -738,6 +767,14 @@ class CnnNet:
         _check(self.lib.cnn_train_step(self.h, x.data_ptr(), target.data_ptr(), N, D, H, W, margin, lr,
                                        C.byref(loss) if want_loss else None), self.h, "cnn_last_error")
         return loss.value if want_loss else None
+
+    def save(self, path):
+        """Parameters to a file (cnn_save)."""
+        _check(self.lib.cnn_save(self.h, os.fsencode(path)), self.h, "cnn_last_error")
+
+    def load(self, path):
+        """Parameters from a file written by save (cnn_load); resets Adam."""
+        _check(self.lib.cnn_load(self.h, os.fsencode(path)), self.h, "cnn_last_error")
 
     def set_loss(self, kind="mse", kappa=None):
         """kind "mse" or "operator" (kappa: two values, one per output channel)."""

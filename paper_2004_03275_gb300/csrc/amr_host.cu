@@ -963,6 +963,42 @@ int amr_regrid(amr_handle* h) {
   return sync_ctl(h);
 }
 
+int amr_set_state_fn(amr_handle* h, amr_prim_fn prim_at, void* user) {
+  if (!h || !prim_at) return AMR_ERR_INVALID_ARG;
+  const int nd = h->nd, B = h->B, nv = h->nv, nc = h->nc;
+  const int passes = std::max(1, h->cfg.max_level);
+  std::vector<double> W, V(nv);
+  for (int pass = 0; pass < passes; ++pass) {
+    if (pass > 0) {
+      int rc = amr_regrid(h);  // refine where the sampled state asks for it, then resample
+      if (rc) return rc;
+    }
+    const size_t nl = h->tree.leaves.size();
+    W.assign(nl * nv * nc, 0.0);
+    for (size_t l = 0; l < nl; ++l) {
+      const LeafH& L = h->tree.leaves[l];
+      double dx[3] = {0.0, 0.0, 0.0};
+      for (int d = 0; d < nd; ++d) {
+        const double cells = (double)h->cfg.base_nblocks[d] * B * (double)(1ll << (L.level - 1));
+        dx[d] = (h->cfg.xmax[d] - h->cfg.xmin[d]) / cells;
+      }
+      for (int cell = 0; cell < nc; ++cell) {
+        const int loc[3] = {cell % B, nd > 1 ? (cell / B) % B : 0, nd > 2 ? cell / (B * B) : 0};
+        double x[3] = {0.0, 0.0, 0.0};
+        for (int d = 0; d < nd; ++d) {
+          const double g = (double)L.c[d] * B + loc[d];  // global cell index on the leaf's level
+          x[d] = h->cfg.xmin[d] + (g + 0.5) * dx[d];
+        }
+        prim_at(x, V.data(), user);
+        for (int v = 0; v < nv; ++v) W[(l * nv + v) * nc + cell] = V[v];
+      }
+    }
+    int rc = amr_set_state(h, W.data(), (long long)W.size(), 0, 1);
+    if (rc) return rc;
+  }
+  return AMR_OK;
+}
+
 int amr_face_neighbors(const amr_handle* h, int* kind, int* nbr, long long cap) {
   if (!h) return AMR_ERR_INVALID_ARG;
   size_t n = h->tb.kind.size();

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstdint>
 #include <cstring>
 #include <memory>
@@ -804,6 +805,48 @@ int cnn_set_loss(cnn_handle* h, int kind, const double* kappa) {
   h->kappa[0] = (float)kappa[0];
   h->kappa[1] = (float)kappa[1];
   return AMR_OK;
+}
+
+int cnn_infer(cnn_handle* h, const float* in, int N, int D, int H, int W, float* out) {
+  return cnn_forward(h, in, N, D, H, W, out);
+}
+
+// parameter file: 8-byte magic, int32 ndim, int32 0, int64 count, count float32 (host byte order)
+static const char kCnnMagic[8] = {'A', 'M', 'R', 'V', 'C', 'N', 'N', '1'};
+
+int cnn_save(cnn_handle* h, const char* path) {
+  if (!h || !path) return AMR_ERR_INVALID_ARG;
+  std::vector<float> p((size_t)h->nparams);
+  int rc = cnn_get_params(h, p.data(), h->nparams);
+  if (rc) return rc;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return h->fail(AMR_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  const int32_t hdr[2] = {h->nd, 0};
+  const int64_t n = h->nparams;
+  bool ok = std::fwrite(kCnnMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+            std::fwrite(&n, sizeof(n), 1, f) == 1 && std::fwrite(p.data(), sizeof(float), p.size(), f) == p.size();
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? AMR_OK : h->fail(AMR_ERR_INVALID_ARG, std::string("cannot write ") + path);
+}
+
+int cnn_load(cnn_handle* h, const char* path) {
+  if (!h || !path) return AMR_ERR_INVALID_ARG;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return h->fail(AMR_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  char magic[8];
+  int32_t hdr[2];
+  int64_t n = 0;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCnnMagic, 8) == 0 &&
+            std::fread(hdr, sizeof(hdr), 1, f) == 1 && std::fread(&n, sizeof(n), 1, f) == 1 && hdr[0] == h->nd &&
+            n == h->nparams;
+  std::vector<float> p;
+  if (ok) {
+    p.resize((size_t)n);
+    ok = std::fread(p.data(), sizeof(float), p.size(), f) == p.size();
+  }
+  std::fclose(f);
+  if (!ok) return h->fail(AMR_ERR_INVALID_ARG, std::string("not a parameter file of this network: ") + path);
+  return cnn_set_params(h, p.data(), h->nparams);
 }
 
 int cnn_kernel_launches(const cnn_handle* h, long long* n) {
