@@ -242,6 +242,37 @@ def make_amr_config(ndim, block_nx, base, max_level=1, xmin=(0, 0, 0), xmax=(1, 
     return c
 
 
+CHECKPOINT_KIND = "amrvac-gb300 block-tree checkpoint v1"
+
+
+def save_checkpoint(solver, path):
+    """Writes a solver's tree (leaf levels and block coordinates, Morton order), time and float64
+    conserved state to an .npz file.  Works on any object with the AmrSolver calls used here."""
+    lev, crd = solver.leaves()
+    cfg = solver.cfg
+    np.savez(path, kind=CHECKPOINT_KIND, ndim=int(cfg.ndim), block_nx=int(cfg.block_nx),
+             base=np.array([cfg.base_nblocks[d] for d in range(3)], dtype=np.int32),
+             max_level=int(cfg.max_level), level=np.asarray(lev, dtype=np.int32),
+             coords=np.asarray(crd, dtype=np.int32), t=float(solver.t), U=np.asarray(solver.read_state()))
+
+
+def load_checkpoint(solver, path):
+    """Restores a checkpoint into a solver created with the same block geometry (ndim, block_nx,
+    base blocks, max_level): tree, then conserved state, then time.  A continuation from it
+    repeats the saved run's steps.  ValueError if the file does not match the solver."""
+    with np.load(path, allow_pickle=False) as d:
+        if str(d["kind"]) != CHECKPOINT_KIND:
+            raise ValueError(f"{path}: not a block-tree checkpoint")
+        cfg = solver.cfg
+        want = (int(cfg.ndim), int(cfg.block_nx), [cfg.base_nblocks[k] for k in range(3)], int(cfg.max_level))
+        got = (int(d["ndim"]), int(d["block_nx"]), [int(v) for v in d["base"]], int(d["max_level"]))
+        if want != got:
+            raise ValueError(f"{path}: geometry {got} does not match the solver's {want}")
+        solver.set_leaves(d["level"], d["coords"])
+        solver.set_state(np.ascontiguousarray(d["U"]), primitive=False)
+        solver.set_time(float(d["t"]))
+
+
 class AmrSolver:
     """Owns one amr_handle.  Methods map one to one onto the C calls."""
 
