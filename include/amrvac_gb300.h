@@ -180,11 +180,10 @@ int amr_kernel_launches(const amr_handle* h, long long* n);
  * CFL step and conserved totals without any device allocation.
  *
  * The paper has no counterpart: this is a service for callers that cannot
- * allocate device memory themselves -- code running while an enclosing
- * framework forbids cudaMalloc (for example during CUDA-graph stream capture
- * in that framework, or under a fixed memory budget owned by a pool
- * allocator), or latency-critical loops that cannot afford cudaMalloc's
- * implicit device synchronisation.
+ * allocate device memory themselves -- code that runs under a fixed memory
+ * budget owned by a pool allocator of an enclosing framework (which hands out
+ * its buffers and forbids cudaMalloc beside it), or latency-critical loops
+ * that cannot afford cudaMalloc's implicit device synchronisation.
  *
  * Computes, for a uniform block grid (every leaf on level 1, leaves in Morton
  * order as amr_leaf_info reports them for a fresh handle), the same two
@@ -204,7 +203,11 @@ int amr_kernel_launches(const amr_handle* h, long long* n);
  * address (cudaGetSymbolAddress); make that first call before any stream
  * capture.  Every call on a device shares the array and keeps the previous
  * call's contents (the call resets what must start at zero): calls that
- * overlap on the GPU (different streams or threads) race.  Synchronous.
+ * overlap on the GPU (different streams or threads) race.  The looked-up
+ * address is kept for the life of the process, so the call must not be used
+ * across a device reset (cudaDeviceReset) of that device.
+ * Synchronous: the call waits for cfg->stream and reads its results back
+ * into the host outputs before it returns.
  * ------------------------------------------------------------------------ */
 #define AMR_NOALLOC_MAX_LEAVES 16384
 int amr_reduce_noalloc(const amr_config* cfg, const double* U, long long nleaves, double* dt_cfl, double* totals);

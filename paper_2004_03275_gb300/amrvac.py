@@ -441,6 +441,12 @@ def reduce_noalloc(U, stream=None, **kw):
     if not dev:
         raise ValueError("U must be device memory")
     nleaves = int(np.prod(list(cfg.base_nblocks)[:cfg.ndim]))
+    # the kernel reads nleaves * (ndim + 2) * block_nx^ndim float64 values from the bare pointer
+    need = nleaves * (cfg.ndim + 2) * cfg.block_nx ** cfg.ndim
+    if str(getattr(U, "dtype", "")) != "torch.float64":
+        raise ValueError(f"U must be a float64 CUDA tensor, got {getattr(U, 'dtype', type(U))}")
+    if nleaves <= NOALLOC_MAX_LEAVES and U.numel() < need:
+        raise ValueError(f"U holds {U.numel()} values, the grid needs {need}")
     dt = C.c_double()
     tot = np.zeros(cfg.ndim + 2)
     rc = lib.amr_reduce_noalloc(C.byref(cfg), p, nleaves, C.byref(dt), tot.ctypes.data_as(_dp))

@@ -4,10 +4,11 @@
 // array of fixed size instead of memory obtained from cudaMalloc.
 //
 // For callers that cannot allocate device memory themselves, e.g. code that
-// runs while an enclosing framework forbids cudaMalloc (a stream being
-// captured into a CUDA graph, a fixed memory budget handed out by a pool, or a
-// latency-critical loop where the implicit synchronisation of cudaMalloc is not
-// acceptable).
+// runs under a fixed memory budget handed out by an enclosing framework's pool
+// allocator (which forbids cudaMalloc beside it), or a latency-critical loop
+// where the implicit synchronisation of cudaMalloc is not acceptable.  The
+// address of the array is looked up once per device and kept for the life of
+// the process: the call must not be used across a reset of that device.
 #include <cuda_runtime.h>
 
 #include <cstddef>

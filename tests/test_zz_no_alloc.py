@@ -42,3 +42,15 @@ def test_noalloc_rejects_too_many_leaves():
     with pytest.raises(amrvac.AmrError) as ei:
         amrvac.reduce_noalloc(U, **kw)
     assert ei.value.code == -7
+
+
+def test_noalloc_binding_rejects_wrong_dtype_and_short_state():
+    """The kernel reads nleaves * (ndim + 2) * B^ndim float64 values through a bare pointer, so the
+    binding refuses a float32 state or a short one on the host, before any launch."""
+    torch = pytest.importorskip("torch")
+    kw = kh(64)
+    need = 16 * 4 * 256
+    with pytest.raises(ValueError):
+        amrvac.reduce_noalloc(torch.zeros(need, device="cuda", dtype=torch.float32), **kw)
+    with pytest.raises(ValueError):
+        amrvac.reduce_noalloc(torch.zeros(need - 1, device="cuda", dtype=torch.float64), **kw)
