@@ -242,35 +242,52 @@ def make_amr_config(ndim, block_nx, base, max_level=1, xmin=(0, 0, 0), xmax=(1, 
     return c
 
 
-CHECKPOINT_KIND = "amrvac-gb300 block-tree checkpoint v1"
+CHECKPOINT_KIND = "amrvac-gb300 block-tree checkpoint v2"
 
 
-def save_checkpoint(solver, path):
-    """Writes a solver's tree (leaf levels and block coordinates, Morton order), time and float64
-    conserved state to an .npz file.  Works on any object with the AmrSolver calls used here."""
+def _update_fields(cfg):
+    """Every amr_config field that changes the update or the regrid (the stream and the
+    capacity do not), as plain Python values in a fixed order."""
+    return {
+        "ndim": int(cfg.ndim), "block_nx": int(cfg.block_nx),
+        "base": [int(cfg.base_nblocks[d]) for d in range(3)], "max_level": int(cfg.max_level),
+        "xmin": [float(cfg.xmin[d]) for d in range(3)], "xmax": [float(cfg.xmax[d]) for d in range(3)],
+        "gamma": float(cfg.gamma), "flux": int(cfg.flux), "limiter": int(cfg.limiter), "rk": int(cfg.rk),
+        "cfl": float(cfg.cfl), "bc": [[int(cfg.bc[d][s]) for s in range(2)] for d in range(3)],
+        "precision": int(cfg.precision), "refine_tol": float(cfg.refine_tol),
+        "coarsen_frac": float(cfg.coarsen_frac), "wavefilter": float(cfg.wavefilter),
+        "refine_var_mask": int(cfg.refine_var_mask),
+    }
+
+
+def save_checkpoint(solver, path, steps=0):
+    """Writes a solver's tree (leaf levels and block coordinates, Morton order), time, step
+    count and float64 conserved state to an .npz file, with every configuration field that
+    affects the update.  Works on any object with the AmrSolver calls used here."""
+    import json
     lev, crd = solver.leaves()
-    cfg = solver.cfg
-    np.savez(path, kind=CHECKPOINT_KIND, ndim=int(cfg.ndim), block_nx=int(cfg.block_nx),
-             base=np.array([cfg.base_nblocks[d] for d in range(3)], dtype=np.int32),
-             max_level=int(cfg.max_level), level=np.asarray(lev, dtype=np.int32),
-             coords=np.asarray(crd, dtype=np.int32), t=float(solver.t), U=np.asarray(solver.read_state()))
+    np.savez(path, kind=CHECKPOINT_KIND, config=json.dumps(_update_fields(solver.cfg)),
+             level=np.asarray(lev, dtype=np.int32), coords=np.asarray(crd, dtype=np.int32), t=float(solver.t),
+             steps=int(steps), U=np.asarray(solver.read_state()))
 
 
 def load_checkpoint(solver, path):
-    """Restores a checkpoint into a solver created with the same block geometry (ndim, block_nx,
-    base blocks, max_level): tree, then conserved state, then time.  A continuation from it
-    repeats the saved run's steps.  ValueError if the file does not match the solver."""
+    """Restores a checkpoint into a solver created with the same configuration (geometry,
+    domain, physics, scheme, precision and refinement fields): tree, then conserved state,
+    then time.  Returns the saved step count.  A continuation from it repeats the saved
+    run's steps.  ValueError if the file does not match the solver."""
+    import json
     with np.load(path, allow_pickle=False) as d:
-        if str(d["kind"]) != CHECKPOINT_KIND:
+        if "kind" not in d.files or str(d["kind"]) != CHECKPOINT_KIND:
             raise ValueError(f"{path}: not a block-tree checkpoint")
-        cfg = solver.cfg
-        want = (int(cfg.ndim), int(cfg.block_nx), [cfg.base_nblocks[k] for k in range(3)], int(cfg.max_level))
-        got = (int(d["ndim"]), int(d["block_nx"]), [int(v) for v in d["base"]], int(d["max_level"]))
-        if want != got:
-            raise ValueError(f"{path}: geometry {got} does not match the solver's {want}")
+        want, got = _update_fields(solver.cfg), json.loads(str(d["config"]))
+        diff = sorted(k for k in want if want[k] != got.get(k))
+        if diff:
+            raise ValueError(f"{path}: configuration differs from the solver's in {diff}")
         solver.set_leaves(d["level"], d["coords"])
         solver.set_state(np.ascontiguousarray(d["U"]), primitive=False)
         solver.set_time(float(d["t"]))
+        return int(d["steps"])
 
 
 class AmrSolver:
@@ -788,6 +805,15 @@ class CnnNet:
         if out is None:
             out = torch.empty((x.shape[0], 2) + tuple(x.shape[2:]), dtype=torch.float32, device=x.device)
         _check(self.lib.cnn_forward(self.h, x.data_ptr(), N, D, H, W, out.data_ptr()), self.h, "cnn_last_error")
+        return out
+
+    def infer(self, x, out=None):
+        """cnn_infer: the forward pass under the inference call's name."""
+        import torch
+        N, D, H, W = self._dims(x)
+        if out is None:
+            out = torch.empty((x.shape[0], 2) + tuple(x.shape[2:]), dtype=torch.float32, device=x.device)
+        _check(self.lib.cnn_infer(self.h, x.data_ptr(), N, D, H, W, out.data_ptr()), self.h, "cnn_last_error")
         return out
 
     def gradient(self, x, target, margin=0):

@@ -65,6 +65,37 @@ def test_other_geometry_is_refused(tmp_path, other):
     amrvac.save_checkpoint(a, path)
     with pytest.raises(ValueError):
         amrvac.load_checkpoint(FakeSolver(**other), path)
+
+
+@pytest.mark.parametrize("field,value", [("gamma", 5 / 3), ("cfl", 0.5), ("flux", 1), ("limiter", 2), ("rk", 2),
+                                         ("precision", 1), ("refine_tol", 0.1), ("coarsen_frac", 0.25),
+                                         ("wavefilter", 0.02), ("refine_var_mask", 3)])
+def test_other_physics_or_scheme_is_refused(tmp_path, field, value):
+    """A file written under one scheme, physics or refinement setting does not load into a solver
+    with another: the continuation would not repeat the saved run."""
+    a = FakeSolver()
+    path = tmp_path / "ck.npz"
+    amrvac.save_checkpoint(a, path, steps=7)
+    b = FakeSolver()
+    assert amrvac.load_checkpoint(b, path) == 7
+    c = FakeSolver()
+    setattr(c.cfg, field, value)
+    with pytest.raises(ValueError, match=field):
+        amrvac.load_checkpoint(c, path)
+
+
+def test_other_domain_or_boundaries_are_refused(tmp_path):
+    a = FakeSolver()
+    path = tmp_path / "ck.npz"
+    amrvac.save_checkpoint(a, path)
+    b = FakeSolver()
+    b.cfg.xmax[0] = 2.0
+    with pytest.raises(ValueError, match="xmax"):
+        amrvac.load_checkpoint(b, path)
+    c = FakeSolver()
+    c.cfg.bc[1][0] = 1
+    with pytest.raises(ValueError, match="bc"):
+        amrvac.load_checkpoint(c, path)
     np.savez(tmp_path / "x.npz", kind="something else")
     with pytest.raises(ValueError):
         amrvac.load_checkpoint(FakeSolver(), tmp_path / "x.npz")
