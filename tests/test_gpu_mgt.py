@@ -1,11 +1,11 @@
 """GPU parity of the multigrid on a 2D block quadtree (float64) against the oracle.
 
 The composite operator is the same arithmetic on both sides (no multiply-add contraction
-on the GPU unit): within 1e-12 of max|Ax|.  V-cycles agree to round-off except for the
-base-level correction solves, which both sides run with the uniform multigrid until the
-base residual has fallen by base_rtol (1e-13 in the fixed-cycle test, where the iterates
-then agree within 1e-10 of max|x|); converged solutions (rtol 1e-10, base_rtol 1e-3) agree
-within 1e-9."""
+on the GPU unit): within 1e-12 of max|Ax|.  The base-level correction solves run the uniform
+multigrid on both sides (multiply-add contraction on the GPU's uniform unit, none in the
+oracle) until the base residual has fallen by base_rtol; with base_rtol 1e-13 the iterates of
+fixed V-cycle counts agree within 1e-12 of max|x| (measured: at most 1.9e-15), and so do the
+converged solutions at rtol 1e-10 (measured: at most 4.9e-15), with the same cycle counts."""
 import numpy as np
 import pytest
 
@@ -47,8 +47,8 @@ def test_fixed_vcycles_match_oracle(case, ncyc):
     cyc, rr = s.solve(b, x, fixed_cycles=ncyc)
     xo, co, ro = O.amg_solve(lev, crd, b, np.zeros_like(b), nb, B, L, lam, fixed_cycles=ncyc, base_rtol=1e-13)
     assert cyc == ncyc == co
-    assert np.max(np.abs(x - xo)) <= 1e-10 * np.max(np.abs(xo))
-    assert rr == pytest.approx(ro, rel=1e-3, abs=1e-14)
+    assert np.max(np.abs(x - xo)) <= 1e-12 * np.max(np.abs(xo))
+    assert rr == pytest.approx(ro, rel=1e-9, abs=1e-15)
 
 
 @pytest.mark.parametrize("case", trees(), ids=lambda c: c[0])
@@ -62,8 +62,8 @@ def test_converged_solve_matches_oracle(case):
     x = np.zeros_like(b)
     cyc, rr = s.solve(b, x)
     xo, co, ro = O.amg_solve(lev, crd, b, np.zeros_like(b), nb, B, L, lam, rtol=1e-10)
-    assert rr <= 1e-10 and abs(cyc - co) <= 1
-    assert np.max(np.abs(x - xo)) <= 1e-9 * np.max(np.abs(xo))
+    assert rr <= 1e-10 and cyc == co
+    assert np.max(np.abs(x - xo)) <= 1e-12 * np.max(np.abs(xo))
     r = b - O.amg_apply(lev, crd, x, nb, B, L, lam)
     assert np.max(np.abs(r)) <= 1e-10 * np.max(np.abs(b)) * 1.0001
 
@@ -115,8 +115,8 @@ def test_gray_scott_steps_match_oracle():
     for _ in range(3):
         uo, vo, c = O.amg_rd_step(lev, crd, uo, vo, nb, B, L, **p)
         co.append(c)
-    assert np.all(np.abs(cyc - np.array(co)) <= 1), (cyc, co)
-    assert np.max(np.abs(ug - uo)) <= 1e-11 and np.max(np.abs(vg - vo)) <= 1e-11
+    assert np.array_equal(np.asarray(cyc).ravel(), np.asarray(co).ravel()), (cyc, co)
+    assert np.max(np.abs(ug - uo)) <= 1e-12 * np.max(np.abs(uo)) and np.max(np.abs(vg - vo)) <= 1e-12 * np.max(np.abs(vo))
 
 
 def test_gray_scott_tree_keeps_the_homogeneous_state():
@@ -174,4 +174,4 @@ def test_gray_scott_with_regrids_matches_oracle():
     gl, gc = s.leaves()
     assert np.array_equal(gl, lo) and np.array_equal(gc, co)
     ug, vg = s.read_state()
-    assert np.max(np.abs(ug - uo)) <= 1e-11 and np.max(np.abs(vg - vo)) <= 1e-11
+    assert np.max(np.abs(ug - uo)) <= 1e-12 * np.max(np.abs(uo)) and np.max(np.abs(vg - vo)) <= 1e-12 * np.max(np.abs(vo))
