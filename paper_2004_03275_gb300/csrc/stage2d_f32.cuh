@@ -23,6 +23,18 @@ namespace f32 {
 
 __device__ __forceinline__ float rcp(float x) { return __fdividef(1.f, x); }
 
+// Packed pairs: one f32x2 add / multiply / multiply-add (Blackwell) does two lanes of float32
+// work, each element rounded as the scalar operation would be.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b, rounded once (b * -1 is exact)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b) {
+  return make_float2(cx ? a.x : b.x, cy ? a.y : b.y);
+}
+
 // s- / s+ times one half: the offsets from the cell value to its two face values
 template <int LIM>
 __device__ __forceinline__ void half_slopes(float a, float b, float& hm, float& hp) {
@@ -55,12 +67,55 @@ __device__ __forceinline__ void half_slopes(float a, float b, float& hm, float& 
   }
 }
 
+// half_slopes for two variables at once (same limiters, packed arithmetic where it applies)
+template <int LIM>
+__device__ __forceinline__ void half_slopes2(float2 a, float2 b, float2& hm, float2& hp) {
+  if (LIM == LIM_NONE) {
+    hm = bc2(0.f);
+    hp = bc2(0.f);
+  } else if (LIM == LIM_MINMOD) {
+    const float2 ab = mul2(a, b);
+    float2 s = make_float2(a.x > 0.f ? fminf(a.x, b.x) : fmaxf(a.x, b.x), a.y > 0.f ? fminf(a.y, b.y) : fmaxf(a.y, b.y));
+    s = sel2(ab.x > 0.f, ab.y > 0.f, mul2(s, bc2(0.5f)), bc2(0.f));
+    hm = s;
+    hp = s;
+  } else if (LIM == LIM_VANLEER) {  // (2ab/(a+b))/2
+    const float2 ab = mul2(a, b), d = add2(a, b);
+    float2 s = mul2(ab, make_float2(rcp(d.x), rcp(d.y)));
+    s = sel2(ab.x > 0.f, ab.y > 0.f, s, bc2(0.f));
+    hm = s;
+    hp = s;
+  } else if (LIM == LIM_MC) {  // minmod((a+b)/2, 2a, 2b) / 2
+    const float2 ab = mul2(a, b), q = mul2(add2(a, b), bc2(0.25f));
+    float2 s = make_float2(fminf(fminf(fabsf(q.x), fabsf(a.x)), fabsf(b.x)), fminf(fminf(fabsf(q.y), fabsf(a.y)), fabsf(b.y)));
+    s = sel2(ab.x > 0.f, ab.y > 0.f, make_float2(copysignf(s.x, a.x), copysignf(s.y, a.y)), bc2(0.f));
+    hm = s;
+    hp = s;
+  } else {  // Koren
+    const float2 ab = mul2(a, b);
+    const float2 A = make_float2(fabsf(a.x), fabsf(a.y)), B = make_float2(fabsf(b.x), fabsf(b.y));
+    const float2 u6 = fma2(A, bc2(1.f / 3.f), mul2(B, bc2(1.f / 6.f)));
+    const float2 d6 = fma2(B, bc2(1.f / 3.f), mul2(A, bc2(1.f / 6.f)));
+    const float2 up = make_float2(fminf(fminf(A.x, u6.x), B.x), fminf(fminf(A.y, u6.y), B.y));
+    const float2 dn = make_float2(fminf(fminf(B.x, d6.x), A.x), fminf(fminf(B.y, d6.y), A.y));
+    const bool sx = ab.x > 0.f, sy = ab.y > 0.f;
+    hp = sel2(sx, sy, make_float2(copysignf(up.x, b.x), copysignf(up.y, b.y)), bc2(0.f));
+    hm = sel2(sx, sy, make_float2(copysignf(dn.x, a.x), copysignf(dn.y, a.y)), bc2(0.f));
+  }
+}
+
+// sound speed c = sqrt(gamma p / rho), formed as (gamma p) / sqrt(gamma p rho): one
+// special-function operation instead of a reciprocal and a square root
+__device__ __forceinline__ float sound(float r, float p, float gam) {
+  const float gp = gam * p;
+  return gp * rsqrtf(gp * r);
+}
+
 // Riemann flux normal to x of the local frame (u normal, w tangential).
 template <int FLUX>
 __device__ __forceinline__ void flux2(float rL, float uL, float wL, float pL, float rR, float uR, float wR, float pR,
                                       float gam, float igm1, float* F) {
-  float irL = rcp(rL), irR = rcp(rR);
-  float cL = sqrtf(gam * pL * irL), cR = sqrtf(gam * pR * irR);
+  const float cL = sound(rL, pL, gam), cR = sound(rR, pR, gam);
   if (FLUX == FLUX_TVDLF) {
     float EL = pL * igm1 + 0.5f * rL * (uL * uL + wL * wL);
     float ER = pR * igm1 + 0.5f * rR * (uR * uR + wR * wR);
@@ -95,13 +150,15 @@ __device__ __forceinline__ void flux2(float rL, float uL, float wL, float pL, fl
   float Ss = (pR - pL + aL * uL - aR * uR) * rcp(aL - aR);
   bool left = SL >= 0.f || (SR > 0.f && Ss >= 0.f);
   float rK = left ? rL : rR, uK = left ? uL : uR, wK = left ? wL : wR, pK = left ? pL : pR;
-  float aK = left ? aL : aR, SK = left ? SL : SR, irK = left ? irL : irR;
+  float aK = left ? aL : aR, SK = left ? SL : SR;
   float EK = pK * igm1 + 0.5f * rK * (uK * uK + wK * wK);
   float mK = rK * uK;
   float FK[4] = {mK, mK * uK + pK, mK * wK, (EK + pK) * uK};
   float UK[4] = {rK, mK, rK * wK, EK};
-  float fac = aK * rcp(SK - Ss);
-  float Us[4] = {fac, fac * Ss, fac * wK, fac * (EK * irK + (Ss - uK) * (Ss + pK * rcp(aK)))};
+  // fac = a_K / (S_K - S*); E* = fac (E_K / rho_K + (S* - u_K) S*) + (S* - u_K) p_K / (S_K - S*),
+  // the star energy with fac (S* - u_K) p_K / a_K written without dividing by a_K
+  float q = rcp(SK - Ss), fac = aK * q, d = Ss - uK;
+  float Us[4] = {fac, fac * Ss, fac * wK, fac * (EK * rcp(rK) + d * Ss) + d * pK * q};
   bool sub = SL < 0.f && SR > 0.f;
 #pragma unroll
   for (int v = 0; v < 4; ++v) F[v] = sub ? FK[v] + SK * (Us[v] - UK[v]) : FK[v];

@@ -46,39 +46,51 @@ constexpr int kTmaWaitLimit = 1 << 20;
 
 namespace march {
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ float4 prim(float r, float mx, float my, float e, float gm1) {
   float ir = f32::rcp(r);
   float vx = mx * ir, vy = my * ir;
   return make_float4(r, vx, vy, gm1 * (e - 0.5f * (mx * vx + my * vy)));
 }
 
-// lower (toward -d) and upper (toward +d) face values of the cell w0 between wm and wp
+// lower (toward -d) and upper (toward +d) face values of the cell w0 from its differences to the
+// cell below, dm = w0 - wm, and to the cell above, dp = wp - w0; the limiter runs on the variable
+// pairs (rho, v_x) and (v_y, p) with packed arithmetic
 template <int LIM>
-__device__ __forceinline__ void faces(const float4& wm, const float4& w0, const float4& wp, float4& lo, float4& hi) {
-  float hm, hp;
-  f32::half_slopes<LIM>(w0.x - wm.x, wp.x - w0.x, hm, hp);
-  lo.x = w0.x - hm;
-  hi.x = w0.x + hp;
-  f32::half_slopes<LIM>(w0.y - wm.y, wp.y - w0.y, hm, hp);
-  lo.y = w0.y - hm;
-  hi.y = w0.y + hp;
-  f32::half_slopes<LIM>(w0.z - wm.z, wp.z - w0.z, hm, hp);
-  lo.z = w0.z - hm;
-  hi.z = w0.z + hp;
-  f32::half_slopes<LIM>(w0.w - wm.w, wp.w - w0.w, hm, hp);
-  lo.w = w0.w - hm;
-  hi.w = w0.w + hp;
+__device__ __forceinline__ void faces(const float4& w0, const float4& dm, const float4& dp, float4& lo, float4& hi) {
+  using namespace f32;
+  float2 hm, hp;
+  const float2 a0 = make_float2(w0.x, w0.y), a1 = make_float2(w0.z, w0.w);
+  half_slopes2<LIM>(make_float2(dm.x, dm.y), make_float2(dp.x, dp.y), hm, hp);
+  const float2 l0 = sub2(a0, hm), h0 = add2(a0, hp);
+  half_slopes2<LIM>(make_float2(dm.z, dm.w), make_float2(dp.z, dp.w), hm, hp);
+  const float2 l1 = sub2(a1, hm), h1 = add2(a1, hp);
+  lo = make_float4(l0.x, l0.y, l1.x, l1.y);
+  hi = make_float4(h0.x, h0.y, h1.x, h1.y);
+}
+
+__device__ __forceinline__ float4 diff(const float4& a, const float4& b) {  // a - b, packed
+  const float2 d0 = f32::sub2(make_float2(a.x, a.y), make_float2(b.x, b.y));
+  const float2 d1 = f32::sub2(make_float2(a.z, a.w), make_float2(b.z, b.w));
+  return make_float4(d0.x, d0.y, d1.x, d1.y);
 }
 
 // flux through the face between cells a (left) and b (right) from face states L, R;
 // first order (the cell values) if a reconstructed density or pressure is not
-// positive.  Result in variable order (rho, m_x, m_y, E).
+// positive (a warp-uniform branch, taken only when some lane needs it).  Result in
+// variable order (rho, m_x, m_y, E).
 template <int FLUX, bool ISY>
 __device__ __forceinline__ void flux(float4 L, float4 R, const float4& a, const float4& b, float gam, float igm1,
                                      float* F) {
-  if (!(L.x > 0.f) || !(R.x > 0.f) || !(L.w > 0.f) || !(R.w > 0.f)) {
-    L = a;
-    R = b;
+  const bool ok = L.x > 0.f && R.x > 0.f && L.w > 0.f && R.w > 0.f;
+  if (__any_sync(0xffffffffu, !ok)) {
+    if (!ok) {
+      L = a;
+      R = b;
+    }
   }
   float G[4];
   if (ISY) {
@@ -99,6 +111,14 @@ __device__ __forceinline__ void flux(float4 L, float4 R, const float4& a, const 
 __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
   float s = hi + x, bb = s - hi;
   lo += (hi - (s - bb)) + (x - bb);
+  hi = s;
+}
+
+// TwoSum accumulation of a variable pair, packed; each element as two_sum_add
+__device__ __forceinline__ void two_sum_add2(float2& hi, float2& lo, float2 x) {
+  using namespace f32;
+  const float2 s = add2(hi, x), bb = sub2(s, hi);
+  lo = add2(lo, add2(sub2(hi, sub2(s, bb)), sub2(x, bb)));
   hi = s;
 }
 
@@ -188,6 +208,14 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4)
       for (int v = 0; v < NV; ++v) gu[f][v] = __ldg(&src[v * stride]);
     }
     lev = __ldg(&a.level[leaf]);
+    // U^n of this leaf is read only by the y march, late: ask for it in L2 now (one 128-byte
+    // line per lane), so that those loads find it there instead of in DRAM
+    if (!FIRST) march::prefetch_l2(a.U0 + (size_t)leaf * NV * NC + lane * 32);
+    // persistent last stage: the next group's leaf too, whose copy is issued only after this one
+    if (LAST) {
+      const int nl = (grp + (int)gridDim.x) * kMarchWarps + warp;
+      if (nl < a.nleaves) march::prefetch_l2(a.Us + (size_t)nl * NV * NC + lane * 32);
+    }
   };
   if (active) load_leaf();
   float dt;
@@ -200,7 +228,7 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4)
 
   float rate = 0.f;
   int bad = 0;
-  float th[NV] = {0.f, 0.f, 0.f, 0.f}, tl[NV] = {0.f, 0.f, 0.f, 0.f};
+  float2 th[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, tl[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 
   while (true) {
     if (TMA && active) {
@@ -257,18 +285,21 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4)
         const int j = lo16;
         const float4* row = &M.T[j + 2][2];  // row[c] = W(c, j)
         float4 wm = row[c0 - 2], w0 = row[c0 - 1], wp = row[c0], wnext = row[c0 + 1];
+        float4 dm = march::diff(w0, wm), dp = march::diff(wp, w0);
         float4 lo, hiPrev;
-        march::faces<LIM>(wm, w0, wp, lo, hiPrev);  // cell c0-1: its upper face value
+        march::faces<LIM>(w0, dm, dp, lo, hiPrev);  // cell c0-1: its upper face value
         wm = w0;
         w0 = wp;
+        dm = dp;
         float Fp[NV];
 #pragma unroll
         for (int k = 0; k <= 8; ++k) {
           const int cc = c0 + k;  // cell whose slope is formed; face cc-1/2
           wp = wnext;
           if (k < 8) wnext = row[cc + 2];
+          dp = march::diff(wp, w0);
           float4 hi;
-          march::faces<LIM>(wm, w0, wp, lo, hi);
+          march::faces<LIM>(w0, dm, dp, lo, hi);
           float F[NV];
           march::flux<FLUX, false>(hiPrev, lo, wm, w0, gam, igm1, F);
           if (a.has_ffx && ((h == 0 && k == 0) || (h == 1 && k == 8))) {
@@ -277,12 +308,14 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4)
 #pragma unroll
               for (int v = 0; v < NV; ++v) a.fflux[((size_t)slot * NV + v) * B + j] = F[v];
           }
-          if (k > 0) M.E[j][cc - 1] = make_float4(F[0] - Fp[0], F[1] - Fp[1], F[2] - Fp[2], F[3] - Fp[3]);
+          if (k > 0)
+            M.E[j][cc - 1] = march::diff(make_float4(F[0], F[1], F[2], F[3]), make_float4(Fp[0], Fp[1], Fp[2], Fp[3]));
 #pragma unroll
           for (int v = 0; v < NV; ++v) Fp[v] = F[v];
           hiPrev = hi;
           wm = w0;
           w0 = wp;
+          dm = dp;
         }
       }
       __syncwarp();
@@ -293,10 +326,12 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4)
         const float4* col = &M.T[2][i + 2];  // col[r * 21] = W(i, r)
         constexpr int RS = 21;
         float4 wm = col[(c0 - 2) * RS], w0 = col[(c0 - 1) * RS], wp = col[c0 * RS], wnext = col[(c0 + 1) * RS];
+        float4 dm = march::diff(w0, wm), dp = march::diff(wp, w0);
         float4 lo, hiPrev;
-        march::faces<LIM>(wm, w0, wp, lo, hiPrev);
+        march::faces<LIM>(w0, dm, dp, lo, hiPrev);
         wm = w0;
         w0 = wp;
+        dm = dp;
         float Fp[NV];
         const float* U0l = a.U0 + (size_t)leaf * NV * NC;
         float* Ol = a.out + (size_t)leaf * NV * NC;
@@ -315,8 +350,9 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4)
           const int rr = c0 + k;  // cell whose slope is formed; face rr-1/2
           wp = wnext;
           if (k < 8) wnext = col[(rr + 2) * RS];
+          dp = march::diff(wp, w0);
           float4 hi;
-          march::faces<LIM>(wm, w0, wp, lo, hi);
+          march::faces<LIM>(w0, dm, dp, lo, hi);
           float F[NV];
           march::flux<FLUX, true>(hiPrev, lo, wm, w0, gam, igm1, F);
           if (a.has_ffx && ((h == 0 && k == 0) || (h == 1 && k == 8))) {
@@ -346,23 +382,33 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4)
                 un2[v] = __ldg(&Ul[v * NC + q + 2 * B]);
                 u0n2[v] = FIRST ? 0.f : __ldg(&U0l[v * NC + q + 2 * B]);
               }
+            // div = E_x idx + (F - F_prev) idy; T = U^(s) - dt div; SSPRK: T + alpha (U^n - T); on the
+            // variable pairs (rho, m_x) and (m_y, E), packed
             float Un[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-              float div = ex[v] * idx + (F[v] - Fp[v]) * idy;
-              float tmp = uc[v] - dt * div;
-              Un[v] = FIRST ? tmp : ssp_combine(a.alpha, a.beta, u0c[v], tmp);
-              Ol[v * NC + q] = Un[v];
+            for (int w = 0; w < 2; ++w) {
+              using namespace f32;
+              const float2 dF = sub2(make_float2(F[2 * w], F[2 * w + 1]), make_float2(Fp[2 * w], Fp[2 * w + 1]));
+              const float2 div = fma2(make_float2(ex[2 * w], ex[2 * w + 1]), bc2(idx), mul2(dF, bc2(idy)));
+              const float2 tmp = fma2(bc2(-dt), div, make_float2(uc[2 * w], uc[2 * w + 1]));
+              const float2 un2 =
+                  FIRST ? tmp : fma2(bc2(a.alpha), sub2(make_float2(u0c[2 * w], u0c[2 * w + 1]), tmp), tmp);
+              Un[2 * w] = un2.x;
+              Un[2 * w + 1] = un2.y;
             }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Ol[v * NC + q] = Un[v];
             if constexpr (LAST) {
               float ir = f32::rcp(Un[0]);
-              float vx = Un[1] * ir, vy = Un[2] * ir;
+              const float2 vv = f32::mul2(make_float2(Un[1], Un[2]), f32::bc2(ir));
+              const float vx = vv.x, vy = vv.y;
               float p = gm1 * (Un[3] - 0.5f * (Un[1] * vx + Un[2] * vy));
               if (!(Un[0] > 0.f) || !(p > 0.f)) bad = 1;
               float cs = sqrtf(gam * p * ir);
               rate = fmaxf(rate, (fabsf(vx) + cs) * idx + (fabsf(vy) + cs) * idy);
 #pragma unroll
-              for (int v = 0; v < NV; ++v) march::two_sum_add(th[v], tl[v], Un[v] * vscale);
+              for (int w = 0; w < 2; ++w)
+                march::two_sum_add2(th[w], tl[w], f32::mul2(make_float2(Un[2 * w], Un[2 * w + 1]), f32::bc2(vscale)));
             }
           }
 #pragma unroll
@@ -370,6 +416,7 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4)
           hiPrev = hi;
           wm = w0;
           w0 = wp;
+          dm = dp;
         }
       }
     }
@@ -387,10 +434,11 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4)
   if (lane == 0) wrate[warp] = rate;
   // each warp parks its (hi, lo) pairs in its own E array, which its y march no longer reads
   float* park = reinterpret_cast<float*>(&M.E[0][0]);
+  const float thv[NV] = {th[0].x, th[0].y, th[1].x, th[1].y}, tlv[NV] = {tl[0].x, tl[0].y, tl[1].x, tl[1].y};
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    park[v * 32 + lane] = th[v];
-    park[(NV + v) * 32 + lane] = tl[v];
+    park[v * 32 + lane] = thv[v];
+    park[(NV + v) * 32 + lane] = tlv[v];
   }
   if (bad) sbad = 1;
   __syncthreads();

@@ -28,8 +28,7 @@ namespace f32 {
 template <int FLUX>
 __device__ __forceinline__ void flux3(float rL, float uL, float vL, float wL, float pL, float rR, float uR, float vR,
                                       float wR, float pR, float gam, float igm1, float* F) {
-  float irL = rcp(rL), irR = rcp(rR);
-  float cL = sqrtf(gam * pL * irL), cR = sqrtf(gam * pR * irR);
+  const float cL = sound(rL, pL, gam), cR = sound(rR, pR, gam);
   if (FLUX == FLUX_TVDLF) {
     float EL = pL * igm1 + 0.5f * rL * (uL * uL + vL * vL + wL * wL);
     float ER = pR * igm1 + 0.5f * rR * (uR * uR + vR * vR + wR * wR);
@@ -65,13 +64,14 @@ __device__ __forceinline__ void flux3(float rL, float uL, float vL, float wL, fl
   float Ss = (pR - pL + aL * uL - aR * uR) * rcp(aL - aR);
   bool left = SL >= 0.f || (SR > 0.f && Ss >= 0.f);
   float rK = left ? rL : rR, uK = left ? uL : uR, vK = left ? vL : vR, wK = left ? wL : wR, pK = left ? pL : pR;
-  float aK = left ? aL : aR, SK = left ? SL : SR, irK = left ? irL : irR;
+  float aK = left ? aL : aR, SK = left ? SL : SR;
   float EK = pK * igm1 + 0.5f * rK * (uK * uK + vK * vK + wK * wK);
   float mK = rK * uK;
   float FK[5] = {mK, mK * uK + pK, mK * vK, mK * wK, (EK + pK) * uK};
   float UK[5] = {rK, mK, rK * vK, rK * wK, EK};
-  float fac = aK * rcp(SK - Ss);
-  float Us[5] = {fac, fac * Ss, fac * vK, fac * wK, fac * (EK * irK + (Ss - uK) * (Ss + pK * rcp(aK)))};
+  // star energy without dividing by a_K (same form as flux2)
+  float q = rcp(SK - Ss), fac = aK * q, d = Ss - uK;
+  float Us[5] = {fac, fac * Ss, fac * vK, fac * wK, fac * (EK * rcp(rK) + d * Ss) + d * pK * q};
   bool sub = SL < 0.f && SR > 0.f;
 #pragma unroll
   for (int v = 0; v < 5; ++v) F[v] = sub ? FK[v] + SK * (Us[v] - UK[v]) : FK[v];
