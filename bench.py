@@ -446,35 +446,44 @@ CNN_FLOP_PER_PIXEL_2D = 11232.0
 # and writes 2 float32 channels (8 B).  51 FLOP/B overall, below GB300's ~285 FLOP/B ridge
 # (measured bf16 peak / measured HBM bandwidth), so the attainable roofline is the HBM one.
 CNN_BYTES_PER_PIXEL_2D = 52.0 + 64.0 + 64.0 + 40.0
+# the fused inference reads the five float32 input channels and writes the two float32 outputs
+CNN_FUSED_BYTES_PER_PIXEL_2D = 5 * 4.0 + 2 * 4.0
 
 
 def bench_cnn_forward(torch, amrvac, stream, peak_tflops, hbm_gbs):
-    """Inference of the learned-guess network on one 2048^2 grid (5 input channels), CUDA events."""
+    """Inference of the learned-guess network on one 2048^2 grid (5 input channels), CUDA events:
+    the fused single-pass kernel (cnn_infer; the inference the solver's guess runs) and the
+    layer-by-layer network (cnn_forward, exact GELU; the training forward pass)."""
     net = amrvac.CnnNet(ndim=2, seed=3, stream=stream.cuda_stream)
     x = torch.from_numpy(np.random.default_rng(3).uniform(size=(1, 5, 2048, 2048)).astype(np.float32)).cuda()
     out = torch.empty((1, 2, 2048, 2048), dtype=torch.float32, device="cuda")
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            net.forward(x, out)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 20
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(reps):
-            net.forward(x, out)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / reps
     px = 2048 * 2048
-    tf = CNN_FLOP_PER_PIXEL_2D * px / (ms * 1e-3) / 1e12
-    gbs = CNN_BYTES_PER_PIXEL_2D * px / (ms * 1e-3) / 1e9
+
+    def timed(fn, reps=20):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn(x, out)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(reps):
+                fn(x, out)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    ms_fused = timed(net.infer)
+    ms_layers = timed(net.forward)
     net.close()
+    tf = CNN_FLOP_PER_PIXEL_2D * px / (ms_fused * 1e-3) / 1e12
+    gbs = CNN_FUSED_BYTES_PER_PIXEL_2D * px / (ms_fused * 1e-3) / 1e9
     return {"workload": "learned-guess CNN inference, 2048^2, 5->16->16->16->2 channels, 3x3, bf16 mma.sync",
-            "ms_per_inference": ms,
-            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_gbs, "unit": "GB/s",
-                         "frac": round(gbs / hbm_gbs, 4), "bytes_per_pixel": CNN_BYTES_PER_PIXEL_2D},
+            "ms_per_inference": ms_fused, "kernel": "cnn_fused2d_kernel (all four layers in one pass)",
+            "ms_per_inference_layer_by_layer": ms_layers,
             "tensor": {"achieved_tflops": round(tf, 1), "peak_tflops": peak_tflops, "frac": round(tf / peak_tflops, 4),
-                       "flop_per_pixel": CNN_FLOP_PER_PIXEL_2D}}
+                       "flop_per_pixel": CNN_FLOP_PER_PIXEL_2D},
+            "hbm": {"achieved": round(gbs, 1), "peak": hbm_gbs, "unit": "GB/s", "frac": round(gbs / hbm_gbs, 4),
+                    "bytes_per_pixel": CNN_FUSED_BYTES_PER_PIXEL_2D}}
 
 
 def bench_blast(torch, amrvac, stream, hbm_gbs, steps=20, regrid_every=10):

@@ -431,7 +431,12 @@ int cnn_train_step(cnn_handle* h, const float* in, const float* target, int N, i
  * loss only and may be NULL for MSE.  AMR_ERR_INVALID_ARG otherwise; a later
  * gradient call with margin < 1 under the operator loss is AMR_ERR_INVALID_ARG. */
 int cnn_set_loss(cnn_handle* h, int kind, const double* kappa);
-/* cnn_forward under the name of the inference call. */
+/* Inference.  2D images whose sides are multiples of 32 (W) and 16 (H) run one fused
+ * kernel for all four layers (activations stay in shared memory; nothing is allocated),
+ * with GELU in its tanh form (Hendrycks and Gimpel, 2016; within 4.7e-4 of the erf form,
+ * plus the hardware tanh's error of order 2^-11 times |z|/2): outputs agree with
+ * cnn_forward to the bf16 tolerance of the network.  Other shapes: cnn_forward.
+ * Arguments and layouts as cnn_forward.  Synchronous. */
 int cnn_infer(cnn_handle* h, const float* in, int N, int D, int H, int W, float* out);
 /* Parameters to / from a file: 8-byte magic "AMRVCNN1", int32 ndim, int32 0, int64 count,
  * count float32 values (host byte order).  cnn_load checks the magic, ndim and count

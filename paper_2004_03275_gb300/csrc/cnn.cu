@@ -421,6 +421,206 @@ __global__ void unpack_output_kernel(const float* __restrict__ o, float* __restr
   out[(n * 2 + 1) * P + p] = o[i * 2 + 1];
 }
 
+// ------------------------------------------------------- fused inference --
+// All four layers of the 2D network in one pass over the image: a CTA stages a
+// (TX+8) x (TY+8) tile of the five input channels (bf16, periodic wrap) and keeps
+// every intermediate activation in shared memory, each layer computing its output
+// on a region one cell smaller per side than its input (38 x 22, 36 x 20, 34 x 18,
+// then the 32 x 16 output tile for TX = 32, TY = 16), so the only global traffic is
+// the float32 input and output images.  Contractions: mma m16n8k8 (layer 1, whose
+// five input channels pad to K = 8) and m16n8k16 (layers 2-4), bf16 operands,
+// float32 accumulation, one tap per K step (implicit GEMM, M = 16 region pixels in
+// raster order); each warp keeps the layer's weight fragments of all nine taps in
+// registers.  Activations in shared memory: 16 bf16 channels at a 48-byte pixel
+// stride (conflict-free fragment loads); the input tile: 8 channels, 16 bytes.
+//
+// GELU here is the tanh form 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))
+// (Hendrycks and Gimpel, 2016) with the hardware tanh approximation, in place of
+// the exact erf form of the training kernels.  The form differs from the erf form
+// by at most 4.7e-4 (at z = 2.70; evaluated in float64 over [-12, 12]); the
+// hardware tanh adds |z|/2 times its own error, of order 2^-11.  Both are of the
+// size of the bf16 rounding of the stored activations (2^-9 relative); the test of
+// this kernel bounds its output against the exact-GELU layer-by-layer network.
+
+__device__ __forceinline__ void mma1688(float* c, const uint32_t* a, uint32_t b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(b));
+}
+
+__device__ __forceinline__ float tanh_approx(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// GELU (tanh form) of a pair, packed float32 arithmetic
+__device__ __forceinline__ float2 gelu_tanh2(float2 z) {
+  const float2 z2 = __fmul2_rn(z, z);
+  const float2 u = __fmul2_rn(z, __ffma2_rn(z2, make_float2(0.0356774081f, 0.0356774081f),
+                                            make_float2(0.7978845608f, 0.7978845608f)));
+  const float2 hz = __fmul2_rn(z, make_float2(0.5f, 0.5f));
+  return __ffma2_rn(hz, make_float2(tanh_approx(u.x), tanh_approx(u.y)), hz);
+}
+
+constexpr int kFuseTX = 32, kFuseTY = 16;  // output tile of the fused inference
+constexpr int kFuseThreads = 256;
+
+struct FusedArgs {
+  const float* in;    // [N][5][H][W]
+  float* out;         // [N][2][H][W]
+  const bf16* w[4];   // packed [tap][npad][CS]
+  const float* b[4];  // biases
+  int N, H, W;
+};
+
+__host__ __device__ constexpr int fused_region(int l, int d) { return (d == 0 ? kFuseTX : kFuseTY) + 2 * (4 - l); }  // side of region l
+__host__ __device__ constexpr int fused_pix(int l) { return fused_region(l, 0) * fused_region(l, 1); }
+constexpr size_t kFusedW = (size_t)3 * 9 * 16 * CS + 9 * 8 * CS;                   // bf16 weights
+constexpr size_t kFusedA = (size_t)fused_pix(2) * CS > (size_t)fused_pix(0) * 8 ? (size_t)fused_pix(2) * CS
+                                                                                 : (size_t)fused_pix(0) * 8;
+constexpr size_t kFusedB = (size_t)fused_pix(1) * CS;
+constexpr size_t kFusedSmem = (kFusedW + kFusedA + kFusedB) * sizeof(bf16);
+
+// one hidden layer: region l-1 (in, stride CIN bf16) -> region l (out, stride CS), bias, GELU
+template <int KS>
+__device__ __forceinline__ void fused_hidden(const bf16* s_in, bf16* s_out, const bf16* s_w, const float* bias, int l,
+                                             int warp, int lane) {
+  constexpr int CIN = KS == 8 ? 8 : CS;  // bf16 stride of the input region's pixels
+  const int g = lane >> 2, t = lane & 3;
+  const int wo = fused_region(l, 0), ho = fused_region(l, 1), wi = wo + 2, npix = wo * ho;
+  const uint32_t* w32 = reinterpret_cast<const uint32_t*>(s_w);
+  uint32_t bq[9][2][KS == 8 ? 1 : 2];
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const int row = tap * 16 + nt * 8 + g;
+      bq[tap][nt][0] = w32[row * (CS / 2) + t];
+      if (KS == 16) bq[tap][nt][KS == 8 ? 0 : 1] = w32[row * (CS / 2) + 4 + t];
+    }
+  const float2 bb0 = make_float2(bias[2 * t], bias[2 * t + 1]), bb1 = make_float2(bias[8 + 2 * t], bias[9 + 2 * t]);
+  const uint32_t* i32 = reinterpret_cast<const uint32_t*>(s_in);
+  uint32_t* o32 = reinterpret_cast<uint32_t*>(s_out);
+  const int nchunks = (npix + 15) / 16;
+  for (int c = warp; c < nchunks; c += kFuseThreads / 32) {
+    const int v0 = 16 * c + g, v1 = v0 + 8;
+    const int u0 = min(v0, npix - 1), u1 = min(v1, npix - 1);  // the tail chunk computes clamped rows
+    const int p0 = (u0 / wo + 1) * wi + u0 % wo + 1, p1 = (u1 / wo + 1) * wi + u1 % wo + 1;
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int off = (tap / 3 - 1) * wi + (tap % 3 - 1);
+      const int q0 = (p0 + off) * (CIN / 2), q1 = (p1 + off) * (CIN / 2);
+      if (KS == 8) {
+        const uint32_t av[2] = {i32[q0 + t], i32[q1 + t]};
+        mma1688(acc[0], av, bq[tap][0][0]);
+        mma1688(acc[1], av, bq[tap][1][0]);
+      } else {
+        const uint32_t av[4] = {i32[q0 + t], i32[q1 + t], i32[q0 + 4 + t], i32[q1 + 4 + t]};
+        mma16816(acc[0], av, bq[tap][0]);
+        mma16816(acc[1], av, bq[tap][1]);
+      }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const float2 bb = nt ? bb1 : bb0;
+      const float2 r0 = gelu_tanh2(__fadd2_rn(make_float2(acc[nt][0], acc[nt][1]), bb));
+      const float2 r1 = gelu_tanh2(__fadd2_rn(make_float2(acc[nt][2], acc[nt][3]), bb));
+      const __nv_bfloat162 h0 = __floats2bfloat162_rn(r0.x, r0.y), h1 = __floats2bfloat162_rn(r1.x, r1.y);
+      if (v0 < npix) o32[v0 * (CS / 2) + nt * 4 + t] = *reinterpret_cast<const uint32_t*>(&h0);
+      if (v1 < npix) o32[v1 * (CS / 2) + nt * 4 + t] = *reinterpret_cast<const uint32_t*>(&h1);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kFuseThreads, 2) cnn_fused2d_kernel(FusedArgs a) {
+  extern __shared__ __align__(16) unsigned char fused_smem[];
+  bf16* s_w = reinterpret_cast<bf16*>(fused_smem);
+  bf16* s_a = s_w + kFusedW;  // region 0 (8-channel input), then region 2
+  bf16* s_b = s_a + kFusedA;  // region 1, then region 3
+  const int tiles_x = a.W / kFuseTX, tiles_y = a.H / kFuseTY;
+  int tile = blockIdx.x;
+  const int x0 = (tile % tiles_x) * kFuseTX;
+  tile /= tiles_x;
+  const int y0 = (tile % tiles_y) * kFuseTY;
+  const int n = tile / tiles_y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // weights of the four layers (packed layouts copied as they are)
+  {
+    const int n1 = 9 * 16 * CS / 8, n4 = 9 * 8 * CS / 8;  // uint4 per layer
+    uint4* d = reinterpret_cast<uint4*>(s_w);
+    for (int r = threadIdx.x; r < 3 * n1 + n4; r += kFuseThreads) {
+      const int l = r < 3 * n1 ? r / n1 : 3, k = r < 3 * n1 ? r % n1 : r - 3 * n1;
+      const bf16* src = l == 0 ? a.w[0] : (l == 1 ? a.w[1] : (l == 2 ? a.w[2] : a.w[3]));  // no dynamic index
+      d[r] = __ldg(reinterpret_cast<const uint4*>(src) + k);
+    }
+  }
+  // region 0: the five input channels of the tile and its 4-cell periodic halo, bf16, 8 per pixel
+  {
+    constexpr int w0 = fused_region(0, 0), np0 = fused_pix(0);
+    const long long P = (long long)a.H * a.W;
+    const float* in = a.in + (long long)n * 5 * P;
+    for (int p = threadIdx.x; p < np0; p += kFuseThreads) {
+      const int gx = wrapi(x0 + p % w0 - 4, a.W), gy = wrapi(y0 + p / w0 - 4, a.H);
+      const long long q = (long long)gy * a.W + gx;
+      float f[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) f[c] = __ldg(in + c * P + q);
+      const __nv_bfloat162 h01 = __floats2bfloat162_rn(f[0], f[1]), h23 = __floats2bfloat162_rn(f[2], f[3]),
+                           h4 = __floats2bfloat162_rn(f[4], 0.f);
+      reinterpret_cast<uint4*>(s_a)[p] = make_uint4(*reinterpret_cast<const uint32_t*>(&h01),
+                                                    *reinterpret_cast<const uint32_t*>(&h23),
+                                                    *reinterpret_cast<const uint32_t*>(&h4), 0u);
+    }
+  }
+  __syncthreads();
+  fused_hidden<8>(s_a, s_b, s_w, a.b[0], 1, warp, lane);
+  __syncthreads();
+  fused_hidden<16>(s_b, s_a, s_w + 9 * 16 * CS, a.b[1], 2, warp, lane);
+  __syncthreads();
+  fused_hidden<16>(s_a, s_b, s_w + 2 * 9 * 16 * CS, a.b[2], 3, warp, lane);
+  __syncthreads();
+  // layer 4: region 3 -> the output tile, two channels (N = 8 padded), no activation
+  {
+    const int g = lane >> 2, t = lane & 3;
+    constexpr int wo = kFuseTX, wi = wo + 2, npix = kFuseTX * kFuseTY;
+    const uint32_t* w32 = reinterpret_cast<const uint32_t*>(s_w + 3 * 9 * 16 * CS);
+    uint32_t bq[9][2];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int row = tap * 8 + g;
+      bq[tap][0] = w32[row * (CS / 2) + t];
+      bq[tap][1] = w32[row * (CS / 2) + 4 + t];
+    }
+    const uint32_t* i32 = reinterpret_cast<const uint32_t*>(s_b);
+    const float b0 = a.b[3][0], b1 = a.b[3][1];
+    const long long P = (long long)a.H * a.W;
+    float* out = a.out + (long long)n * 2 * P;
+    for (int c = warp; c < npix / 16; c += kFuseThreads / 32) {
+      const int v0 = 16 * c + g, v1 = v0 + 8;
+      const int p0 = (v0 / wo + 1) * wi + v0 % wo + 1, p1 = (v1 / wo + 1) * wi + v1 % wo + 1;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const int off = (tap / 3 - 1) * wi + (tap % 3 - 1);
+        const int q0 = (p0 + off) * (CS / 2), q1 = (p1 + off) * (CS / 2);
+        const uint32_t av[4] = {i32[q0 + t], i32[q1 + t], i32[q0 + 4 + t], i32[q1 + 4 + t]};
+        mma16816(acc, av, bq[tap]);
+      }
+      if (t == 0) {  // columns 0 and 1 are the two output channels
+        const long long o0 = (long long)(y0 + v0 / wo) * a.W + x0 + v0 % wo;
+        const long long o1 = (long long)(y0 + v1 / wo) * a.W + x0 + v1 % wo;
+        out[o0] = acc[0] + b0;
+        out[P + o0] = acc[1] + b1;
+        out[o1] = acc[2] + b0;
+        out[P + o1] = acc[3] + b1;
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------- host --
 struct Buf {
   void* p = nullptr;
@@ -636,9 +836,60 @@ struct cnn_handle {
 };
 
 // inference on `stream` (NULL = the handle's own) without a final synchronisation
-int cnn_forward_async(cnn_handle* h, const float* in, int N, int D, int H, int W, float* out, cudaStream_t stream) {
+// the fused single-pass inference applies to 2D images whose sides tile by 32 x 16
+static bool fused_ok(const cnn_handle* h, int D, int H, int W) {
+  return h->nd == 2 && D == 1 && W % kFuseTX == 0 && H % kFuseTY == 0;
+}
+
+static int fused_forward(cnn_handle* h, const float* in, int N, int H, int W, float* out, cudaStream_t s) {
+  FusedArgs a{};
+  a.in = in;
+  a.out = out;
+  for (int l = 0; l < 4; ++l) {
+    a.w[l] = h->wfwd[l].as<bf16>();
+    a.b[l] = h->params.as<float>() + layer_off(2, l) + (long long)kCh[l + 1] * kCh[l] * 9;
+  }
+  a.N = N;
+  a.H = H;
+  a.W = W;
+  const unsigned tiles = (unsigned)N * (H / kFuseTY) * (W / kFuseTX);
+  cnn_fused2d_kernel<<<tiles, kFuseThreads, kFusedSmem, s>>>(a);
+  ++h->launches;
+  return h->cuda(cudaGetLastError(), "fused inference");
+}
+
+bool cnn_fused_applies(const cnn_handle* h, int D, int H, int W) { return h && fused_ok(h, D, H, W); }
+
+cudaStream_t cnn_own_stream(const cnn_handle* h) { return h ? h->stream : nullptr; }
+
+int cnn_enqueue_fused(cnn_handle* h, const float* in, int N, int H, int W, float* out, cudaStream_t s) {
+  if (!h || !in || !out || N < 1 || !fused_ok(h, 1, H, W)) return AMR_ERR_INVALID_ARG;
+  return fused_forward(h, in, N, H, W, out, s);
+}
+
+int cnn_forward_async(cnn_handle* h, const float* in, int N, int D, int H, int W, float* out, cudaStream_t stream,
+                      bool fused) {
   if (!h || !in || !out || !h->shape_ok(N, D, H, W)) return AMR_ERR_INVALID_ARG;
   long long P = (long long)D * H * W, npix = (long long)N * P;
+  if (fused && fused_ok(h, D, H, W)) {
+    // no intermediate buffers (nothing to allocate): one kernel on `stream`, ordered after the
+    // handle's pending work (weight repacks) by an event when the streams differ
+    cudaStream_t own = h->stream;
+    int rc;
+    if (stream && stream != own) {
+      if (!h->order_ev && (rc = h->cuda(cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming), "event")))
+        return rc;
+      if ((rc = h->cuda(cudaEventRecord(h->order_ev, own), "event")) ||
+          (rc = h->cuda(cudaStreamWaitEvent(stream, h->order_ev, 0), "event")))
+        return rc;
+    }
+    if ((rc = fused_forward(h, in, N, H, W, out, stream ? stream : own))) return rc;
+    if (stream && stream != own &&  // the handle's later work (repacks) after this inference
+        ((rc = h->cuda(cudaEventRecord(h->order_ev, stream), "event")) ||
+         (rc = h->cuda(cudaStreamWaitEvent(own, h->order_ev, 0), "event"))))
+      return rc;
+    return AMR_OK;
+  }
   cudaStream_t own = h->stream;
   int rc;
   const bool other = stream && stream != own;
@@ -690,7 +941,9 @@ int cnn_create(int ndim, unsigned long long seed, void* stream, cnn_handle** out
       cudaFuncSetAttribute(conv_kernel<3, FWD_INFER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)conv_smem_bytes<3, FWD_INFER>()) != cudaSuccess ||
       cudaFuncSetAttribute(conv_kernel<3, BWD_GELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)conv_smem_bytes<3, BWD_GELU>()) != cudaSuccess)
+                           (int)conv_smem_bytes<3, BWD_GELU>()) != cudaSuccess ||
+      cudaFuncSetAttribute(cnn_fused2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem) !=
+          cudaSuccess)
     return AMR_ERR_CUDA;
   size_t pb = (size_t)h->nparams * sizeof(float);
   int rc;
@@ -757,7 +1010,7 @@ int cnn_get_params(cnn_handle* h, float* p, long long n) {
 }
 
 int cnn_forward(cnn_handle* h, const float* in, int N, int D, int H, int W, float* out) {
-  int rc = cnn_forward_async(h, in, N, D, H, W, out, nullptr);
+  int rc = cnn_forward_async(h, in, N, D, H, W, out, nullptr, false);
   if (rc) return rc;
   return h->cuda(cudaStreamSynchronize(h->stream), "sync");
 }
@@ -808,7 +1061,9 @@ int cnn_set_loss(cnn_handle* h, int kind, const double* kappa) {
 }
 
 int cnn_infer(cnn_handle* h, const float* in, int N, int D, int H, int W, float* out) {
-  return cnn_forward(h, in, N, D, H, W, out);
+  int rc = cnn_forward_async(h, in, N, D, H, W, out, nullptr, true);
+  if (rc) return rc;
+  return h->cuda(cudaStreamSynchronize(h->stream), "sync");
 }
 
 // parameter file: 8-byte magic, int32 ndim, int32 0, int64 count, count float32 (host byte order)

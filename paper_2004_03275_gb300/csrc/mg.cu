@@ -1645,10 +1645,19 @@ struct rd_handle {
   Mg mg;
   cudaGraphExec_t egraph = nullptr;  // kExplicitGraphSteps explicit steps
   cudaGraphExec_t stgraph = nullptr; // one implicit step with its device-side solve
+  cudaGraphExec_t gstgraph = nullptr;  // the same with the learned guess (fused inference)
+  long long guess_launches = 0;        // kernels of the learned guess in one step
+  cudaEvent_t order_ev = nullptr;      // orders the network's own stream around the step replays
   DevBuf d_log, d_stepctr;           // per-step cycle log ([kLogSteps][2 n_inst]) and its counter
+  void drop_guess_graph() {
+    if (gstgraph) cudaGraphExecDestroy(gstgraph);
+    gstgraph = nullptr;
+  }
   ~rd_handle() {
     if (egraph) cudaGraphExecDestroy(egraph);
     if (stgraph) cudaGraphExecDestroy(stgraph);
+    drop_guess_graph();
+    if (order_ev) cudaEventDestroy(order_ev);
   }
   rd_config cfg{};
   std::vector<int> sizes;
@@ -1889,51 +1898,82 @@ int rd_step(rd_handle* h, int nsteps, int* cycles) {
   double* wn = h->d_wn.as<double>();
   double* prev = h->d_prev.as<double>();
   double* pin = h->d_pin.as<double>();
-  if (!h->guess) {
-    // Each step is one graph launch: (IMEX: keep w_n and the previous solution) right-hand
-    // side, the solve with its device-side convergence loop, (IMEX: keep the solution)
-    // finish, and a row of the cycle log.  The host waits once per kLogSteps steps.
-    if (!h->stgraph) {
-      cudaGraph_t g;
-      if ((rc = M.cuda(cudaStreamBeginCapture(M.stream, cudaStreamCaptureModeThreadLocal), "capture"))) return rc;
-      int crc = AMR_OK;
-      if (scheme == RD_IMEX) {
-        cudaMemcpyAsync(wn, h->d_u.p, cb, cudaMemcpyDeviceToDevice, M.stream);
-        cudaMemcpyAsync(wn + h->cells, h->d_v.p, cb, cudaMemcpyDeviceToDevice, M.stream);
-        cudaMemcpyAsync(pin, prev, 2 * cb, cudaMemcpyDeviceToDevice, M.stream);
-        rd_rhs_kernel<RD_IMEX><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
-      } else {
-        rd_rhs_kernel<RD_SPLIT><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
-      }
-      crc = M.capture_solve_any();
-      if (scheme == RD_IMEX) {
-        cudaMemcpyAsync(prev, M.d_X.p, 2 * cb, cudaMemcpyDeviceToDevice, M.stream);
-        rd_finish_kernel<RD_IMEX><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
-      } else {
-        rd_finish_kernel<RD_SPLIT><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
-      }
-      log_kernel<<<1, 256, 0, M.stream>>>(M.state(), M.ninst, h->d_log.as<int>(), h->d_stepctr.as<int>(), kLogSteps);
-      cudaError_t ec = cudaStreamEndCapture(M.stream, &g);
-      if (crc) {
-        if (ec == cudaSuccess) cudaGraphDestroy(g);
-        return crc;
-      }
-      if ((rc = M.cuda(ec, "end capture"))) return rc;
-      rc = M.cuda(cudaGraphInstantiate(&h->stgraph, g, 0), "instantiate");
-      cudaGraphDestroy(g);
-      if (rc) return rc;
+  // learned guess: per instance the network's input channels, one inference and the guess
+  // X = w_n + scale * net, before the solve.  captured: the fused inference's single launch
+  // (no event, no allocation), for a step replayed from a graph.
+  auto enqueue_guess = [&](bool captured) -> int {
+    for (int i = 0; i < ni; ++i) {
+      const InstDev& I = M.insts[i];
+      long long n0 = 1;
+      for (int d = 0; d < h->cfg.ndim; ++d) n0 *= I.n[0];
+      unsigned nb = (unsigned)((n0 + 255) / 256);
+      rd_cnn_input_kernel<<<nb, 256, 0, M.stream>>>(M.d_inst.as<InstDev>(), i, i + ni, M.d_B.as<double>(), wn, pin,
+                                                     h->cells, n0, (float)h->cfg.dt, h->guess_inputs, h->cfg.ndim,
+                                                     h->cfg.bc == MG_BC_NEUMANN ? 1 : 0, 1.0 / h->guess_scale,
+                                                     h->d_cin.as<float>());
+      int n = I.n[0];
+      int crc = captured ? cnn_enqueue_fused(h->guess, h->d_cin.as<float>(), 1, n, n, h->d_cout.as<float>(), M.stream)
+                         : cnn_forward_async(h->guess, h->d_cin.as<float>(), 1, h->cfg.ndim == 3 ? n : 1, n, n,
+                                             h->d_cout.as<float>(), M.stream, true);
+      if (crc) return M.fail(crc, std::string("learned guess: ") + cnn_last_error(h->guess));
+      rd_cnn_guess_kernel<<<nb, 256, 0, M.stream>>>(M.d_inst.as<InstDev>(), i, i + ni, h->d_cout.as<float>(), n0,
+                                                    h->guess_scale, M.d_X.as<double>(), wn, h->cells);
+      M.launches += 2;
     }
+    return AMR_OK;
+  };
+  // One implicit step as a graph: (IMEX: keep w_n and the previous solution) right-hand side,
+  // (learned guess), the solve with its device-side convergence loop, (IMEX: keep the
+  // solution) finish, and a row of the cycle log.
+  auto capture_step = [&](cudaGraphExec_t* out, bool with_guess) -> int {
+    cudaGraph_t g;
+    int rc2;
+    if ((rc2 = M.cuda(cudaStreamBeginCapture(M.stream, cudaStreamCaptureModeThreadLocal), "capture"))) return rc2;
+    int crc = AMR_OK;
+    if (scheme == RD_IMEX) {
+      cudaMemcpyAsync(wn, h->d_u.p, cb, cudaMemcpyDeviceToDevice, M.stream);
+      cudaMemcpyAsync(wn + h->cells, h->d_v.p, cb, cudaMemcpyDeviceToDevice, M.stream);
+      cudaMemcpyAsync(pin, prev, 2 * cb, cudaMemcpyDeviceToDevice, M.stream);
+      rd_rhs_kernel<RD_IMEX><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
+    } else {
+      rd_rhs_kernel<RD_SPLIT><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
+    }
+    const long long l0 = M.launches;
+    if (with_guess) crc = enqueue_guess(true);
+    h->guess_launches = M.launches - l0;
+    M.launches = l0;
+    if (!crc) crc = M.capture_solve_any();
+    if (scheme == RD_IMEX) {
+      cudaMemcpyAsync(prev, M.d_X.p, 2 * cb, cudaMemcpyDeviceToDevice, M.stream);
+      rd_finish_kernel<RD_IMEX><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
+    } else {
+      rd_finish_kernel<RD_SPLIT><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
+    }
+    log_kernel<<<1, 256, 0, M.stream>>>(M.state(), M.ninst, h->d_log.as<int>(), h->d_stepctr.as<int>(), kLogSteps);
+    cudaError_t ec = cudaStreamEndCapture(M.stream, &g);
+    if (crc) {
+      if (ec == cudaSuccess) cudaGraphDestroy(g);
+      return crc;
+    }
+    if ((rc2 = M.cuda(ec, "end capture"))) return rc2;
+    rc2 = M.cuda(cudaGraphInstantiate(out, g, 0), "instantiate");
+    cudaGraphDestroy(g);
+    return rc2;
+  };
+  // k replays of a step graph from step s_first; the host waits once per kLogSteps steps
+  auto replay = [&](cudaGraphExec_t gx, int s_first, int k_all, long long extra_launches) -> int {
     std::vector<int> log((size_t)kLogSteps * 2 * ni);
     bool failed = false;
-    for (int s0 = 0; s0 < nsteps; s0 += kLogSteps) {
-      const int k = std::min(kLogSteps, nsteps - s0);
-      if ((rc = M.cuda(cudaMemsetAsync(h->d_stepctr.p, 0, sizeof(int), M.stream), "memset"))) return rc;
+    int rc2;
+    for (int s0 = 0; s0 < k_all; s0 += kLogSteps) {
+      const int k = std::min(kLogSteps, k_all - s0);
+      if ((rc2 = M.cuda(cudaMemsetAsync(h->d_stepctr.p, 0, sizeof(int), M.stream), "memset"))) return rc2;
       for (int s = 0; s < k; ++s)
-        if ((rc = M.cuda(cudaGraphLaunch(h->stgraph, M.stream), "step graph launch"))) return rc;
-      if ((rc = M.cuda(cudaMemcpyAsync(log.data(), h->d_log.p, (size_t)k * 2 * ni * sizeof(int),
-                                       cudaMemcpyDeviceToHost, M.stream), "copy log")))
-        return rc;
-      if ((rc = M.cuda(cudaStreamSynchronize(M.stream), "sync"))) return rc;
+        if ((rc2 = M.cuda(cudaGraphLaunch(gx, M.stream), "step graph launch"))) return rc2;
+      if ((rc2 = M.cuda(cudaMemcpyAsync(log.data(), h->d_log.p, (size_t)k * 2 * ni * sizeof(int),
+                                        cudaMemcpyDeviceToHost, M.stream), "copy log")))
+        return rc2;
+      if ((rc2 = M.cuda(cudaStreamSynchronize(M.stream), "sync"))) return rc2;
       for (int s = 0; s < k; ++s) {
         int maxc = 0;
         for (int i = 0; i < 2 * ni; ++i) {
@@ -1943,16 +1983,30 @@ int rd_step(rd_handle* h, int nsteps, int* cycles) {
             e = -1 - e;
           }
           maxc = std::max(maxc, e);
-          if (cycles) cycles[(size_t)(s0 + s) * 2 * ni + i] = e;
+          if (cycles) cycles[(size_t)(s_first + s0 + s) * 2 * ni + i] = e;
         }
-        M.launches += 3 + M.solve_kernels(maxc);
+        M.launches += 3 + extra_launches + M.solve_kernels(maxc);
       }
     }
-    if (scheme == RD_IMEX && nsteps > 0) h->have_prev = true;
+    if (scheme == RD_IMEX && k_all > 0) h->have_prev = true;
     if (failed) return M.fail(MG_ERR_NOT_CONVERGED, "an instance did not reach rtol within max_cycles");
     return M.cuda(cudaGetLastError(), "rd step");
+  };
+  if (!h->guess) {
+    if (!h->stgraph && (rc = capture_step(&h->stgraph, false))) return rc;
+    return replay(h->stgraph, 0, nsteps, 0);
   }
-  for (int s = 0; s < nsteps; ++s) {
+  // Learned guess.  Steps replay one captured graph, like the previous-step guess, when the
+  // network's fused inference applies to every instance (2D, sides multiples of 32 and 16)
+  // and a previous solution exists; otherwise (and for the first step after a new state,
+  // whose network inputs use w_n for the missing previous solution) steps run launch by launch.
+  bool capturable = scheme == RD_IMEX;
+  for (int i = 0; i < ni; ++i) {
+    const int n = M.insts[i].n[0];
+    capturable = capturable && cnn_fused_applies(h->guess, h->cfg.ndim == 3 ? n : 1, n, n);
+  }
+  const int eager = capturable ? (h->have_prev ? 0 : std::min(1, nsteps)) : nsteps;
+  for (int s = 0; s < eager; ++s) {
     if (scheme == RD_IMEX) {
       // keep w_n and the previous solution (inputs of the learned guess and of training crops)
       if ((rc = M.cuda(cudaMemcpyAsync(wn, h->d_u.p, cb, cudaMemcpyDeviceToDevice, M.stream), "copy")) ||
@@ -1965,26 +2019,8 @@ int rd_step(rd_handle* h, int nsteps, int* cycles) {
       rd_rhs_kernel<RD_SPLIT><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
     }
     ++M.launches;
-    if (h->guess) {
-      // the network runs in order on the solver's stream (no host synchronisation)
-      for (int i = 0; i < ni; ++i) {
-        const InstDev& I = M.insts[i];
-        long long n0 = 1;
-        for (int d = 0; d < h->cfg.ndim; ++d) n0 *= I.n[0];
-        unsigned nb = (unsigned)((n0 + 255) / 256);
-        rd_cnn_input_kernel<<<nb, 256, 0, M.stream>>>(M.d_inst.as<InstDev>(), i, i + ni, M.d_B.as<double>(), wn, pin,
-                                                       h->cells, n0, (float)h->cfg.dt, h->guess_inputs,
-                                                       h->cfg.ndim, h->cfg.bc == MG_BC_NEUMANN ? 1 : 0,
-                                                       1.0 / h->guess_scale, h->d_cin.as<float>());
-        int n = I.n[0];
-        int crc = cnn_forward_async(h->guess, h->d_cin.as<float>(), 1, h->cfg.ndim == 3 ? n : 1, n, n,
-                                    h->d_cout.as<float>(), M.stream);
-        if (crc) return M.fail(crc, std::string("learned guess: ") + cnn_last_error(h->guess));
-        rd_cnn_guess_kernel<<<nb, 256, 0, M.stream>>>(M.d_inst.as<InstDev>(), i, i + ni, h->d_cout.as<float>(), n0,
-                                                      h->guess_scale, M.d_X.as<double>(), wn, h->cells);
-        M.launches += 2;
-      }
-    }
+    // the network runs in order on the solver's stream (no host synchronisation)
+    if ((rc = enqueue_guess(false))) return rc;
     rc = M.solve_device_any();
     if (rc) return rc;
     if (scheme == RD_IMEX) {
@@ -2002,6 +2038,25 @@ int rd_step(rd_handle* h, int nsteps, int* cycles) {
       rd_finish_kernel<RD_SPLIT><<<nch0, kChunk, 0, M.stream>>>(A, ch0);
     ++M.launches;
     if ((rc = M.cuda(cudaGetLastError(), "rd launch"))) return rc;
+  }
+  if (eager < nsteps) {
+    if (!h->gstgraph && (rc = capture_step(&h->gstgraph, true))) return rc;
+    // the network's pending work (weight repacks) before the replays, its later work after them
+    cudaStream_t ns = cnn_own_stream(h->guess);
+    if (!h->order_ev && (rc = M.cuda(cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming), "event")))
+      return rc;
+    if (ns && ns != M.stream &&
+        ((rc = M.cuda(cudaEventRecord(h->order_ev, ns), "event")) ||
+         (rc = M.cuda(cudaStreamWaitEvent(M.stream, h->order_ev, 0), "event"))))
+      return rc;
+    rc = replay(h->gstgraph, eager, nsteps - eager, h->guess_launches);
+    if (ns && ns != M.stream) {
+      int rc2;
+      if ((rc2 = M.cuda(cudaEventRecord(h->order_ev, M.stream), "event")) ||
+          (rc2 = M.cuda(cudaStreamWaitEvent(ns, h->order_ev, 0), "event")))
+        return rc ? rc : rc2;
+    }
+    return rc;
   }
   return M.cuda(cudaStreamSynchronize(M.stream), "sync");
 }
@@ -2038,12 +2093,14 @@ int rd_set_guess(rd_handle* h, cnn_handle* net, double scale) {
   }
   h->guess = net;
   h->guess_scale = net ? scale : 1.0;
+  h->drop_guess_graph();  // its buffers, network and scale are baked into the graph
   return AMR_OK;
 }
 
 int rd_set_guess_inputs(rd_handle* h, int kind) {
   if (!h || (kind != RD_GUESS_IN_PREV && kind != RD_GUESS_IN_RESIDUAL)) return AMR_ERR_INVALID_ARG;
   h->guess_inputs = kind;
+  h->drop_guess_graph();
   return AMR_OK;
 }
 

@@ -125,3 +125,25 @@ def test_shape_validation():
     x = torch.zeros((1, 5, 20, 32), device="cuda")
     with pytest.raises(amrvac.AmrError):
         net.forward(x)
+
+
+@pytest.mark.parametrize("shape", [(2, 5, 48, 64), (1, 5, 256, 256)])
+def test_fused_inference_matches_oracle_and_layer_path(shape):
+    """cnn_infer on 2D images whose sides tile by 32 x 16 runs the fused four-layer kernel with the
+    tanh-form GELU (within 4.7e-4 of the erf form, plus the hardware tanh's error): against the FP64
+    oracle network within the forward test's 3e-2 of the max norm, against the layer-by-layer bf16
+    network (exact GELU) within 2e-2, periodic wrap included (the tiles' halos cross the image edge);
+    repeated calls are identical."""
+    rng = np.random.default_rng(31)
+    p = rand_params(2, rng)
+    x = bf16_round(rng.uniform(0, 1, size=shape)).astype(np.float64)
+    net = amrvac.CnnNet(ndim=2)
+    net.set_params(p)
+    xd = torch.from_numpy(x.astype(np.float32)).cuda()
+    fused = net.infer(xd).cpu().numpy()
+    layer = net.forward(xd).cpu().numpy()
+    ref = O.cnn_forward(p, x, ndim=2)
+    m = np.max(np.abs(ref))
+    assert np.max(np.abs(fused - ref)) / m <= 3e-2
+    assert np.max(np.abs(fused - layer)) / np.max(np.abs(layer)) <= 2e-2
+    assert np.array_equal(net.infer(xd).cpu().numpy(), fused)
