@@ -475,71 +475,115 @@ struct FusedArgs {
   int N, H, W;
 };
 
-__host__ __device__ constexpr int fused_region(int l, int d) { return (d == 0 ? kFuseTX : kFuseTY) + 2 * (4 - l); }  // side of region l
+__host__ __device__ constexpr int fused_region(int l, int d) { return (d == 0 ? kFuseTX : kFuseTY) + 2 * (4 - l); }
 __host__ __device__ constexpr int fused_pix(int l) { return fused_region(l, 0) * fused_region(l, 1); }
-constexpr size_t kFusedW = (size_t)3 * 9 * 16 * CS + 9 * 8 * CS;                   // bf16 weights
 constexpr size_t kFusedA = (size_t)fused_pix(2) * CS > (size_t)fused_pix(0) * 8 ? (size_t)fused_pix(2) * CS
                                                                                  : (size_t)fused_pix(0) * 8;
 constexpr size_t kFusedB = (size_t)fused_pix(1) * CS;
-constexpr size_t kFusedSmem = (kFusedW + kFusedA + kFusedB) * sizeof(bf16);
+constexpr size_t kFusedSmem = (kFusedA + kFusedB) * sizeof(bf16);
 
-// one hidden layer: region l-1 (in, stride CIN bf16) -> region l (out, stride CS), bias, GELU
-template <int KS>
-__device__ __forceinline__ void fused_hidden(const bf16* s_in, bf16* s_out, const bf16* s_w, const float* bias, int l,
-                                             int warp, int lane) {
-  constexpr int CIN = KS == 8 ? 8 : CS;  // bf16 stride of the input region's pixels
+// four (x4) or two (x2) 8x8 bf16 matrices from shared memory, one 16-byte row address per lane
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t* r, uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(addr));
+}
+
+// Layer L (1..4): region L-1 (in; 8 bf16 per pixel for L = 1, else CS) -> region L.  Each warp
+// takes pairs of 16-pixel chunks (four independent accumulator chains); the A fragments of a
+// tap come by one ldmatrix per chunk (lane = pixel row (lane & 15), K half (lane >> 4)), the
+// weight fragments of all nine taps from global memory into registers once per layer.
+// Hidden layers: bias, GELU, bf16 into `out` (shared); layer 4: bias, float32 into the image.
+template <int L>
+__device__ __forceinline__ void fused_layer(const FusedArgs& a, const bf16* s_in, bf16* s_out, int n, int x0, int y0,
+                                            int warp, int lane) {
+  constexpr bool LAST = L == 4, K8 = L == 1;
+  constexpr int NT = LAST ? 1 : 2, NPAD = LAST ? 8 : 16, PB = K8 ? 16 : CS * 2;  // pixel stride (bytes) of `in`
+  constexpr int wo = fused_region(L, 0), ho = fused_region(L, 1), wi = wo + 2, npix = wo * ho;
+  constexpr int nchunks = (npix + 15) / 16;
   const int g = lane >> 2, t = lane & 3;
-  const int wo = fused_region(l, 0), ho = fused_region(l, 1), wi = wo + 2, npix = wo * ho;
-  const uint32_t* w32 = reinterpret_cast<const uint32_t*>(s_w);
-  uint32_t bq[9][2][KS == 8 ? 1 : 2];
+  const uint32_t* w32 = reinterpret_cast<const uint32_t*>(a.w[L - 1]);
+  uint32_t bq[9][NT][K8 ? 1 : 2];
 #pragma unroll
   for (int tap = 0; tap < 9; ++tap)
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt) {
-      const int row = tap * 16 + nt * 8 + g;
-      bq[tap][nt][0] = w32[row * (CS / 2) + t];
-      if (KS == 16) bq[tap][nt][KS == 8 ? 0 : 1] = w32[row * (CS / 2) + 4 + t];
+    for (int nt = 0; nt < NT; ++nt) {
+      const int row = tap * NPAD + nt * 8 + g;
+      bq[tap][nt][0] = __ldg(w32 + row * (CS / 2) + t);
+      if (!K8) bq[tap][nt][K8 ? 0 : 1] = __ldg(w32 + row * (CS / 2) + 4 + t);
     }
-  const float2 bb0 = make_float2(bias[2 * t], bias[2 * t + 1]), bb1 = make_float2(bias[8 + 2 * t], bias[9 + 2 * t]);
-  const uint32_t* i32 = reinterpret_cast<const uint32_t*>(s_in);
-  uint32_t* o32 = reinterpret_cast<uint32_t*>(s_out);
-  const int nchunks = (npix + 15) / 16;
-  for (int c = warp; c < nchunks; c += kFuseThreads / 32) {
-    const int v0 = 16 * c + g, v1 = v0 + 8;
-    const int u0 = min(v0, npix - 1), u1 = min(v1, npix - 1);  // the tail chunk computes clamped rows
-    const int p0 = (u0 / wo + 1) * wi + u0 % wo + 1, p1 = (u1 / wo + 1) * wi + u1 % wo + 1;
-    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  const float* bias = a.b[L - 1];
+  const float2 bb0 = make_float2(__ldg(bias + 2 * t), __ldg(bias + 2 * t + 1));
+  const float2 bb1 = LAST ? bb0 : make_float2(__ldg(bias + 8 + 2 * t), __ldg(bias + 9 + 2 * t));
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(s_in) + (K8 ? 0 : (lane >> 4) * 16);
+  const int r = lane & 15;
+  for (int c = 2 * warp; c < nchunks; c += 2 * (kFuseThreads / 32)) {
+    uint32_t prow[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int u = min(16 * (c + j) + r, npix - 1);  // rows beyond the region compute a clamped pixel
+      prow[j] = sbase + ((u / wo + 1) * wi + u % wo + 1) * PB;
+    }
+    float acc[2][NT][4];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) acc[j][nt][0] = acc[j][nt][1] = acc[j][nt][2] = acc[j][nt][3] = 0.f;
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
-      const int off = (tap / 3 - 1) * wi + (tap % 3 - 1);
-      const int q0 = (p0 + off) * (CIN / 2), q1 = (p1 + off) * (CIN / 2);
-      if (KS == 8) {
-        const uint32_t av[2] = {i32[q0 + t], i32[q1 + t]};
-        mma1688(acc[0], av, bq[tap][0][0]);
-        mma1688(acc[1], av, bq[tap][1][0]);
-      } else {
-        const uint32_t av[4] = {i32[q0 + t], i32[q1 + t], i32[q0 + 4 + t], i32[q1 + 4 + t]};
-        mma16816(acc[0], av, bq[tap][0]);
-        mma16816(acc[1], av, bq[tap][1]);
+      const int off = ((tap / 3 - 1) * wi + (tap % 3 - 1)) * PB;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        if (K8) {
+          uint32_t av[2];
+          ldsm_x2(av, prow[j] + off);
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) mma1688(acc[j][nt], av, bq[tap][nt][0]);
+        } else {
+          uint32_t av[4];
+          ldsm_x4(av, prow[j] + off);
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) mma16816(acc[j][nt], av, bq[tap][nt]);
+        }
       }
     }
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt) {
-      const float2 bb = nt ? bb1 : bb0;
-      const float2 r0 = gelu_tanh2(__fadd2_rn(make_float2(acc[nt][0], acc[nt][1]), bb));
-      const float2 r1 = gelu_tanh2(__fadd2_rn(make_float2(acc[nt][2], acc[nt][3]), bb));
-      const __nv_bfloat162 h0 = __floats2bfloat162_rn(r0.x, r0.y), h1 = __floats2bfloat162_rn(r1.x, r1.y);
-      if (v0 < npix) o32[v0 * (CS / 2) + nt * 4 + t] = *reinterpret_cast<const uint32_t*>(&h0);
-      if (v1 < npix) o32[v1 * (CS / 2) + nt * 4 + t] = *reinterpret_cast<const uint32_t*>(&h1);
+    for (int j = 0; j < 2; ++j) {
+      const int v0 = 16 * (c + j) + g, v1 = v0 + 8;
+      if (LAST) {
+        if (t == 0) {  // columns 0 and 1 are the two output channels
+          const long long P = (long long)a.H * a.W;
+          float* out = a.out + (long long)n * 2 * P;
+          const long long o0 = (long long)(y0 + v0 / wo) * a.W + x0 + v0 % wo;
+          const long long o1 = (long long)(y0 + v1 / wo) * a.W + x0 + v1 % wo;
+          out[o0] = acc[j][0][0] + bb0.x;
+          out[P + o0] = acc[j][0][1] + bb0.y;
+          out[o1] = acc[j][0][2] + bb0.x;
+          out[P + o1] = acc[j][0][3] + bb0.y;
+        }
+      } else {
+        uint32_t* o32 = reinterpret_cast<uint32_t*>(s_out);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          const float2 bb = nt ? bb1 : bb0;
+          const float2 r0 = gelu_tanh2(__fadd2_rn(make_float2(acc[j][nt][0], acc[j][nt][1]), bb));
+          const float2 r1 = gelu_tanh2(__fadd2_rn(make_float2(acc[j][nt][2], acc[j][nt][3]), bb));
+          const __nv_bfloat162 h0 = __floats2bfloat162_rn(r0.x, r0.y), h1 = __floats2bfloat162_rn(r1.x, r1.y);
+          if (v0 < npix) o32[v0 * (CS / 2) + nt * 4 + t] = *reinterpret_cast<const uint32_t*>(&h0);
+          if (v1 < npix) o32[v1 * (CS / 2) + nt * 4 + t] = *reinterpret_cast<const uint32_t*>(&h1);
+        }
+      }
     }
   }
 }
 
-__global__ void __launch_bounds__(kFuseThreads, 2) cnn_fused2d_kernel(FusedArgs a) {
+__global__ void __launch_bounds__(kFuseThreads, 3) cnn_fused2d_kernel(FusedArgs a) {
   extern __shared__ __align__(16) unsigned char fused_smem[];
-  bf16* s_w = reinterpret_cast<bf16*>(fused_smem);
-  bf16* s_a = s_w + kFusedW;  // region 0 (8-channel input), then region 2
-  bf16* s_b = s_a + kFusedA;  // region 1, then region 3
+  bf16* s_a = reinterpret_cast<bf16*>(fused_smem);  // region 0 (8-channel input), then region 2
+  bf16* s_b = s_a + kFusedA;                        // region 1, then region 3
   const int tiles_x = a.W / kFuseTX, tiles_y = a.H / kFuseTY;
   int tile = blockIdx.x;
   const int x0 = (tile % tiles_x) * kFuseTX;
@@ -547,16 +591,6 @@ __global__ void __launch_bounds__(kFuseThreads, 2) cnn_fused2d_kernel(FusedArgs 
   const int y0 = (tile % tiles_y) * kFuseTY;
   const int n = tile / tiles_y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // weights of the four layers (packed layouts copied as they are)
-  {
-    const int n1 = 9 * 16 * CS / 8, n4 = 9 * 8 * CS / 8;  // uint4 per layer
-    uint4* d = reinterpret_cast<uint4*>(s_w);
-    for (int r = threadIdx.x; r < 3 * n1 + n4; r += kFuseThreads) {
-      const int l = r < 3 * n1 ? r / n1 : 3, k = r < 3 * n1 ? r % n1 : r - 3 * n1;
-      const bf16* src = l == 0 ? a.w[0] : (l == 1 ? a.w[1] : (l == 2 ? a.w[2] : a.w[3]));  // no dynamic index
-      d[r] = __ldg(reinterpret_cast<const uint4*>(src) + k);
-    }
-  }
   // region 0: the five input channels of the tile and its 4-cell periodic halo, bf16, 8 per pixel
   {
     constexpr int w0 = fused_region(0, 0), np0 = fused_pix(0);
@@ -576,49 +610,13 @@ __global__ void __launch_bounds__(kFuseThreads, 2) cnn_fused2d_kernel(FusedArgs 
     }
   }
   __syncthreads();
-  fused_hidden<8>(s_a, s_b, s_w, a.b[0], 1, warp, lane);
+  fused_layer<1>(a, s_a, s_b, n, x0, y0, warp, lane);
   __syncthreads();
-  fused_hidden<16>(s_b, s_a, s_w + 9 * 16 * CS, a.b[1], 2, warp, lane);
+  fused_layer<2>(a, s_b, s_a, n, x0, y0, warp, lane);
   __syncthreads();
-  fused_hidden<16>(s_a, s_b, s_w + 2 * 9 * 16 * CS, a.b[2], 3, warp, lane);
+  fused_layer<3>(a, s_a, s_b, n, x0, y0, warp, lane);
   __syncthreads();
-  // layer 4: region 3 -> the output tile, two channels (N = 8 padded), no activation
-  {
-    const int g = lane >> 2, t = lane & 3;
-    constexpr int wo = kFuseTX, wi = wo + 2, npix = kFuseTX * kFuseTY;
-    const uint32_t* w32 = reinterpret_cast<const uint32_t*>(s_w + 3 * 9 * 16 * CS);
-    uint32_t bq[9][2];
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int row = tap * 8 + g;
-      bq[tap][0] = w32[row * (CS / 2) + t];
-      bq[tap][1] = w32[row * (CS / 2) + 4 + t];
-    }
-    const uint32_t* i32 = reinterpret_cast<const uint32_t*>(s_b);
-    const float b0 = a.b[3][0], b1 = a.b[3][1];
-    const long long P = (long long)a.H * a.W;
-    float* out = a.out + (long long)n * 2 * P;
-    for (int c = warp; c < npix / 16; c += kFuseThreads / 32) {
-      const int v0 = 16 * c + g, v1 = v0 + 8;
-      const int p0 = (v0 / wo + 1) * wi + v0 % wo + 1, p1 = (v1 / wo + 1) * wi + v1 % wo + 1;
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        const int off = (tap / 3 - 1) * wi + (tap % 3 - 1);
-        const int q0 = (p0 + off) * (CS / 2), q1 = (p1 + off) * (CS / 2);
-        const uint32_t av[4] = {i32[q0 + t], i32[q1 + t], i32[q0 + 4 + t], i32[q1 + 4 + t]};
-        mma16816(acc, av, bq[tap]);
-      }
-      if (t == 0) {  // columns 0 and 1 are the two output channels
-        const long long o0 = (long long)(y0 + v0 / wo) * a.W + x0 + v0 % wo;
-        const long long o1 = (long long)(y0 + v1 / wo) * a.W + x0 + v1 % wo;
-        out[o0] = acc[0] + b0;
-        out[P + o0] = acc[1] + b1;
-        out[o1] = acc[2] + b0;
-        out[P + o1] = acc[3] + b1;
-      }
-    }
-  }
+  fused_layer<4>(a, s_b, nullptr, n, x0, y0, warp, lane);
 }
 
 // ------------------------------------------------------------------- host --
