@@ -249,23 +249,27 @@ def bench_learned_guess(torch, amrvac, stream, eval_steps=6):
     c0, t0s, _, r0 = LG.evaluate(torch, [n], [10000], L, steps=eval_steps, warm=40)
     out = {"workload": "Gray-Scott IMEX 2048^2 (seed 10000, after 40 warm-up steps), MG rtol 1e-10",
            "training_data": "crops 64^2 after each of 24 steps of two 2048^2 runs (seeds 0, 1; 40 warm-up steps), "
-                            "48 crops per step",
+                            "48 crops per step (1152 pairs); the _20k_pairs entry: 50 steps, 200 crops per step",
            "vcycles_per_solve_previous_step_guess": float(np.mean(c0)),
            "initial_rel_residual_median_previous_step": float(np.median(r0)),
            "ms_per_step_previous_step_guess": t0s * 1e3, "operator_kappa": [round(k, 5) for k in kappa]}
-    for inp, loss, iters in (("residual", "operator", 5000), ("prev", "mse", 1500)):
+    # (inputs, loss, Adam steps, crops per step, steps per run): the two networks on 1152 crops, and
+    # the residual network on the configuration's 20k training pairs (two runs x 50 steps x 200 crops)
+    for inp, loss, iters, cps, nst in (("residual", "operator", 5000, 48, 24), ("prev", "mse", 1500, 48, 24),
+                                       ("residual", "operator", 5000, 200, 50)):
         t0 = time.perf_counter()
-        X, Y, scale = LG.generate(torch, [n, n], [0, 1], L, steps=24, crops_per_step=48, crop=64, warm=40,
+        X, Y, scale = LG.generate(torch, [n, n], [0, 1], L, steps=nst, crops_per_step=cps, crop=64, warm=40,
                                   inputs=inp)
         gen_s = time.perf_counter() - t0
         net, info = _train_guess(torch, amrvac, LG, X, Y, 2, loss, kappa, iters=iters, batch=64)
         c1, t1s, _, r1 = LG.evaluate(torch, [n], [10000], L, steps=eval_steps, warm=40, net=net, scale=scale,
                                      inputs=inp)
-        info.update({"data_s": round(gen_s, 2), "adam_steps": iters, "batch": 64, "lr": 1e-3,
+        info.update({"data_s": round(gen_s, 2), "training_pairs": int(X.shape[0]), "adam_steps": iters, "batch": 64,
+                     "lr": 1e-3,
                      "vcycles_per_solve": float(np.mean(c1)), "vcycles_per_solve_each": [int(x) for x in c1.ravel()],
                      "initial_rel_residual_median": float(np.median(r1)), "ms_per_step": t1s * 1e3,
                      "cnn_launches": net.kernel_launches()})
-        out[f"learned_{inp}_inputs_{loss}_loss"] = info
+        out[f"learned_{inp}_inputs_{loss}_loss" + ("_20k_pairs" if X.shape[0] >= 20000 else "")] = info
         net.close()
         del X, Y
     return out

@@ -899,9 +899,44 @@ __device__ __forceinline__ double rd_guess_residual(const InstDev& I, const doub
   return (B[I.off0 + p] - Aw) * inv_scale / (2.0 * ndim * ih2);
 }
 
+// The same residual as the network's input, in float32 from float32 copies of w_n and B made
+// by bit narrowing (no float64 unit work: GB300's float64 rate is ~1/64 of float32).  B and
+// lambda w_n nearly cancel: with the narrowing's 2^-23 relative error the result keeps about
+// max|B| 2^-22 absolute accuracy, far below the bf16 resolution of the network's input (2^-9
+// of the residual's own size) wherever the residual is above 1e-4 of max|B|.
+__device__ __forceinline__ float rd_guess_residual_f(const InstDev& I, const double* __restrict__ B,
+                                                     const double* __restrict__ w, long long p, int ndim, int neu,
+                                                     float inv_scale) {
+  const int n = I.n[0];
+  int c[3] = {(int)(p % n), ndim > 1 ? (int)((p / n) % n) : 0, ndim > 2 ? (int)(p / ((long long)n * n)) : 0};
+  long long stride = 1;
+  float nb = 0.f;
+  int cnt = 0;
+  for (int d = 0; d < ndim; ++d) {
+    if (c[d] > 0) {
+      nb += narrow<float>(w[p - stride]);
+      ++cnt;
+    } else if (!neu) {
+      nb += narrow<float>(w[p + (long long)(n - 1) * stride]);
+      ++cnt;
+    }
+    if (c[d] < n - 1) {
+      nb += narrow<float>(w[p + stride]);
+      ++cnt;
+    } else if (!neu) {
+      nb += narrow<float>(w[p - (long long)(n - 1) * stride]);
+      ++cnt;
+    }
+    stride *= n;
+  }
+  const float ih2 = I.ih2f[0], wp = narrow<float>(w[p]);
+  const float Aw = I.lamf * wp - (nb - (float)cnt * wp) * ih2;
+  return (narrow<float>(B[I.off0 + p]) - Aw) * (inv_scale / (2.f * (float)ndim * ih2));
+}
+
 // network input of one instance as float [5][cells]: (u_n, v_n, c2, c3, dt) with
 // (c2, c3) = (u*_prev, v*_prev) (RD_GUESS_IN_PREV) or the normalised residuals of the
-// previous-step guess (RD_GUESS_IN_RESIDUAL)
+// previous-step guess (RD_GUESS_IN_RESIDUAL); float64 values narrowed on the integer units
 __global__ void rd_cnn_input_kernel(const InstDev* __restrict__ inst, int iu, int iv, const double* __restrict__ B,
                                     const double* __restrict__ wn, const double* __restrict__ pin, long long cells,
                                     long long n0, float dt, int kind, int ndim, int neu, double inv_scale,
@@ -910,20 +945,20 @@ __global__ void rd_cnn_input_kernel(const InstDev* __restrict__ inst, int iu, in
   if (t >= n0) return;
   const InstDev& Iu = inst[iu];
   const long long off = Iu.off0;
-  cin[0 * n0 + t] = (float)wn[off + t];
-  cin[1 * n0 + t] = (float)wn[cells + off + t];
+  cin[0 * n0 + t] = narrow<float>(wn[off + t]);
+  cin[1 * n0 + t] = narrow<float>(wn[cells + off + t]);
   if (kind == RD_GUESS_IN_RESIDUAL) {
-    cin[2 * n0 + t] = (float)rd_guess_residual(Iu, B, wn + off, t, ndim, neu, inv_scale);
-    cin[3 * n0 + t] = (float)rd_guess_residual(inst[iv], B, wn + cells + off, t, ndim, neu, inv_scale);
+    cin[2 * n0 + t] = rd_guess_residual_f(Iu, B, wn + off, t, ndim, neu, (float)inv_scale);
+    cin[3 * n0 + t] = rd_guess_residual_f(inst[iv], B, wn + cells + off, t, ndim, neu, (float)inv_scale);
   } else {
-    cin[2 * n0 + t] = (float)pin[off + t];
-    cin[3 * n0 + t] = (float)pin[cells + off + t];
+    cin[2 * n0 + t] = narrow<float>(pin[off + t]);
+    cin[3 * n0 + t] = narrow<float>(pin[cells + off + t]);
   }
   cin[4 * n0 + t] = dt;
 }
 
 // multigrid guess X = w_n + scale * network output (per species): the network
-// predicts the increment over the previous-step guess
+// predicts the increment over the previous-step guess (formed in float32, widened exactly)
 __global__ void rd_cnn_guess_kernel(const InstDev* __restrict__ inst, int iu, int iv, const float* __restrict__ cout,
                                     long long n0, double scale, double* __restrict__ X, const double* __restrict__ wn,
                                     long long cells) {
@@ -931,8 +966,9 @@ __global__ void rd_cnn_guess_kernel(const InstDev* __restrict__ inst, int iu, in
   if (t >= n0) return;
   const InstDev& Iu = inst[iu];
   const InstDev& Iv = inst[iv];
-  X[Iu.off0 + t] = wn[Iu.off0 + t] + scale * (double)cout[t];
-  X[Iv.off0 + t] = wn[cells + Iu.off0 + t] + scale * (double)cout[n0 + t];
+  const float sf = (float)scale;
+  X[Iu.off0 + t] = __dadd_rn(wn[Iu.off0 + t], widen(sf * cout[t]));
+  X[Iv.off0 + t] = __dadd_rn(wn[cells + Iu.off0 + t], widen(sf * cout[n0 + t]));
 }
 
 // training pairs: crops of the network input (as rd_cnn_input_kernel) and target (w* - w_n) / scale

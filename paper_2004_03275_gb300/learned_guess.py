@@ -84,6 +84,7 @@ def generate(torch, sizes, seeds, L, steps, crops_per_step, crop=64, warm=0, sca
             scale = float(torch.sqrt(torch.mean(yi.double() ** 2)).item())
         xi = torch.empty((crops_per_step, 5) + box, device="cuda")
         yi = torch.empty((crops_per_step, 2) + box, device="cuda")
+        torch.cuda.synchronize()  # the buffers are free on every stream before the solver writes them
         rd.extract_crops(inst, corners, crop, scale, xi, yi)
         X.append(xi)
         Y.append(yi)
@@ -107,9 +108,14 @@ def train(torch, net, X, Y, iters, batch=32, lr=1e-3, margin=4, seed=1):
     losses = []
     t0 = time.perf_counter()
     for it in range(iters):
+        # the network's kernels run on its own stream: the device-wide synchronisation orders the
+        # previous step's reads of the last batch before torch may reuse that memory, and the
+        # gather of this batch (on torch's stream) before the step reads it
+        torch.cuda.synchronize()
         idx = torch.from_numpy(rng.integers(0, X.shape[0], batch)).cuda()
         xb = X.index_select(0, idx).contiguous()
         yb = Y.index_select(0, idx).contiguous()
+        torch.cuda.synchronize()
         want = it == 0 or it == iters - 1 or (it + 1) % 100 == 0
         loss = net.train_step(xb, yb, lr=lr_at(it, iters, lr), margin=margin, want_loss=want)
         if want:
@@ -121,6 +127,7 @@ def train(torch, net, X, Y, iters, batch=32, lr=1e-3, margin=4, seed=1):
 def dataset_loss(torch, net, X, Y, margin=4, chunk=16):
     """Masked MSE of the network over the whole data set (chunks in order, weighted by size)."""
     tot = 0.0
+    torch.cuda.synchronize()  # X, Y complete before the network's stream reads them
     for i in range(0, X.shape[0], chunk):
         xb, yb = X[i:i + chunk].contiguous(), Y[i:i + chunk].contiguous()
         loss, _ = net.gradient(xb, yb, margin=margin)
