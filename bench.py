@@ -249,14 +249,14 @@ def bench_learned_guess(torch, amrvac, stream, eval_steps=6):
     c0, t0s, _, r0 = LG.evaluate(torch, [n], [10000], L, steps=eval_steps, warm=40)
     out = {"workload": "Gray-Scott IMEX 2048^2 (seed 10000, after 40 warm-up steps), MG rtol 1e-10",
            "training_data": "crops 64^2 after each of 24 steps of two 2048^2 runs (seeds 0, 1; 40 warm-up steps), "
-                            "48 crops per step (1152 pairs); the _20k_pairs entry: 50 steps, 200 crops per step",
+                            "48 crops per step (1152 pairs); the 20000-pair entry: 100 steps, 200 crops per step",
            "vcycles_per_solve_previous_step_guess": float(np.mean(c0)),
            "initial_rel_residual_median_previous_step": float(np.median(r0)),
            "ms_per_step_previous_step_guess": t0s * 1e3, "operator_kappa": [round(k, 5) for k in kappa]}
-    # (inputs, loss, Adam steps, crops per step, steps per run): the two networks on 1152 crops, and
-    # the residual network on the configuration's 20k training pairs (two runs x 50 steps x 200 crops)
+    # (inputs, loss, Adam steps, crops per step, steps): the two networks on 1152 crops, and the
+    # residual network on the configuration's 20k training pairs (100 steps x 200 crops of the two runs)
     for inp, loss, iters, cps, nst in (("residual", "operator", 5000, 48, 24), ("prev", "mse", 1500, 48, 24),
-                                       ("residual", "operator", 5000, 200, 50)):
+                                       ("residual", "operator", 5000, 200, 100)):
         t0 = time.perf_counter()
         X, Y, scale = LG.generate(torch, [n, n], [0, 1], L, steps=nst, crops_per_step=cps, crop=64, warm=40,
                                   inputs=inp)
@@ -269,7 +269,7 @@ def bench_learned_guess(torch, amrvac, stream, eval_steps=6):
                      "vcycles_per_solve": float(np.mean(c1)), "vcycles_per_solve_each": [int(x) for x in c1.ravel()],
                      "initial_rel_residual_median": float(np.median(r1)), "ms_per_step": t1s * 1e3,
                      "cnn_launches": net.kernel_launches()})
-        out[f"learned_{inp}_inputs_{loss}_loss" + ("_20k_pairs" if X.shape[0] >= 20000 else "")] = info
+        out[f"learned_{inp}_inputs_{loss}_loss_{int(X.shape[0])}_pairs"] = info
         net.close()
         del X, Y
     return out
@@ -562,11 +562,8 @@ def bench_blast(torch, amrvac, stream, hbm_gbs, steps=20, regrid_every=10):
     return out
 
 
-def oracle_cpu_baseline(budget_s=12.0, max_side=512):
-    """The FP64 oracle as it stands (single thread) on a bounded KH sample."""
-    import oracle as O
-    side = max_side
-    nb = side // BNX
+def _oracle_kh_rate(O, side, budget_s):
+    """cell-stages/s of the oracle on KH side^2 (SSPRK3 steps until budget_s has passed)."""
     kw = kh_kwargs(side)
     kw.pop("precision")
     kw.pop("stream")
@@ -581,9 +578,62 @@ def oracle_cpu_baseline(budget_s=12.0, max_side=512):
         if time.perf_counter() - t0 >= budget_s:
             break
     el = time.perf_counter() - t0
-    cells = side * side
-    return {"value": cells * 3 * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"KH {side}^2 ({nb * nb} blocks of 16^2), {n} SSPRK3 steps, FP64, single thread, {el:.1f} s"}
+    return side * side * 3 * n / el, n, el
+
+
+def oracle_cpu_baseline(budget_s=8.0):
+    """The FP64 oracle as it stands on the host cores: KH on one thread and on all cores (its
+    OpenMP loops over blocks give the one-thread result bit for bit), plus bounded samples of
+    the batched multigrid V-cycle and of the 3D blast tree on all cores."""
+    import oracle as O
+    nproc = os.cpu_count() or 1
+    O.set_threads(1)
+    v1, n1, el1 = _oracle_kh_rate(O, 512, budget_s)
+    O.set_threads(nproc)
+    vn, nn, eln = _oracle_kh_rate(O, 1024, budget_s)
+    out = {"value": vn, "unit": UNIT, "cores": nproc, "nproc": nproc, "kind": "oracle",
+           "sample": f"KH 1024^2 (4096 blocks of 16^2), {nn} SSPRK3 steps, FP64, {nproc} threads, {eln:.1f} s",
+           "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                             "sample": f"KH 512^2, {n1} SSPRK3 steps, FP64, 1 thread, {el1:.1f} s"}}
+    # multigrid: V-cycles of the oracle on one 1024^2 periodic grid (lambda of the Gray-Scott u
+    # species at 2048^2), unknown-V-cycles/s, one thread and all cores
+    n = 1024
+    r = np.random.default_rng(7).standard_normal((n, n))
+    lam = 2.0 / (0.5 * 2e-5)
+    mg = {}
+    for th in (1, nproc):
+        O.set_threads(th)
+        t0 = time.perf_counter()
+        k = 0
+        while k < 2 or time.perf_counter() - t0 < budget_s / 2:
+            O.mg_vcycle(r, 2.5 * n / 2048, lam)
+            k += 1
+        el = time.perf_counter() - t0
+        mg[f"threads_{th}"] = {"value": n * n * k / el, "unit": "unknown-V-cycles/s", "vcycles": k,
+                               "seconds": round(el, 2)}
+    out["mg_vcycle"] = dict(mg, sample="FP64 V-cycles (2 + 2 red-black sweeps) on one periodic 1024^2 grid")
+    # blast: base 2^3 blocks of 16^3, 3 levels, initial refinement, then steps on all cores
+    from paper_2004_03275_gb300 import inputs
+    kw = dict(ndim=3, block_nx=16, base=[2, 2, 2], max_level=3, gamma=5.0 / 3.0, cfl=0.8, flux="hllc",
+              limiter="koren", rk=3, bc="periodic", refine_tol=0.2, coarsen_frac=0.5, var_mask=1 | 16)
+    g = O.Grid(**kw)
+    for it in range(3):
+        lev, crd = g.leaves()
+        x, _ = inputs.cell_centres(lev, crd, 3, 16, [2, 2, 2], [0, 0, 0], [1, 1, 1])
+        g.set_prim(inputs.blast(x, seed=7))
+        if it < 2:
+            g.regrid()
+    cells = g.nleaves * 16 ** 3
+    t0 = time.perf_counter()
+    k = 0
+    while k < 1 or time.perf_counter() - t0 < budget_s / 2:
+        g.step()
+        k += 1
+    el = time.perf_counter() - t0
+    out["blast3d"] = {"value": cells * 3 * k / el, "unit": UNIT, "cores": nproc, "leaves": g.nleaves,
+                      "sample": f"blast, 2^3 base blocks of 16^3, 3 levels ({g.nleaves} leaves), {k} SSPRK3 steps, "
+                                f"{nproc} threads, {el:.1f} s"}
+    return out
 
 
 def run_reference(args, ws, rank):
@@ -591,11 +641,13 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return 0
     import oracle as O
+    nproc = os.cpu_count() or 1
+    O.set_threads(nproc)
     total = args.steps + args.warmup
     budget = 150.0 / max(total, 1)  # seconds per step so that the run stays within a few minutes
     side = 32
-    for s in (64, 96, 128, 192, 256, 384, 512, 768, 1024):
-        if s * s * 3 * 1.0e-6 <= budget:  # ~1 us per cell-stage on one core
+    for s in (64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048):
+        if s * s * 3 * 1.0e-6 / nproc <= budget:  # ~1 us per cell-stage on one core
             side = s
     kw = kh_kwargs(side)
     kw.pop("precision")
@@ -614,8 +666,8 @@ def run_reference(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_side": side, "parallelism": "cpu oracle, 1 thread"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "config": {"workload": WORKLOAD, "sample_side": side, "parallelism": f"cpu oracle, {nproc} threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nproc, "kind": "oracle",
                              "sample": f"KH {side}^2 per step (bounded sample of the 2048^2 workload)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

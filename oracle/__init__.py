@@ -104,6 +104,8 @@ def lib():
         L.orc_amg_regrid.argtypes = [C.POINTER(OrcAmgConfig), C.c_int, _ip, _ip, _dp, _dp, C.c_double, C.c_double,
                                      C.c_double, C.c_int, C.c_int, _ip, _ip, _dp, _dp, _dp]
         L.orc_amg_rd_step.argtypes = [C.POINTER(OrcAmgConfig), C.c_int, _ip, _ip] + [C.c_double] * 5 + [_dp, _dp, _ip]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_set_threads.restype = C.c_int
         if hasattr(L, "orc_cnn_forward"):
             _bind_cnn(L)
         _lib = L
@@ -237,6 +239,11 @@ class Grid:
         out = np.zeros((self.nv, 2 * self.ndim, 2, nt))
         lib().orc_face_ghosts(self.h, leaf, _d(out))
         return out
+
+
+def set_threads(n=0):
+    """Threads of the oracle's OpenMP loops (n <= 0 keeps the current setting); returns the count."""
+    return lib().orc_set_threads(int(n))
 
 
 def prim_to_cons(ndim, gamma, V):

@@ -86,6 +86,7 @@ void laplacian(const Grid& g, const double* x, double* out) {
 void residual(const Grid& g, double lambda, const double* x, const double* b, double* r) {
   double ih2 = 1.0 / (g.h * g.h);
   int nz = g.nd > 2 ? g.n : 1, ny = g.nd > 1 ? g.n : 1;
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < g.n; ++i) {
@@ -102,6 +103,9 @@ void rbgs(const Grid& g, double lambda, double* x, const double* b) {
   double ih2 = 1.0 / (g.h * g.h);
   int nz = g.nd > 2 ? g.n : 1, ny = g.nd > 1 ? g.n : 1;
   for (int colour = 0; colour < 2; ++colour)
+    // a cell of one colour reads only cells of the other: any order within a colour (OpenMP
+    // timing build) gives the same sweep
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < nz; ++k)
       for (int j = 0; j < ny; ++j)
         for (int i = 0; i < g.n; ++i) {
@@ -116,6 +120,7 @@ void rbgs(const Grid& g, double lambda, double* x, const double* b) {
 void restrict_mean(const Grid& f, const Grid& c, const double* rf, double* bc) {
   int nz = c.nd > 2 ? c.n : 1, ny = c.nd > 1 ? c.n : 1;
   int oz = c.nd > 2 ? 2 : 1, oy = c.nd > 1 ? 2 : 1;
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < c.n; ++i) {
@@ -134,6 +139,7 @@ void restrict_mean(const Grid& f, const Grid& c, const double* rf, double* bc) {
 void prolong_add(const Grid& c, const Grid& f, const double* ec, double* xf) {
   int nz = f.nd > 2 ? f.n : 1, ny = f.nd > 1 ? f.n : 1;
   int cz = f.nd > 2 ? 2 : 1, cy = f.nd > 1 ? 2 : 1;
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < f.n; ++i) {

@@ -76,6 +76,9 @@ double orc_dt(const orc_grid* g, double t_end);        /* CFL step clipped to t_
 double orc_step(orc_grid* g, double t_end);            /* one SSPRK step; returns dt */
 void orc_totals(const orc_grid* g, double* tot);       /* sum U dV per variable */
 void orc_lohner(const orc_grid* g, double* err);       /* max estimator per leaf */
+/* threads of the OpenMP loops over blocks and cells (the timed CPU baseline); n <= 0 keeps the
+   current count; returns it (1 in a build without OpenMP).  Results do not depend on it. */
+int orc_set_threads(int n);
 int orc_regrid(orc_grid* g);                           /* returns new number of leaves */
 /* face-ghost values of one leaf (for tests): [var][face 0..2*ndim-1][layer 0..1][tangential cells] */
 void orc_face_ghosts(const orc_grid* g, int leaf, double* out);

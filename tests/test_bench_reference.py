@@ -19,15 +19,22 @@ def run_bench(env_extra, *args):
 
 
 def test_reference_arm_prints_one_line_with_the_contract_keys():
-    # 12500 steps leave ~12 ms per step: the smallest (32^2) KH sample, a few seconds in all
-    lines = run_bench({"RANK": "0", "WORLD_SIZE": "1", "LOCAL_RANK": "0"}, "--steps", "12500", "--warmup", "0")
+    # 3 steps leave 50 s per step: the largest KH sample the rule allows (2048^2 on a few cores),
+    # a few seconds per step
+    lines = run_bench({"RANK": "0", "WORLD_SIZE": "1", "LOCAL_RANK": "0"}, "--steps", "3", "--warmup", "0")
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["higher_is_better"] is True and d["value"] > 0
-    assert d["unit"] == "cell-stages/s" and d["steps"] == 12500 and d["warmup"] == 0
-    assert d["config"]["sample_side"] == 32
+    assert d["unit"] == "cell-stages/s" and d["steps"] == 3 and d["warmup"] == 0
+    nproc = os.cpu_count() or 1
+    want = 32
+    for s in (64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048):
+        if s * s * 3 * 1.0e-6 / nproc <= 150.0 / 3:
+            want = s
+    assert d["config"]["sample_side"] == want
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and "32^2" in cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == nproc and cb["value"] == d["value"]
+    assert f"{want}^2" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["ms_per_step"] > 0
 

@@ -4,6 +4,8 @@ Each test ties the oracle to something outside itself: an exact Riemann
 solution, a textbook limiter function, conservation, a measured order of
 accuracy, an invariant of the tree algorithms.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -361,3 +363,29 @@ def test_ssprk_temporal_order(rk, lo, hi):
     e = np.array([np.max(np.abs(run(c) - ref)) for c in (0.8, 0.4, 0.2)])
     orders = np.log2(e[:-1] / e[1:])
     assert np.all((orders > lo) & (orders < hi)), (e, orders)
+
+
+def test_parallel_oracle_equals_serial():
+    """The oracle's OpenMP loops (blocks of the stage update, the CFL rate, the multigrid's
+    colour sweeps, residuals and transfers) give the serial result bit for bit: the all-core
+    CPU baseline times the same computation as the one-thread one."""
+    from paper_2004_03275_gb300 import inputs
+    nproc = os.cpu_count() or 1
+    kw = dict(ndim=2, block_nx=16, base=[4, 4], gamma=1.4, cfl=0.8, flux="hllc", limiter="vanleer", rk=3,
+              bc="periodic")
+    res = []
+    for threads in (1, max(2, nproc)):
+        O.set_threads(threads)
+        g = O.Grid(**kw)
+        lev, crd = g.leaves()
+        x, gi = inputs.cell_centres(lev, crd, 2, 16, [4, 4, 1], [0, 0, 0], [1, 1, 1])
+        g.set_prim(inputs.kelvin_helmholtz(x, gi, 64, seed=2004))
+        for _ in range(3):
+            g.step()
+        b = np.random.default_rng(5).standard_normal((48, 48))
+        xo, cyc, rr = O.mg_solve(b, np.zeros_like(b), 2.5, 30.0, rtol=1e-10)
+        res.append((g.get_cons(), g.t, xo, cyc))
+    O.set_threads(nproc)
+    a, b2 = res
+    assert np.array_equal(a[0], b2[0]) and a[1] == b2[1]
+    assert np.array_equal(a[2], b2[2]) and a[3] == b2[3]
