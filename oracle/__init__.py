@@ -16,7 +16,7 @@ from . import build as _build
 _lib = None
 
 FLUX = {"tvdlf": 0, "hll": 1, "hllc": 2}
-LIMITER = {"minmod": 0, "vanleer": 1, "koren": 2, "none": 3, "mc": 4}
+LIMITER = {"minmod": 0, "vanleer": 1, "koren": 2, "none": 3, "mc": 4, "cada": 5}
 BC = {"periodic": 0, "outflow": 1}
 MG_BC = {"periodic": 0, "neumann": 1}
 RD_MODEL = {"gray-scott": 0, "schnakenberg": 1}

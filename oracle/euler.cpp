@@ -146,9 +146,38 @@ void riemann_flux(int nd, int dir, int kind, double gam, const double* VL, const
 }
 
 // READING (limiters are named in Sec. 2.3.1 / 2.4 but not written out):
-// a = q_i - q_{i-1}, b = q_{i+1} - q_i; s- is used towards i-1/2, s+ towards i+1/2.
+// a = q_i - q_{i-1}, b = q_{i+1} - q_i; s- is used towards i-1/2, s+ towards i+1/2
+// (face values q_i - s-/2 and q_i + s+/2).
+//  * minmod, van Leer, monotonized central: one symmetric slope, zero at extrema.
+//  * Koren (1993): the third-order upwind-biased (kappa = 1/3) face values
+//    q_i + (a + 2b)/6 and q_i - (2a + b)/6, limited into the TVD region:
+//    s+ = sgn(b) min(2|a|, (|a| + 2|b|)/3, 2|b|), s- = sgn(a) min(2|b|, (2|a| + |b|)/3, 2|a|),
+//    zero where a b <= 0.
+//  * Cada: the third-order limiter of Cada and Torrilhon (J. Comput. Phys. 228 (2009) 4118,
+//    "Compact third-order limiter functions for finite volume methods"), which Sec. 2.3.1
+//    uses.  With theta = a / b the face offset is phi(theta) b / 2, phi_3(theta) = (2 + theta)/3
+//    the unlimited third-order function and
+//      phi(theta) = max(0, min(phi_3(theta), max(-theta, min(2 theta, phi_3(theta), 1.5)))),
+//    and the mirror image, theta = b / a times a, towards i-1/2.  Unlike the TVD limiters it
+//    keeps a slope where a and b differ in sign (|theta| small: a one-sided extremum), bounded
+//    by -theta.  READING: the limited function everywhere; the paper's switch to phi_3 near
+//    smooth extrema, which depends on a dimensional radius, is not used.
 void limited_slopes(int lim, double a, double b, double* sm, double* sp) {
   bool same = (a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0);
+  if (lim == ORC_LIM_CADA) {
+    double A = std::fabs(a), B = std::fabs(b);
+    double up = 0.0, dn = 0.0;
+    if (same) {
+      up = std::min(std::min(2.0 * A, (A + 2.0 * B) / 3.0), 1.5 * B);
+      dn = std::min(std::min(2.0 * B, (2.0 * A + B) / 3.0), 1.5 * A);
+    } else if (a != 0.0 && b != 0.0) {
+      up = std::max(0.0, std::min((2.0 * B - A) / 3.0, A));
+      dn = std::max(0.0, std::min((2.0 * A - B) / 3.0, B));
+    }
+    *sp = (b > 0.0) ? up : -up;
+    *sm = (a > 0.0) ? dn : -dn;
+    return;
+  }
   if (lim == ORC_LIM_NONE || !same) {
     *sm = 0.0;
     *sp = 0.0;
@@ -167,10 +196,10 @@ void limited_slopes(int lim, double a, double b, double* sm, double* sp) {
     double s = std::min(std::min(0.5 * (A + B), 2.0 * A), 2.0 * B);
     *sm = (a > 0.0) ? s : -s;
     *sp = *sm;
-  } else {  // Koren, phi(r) = max(0, min(2r, (1+2r)/3, 2)) applied on each side
+  } else {  // Koren: kappa = 1/3 face values limited into the TVD region
     double A = std::fabs(a), B = std::fabs(b);
-    double up = std::min(std::min(2.0 * A, (2.0 * A + B) / 3.0), 2.0 * B);
-    double dn = std::min(std::min(2.0 * B, (A + 2.0 * B) / 3.0), 2.0 * A);
+    double up = std::min(std::min(2.0 * A, (A + 2.0 * B) / 3.0), 2.0 * B);
+    double dn = std::min(std::min(2.0 * B, (2.0 * A + B) / 3.0), 2.0 * A);
     *sp = (b > 0.0) ? up : -up;
     *sm = (a > 0.0) ? dn : -dn;
   }

@@ -40,7 +40,7 @@ extern "C" {
 #endif
 
 enum { ORC_FLUX_TVDLF = 0, ORC_FLUX_HLL = 1, ORC_FLUX_HLLC = 2 };
-enum { ORC_LIM_MINMOD = 0, ORC_LIM_VANLEER = 1, ORC_LIM_KOREN = 2, ORC_LIM_NONE = 3, ORC_LIM_MC = 4 };
+enum { ORC_LIM_MINMOD = 0, ORC_LIM_VANLEER = 1, ORC_LIM_KOREN = 2, ORC_LIM_NONE = 3, ORC_LIM_MC = 4, ORC_LIM_CADA = 5 };
 enum { ORC_SSPRK2 = 2, ORC_SSPRK3 = 3 };
 enum { ORC_BC_PERIODIC = 0, ORC_BC_OUTFLOW = 1 };
 

@@ -20,7 +20,7 @@ STATUS = {0: "AMR_OK", -1: "AMR_ERR_INVALID_ARG", -2: "AMR_ERR_OOM", -3: "AMR_ER
           -4: "AMR_ERR_NONPHYSICAL", -5: "AMR_ERR_TIMEOUT", -6: "MG_ERR_NOT_CONVERGED",
           -7: "AMR_ERR_CAPACITY", -8: "AMR_ERR_UNBALANCED"}
 FLUX = {"tvdlf": 0, "hll": 1, "hllc": 2}
-LIMITER = {"minmod": 0, "vanleer": 1, "koren": 2, "none": 3, "mc": 4}
+LIMITER = {"minmod": 0, "vanleer": 1, "koren": 2, "none": 3, "mc": 4, "cada": 5}
 BC = {"periodic": 0, "outflow": 1}
 PRECISION = {"fp64": 0, "fp32": 1}
 
