@@ -38,7 +38,8 @@ typedef enum {
 } amr_status;
 
 enum { AMR_FLUX_TVDLF = 0, AMR_FLUX_HLL = 1, AMR_FLUX_HLLC = 2 };
-enum { AMR_LIM_MINMOD = 0, AMR_LIM_VANLEER = 1, AMR_LIM_KOREN = 2, AMR_LIM_NONE = 3, AMR_LIM_MC = 4 };
+enum { AMR_LIM_MINMOD = 0, AMR_LIM_VANLEER = 1, AMR_LIM_KOREN = 2, AMR_LIM_NONE = 3, AMR_LIM_MC = 4,
+       AMR_LIM_CADA = 5 };
 enum { AMR_SSPRK2 = 2, AMR_SSPRK3 = 3 };
 enum { AMR_BC_PERIODIC = 0, AMR_BC_OUTFLOW = 1 };
 enum { AMR_FP64 = 0, AMR_FP32 = 1 };

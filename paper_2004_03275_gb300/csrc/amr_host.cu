@@ -546,7 +546,7 @@ int amr_create(const amr_config* cfg, amr_handle** out) {
   if (cfg->ndim < 1 || cfg->ndim > 3) return AMR_ERR_INVALID_ARG;
   if (cfg->block_nx != 8 && cfg->block_nx != 16) return AMR_ERR_INVALID_ARG;
   if (cfg->max_level < 1 || cfg->max_level > kMaxLevel) return AMR_ERR_INVALID_ARG;
-  if (cfg->flux < 0 || cfg->flux > 2 || cfg->limiter < 0 || cfg->limiter > 4) return AMR_ERR_INVALID_ARG;
+  if (cfg->flux < 0 || cfg->flux > 2 || cfg->limiter < 0 || cfg->limiter > 5) return AMR_ERR_INVALID_ARG;
   if (cfg->rk != AMR_SSPRK2 && cfg->rk != AMR_SSPRK3) return AMR_ERR_INVALID_ARG;
   if (cfg->precision != AMR_FP64 && cfg->precision != AMR_FP32) return AMR_ERR_INVALID_ARG;
   if (!(cfg->gamma > 1.0) || !(cfg->cfl > 0.0)) return AMR_ERR_INVALID_ARG;

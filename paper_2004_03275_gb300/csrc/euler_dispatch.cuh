@@ -63,6 +63,7 @@ cudaError_t stage2d_f32_prepare(int lim) {
     case LIM_VANLEER: return stage2d_f32_prepare_one<B, FLUX, LIM_VANLEER>();
     case LIM_KOREN: return stage2d_f32_prepare_one<B, FLUX, LIM_KOREN>();
     case LIM_MC: return stage2d_f32_prepare_one<B, FLUX, LIM_MC>();
+    case LIM_CADA: return stage2d_f32_prepare_one<B, FLUX, LIM_CADA>();
     default: return stage2d_f32_prepare_one<B, FLUX, LIM_NONE>();
   }
 }
@@ -97,6 +98,7 @@ cudaError_t stage2d_f32_launch(const StageArgs<float>& a, const Geometry& G, cud
     case LIM_VANLEER: stage2d_f32_go<B, FLUX, LIM_VANLEER>(a, G, s); break;
     case LIM_KOREN: stage2d_f32_go<B, FLUX, LIM_KOREN>(a, G, s); break;
     case LIM_MC: stage2d_f32_go<B, FLUX, LIM_MC>(a, G, s); break;
+    case LIM_CADA: stage2d_f32_go<B, FLUX, LIM_CADA>(a, G, s); break;
     default: stage2d_f32_go<B, FLUX, LIM_NONE>(a, G, s); break;
   }
   return cudaGetLastError();
@@ -120,6 +122,7 @@ cudaError_t stage3d_f32_launch(const StageArgs<float>& a, const Geometry& G, cud
     case LIM_VANLEER: stage3d_f32_go<FLUX, LIM_VANLEER>(a, G, s); break;
     case LIM_KOREN: stage3d_f32_go<FLUX, LIM_KOREN>(a, G, s); break;
     case LIM_MC: stage3d_f32_go<FLUX, LIM_MC>(a, G, s); break;
+    case LIM_CADA: stage3d_f32_go<FLUX, LIM_CADA>(a, G, s); break;
     default: stage3d_f32_go<FLUX, LIM_NONE>(a, G, s); break;
   }
   return cudaGetLastError();
@@ -141,6 +144,7 @@ cudaError_t stage3d_f32_prepare(int lim) {
                   : lim == LIM_VANLEER ? stage3d_z_prepare<FLUX, LIM_VANLEER>()
                   : lim == LIM_KOREN   ? stage3d_z_prepare<FLUX, LIM_KOREN>()
                   : lim == LIM_MC      ? stage3d_z_prepare<FLUX, LIM_MC>()
+                  : lim == LIM_CADA    ? stage3d_z_prepare<FLUX, LIM_CADA>()
                                        : stage3d_z_prepare<FLUX, LIM_NONE>();
   if (e != cudaSuccess) return e;
   switch (lim) {
@@ -155,6 +159,9 @@ cudaError_t stage3d_f32_prepare(int lim) {
                                   (int)kXy3Smem);
     case LIM_MC:
       return cudaFuncSetAttribute(stage3d_xy_kernel<FLUX, LIM_MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kXy3Smem);
+    case LIM_CADA:
+      return cudaFuncSetAttribute(stage3d_xy_kernel<FLUX, LIM_CADA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kXy3Smem);
     default:
       return cudaFuncSetAttribute(stage3d_xy_kernel<FLUX, LIM_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -18,7 +18,7 @@
 namespace amrgpu {
 
 enum { FLUX_TVDLF = 0, FLUX_HLL = 1, FLUX_HLLC = 2 };
-enum { LIM_MINMOD = 0, LIM_VANLEER = 1, LIM_KOREN = 2, LIM_NONE = 3, LIM_MC = 4 };
+enum { LIM_MINMOD = 0, LIM_VANLEER = 1, LIM_KOREN = 2, LIM_NONE = 3, LIM_MC = 4, LIM_CADA = 5 };
 
 // ------------------------------------------------------------------ physics --
 template <typename real, int ND>
@@ -125,11 +125,28 @@ __device__ __forceinline__ void riemann(int dir, const real* VL, const real* VR,
 }
 
 // Limited slopes of a cell from a = q_i - q_{i-1}, b = q_{i+1} - q_i:
-// s- towards i-1/2, s+ towards i+1/2 (minmod, van Leer, Koren phi(r) =
-// max(0, min(2r, (1+2r)/3, 2)) on each side).
+// s- towards i-1/2, s+ towards i+1/2 (face values q_i -+ s/2).  minmod, van Leer,
+// monotonized central: one symmetric slope.  Koren (1993): the third-order kappa = 1/3
+// face values q_i + (a + 2b)/6, q_i - (2a + b)/6 limited into the TVD region.  Cada and
+// Torrilhon (2009), the third-order limiter of Sec. 2.3.1: theta = a/b, offset phi(theta) b/2
+// with phi = max(0, min(phi_3, max(-theta, min(2 theta, phi_3, 3/2)))), phi_3 = (2 + theta)/3,
+// and its mirror image towards i-1/2; it keeps a slope where a and b differ in sign.
 template <typename real>
 __device__ __forceinline__ void limited_slopes(int lim, real a, real b, real& sm, real& sp) {
   bool same = (a > real(0) && b > real(0)) || (a < real(0) && b < real(0));
+  if (lim == LIM_CADA) {
+    real A = fabs(a), Bb = fabs(b), up = real(0), dn = real(0);
+    if (same) {
+      up = fmin(fmin(real(2) * A, (A + real(2) * Bb) / real(3)), real(1.5) * Bb);
+      dn = fmin(fmin(real(2) * Bb, (real(2) * A + Bb) / real(3)), real(1.5) * A);
+    } else if (a != real(0) && b != real(0)) {
+      up = fmax(real(0), fmin((real(2) * Bb - A) / real(3), A));
+      dn = fmax(real(0), fmin((real(2) * A - Bb) / real(3), Bb));
+    }
+    sp = (b > real(0)) ? up : -up;
+    sm = (a > real(0)) ? dn : -dn;
+    return;
+  }
   if (lim == LIM_NONE || !same) {
     sm = real(0);
     sp = real(0);
@@ -148,10 +165,10 @@ __device__ __forceinline__ void limited_slopes(int lim, real a, real b, real& sm
     real s = fmin(fmin(real(0.5) * (A + Bb), real(2) * A), real(2) * Bb);
     sm = (a > real(0)) ? s : -s;
     sp = sm;
-  } else {
+  } else {  // Koren
     real A = fabs(a), Bb = fabs(b);
-    real up = fmin(fmin(real(2) * A, (real(2) * A + Bb) / real(3)), real(2) * Bb);
-    real dn = fmin(fmin(real(2) * Bb, (A + real(2) * Bb) / real(3)), real(2) * A);
+    real up = fmin(fmin(real(2) * A, (A + real(2) * Bb) / real(3)), real(2) * Bb);
+    real dn = fmin(fmin(real(2) * Bb, (real(2) * A + Bb) / real(3)), real(2) * A);
     sp = (b > real(0)) ? up : -up;
     sm = (a > real(0)) ? dn : -dn;
   }

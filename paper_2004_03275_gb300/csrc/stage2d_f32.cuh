@@ -57,10 +57,18 @@ __device__ __forceinline__ void half_slopes(float a, float b, float& hm, float& 
     s = (a * b > 0.f) ? copysignf(s, a) : 0.f;
     hm = s;
     hp = s;
-  } else {  // Koren
+  } else if (LIM == LIM_CADA) {  // Cada and Torrilhon (2009), halved; see limited_slopes
+    const float A = fabsf(a), B = fabsf(b), ab = a * b;
+    const float up = ab > 0.f ? fminf(fminf(A, (A + 2.f * B) * (1.f / 6.f)), 0.75f * B)
+                              : fmaxf(0.f, fminf((2.f * B - A) * (1.f / 6.f), 0.5f * A));
+    const float dn = ab > 0.f ? fminf(fminf(B, (2.f * A + B) * (1.f / 6.f)), 0.75f * A)
+                              : fmaxf(0.f, fminf((2.f * A - B) * (1.f / 6.f), 0.5f * B));
+    hp = ab != 0.f ? copysignf(up, b) : 0.f;
+    hm = ab != 0.f ? copysignf(dn, a) : 0.f;
+  } else {  // Koren: kappa = 1/3 face values limited into the TVD region, halved
     float A = fabsf(a), B = fabsf(b);
-    float up = fminf(fminf(A, (2.f * A + B) * (1.f / 6.f)), B);
-    float dn = fminf(fminf(B, (A + 2.f * B) * (1.f / 6.f)), A);
+    float up = fminf(fminf(A, (A + 2.f * B) * (1.f / 6.f)), B);
+    float dn = fminf(fminf(B, (2.f * A + B) * (1.f / 6.f)), A);
     bool same = a * b > 0.f;
     hp = same ? copysignf(up, b) : 0.f;
     hm = same ? copysignf(dn, a) : 0.f;
@@ -91,11 +99,14 @@ __device__ __forceinline__ void half_slopes2(float2 a, float2 b, float2& hm, flo
     s = sel2(ab.x > 0.f, ab.y > 0.f, make_float2(copysignf(s.x, a.x), copysignf(s.y, a.y)), bc2(0.f));
     hm = s;
     hp = s;
-  } else {  // Koren
+  } else if (LIM == LIM_CADA) {  // Cada and Torrilhon (2009), halved; per element as half_slopes
+    half_slopes<LIM_CADA>(a.x, b.x, hm.x, hp.x);
+    half_slopes<LIM_CADA>(a.y, b.y, hm.y, hp.y);
+  } else {  // Koren: kappa = 1/3 face values (a + 2b)/6 up, (2a + b)/6 down, limited
     const float2 ab = mul2(a, b);
     const float2 A = make_float2(fabsf(a.x), fabsf(a.y)), B = make_float2(fabsf(b.x), fabsf(b.y));
-    const float2 u6 = fma2(A, bc2(1.f / 3.f), mul2(B, bc2(1.f / 6.f)));
-    const float2 d6 = fma2(B, bc2(1.f / 3.f), mul2(A, bc2(1.f / 6.f)));
+    const float2 u6 = fma2(B, bc2(1.f / 3.f), mul2(A, bc2(1.f / 6.f)));
+    const float2 d6 = fma2(A, bc2(1.f / 3.f), mul2(B, bc2(1.f / 6.f)));
     const float2 up = make_float2(fminf(fminf(A.x, u6.x), B.x), fminf(fminf(A.y, u6.y), B.y));
     const float2 dn = make_float2(fminf(fminf(B.x, d6.x), A.x), fminf(fminf(B.y, d6.y), A.y));
     const bool sx = ab.x > 0.f, sy = ab.y > 0.f;

@@ -55,7 +55,7 @@ def test_sod_config_parity_and_exact():
 
 
 @pytest.mark.parametrize("flux", ["tvdlf", "hll", "hllc"])
-@pytest.mark.parametrize("limiter", ["minmod", "vanleer", "koren", "none", "mc"])
+@pytest.mark.parametrize("limiter", ["minmod", "vanleer", "koren", "none", "mc", "cada"])
 def test_2d_schemes_fp64_parity(flux, limiter):
     """Every flux x limiter pair, 15 leaves of 8^2 (ragged last CTA), 6 steps."""
     kw = dict(ndim=2, block_nx=8, base=[3, 5], gamma=1.4, cfl=0.8, flux=flux, limiter=limiter, rk=3,
@@ -73,8 +73,9 @@ def test_2d_schemes_fp64_parity(flux, limiter):
 
 @pytest.mark.parametrize("bnx", [8, 16])
 @pytest.mark.parametrize("rk", [2, 3])
-def test_1d_parity(bnx, rk):
-    kw = dict(ndim=1, block_nx=bnx, base=[9], gamma=1.4, cfl=0.6, flux="hllc", limiter="koren", rk=rk,
+@pytest.mark.parametrize("limiter", ["koren", "cada"])
+def test_1d_parity(bnx, rk, limiter):
+    kw = dict(ndim=1, block_nx=bnx, base=[9], gamma=1.4, cfl=0.6, flux="hllc", limiter=limiter, rk=rk,
               bc="periodic")
     s, g = pair(**kw)
     lev, crd = s.leaves()
@@ -90,9 +91,9 @@ def test_1d_parity(bnx, rk):
 
 
 @pytest.mark.parametrize("bnx,base", [(8, [2, 2, 3]), (16, [2, 1, 1])])
-@pytest.mark.parametrize("flux", ["hll", "hllc"])
-def test_3d_parity(bnx, base, flux):
-    kw = dict(ndim=3, block_nx=bnx, base=base, gamma=5.0 / 3.0, cfl=0.8, flux=flux, limiter="koren", rk=3,
+@pytest.mark.parametrize("flux,limiter", [("hll", "koren"), ("hllc", "koren"), ("hllc", "cada")])
+def test_3d_parity(bnx, base, flux, limiter):
+    kw = dict(ndim=3, block_nx=bnx, base=base, gamma=5.0 / 3.0, cfl=0.8, flux=flux, limiter=limiter, rk=3,
               bc="periodic", xmax=(base[0] / max(base), base[1] / max(base), base[2] / max(base)))
     s, g = pair(**kw)
     lev, crd = s.leaves()
@@ -222,7 +223,7 @@ def test_full_size_kh_one_step(precision):
 
 
 @pytest.mark.parametrize("flux", ["tvdlf", "hll", "hllc"])
-@pytest.mark.parametrize("limiter", ["minmod", "vanleer", "koren", "none", "mc"])
+@pytest.mark.parametrize("limiter", ["minmod", "vanleer", "koren", "none", "mc", "cada"])
 @pytest.mark.parametrize("bnx,base", [(8, [3, 5]), (16, [3, 2])])
 def test_2d_fp32_schemes(flux, limiter, bnx, base):
     """FP32 batched kernel: every flux x limiter, ragged last CTA for 8^2 leaves.

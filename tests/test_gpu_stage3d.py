@@ -34,7 +34,7 @@ def scaled_err(a, b):
 
 
 @pytest.mark.parametrize("flux", ["tvdlf", "hll", "hllc"])
-@pytest.mark.parametrize("limiter", ["minmod", "vanleer", "koren", "none", "mc"])
+@pytest.mark.parametrize("limiter", ["minmod", "vanleer", "koren", "none", "mc", "cada"])
 def test_3d_fp32_schemes(flux, limiter):
     base = [2, 1, 1]
     kw = dict(ndim=3, block_nx=16, base=base, gamma=5.0 / 3.0, cfl=0.8, flux=flux, limiter=limiter, rk=3,
