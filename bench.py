@@ -736,6 +736,9 @@ def main():
     value = replica_value(ncells * 3, ws, ms32)
     roof = stage_roofline(s32, 5, 4, 4, ncells, hbm, ms32, traffic=STAGE2D_F32_TRAFFIC)
     roof["peak_source"] = peak_src
+    pick, pick_us = s32.march_tuning()
+    roof["tuned_launch"] = {kind: {"warps_per_cta": nw, "persistent": bool(p), "us": round(u, 2)}
+                            for kind, (nw, p), u in zip(("first", "middle", "last"), pick, pick_us)}
 
     # ---------------------------------------------------------------- FP64 plain
     fp64 = None

@@ -174,6 +174,21 @@ int amr_face_ghosts(amr_handle* h, long long leaf, double* out, long long cap);
  * For measurement only (the events add a little launch overhead). */
 int amr_profile_step(amr_handle* h, double t_end, float* ms, int* kind, int cap, int* nkernels);
 
+/* Launch shapes of the float32 2D stage kernel for 16^2 leaves (the project's stage-kernel
+ * tuner; the paper has no counterpart).  Per stage kind k (0 first, 1 middle, 2 last with the
+ * CFL and totals reductions): choice[2k] = warps (= leaves) per CTA (2, 4 or 8; 4 for the
+ * last stage), choice[2k+1] = 1 for a grid of resident CTAs looping over the leaf groups,
+ * 0 for one CTA per group.  Before the first captured step of a float32 2D 16^2 handle on a
+ * uniform grid with SSPRK3, a tuner times every candidate on the handle's state (5 launches
+ * after a warm-up, CUDA events; neither the state nor the time advances) and keeps the
+ * fastest per kind; every candidate computes the same state bit for bit.
+ * amr_march_tuning: the current choice (host int[6]) and, when tuned, the chosen launch's
+ * time per kind in microseconds (host float[3] or NULL; 0 where not measured).
+ * amr_set_march_tuning: use `choice` (host int[6]) and skip the tuner; invalid values give
+ * AMR_ERR_INVALID_ARG and leave the choice unchanged. */
+int amr_march_tuning(amr_handle* h, int* choice, float* us);
+int amr_set_march_tuning(amr_handle* h, const int* choice);
+
 /* Device launch counters: kernels launched by this handle since creation. */
 int amr_kernel_launches(const amr_handle* h, long long* n);
 

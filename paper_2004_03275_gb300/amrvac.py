@@ -105,6 +105,8 @@ _SIGS = {
     "amr_face_ghosts": ([_vp, C.c_longlong, _dp, C.c_longlong], C.c_int),
     "amr_kernel_launches": ([_vp, _llp], C.c_int),
     "amr_profile_step": ([_vp, C.c_double, C.POINTER(C.c_float), _ip, C.c_int, _ip], C.c_int),
+    "amr_march_tuning": ([_vp, _ip, C.POINTER(C.c_float)], C.c_int),
+    "amr_set_march_tuning": ([_vp, _ip], C.c_int),
     "amr_reduce_noalloc": ([C.POINTER(AmrConfig), _vp, C.c_longlong, _dp, _dp], C.c_int),
     "mg_create": ([C.POINTER(MgConfig), C.POINTER(_vp)], C.c_int),
     "mg_destroy": ([_vp], C.c_int),
@@ -443,6 +445,18 @@ class AmrSolver:
         n = C.c_longlong()
         _check(self.lib.amr_kernel_launches(self.h, C.byref(n)), self.h)
         return n.value
+
+    def march_tuning(self):
+        """amr_march_tuning: ([(warps per CTA, persistent)] per stage kind, [us per kind])."""
+        ch = np.zeros(6, dtype=np.int32)
+        us = (C.c_float * 3)()
+        _check(self.lib.amr_march_tuning(self.h, ch.ctypes.data_as(_ip), us), self.h)
+        return [(int(ch[2 * k]), int(ch[2 * k + 1])) for k in range(3)], [float(us[k]) for k in range(3)]
+
+    def set_march_tuning(self, choice):
+        """amr_set_march_tuning: choice = [(warps per CTA, persistent)] for the three stage kinds."""
+        ch = np.ascontiguousarray(np.array(choice, dtype=np.int32).ravel())
+        _check(self.lib.amr_set_march_tuning(self.h, ch.ctypes.data_as(_ip)), self.h)
 
 
 NOALLOC_MAX_LEAVES = 16384

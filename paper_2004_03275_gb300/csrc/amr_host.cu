@@ -294,6 +294,11 @@ struct amr_handle {
   long long steps_seen = 0;
   cudaGraphExec_t graph = nullptr;
   int graph_kernels = 0;
+  // float32 2D 16^2 march kernel, per stage kind (first, middle, last): warps per CTA and
+  // persistence; chosen by tune_march() before the first captured step unless set by the caller
+  int march_tune[3][2] = {{4, 0}, {4, 0}, {4, 1}};
+  float march_us[3] = {0.f, 0.f, 0.f};  // time of the chosen launch per stage kind (us)
+  bool march_tuned = false;
   long long launches = 0;
   // profiling: when prof_ev is set, events bracket every kernel of a step
   std::vector<cudaEvent_t>* prof_ev = nullptr;  // pairs (before, after)
@@ -384,6 +389,11 @@ struct amr_handle {
       a.has_ffx = jumps;
       a.limiter = cfg.limiter;
       a.nleaves = nl;
+      {
+        const int kind = a.fuse_reduce ? 2 : (a.stage1 ? 0 : 1);
+        a.march_nw = march_tune[kind][0];
+        a.march_persist = march_tune[kind][1];
+      }
       int rc = dispatch_stage<real, ND>(a);
       if (rc) return rc;
       if (jumps) {
@@ -762,8 +772,7 @@ int amr_set_time(amr_handle* h, double t) {
   return AMR_OK;
 }
 
-static int ensure_graph(amr_handle* h) {
-  if (h->graph) return AMR_OK;
+static int capture_graph(amr_handle* h) {
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   long long before = h->launches;
@@ -780,6 +789,125 @@ static int ensure_graph(amr_handle* h) {
     return h->fail_cuda(ei, "cudaGraphInstantiate");
   }
   return AMR_OK;
+}
+
+// Stage-kernel tuner (float32 2D 16^2 leaves, uniform grids, SSPRK3).  Candidates per stage
+// kind: warps (leaves) per CTA in {2, 4, 8} and grid or persistent launch for the first and
+// middle stages, grid or persistent launch for the last stage (its CTAs have 4 warps).  The
+// kinds are tuned in turn, the others at their current choice: each candidate's step is
+// captured as the run's graph would be and replayed kTuneWarm times untimed and kTuneSteps times timed,
+// in kTuneRounds rounds over the candidates (best round kept)
+// (CUDA events around the replays, so every stage sees the cache state and launch sequence
+// of a real step), from a saved copy of the state and control block that is put back after
+// every candidate and at the end, so that neither the state nor the time advances.  Every candidate computes the same state bit for bit (tested); the fastest step
+// is kept.  Runs once, before the first captured step.
+constexpr int kTuneSteps = 10;
+constexpr int kTuneRounds = 3;
+constexpr int kTuneWarm = 5;
+
+static int tune_march(amr_handle* h) {
+  h->march_tuned = true;
+  if (h->cfg.precision != AMR_FP32 || h->nd != 2 || h->B != 16 || !h->tb.slabs.empty() ||
+      h->tree.leaves.empty() || h->cfg.rk != AMR_SSPRK3)
+    return AMR_OK;
+  const size_t sb = h->state_bytes(h->tree.leaves.size());
+  DBuf keepU, keepC;
+  CK(keepU.ensure(sb));
+  CK(keepC.ensure(sizeof(DevCtl)));
+  CK(cudaMemcpyAsync(keepU.p, h->U0.p, sb, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(keepC.p, h->ctl.p, sizeof(DevCtl), cudaMemcpyDeviceToDevice, h->stream));
+  auto restore = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(h->U0.p, keepU.p, sb, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->ctl.p, keepC.p, sizeof(DevCtl), cudaMemcpyDeviceToDevice, h->stream);
+    return e;
+  };
+  CK(ctl_set_t_end(h->ctl.as<DevCtl>(), 1e300, h->stream));  // no end-time clip while timing (restored after)
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int rc = AMR_OK;
+  static const int cands[2][6][2] = {{{4, 0}, {2, 0}, {8, 0}, {4, 1}, {2, 1}, {8, 1}},
+                                     {{4, 1}, {4, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}}};
+  for (int k = 0; k < 3 && !rc; ++k) {
+    const int nc = k < 2 ? 6 : 2;
+    // one captured step per candidate, then kTuneRounds rounds over the candidates in turn (so
+    // that clock ramps and cache history spread over all of them); a candidate's time is its
+    // best round
+    cudaGraphExec_t gx[6] = {};
+    float best[6];
+    for (int c = 0; c < nc; ++c) best[c] = 1e30f;
+    for (int c = 0; c < nc && !rc; ++c) {
+      h->march_tune[k][0] = cands[k < 2 ? 0 : 1][c][0];
+      h->march_tune[k][1] = cands[k < 2 ? 0 : 1][c][1];
+      h->drop_graph();
+      rc = capture_graph(h);
+      gx[c] = h->graph;
+      h->graph = nullptr;
+    }
+    for (int round = 0; round < kTuneRounds && !rc; ++round)
+      for (int c = 0; c < nc && !rc; ++c) {
+        // warm-up steps: the restore leaves the whole state in L2, which a real run's stages
+        // do not see; a few steps bring the cache back to its running state
+        cudaError_t e = cudaSuccess;
+        for (int r = 0; r < kTuneWarm && e == cudaSuccess; ++r) e = cudaGraphLaunch(gx[c], h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < kTuneSteps && e == cudaSuccess; ++r) e = cudaGraphLaunch(gx[c], h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = restore();
+        if (e == cudaSuccess) e = ctl_set_t_end(h->ctl.as<DevCtl>(), 1e300, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+          rc = h->fail_cuda(e, "stage tuner");
+          break;
+        }
+        best[c] = std::min(best[c], ms);
+      }
+    for (int c = 0; c < nc; ++c)
+      if (gx[c]) cudaGraphExecDestroy(gx[c]);
+    int bc = 0;
+    for (int c = 1; c < nc; ++c)
+      if (best[c] < best[bc]) bc = c;
+    h->march_tune[k][0] = cands[k < 2 ? 0 : 1][bc][0];
+    h->march_tune[k][1] = cands[k < 2 ? 0 : 1][bc][1];
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->drop_graph();  // the caller captures the step with the chosen launches
+  if (rc) {
+    restore();
+    return rc;
+  }
+  CK(restore());
+  CK(ctl_set_t_end(h->ctl.as<DevCtl>(), 1e300, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  // the chosen launches' own times, from one profiled step of the restored state
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kinds;
+  h->prof_ev = &ev;
+  h->prof_kind = &kinds;
+  rc = h->enqueue_step<float, 2>();
+  h->prof_ev = nullptr;
+  h->prof_kind = nullptr;
+  cudaError_t e = rc ? cudaSuccess : cudaStreamSynchronize(h->stream);
+  for (size_t i = 0; e == cudaSuccess && i + 1 < ev.size() && i / 2 < 3; i += 2) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+    h->march_us[i / 2] = ms * 1e3f;
+  }
+  for (cudaEvent_t x : ev) cudaEventDestroy(x);
+  if (!rc && e != cudaSuccess) rc = h->fail_cuda(e, "stage tuner events");
+  if (!rc) CK(restore());
+  if (!rc) CK(cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
+static int ensure_graph(amr_handle* h) {
+  if (h->graph) return AMR_OK;
+  if (!h->march_tuned)
+    if (int rc = tune_march(h)) return rc;
+  return capture_graph(h);
 }
 
 int amr_run(amr_handle* h, int nsteps, double t_end) {
@@ -1025,6 +1153,32 @@ int amr_face_ghosts(amr_handle* h, long long leaf, double* out, long long cap) {
   if (rc) return rc;
   CK(cudaMemcpyAsync(out, h->stagebuf.p, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  return AMR_OK;
+}
+
+int amr_march_tuning(amr_handle* h, int* choice, float* us) {
+  if (!h || !choice) return AMR_ERR_INVALID_ARG;
+  for (int k = 0; k < 3; ++k) {
+    choice[2 * k] = h->march_tune[k][0];
+    choice[2 * k + 1] = h->march_tune[k][1];
+    if (us) us[k] = h->march_us[k];
+  }
+  return AMR_OK;
+}
+
+int amr_set_march_tuning(amr_handle* h, const int* choice) {
+  if (!h || !choice) return AMR_ERR_INVALID_ARG;
+  for (int k = 0; k < 3; ++k) {
+    const int nw = choice[2 * k], p = choice[2 * k + 1];
+    if ((nw != 2 && nw != 4 && nw != 8) || (k == 2 && nw != 4) || (p != 0 && p != 1)) return AMR_ERR_INVALID_ARG;
+  }
+  for (int k = 0; k < 3; ++k) {
+    h->march_tune[k][0] = choice[2 * k];
+    h->march_tune[k][1] = choice[2 * k + 1];
+    h->march_us[k] = 0.f;
+  }
+  h->march_tuned = true;
+  h->drop_graph();
   return AMR_OK;
 }
 

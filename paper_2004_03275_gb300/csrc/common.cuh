@@ -91,6 +91,8 @@ struct StageArgs {
   int has_ffx;
   int limiter;
   int nleaves;
+  int march_nw;        // float32 2D 16^2 march kernel, first and middle stages: warps (leaves) per CTA
+  int march_persist;   // ... and whether a grid of resident CTAs loops over the leaf groups
 };
 
 }  // namespace amrgpu

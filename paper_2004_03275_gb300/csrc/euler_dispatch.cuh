@@ -40,19 +40,45 @@ int& stage2d_f32_grid() {
   return g;
 }
 
+// march kernel (16^2 leaves): resident CTAs x SMs per stage kind and warps per CTA (2, 4, 8)
+template <int FLUX, int LIM>
+int (&march_caps())[3][3] {
+  static int c[3][3] = {};
+  return c;
+}
+constexpr int march_nw_index(int nw) { return nw == 2 ? 0 : (nw == 4 ? 1 : 2); }
+constexpr size_t march_smem(int nw) { return (size_t)nw * sizeof(MarchSmem) + 128; }
+
+template <int FLUX, int LIM, int SK, bool P>
+cudaError_t march_prepare_kind(int sms) {
+  cudaError_t e = cudaFuncSetAttribute(stage2d_march_kernel<FLUX, LIM, SK, P>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem(kMarchMaxWarps));
+  if (!P) return e;  // one CTA per leaf group: no resident-CTA count needed
+  for (int nw : {2, 4, 8}) {
+    int per = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stage2d_march_kernel<FLUX, LIM, SK, P>, 32 * nw,
+                                                        march_smem(nw));
+    march_caps<FLUX, LIM>()[SK][march_nw_index(nw)] = sms * (per > 0 ? per : 1);
+  }
+  return e;
+}
+
 template <int B, int FLUX, int LIM>
 cudaError_t stage2d_f32_prepare_one() {
   int dev, sms, per;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if constexpr (B == 16) {  // persistent grid of the march kernel's last stage
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stage2d_march_kernel<FLUX, LIM, kStageLast>,
-                                                        32 * kMarchWarps, 0);
+  if constexpr (B == 16) {  // dynamic shared memory and resident-CTA counts of the march kernels
+    if (e == cudaSuccess) e = march_prepare_kind<FLUX, LIM, kStageFirst, false>(sms);
+    if (e == cudaSuccess) e = march_prepare_kind<FLUX, LIM, kStageFirst, true>(sms);
+    if (e == cudaSuccess) e = march_prepare_kind<FLUX, LIM, kStageMid, false>(sms);
+    if (e == cudaSuccess) e = march_prepare_kind<FLUX, LIM, kStageMid, true>(sms);
+    if (e == cudaSuccess) e = march_prepare_kind<FLUX, LIM, kStageLast, true>(sms);
   } else if (e == cudaSuccess) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stage2d_f32_kernel<B, FLUX, LIM>, 256, 0);
+    if (e == cudaSuccess) stage2d_f32_grid<B, FLUX, LIM>() = sms * (per > 0 ? per : 1);
   }
-  if (e == cudaSuccess) stage2d_f32_grid<B, FLUX, LIM>() = sms * (per > 0 ? per : 1);
   return e;
 }
 
@@ -71,16 +97,23 @@ cudaError_t stage2d_f32_prepare(int lim) {
 template <int B, int FLUX, int LIM>
 void stage2d_f32_go(const StageArgs<float>& a, const Geometry& G, cudaStream_t s) {
   if constexpr (B == 16) {
-    int grid = (a.nleaves + kMarchWarps - 1) / kMarchWarps;
-    int cap = stage2d_f32_grid<B, FLUX, LIM>();
+    const int kind = a.fuse_reduce ? kStageLast : (a.stage1 ? kStageFirst : kStageMid);
+    const int nw = kind == kStageLast ? kMarchWarps : (a.march_nw == 2 || a.march_nw == 8 ? a.march_nw : 4);
+    const bool persist = a.march_persist > 0;
+    const int ngroups = (a.nleaves + nw - 1) / nw;
+    const int cap = march_caps<FLUX, LIM>()[kind][march_nw_index(nw)];
+    const int grid = persist && cap > 0 && cap < ngroups ? cap : ngroups;
     const CUtensorMap& tm = *static_cast<const CUtensorMap*>(a.tmap_us);
-    if (a.fuse_reduce)
-      stage2d_march_kernel<FLUX, LIM, kStageLast>
-          <<<cap > 0 && cap < grid ? cap : grid, 32 * kMarchWarps, 0, s>>>(a, G, tm);
-    else if (a.stage1)
-      stage2d_march_kernel<FLUX, LIM, kStageFirst><<<grid, 32 * kMarchWarps, 0, s>>>(a, G, tm);
+    if (kind == kStageLast)
+      stage2d_march_kernel<FLUX, LIM, kStageLast, true><<<grid, 32 * nw, march_smem(nw), s>>>(a, G, tm);
+    else if (kind == kStageFirst && persist)
+      stage2d_march_kernel<FLUX, LIM, kStageFirst, true><<<grid, 32 * nw, march_smem(nw), s>>>(a, G, tm);
+    else if (kind == kStageFirst)
+      stage2d_march_kernel<FLUX, LIM, kStageFirst, false><<<grid, 32 * nw, march_smem(nw), s>>>(a, G, tm);
+    else if (persist)
+      stage2d_march_kernel<FLUX, LIM, kStageMid, true><<<grid, 32 * nw, march_smem(nw), s>>>(a, G, tm);
     else
-      stage2d_march_kernel<FLUX, LIM, kStageMid><<<grid, 32 * kMarchWarps, 0, s>>>(a, G, tm);
+      stage2d_march_kernel<FLUX, LIM, kStageMid, false><<<grid, 32 * nw, march_smem(nw), s>>>(a, G, tm);
     return;
   }
   constexpr int LPB = 256 / (B * B);

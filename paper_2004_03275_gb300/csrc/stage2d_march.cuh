@@ -32,7 +32,8 @@
 
 namespace amrgpu {
 
-constexpr int kMarchWarps = 4;  // warps (= leaves) per CTA
+constexpr int kMarchWarps = 4;     // warps (= leaves) per CTA of the last stage (its reduction's thread count)
+constexpr int kMarchMaxWarps = 8;  // largest CTA of the first and middle stages (launch parameter)
 
 struct MarchSmem {
   float4 E[16][17];  // x flux differences of the interior cells, E[j][i]; before the x march it
@@ -134,8 +135,14 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float h2, float l2)
 // SK: stage kind, fixed at compile time so every kernel carries only its own path
 enum { kStageFirst = 0, kStageMid = 1, kStageLast = 2 };
 
-template <int FLUX, int LIM, int SK>
-__global__ void __launch_bounds__(32 * kMarchWarps, 4)
+// Launch: block 32 x NW threads (NW warps = leaves per CTA; the last stage takes
+// kMarchWarps), dynamic shared memory NW x sizeof(MarchSmem) + 128 bytes of alignment
+// slack; grid = leaf groups, or fewer CTAs that loop over the groups (persistent).  Every
+// choice gives the same state bit for bit (the per-cell arithmetic does not depend on it).
+// PERSIST: CTAs loop over the leaf groups (the last stage always does; its grid may still
+// cover every group); without it each CTA takes one group and the kernel has no loop.
+template <int FLUX, int LIM, int SK, bool PERSIST>
+__global__ void __launch_bounds__(32 * kMarchMaxWarps, 2)
     stage2d_march_kernel(const __grid_constant__ StageArgs<float> a, const __grid_constant__ Geometry G,
                          const __grid_constant__ CUtensorMap tmU) {
   constexpr int B = 16, NC = B * B, NV = 4;
@@ -145,10 +152,13 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4)
   // copy measured ~1 us faster per launch in the former and ~3.5 us slower in the latter
   // (one 4 KB copy per warp against 256 requests in flight).
   constexpr bool TMA = LAST;
-  __shared__ __align__(128) MarchSmem S[kMarchWarps];
-  __shared__ uint64_t tbar[kMarchWarps];
-  __shared__ float wrate[kMarchWarps];
+  extern __shared__ __align__(128) unsigned char march_smem_raw[];
+  MarchSmem* S = reinterpret_cast<MarchSmem*>(march_smem_raw +
+                                              ((128u - (tma::smem_addr(march_smem_raw) & 127u)) & 127u));
+  __shared__ uint64_t tbar[kMarchMaxWarps];
+  __shared__ float wrate[kMarchMaxWarps];
   __shared__ int sbad;
+  const int NW = LAST ? kMarchWarps : (int)(blockDim.x >> 5);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lo16 = lane & 15, h = lane >> 4;
   MarchSmem& M = S[warp];
@@ -157,13 +167,12 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4)
   __syncwarp();
   unsigned phase = 0;
 
-  // Leaf groups (kMarchWarps consecutive leaves, one per warp): the first and
-  // middle stages take one group per CTA; the last stage is persistent, CTA b
-  // taking groups b, b + gridDim.x, ... in that order, so that the per-thread
-  // totals are summed in a fixed order and the finish runs once per CTA.
-  const int ngroups = (a.nleaves + kMarchWarps - 1) / kMarchWarps;
+  // Leaf groups (NW consecutive leaves, one per warp): CTA b takes groups b, b + gridDim.x,
+  // ... in that order (one group when the grid covers them all).  On the last stage the
+  // per-thread totals are so summed in a fixed order and the finish runs once per CTA.
+  const int ngroups = (a.nleaves + NW - 1) / NW;
   int grp = blockIdx.x;
-  int leaf = grp * kMarchWarps + warp;
+  int leaf = grp * NW + warp;
   bool active = leaf < a.nleaves;
   float gu[4][NV];
   float4 u[NV][2];
@@ -212,8 +221,8 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4)
     // line per lane), so that those loads find it there instead of in DRAM
     if (!FIRST) march::prefetch_l2(a.U0 + (size_t)leaf * NV * NC + lane * 32);
     // persistent last stage: the next group's leaf too, whose copy is issued only after this one
-    if (LAST) {
-      const int nl = (grp + (int)gridDim.x) * kMarchWarps + warp;
+    if (LAST || PERSIST) {
+      const int nl = (grp + (int)gridDim.x) * NW + warp;
       if (nl < a.nleaves) march::prefetch_l2(a.Us + (size_t)nl * NV * NC + lane * 32);
     }
   };
@@ -420,15 +429,16 @@ __global__ void __launch_bounds__(32 * kMarchWarps, 4)
         }
       }
     }
-    if constexpr (!LAST) return;
+    if constexpr (!LAST && !PERSIST) return;
     grp += gridDim.x;
     if (grp >= ngroups) break;
-    leaf = grp * kMarchWarps + warp;
+    leaf = grp * NW + warp;
     active = leaf < a.nleaves;
     __syncwarp();  // every lane of this warp is done with its tile and E before the next leaf
     if (active) load_leaf();
   }
 
+  if constexpr (!LAST) return;
   // ---- last stage: CTA max rate, CTA totals (fixed order), two-level finish
   for (int o = 16; o > 0; o >>= 1) rate = fmaxf(rate, __shfl_xor_sync(0xffffffffu, rate, o));
   if (lane == 0) wrate[warp] = rate;

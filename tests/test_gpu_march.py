@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from paper_2004_03275_gb300 import amrvac
+from paper_2004_03275_gb300 import amrvac, inputs
 from gpu_util import centres_for
 from treeutil import random_balanced_tree
 
@@ -99,3 +99,39 @@ def test_fp32_uniform_state_is_kept_exactly(ndim, bnx, base, rk):
     s.sync()
     U1 = s.read_state()
     assert np.array_equal(U0, U1), float(np.max(np.abs(U1 - U0)))
+
+
+def test_stage_tuner_candidates_give_identical_states():
+    """Every launch shape the stage-kernel tuner may pick (warps per CTA 2/4/8, grid or persistent,
+    per stage kind) advances the state to the same bits; the tuner's own pick is one of them and
+    reports a time per stage kind."""
+    n = 256
+    kw = dict(ndim=2, block_nx=16, base=[n // 16, n // 16], gamma=1.4, cfl=0.8, flux="hllc", limiter="vanleer",
+              rk=3, bc="periodic")
+    s0 = amrvac.AmrSolver(precision="fp32", **kw)
+    lev, crd = s0.leaves()
+    x, gi = inputs.cell_centres(lev, crd, 2, 16, kw["base"] + [1], [0, 0, 0], [1, 1, 1])
+    V = inputs.kelvin_helmholtz(x, gi, n, seed=2004)
+    choices = [[(4, 0), (4, 0), (4, 1)], [(2, 0), (8, 1), (4, 0)], [(8, 0), (2, 1), (4, 1)],
+               [(2, 1), (4, 1), (4, 0)], [(8, 1), (8, 0), (4, 1)]]
+    states = []
+    for ch in choices:
+        s = amrvac.AmrSolver(precision="fp32", **kw)
+        s.set_prim(V)
+        s.set_march_tuning(ch)
+        s.run(5)
+        s.sync()
+        assert s.march_tuning()[0] == [tuple(c) for c in ch]
+        states.append(s.read_state())
+        s.close()
+    for st in states[1:]:
+        assert np.array_equal(st, states[0])
+    s0.set_prim(V)
+    s0.run(5)
+    s0.sync()
+    pick, us = s0.march_tuning()
+    assert pick[2][0] == 4 and all(nw in (2, 4, 8) and p in (0, 1) for nw, p in pick)
+    assert all(u > 0 for u in us)
+    assert np.array_equal(s0.read_state(), states[0])
+    with pytest.raises(amrvac.AmrError):
+        s0.set_march_tuning([(3, 0), (4, 0), (4, 1)])
