@@ -49,6 +49,65 @@ def kh_state(lev, crd, nside=NSIDE, seed=2004):
     return inputs.kelvin_helmholtz(x, gi, nside, seed=seed)
 
 
+# Config 3 at a size the oracle finishes in seconds: base 2^3 blocks of 16^3, 3 levels (effective
+# 128^3), 100 SSPRK3 steps with a regrid after every 10
+BLAST128_BASE = [2, 2, 2]
+BLAST128_KW = dict(ndim=3, block_nx=16, base=BLAST128_BASE, max_level=3, gamma=5.0 / 3.0, cfl=0.8, flux="hllc",
+                   limiter="koren", rk=3, bc="periodic", refine_tol=0.2, coarsen_frac=0.5, var_mask=1 | 16)
+BLAST128_STEPS, BLAST128_REGRID = 100, 10
+
+
+def blast_initial_refinement(g, base, max_level, seed=7):
+    """Sample the blast on the tree, regrid, repeat (max_level passes): the same sequence for the
+    oracle grid and the GPU solver."""
+    from paper_2004_03275_gb300 import inputs
+    for it in range(max_level):
+        lev, crd = g.leaves()
+        x, _ = inputs.cell_centres(lev, crd, 3, 16, base, [0, 0, 0], [1, 1, 1])
+        g.set_prim(inputs.blast(x, seed=seed))
+        if it < max_level - 1:
+            g.regrid()
+
+
+def fp32_accuracy_vs_oracle(amrvac, stream, ref):
+    """Normalised L1(rho) of the float32 GPU path against the FP64 oracle states kept by the CPU
+    baseline: the blast (effective 128^3, 100 steps with regrids; both runs regrid at the oracle's
+    regrid times, both states projected to uniform 128^3) and KH 512^2 after 100 steps."""
+    from paper_2004_03275_gb300 import analysis
+    s = amrvac.AmrSolver(**BLAST128_KW, precision="fp32", stream=stream.cuda_stream)
+    blast_initial_refinement(s, BLAST128_BASE, 3)
+    nblk = len(ref["blast_marks"])
+    for blk, t_mark in enumerate(ref["blast_marks"]):
+        for _ in range(4):  # to the oracle's time (float32 dt may differ in the last digits)
+            if s.t >= t_mark:
+                break
+            s.run(BLAST128_REGRID, t_end=t_mark)
+            s.sync()
+        if blk < nblk - 1:
+            s.regrid()
+    lev, crd = s.leaves()
+    rho = analysis.project_uniform(lev, crd, s.read_state()[:, 0], 3, 16, BLAST128_BASE, 3)
+    out = {"blast_128": {"l1_rho": analysis.l1_relative(rho, ref["blast_rho"]), "t": s.t,
+                         "leaves": int(len(lev)),
+                         "definition": "sum|rho32 - rho_oracle| / sum|rho_oracle| on uniform 128^3 after "
+                                       f"{BLAST128_STEPS} steps, regrid every {BLAST128_REGRID}; both states "
+                                       "projected (coarser leaves replicated)"}}
+    s.close()
+    kw = kh_kwargs(512, "fp32", stream.cuda_stream)
+    s = amrvac.AmrSolver(**kw)
+    lev, crd = s.leaves()
+    s.set_prim(kh_state(lev, crd, 512))
+    for _ in range(4):
+        if s.t >= ref["kh512_t"]:
+            break
+        s.run(100, t_end=ref["kh512_t"])
+        s.sync()
+    out["kh_512"] = {"l1_rho": analysis.l1_relative(s.read_state()[:, 0], ref["kh512_rho"]), "t": s.t,
+                     "definition": "sum|rho32 - rho_oracle| / sum|rho_oracle| after 100 steps (oracle's time)"}
+    s.close()
+    return out
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -329,7 +388,19 @@ def bench_mg_vcycle(torch, amrvac, stream, hbm_gbs):
             el = time.perf_counter() - t0
             best = el if best is None else min(best, el)
         res[rtol] = (best, int(np.max(cyc)))
+        if rtol == 1e-12:  # one V-cycle kernel by kernel (CUDA events between launches), 5 times
+            with torch.cuda.nvtx.range("mg_profile_vcycle"):
+                prof = [s.profile_vcycle() for _ in range(6)][1:]
         s.close()
+    kinds = {}
+    for p in prof:
+        for k, us in p:
+            kinds.setdefault(k, [0, 0.0])
+            kinds[k][0] += 1
+            kinds[k][1] += us / len(prof)
+    tot = sum(v[1] for v in kinds.values())
+    # the first launch is depth 0's first pre-sweep over every instance: 12 B per unknown
+    sweep0 = float(np.mean([p[0][1] for p in prof]))
     (t_lo, c_lo), (t_hi, c_hi) = res[1e-3], res[1e-12]
     tv = (t_hi - t_lo) / max(1, c_hi - c_lo)
     gbs = MG_BYTES_PER_UNKNOWN_VCYCLE * n / tv / 1e9
@@ -339,7 +410,16 @@ def bench_mg_vcycle(torch, amrvac, stream, hbm_gbs):
             "roofline": {"bound": "hbm", "bytes_per_unknown": MG_BYTES_PER_UNKNOWN_VCYCLE,
                          "achieved": round(gbs, 1), "peak": hbm_gbs, "unit": "GB/s", "frac": round(gbs / hbm_gbs, 4)},
             "timing": "host wall clock around synchronous solves (includes the per-cycle residual check and "
-                      "host poll), best of 5, difference of two tolerances"}
+                      "host poll), best of 5, difference of two tolerances",
+            "kernels_of_one_vcycle": {"us_by_kind": {k: round(v[1], 1) for k, v in kinds.items()},
+                                      "launches_by_kind": {k: v[0] // len(prof) for k, v in kinds.items()},
+                                      "sum_us": round(tot, 1),
+                                      "depth0_sweep_us": round(sweep0, 1),
+                                      "sequence_us": [[k, round(float(np.mean([p[i][1] for p in prof])), 1)]
+                                                      for i, (k, _) in enumerate(prof[0])],
+                                      "depth0_sweep_gbs": round(12.0 * n / (sweep0 * 1e-6) / 1e9, 1),
+                                      "timing": "mg_profile_vcycle: kernels launched one by one with CUDA events "
+                                                "between them (not graph-replayed), mean of 5 cycles"}}
 
 
 def bench_schnakenberg(torch, amrvac, stream):
@@ -498,12 +578,7 @@ def bench_blast(torch, amrvac, stream, hbm_gbs, steps=20, regrid_every=10):
               limiter="koren", rk=3, bc="periodic", refine_tol=0.2, coarsen_frac=0.5, var_mask=1 | 16,
               precision="fp32", max_blocks=20000, stream=stream.cuda_stream)
     s = amrvac.AmrSolver(**kw)
-    for it in range(4):  # sample the initial condition on the tree, refine, repeat
-        lev, crd = s.leaves()
-        x, _ = inputs.cell_centres(lev, crd, 3, 16, [4, 4, 4], [0, 0, 0], [1, 1, 1])
-        s.set_prim(inputs.blast(x, seed=7))
-        if it < 3:
-            s.regrid()
+    blast_initial_refinement(s, [4, 4, 4], 4)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step_ms, cells_steps, t_regrid, levels = 0.0, 0, 0.0, []
     done = 0
@@ -584,7 +659,8 @@ def _oracle_kh_rate(O, side, budget_s):
 def oracle_cpu_baseline(budget_s=8.0):
     """The FP64 oracle as it stands on the host cores: KH on one thread and on all cores (its
     OpenMP loops over blocks give the one-thread result bit for bit), plus bounded samples of
-    the batched multigrid V-cycle and of the 3D blast tree on all cores."""
+    the batched multigrid V-cycle and of the 3D blast tree on all cores.  Returns the report and
+    the oracle states (blast and KH 512^2) that the float32 accuracy figures are taken against."""
     import oracle as O
     nproc = os.cpu_count() or 1
     O.set_threads(1)
@@ -612,28 +688,38 @@ def oracle_cpu_baseline(budget_s=8.0):
         mg[f"threads_{th}"] = {"value": n * n * k / el, "unit": "unknown-V-cycles/s", "vcycles": k,
                                "seconds": round(el, 2)}
     out["mg_vcycle"] = dict(mg, sample="FP64 V-cycles (2 + 2 red-black sweeps) on one periodic 1024^2 grid")
-    # blast: base 2^3 blocks of 16^3, 3 levels, initial refinement, then steps on all cores
-    from paper_2004_03275_gb300 import inputs
-    kw = dict(ndim=3, block_nx=16, base=[2, 2, 2], max_level=3, gamma=5.0 / 3.0, cfl=0.8, flux="hllc",
-              limiter="koren", rk=3, bc="periodic", refine_tol=0.2, coarsen_frac=0.5, var_mask=1 | 16)
-    g = O.Grid(**kw)
-    for it in range(3):
-        lev, crd = g.leaves()
-        x, _ = inputs.cell_centres(lev, crd, 3, 16, [2, 2, 2], [0, 0, 0], [1, 1, 1])
-        g.set_prim(inputs.blast(x, seed=7))
-        if it < 2:
+    # blast: base 2^3 blocks of 16^3, 3 levels (effective 128^3), initial refinement, then 100
+    # SSPRK3 steps with a regrid after every 10 (regrids not timed), all cores.  The final state
+    # and the regrid times are kept for the float32 GPU run of the same configuration.
+    from paper_2004_03275_gb300 import analysis
+    g = O.Grid(**BLAST128_KW)
+    blast_initial_refinement(g, BLAST128_BASE, 3)
+    el, cell_stages, marks, leaves = 0.0, 0, [], []
+    for blk in range(BLAST128_STEPS // BLAST128_REGRID):
+        leaves.append(g.nleaves)
+        t0 = time.perf_counter()
+        k = g.run(BLAST128_REGRID)
+        el += time.perf_counter() - t0
+        cell_stages += g.nleaves * 16 ** 3 * 3 * k
+        marks.append(g.t)
+        if blk < BLAST128_STEPS // BLAST128_REGRID - 1:
             g.regrid()
-    cells = g.nleaves * 16 ** 3
-    t0 = time.perf_counter()
-    k = 0
-    while k < 1 or time.perf_counter() - t0 < budget_s / 2:
-        g.step()
-        k += 1
-    el = time.perf_counter() - t0
-    out["blast3d"] = {"value": cells * 3 * k / el, "unit": UNIT, "cores": nproc, "leaves": g.nleaves,
-                      "sample": f"blast, 2^3 base blocks of 16^3, 3 levels ({g.nleaves} leaves), {k} SSPRK3 steps, "
-                                f"{nproc} threads, {el:.1f} s"}
-    return out
+    lev, crd = g.leaves()
+    rho = analysis.project_uniform(lev, crd, g.get_cons()[:, 0], 3, 16, BLAST128_BASE, 3)
+    out["blast3d"] = {"value": cell_stages / el, "unit": UNIT, "cores": nproc, "leaves_per_block_of_10_steps": leaves,
+                      "sample": f"blast, 2^3 base blocks of 16^3, 3 levels (effective 128^3), {BLAST128_STEPS} SSPRK3 "
+                                f"steps with a regrid every {BLAST128_REGRID} (not timed), {nproc} threads, "
+                                f"{el:.1f} s", "t_end": g.t}
+    # KH 512^2, 100 steps, all cores: the reference state of the float32 accuracy figure
+    kw = kh_kwargs(512)
+    kw.pop("precision")
+    kw.pop("stream")
+    gk = O.Grid(**kw)
+    lev, crd = gk.leaves()
+    gk.set_prim(kh_state(lev, crd, 512))
+    gk.run(100)
+    return out, {"blast_marks": marks, "blast_rho": rho, "kh512_t": gk.t, "kh512_rho": gk.get_cons()[:, 0].copy(),
+                 "kh512_leaves": (lev, crd)}
 
 
 def run_reference(args, ws, rank):
@@ -817,15 +903,21 @@ def main():
                 "schnakenberg": lambda: bench_schnakenberg(torch, amrvac, stream),
                 "gray_scott_tree": lambda: bench_gray_scott_tree(torch, amrvac, stream)}
         for name in want:
-            # an extra workload that fails is reported as such; the headline line still prints
+            # an extra workload that fails is reported as such; the headline line still prints;
+            # each runs inside an NVTX range of its name (a profiler can select one by it)
             try:
-                extra[name] = runs[name]()
+                with torch.cuda.nvtx.range(name):
+                    extra[name] = runs[name]()
             except Exception as e:  # noqa: BLE001
                 extra[name] = {"error": f"{type(e).__name__}: {e}"[:500]}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
-        cpu = oracle_cpu_baseline()
+        cpu, ref = oracle_cpu_baseline()
+        try:
+            cpu["fp32_accuracy_vs_oracle"] = fp32_accuracy_vs_oracle(amrvac, stream, ref)
+        except Exception as e:  # noqa: BLE001
+            cpu["fp32_accuracy_vs_oracle"] = {"error": f"{type(e).__name__}: {e}"[:500]}
 
     if rank == 0:
         line = {

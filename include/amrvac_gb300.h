@@ -271,6 +271,16 @@ int mg_solve(mg_handle* h, const double* b, double* x, int on_device, int* cycle
 int mg_num_unknowns(const mg_handle* h, long long* n);
 /* kernels this handle has launched so far (graph nodes included) */
 int mg_kernel_launches(const mg_handle* h, long long* n);
+/* One more V-cycle (Sec. 1.4; the correction of the current defect, as one loop iteration
+ * of mg_solve, which must have run before) over every instance, converged or not, its
+ * kernels launched one by one with a CUDA event
+ * after each: kind[i] and us[i] = microseconds between consecutive events for kernel i, for
+ * up to cap kernels; *nkernels = kernels of the cycle.  Kinds: 0 2D red-black sweep, 1 copy,
+ * 2 3D half sweep, 3 residual + restriction, 4 coarsest solve, 5 prolongation, 6 float32
+ * update (X += e, R -= A e), 7 zero correction, 8 float64 correction, 9 float64 defect.
+ * The iterate advances by that cycle.  Synchronous; for measurement only.
+ * AMR_ERR_INVALID_ARG before the first mg_solve. */
+int mg_profile_vcycle(mg_handle* h, int* kind, float* us, int cap, int* nkernels);
 /* 2D: the strip height of the red-black sweep used for levels of side `side`, chosen by
  * the autotuner at mg_create: per depth of the batch, the sweep of all instances' levels
  * of that depth is timed with each candidate height (4..64, or the side-based default

@@ -141,6 +141,7 @@ _SIGS = {
     "rd_extract_crops": ([_vp, C.c_int, _ip, _ip, C.c_int, C.c_double, _vp, _vp], C.c_int),
     "mg_kernel_launches": ([_vp, _llp], C.c_int),
     "mg_strip_height": ([_vp, C.c_int, _ip], C.c_int),
+    "mg_profile_vcycle": ([_vp, _ip, C.POINTER(C.c_float), C.c_int, _ip], C.c_int),
     "rd_kernel_launches": ([_vp, _llp], C.c_int),
     "mgt_create": ([C.POINTER(MgtConfig), C.c_int, _ip, _ip, C.POINTER(_vp)], C.c_int),
     "mgt_destroy": ([_vp], C.c_int),
@@ -548,6 +549,19 @@ class MgSolver:
             e.cycles, e.relres = cyc, rr
             raise e
         return cyc, rr
+
+    MG_KINDS = ("sweep", "copy", "smooth3d", "resrestrict", "coarse", "prolong", "update", "zero", "correct64",
+                "residual64")
+
+    def profile_vcycle(self, cap=4096):
+        """One more V-cycle (after a solve), kernel by kernel: [(kind name, microseconds)]."""
+        kind = np.zeros(cap, dtype=np.int32)
+        us = np.zeros(cap, dtype=np.float32)
+        n = C.c_int()
+        _check(self.lib.mg_profile_vcycle(self.h, kind.ctypes.data_as(_ip), us.ctypes.data_as(C.POINTER(C.c_float)),
+                                          cap, C.byref(n)), self.h, "mg_last_error")
+        m = min(n.value, cap)
+        return [(self.MG_KINDS[k], float(t)) for k, t in zip(kind[:m], us[:m])]
 
 
 class RdSolver:

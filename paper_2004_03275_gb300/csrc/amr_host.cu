@@ -137,8 +137,7 @@ struct Tree {
 struct Tables {
   std::vector<int> nb, kind, nbr, ffx;
   std::vector<SlabDesc> slabs;
-  std::vector<RefluxRec> rec;  // sorted by face dimension
-  int rec_off[4] = {0, 0, 0, 0};
+  std::vector<RefluxRec> rec;  // grouped by coarse leaf, faces ascending within a group
   int nslots = 0;
 };
 
@@ -225,15 +224,14 @@ bool build_tables(const Tree& T, Tables& tb, std::string* err) {
       tb.nbr[o] = D.src[0];
     }
   }
-  // A coarse cell at a leaf corner may border level jumps in several directions:
-  // corrections are applied one direction per launch so that no two threads of a
-  // launch update the same cell, in the fixed order x, y, z.
-  std::stable_sort(tb.rec.begin(), tb.rec.end(),
-                   [](const RefluxRec& a, const RefluxRec& b) { return (a.face >> 1) < (b.face >> 1); });
-  for (int d = 0; d <= 3; ++d) {
-    tb.rec_off[d] = 0;
-    for (const RefluxRec& r : tb.rec)
-      if ((r.face >> 1) < d) ++tb.rec_off[d];
+  // A coarse cell at a leaf edge or corner may border level jumps in several
+  // directions: the records of one coarse leaf form a group (built leaf by leaf,
+  // faces ascending) whose corrections a cell receives in that order, x then y then z.
+  for (size_t k = 0; k < tb.rec.size();) {
+    size_t e = k;
+    while (e < tb.rec.size() && tb.rec[e].coarse == tb.rec[k].coarse) ++e;
+    for (size_t j = k; j < e; ++j) tb.rec[j].first = (int)k, tb.rec[j].last = (int)e;
+    k = e;
   }
   return true;
 }
@@ -280,7 +278,8 @@ struct amr_handle {
   Tables tb;
   Geometry G{};
   // device state
-  DBuf U0, Ua, Ub, Unew, stagebuf, partials, gpart, gcount, ctl, nb, level, ffx, slabdesc, slabbuf, rec, fflux, ops, errbuf;
+  DBuf U0, Ua, Ub, Unew, stagebuf, partials, gpart, gcount, ctl, nb, level, ffx, slabdesc, slabbuf, rec, fflux, ops,
+      errbuf;
   DBuf xyscr;  // float32 3D 16^3: x + y flux differences of the stage (like the state)
   // float32 2D 16^2: TMA tensor maps of the three state buffers viewed as [leaf*4 + var][256]
   CUtensorMap tmaps[3];
@@ -397,12 +396,10 @@ struct amr_handle {
       int rc = dispatch_stage<real, ND>(a);
       if (rc) return rc;
       if (jumps) {
-        for (int d = 0; d < ND; ++d) {
-          int r0 = tb.rec_off[d], nr = tb.rec_off[d + 1] - r0;
-          if (nr == 0) continue;
+        if (!tb.rec.empty()) {
           mark_begin();
-          CK((EulerOps<real, ND>::reflux(B, out, fflux.as<real>(), rec.as<RefluxRec>() + r0, nr, level.as<int>(),
-                                         G, ctl.as<DevCtl>(), beta, stream)));
+          CK((EulerOps<real, ND>::reflux(B, out, fflux.as<real>(), rec.as<RefluxRec>(), (int)tb.rec.size(),
+                                         level.as<int>(), G, ctl.as<DevCtl>(), beta, stream)));
           ++launches;
           mark(2);
         }

@@ -38,6 +38,8 @@ struct RefluxRec {
   int face;     // its face
   int cslot;    // face-flux slot written by the coarse leaf
   int fslot[4]; // face-flux slots of the fine leaves per tangential quadrant
+  int first;    // the records of the same coarse leaf: [first, last), faces ascending
+  int last;
 };
 
 // New leaf after a regrid.

@@ -53,13 +53,14 @@ template <int FLUX, int LIM, int SK, bool P>
 cudaError_t march_prepare_kind(int sms) {
   cudaError_t e = cudaFuncSetAttribute(stage2d_march_kernel<FLUX, LIM, SK, P>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem(kMarchMaxWarps));
-  if (!P) return e;  // one CTA per leaf group: no resident-CTA count needed
-  for (int nw : {2, 4, 8}) {
-    int per = 0;
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stage2d_march_kernel<FLUX, LIM, SK, P>, 32 * nw,
-                                                        march_smem(nw));
-    march_caps<FLUX, LIM>()[SK][march_nw_index(nw)] = sms * (per > 0 ? per : 1);
+  if constexpr (P) {  // resident-CTA counts (one CTA per leaf group otherwise: none needed)
+    for (int nw : {2, 4, 8}) {
+      int per = 0;
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stage2d_march_kernel<FLUX, LIM, SK, P>, 32 * nw,
+                                                          march_smem(nw));
+      march_caps<FLUX, LIM>()[SK][march_nw_index(nw)] = sms * (per > 0 ? per : 1);
+    }
   }
   return e;
 }
@@ -275,8 +276,12 @@ cudaError_t EulerOps<real, ND>::reduce(int B, const real* U, const int* level, c
   ([&]() {                                                                                         \
     constexpr int NC = Tile<ND, BB>::NC;                                                           \
     constexpr int LPB = ReduceShape<NC>::LPB;                                                      \
-    reduce_kernel<real, ND, BB><<<(nleaves + LPB - 1) / LPB, 256, 0, s>>>(U, level, G, ctl, partials, \
-                                                                         gpart, gcount, nleaves, advance); \
+    if constexpr (sizeof(real) == 4 && NC % 1024 == 0)                                             \
+      reduce_split_kernel<ND, BB><<<nleaves * (NC / 1024), 256, 0, s>>>(                           \
+          reinterpret_cast<const float*>(U), level, G, ctl, partials, gpart, gcount, nleaves, advance); \
+    else                                                                                           \
+      reduce_kernel<real, ND, BB><<<(nleaves + LPB - 1) / LPB, 256, 0, s>>>(U, level, G, ctl, partials, \
+                                                                           gpart, gcount, nleaves, advance); \
     return cudaGetLastError();                                                                     \
   }())
   return AMRGPU_BSWITCH(B, CALL);
@@ -289,8 +294,7 @@ cudaError_t EulerOps<real, ND>::ghost_fill(int B, const real* U, real* slabs, co
   if (nslabs == 0) return cudaSuccess;
 #define CALL(BB)                                                                                  \
   ([&]() {                                                                                        \
-    long long n = (long long)nslabs * 2 * Tile<ND, BB>::NT;                                       \
-    ghost_fill_kernel<real, ND, BB><<<detail::blocks_for(n, 256), 256, 0, s>>>(U, slabs, desc, nslabs); \
+    ghost_fill_kernel<real, ND, BB><<<nslabs, GhostShape<ND, BB>::THREADS, 0, s>>>(U, slabs, desc, nslabs); \
     return cudaGetLastError();                                                                    \
   }())
   return AMRGPU_BSWITCH(B, CALL);

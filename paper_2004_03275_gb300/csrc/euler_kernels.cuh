@@ -609,7 +609,7 @@ struct Stage3DSmem {
 
 template <typename real, int B, int FLUX>
 __global__ void __launch_bounds__(256) stage_kernel_3d(StageArgs<real> a, Geometry G) {
-  constexpr int ND = 3, NV = 5, NC = B * B * B, NT = B * B, P = B + 4, COLS = B * B;
+  constexpr int NV = 5, NC = B * B * B, NT = B * B, P = B + 4, COLS = B * B;
   constexpr int LPB = 256 / COLS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Stage3DSmem<real, B>& S = *reinterpret_cast<Stage3DSmem<real, B>*>(smem_raw);
@@ -800,6 +800,13 @@ __device__ __forceinline__ void twosum_acc(float& hi, float& lo, float x) {
   hi = s;
 }
 
+// (hi, lo) += (h2, l2) for float-float accumulators (TwoSum of the high parts)
+__device__ __forceinline__ void ff_acc(float& hi, float& lo, float h2, float l2) {
+  const float s = hi + h2, bb = s - hi;
+  lo = lo + l2 + ((hi - (s - bb)) + (h2 - bb));
+  hi = s;
+}
+
 template <typename real, int ND, int B>
 __global__ void __launch_bounds__(256) reduce_kernel(const real* __restrict__ U, const int* __restrict__ level,
                                                      Geometry G, DevCtl* ctl, double* partials, double* gpart,
@@ -825,15 +832,25 @@ __global__ void __launch_bounds__(256) reduce_kernel(const real* __restrict__ U,
     float hi[NV], lo[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) hi[v] = lo[v] = 0.f;
-    for (int c = tc; c < NC; c += TPL) {
-      real Uc[NV];
+    // cells tc, tc + TPL, ... in that order; the loads of RB consecutive cells of the thread are
+    // issued together so that a thread keeps RB x NV loads in flight
+    constexpr int CPT = NC / TPL, RB = CPT % 4 == 0 && sizeof(real) == 4 ? 4 : (CPT % 2 == 0 ? 2 : 1);
+    static_assert(NC % (RB * TPL) == 0, "cells per thread split into whole batches");
+    const real* Ul = U + (size_t)leaf * NV * NC;
+    for (int c0 = tc; c0 < NC; c0 += RB * TPL) {
+      real Ub[RB][NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Uc[v] = U[((size_t)leaf * NV + v) * NC + c];
-      rate = fmax(rate, cell_rate<real, ND>(Uc, gam, gm1, dx, &bad));
+      for (int k = 0; k < RB; ++k)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        if constexpr (sizeof(real) == 4) twosum_acc(hi[v], lo[v], Uc[v]);
-        else sums[v] += (double)Uc[v];
+        for (int v = 0; v < NV; ++v) Ub[k][v] = Ul[(size_t)v * NC + c0 + k * TPL];
+#pragma unroll
+      for (int k = 0; k < RB; ++k) {
+        rate = fmax(rate, cell_rate<real, ND>(Ub[k], gam, gm1, dx, &bad));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          if constexpr (sizeof(real) == 4) twosum_acc(hi[v], lo[v], Ub[k][v]);
+          else sums[v] += (double)Ub[k][v];
+        }
       }
     }
 #pragma unroll
@@ -846,139 +863,319 @@ __global__ void __launch_bounds__(256) reduce_kernel(const real* __restrict__ U,
                                      nleaves, advance != 0, dt, bad);
 }
 
-// ====================================================== ghost slab fill ==
-// One thread per (slab, var, layer, tangential cell).  Restriction: mean of the
-// 2^ndim fine cells (x-fastest sum).  Prolongation: q_p + 1/4 sum_e sigma_e s_e,
-// minmod slopes; normal inner neighbour = restriction of the target leaf;
-// tangential neighbours outside the coarse leaf give s_e = 0.
-template <typename real, int ND, int B>
-__global__ void ghost_fill_kernel(const real* __restrict__ U, real* __restrict__ slabs,
-                                  const SlabDesc* __restrict__ desc, int nslabs) {
-  constexpr int NV = ND + 2, NC = Tile<ND, B>::NC, NT = Tile<ND, B>::NT;
-  // 2 NT threads per slab.  Restriction slabs: one thread per (layer, tangential cell), the
-  // variables unrolled so that their loads are in flight together.  Prolongation slabs: one
-  // thread per (coarse face cell, variable), each writing the 2 layers x 2^(ND-1) fine ghost
-  // cells that share its coarse value, inner restriction and slopes.
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= nslabs * 2 * NT) return;
-  const int q = gid % (2 * NT);
-  const int s = gid / (2 * NT);
-  SlabDesc D = desc[s];
-  int d = D.face >> 1, side = D.face & 1;
-  int e1 = -1, e2 = -1;
-  for (int e = 0; e < ND; ++e)
-    if (e != d) {
-      if (e1 < 0) e1 = e; else e2 = e;
+// Float32 reduction for leaves of >= 1024 cells: NC / 1024 CTAs per leaf, four consecutive
+// cells per thread read as one float4 per variable (all five loads in flight at once).  The
+// sums stay float-float (TwoSum) through the warp butterflies and the fixed-order combination
+// of the warps; one thread widens the CTA's sums to float64 and scales them by the cell volume
+// (GB300's float64 pipe is too narrow for per-thread float64 work).  Each CTA writes one
+// partial; the two-level finish sums the partials in CTA order.
+template <int ND, int B>
+__global__ void __launch_bounds__(256) reduce_split_kernel(const float* __restrict__ U, const int* __restrict__ level,
+                                                           Geometry G, DevCtl* ctl, double* partials, double* gpart,
+                                                           unsigned* gcount, int nleaves, int advance) {
+  constexpr int NV = ND + 2, NC = Tile<ND, B>::NC, CPL = NC / 1024;
+  static_assert(NC % 1024 == 0, "four cells per thread, 256 threads per CTA");
+  __shared__ float red[8][2 * NV + 1];
+  __shared__ int sbad;
+  const int leaf = blockIdx.x / CPL, part = blockIdx.x % CPL;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool active = leaf < nleaves;
+  float4 q[NV];
+  if (active) {
+    const float* Ul = U + (size_t)leaf * NV * NC + (part * 256 + threadIdx.x) * 4;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = __ldg(reinterpret_cast<const float4*>(Ul + (size_t)v * NC));
+  }
+  if (threadIdx.x == 0) sbad = 0;
+  const double dt = cta_stage_dt(ctl, nullptr);  // its barrier also orders sbad
+  const float gam = G.gammaf, gm1 = gam - 1.f;
+  const int lev = active ? level[leaf] : 1;
+  float rate = 0.f, hi[NV], lo[NV];
+  int bad = 0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) hi[v] = lo[v] = 0.f;
+  if (active) {
+    float dx[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dx[d] = geo_dx<float>(G, lev, d);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float Uc[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Uc[v] = k == 0 ? q[v].x : k == 1 ? q[v].y : k == 2 ? q[v].z : q[v].w;
+      rate = fmaxf(rate, cell_rate<float, ND>(Uc, gam, gm1, dx, &bad));
+#pragma unroll
+      for (int v = 0; v < NV; ++v) twosum_acc(hi[v], lo[v], Uc[v]);
     }
-  const real inv = real(1) / real(1 << ND);
-  if (D.kind == 0) {
-    const int t = q % NT, m = q / NT;
-    int tl[3] = {0, 0, 0};
-    if (e1 >= 0) tl[e1] = t % B;
-    if (e2 >= 0) tl[e2] = t / B;
-    int q1 = e1 >= 0 ? tl[e1] / (B / 2) : 0, q2 = e2 >= 0 ? tl[e2] / (B / 2) : 0;
-    int F = D.src[q1 + 2 * q2];
+  }
+  if (bad) sbad = 1;
+  for (int o = 16; o > 0; o >>= 1) {
+    rate = fmaxf(rate, __shfl_xor_sync(0xffffffffu, rate, o));
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      real sum = real(0);
-      for (int o = 0; o < (1 << ND); ++o) {
-        int loc[3] = {0, 0, 0};
-        for (int e = 0; e < ND; ++e) {
-          int oe = (o >> e) & 1;
-          if (e == d) loc[e] = (side == 0 ? B - 2 - 2 * m : 2 * m) + oe;
-          else loc[e] = 2 * tl[e] + oe - (e == e1 ? q1 : q2) * B;
-        }
-        sum = sum + U[((size_t)F * NV + v) * NC + loc[0] + B * (loc[1] + B * loc[2])];
+      const float h2 = __shfl_xor_sync(0xffffffffu, hi[v], o), l2 = __shfl_xor_sync(0xffffffffu, lo[v], o);
+      ff_acc(hi[v], lo[v], h2, l2);
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) red[warp][v] = hi[v], red[warp][NV + v] = lo[v];
+    red[warp][2 * NV] = rate;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float mm = red[0][2 * NV];
+    for (int w = 1; w < 8; ++w) {
+      mm = fmaxf(mm, red[w][2 * NV]);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) ff_acc(hi[v], lo[v], red[w][v], red[w][NV + v]);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) partials[(size_t)blockIdx.x * NV + v] = ((double)hi[v] + (double)lo[v]) * G.dV[lev];
+    __threadfence();  // the partial is visible before the group counter counts this CTA
+    atomicMax(&ctl->smax_bits, MaxKey<float>::enc(mm));
+    if (sbad) atomicOr(&ctl->status, 1);
+  }
+  last_cta_finish<float, NV, 256>(ctl, partials, gpart, gcount, (int)gridDim.x, 1, advance != 0, dt, false);
+}
+
+// ====================================================== ghost slab fill ==
+// One CTA per slab.  Restriction: mean of the 2^ndim fine cells (x-fastest sum).
+// Prolongation: q_p + 1/4 sum_e sigma_e s_e, minmod slopes; normal inner
+// neighbour = restriction of the target leaf; tangential neighbours outside the
+// coarse leaf give s_e = 0.  The face direction D is a template parameter so that
+// every cell index is formed in registers; runs of consecutive x cells are read as
+// one vector (4 fine layers of an x face, x pairs otherwise).
+
+// n consecutive values at p (p aligned to n * sizeof(real), or to 16 bytes for double)
+template <typename real>
+__device__ __forceinline__ void ld_run4(const real* p, real* o) {
+  if constexpr (sizeof(real) == 4) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = a.x, o[1] = a.y, o[2] = a.z, o[3] = a.w;
+  } else {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    o[0] = a.x, o[1] = a.y, o[2] = b.x, o[3] = b.y;
+  }
+}
+template <typename real>
+__device__ __forceinline__ void ld_run2(const real* p, real* o) {
+  if constexpr (sizeof(real) == 4) {
+    const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+    o[0] = a.x, o[1] = a.y;
+  } else {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    o[0] = a.x, o[1] = a.y;
+  }
+}
+template <typename real>
+__device__ __forceinline__ void st_run2(real* p, real a, real b) {
+  if constexpr (sizeof(real) == 4) *reinterpret_cast<float2*>(p) = make_float2(a, b);
+  else *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+
+// the tangential dimensions of face direction D (E1 < E2; -1 where ND has none)
+template <int ND, int D>
+struct FaceDims {
+  static constexpr int E1 = ND < 2 ? -1 : (D == 0 ? 1 : 0);
+  static constexpr int E2 = ND < 3 ? -1 : (D == 2 ? 1 : 2);
+};
+
+template <int ND, int B, int D>
+__device__ __forceinline__ int face_cell(int n, int a1, int a2) {
+  constexpr int E1 = FaceDims<ND, D>::E1, E2 = FaceDims<ND, D>::E2;
+  int x[3] = {0, 0, 0};
+  x[D] = n;
+  if constexpr (E1 >= 0) x[E1] = a1;
+  if constexpr (E2 >= 0) x[E2] = a2;
+  return x[0] + B * (x[1] + B * x[2]);
+}
+
+// restriction ghosts of one (tangential cell t, variable v) of a slab, both layers
+template <typename real, int ND, int B, int D>
+__device__ __forceinline__ void ghost_restrict(const real* __restrict__ U, real* __restrict__ slab,
+                                               const SlabDesc& S, int t, int v) {
+  constexpr int NV = ND + 2, NC = Tile<ND, B>::NC, NT = Tile<ND, B>::NT;
+  constexpr int E1 = FaceDims<ND, D>::E1, E2 = FaceDims<ND, D>::E2;
+  constexpr int NA = E1 >= 0 ? 2 : 1, NB = E2 >= 0 ? 2 : 1;
+  const int side = S.face & 1;
+  const int t1 = E1 >= 0 ? t % B : 0, t2 = E2 >= 0 ? t / B : 0;
+  const int q1 = t1 / (B / 2), q2 = t2 / (B / 2);
+  const real* Uf = U + ((size_t)S.src[q1 + 2 * q2] * NV + v) * NC;
+  const int f1 = 2 * t1 - q1 * B, f2 = 2 * t2 - q2 * B;  // first fine cell along E1, E2
+  const int n0 = side == 0 ? B - 4 : 0;                  // the four fine layers next to the face
+  real c[4][2][2];  // [normal layer n0 + k][offset along E1][offset along E2]
+  if constexpr (D == 0) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int a = 0; a < NA; ++a) {
+        real r[4];
+        ld_run4(Uf + face_cell<ND, B, D>(n0, f1 + a, f2 + b), r);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[k][a][b] = r[k];
       }
-      slabs[(((size_t)s * NV + v) * 2 + m) * NT + t] = sum * inv;
+  } else {  // E1 = 0: fine x pairs
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        real r[2];
+        ld_run2(Uf + face_cell<ND, B, D>(n0 + k, f1, f2 + b), r);
+        c[k][0][b] = r[0], c[k][1][b] = r[1];
+      }
+  }
+  // mean over the 2^ND fine cells of the layer pair starting at normal offset kb, x fastest
+  auto mean = [&](int kb) {
+    real sum = real(0);
+#pragma unroll
+    for (int o = 0; o < (1 << ND); ++o) {
+      const int k = kb + ((o >> D) & 1);
+      const int a = E1 >= 0 ? (o >> E1) & 1 : 0, b = E2 >= 0 ? (o >> E2) & 1 : 0;
+      sum = sum + c[k][a][b];
+    }
+    return sum * (real(1) / real(1 << ND));
+  };
+  const real lo = mean(0), hi = mean(2);
+  // layer m = 0 is the one next to the face: fine layers B-2, B-1 (side 0) or 0, 1 (side 1)
+  slab[((size_t)v * 2 + 0) * NT + t] = side == 0 ? hi : lo;
+  slab[((size_t)v * 2 + 1) * NT + t] = side == 0 ? lo : hi;
+}
+
+// prolongation ghosts of one (coarse face cell qc, variable v): 2 layers x 2^(ND-1) fine cells
+template <typename real, int ND, int B, int D>
+__device__ __forceinline__ void ghost_prolong(const real* __restrict__ U, real* __restrict__ slab,
+                                              const SlabDesc& S, int qc, int v) {
+  constexpr int NV = ND + 2, NC = Tile<ND, B>::NC, NT = Tile<ND, B>::NT, HB = B / 2;
+  constexpr int E1 = FaceDims<ND, D>::E1, E2 = FaceDims<ND, D>::E2;
+  constexpr int NA = E1 >= 0 ? 2 : 1, NB = E2 >= 0 ? 2 : 1;
+  const int side = S.face & 1;
+  const int c1 = E1 >= 0 ? qc % HB : 0, c2 = E2 >= 0 ? qc / HB : 0;  // the target's coarse cell
+  const int p1 = S.off[0] + c1, p2 = S.off[1] + c2;                  // the coarse cell in its leaf
+  const int pn = side == 0 ? B - 1 : 0;
+  const real* Uc = U + ((size_t)S.src[0] * NV + v) * NC;
+  const real* Ut = U + ((size_t)S.target * NV + v) * NC;
+  const real qp = __ldg(Uc + face_cell<ND, B, D>(pn, p1, p2));
+  const real away = __ldg(Uc + face_cell<ND, B, D>(side == 0 ? pn - 1 : pn + 1, p1, p2));
+  // restriction of the target's fine cells next to the face (normal inner neighbour)
+  const int fn = side == 0 ? 0 : B - 2;
+  real g[2][2][2];  // [normal offset][offset along E1][offset along E2]
+  if constexpr (D == 0) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int a = 0; a < NA; ++a) {
+        real r[2];
+        ld_run2(Ut + face_cell<ND, B, D>(fn, 2 * c1 + a, 2 * c2 + b), r);
+        g[0][a][b] = r[0], g[1][a][b] = r[1];
+      }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        real r[2];
+        ld_run2(Ut + face_cell<ND, B, D>(fn + k, 2 * c1, 2 * c2 + b), r);
+        g[k][0][b] = r[0], g[k][1][b] = r[1];
+      }
+  }
+  real inner = real(0);
+#pragma unroll
+  for (int o = 0; o < (1 << ND); ++o) {
+    const int k = (o >> D) & 1;
+    const int a = E1 >= 0 ? (o >> E1) & 1 : 0, b = E2 >= 0 ? (o >> E2) & 1 : 0;
+    inner = inner + g[k][a][b];
+  }
+  inner = inner * (real(1) / real(1 << ND));
+  real sl[3] = {real(0), real(0), real(0)};
+  sl[D] = side == 0 ? minmod2(qp - away, inner - qp) : minmod2(qp - inner, away - qp);
+  if constexpr (E1 >= 0) {
+    const bool ok = p1 >= 1 && p1 + 1 < B;
+    sl[E1] = ok ? minmod2(qp - __ldg(Uc + face_cell<ND, B, D>(pn, p1 - 1, p2)),
+                          __ldg(Uc + face_cell<ND, B, D>(pn, p1 + 1, p2)) - qp)
+                : real(0);
+  }
+  if constexpr (E2 >= 0) {
+    const bool ok = p2 >= 1 && p2 + 1 < B;
+    sl[E2] = ok ? minmod2(qp - __ldg(Uc + face_cell<ND, B, D>(pn, p1, p2 - 1)),
+                          __ldg(Uc + face_cell<ND, B, D>(pn, p1, p2 + 1)) - qp)
+                : real(0);
+  }
+  // fine ghost (layer m, offsets a, b along E1, E2): sigma_e = +1 on the upper fine half
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      real val[2];
+#pragma unroll
+      for (int a = 0; a < NA; ++a) {
+        real acc = real(0);
+#pragma unroll
+        for (int e = 0; e < ND; ++e) {
+          real sg;
+          if (e == D) sg = (side == 0) == (m == 0) ? real(1) : real(-1);
+          else sg = ((e == E1 ? a : b) == 1) ? real(1) : real(-1);
+          acc = acc + sg * sl[e];
+        }
+        val[a] = qp + real(0.25) * acc;
+      }
+      real* o = slab + ((size_t)v * 2 + m) * NT;
+      if constexpr (NA == 2) st_run2(o + (2 * c1) + B * (2 * c2 + b), val[0], val[1]);
+      else o[0] = val[0];
+    }
+}
+
+template <int ND, int B>
+struct GhostShape {
+  static constexpr int NV = ND + 2, HB = B / 2;
+  static constexpr int NCC = ND == 1 ? 1 : (ND == 2 ? HB : HB * HB);  // coarse cells of a prolongation slab
+  static constexpr int THREADS = (NCC * NV + 31) / 32 * 32;
+};
+
+template <typename real, int ND, int B>
+__global__ void __launch_bounds__(GhostShape<ND, B>::THREADS)
+ghost_fill_kernel(const real* __restrict__ U, real* __restrict__ slabs, const SlabDesc* __restrict__ desc,
+                  int nslabs) {
+  constexpr int NV = ND + 2, NT = Tile<ND, B>::NT;
+  constexpr int NCC = GhostShape<ND, B>::NCC, NTH = GhostShape<ND, B>::THREADS;
+  const int s = blockIdx.x;
+  if (s >= nslabs) return;
+  const SlabDesc S = desc[s];
+  real* slab = slabs + (size_t)s * NV * 2 * NT;
+  const int d = S.face >> 1;
+  if (S.kind == 0) {
+    // (tangential cell, variable) items, NT * NV of them, strided over the CTA
+#pragma unroll
+    for (int i = 0; i < (NT * NV + NTH - 1) / NTH; ++i) {
+      const int q = threadIdx.x + i * NTH;
+      if (q < NT * NV) {
+        const int t = q % NT, v = q / NT;
+        if (d == 0) ghost_restrict<real, ND, B, 0>(U, slab, S, t, v);
+        else if constexpr (ND >= 2) {
+          if (d == 1) ghost_restrict<real, ND, B, 1>(U, slab, S, t, v);
+          else if constexpr (ND == 3) ghost_restrict<real, ND, B, 2>(U, slab, S, t, v);
+        }
+      }
     }
     return;
   }
-  // prolongation: coarse face cell (c1, c2) in the target's tangential half-resolution grid
-  constexpr int HB = B / 2, NCC = ND == 1 ? 1 : (ND == 2 ? HB : HB * HB);
-  // one thread per (coarse face cell, variable) where the slab's threads suffice (2D, 3D);
-  // in 1D one thread per coarse face cell loops over the variables
-  constexpr bool PERVAR = NCC * NV <= 2 * NT;
-  if (q >= (PERVAR ? NCC * NV : NCC)) return;
-  const int qc = q % NCC;
-  const int v0 = PERVAR ? q / NCC : 0, v1 = PERVAR ? v0 + 1 : NV;
-  const int c1 = ND >= 2 ? qc % HB : 0, c2 = ND == 3 ? qc / HB : 0;
-  const int Cl = D.src[0];
-  int p[3] = {0, 0, 0}, cc[3] = {0, 0, 0};  // coarse cell; the target's coarse-cell index per direction
-  if (e1 >= 0) cc[e1] = c1;
-  if (e2 >= 0) cc[e2] = c2;
-  for (int e = 0; e < ND; ++e) {
-    if (e == d) p[e] = side == 0 ? B - 1 : 0;
-    else p[e] = ((e == e1) ? D.off[0] : D.off[1]) + cc[e];
-  }
-  for (int v = v0; v < v1; ++v) {
-    auto cval = [&](const int* c) { return U[((size_t)Cl * NV + v) * NC + c[0] + B * (c[1] + B * c[2])]; };
-    const real qp = cval(p);
-    // restriction of the target's fine cells next to the face (normal inner neighbour)
-    real inner;
-    {
-      real sum = real(0);
-      for (int o = 0; o < (1 << ND); ++o) {
-        int loc[3] = {0, 0, 0};
-        for (int e = 0; e < ND; ++e) {
-          int oe = (o >> e) & 1;
-          if (e == d) loc[e] = (side == 0 ? 0 : B - 2) + oe;
-          else loc[e] = 2 * cc[e] + oe;
-        }
-        sum = sum + U[((size_t)D.target * NV + v) * NC + loc[0] + B * (loc[1] + B * loc[2])];
-      }
-      inner = sum * inv;
-    }
-    real sl[3] = {real(0), real(0), real(0)};
-    for (int e = 0; e < ND; ++e) {
-      real qm, qq;
-      bool ok = true;
-      int c[3] = {p[0], p[1], p[2]};
-      if (e == d) {
-        c[e] = side == 0 ? p[e] - 1 : p[e] + 1;
-        real away = cval(c);
-        if (side == 0) { qm = away; qq = inner; } else { qm = inner; qq = away; }
-      } else {
-        int cm[3] = {p[0], p[1], p[2]}, cp[3] = {p[0], p[1], p[2]};
-        cm[e] -= 1;
-        cp[e] += 1;
-        ok = cm[e] >= 0 && cp[e] < B;
-        qm = ok ? cval(cm) : real(0);
-        qq = ok ? cval(cp) : real(0);
-      }
-      sl[e] = ok ? minmod2(qp - qm, qq - qp) : real(0);
-    }
-    // the fine ghost cells of this coarse cell: layer m, fine offsets (a, b) along (e1, e2)
-    for (int m = 0; m < 2; ++m)
-      for (int b = 0; b < (ND == 3 ? 2 : 1); ++b)
-        for (int a = 0; a < (ND >= 2 ? 2 : 1); ++a) {
-          real acc = real(0);
-          for (int e = 0; e < ND; ++e) {
-            real sg;
-            if (e == d) sg = (side == 0) == (m == 0) ? real(1) : real(-1);
-            else sg = ((e == e1 ? a : b) == 1) ? real(1) : real(-1);
-            acc = acc + sg * sl[e];
-          }
-          const int t = ND == 1 ? 0 : (ND == 2 ? 2 * c1 + a : (2 * c1 + a) + B * (2 * c2 + b));
-          slabs[(((size_t)s * NV + v) * 2 + m) * NT + t] = qp + real(0.25) * acc;
-        }
+  const int q = threadIdx.x;
+  if (q >= NCC * NV) return;
+  const int qc = q % NCC, v = q / NCC;
+  if (d == 0) ghost_prolong<real, ND, B, 0>(U, slab, S, qc, v);
+  else if constexpr (ND >= 2) {
+    if (d == 1) ghost_prolong<real, ND, B, 1>(U, slab, S, qc, v);
+    else if constexpr (ND == 3) ghost_prolong<real, ND, B, 2>(U, slab, S, qc, v);
   }
 }
 
 // ================================================================ reflux ==
 // Coarse cell next to a level jump: out += +-beta*dt/dx_c*(mean fine flux - coarse flux).
 template <typename real, int ND, int B>
-__global__ void reflux_kernel(real* __restrict__ out, const real* __restrict__ fflux, const RefluxRec* __restrict__ rec,
-                              int nrec, const int* __restrict__ level, Geometry G, const DevCtl* ctl, real beta) {
-  constexpr int NV = ND + 2, NC = Tile<ND, B>::NC, NT = Tile<ND, B>::NT;
-  long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  float dtf;
-  double dt = cta_stage_dt(ctl, &dtf);
-  if (gid >= (long long)nrec * NV * NT) return;
-  if (!(dt > 0.0)) return;
-  int t = gid % NT, v = (gid / NT) % NV, r = gid / (NT * NV);
-  RefluxRec R = rec[r];
-  int d = R.face >> 1, side = R.face & 1;
+__device__ __forceinline__ real reflux_corr(const real* __restrict__ fflux, const RefluxRec& R, int t, int v,
+                                            real dxc, real dtr, real beta) {
+  constexpr int NV = ND + 2, NT = Tile<ND, B>::NT;
+  int d = R.face >> 1;
   int e1 = -1, e2 = -1;
   for (int e = 0; e < ND; ++e)
     if (e != d) {
@@ -997,13 +1194,43 @@ __global__ void reflux_kernel(real* __restrict__ out, const real* __restrict__ f
     }
   real mean = sum * (real(1) / real(1 << (ND - 1)));
   real Fc = fflux[((size_t)R.cslot * NV + v) * NT + t];
-  int lev = level[R.coarse];
-  real dxc = geo_dx<real>(G, lev, d);
-  real corr = beta * (sizeof(real) == 4 ? (real)dtf : (real)dt) * (mean - Fc) / dxc;
-  int n = side == 0 ? 0 : B - 1;
-  int cell = compose_cell<ND, B>(d, n, t);
-  size_t o = ((size_t)R.coarse * NV + v) * NC + cell;
-  out[o] = side == 0 ? out[o] + corr : out[o] - corr;
+  return beta * dtr * (mean - Fc) / dxc;
+}
+
+// One thread per (record, variable, tangential cell).  A cell at a leaf edge or corner
+// borders level jumps through several faces of its leaf: the thread of the first such
+// record (faces ascending, i.e. x before y before z) applies all of them in that
+// order and the others skip the cell, so every cell has one writer.
+template <typename real, int ND, int B>
+__global__ void reflux_kernel(real* __restrict__ out, const real* __restrict__ fflux, const RefluxRec* __restrict__ rec,
+                              int nrec, const int* __restrict__ level, Geometry G, const DevCtl* ctl, real beta) {
+  constexpr int NV = ND + 2, NC = Tile<ND, B>::NC, NT = Tile<ND, B>::NT;
+  long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float dtf;
+  double dt = cta_stage_dt(ctl, &dtf);
+  if (gid >= (long long)nrec * NV * NT) return;
+  if (!(dt > 0.0)) return;
+  const real dtr = sizeof(real) == 4 ? (real)dtf : (real)dt;
+  int t = gid % NT, v = (gid / NT) % NV, r = gid / (NT * NV);
+  const RefluxRec R = rec[r];
+  const int cell = compose_cell<ND, B>(R.face >> 1, (R.face & 1) ? B - 1 : 0, t);
+  const int x[3] = {cell % B, ND > 1 ? (cell / B) % B : 0, ND > 2 ? cell / (B * B) : 0};
+  auto touches = [&](int face) { return x[face >> 1] == ((face & 1) ? B - 1 : 0); };
+  for (int k = R.first; k < r; ++k)
+    if (touches(rec[k].face)) return;
+  const int lev = level[R.coarse];
+  const size_t o = ((size_t)R.coarse * NV + v) * NC + cell;
+  real val = out[o];
+  for (int k = r; k < R.last; ++k) {
+    const RefluxRec K = rec[k];
+    if (k > r && !touches(K.face)) continue;
+    const int dk = K.face >> 1;
+    // tangential index of the cell on face dk (the inverse of compose_cell)
+    const int tk = ND == 1 ? 0 : (ND == 2 ? x[dk == 0 ? 1 : 0] : (dk == 0 ? x[1] + B * x[2] : (dk == 1 ? x[0] + B * x[2] : x[0] + B * x[1])));
+    const real corr = reflux_corr<real, ND, B>(fflux, K, tk, v, geo_dx<real>(G, lev, dk), dtr, beta);
+    val = (K.face & 1) == 0 ? val + corr : val - corr;
+  }
+  out[o] = val;
 }
 
 // ============================================================ estimator ==

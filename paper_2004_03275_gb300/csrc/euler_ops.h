@@ -14,6 +14,7 @@ struct EulerOps {
                             cudaStream_t s);
   static cudaError_t ghost_fill(int B, const real* U, real* slabs, const SlabDesc* desc, int nslabs,
                                 cudaStream_t s);
+  // rec: records grouped by coarse leaf, faces ascending within a group ([first, last) of each)
   static cudaError_t reflux(int B, real* out, const real* fflux, const RefluxRec* rec, int nrec,
                             const int* level, const Geometry& G, const DevCtl* ctl, real beta, cudaStream_t s);
   static cudaError_t lohner(int B, const real* U, const real* slabs, const int* nb, double gamma, double eps,

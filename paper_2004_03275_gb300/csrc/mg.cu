@@ -407,7 +407,7 @@ __device__ __forceinline__ StripGeom strip_geom(int n, long long start, int H, i
 
 __device__ __forceinline__ int wrap_row(int r, int n) { return r < 0 ? r + n : (r >= n ? r - n : r); }
 
-template <typename real, bool NEU>
+template <typename real, bool NEU, bool XZERO = false>
 __global__ void __launch_bounds__(128)
     sweep2d_kernel(MgState S, const real* __restrict__ xin, real* __restrict__ xout, const real* __restrict__ bl,
                    const Chunk* ch, int nch) {
@@ -430,7 +430,11 @@ __global__ void __launch_bounds__(128)
   const int craw = g.x0 - 2 + lane;  // this lane's column before the periodic wrap
   const bool colin = craw >= 0 && craw < n;
   auto inside = [&](int r) { return !NEU || (colin && r >= 0 && r < n); };
-  auto ldx = [&](int r) { return inside(r) ? x[rowof(r) * n + c] : real(0); };
+  // XZERO: the first sweep of a correction, whose initial iterate is zero (not read)
+  auto ldx = [&](int r) {
+    if constexpr (XZERO) return real(0);
+    else return inside(r) ? x[rowof(r) * n + c] : real(0);
+  };
   auto ldb = [&](int r) { return b[rowof(r) * n + c]; };
   // reciprocal diagonal of this lane's cell in row r
   auto idg_at = [&](int r) {
@@ -664,7 +668,8 @@ __device__ __forceinline__ FF ff_mul(FF a, float chi, float clo) {
 // ~2^-44 of its largest term, far below the stopping tolerance), so the only float64
 // operations per cell are the two updates and one widening add.  R replaces the float64
 // re-evaluation of the stencil of X, which kept GB300's float64 pipe busy.  e is not zeroed
-// here (its neighbours are still being read); zero0_kernel follows.
+// here (its neighbours are still being read): in 2D the next cycle's first pre-sweep starts
+// from zero without reading it, in 3D zero0_kernel follows.
 template <bool NEU>
 __global__ void update64_kernel(MgState S, Lvl<float> L, const Chunk* ch) {
   Chunk C = ch[blockIdx.x];
@@ -1097,6 +1102,20 @@ void add_chunks(std::vector<Chunk>& v, int inst, int lev, long long count) {
   for (long long s = 0; s < count; s += kChunk) v.push_back(Chunk{inst, lev, s, (int)std::min<long long>(kChunk, count - s)});
 }
 
+// kernel kinds of one V-cycle (mg_profile_vcycle)
+enum MgKind {
+  kMgSweep = 0,        // 2D red-black sweep (one tiled pass per sweep)
+  kMgCopy = 1,         // 2D copy after an odd number of sweeps
+  kMgSmooth = 2,       // 3D red-black half sweep (one colour)
+  kMgResRestrict = 3,  // residual and restriction to the next depth
+  kMgCoarse = 4,       // coarsest-level direct solve
+  kMgProlong = 5,      // prolongation of the correction
+  kMgUpdate = 6,       // float32 cycles: X += e, R -= A e (float-float)
+  kMgZero = 7,         // float32 cycles: zero the level-0 correction
+  kMgCorrect = 8,      // float64 cycles: X += e
+  kMgResidual = 9      // float64 cycles: new level-0 defect
+};
+
 struct Mg {
   int nd = 2, ninst = 0, nu1 = 2, nu2 = 2, max_cycles = 50, precision = AMR_FP32;
   bool neu = false;  // Neumann (zero-flux) boundaries, else periodic
@@ -1123,6 +1142,21 @@ struct Mg {
   int* h_any = nullptr;
   cudaGraphExec_t vgraph = nullptr;
   long long launches = 0;
+  bool solved = false;  // a solve has run: the level-0 defect and the level arrays are set
+  // measurement: while prof_ev is set, every kernel enqueue_vcycle launches is followed by an
+  // event on the stream (prof_ev[0] is recorded before the first), and its kind is kept
+  std::vector<cudaEvent_t>* prof_ev = nullptr;
+  std::vector<int>* prof_kind = nullptr;
+  void mark(int kind) {
+    ++launches;
+    if (!prof_ev) return;
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) == cudaSuccess) {
+      cudaEventRecord(e, stream);
+      prof_ev->push_back(e);
+      prof_kind->push_back(kind);
+    }
+  }
   int vcycle_kernels = 0;
 
   ~Mg() {
@@ -1427,7 +1461,7 @@ struct Mg {
     Lvl<real> Lv = lvl<real>();
     const Chunk* all = d_chall.as<Chunk>();
     real* Y = d_yl.as<real>();
-    auto smooth = [&](int l, int sweeps) {  // `sweeps` red-black sweeps of depth l
+    auto smooth = [&](int l, int sweeps, bool first) {  // `sweeps` red-black sweeps of depth l
       if (nd == 2) {
         if (ch_tile[l].empty()) return;
         const int nch = (int)ch_tile[l].size();
@@ -1435,15 +1469,25 @@ struct Mg {
         const Chunk* tl = all + off_tile[l];
         for (int s = 0; s < sweeps; ++s) {
           bool even = (s & 1) == 0;
-          if (neu)
-            sweep2d_kernel<real, true><<<nb, 128, 0, stream>>>(S, even ? Lv.x : Y, even ? Y : Lv.x, Lv.b, tl, nch);
-          else
-            sweep2d_kernel<real, false><<<nb, 128, 0, stream>>>(S, even ? Lv.x : Y, even ? Y : Lv.x, Lv.b, tl, nch);
-          ++launches;
+          // the first pre-sweep starts from the zero correction (set by the residual, the
+          // restriction or, for depth 0 of later cycles, by nobody: it is never read)
+          const bool xz = first && s == 0;
+          if (neu) {
+            if (xz)
+              sweep2d_kernel<real, true, true><<<nb, 128, 0, stream>>>(S, Lv.x, Y, Lv.b, tl, nch);
+            else
+              sweep2d_kernel<real, true><<<nb, 128, 0, stream>>>(S, even ? Lv.x : Y, even ? Y : Lv.x, Lv.b, tl, nch);
+          } else {
+            if (xz)
+              sweep2d_kernel<real, false, true><<<nb, 128, 0, stream>>>(S, Lv.x, Y, Lv.b, tl, nch);
+            else
+              sweep2d_kernel<real, false><<<nb, 128, 0, stream>>>(S, even ? Lv.x : Y, even ? Y : Lv.x, Lv.b, tl, nch);
+          }
+          mark(kMgSweep);
         }
         if (sweeps & 1) {
           copy2d_kernel<real><<<nb, 128, 0, stream>>>(S, Y, Lv.x, tl, nch);
-          ++launches;
+          mark(kMgCopy);
         }
         return;
       }
@@ -1454,37 +1498,37 @@ struct Mg {
             smooth_kernel<real, true><<<(unsigned)ch_half[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_half[l], colour);
           else
             smooth_kernel<real, false><<<(unsigned)ch_half[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_half[l], colour);
-          ++launches;
+          mark(kMgSmooth);
         }
     };
     for (int l = 0; l + 1 < maxdepth; ++l) {
-      smooth(l, nu1);
+      smooth(l, nu1, true);
       if (!ch_coarse[l].empty()) {
         if (neu)
           resrestrict_kernel<real, true><<<(unsigned)ch_coarse[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
         else
           resrestrict_kernel<real, false><<<(unsigned)ch_coarse[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
-        ++launches;
+        mark(kMgResRestrict);
       }
     }
     coarse_kernel<real><<<(unsigned)coarse_inst.size(), 256, 0, stream>>>(S, Lv, d_cinst.as<int>(), d_crow0.as<int>(),
                                                                           (int)coarse_inst.size());
-    ++launches;
+    mark(kMgCoarse);
     for (int l = maxdepth - 2; l >= 0; --l) {
       if (nd == 2 && !ch_coarse[l].empty()) {
         if (neu)
           prolong2d_kernel<real, true><<<(unsigned)ch_coarse[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
         else
           prolong2d_kernel<real, false><<<(unsigned)ch_coarse[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
-        ++launches;
+        mark(kMgProlong);
       } else if (nd != 2 && !ch_fine[l].empty()) {
         if (neu)
           prolong_kernel<real, true><<<(unsigned)ch_fine[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_fine[l]);
         else
           prolong_kernel<real, false><<<(unsigned)ch_fine[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_fine[l]);
-        ++launches;
+        mark(kMgProlong);
       }
-      smooth(l, nu2);
+      smooth(l, nu2, false);
     }
     // the correction and the new level-0 defect: float32 cycles update R by A e; float64
     // cycles correct X and re-evaluate the residual
@@ -1493,15 +1537,20 @@ struct Mg {
         update64_kernel<true><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
       else
         update64_kernel<false><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
-      zero0_kernel<<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+      mark(kMgUpdate);
+      if (nd != 2 || nu1 == 0) {  // 2D pre-sweeps never read the correction they start from
+        zero0_kernel<<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+        mark(kMgZero);
+      }
     } else {
       correct64_kernel<real><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+      mark(kMgCorrect);
       if (neu)
         residual64_kernel<real, true><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
       else
         residual64_kernel<real, false><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+      mark(kMgResidual);
     }
-    launches += 2;
     return cuda(cudaGetLastError(), "vcycle launch");
   }
 
@@ -1641,6 +1690,41 @@ struct Mg {
 
   int solve_device_any() { return precision == AMR_FP64 ? solve_device<double>() : solve_device<float>(); }
 
+  // One V-cycle from the current defect with every instance taking part (a converged one
+  // too: its active flag is set, as at the start of a solve), its kernels launched one by one
+  // with an event after each; kind[i] and us[i] (microseconds between consecutive events) for
+  // up to cap kernels.
+  int profile_vcycle(int* kind, float* us, int cap, int* n) {
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kinds;
+    cudaEvent_t e0 = nullptr;
+    int rc = cuda(cudaMemsetAsync(d_active.p, 1, (size_t)ninst * sizeof(int), stream), "active");  // nonzero
+    if (!rc) rc = cuda(cudaEventCreate(&e0), "event");
+    if (!rc) {
+      ev.push_back(e0);
+      rc = cuda(cudaEventRecord(e0, stream), "event");
+    }
+    if (!rc) {
+      prof_ev = &ev;
+      prof_kind = &kinds;
+      rc = precision == AMR_FP64 ? enqueue_vcycle<double>() : enqueue_vcycle<float>();
+      prof_ev = nullptr;
+      prof_kind = nullptr;
+    }
+    if (!rc) rc = cuda(cudaStreamSynchronize(stream), "sync");
+    if (!rc) {
+      *n = (int)kinds.size();
+      for (int i = 0; i < (int)kinds.size() && i < cap; ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+        kind[i] = kinds[i];
+        us[i] = ms * 1e3f;
+      }
+    }
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    return rc;
+  }
+
   int results(int* cycles, double* relres, bool* all_ok) {
     std::vector<int> cyc(ninst), fl(ninst);
     std::vector<double> lr(ninst), bn(ninst);
@@ -1764,6 +1848,12 @@ int mg_strip_height(const mg_handle* h, int side, int* height) {
   return AMR_OK;
 }
 
+int mg_profile_vcycle(mg_handle* h, int* kind, float* us, int cap, int* nkernels) {
+  if (!h || !kind || !us || !nkernels || cap < 0) return AMR_ERR_INVALID_ARG;
+  if (!h->mg.solved) return h->mg.fail(AMR_ERR_INVALID_ARG, "mg_profile_vcycle needs a prior mg_solve");
+  return h->mg.profile_vcycle(kind, us, cap, nkernels);
+}
+
 int mg_kernel_launches(const mg_handle* h, long long* n) {
   if (!h || !n) return AMR_ERR_INVALID_ARG;
   *n = h->mg.launches;
@@ -1784,6 +1874,7 @@ int mg_solve(mg_handle* h, const double* b, double* x, int on_device, int* cycle
   if (int rc = M.cuda(cudaMemcpyAsync(M.d_X.p, x, M.n0 * 8, k, M.stream), "copy x")) return rc;
   int rc = M.solve_graph_launch_any();
   if (rc) return rc;
+  M.solved = true;
   cudaMemcpyKind kb = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if ((rc = M.cuda(cudaMemcpyAsync(x, M.d_X.p, M.n0 * 8, kb, M.stream), "copy x back"))) return rc;
   if ((rc = M.cuda(cudaStreamSynchronize(M.stream), "sync"))) return rc;

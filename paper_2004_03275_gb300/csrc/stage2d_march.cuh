@@ -438,43 +438,44 @@ __global__ void __launch_bounds__(32 * kMarchMaxWarps, 2)
     if (active) load_leaf();
   }
 
-  if constexpr (!LAST) return;
-  // ---- last stage: CTA max rate, CTA totals (fixed order), two-level finish
-  for (int o = 16; o > 0; o >>= 1) rate = fmaxf(rate, __shfl_xor_sync(0xffffffffu, rate, o));
-  if (lane == 0) wrate[warp] = rate;
-  // each warp parks its (hi, lo) pairs in its own E array, which its y march no longer reads
-  float* park = reinterpret_cast<float*>(&M.E[0][0]);
-  const float thv[NV] = {th[0].x, th[0].y, th[1].x, th[1].y}, tlv[NV] = {tl[0].x, tl[0].y, tl[1].x, tl[1].y};
+  if constexpr (LAST) {
+    // ---- last stage: CTA max rate, CTA totals (fixed order), two-level finish
+    for (int o = 16; o > 0; o >>= 1) rate = fmaxf(rate, __shfl_xor_sync(0xffffffffu, rate, o));
+    if (lane == 0) wrate[warp] = rate;
+    // each warp parks its (hi, lo) pairs in its own E array, which its y march no longer reads
+    float* park = reinterpret_cast<float*>(&M.E[0][0]);
+    const float thv[NV] = {th[0].x, th[0].y, th[1].x, th[1].y}, tlv[NV] = {tl[0].x, tl[0].y, tl[1].x, tl[1].y};
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    park[v * 32 + lane] = thv[v];
-    park[(NV + v) * 32 + lane] = tlv[v];
-  }
-  if (bad) sbad = 1;
-  __syncthreads();
-  if (warp == 0) {
-    // lane = 8 v + g: variable v, threads 16 g .. 16 g + 15 in order, then the 8 groups
-    constexpr int PER = 32 * kMarchWarps / 8;
-    const int v = lane >> 3, g = lane & 7;
-    auto hi_of = [&](int t) { return reinterpret_cast<const float*>(&S[t >> 5].E[0][0])[v * 32 + (t & 31)]; };
-    auto lo_of = [&](int t) { return reinterpret_cast<const float*>(&S[t >> 5].E[0][0])[(NV + v) * 32 + (t & 31)]; };
-    float hh = hi_of(g * PER), ll = lo_of(g * PER);
-    for (int t = 1; t < PER; ++t) march::ff_add(hh, ll, hi_of(g * PER + t), lo_of(g * PER + t));
-    for (int o = 4; o > 0; o >>= 1) {
-      float h2 = __shfl_down_sync(0xffffffffu, hh, o), l2 = __shfl_down_sync(0xffffffffu, ll, o);
-      if (g < o) march::ff_add(hh, ll, h2, l2);
+    for (int v = 0; v < NV; ++v) {
+      park[v * 32 + lane] = thv[v];
+      park[(NV + v) * 32 + lane] = tlv[v];
     }
-    if (g == 0) a.partials[(size_t)blockIdx.x * NV + v] = ((double)hh + (double)ll) * G.dV[1];
-    __threadfence();  // the partials are visible before the group counter counts this CTA
-    if (lane == 0) {
-      float mm = wrate[0];
-      for (int w = 1; w < kMarchWarps; ++w) mm = fmaxf(mm, wrate[w]);
-      atomicMax(&a.ctl->smax_bits, MaxKey<float>::enc(mm));
-      if (sbad) atomicOr(&a.ctl->status, 1);
+    if (bad) sbad = 1;
+    __syncthreads();
+    if (warp == 0) {
+      // lane = 8 v + g: variable v, threads 16 g .. 16 g + 15 in order, then the 8 groups
+      constexpr int PER = 32 * kMarchWarps / 8;
+      const int v = lane >> 3, g = lane & 7;
+      auto hi_of = [&](int t) { return reinterpret_cast<const float*>(&S[t >> 5].E[0][0])[v * 32 + (t & 31)]; };
+      auto lo_of = [&](int t) { return reinterpret_cast<const float*>(&S[t >> 5].E[0][0])[(NV + v) * 32 + (t & 31)]; };
+      float hh = hi_of(g * PER), ll = lo_of(g * PER);
+      for (int t = 1; t < PER; ++t) march::ff_add(hh, ll, hi_of(g * PER + t), lo_of(g * PER + t));
+      for (int o = 4; o > 0; o >>= 1) {
+        float h2 = __shfl_down_sync(0xffffffffu, hh, o), l2 = __shfl_down_sync(0xffffffffu, ll, o);
+        if (g < o) march::ff_add(hh, ll, h2, l2);
+      }
+      if (g == 0) a.partials[(size_t)blockIdx.x * NV + v] = ((double)hh + (double)ll) * G.dV[1];
+      __threadfence();  // the partials are visible before the group counter counts this CTA
+      if (lane == 0) {
+        float mm = wrate[0];
+        for (int w = 1; w < kMarchWarps; ++w) mm = fmaxf(mm, wrate[w]);
+        atomicMax(&a.ctl->smax_bits, MaxKey<float>::enc(mm));
+        if (sbad) atomicOr(&a.ctl->status, 1);
+      }
     }
+    last_cta_finish<float, NV, 32 * kMarchWarps>(a.ctl, a.partials, a.gpart, a.gcount, (int)gridDim.x, 1, true, dtd,
+                                                 false);
   }
-  last_cta_finish<float, NV, 32 * kMarchWarps>(a.ctl, a.partials, a.gpart, a.gcount, (int)gridDim.x, 1, true, dtd,
-                                               false);
 }
 
 }  // namespace amrgpu

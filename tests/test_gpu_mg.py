@@ -247,3 +247,34 @@ def test_autotuned_strip_heights():
     for i in range(len(sizes)):
         xo, _, _ = O.mg_solve(bs[i], np.zeros_like(bs[i]), L, lam[i])
         assert np.max(np.abs(xs[i] - xo)) <= 1e-12 * np.max(np.abs(xo))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_profile_vcycle_is_one_more_cycle(precision):
+    """mg_profile_vcycle runs one V-cycle kernel by kernel: before any solve it is refused; after
+    a solve it reports every kernel of the cycle (the sweeps, one residual-restriction and one
+    prolongation per depth above the coarsest, one coarse solve, and the level-0 update of the
+    precision), each with a positive time, and the handle stays usable."""
+    sizes, L = [64, 48, 32], 1.3
+    lam, bs = batch(sizes, 2, 21)
+    s = amrvac.MgSolver(2, sizes, lam, L, rtol=1e-4, precision=precision)
+    with pytest.raises(amrvac.AmrError):
+        s.profile_vcycle()
+    b = pack(bs)
+    x = np.zeros(s.n)
+    s.solve(b, x)
+    prof = s.profile_vcycle()
+    kinds = [k for k, _ in prof]
+    depths = 3  # 64 -> 32 -> 16 -> 8: the largest instance has the most depths
+    assert kinds.count("sweep") == 4 * depths
+    assert kinds.count("resrestrict") == depths and kinds.count("prolong") == depths
+    assert kinds.count("coarse") == 1
+    # float32 cycles end with the defect update (in 2D the next cycle's first pre-sweep starts
+    # from a zero correction without reading it, so no zeroing kernel follows)
+    tail = ["sweep", "update"] if precision == "fp32" else ["correct64", "residual64"]
+    assert kinds[-2:] == tail and "zero" not in kinds
+    assert all(us > 0.0 for _, us in prof)
+    # a second solve from the first one's result is converged at once
+    cyc, rr = s.solve(b, x)
+    assert np.all(cyc == 0) and np.all(rr <= 1e-4)
+    s.close()
