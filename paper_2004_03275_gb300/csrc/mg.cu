@@ -356,20 +356,23 @@ __global__ void smooth_kernel(MgState S, Lvl<real> L, const Chunk* ch, int colou
 }
 
 // One full red-black sweep of a 2D level, one warp per strip of kStripW columns and
-// H rows (H = clamp(n / 32, 8, 64) on a level of side n, carried in the chunk's count:
-// short strips on coarse levels keep the serial march short where there is little
-// parallelism).  Lane k holds column x0 - 2 + k (periodic); the two lanes at each edge
-// are halo.  Walking the strip's rows, a lane keeps three rows of old values and three
-// rows of red-updated values in registers (loads run kPre rows ahead): at row s it
-// updates the red cells of row s + 1 (old black neighbours: its own rows s and s + 2,
-// row s + 1 of the lanes beside it), then the black cells of row s (red-updated
-// neighbours: its own rows s - 1 and s + 1, row s of the lanes beside it), and stores
-// row s.  It reads one iterate array and writes the other, so no warp sees another's
-// writes; the updates and their arithmetic are those of two in-place colour sweeps.
-// NEU (zero-flux boundaries): cells outside the domain read as 0 and are never
-// updated, so they add nothing to a neighbour sum, and a boundary cell divides by its
-// own diagonal lambda + count / h^2.
-constexpr int kStripW = 28, kStripHMax = 64, kPre = 4;
+// H rows (H per depth from the strip-height tuner, carried in the chunk's count).  Lane k
+// holds the column pair (x0 - 2 + 2k, x0 - 1 + 2k) (periodic): one red and one black cell
+// per row, read and written as one float2 / double2 (swept levels have an even side and
+// level offsets are multiples of 4 cells, so pairs are aligned and never straddle the
+// periodic wrap); lanes 0 and 31 are halo.  Walking the strip's rows, a lane keeps three
+// rows of old values and three rows of red-updated values in registers (loads run kPre
+// rows ahead): at row s it updates the red cell of row s + 1 (old black neighbours: its
+// own rows s and s + 2, its own black cell and one from the lane beside it), then the
+// black cell of row s (red-updated neighbours: its rows s - 1 and s + 1, its own red cell
+// and one from the lane beside it), and stores row s.  It reads one iterate array and
+// writes the other, so no warp sees another's writes; the updates and their arithmetic
+// (neighbour sums in the order x-, x+, y-, y+) are those of two in-place colour sweeps.
+// NEU (zero-flux boundaries): cells outside the domain read as 0 and are never updated,
+// so they add nothing to a neighbour sum, and a boundary cell divides by its own diagonal
+// lambda + count / h^2.  XZERO: the first sweep of a correction, whose initial iterate is
+// zero (not read).
+constexpr int kStripW = 60, kStripHMax = 64, kPre = 4;
 
 inline int strip_height(int n) { return std::min(kStripHMax, std::max(8, n / 32)); }
 
@@ -386,11 +389,23 @@ inline std::mutex& strip_cache_mutex() {
 }
 constexpr unsigned kFull = 0xffffffffu;
 
+template <typename real>
+struct Pair;
+template <>
+struct Pair<float> {
+  using T = float2;
+};
+template <>
+struct Pair<double> {
+  using T = double2;
+};
+
 struct StripGeom {
-  int n, c, x0, y0, y1;
+  int n, ca, cw, x0, y0, y1;
   bool out_lane;
 };
 
+// strip `start` of a level of (even) side n with strips of H rows, seen by lane `lane`
 __device__ __forceinline__ StripGeom strip_geom(int n, long long start, int H, int lane) {
   StripGeom g;
   const int nsx = (n + kStripW - 1) / kStripW;
@@ -399,9 +414,9 @@ __device__ __forceinline__ StripGeom strip_geom(int n, long long start, int H, i
   g.x0 = sx * kStripW;
   g.y0 = sy * H;
   g.y1 = min(g.y0 + H, n);
-  const int c = g.x0 - 2 + lane;
-  g.c = ((c % n) + n) % n;
-  g.out_lane = lane >= 2 && lane < 2 + kStripW && c < n;
+  g.ca = g.x0 - 2 + 2 * lane;  // the pair's first column before the periodic wrap
+  g.cw = ((g.ca % n) + n) % n;
+  g.out_lane = lane >= 1 && lane <= 30 && g.ca < n;
   return g;
 }
 
@@ -411,6 +426,7 @@ template <typename real, bool NEU, bool XZERO = false>
 __global__ void __launch_bounds__(128)
     sweep2d_kernel(MgState S, const real* __restrict__ xin, real* __restrict__ xout, const real* __restrict__ bl,
                    const Chunk* ch, int nch) {
+  using V2 = typename Pair<real>::T;
   const int lane = threadIdx.x & 31;
   const int wi = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (wi >= nch) return;
@@ -419,7 +435,7 @@ __global__ void __launch_bounds__(128)
   const InstDev& I = S.inst[C.inst];
   const int l = C.lev;
   const StripGeom g = strip_geom(I.n[l], C.start, C.count, lane);
-  const int n = g.n, c = g.c;
+  const int n = g.n, ca = g.ca, cw = g.cw;
   const real* x = xin + I.off[l];
   const real* b = bl + I.off[l];
   real* xo = xout + I.off[l];
@@ -427,58 +443,71 @@ __global__ void __launch_bounds__(128)
   // rows stay within one period of [0, n) when n > H + kPre + 2; else a full modulo
   const bool one_wrap = n > C.count + kPre + 2;
   auto rowof = [&](int r) { return one_wrap ? wrap_row(r, n) : ((r % n) + n) % n; };
-  const int craw = g.x0 - 2 + lane;  // this lane's column before the periodic wrap
-  const bool colin = craw >= 0 && craw < n;
+  const bool colin = ca >= 0 && ca < n;  // the pair lies in the domain (both or neither: n even)
   auto inside = [&](int r) { return !NEU || (colin && r >= 0 && r < n); };
-  // XZERO: the first sweep of a correction, whose initial iterate is zero (not read)
+  auto ld2 = [&](const real* p, int r) { return *reinterpret_cast<const V2*>(p + rowof(r) * n + cw); };
   auto ldx = [&](int r) {
-    if constexpr (XZERO) return real(0);
-    else return inside(r) ? x[rowof(r) * n + c] : real(0);
+    if constexpr (XZERO) return V2{real(0), real(0)};
+    else return inside(r) ? ld2(x, r) : V2{real(0), real(0)};
   };
-  auto ldb = [&](int r) { return b[rowof(r) * n + c]; };
-  // reciprocal diagonal of this lane's cell in row r
-  auto idg_at = [&](int r) {
+  auto ldb = [&](int r) { return ld2(b, r); };
+  // reciprocal diagonal of the pair's cell in column ca + e, row r
+  auto idg_at = [&](int e, int r) {
     if constexpr (!NEU) return idg;
-    const int m = (craw == 0) + (craw == n - 1) + (r == 0) + (r == n - 1);
+    const int c = ca + e;
+    const int m = (c == 0) + (c == n - 1) + (r == 0) + (r == n - 1);
     return idiag_of<real>(I, l, m);
   };
-  // red update of row r from old rows om, o0 (row r), op; black cells keep o0
-  auto red = [&](real om, real o0, real op, real bb, int r) {
-    const real lft = __shfl_up_sync(kFull, o0, 1), rgt = __shfl_down_sync(kFull, o0, 1);
-    const real v = (bb + (lft + rgt + om + op) * ih2) * idg_at(r);
-    return inside(r) ? (((c + rowof(r)) & 1) == 0 ? v : o0) : real(0);
+  // red update of row r from old rows om, o0 (row r), op: the red cell is the first of the
+  // pair on even rows (n even: the parity of r is that of its periodic image), the second on
+  // odd ones; the black cell keeps o0
+  auto red = [&](V2 om, V2 o0, V2 op, V2 bb, int r) {
+    V2 out;
+    if ((r & 1) == 0) {
+      const real lft = __shfl_up_sync(kFull, o0.y, 1);
+      out = V2{(bb.x + (lft + o0.y + om.x + op.x) * ih2) * idg_at(0, r), o0.y};
+    } else {
+      const real rgt = __shfl_down_sync(kFull, o0.x, 1);
+      out = V2{o0.x, (bb.y + (o0.x + rgt + om.y + op.y) * ih2) * idg_at(1, r)};
+    }
+    return inside(r) ? out : V2{real(0), real(0)};
   };
   const int y0 = g.y0, y1 = g.y1;
   // old rows y0-2 .. y0+1, red rows y0-1 and y0
-  real o_a = ldx(y0 - 2), o_b = ldx(y0 - 1), o_c = ldx(y0), o_d = ldx(y0 + 1);
-  real b_c = ldb(y0 - 1), b_d = ldb(y0);
-  real r_m = red(o_a, o_b, o_c, b_c, y0 - 1);
-  real r_0 = red(o_b, o_c, o_d, b_d, y0);
-  real b_0 = b_d;
+  V2 o_a = ldx(y0 - 2), o_b = ldx(y0 - 1), o_c = ldx(y0), o_d = ldx(y0 + 1);
+  V2 b_c = ldb(y0 - 1), b_d = ldb(y0);
+  V2 r_m = red(o_a, o_b, o_c, b_c, y0 - 1);
+  V2 r_0 = red(o_b, o_c, o_d, b_d, y0);
+  V2 b_0 = b_d;
   // prefetch ring: old rows s+2 .. s+1+kPre and right-hand sides of rows s+1 .. s+kPre
-  real px[kPre], pb[kPre];
+  V2 px[kPre], pb[kPre];
 #pragma unroll
   for (int k = 0; k < kPre; ++k) {
-    px[k] = y0 + 2 + k <= y1 + 1 ? ldx(y0 + 2 + k) : real(0);
-    pb[k] = y0 + 1 + k <= y1 ? ldb(y0 + 1 + k) : real(0);
+    px[k] = y0 + 2 + k <= y1 + 1 ? ldx(y0 + 2 + k) : V2{real(0), real(0)};
+    pb[k] = y0 + 1 + k <= y1 ? ldb(y0 + 1 + k) : V2{real(0), real(0)};
   }
-  real o_s = o_c, o_s1 = o_d;  // old rows s, s+1
+  V2 o_s = o_c, o_s1 = o_d;  // old rows s, s+1
 #pragma unroll 4
   for (int s = y0; s < y1; ++s) {
-    const real o_s2 = px[0], b_s1 = pb[0];
+    const V2 o_s2 = px[0], b_s1 = pb[0];
 #pragma unroll
     for (int k = 0; k + 1 < kPre; ++k) {
       px[k] = px[k + 1];
       pb[k] = pb[k + 1];
     }
-    px[kPre - 1] = s + 2 + kPre <= y1 + 1 ? ldx(s + 2 + kPre) : real(0);
-    pb[kPre - 1] = s + 1 + kPre <= y1 ? ldb(s + 1 + kPre) : real(0);
-    const real r_p = red(o_s, o_s1, o_s2, b_s1, s + 1);
-    // black cells of row s
-    const real lft = __shfl_up_sync(kFull, r_0, 1), rgt = __shfl_down_sync(kFull, r_0, 1);
-    const real v = (b_0 + (lft + rgt + r_m + r_p) * ih2) * idg_at(s);
-    const real outv = ((c + rowof(s)) & 1) == 1 ? v : r_0;
-    if (g.out_lane) xo[s * n + c] = outv;
+    px[kPre - 1] = s + 2 + kPre <= y1 + 1 ? ldx(s + 2 + kPre) : V2{real(0), real(0)};
+    pb[kPre - 1] = s + 1 + kPre <= y1 ? ldb(s + 1 + kPre) : V2{real(0), real(0)};
+    const V2 r_p = red(o_s, o_s1, o_s2, b_s1, s + 1);
+    // black cell of row s: the second of the pair on even rows, the first on odd ones
+    V2 outv;
+    if ((s & 1) == 0) {
+      const real rgt = __shfl_down_sync(kFull, r_0.x, 1);
+      outv = V2{r_0.x, (b_0.y + (r_0.x + rgt + r_m.y + r_p.y) * ih2) * idg_at(1, s)};
+    } else {
+      const real lft = __shfl_up_sync(kFull, r_0.y, 1);
+      outv = V2{(b_0.x + (lft + r_0.y + r_m.x + r_p.x) * ih2) * idg_at(0, s), r_0.y};
+    }
+    if (g.out_lane) *reinterpret_cast<V2*>(xo + s * n + ca) = outv;
     r_m = r_0;
     r_0 = r_p;
     b_0 = b_s1;
@@ -491,6 +520,7 @@ __global__ void __launch_bounds__(128)
 template <typename real>
 __global__ void __launch_bounds__(128) copy2d_kernel(MgState S, const real* __restrict__ xin, real* __restrict__ xout,
                                                      const Chunk* ch, int nch) {
+  using V2 = typename Pair<real>::T;
   const int lane = threadIdx.x & 31;
   const int wi = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (wi >= nch) return;
@@ -500,10 +530,66 @@ __global__ void __launch_bounds__(128) copy2d_kernel(MgState S, const real* __re
   const StripGeom g = strip_geom(I.n[C.lev], C.start, C.count, lane);
   if (!g.out_lane) return;
   const long long o = I.off[C.lev];
-  for (int s = g.y0; s < g.y1; ++s) xout[o + s * g.n + g.c] = xin[o + s * g.n + g.c];
+  for (int s = g.y0; s < g.y1; ++s)
+    *reinterpret_cast<V2*>(xout + o + s * g.n + g.ca) = *reinterpret_cast<const V2*>(xin + o + s * g.n + g.ca);
 }
 
 // 2D prolongation, one thread per coarse cell writing its four fine children
+// 2D residual and restriction, one thread per coarse cell: the 4 x 4 patch of fine iterate
+// values around its 2 x 2 children (corners excepted) is loaded once, then each child's
+// residual b - (lambda x - lap x) is formed with the neighbour sum in the order x-, x+, y-,
+// y+ (as nbsum) and the four are summed in x-fastest order (as resrestrict_kernel).
+template <typename real, bool NEU>
+__global__ void resrestrict2d_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
+  Chunk C = ch[blockIdx.x];
+  if (!S.active[C.inst] || threadIdx.x >= C.count) return;
+  const InstDev& I = S.inst[C.inst];
+  const int l = C.lev;
+  const int nc = I.n[l + 1], nf = I.n[l];
+  const unsigned t = (unsigned)C.start + threadIdx.x;  // coarse cell
+  const int cj = (int)(t / (unsigned)nc), ci = (int)(t - (unsigned)cj * (unsigned)nc);
+  const real* x = L.x + I.off[l];
+  const real* b = L.b + I.off[l];
+  const real ih2 = ih2_of<real>(I, l), lam = lam_of<real>(I);
+  const int x0 = 2 * ci, y0 = 2 * cj;
+  // patch columns x0-1 .. x0+2 and rows y0-1 .. y0+2: periodic images, or -1 outside a
+  // zero-flux boundary
+  const int col[4] = {x0 > 0 ? x0 - 1 : (NEU ? -1 : nf - 1), x0, x0 + 1, x0 + 2 < nf ? x0 + 2 : (NEU ? -1 : 0)};
+  const int row[4] = {y0 > 0 ? y0 - 1 : (NEU ? -1 : nf - 1), y0, y0 + 1, y0 + 2 < nf ? y0 + 2 : (NEU ? -1 : 0)};
+  real P[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const bool corner = (r == 0 || r == 3) && (c == 0 || c == 3);
+      P[r][c] = (!corner && row[r] >= 0 && col[c] >= 0) ? x[row[r] * nf + col[c]] : real(0);
+    }
+  real sum = real(0);
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const int a = o & 1, bb = o >> 1, r = 1 + bb, c = 1 + a;
+    const real xv = P[r][c];
+    int miss = 0;
+    real sn;
+    if constexpr (!NEU) {
+      sn = P[r][c - 1];
+      sn = sn + P[r][c + 1];
+      sn = sn + P[r - 1][c];
+      sn = sn + P[r + 1][c];
+    } else {
+      sn = real(0);
+      if (col[c - 1] >= 0) sn = sn + P[r][c - 1]; else ++miss;
+      if (col[c + 1] >= 0) sn = sn + P[r][c + 1]; else ++miss;
+      if (row[r - 1] >= 0) sn = sn + P[r - 1][c]; else ++miss;
+      if (row[r + 1] >= 0) sn = sn + P[r + 1][c]; else ++miss;
+    }
+    const real lap = (sn - real(4 - miss) * xv) * ih2;
+    sum = sum + (b[row[r] * nf + col[c]] - (lam * xv - lap));
+  }
+  L.b[I.off[l + 1] + t] = sum * real(0.25);
+  L.x[I.off[l + 1] + t] = real(0);
+}
+
 template <typename real, bool NEU>
 __global__ void prolong2d_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
   Chunk C = ch[blockIdx.x];
@@ -670,33 +756,54 @@ __device__ __forceinline__ FF ff_mul(FF a, float chi, float clo) {
 // re-evaluation of the stencil of X, which kept GB300's float64 pipe busy.  e is not zeroed
 // here (its neighbours are still being read): in 2D the next cycle's first pre-sweep starts
 // from zero without reading it, in 3D zero0_kernel follows.
-template <bool NEU>
-__global__ void update64_kernel(MgState S, Lvl<float> L, const Chunk* ch) {
-  Chunk C = ch[blockIdx.x];
+constexpr int kUpdCells = 4;  // cells per thread of update64_kernel: chunks of kUpdCells * kChunk cells
+
+template <bool NEU, int ND>
+__global__ void __launch_bounds__(kChunk) update64_kernel(MgState S, Lvl<float> L, const Chunk* ch) {
+  const Chunk C = ch[blockIdx.x];
   if (!S.active[C.inst]) return;
-  unsigned long long m = 0ull;
   const InstDev& I = S.inst[C.inst];
-  if (threadIdx.x < C.count) {
-    const long long t = C.start + threadIdx.x;
-    const int n = I.n[0];
-    int c[3];
-    cell_of(t, n, S.ndim, c);
-    const float* E = L.x + I.off[0];
+  const int n = I.n[0];
+  const unsigned un = (unsigned)n, plane = un * un;
+  const float* E = L.x + I.off[0];
+  float* Bf = L.b + I.off[0];
+  double* X = S.X + I.off0;
+  double* R = S.R + I.off0;
+  const float ih2hi = I.ih2f[0], ih2lo = I.ih2lo0, lamhi = I.lamf, lamlo = I.lamlo;
+  unsigned long long m = 0ull;
+  // cells start + threadIdx.x + k kChunk: each access of the k loop is coalesced
+#pragma unroll
+  for (int k = 0; k < kUpdCells; ++k) {
+    const int j = threadIdx.x + k * kChunk;
+    if (j >= C.count) break;
+    const unsigned t = (unsigned)C.start + (unsigned)j;
+    unsigned c[3] = {t % un, ND > 1 ? (t / un) % un : 0u, ND > 2 ? t / plane : 0u};
+    const unsigned stride[3] = {1u, un, plane};
     const float e = E[t];
-    // lap e * h^2 = sum of the neighbours - count e, in float-float
+    // lap e * h^2 = sum of the neighbours (x-, x+, y-, y+, z-, z+) - count e, in float-float
     FF sum{0.f, 0.f};
     int cnt = 0;
-    for (int d = 0; d < S.ndim; ++d) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
 #pragma unroll
       for (int side = -1; side <= 1; side += 2) {
-        int q[3] = {c[0], c[1], c[2]};
-        int u = c[d] + side;
-        if (u < 0 || u >= n) {
-          if (NEU) continue;
-          u = u < 0 ? u + n : u - n;
+        unsigned q;
+        if (side < 0) {
+          if (c[d] == 0u) {
+            if (NEU) continue;
+            q = t + (un - 1u) * stride[d];
+          } else {
+            q = t - stride[d];
+          }
+        } else {
+          if (c[d] == un - 1u) {
+            if (NEU) continue;
+            q = t - (un - 1u) * stride[d];
+          } else {
+            q = t + stride[d];
+          }
         }
-        q[d] = u;
-        sum = ff_add(sum, E[lin(q, n)]);
+        sum = ff_add(sum, E[q]);
         ++cnt;
       }
     }
@@ -704,16 +811,15 @@ __global__ void update64_kernel(MgState S, Lvl<float> L, const Chunk* ch) {
     const float ce_err = __fmaf_rn((float)cnt, e, -ce);
     sum = ff_add(sum, -ce);
     sum = ff_add(sum, -ce_err);
-    const FF lap = ff_mul(sum, I.ih2f[0], I.ih2lo0);
-    const FF le = ff_mul(FF{e, 0.f}, I.lamf, I.lamlo);
+    const FF lap = ff_mul(sum, ih2hi, ih2lo);
+    const FF le = ff_mul(FF{e, 0.f}, lamhi, lamlo);
     const FF ae = ff_sub(le, lap);
-    double* X = S.X + I.off0;
-    double* R = S.R + I.off0;
     X[t] = __dadd_rn(X[t], widen(e));
     const double r = __dsub_rn(R[t], __dadd_rn(widen(ae.hi), widen(ae.lo)));
     R[t] = r;
-    L.b[I.off[0] + t] = narrow<float>(r);
-    m = (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;  // |r| as bits
+    Bf[t] = narrow<float>(r);
+    const unsigned long long rb = (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;  // |r| bits
+    m = rb > m ? rb : m;
   }
   block_max_atomic(m, &S.rnorm[C.inst]);
 }
@@ -1128,6 +1234,7 @@ struct Mg {
   long long n0 = 0, nlevtot = 0;
   // chunk lists: level 0 cells; per depth: colour cells, coarse cells, fine cells
   std::vector<Chunk> ch0;
+  std::vector<Chunk> ch0q;  // level 0 in chunks of kUpdCells * kChunk cells (update64_kernel)
   std::vector<std::vector<Chunk>> ch_half, ch_coarse, ch_fine, ch_tile;
   std::vector<int> coarse_inst, coarse_row0;
   DevBuf d_yl;  // 2D: second iterate array for the tiled sweeps
@@ -1137,7 +1244,7 @@ struct Mg {
   cudaStream_t cstream = nullptr;   // captures the body of the device-side solve loop
   cudaGraphExec_t sgraph = nullptr; // one whole solve (device-side convergence loop)
   long long solve_loop_kernels = 0; // kernels per iteration of that loop
-  DevBuf d_ch0, d_chall, d_cinst, d_crow0;
+  DevBuf d_ch0, d_ch0q, d_chall, d_cinst, d_crow0;
   std::vector<size_t> off_half, off_coarse, off_fine, off_tile;
   int* h_any = nullptr;
   cudaGraphExec_t vgraph = nullptr;
@@ -1242,7 +1349,7 @@ struct Mg {
         I.off[l] = off;
         long long cells = 1;
         for (int d = 0; d < nd; ++d) cells *= m;
-        off += cells;
+        off += (cells + 3) & ~3LL;  // every level starts at a multiple of 4 cells (aligned pairs)
         double h = L / m;
         I.ih2[l] = 1.0 / (h * h);
         I.ih2f[l] = (float)I.ih2[l];
@@ -1270,10 +1377,13 @@ struct Mg {
     nlevtot = off;
     // chunk lists
     ch0.clear();
+    ch0q.clear();
     for (int i = 0; i < n_inst; ++i) {
       long long c = 1;
       for (int d = 0; d < nd; ++d) c *= insts[i].n[0];
       add_chunks(ch0, i, 0, c);
+      for (long long s0 = 0; s0 < c; s0 += kUpdCells * kChunk)
+        ch0q.push_back(Chunk{i, 0, s0, (int)std::min<long long>(kUpdCells * kChunk, c - s0)});
     }
     ch_half.assign(maxdepth, {});
     ch_coarse.assign(maxdepth, {});
@@ -1350,11 +1460,13 @@ struct Mg {
       all.insert(all.end(), ch_fine[l].begin(), ch_fine[l].end());
     }
     if ((rc = cuda(d_ch0.alloc(ch0.size() * sizeof(Chunk)), "alloc")) ||
+        (rc = cuda(d_ch0q.alloc(ch0q.size() * sizeof(Chunk)), "alloc")) ||
         (rc = cuda(d_chall.alloc(all.size() * sizeof(Chunk)), "alloc")) ||
         (rc = cuda(d_cinst.alloc(coarse_inst.size() * 4), "alloc")) ||
         (rc = cuda(d_crow0.alloc(coarse_row0.size() * 4), "alloc")))
       return rc;
     if ((rc = upload(d_ch0.p, ch0.data(), ch0.size() * sizeof(Chunk))) ||
+        (rc = upload(d_ch0q.p, ch0q.data(), ch0q.size() * sizeof(Chunk))) ||
         (rc = upload(d_chall.p, all.data(), all.size() * sizeof(Chunk))) ||
         (rc = upload(d_cinst.p, coarse_inst.data(), coarse_inst.size() * 4)) ||
         (rc = upload(d_crow0.p, coarse_row0.data(), coarse_row0.size() * 4)))
@@ -1504,10 +1616,18 @@ struct Mg {
     for (int l = 0; l + 1 < maxdepth; ++l) {
       smooth(l, nu1, true);
       if (!ch_coarse[l].empty()) {
-        if (neu)
-          resrestrict_kernel<real, true><<<(unsigned)ch_coarse[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
-        else
-          resrestrict_kernel<real, false><<<(unsigned)ch_coarse[l].size(), kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
+        const unsigned g = (unsigned)ch_coarse[l].size();
+        if (nd == 2) {
+          if (neu)
+            resrestrict2d_kernel<real, true><<<g, kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
+          else
+            resrestrict2d_kernel<real, false><<<g, kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
+        } else {
+          if (neu)
+            resrestrict_kernel<real, true><<<g, kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
+          else
+            resrestrict_kernel<real, false><<<g, kChunk, 0, stream>>>(S, Lv, all + off_coarse[l]);
+        }
         mark(kMgResRestrict);
       }
     }
@@ -1533,10 +1653,20 @@ struct Mg {
     // the correction and the new level-0 defect: float32 cycles update R by A e; float64
     // cycles correct X and re-evaluate the residual
     if constexpr (sizeof(real) == 4) {
-      if (neu)
-        update64_kernel<true><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
-      else
-        update64_kernel<false><<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());
+      {
+        const unsigned g = (unsigned)ch0q.size();
+        const Chunk* cq = d_ch0q.as<Chunk>();
+        if (nd == 2) {
+          if (neu) update64_kernel<true, 2><<<g, kChunk, 0, stream>>>(S, Lv, cq);
+          else update64_kernel<false, 2><<<g, kChunk, 0, stream>>>(S, Lv, cq);
+        } else if (nd == 3) {
+          if (neu) update64_kernel<true, 3><<<g, kChunk, 0, stream>>>(S, Lv, cq);
+          else update64_kernel<false, 3><<<g, kChunk, 0, stream>>>(S, Lv, cq);
+        } else {
+          if (neu) update64_kernel<true, 1><<<g, kChunk, 0, stream>>>(S, Lv, cq);
+          else update64_kernel<false, 1><<<g, kChunk, 0, stream>>>(S, Lv, cq);
+        }
+      }
       mark(kMgUpdate);
       if (nd != 2 || nu1 == 0) {  // 2D pre-sweeps never read the correction they start from
         zero0_kernel<<<(unsigned)ch0.size(), kChunk, 0, stream>>>(S, Lv, d_ch0.as<Chunk>());

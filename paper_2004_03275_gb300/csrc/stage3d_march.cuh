@@ -92,15 +92,24 @@ __device__ __forceinline__ void prim5(const float* u, float gm1, float* w) {
   w[4] = gm1 * (u[4] - 0.5f * (u[1] * vx + u[2] * vy + u[3] * vz));
 }
 
+// the two face values of the middle cell: (rho, v_x) and (v_y, v_z) as packed pairs, p alone
 template <int LIM>
 __device__ __forceinline__ void faces5(const float* wm, const float* w0, const float* wp, float* lo, float* hi) {
+  using namespace f32;
 #pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    float hm, hp;
-    f32::half_slopes<LIM>(w0[v] - wm[v], wp[v] - w0[v], hm, hp);
-    lo[v] = w0[v] - hm;
-    hi[v] = w0[v] + hp;
+  for (int q = 0; q < 2; ++q) {
+    const float2 m = make_float2(wm[2 * q], wm[2 * q + 1]), c = make_float2(w0[2 * q], w0[2 * q + 1]);
+    const float2 p = make_float2(wp[2 * q], wp[2 * q + 1]);
+    float2 hm, hp;
+    half_slopes2<LIM>(sub2(c, m), sub2(p, c), hm, hp);
+    const float2 l = sub2(c, hm), h = add2(c, hp);
+    lo[2 * q] = l.x, lo[2 * q + 1] = l.y;
+    hi[2 * q] = h.x, hi[2 * q + 1] = h.y;
   }
+  float hm, hp;
+  f32::half_slopes<LIM>(w0[4] - wm[4], wp[4] - w0[4], hm, hp);
+  lo[4] = w0[4] - hm;
+  hi[4] = w0[4] + hp;
 }
 
 // flux through a face normal to direction D (0 x, 1 y, 2 z) from face states L, R (W
@@ -433,13 +442,26 @@ __global__ void __launch_bounds__(128, 3) stage3d_z_kernel(StageArgs<float> a, G
           dc[v] = sD[v * kZVar + r * kZPlane];
           u0c[v] = a.stage1 ? 0.f : sU0[v * kZVar + r * kZPlane];
         }
+        // Un = U - dt (D + (F - Fp) / dz), then the SSPRK combination T + alpha (U^n - T);
+        // variables (0, 1) and (2, 3) as packed pairs, 4 alone
         float Un[NV];
+        {
+          using namespace f32;
+          const float2 mdt = bc2(-dt), iz = bc2(idz), al = bc2(a.alpha);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          float tmp = uc[v] - dt * (dc[v] + (F[v] - Fp[v]) * idz);
-          Un[v] = a.stage1 ? tmp : ssp_combine(a.alpha, a.beta, u0c[v], tmp);
-          Ol[v * NC + r * NT] = Un[v];
+          for (int q = 0; q < 2; ++q) {
+            const int v = 2 * q;
+            const float2 div = fma2(sub2(make_float2(F[v], F[v + 1]), make_float2(Fp[v], Fp[v + 1])), iz,
+                                    make_float2(dc[v], dc[v + 1]));
+            float2 t = fma2(mdt, div, make_float2(uc[v], uc[v + 1]));
+            if (!a.stage1) t = fma2(al, sub2(make_float2(u0c[v], u0c[v + 1]), t), t);
+            Un[v] = t.x, Un[v + 1] = t.y;
+          }
+          const float tmp = uc[4] - dt * (dc[4] + (F[4] - Fp[4]) * idz);
+          Un[4] = a.stage1 ? tmp : ssp_combine(a.alpha, a.beta, u0c[4], tmp);
         }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Ol[v * NC + r * NT] = Un[v];
         if constexpr (LAST) {
           float wn[NV];
           march3::prim5(Un, gm1, wn);
