@@ -277,7 +277,8 @@ int mg_kernel_launches(const mg_handle* h, long long* n);
  * after each: kind[i] and us[i] = microseconds between consecutive events for kernel i, for
  * up to cap kernels; *nkernels = kernels of the cycle.  Kinds: 0 2D red-black sweep, 1 copy,
  * 2 3D half sweep, 3 residual + restriction, 4 coarsest solve, 5 prolongation, 6 float32
- * update (X += e, R -= A e), 7 zero correction, 8 float64 correction, 9 float64 defect.
+ * update (X += e, R -= A e), 7 zero correction, 8 float64 correction, 9 float64 defect,
+ * 10 the coarse depths of 2D instances in shared memory (one CTA per instance).
  * The iterate advances by that cycle.  Synchronous; for measurement only.
  * AMR_ERR_INVALID_ARG before the first mg_solve. */
 int mg_profile_vcycle(mg_handle* h, int* kind, float* us, int cap, int* nkernels);

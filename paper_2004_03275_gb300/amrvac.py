@@ -551,7 +551,7 @@ class MgSolver:
         return cyc, rr
 
     MG_KINDS = ("sweep", "copy", "smooth3d", "resrestrict", "coarse", "prolong", "update", "zero", "correct64",
-                "residual64")
+                "residual64", "coarse_cycle")
 
     def profile_vcycle(self, cap=4096):
         """One more V-cycle (after a solve), kernel by kernel: [(kind name, microseconds)]."""

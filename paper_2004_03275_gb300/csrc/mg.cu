@@ -63,6 +63,7 @@ struct InstDev {
   float idiagf[kMaxLev][7];     // Neumann boundary (m = 0 inside and on periodic grids)
   long long off0;          // offset into X / B
   long long inv_off;       // offset into the coarsest inverse matrices
+  int dsm;                 // 2D: first depth whose V-cycle part runs in shared memory, or -1
 };
 
 struct MgState {
@@ -80,6 +81,7 @@ struct MgState {
   int* any;                   // any instance active (for the host)
   int* iters;                 // loop iterations of the current solve (device-side loop cap)
   const double* inv;          // dense inverses of the coarsest operators
+  const float* invf;          // the same rounded to float32 (float32 cycles solve in float32)
   int ndim;
   int neu;                    // Neumann (zero-flux) boundaries, else periodic
   double rtol;
@@ -535,22 +537,14 @@ __global__ void __launch_bounds__(128) copy2d_kernel(MgState S, const real* __re
 }
 
 // 2D prolongation, one thread per coarse cell writing its four fine children
-// 2D residual and restriction, one thread per coarse cell: the 4 x 4 patch of fine iterate
-// values around its 2 x 2 children (corners excepted) is loaded once, then each child's
-// residual b - (lambda x - lap x) is formed with the neighbour sum in the order x-, x+, y-,
-// y+ (as nbsum) and the four are summed in x-fastest order (as resrestrict_kernel).
+// 2D residual and restriction of coarse cell (ci, cj): the 4 x 4 patch of fine iterate values
+// around its 2 x 2 children (corners excepted) is loaded once, then each child's residual
+// b - (lambda x - lap x) is formed with the neighbour sum in the order x-, x+, y-, y+ (as
+// nbsum) and the four are summed in x-fastest order (as resrestrict_kernel).  x, b: the fine
+// level (global or shared memory); nf its side.
 template <typename real, bool NEU>
-__global__ void resrestrict2d_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
-  Chunk C = ch[blockIdx.x];
-  if (!S.active[C.inst] || threadIdx.x >= C.count) return;
-  const InstDev& I = S.inst[C.inst];
-  const int l = C.lev;
-  const int nc = I.n[l + 1], nf = I.n[l];
-  const unsigned t = (unsigned)C.start + threadIdx.x;  // coarse cell
-  const int cj = (int)(t / (unsigned)nc), ci = (int)(t - (unsigned)cj * (unsigned)nc);
-  const real* x = L.x + I.off[l];
-  const real* b = L.b + I.off[l];
-  const real ih2 = ih2_of<real>(I, l), lam = lam_of<real>(I);
+__device__ __forceinline__ real restrict_cell2d(const real* x, const real* b, int nf, int ci, int cj, real ih2,
+                                                real lam) {
   const int x0 = 2 * ci, y0 = 2 * cj;
   // patch columns x0-1 .. x0+2 and rows y0-1 .. y0+2: periodic images, or -1 outside a
   // zero-flux boundary
@@ -586,8 +580,54 @@ __global__ void resrestrict2d_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
     const real lap = (sn - real(4 - miss) * xv) * ih2;
     sum = sum + (b[row[r] * nf + col[c]] - (lam * xv - lap));
   }
-  L.b[I.off[l + 1] + t] = sum * real(0.25);
+  return sum * real(0.25);
+}
+
+// 2D residual and restriction, one thread per coarse cell
+template <typename real, bool NEU>
+__global__ void resrestrict2d_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
+  Chunk C = ch[blockIdx.x];
+  if (!S.active[C.inst] || threadIdx.x >= C.count) return;
+  const InstDev& I = S.inst[C.inst];
+  const int l = C.lev;
+  const int nc = I.n[l + 1], nf = I.n[l];
+  const unsigned t = (unsigned)C.start + threadIdx.x;  // coarse cell
+  const int cj = (int)(t / (unsigned)nc), ci = (int)(t - (unsigned)cj * (unsigned)nc);
+  L.b[I.off[l + 1] + t] =
+      restrict_cell2d<real, NEU>(L.x + I.off[l], L.b + I.off[l], nf, ci, cj, ih2_of<real>(I, l), lam_of<real>(I));
   L.x[I.off[l + 1] + t] = real(0);
+}
+
+// 2D prolongation of coarse cell (ci, cj) of ec (side nc) onto its four children in xf (side
+// nf): bilinear weights 9/16, 3/16, 3/16, 1/16 in the order (x, y) = (0,0), (1,0), (0,1), (1,1),
+// the coarse cell itself beyond a zero-flux boundary
+template <typename real, bool NEU>
+__device__ __forceinline__ void prolong_cell2d(const real* ec, real* xf, int nc, int nf, int ci, int cj) {
+  real v[3][3];
+#pragma unroll
+  for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+    for (int di = -1; di <= 1; ++di)
+      v[dj + 1][di + 1] = ec[nbr_or_self(cj + dj, cj, nc, NEU) * nc + nbr_or_self(ci + di, ci, nc, NEU)];
+  // each row pair of children as one vector (nf even, level offsets multiples of 4 cells)
+  using V2 = typename Pair<real>::T;
+#pragma unroll
+  for (int b2 = 0; b2 < 2; ++b2) {
+    const int sy = b2 ? 1 : -1;
+    real acc[2];
+#pragma unroll
+    for (int a2 = 0; a2 < 2; ++a2) {
+      const int sx = a2 ? 1 : -1;
+      acc[a2] = real(0);
+      acc[a2] = acc[a2] + real(0.5625) * v[1][1];
+      acc[a2] = acc[a2] + real(0.1875) * v[1][1 + sx];
+      acc[a2] = acc[a2] + real(0.1875) * v[1 + sy][1];
+      acc[a2] = acc[a2] + real(0.0625) * v[1 + sy][1 + sx];
+    }
+    V2* q = reinterpret_cast<V2*>(xf + (2 * cj + b2) * nf + 2 * ci);
+    const V2 o = *q;
+    *q = V2{o.x + acc[0], o.y + acc[1]};
+  }
 }
 
 template <typename real, bool NEU>
@@ -599,29 +639,7 @@ __global__ void prolong2d_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
   const int nf = I.n[l], nc = I.n[l + 1];
   unsigned t = (unsigned)(C.start + threadIdx.x);  // coarse cell
   int cj = (int)(t / (unsigned)nc), ci = (int)(t - (unsigned)cj * (unsigned)nc);
-  const real* ec = L.x + I.off[l + 1];
-  constexpr bool neu = NEU;
-  real v[3][3];
-#pragma unroll
-  for (int dj = -1; dj <= 1; ++dj)
-#pragma unroll
-    for (int di = -1; di <= 1; ++di)
-      v[dj + 1][di + 1] = ec[(long long)nbr_or_self(cj + dj, cj, nc, neu) * nc + nbr_or_self(ci + di, ci, nc, neu)];
-  real* xf = L.x + I.off[l];
-#pragma unroll
-  for (int b2 = 0; b2 < 2; ++b2)
-#pragma unroll
-    for (int a2 = 0; a2 < 2; ++a2) {
-      int sx = a2 ? 1 : -1, sy = b2 ? 1 : -1;
-      // corners in the order (x, y) = (0,0), (1,0), (0,1), (1,1), weights 9/16, 3/16, 3/16, 1/16
-      real acc = real(0);
-      acc = acc + real(0.5625) * v[1][1];
-      acc = acc + real(0.1875) * v[1][1 + sx];
-      acc = acc + real(0.1875) * v[1 + sy][1];
-      acc = acc + real(0.0625) * v[1 + sy][1 + sx];
-      long long q = (long long)(2 * cj + b2) * nf + 2 * ci + a2;
-      xf[q] = xf[q] + acc;
-    }
+  prolong_cell2d<real, NEU>(L.x + I.off[l + 1], L.x + I.off[l], nc, nf, ci, cj);
 }
 
 // residual of level l restricted to level l+1 (mean of the 2^ndim children), x_{l+1} = 0
@@ -684,6 +702,21 @@ __global__ void prolong_kernel(MgState S, Lvl<real> L, const Chunk* ch) {
 }
 
 // coarsest level: x = inverse(A) b, float64, a warp per row
+// float32 cycles: the float32 inverse and float32 sums (the correction is float32 anyway, and
+// GB300's float64 pipe made the float64 product the slowest kernel of the coarse levels)
+__device__ __forceinline__ float coarse_row(const float* A, int r, int m, const float* b, int lane) {
+  float acc = 0.f;
+  for (int c = lane; c < m; c += 32) acc = fmaf(A[(size_t)r * m + c], b[c], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
+}
+__device__ __forceinline__ double coarse_row(const double* A, int r, int m, const double* b, int lane) {
+  double acc = 0.0;
+  for (int c = lane; c < m; c += 32) acc += A[(size_t)r * m + c] * b[c];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
+}
+
 template <typename real>
 __global__ void coarse_kernel(MgState S, Lvl<real> L, const int* insts, const int* rows0, int nitems) {
   int item = blockIdx.x;
@@ -696,13 +729,120 @@ __global__ void coarse_kernel(MgState S, Lvl<real> L, const int* insts, const in
   for (int d = 1; d < S.ndim; ++d) m *= n;
   const real* b = L.b + I.off[l];
   real* x = L.x + I.off[l];
-  const double* A = S.inv + I.inv_off;
+  const real* A;
+  if constexpr (sizeof(real) == 4) A = S.invf + I.inv_off;
+  else A = S.inv + I.inv_off;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int r = rows0[item] + warp; r < min(m, rows0[item] + 64); r += blockDim.x / 32) {
-    double acc = 0.0;
-    for (int c = lane; c < m; c += 32) acc += A[(size_t)r * m + c] * (double)b[c];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) x[r] = (real)acc;
+    const real acc = coarse_row(A, r, m, b, lane);
+    if (lane == 0) x[r] = acc;
+  }
+}
+
+// The coarse part of a 2D V-cycle of one instance in shared memory, one CTA per instance:
+// depths I.dsm .. nlev - 1 (sides up to 128 in float32, 64 in float64).  It takes the
+// right-hand side of depth dsm from the restriction above it and returns the correction of
+// that depth, doing in between what the per-depth kernels do, in their order and with their
+// arithmetic: nu1 red-black sweeps from a zero correction (each an in-place red pass, then a
+// black pass, as the strip sweep computes them), residual and restriction, the dense solve
+// of the coarsest level, then prolongation and nu2 sweeps back up.  A block barrier separates
+// the passes.  Shared layout per depth: x, then b, each padded to 4 cells.
+constexpr int kCoarseThreads = 1024;
+constexpr int kCoarseSideF32 = 128, kCoarseSideF64 = 64;  // largest side of its first depth
+
+template <typename real, bool NEU>
+__global__ void __launch_bounds__(kCoarseThreads)
+    coarse2d_kernel(MgState S, Lvl<real> L, const int* insts, int nu1, int nu2) {
+  extern __shared__ __align__(16) unsigned char cv_smem[];
+  real* sm = reinterpret_cast<real*>(cv_smem);
+  const int i = insts[blockIdx.x];
+  if (!S.active[i]) return;
+  const InstDev& I = S.inst[i];
+  const int d0 = I.dsm, nl = I.nlev, tid = threadIdx.x;
+  __shared__ int so[kMaxLev];  // shared offset of each depth's x
+  if (tid == 0) {
+    int o = 0;
+    for (int l = d0; l < nl; ++l) {
+      so[l] = o;
+      o += 2 * ((I.n[l] * I.n[l] + 3) & ~3);
+    }
+  }
+  __syncthreads();
+  auto X = [&](int l) { return sm + so[l]; };
+  auto Bv = [&](int l) { return sm + so[l] + ((I.n[l] * I.n[l] + 3) & ~3); };
+  {
+    const int m = I.n[d0] * I.n[d0];
+    const real* bg = L.b + I.off[d0];
+    for (int c = tid; c < m; c += kCoarseThreads) {
+      Bv(d0)[c] = bg[c];
+      X(d0)[c] = real(0);
+    }
+  }
+  __syncthreads();
+  // one red-black sweep of depth l in place: cells (c + r) even, then odd; neighbour sums in
+  // the order x-, x+, y-, y+, cells beyond a zero-flux boundary read as zero
+  // threads as 16 rows x 64 cells of one colour (a side of at most 128)
+  const int tx = tid & 63, ty = tid >> 6;
+  auto sweep = [&](int l) {
+    const int n = I.n[l], hn = n / 2;
+    real* x = X(l);
+    const real* b = Bv(l);
+    const real ih2 = ih2_of<real>(I, l), idg = idiag_of<real>(I, l, 0);
+    for (int colour = 0; colour < 2; ++colour) {
+      for (int r = ty; r < n; r += kCoarseThreads / 64)
+        for (int k = tx; k < hn; k += 64) {
+          const int c = 2 * k + ((r + colour) & 1);
+          const int cm = c > 0 ? c - 1 : n - 1, cp = c + 1 < n ? c + 1 : 0;
+          const int rm = r > 0 ? r - 1 : n - 1, rp = r + 1 < n ? r + 1 : 0;
+          real lft = x[r * n + cm], rgt = x[r * n + cp], dn = x[rm * n + c], up = x[rp * n + c];
+          real d = idg;
+          if constexpr (NEU) {
+            lft = c > 0 ? lft : real(0);
+            rgt = c + 1 < n ? rgt : real(0);
+            dn = r > 0 ? dn : real(0);
+            up = r + 1 < n ? up : real(0);
+            d = idiag_of<real>(I, l, (c == 0) + (c == n - 1) + (r == 0) + (r == n - 1));
+          }
+          x[r * n + c] = (b[r * n + c] + (lft + rgt + dn + up) * ih2) * d;
+        }
+      __syncthreads();
+    }
+  };
+  for (int l = d0; l + 1 < nl; ++l) {
+    for (int s2 = 0; s2 < nu1; ++s2) sweep(l);
+    const int nc = I.n[l + 1];
+    for (int t = tid; t < nc * nc; t += kCoarseThreads) {
+      const int cj = t / nc, ci = t - cj * nc;
+      Bv(l + 1)[t] = restrict_cell2d<real, NEU>(X(l), Bv(l), I.n[l], ci, cj, ih2_of<real>(I, l), lam_of<real>(I));
+      X(l + 1)[t] = real(0);
+    }
+    __syncthreads();
+  }
+  {
+    const int m = I.n[nl - 1] * I.n[nl - 1];
+    const real* A;
+    if constexpr (sizeof(real) == 4) A = S.invf + I.inv_off;
+    else A = S.inv + I.inv_off;
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int r = warp; r < m; r += kCoarseThreads / 32) {
+      const real acc = coarse_row(A, r, m, Bv(nl - 1), lane);
+      if (lane == 0) X(nl - 1)[r] = acc;
+    }
+    __syncthreads();
+  }
+  for (int l = nl - 2; l >= d0; --l) {
+    const int nc = I.n[l + 1];
+    for (int t = tid; t < nc * nc; t += kCoarseThreads) {
+      const int cj = t / nc, ci = t - cj * nc;
+      prolong_cell2d<real, NEU>(X(l + 1), X(l), nc, I.n[l], ci, cj);
+    }
+    __syncthreads();
+    for (int s2 = 0; s2 < nu2; ++s2) sweep(l);
+  }
+  {
+    const int m = I.n[d0] * I.n[d0];
+    real* xg = L.x + I.off[d0];
+    for (int c = tid; c < m; c += kCoarseThreads) xg[c] = X(d0)[c];
   }
 }
 
@@ -1219,7 +1359,8 @@ enum MgKind {
   kMgUpdate = 6,       // float32 cycles: X += e, R -= A e (float-float)
   kMgZero = 7,         // float32 cycles: zero the level-0 correction
   kMgCorrect = 8,      // float64 cycles: X += e
-  kMgResidual = 9      // float64 cycles: new level-0 defect
+  kMgResidual = 9,     // float64 cycles: new level-0 defect
+  kMgCoarseCycle = 10  // 2D: the coarse depths of the cycle in shared memory
 };
 
 struct Mg {
@@ -1239,12 +1380,16 @@ struct Mg {
   std::vector<int> coarse_inst, coarse_row0;
   DevBuf d_yl;  // 2D: second iterate array for the tiled sweeps
   DevBuf d_R;  // float32 V-cycles: level-0 float64 defect
-  DevBuf d_inst, d_X, d_B, d_xl, d_bl, d_rnorm, d_bnorm, d_lastres, d_initres, d_active, d_cycles, d_failed, d_any, d_inv;
+  DevBuf d_inst, d_X, d_B, d_xl, d_bl, d_rnorm, d_bnorm, d_lastres, d_initres, d_active, d_cycles, d_failed, d_any, d_inv, d_invf;
   DevBuf d_iters;
   cudaStream_t cstream = nullptr;   // captures the body of the device-side solve loop
   cudaGraphExec_t sgraph = nullptr; // one whole solve (device-side convergence loop)
   long long solve_loop_kernels = 0; // kernels per iteration of that loop
-  DevBuf d_ch0, d_ch0q, d_chall, d_cinst, d_crow0;
+  DevBuf d_ch0, d_ch0q, d_chall, d_cinst, d_crow0, d_sinst;
+  std::vector<int> smem_inst;  // 2D instances whose coarse depths run in shared memory
+  size_t smem_bytes = 0;       // the largest such instance's levels
+  // per-depth kernels run on depths 0 .. per_depth_end - 1 of an instance
+  static int per_depth_end(const InstDev& I) { return I.dsm >= 0 ? I.dsm : I.nlev - 1; }
   std::vector<size_t> off_half, off_coarse, off_fine, off_tile;
   int* h_any = nullptr;
   cudaGraphExec_t vgraph = nullptr;
@@ -1299,6 +1444,7 @@ struct Mg {
     S.any = d_any.as<int>();
     S.iters = d_iters.as<int>();
     S.inv = d_inv.as<double>();
+    S.invf = d_invf.as<float>();
     S.ndim = nd;
     S.neu = neu ? 1 : 0;
     S.rtol = rtol;
@@ -1364,6 +1510,15 @@ struct Mg {
       }
       I.nlev = l;
       I.ih2lo0 = (float)(I.ih2[0] - (double)I.ih2f[0]);
+      // 2D: the depths from the first one (below 0) whose side fits the shared-memory coarse
+      // cycle run in one CTA; instances with a single level keep the per-depth kernels
+      I.dsm = -1;
+      if (nd == 2 && l >= 2)
+        for (int d = 1; d < l; ++d)
+          if (I.n[d] <= (prec == AMR_FP64 ? kCoarseSideF64 : kCoarseSideF32)) {
+            I.dsm = d;
+            break;
+          }
       maxdepth = std::max(maxdepth, l);
       int mc = I.n[l - 1];
       long long msz = 1;
@@ -1391,9 +1546,11 @@ struct Mg {
     ch_tile.assign(maxdepth, {});
     coarse_inst.clear();
     coarse_row0.clear();
+    smem_inst.clear();
+    smem_bytes = 0;
     for (int i = 0; i < n_inst; ++i) {
       const InstDev& I = insts[i];
-      for (int l = 0; l + 1 < I.nlev; ++l) {
+      for (int l = 0; l < per_depth_end(I); ++l) {
         long long cf = 1, cc = 1;
         for (int d = 0; d < nd; ++d) {
           cf *= I.n[l];
@@ -1402,6 +1559,13 @@ struct Mg {
         add_chunks(ch_half[l], i, l, cf / 2);
         add_chunks(ch_coarse[l], i, l, cc);
         add_chunks(ch_fine[l], i, l, cf);
+      }
+      if (I.dsm >= 0) {
+        smem_inst.push_back(i);
+        size_t cells = 0;
+        for (int l = I.dsm; l < I.nlev; ++l) cells += 2 * ((I.n[l] * I.n[l] + 3) & ~3);
+        smem_bytes = std::max(smem_bytes, cells * (precision == AMR_FP64 ? 8 : 4));
+        continue;
       }
       long long m = 1;
       for (int d = 0; d < nd; ++d) m *= I.n[I.nlev - 1];
@@ -1423,7 +1587,8 @@ struct Mg {
         (rc = cuda(d_active.alloc(n_inst * 4), "alloc")) ||
         (rc = cuda(d_cycles.alloc(n_inst * 4), "alloc")) || (rc = cuda(d_failed.alloc(n_inst * 4), "alloc")) ||
         (rc = cuda(d_any.alloc(4), "alloc")) || (rc = cuda(d_iters.alloc(4), "alloc")) ||
-        (rc = cuda(d_inv.alloc(invoff * 8), "alloc inverse")))
+        (rc = cuda(d_inv.alloc(invoff * 8), "alloc inverse")) ||
+        (rc = cuda(d_invf.alloc(invoff * 4), "alloc inverse")))
       return rc;
     if ((rc = cuda(cudaMallocHost(&h_any, 4), "host alloc"))) return rc;
     // host-to-device copy of a table (empty tables copy nothing)
@@ -1431,14 +1596,20 @@ struct Mg {
       return bytes ? cuda(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice), "copy table") : AMR_OK;
     };
     if ((rc = upload(d_inst.p, insts.data(), insts.size() * sizeof(InstDev)))) return rc;
-    for (int i = 0; i < n_inst; ++i)
-      if ((rc = upload(d_inv.as<double>() + insts[i].inv_off, invs[i].data(), invs[i].size() * 8))) return rc;
+    {
+      std::vector<float> f;
+      for (int i = 0; i < n_inst; ++i) {
+        if ((rc = upload(d_inv.as<double>() + insts[i].inv_off, invs[i].data(), invs[i].size() * 8))) return rc;
+        f.assign(invs[i].begin(), invs[i].end());
+        if ((rc = upload(d_invf.as<float>() + insts[i].inv_off, f.data(), f.size() * 4))) return rc;
+      }
+    }
     if ((rc = cuda(cudaMemset(d_rnorm.p, 0, n_inst * 8), "memset"))) return rc;
     if (nd == 2) {  // strip heights: measured per level side, then the tile lists
       if ((rc = precision == AMR_FP64 ? tune_strips<double>() : tune_strips<float>())) return rc;
       for (int i = 0; i < n_inst; ++i) {
         const InstDev& I = insts[i];
-        for (int l = 0; l + 1 < I.nlev; ++l) {
+        for (int l = 0; l < per_depth_end(I); ++l) {
           const int H = height_for(l, I.n[l]);
           for (int k = 0; k < tiles_of(I.n[l], H); ++k) ch_tile[l].push_back(Chunk{i, l, k, H});
         }
@@ -1463,14 +1634,27 @@ struct Mg {
         (rc = cuda(d_ch0q.alloc(ch0q.size() * sizeof(Chunk)), "alloc")) ||
         (rc = cuda(d_chall.alloc(all.size() * sizeof(Chunk)), "alloc")) ||
         (rc = cuda(d_cinst.alloc(coarse_inst.size() * 4), "alloc")) ||
-        (rc = cuda(d_crow0.alloc(coarse_row0.size() * 4), "alloc")))
+        (rc = cuda(d_crow0.alloc(coarse_row0.size() * 4), "alloc")) ||
+        (rc = cuda(d_sinst.alloc(smem_inst.size() * 4), "alloc")))
       return rc;
     if ((rc = upload(d_ch0.p, ch0.data(), ch0.size() * sizeof(Chunk))) ||
         (rc = upload(d_ch0q.p, ch0q.data(), ch0q.size() * sizeof(Chunk))) ||
         (rc = upload(d_chall.p, all.data(), all.size() * sizeof(Chunk))) ||
         (rc = upload(d_cinst.p, coarse_inst.data(), coarse_inst.size() * 4)) ||
-        (rc = upload(d_crow0.p, coarse_row0.data(), coarse_row0.size() * 4)))
+        (rc = upload(d_crow0.p, coarse_row0.data(), coarse_row0.size() * 4)) ||
+        (rc = upload(d_sinst.p, smem_inst.data(), smem_inst.size() * 4)))
       return rc;
+    if (!smem_inst.empty()) {
+      const int sb = (int)smem_bytes;
+      cudaError_t e = cudaSuccess;
+      if (precision == AMR_FP64)
+        e = neu ? cudaFuncSetAttribute(coarse2d_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb)
+                : cudaFuncSetAttribute(coarse2d_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+      else
+        e = neu ? cudaFuncSetAttribute(coarse2d_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb)
+                : cudaFuncSetAttribute(coarse2d_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+      if ((rc = cuda(e, "coarse cycle shared memory"))) return rc;
+    }
     return cuda(cudaDeviceSynchronize(), "setup");
   }
 
@@ -1505,7 +1689,7 @@ struct Mg {
       std::vector<int> sides;  // instances swept at this depth
       std::vector<int> who;
       for (int i = 0; i < ninst; ++i)
-        if (l + 1 < insts[i].nlev) {
+        if (l < per_depth_end(insts[i])) {
           sides.push_back(insts[i].n[l]);
           who.push_back(i);
         }
@@ -1562,7 +1746,7 @@ struct Mg {
     if (!rc) rc = cuda(cudaGetLastError(), "tuning");
     if (!rc)
       for (int i = 0; i < ninst; ++i)
-        for (int l = 0; l + 1 < insts[i].nlev; ++l)
+        for (int l = 0; l < per_depth_end(insts[i]); ++l)
           if (!strip_h.count(insts[i].n[l])) strip_h[insts[i].n[l]] = height_for(l, insts[i].n[l]);
     return rc;
   }
@@ -1631,9 +1815,19 @@ struct Mg {
         mark(kMgResRestrict);
       }
     }
-    coarse_kernel<real><<<(unsigned)coarse_inst.size(), 256, 0, stream>>>(S, Lv, d_cinst.as<int>(), d_crow0.as<int>(),
-                                                                          (int)coarse_inst.size());
-    mark(kMgCoarse);
+    if (!coarse_inst.empty()) {
+      coarse_kernel<real><<<(unsigned)coarse_inst.size(), 256, 0, stream>>>(S, Lv, d_cinst.as<int>(),
+                                                                            d_crow0.as<int>(), (int)coarse_inst.size());
+      mark(kMgCoarse);
+    }
+    if (!smem_inst.empty()) {
+      const unsigned g = (unsigned)smem_inst.size();
+      if (neu)
+        coarse2d_kernel<real, true><<<g, kCoarseThreads, smem_bytes, stream>>>(S, Lv, d_sinst.as<int>(), nu1, nu2);
+      else
+        coarse2d_kernel<real, false><<<g, kCoarseThreads, smem_bytes, stream>>>(S, Lv, d_sinst.as<int>(), nu1, nu2);
+      mark(kMgCoarseCycle);
+    }
     for (int l = maxdepth - 2; l >= 0; --l) {
       if (nd == 2 && !ch_coarse[l].empty()) {
         if (neu)

@@ -234,13 +234,15 @@ def test_autotuned_strip_heights():
     the fastest; the heights are candidates, a side that is not swept has none, and the
     solve reaches the oracle's solution whatever was chosen (every height gives the same
     iterate)."""
-    sizes, L = [96, 80, 144], 2.1
+    sizes, L = [256, 160, 288], 2.1
     lam, bs = batch(sizes, 2, 13)
     s = amrvac.MgSolver(2, sizes, lam, L, precision="fp64")
-    for n in (96, 48, 24, 12, 80, 40, 20, 10, 144, 72, 36, 18):
+    # strip sweeps run above the shared-memory coarse cycle (float64: from the first side <= 64)
+    for n in (256, 128, 160, 80, 288, 144, 72):
         assert s.strip_height(n) in (4, 8, 16, 32, 64), n
-    with pytest.raises(amrvac.AmrError):
-        s.strip_height(6)  # the coarsest side of 96: solved densely, never swept
+    for n in (64, 40, 36, 5):  # depths of the shared-memory cycle, and a coarsest side
+        with pytest.raises(amrvac.AmrError):
+            s.strip_height(n)
     x = np.zeros(s.n)
     s.solve(pack(bs), x)
     xs = unpack(x, sizes, 2)
@@ -252,9 +254,10 @@ def test_autotuned_strip_heights():
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_profile_vcycle_is_one_more_cycle(precision):
     """mg_profile_vcycle runs one V-cycle kernel by kernel: before any solve it is refused; after
-    a solve it reports every kernel of the cycle (the sweeps, one residual-restriction and one
-    prolongation per depth above the coarsest, one coarse solve, and the level-0 update of the
-    precision), each with a positive time, and the handle stays usable."""
+    a solve it reports every kernel of the cycle (the sweeps, residual-restriction and
+    prolongation of the depths above the shared-memory ones, the shared-memory coarse cycle,
+    and the level-0 update of the precision), each with a positive time, and the handle stays
+    usable."""
     sizes, L = [64, 48, 32], 1.3
     lam, bs = batch(sizes, 2, 21)
     s = amrvac.MgSolver(2, sizes, lam, L, rtol=1e-4, precision=precision)
@@ -265,10 +268,10 @@ def test_profile_vcycle_is_one_more_cycle(precision):
     s.solve(b, x)
     prof = s.profile_vcycle()
     kinds = [k for k, _ in prof]
-    depths = 3  # 64 -> 32 -> 16 -> 8: the largest instance has the most depths
-    assert kinds.count("sweep") == 4 * depths
-    assert kinds.count("resrestrict") == depths and kinds.count("prolong") == depths
-    assert kinds.count("coarse") == 1
+    # depth 0 by per-depth kernels (2 + 2 sweeps, one restriction, one prolongation); the coarse
+    # depths (sides <= 128 in float32, <= 64 in float64) of every instance in shared memory
+    assert kinds.count("sweep") == 4 and kinds.count("resrestrict") == 1 and kinds.count("prolong") == 1
+    assert kinds.count("coarse_cycle") == 1 and kinds.count("coarse") == 0
     # float32 cycles end with the defect update (in 2D the next cycle's first pre-sweep starts
     # from a zero correction without reading it, so no zeroing kernel follows)
     tail = ["sweep", "update"] if precision == "fp32" else ["correct64", "residual64"]
