@@ -138,7 +138,11 @@ cudaError_t stage2d_f32_launch(const StageArgs<float>& a, const Geometry& G, cud
   return cudaGetLastError();
 }
 
-// float32 3D, 16^3 leaves: xy pass then z pass (4 CTAs of 4 warps per leaf each)
+// float32 3D, 16^3 leaves: xy pass (4 CTAs of 4 warps per leaf), then z pass (kZRows rows of
+// the leaf per CTA; 4 with the fused reduction).  Rows per CTA measured on the blast step:
+// 2 rows (6 CTAs of 2 warps per SM) 0.74 ms, 4 rows (3 CTAs of 4 warps) 0.70 ms.
+constexpr int kZRows = 4;
+
 template <int FLUX, int LIM>
 void stage3d_f32_go(const StageArgs<float>& a, const Geometry& G, cudaStream_t s) {
   const int grid = a.nleaves * 4;
@@ -146,7 +150,8 @@ void stage3d_f32_go(const StageArgs<float>& a, const Geometry& G, cudaStream_t s
   if (a.fuse_reduce)
     stage3d_z_kernel<FLUX, LIM, true><<<grid, 128, kZSmem, s>>>(a, G);
   else
-    stage3d_z_kernel<FLUX, LIM, false><<<grid, 128, kZSmem, s>>>(a, G);
+    stage3d_z_kernel<FLUX, LIM, false, kZRows>
+        <<<a.nleaves * (16 / kZRows), 32 * kZRows, ZGeom<kZRows>::Smem, s>>>(a, G);
 }
 
 template <int FLUX>
@@ -167,8 +172,8 @@ cudaError_t stage3d_z_prepare() {
   cudaError_t e = cudaFuncSetAttribute(stage3d_z_kernel<FLUX, LIM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kZSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(stage3d_z_kernel<FLUX, LIM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kZSmem);
+    e = cudaFuncSetAttribute(stage3d_z_kernel<FLUX, LIM, false, kZRows>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ZGeom<kZRows>::Smem);
   return e;
 }
 
