@@ -324,7 +324,7 @@ cudaError_t EulerOps<real, ND>::reflux(int B, real* out, const real* fflux, cons
 
 // shared memory of the staged estimator for the selected variables, 0 where it does not apply
 // (1D, or more than 200 KB)
-template <int ND, int B>
+template <typename real, int ND, int B>
 size_t lohner_tile_smem(unsigned mask) {
   if constexpr (ND < 2) {
     return 0;
@@ -332,7 +332,7 @@ size_t lohner_tile_smem(unsigned mask) {
     int nsel = 0;
     for (int v = 0; v < ND + 2; ++v) nsel += (mask >> v) & 1u;
     size_t pt = ND == 2 ? (size_t)(B + 2) * (B + 2) : (size_t)(B + 2) * (B + 2) * (B + 2);
-    size_t bytes = (size_t)nsel * pt * sizeof(double);
+    size_t bytes = (size_t)nsel * pt * sizeof(real);
     return nsel > 0 && bytes <= 200 * 1024 ? bytes : 0;
   }
 }
@@ -345,7 +345,7 @@ cudaError_t EulerOps<real, ND>::lohner(int B, const real* U, const real* slabs, 
   ([&]() {                                                                                         \
     constexpr int NC = Tile<ND, BB>::NC;                                                           \
     constexpr int LPB = NC >= 256 ? 1 : 256 / NC;                                                  \
-    const size_t smem = lohner_tile_smem<ND, BB>(mask);                                            \
+    const size_t smem = lohner_tile_smem<real, ND, BB>(mask);                                            \
     if constexpr (ND >= 2) if (smem > 0) {                                                         \
       if (smem > 48 * 1024) {                                                                      \
         cudaError_t e = cudaFuncSetAttribute(lohner_tile_kernel<real, ND, BB>,                     \

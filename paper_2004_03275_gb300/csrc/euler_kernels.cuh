@@ -1308,9 +1308,11 @@ __global__ void __launch_bounds__(256) lohner_kernel(const real* __restrict__ U,
 
 // Same estimator with each primitive value computed once: one CTA per leaf converts the leaf's
 // cells and its face ghosts (layer 0) to primitive variables, keeps the nsel selected ones in
-// a (B+2)^ND shared tile, then evaluates every cell from the tile.  The values and the
-// arithmetic are those of lohner_kernel (which converts each cell up to 2 ND + 1 times), so
-// the result is the same bit for bit.  Dynamic shared memory nsel (B+2)^ND doubles.
+// a (B+2)^ND shared tile, then evaluates every cell from the tile.  On a float64 state the
+// values and the arithmetic are those of lohner_kernel (which converts each cell up to 2 ND + 1
+// times), so the result is the same bit for bit; a float32 state is evaluated in float32
+// (GB300's float64 pipe made the float64 evaluation most of a regrid).  Dynamic shared memory
+// nsel (B+2)^ND values of the state's type.
 template <typename real, int ND, int B>
 __global__ void __launch_bounds__(256) lohner_tile_kernel(const real* __restrict__ U, const real* __restrict__ slabs,
                                                           const int* __restrict__ nb, double gamma, double eps,
@@ -1318,22 +1320,24 @@ __global__ void __launch_bounds__(256) lohner_tile_kernel(const real* __restrict
   constexpr int NV = ND + 2, NC = Tile<ND, B>::NC, NT = Tile<ND, B>::NT, P1 = B + 2;
   constexpr int PT = ND == 2 ? P1 * P1 : P1 * P1 * P1;
   static_assert(ND >= 2, "2D and 3D leaves");
-  extern __shared__ double ptile[];  // [selected variable][(B+2)^ND], cell (i, j, k) at i+1 + P1 (j+1 + P1 (k+1))
-  __shared__ double wmax[8];
+  extern __shared__ __align__(16) unsigned char lohner_smem[];
+  using acc = real;  // float32 state: float32 estimator; float64 state: float64 (bit-exact with the oracle)
+  acc* ptile = reinterpret_cast<acc*>(lohner_smem);  // [selected variable][(B+2)^ND], cell (i, j, k) at i+1 + P1 (j+1 + P1 (k+1))
+  __shared__ acc wmax[8];
   const int leaf = blockIdx.x;
   if (leaf >= nleaves) return;
   int sel[NV], nsel = 0;
 #pragma unroll
   for (int v = 0; v < NV; ++v)
     if ((mask >> v) & 1u) sel[nsel++] = v;
-  const double gm1 = gamma - 1.0;
+  const acc gm1 = acc(gamma) - acc(1), epsa = acc(eps);
   auto at = [&](int i, int j, int k) { return (i + 1) + P1 * ((j + 1) + (ND == 3 ? P1 * (k + 1) : 0)); };
   for (int c = threadIdx.x; c < NC; c += blockDim.x) {
     const int i = c % B, j = (c / B) % B, k = ND == 3 ? c / (B * B) : 0;
-    double Uq[NV], V[NV];
+    acc Uq[NV], V[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Uq[v] = (double)U[((size_t)leaf * NV + v) * NC + c];
-    cons_to_prim<double, ND>(Uq, V, gm1);
+    for (int v = 0; v < NV; ++v) Uq[v] = (acc)U[((size_t)leaf * NV + v) * NC + c];
+    cons_to_prim<acc, ND>(Uq, V, gm1);
     for (int q = 0; q < nsel; ++q) ptile[q * PT + at(i, j, k)] = V[sel[q]];
   }
   for (int g = threadIdx.x; g < 2 * ND * NT; g += blockDim.x) {
@@ -1345,29 +1349,29 @@ __global__ void __launch_bounds__(256) lohner_tile_kernel(const real* __restrict
         ++kk;
       }
     ci[d] = side == 0 ? -1 : B;
-    double Un[NV], V[NV];
+    acc Un[NV], V[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Un[v] = (double)fetch_ghost<real, ND, B>(U, slabs, nb, leaf, f, 0, t, v);
-    cons_to_prim<double, ND>(Un, V, gm1);
+    for (int v = 0; v < NV; ++v) Un[v] = (acc)fetch_ghost<real, ND, B>(U, slabs, nb, leaf, f, 0, t, v);
+    cons_to_prim<acc, ND>(Un, V, gm1);
     for (int q = 0; q < nsel; ++q) ptile[q * PT + at(ci[0], ci[1], ci[2])] = V[sel[q]];
   }
   __syncthreads();
-  double emax = 0.0;
+  acc emax = acc(0);
   for (int c = threadIdx.x; c < NC; c += blockDim.x) {
     const int i = c % B, j = (c / B) % B, k = ND == 3 ? c / (B * B) : 0;
-    double ecell = 0.0;
+    acc ecell = acc(0);
     for (int q = 0; q < nsel; ++q) {
-      const double* P = ptile + q * PT;
-      double num = 0.0, den = 0.0;
+      const acc* P = ptile + q * PT;
+      acc num = acc(0), den = acc(0);
       for (int d = 0; d < ND; ++d) {
         const int m[3] = {i - (d == 0), j - (d == 1), k - (d == 2)}, pp[3] = {i + (d == 0), j + (d == 1), k + (d == 2)};
-        const double qm = P[at(m[0], m[1], m[2])], q0 = P[at(i, j, k)], qp = P[at(pp[0], pp[1], pp[2])];
-        double d2 = qp - 2.0 * q0 + qm;
-        double d1 = fabs(qp - q0) + fabs(q0 - qm) + eps * (fabs(qp) + 2.0 * fabs(q0) + fabs(qm));
+        const acc qm = P[at(m[0], m[1], m[2])], q0 = P[at(i, j, k)], qp = P[at(pp[0], pp[1], pp[2])];
+        acc d2 = qp - acc(2) * q0 + qm;
+        acc d1 = fabs(qp - q0) + fabs(q0 - qm) + epsa * (fabs(qp) + acc(2) * fabs(q0) + fabs(qm));
         num = num + d2 * d2;
         den = den + d1 * d1;
       }
-      double e = den > 0.0 ? sqrt(num / den) : 0.0;
+      acc e = den > acc(0) ? sqrt(num / den) : acc(0);
       ecell = fmax(ecell, e);
     }
     emax = fmax(emax, ecell);
@@ -1377,7 +1381,7 @@ __global__ void __launch_bounds__(256) lohner_tile_kernel(const real* __restrict
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) emax = fmax(emax, wmax[w]);
-    err[leaf] = emax;
+    err[leaf] = (double)emax;
   }
 }
 

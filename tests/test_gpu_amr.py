@@ -147,6 +147,26 @@ def test_estimator_bit_exact(ndim, bnx, allvars):
     assert np.array_equal(s.estimate(), g.lohner())
 
 
+@pytest.mark.parametrize("ndim,bnx,allvars", [(2, 16, False), (3, 8, True), (3, 16, False), (3, 16, True)])
+def test_estimator_fp32_state(ndim, bnx, allvars):
+    """A float32 state is evaluated in float32: per leaf within 1e-5 (relative, or 1e-6 absolute)
+    of the oracle's float64 estimator on the same (widened) state."""
+    rng = np.random.default_rng(70 + ndim)
+    base = [2] * ndim + [1] * (3 - ndim)
+    lev, crd = random_balanced_tree(ndim, base, 3, rng, 4)
+    mask = (1 << (ndim + 2)) - 1 if allvars else 1 | (1 << (ndim + 1))
+    s, g, kw = make_pair(ndim, bnx, base, 3, lev, crd, precision="fp32", var_mask=mask)
+    l2, c2 = s.leaves()
+    x, _ = centres_for(l2, c2, kw)
+    V = smooth_state(x, ndim, seed=3)
+    r2 = sum((x[:, d] - 0.4) ** 2 for d in range(ndim))
+    V[:, ndim + 1] = np.where(r2 < 0.05, 20.0, V[:, ndim + 1])
+    s.set_prim(V)
+    g.set_cons(s.read_state())
+    e32, e64 = s.estimate(), g.lohner()
+    assert np.all(np.abs(e32 - e64) <= 1e-5 * np.abs(e64) + 1e-6), np.max(np.abs(e32 - e64))
+
+
 def blast_setup(ndim, bnx, base, max_level, precision="fp64", cycles=None):
     s, g, kw = make_pair(ndim, bnx, base, max_level, precision=precision, gamma=5.0 / 3.0, cfl=0.8,
                          var_mask=1 | (1 << (ndim + 1)))
