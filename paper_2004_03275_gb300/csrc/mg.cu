@@ -740,7 +740,7 @@ __global__ void coarse_kernel(MgState S, Lvl<real> L, const int* insts, const in
 }
 
 // The coarse part of a 2D V-cycle of one instance in shared memory, one CTA per instance:
-// depths I.dsm .. nlev - 1 (sides up to 128 in float32, 64 in float64).  It takes the
+// depths I.dsm .. nlev - 1 (sides up to 64).  It takes the
 // right-hand side of depth dsm from the restriction above it and returns the correction of
 // that depth, doing in between what the per-depth kernels do, in their order and with their
 // arithmetic: nu1 red-black sweeps from a zero correction (each an in-place red pass, then a
@@ -748,7 +748,7 @@ __global__ void coarse_kernel(MgState S, Lvl<real> L, const int* insts, const in
 // of the coarsest level, then prolongation and nu2 sweeps back up.  A block barrier separates
 // the passes.  Shared layout per depth: x, then b, each padded to 4 cells.
 constexpr int kCoarseThreads = 1024;
-constexpr int kCoarseSideF32 = 128, kCoarseSideF64 = 64;  // largest side of its first depth
+constexpr int kCoarseSideF32 = 64, kCoarseSideF64 = 64;  // largest side of its first depth
 
 template <typename real, bool NEU>
 __global__ void __launch_bounds__(kCoarseThreads)
