@@ -898,6 +898,24 @@ __device__ __forceinline__ FF ff_mul(FF a, float chi, float clo) {
 // from zero without reading it, in 3D zero0_kernel follows.
 constexpr int kUpdCells = 4;  // cells per thread of update64_kernel: chunks of kUpdCells * kChunk cells
 
+// the defect update of one cell from its correction e and the float-float sum of its cnt
+// neighbours' corrections; returns |r| as bits
+__device__ __forceinline__ unsigned long long upd_cell(const InstDev& I, double* X, double* R, float& bout, unsigned t,
+                                                       float e, FF sum, int cnt) {
+  const float ce = __fmul_rn((float)cnt, e);  // cnt e exactly as ce + ce_err
+  const float ce_err = __fmaf_rn((float)cnt, e, -ce);
+  sum = ff_add(sum, -ce);
+  sum = ff_add(sum, -ce_err);
+  const FF lap = ff_mul(sum, I.ih2f[0], I.ih2lo0);
+  const FF le = ff_mul(FF{e, 0.f}, I.lamf, I.lamlo);
+  const FF ae = ff_sub(le, lap);
+  X[t] = __dadd_rn(X[t], widen(e));
+  const double r = __dsub_rn(R[t], __dadd_rn(widen(ae.hi), widen(ae.lo)));
+  R[t] = r;
+  bout = narrow<float>(r);
+  return (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;
+}
+
 template <bool NEU, int ND>
 __global__ void __launch_bounds__(kChunk) update64_kernel(MgState S, Lvl<float> L, const Chunk* ch) {
   const Chunk C = ch[blockIdx.x];
@@ -909,57 +927,82 @@ __global__ void __launch_bounds__(kChunk) update64_kernel(MgState S, Lvl<float> 
   float* Bf = L.b + I.off[0];
   double* X = S.X + I.off0;
   double* R = S.R + I.off0;
-  const float ih2hi = I.ih2f[0], ih2lo = I.ih2lo0, lamhi = I.lamf, lamlo = I.lamlo;
   unsigned long long m = 0ull;
-  // cells start + threadIdx.x + k kChunk: each access of the k loop is coalesced
+  if (ND == 2 && (n & 3) == 0) {
+    // four consecutive cells of one row per thread (a side divisible by 4; level offsets are
+    // multiples of 4 cells): the row's corrections and those of the rows below and above as
+    // one float4 each, plus the cells left and right of the four
+    const int j4 = 4 * (int)threadIdx.x;
+    if (j4 < C.count) {
+      const unsigned t0 = (unsigned)C.start + (unsigned)j4;
+      const unsigned r = t0 / un, c0 = t0 - r * un;
+      const bool hasdn = r > 0u, hasup = r + 1u < un, hasl = c0 > 0u, hasr = c0 + 4u < un;
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 e4 = *reinterpret_cast<const float4*>(E + t0);
+      const float4 d4 = (NEU && !hasdn) ? z4 : *reinterpret_cast<const float4*>(E + (hasdn ? t0 - un : t0 + (un - 1u) * un));
+      const float4 u4 = (NEU && !hasup) ? z4 : *reinterpret_cast<const float4*>(E + (hasup ? t0 + un : t0 - (un - 1u) * un));
+      const float lft = (NEU && !hasl) ? 0.f : E[hasl ? t0 - 1u : t0 + un - 1u];
+      const float rgt = (NEU && !hasr) ? 0.f : E[hasr ? t0 + 4u : t0 + 4u - un];
+      const float ev[6] = {lft, e4.x, e4.y, e4.z, e4.w, rgt};
+      const float dv[4] = {d4.x, d4.y, d4.z, d4.w}, uv[4] = {u4.x, u4.y, u4.z, u4.w};
+      float bo[4];
 #pragma unroll
-  for (int k = 0; k < kUpdCells; ++k) {
-    const int j = threadIdx.x + k * kChunk;
-    if (j >= C.count) break;
-    const unsigned t = (unsigned)C.start + (unsigned)j;
-    unsigned c[3] = {t % un, ND > 1 ? (t / un) % un : 0u, ND > 2 ? t / plane : 0u};
-    const unsigned stride[3] = {1u, un, plane};
-    const float e = E[t];
-    // lap e * h^2 = sum of the neighbours (x-, x+, y-, y+, z-, z+) - count e, in float-float
-    FF sum{0.f, 0.f};
-    int cnt = 0;
-#pragma unroll
-    for (int d = 0; d < ND; ++d) {
-#pragma unroll
-      for (int side = -1; side <= 1; side += 2) {
-        unsigned q;
-        if (side < 0) {
-          if (c[d] == 0u) {
-            if (NEU) continue;
-            q = t + (un - 1u) * stride[d];
-          } else {
-            q = t - stride[d];
-          }
-        } else {
-          if (c[d] == un - 1u) {
-            if (NEU) continue;
-            q = t - (un - 1u) * stride[d];
-          } else {
-            q = t + stride[d];
-          }
-        }
-        sum = ff_add(sum, E[q]);
-        ++cnt;
+      for (int q = 0; q < 4; ++q) {
+        // neighbours in the order x-, x+, y-, y+ (cells beyond a zero-flux boundary left out)
+        FF sum{0.f, 0.f};
+        int cnt = 0;
+        if (!(NEU && q == 0 && !hasl)) sum = ff_add(sum, ev[q]), ++cnt;
+        if (!(NEU && q == 3 && !hasr)) sum = ff_add(sum, ev[q + 2]), ++cnt;
+        if (!(NEU && !hasdn)) sum = ff_add(sum, dv[q]), ++cnt;
+        if (!(NEU && !hasup)) sum = ff_add(sum, uv[q]), ++cnt;
+        const unsigned long long rb = upd_cell(I, X, R, bo[q], t0 + q, ev[q + 1], sum, cnt);
+        m = rb > m ? rb : m;
       }
+      *reinterpret_cast<float4*>(Bf + t0) = make_float4(bo[0], bo[1], bo[2], bo[3]);
     }
-    const float ce = __fmul_rn((float)cnt, e);  // cnt e exactly as ce + ce_err
-    const float ce_err = __fmaf_rn((float)cnt, e, -ce);
-    sum = ff_add(sum, -ce);
-    sum = ff_add(sum, -ce_err);
-    const FF lap = ff_mul(sum, ih2hi, ih2lo);
-    const FF le = ff_mul(FF{e, 0.f}, lamhi, lamlo);
-    const FF ae = ff_sub(le, lap);
-    X[t] = __dadd_rn(X[t], widen(e));
-    const double r = __dsub_rn(R[t], __dadd_rn(widen(ae.hi), widen(ae.lo)));
-    R[t] = r;
-    Bf[t] = narrow<float>(r);
-    const unsigned long long rb = (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;  // |r| bits
-    m = rb > m ? rb : m;
+  } else {
+    // cells start + threadIdx.x + k kChunk: each access of the k loop is coalesced
+#pragma unroll
+    for (int k = 0; k < kUpdCells; ++k) {
+      const int j = threadIdx.x + k * kChunk;
+      if (j >= C.count) break;
+      const unsigned t = (unsigned)C.start + (unsigned)j;
+      const unsigned qr = t / un;
+      const unsigned c[3] = {t - qr * un, ND > 2 ? qr % un : qr, ND > 2 ? t / plane : 0u};
+      const unsigned stride[3] = {1u, un, plane};
+      const float e = E[t];
+      // lap e * h^2 = sum of the neighbours (x-, x+, y-, y+, z-, z+) - count e, in float-float
+      FF sum{0.f, 0.f};
+      int cnt = 0;
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+#pragma unroll
+        for (int side = -1; side <= 1; side += 2) {
+          unsigned q;
+          if (side < 0) {
+            if (c[d] == 0u) {
+              if (NEU) continue;
+              q = t + (un - 1u) * stride[d];
+            } else {
+              q = t - stride[d];
+            }
+          } else {
+            if (c[d] == un - 1u) {
+              if (NEU) continue;
+              q = t - (un - 1u) * stride[d];
+            } else {
+              q = t + stride[d];
+            }
+          }
+          sum = ff_add(sum, E[q]);
+          ++cnt;
+        }
+      }
+      float bo;
+      const unsigned long long rb = upd_cell(I, X, R, bo, t, e, sum, cnt);
+      Bf[t] = bo;
+      m = rb > m ? rb : m;
+    }
   }
   block_max_atomic(m, &S.rnorm[C.inst]);
 }
