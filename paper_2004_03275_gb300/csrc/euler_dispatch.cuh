@@ -249,6 +249,18 @@ cudaError_t stage_b(int flux, const StageArgs<real>& a, const Geometry& G, cudaS
 }
 
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+// resident CTAs of the float32 reduction walk: 3 per SM of the current device
+inline int reduce_ctas() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      n = 3 * sms;
+    else
+      n = 3 * 152;
+  }
+  return n;
+}
 
 }  // namespace detail
 
@@ -282,7 +294,7 @@ cudaError_t EulerOps<real, ND>::reduce(int B, const real* U, const int* level, c
     constexpr int NC = Tile<ND, BB>::NC;                                                           \
     constexpr int LPB = ReduceShape<NC>::LPB;                                                      \
     if constexpr (sizeof(real) == 4 && NC % 1024 == 0)                                             \
-      reduce_split_kernel<ND, BB><<<nleaves * (NC / 1024), 256, 0, s>>>(                           \
+      reduce_split_kernel<ND, BB><<<std::min(nleaves * (NC / 1024), detail::reduce_ctas()), 256, 0, s>>>( \
           reinterpret_cast<const float*>(U), level, G, ctl, partials, gpart, gcount, nleaves, advance); \
     else                                                                                           \
       reduce_kernel<real, ND, BB><<<(nleaves + LPB - 1) / LPB, 256, 0, s>>>(U, level, G, ctl, partials, \

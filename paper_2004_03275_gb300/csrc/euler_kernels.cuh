@@ -863,38 +863,47 @@ __global__ void __launch_bounds__(256) reduce_kernel(const real* __restrict__ U,
                                      nleaves, advance != 0, dt, bad);
 }
 
-// Float32 reduction for leaves of >= 1024 cells: NC / 1024 CTAs per leaf, four consecutive
-// cells per thread read as one float4 per variable (all five loads in flight at once).  The
-// sums stay float-float (TwoSum) through the warp butterflies and the fixed-order combination
-// of the warps; one thread widens the CTA's sums to float64 and scales them by the cell volume
+// Float32 reduction for leaves of >= 1024 cells.  Items are quarters (NC / 1024 parts) of
+// leaves; a grid of resident CTAs walks them (CTA b takes items b, b + grid, ...), four
+// consecutive cells per thread read as one float4 per variable, the next item's loads issued
+// before the current one is reduced.  Cell values are scaled by the exact power of two
+// dV(level) / dV(1) so that one float-float (TwoSum) sum per thread and variable serves every
+// level; the sums stay float-float through the warp butterflies and the fixed-order combination
+// of the warps, and one thread widens the CTA's sums to float64 and scales them by dV(1)
 // (GB300's float64 pipe is too narrow for per-thread float64 work).  Each CTA writes one
-// partial; the two-level finish sums the partials in CTA order.
+// partial; the two-level finish sums the partials in CTA order, so the result depends on the
+// grid size only.
 template <int ND, int B>
-__global__ void __launch_bounds__(256) reduce_split_kernel(const float* __restrict__ U, const int* __restrict__ level,
+__global__ void __launch_bounds__(256, 3) reduce_split_kernel(const float* __restrict__ U, const int* __restrict__ level,
                                                            Geometry G, DevCtl* ctl, double* partials, double* gpart,
                                                            unsigned* gcount, int nleaves, int advance) {
   constexpr int NV = ND + 2, NC = Tile<ND, B>::NC, CPL = NC / 1024;
   static_assert(NC % 1024 == 0, "four cells per thread, 256 threads per CTA");
   __shared__ float red[8][2 * NV + 1];
   __shared__ int sbad;
-  const int leaf = blockIdx.x / CPL, part = blockIdx.x % CPL;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool active = leaf < nleaves;
-  float4 q[NV];
-  if (active) {
+  const int items = nleaves * CPL;
+  auto load = [&](int it, float4* q) {
+    const int leaf = it / CPL, part = it - leaf * CPL;
     const float* Ul = U + (size_t)leaf * NV * NC + (part * 256 + threadIdx.x) * 4;
 #pragma unroll
     for (int v = 0; v < NV; ++v) q[v] = __ldg(reinterpret_cast<const float4*>(Ul + (size_t)v * NC));
-  }
+  };
+  float4 q[NV], qn[NV];
+  int it = blockIdx.x;
+  if (it < items) load(it, q);
   if (threadIdx.x == 0) sbad = 0;
   const double dt = cta_stage_dt(ctl, nullptr);  // its barrier also orders sbad
   const float gam = G.gammaf, gm1 = gam - 1.f;
-  const int lev = active ? level[leaf] : 1;
   float rate = 0.f, hi[NV], lo[NV];
   int bad = 0;
 #pragma unroll
   for (int v = 0; v < NV; ++v) hi[v] = lo[v] = 0.f;
-  if (active) {
+  for (; it < items; it += gridDim.x) {
+    const int nx = it + (int)gridDim.x;
+    if (nx < items) load(nx, qn);
+    const int lev = level[it / CPL];
+    const float vscale = __int_as_float((127 - ND * (lev - 1)) << 23);  // dV(lev) / dV(1), exact
     float dx[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) dx[d] = geo_dx<float>(G, lev, d);
@@ -905,8 +914,10 @@ __global__ void __launch_bounds__(256) reduce_split_kernel(const float* __restri
       for (int v = 0; v < NV; ++v) Uc[v] = k == 0 ? q[v].x : k == 1 ? q[v].y : k == 2 ? q[v].z : q[v].w;
       rate = fmaxf(rate, cell_rate<float, ND>(Uc, gam, gm1, dx, &bad));
 #pragma unroll
-      for (int v = 0; v < NV; ++v) twosum_acc(hi[v], lo[v], Uc[v]);
+      for (int v = 0; v < NV; ++v) twosum_acc(hi[v], lo[v], Uc[v] * vscale);
     }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = qn[v];
   }
   if (bad) sbad = 1;
   for (int o = 16; o > 0; o >>= 1) {
@@ -931,7 +942,7 @@ __global__ void __launch_bounds__(256) reduce_split_kernel(const float* __restri
       for (int v = 0; v < NV; ++v) ff_acc(hi[v], lo[v], red[w][v], red[w][NV + v]);
     }
 #pragma unroll
-    for (int v = 0; v < NV; ++v) partials[(size_t)blockIdx.x * NV + v] = ((double)hi[v] + (double)lo[v]) * G.dV[lev];
+    for (int v = 0; v < NV; ++v) partials[(size_t)blockIdx.x * NV + v] = ((double)hi[v] + (double)lo[v]) * G.dV[1];
     __threadfence();  // the partial is visible before the group counter counts this CTA
     atomicMax(&ctl->smax_bits, MaxKey<float>::enc(mm));
     if (sbad) atomicOr(&ctl->status, 1);
