@@ -77,8 +77,10 @@ def test_instance_size_limit():
     assert ei.value.code == -1
 
 
-@pytest.mark.parametrize("ndim,sizes", [(2, SIZES_2D), (3, [16, 12, 24])])
+@pytest.mark.parametrize("ndim,sizes", [(2, SIZES_2D), (2, [18, 30, 10, 22]), (3, [16, 12, 24])])
 def test_fp32_defect_correction_within_bound(ndim, sizes):
+    """(2D sides not divisible by 4 take the defect update's strided form, the others its
+    four-consecutive-cell form.)"""
     L, rtol = 2.5, 1e-10
     lam, bs = batch(sizes, ndim, 4, lam_scale=10.0)
     s = amrvac.MgSolver(ndim, sizes, lam, L, precision="fp32", rtol=rtol)
