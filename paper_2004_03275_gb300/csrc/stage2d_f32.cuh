@@ -156,23 +156,27 @@ __device__ __forceinline__ void flux2(float rL, float uL, float wL, float pL, fl
     }
     return;
   }
-  // HLLC on the upwind side K of the contact only
+  // HLLC on the upwind side K of the contact only: F_K, plus S_K (U*_K - U_K) inside the fan
   float aL = rL * (SL - uL), aR = rR * (SR - uR);
   float Ss = (pR - pL + aL * uL - aR * uR) * rcp(aL - aR);
-  bool left = SL >= 0.f || (SR > 0.f && Ss >= 0.f);
+  const bool left = SL >= 0.f || (SR > 0.f && Ss >= 0.f), fan = SL < 0.f && SR > 0.f;
   float rK = left ? rL : rR, uK = left ? uL : uR, wK = left ? wL : wR, pK = left ? pL : pR;
-  float aK = left ? aL : aR, SK = left ? SL : SR;
+  float SK = left ? SL : SR;
   float EK = pK * igm1 + 0.5f * rK * (uK * uK + wK * wK);
-  float mK = rK * uK;
-  float FK[4] = {mK, mK * uK + pK, mK * wK, (EK + pK) * uK};
-  float UK[4] = {rK, mK, rK * wK, EK};
-  // fac = a_K / (S_K - S*); E* = fac (E_K / rho_K + (S* - u_K) S*) + (S* - u_K) p_K / (S_K - S*),
-  // the star energy with fac (S* - u_K) p_K / a_K written without dividing by a_K
-  float q = rcp(SK - Ss), fac = aK * q, d = Ss - uK;
-  float Us[4] = {fac, fac * Ss, fac * wK, fac * (EK * rcp(rK) + d * Ss) + d * pK * q};
-  bool sub = SL < 0.f && SR > 0.f;
-#pragma unroll
-  for (int v = 0; v < 4; ++v) F[v] = sub ? FK[v] + SK * (Us[v] - UK[v]) : FK[v];
+  float mK = rK * uK, eK = EK + pK;
+  const float2 FK01 = make_float2(mK, mK * uK + pK), FK23 = make_float2(mK * wK, eK * uK);
+  // U*_K - U_K with d = S* - u_K, q = 1 / (S_K - S*), g = d q (so that rho* = rho_K (1 + g)):
+  //   (rho_K g, rho_K d + rho_K g S*, rho_K g w_K, d (q (E_K + p_K) + rho* S*)),
+  // the star state of the fan with no division by rho_K and no difference of near-equal terms.
+  // Outside the fan q and the wave-speed factor are zero, so the flux is F_K exactly.
+  const float q = fan ? rcp(SK - Ss) : 0.f, s = fan ? SK : 0.f;
+  const float d = Ss - uK, g0 = rK * (d * q);
+  const float2 dU01 = make_float2(g0, g0 * Ss + rK * d), dU23 = make_float2(g0 * wK, d * (q * eK + (rK + g0) * Ss));
+  const float2 F01 = fma2(bc2(s), dU01, FK01), F23 = fma2(bc2(s), dU23, FK23);
+  F[0] = F01.x;
+  F[1] = F01.y;
+  F[2] = F23.x;
+  F[3] = F23.y;
 }
 
 }  // namespace f32

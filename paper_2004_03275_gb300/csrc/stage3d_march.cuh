@@ -59,22 +59,24 @@ __device__ __forceinline__ void flux3(float rL, float uL, float vL, float wL, fl
     }
     return;
   }
-  // HLLC on the upwind side K of the contact only
+  // HLLC on the upwind side K of the contact only; U*_K - U_K in the form of flux2
   float aL = rL * (SL - uL), aR = rR * (SR - uR);
   float Ss = (pR - pL + aL * uL - aR * uR) * rcp(aL - aR);
-  bool left = SL >= 0.f || (SR > 0.f && Ss >= 0.f);
+  const bool left = SL >= 0.f || (SR > 0.f && Ss >= 0.f), fan = SL < 0.f && SR > 0.f;
   float rK = left ? rL : rR, uK = left ? uL : uR, vK = left ? vL : vR, wK = left ? wL : wR, pK = left ? pL : pR;
-  float aK = left ? aL : aR, SK = left ? SL : SR;
+  float SK = left ? SL : SR;
   float EK = pK * igm1 + 0.5f * rK * (uK * uK + vK * vK + wK * wK);
-  float mK = rK * uK;
-  float FK[5] = {mK, mK * uK + pK, mK * vK, mK * wK, (EK + pK) * uK};
-  float UK[5] = {rK, mK, rK * vK, rK * wK, EK};
-  // star energy without dividing by a_K (same form as flux2)
-  float q = rcp(SK - Ss), fac = aK * q, d = Ss - uK;
-  float Us[5] = {fac, fac * Ss, fac * vK, fac * wK, fac * (EK * rcp(rK) + d * Ss) + d * pK * q};
-  bool sub = SL < 0.f && SR > 0.f;
-#pragma unroll
-  for (int v = 0; v < 5; ++v) F[v] = sub ? FK[v] + SK * (Us[v] - UK[v]) : FK[v];
+  float mK = rK * uK, eK = EK + pK;
+  const float2 FK01 = make_float2(mK, mK * uK + pK), FK23 = make_float2(mK * vK, mK * wK);
+  const float q = fan ? rcp(SK - Ss) : 0.f, s = fan ? SK : 0.f;
+  const float d = Ss - uK, g0 = rK * (d * q);
+  const float2 dU01 = make_float2(g0, g0 * Ss + rK * d), dU23 = make_float2(g0 * vK, g0 * wK);
+  const float2 F01 = fma2(bc2(s), dU01, FK01), F23 = fma2(bc2(s), dU23, FK23);
+  F[0] = F01.x;
+  F[1] = F01.y;
+  F[2] = F23.x;
+  F[3] = F23.y;
+  F[4] = s * (d * (q * eK + (rK + g0) * Ss)) + eK * uK;
 }
 
 }  // namespace f32
