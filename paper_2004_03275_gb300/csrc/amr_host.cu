@@ -764,7 +764,8 @@ int amr_read_state(amr_handle* h, double* U, long long cap_values, int on_device
 
 int amr_set_time(amr_handle* h, double t) {
   if (!h) return AMR_ERR_INVALID_ARG;
-  CK(cudaMemcpyAsync((char*)h->ctl.p + offsetof(DevCtl, t), &t, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(ctl_set_t(h->ctl.as<DevCtl>(), t, h->stream));
+  ++h->launches;
   CK(cudaStreamSynchronize(h->stream));
   return AMR_OK;
 }

@@ -21,7 +21,15 @@ struct DevCtl {
   int status;                    // bit 0: non-physical state met
   long long steps;
   double totals[5];
+  float dt_stepf;    // (float) of the current step's dt, min(dt_cfl, t_end - t): rewritten by every
+                     // writer of t, t_end and dt_cfl, so that float32 kernels read the step's dt
+                     // without float64 instructions (GB300 runs float64 at 1/64 of the float32 rate)
 };
+
+// dt of a step from the time, the CFL step and the end time: the CFL step clipped to t_end
+__host__ __device__ __forceinline__ double step_dt(double t, double dt_cfl, double t_end) {
+  return t + dt_cfl > t_end ? t_end - t : dt_cfl;
+}
 
 // Ghost slab of one leaf face at a level jump.
 struct SlabDesc {

@@ -217,11 +217,11 @@ struct MaxKey<float> {
   static __device__ double dec(unsigned long long b) { return (double)__uint_as_float((unsigned int)b); }
 };
 
-// dt of the current step: the CFL step clipped to t_end (same on every CTA)
-__device__ __forceinline__ double stage_dt(const DevCtl* ctl) {
-  double t = ctl->t, dt = ctl->dt_cfl;
-  if (t + dt > ctl->t_end) dt = ctl->t_end - t;
-  return dt;
+// dt of the current step: the CFL step clipped to t_end (same on every CTA; step_dt in common.cuh)
+__device__ __forceinline__ double stage_dt(const DevCtl* ctl) { return step_dt(ctl->t, ctl->dt_cfl, ctl->t_end); }
+// DevCtl::dt_stepf from the current t, dt_cfl and t_end (one thread, after it changed one of them)
+__device__ __forceinline__ void refresh_dt_step(volatile DevCtl* c) {
+  c->dt_stepf = (float)step_dt(c->t, c->dt_cfl, c->t_end);
 }
 
 // dt of the current step computed once per CTA (thread 0) and shared: keeps
@@ -237,6 +237,15 @@ __device__ __forceinline__ double cta_stage_dt(const DevCtl* ctl, float* dtf) {
   __syncthreads();
   if (dtf) *dtf = s_dtf;
   return s_dt;
+}
+
+// float32 kernels: the step's dt as a float, read once per CTA and shared (the barrier is
+// part of the contract, as in cta_stage_dt); no float64 instruction is issued
+__device__ __forceinline__ float cta_stage_dtf(const DevCtl* ctl) {
+  __shared__ float s_dtf;
+  if (threadIdx.x == 0) s_dtf = *reinterpret_cast<const volatile float*>(&ctl->dt_stepf);
+  __syncthreads();
+  return s_dtf;
 }
 
 template <typename real>
@@ -301,6 +310,7 @@ __device__ __forceinline__ void publish_reduction(DevCtl* ctl, const double* acc
     c->steps = c->steps + 1;
   }
   c->dt_cfl = c->cfl / smax;
+  refresh_dt_step(c);
   c->smax_bits = 0ull;
   c->done = 0u;
 }
@@ -312,10 +322,13 @@ __device__ __forceinline__ void publish_reduction(DevCtl* ctl, const double* acc
 // CTA calls this after its CTA's partials and atomicMax are issued.  No CTA
 // waits on another; counters are reset by the CTA that consumed them.
 // fence_all = false: the threads that wrote the CTA's partials have already
-// issued their fence, so the others skip it.
+// issued their fence, so the others skip it.  dt_from_ctl: the step's dt is read
+// from the control block by the finishing thread (float32 kernels carry only its
+// float copy; t, dt_cfl and t_end do not change before this finish).
 template <typename real, int NV, int NTHREADS>
 __device__ void last_cta_finish(DevCtl* ctl, const double* partials, double* gpart, unsigned* gcount,
-                                int nleaves, int lpb, bool advance, double dt, bool fence_all = true) {
+                                int nleaves, int lpb, bool advance, double dt, bool fence_all = true,
+                                bool dt_from_ctl = false) {
   __shared__ bool flag;
   const int g = blockIdx.x / kGroupCTAs;
   const int ngroups = (gridDim.x + kGroupCTAs - 1) / kGroupCTAs;
@@ -361,7 +374,13 @@ __device__ void last_cta_finish(DevCtl* ctl, const double* partials, double* gpa
     for (int v = 0; v < NV; ++v) acc[v] += __ldcg(&gpart[(size_t)q * NV + v]);
   __syncthreads();  // wred reuse
   block_sum_fixed<NV, NTHREADS>(acc);
-  if (threadIdx.x == 0) publish_reduction<real, NV>(ctl, acc, advance, dt);
+  if (threadIdx.x == 0) {
+    if (dt_from_ctl) {
+      const volatile DevCtl* c = ctl;
+      dt = step_dt(c->t, c->dt_cfl, c->t_end);
+    }
+    publish_reduction<real, NV>(ctl, acc, advance, dt);
+  }
 }
 
 // Block-wide reduction of (max rate, per-variable FP64 sums) and the last-CTA
@@ -893,7 +912,7 @@ __global__ void __launch_bounds__(256, 3) reduce_split_kernel(const float* __res
   int it = blockIdx.x;
   if (it < items) load(it, q);
   if (threadIdx.x == 0) sbad = 0;
-  const double dt = cta_stage_dt(ctl, nullptr);  // its barrier also orders sbad
+  __syncthreads();  // orders sbad (the step's dt, when advancing, is read by the finishing thread)
   const float gam = G.gammaf, gm1 = gam - 1.f;
   float rate = 0.f, hi[NV], lo[NV];
   int bad = 0;
@@ -947,7 +966,7 @@ __global__ void __launch_bounds__(256, 3) reduce_split_kernel(const float* __res
     atomicMax(&ctl->smax_bits, MaxKey<float>::enc(mm));
     if (sbad) atomicOr(&ctl->status, 1);
   }
-  last_cta_finish<float, NV, 256>(ctl, partials, gpart, gcount, (int)gridDim.x, 1, advance != 0, dt, false);
+  last_cta_finish<float, NV, 256>(ctl, partials, gpart, gcount, (int)gridDim.x, 1, advance != 0, 0.0, false, true);
 }
 
 // ====================================================== ghost slab fill ==

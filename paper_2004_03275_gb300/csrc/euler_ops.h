@@ -30,5 +30,6 @@ struct EulerOps {
 
 // tiny control kernels (ctl_kernels.cu)
 cudaError_t ctl_set_t_end(DevCtl* ctl, double t_end, cudaStream_t s);
+cudaError_t ctl_set_t(DevCtl* ctl, double t, cudaStream_t s);
 
 }  // namespace amrgpu

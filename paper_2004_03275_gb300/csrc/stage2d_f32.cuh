@@ -268,9 +268,8 @@ __global__ void __launch_bounds__(256, 5) stage2d_f32_kernel(StageArgs<float> a,
   __shared__ Stage2DF32Smem<B> S;
   __shared__ float wmax[8];
   __shared__ int sbad;
-  float dt;
-  const double dtd = cta_stage_dt(a.ctl, &dt);
-  if (!(dtd > 0.0)) return;
+  const float dt = cta_stage_dtf(a.ctl);
+  if (!(dt > 0.f)) return;
   const float gam = G.gammaf, gm1 = gam - 1.f, igm1 = 1.f / gm1;
   const int lb = threadIdx.x / NC, tc = threadIdx.x % NC;
   const int ic = tc % B, jc = tc / B;
@@ -449,7 +448,7 @@ __global__ void __launch_bounds__(256, 5) stage2d_f32_kernel(StageArgs<float> a,
     atomicMax(&a.ctl->smax_bits, MaxKey<float>::enc(mm));
     if (sbad) atomicOr(&a.ctl->status, 1);
   }
-  last_cta_finish<float, NV, 256>(a.ctl, a.partials, a.gpart, a.gcount, a.nleaves, LPB, true, dtd);
+  last_cta_finish<float, NV, 256>(a.ctl, a.partials, a.gpart, a.gcount, a.nleaves, LPB, true, 0.0, true, true);
 }
 
 }  // namespace amrgpu

@@ -227,9 +227,13 @@ __global__ void __launch_bounds__(32 * kMarchMaxWarps, 2)
     }
   };
   if (active) load_leaf();
+  // the first and middle stages read the float copy of dt (no float64 instruction); the last
+  // stage, a few resident CTAs, keeps the float64 dt for its finish (fewer registers live)
   float dt;
-  const double dtd = cta_stage_dt(a.ctl, &dt);
-  if (!(dt > 0.f)) {  // same decision as dtd > 0; the first leaf's copy must land before the exit
+  double dtd = 0.0;
+  if constexpr (LAST) dtd = cta_stage_dt(a.ctl, &dt);
+  else dt = cta_stage_dtf(a.ctl);
+  if (!(dt > 0.f)) {  // no step to take; the first leaf's copy must land before the exit
     if (TMA && active) tma::bar_wait(&tbar[warp], phase, kTmaWaitLimit);
     return;
   }

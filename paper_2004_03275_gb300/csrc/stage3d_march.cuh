@@ -386,8 +386,7 @@ __global__ void __launch_bounds__(32 * ZR, 12 / ZR) stage3d_z_kernel(StageArgs<f
       for (int v = 0; v < NV; ++v) gz[m][v] = __ldg(&src[v * stride]);
     }
   }
-  float dt;
-  const double dtd = cta_stage_dt(a.ctl, &dt);  // its barrier also publishes the staged arrays
+  const float dt = cta_stage_dtf(a.ctl);  // its barrier also publishes the staged arrays
   if (!(dt > 0.f)) return;
   const float gam = G.gammaf, gm1 = gam - 1.f, igm1 = 1.f / gm1;
   float rate = 0.f;
@@ -530,9 +529,7 @@ __global__ void __launch_bounds__(32 * ZR, 12 / ZR) stage3d_z_kernel(StageArgs<f
       atomicMax(&a.ctl->smax_bits, MaxKey<float>::enc(mm));
       if (sbad) atomicOr(&a.ctl->status, 1);
     }
-    last_cta_finish<float, NV, 128>(a.ctl, a.partials, a.gpart, a.gcount, (int)gridDim.x, 1, true, dtd, false);
-  } else {
-    (void)dtd;
+    last_cta_finish<float, NV, 128>(a.ctl, a.partials, a.gpart, a.gcount, (int)gridDim.x, 1, true, 0.0, false, true);
   }
 }
 
