@@ -130,6 +130,8 @@ int amr_set_state_fn(amr_handle* h, amr_prim_fn prim_at, void* user);
  * kernel; pageable host memory is staged through a device buffer. */
 int amr_read_state(amr_handle* h, double* U, long long cap_values, int on_device);
 
+/* Sets the simulation time t (a one-thread control kernel on the handle's stream,
+ * which also refreshes the float copy of the next step's dt).  Synchronous. */
 int amr_set_time(amr_handle* h, double t);
 
 /* One SSPRK step with dt = min(cfl-step, t_end - t).  Synchronous; returns the
