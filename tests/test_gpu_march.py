@@ -135,3 +135,30 @@ def test_stage_tuner_candidates_give_identical_states():
     assert np.array_equal(s0.read_state(), states[0])
     with pytest.raises(amrvac.AmrError):
         s0.set_march_tuning([(3, 0), (4, 0), (4, 1)])
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_fp32_step_after_set_time_takes_the_clipped_dt(ndim):
+    """The float32 stage kernels read the step's dt from a float copy in the control block,
+    rewritten by every writer of t, t_end and dt_cfl.  A step clipped to the end time 1 + h after
+    amr_set_time(1) must use dt = h exactly as a step from t = 0 clipped to h does: same state
+    bit for bit, and t lands on 1 + h (h = 2^-16, far below the CFL step, 1 + h exact)."""
+    base = [4, 4] if ndim == 2 else [2, 2, 2]
+    kw = dict(ndim=ndim, block_nx=16, base=base, gamma=1.4, cfl=0.8, flux="hllc",
+              limiter="vanleer" if ndim == 2 else "koren", rk=3, bc="periodic")
+    h = 2.0 ** -16
+    runs = []
+    for t0 in (0.0, 1.0):
+        s = amrvac.AmrSolver(precision="fp32", **kw)
+        lev, crd = s.leaves()
+        x, gi = inputs.cell_centres(lev, crd, ndim, 16, base + [1] * (3 - ndim), [0, 0, 0], [1, 1, 1])
+        s.set_prim(inputs.kelvin_helmholtz(x, gi, 16 * base[0], seed=3) if ndim == 2 else inputs.blast(x, seed=7))
+        if t0:
+            s.set_time(t0)
+        assert s.step(t0 + h) == h
+        assert s.t == t0 + h
+        s.run(3, t0 + h)  # past the end time: device no-ops
+        assert s.t == t0 + h
+        runs.append(s.read_state())
+        s.close()
+    assert np.array_equal(runs[0], runs[1])
