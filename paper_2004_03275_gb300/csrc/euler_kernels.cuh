@@ -383,6 +383,29 @@ __device__ void last_cta_finish(DevCtl* ctl, const double* partials, double* gpa
   }
 }
 
+// One-level finish for a grid whose CTAs each wrote one row of NV partials (row = blockIdx.x):
+// the last CTA to arrive sums the rows in a fixed order (thread t: rows t, t + NTHREADS, ...;
+// then the block sum) and publishes.  One counter atomic, one fence and one pass over the
+// partials, against two of each in last_cta_finish: for a few hundred CTAs this shortens the
+// serial tail at the end of the launch.  The caller fences its partials before the barrier.
+template <typename real, int NV, int NTHREADS>
+__device__ void last_cta_finish_flat(DevCtl* ctl, const double* partials, bool advance, double dt) {
+  __shared__ bool flag;
+  __syncthreads();
+  if (threadIdx.x == 0) flag = atomicAdd(&ctl->done, 1u) == gridDim.x - 1u;
+  __syncthreads();
+  if (!flag) return;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  for (int r = threadIdx.x; r < (int)gridDim.x; r += NTHREADS)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] += __ldcg(&partials[(size_t)r * NV + v]);
+  block_sum_fixed<NV, NTHREADS>(acc);
+  if (threadIdx.x == 0) publish_reduction<real, NV>(ctl, acc, advance, dt);
+}
+
 // Block-wide reduction of (max rate, per-variable FP64 sums) and the last-CTA
 // finalisation: totals = fixed-order sum of per-leaf partials, dt_cfl = cfl/smax,
 // and, when `advance`, t += dt of the step just taken.  Deterministic for any

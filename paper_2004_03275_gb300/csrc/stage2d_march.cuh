@@ -22,10 +22,11 @@
 //
 // Conserved totals on the last stage: every thread accumulates its cells in
 // float-float (TwoSum), scaled by 4^-(level-1) so that all levels share one unit
-// (dV halves exactly per level and per dimension); one warp adds the CTA's
-// threads in a fixed order into one float64 partial per variable, and the
-// two-level last-CTA finish sums the partials in CTA order.  The result is
-// deterministic for a given tree.
+// (dV halves exactly per level and per dimension); each warp adds its lanes by a
+// fixed float-float butterfly, one warp adds the CTA's warps in order into one
+// float64 partial per variable, and the last CTA to finish sums the partials in
+// CTA order (one level up to kFlatFinishMax CTAs, else the two-level finish).  The
+// result is deterministic for a given tree.
 #pragma once
 #include "stage2d_f32.cuh"
 #include "tma.cuh"
@@ -34,6 +35,7 @@ namespace amrgpu {
 
 constexpr int kMarchWarps = 4;     // warps (= leaves) per CTA of the last stage (its reduction's thread count)
 constexpr int kMarchMaxWarps = 8;  // largest CTA of the first and middle stages (launch parameter)
+constexpr int kFlatFinishMax = 4096;  // last stage: one-level finish up to this many CTAs
 
 struct MarchSmem {
   float4 E[16][17];  // x flux differences of the interior cells, E[j][i]; before the x march it
@@ -157,6 +159,7 @@ __global__ void __launch_bounds__(32 * kMarchMaxWarps, 2)
                                               ((128u - (tma::smem_addr(march_smem_raw) & 127u)) & 127u));
   __shared__ uint64_t tbar[kMarchMaxWarps];
   __shared__ float wrate[kMarchMaxWarps];
+  __shared__ float wtot[2][kMarchWarps][4];  // last stage: per warp (hi, lo) of each variable
   __shared__ int sbad;
   const int NW = LAST ? kMarchWarps : (int)(blockDim.x >> 5);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -443,33 +446,34 @@ __global__ void __launch_bounds__(32 * kMarchMaxWarps, 2)
   }
 
   if constexpr (LAST) {
-    // ---- last stage: CTA max rate, CTA totals (fixed order), two-level finish
+    // ---- last stage: CTA max rate, CTA totals (fixed order), finish
     for (int o = 16; o > 0; o >>= 1) rate = fmaxf(rate, __shfl_xor_sync(0xffffffffu, rate, o));
-    if (lane == 0) wrate[warp] = rate;
-    // each warp parks its (hi, lo) pairs in its own E array, which its y march no longer reads
-    float* park = reinterpret_cast<float*>(&M.E[0][0]);
-    const float thv[NV] = {th[0].x, th[0].y, th[1].x, th[1].y}, tlv[NV] = {tl[0].x, tl[0].y, tl[1].x, tl[1].y};
+    // each warp adds its 32 lanes' (hi, lo) pairs by a fixed butterfly (both partners of an
+    // exchange get the same bits: TwoSum's error term is exact whatever the operand order)
+    float hv[NV] = {th[0].x, th[0].y, th[1].x, th[1].y}, lv[NV] = {tl[0].x, tl[0].y, tl[1].x, tl[1].y};
+    for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      park[v * 32 + lane] = thv[v];
-      park[(NV + v) * 32 + lane] = tlv[v];
+      for (int v = 0; v < NV; ++v) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hv[v], o), l2 = __shfl_xor_sync(0xffffffffu, lv[v], o);
+        march::ff_add(hv[v], lv[v], h2, l2);
+      }
+    if (lane == 0) {
+      wrate[warp] = rate;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        wtot[0][warp][v] = hv[v];
+        wtot[1][warp][v] = lv[v];
+      }
     }
     if (bad) sbad = 1;
     __syncthreads();
     if (warp == 0) {
-      // lane = 8 v + g: variable v, threads 16 g .. 16 g + 15 in order, then the 8 groups
-      constexpr int PER = 32 * kMarchWarps / 8;
-      const int v = lane >> 3, g = lane & 7;
-      auto hi_of = [&](int t) { return reinterpret_cast<const float*>(&S[t >> 5].E[0][0])[v * 32 + (t & 31)]; };
-      auto lo_of = [&](int t) { return reinterpret_cast<const float*>(&S[t >> 5].E[0][0])[(NV + v) * 32 + (t & 31)]; };
-      float hh = hi_of(g * PER), ll = lo_of(g * PER);
-      for (int t = 1; t < PER; ++t) march::ff_add(hh, ll, hi_of(g * PER + t), lo_of(g * PER + t));
-      for (int o = 4; o > 0; o >>= 1) {
-        float h2 = __shfl_down_sync(0xffffffffu, hh, o), l2 = __shfl_down_sync(0xffffffffu, ll, o);
-        if (g < o) march::ff_add(hh, ll, h2, l2);
+      if (lane < NV) {  // lane v: the warps' pairs in warp order
+        float hh = wtot[0][0][lane], ll = wtot[1][0][lane];
+        for (int w = 1; w < kMarchWarps; ++w) march::ff_add(hh, ll, wtot[0][w][lane], wtot[1][w][lane]);
+        a.partials[(size_t)blockIdx.x * NV + lane] = ((double)hh + (double)ll) * G.dV[1];
       }
-      if (g == 0) a.partials[(size_t)blockIdx.x * NV + v] = ((double)hh + (double)ll) * G.dV[1];
-      __threadfence();  // the partials are visible before the group counter counts this CTA
+      __threadfence();  // the partials are visible before the counter counts this CTA
       if (lane == 0) {
         float mm = wrate[0];
         for (int w = 1; w < kMarchWarps; ++w) mm = fmaxf(mm, wrate[w]);
@@ -477,8 +481,11 @@ __global__ void __launch_bounds__(32 * kMarchMaxWarps, 2)
         if (sbad) atomicOr(&a.ctl->status, 1);
       }
     }
-    last_cta_finish<float, NV, 32 * kMarchWarps>(a.ctl, a.partials, a.gpart, a.gcount, (int)gridDim.x, 1, true, dtd,
-                                                 false);
+    if (gridDim.x <= kFlatFinishMax)
+      last_cta_finish_flat<float, NV, 32 * kMarchWarps>(a.ctl, a.partials, true, dtd);
+    else
+      last_cta_finish<float, NV, 32 * kMarchWarps>(a.ctl, a.partials, a.gpart, a.gcount, (int)gridDim.x, 1, true, dtd,
+                                                   false);
   }
 }
 
