@@ -227,7 +227,7 @@ def time_steps(torch, solver, stream, steps):
 # dram__bytes_read.sum + dram__bytes_write.sum per stage launch (mean of the three stages of a
 # step) from the ncu capture of the stage kernel summarised in profiles/stage2d_march_kh2048.md;
 # None when the kernel has changed since the counters were taken.
-STAGE2D_F32_TRAFFIC = 144.6e6
+STAGE2D_F32_TRAFFIC = 144.8e6
 
 
 def stage_roofline(solver, nsteps, nv, wbytes, ncells, hbm_gbs, ms_per_step, nstages=3, traffic=None):
