@@ -5,7 +5,9 @@
   ghost value of the slab is written exactly once;
 * `reflux_kernel` (one thread per record, variable and tangential cell): for any set of faces
   of one coarse leaf with level jumps, every (face, cell) correction is applied exactly once,
-  each cell by one thread, in the order x, y, z.
+  each cell by one thread, in the order x, y, z;
+* the float32 march kernel's last-stage totals: the per-warp float-float butterfly leaves every
+  lane with the same bits, and the CTA's total is the exact sum to float-float accuracy.
 """
 import itertools
 
@@ -141,3 +143,45 @@ def test_reflux_single_writer_in_face_order(nd, B):
                 assert (g, cell) not in pairs
                 pairs.add((g, cell))
         assert len(pairs) == len(faces) * NT
+
+
+def ff_add(hi, lo, h2, l2):
+    """float-float add of the kernel (TwoSum of the high parts, low parts added), in float32."""
+    f = np.float32
+    s = f(hi + h2)
+    bb = f(s - hi)
+    e = f(f(hi - f(s - bb)) + f(h2 - bb))
+    return s, f(f(lo + l2) + e)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_last_stage_totals_butterfly(seed):
+    rng = np.random.default_rng(seed)
+    f = np.float32
+    nwarps, cells = 4, 13  # 4 warps of the last stage's CTA; ~13 cells per thread (8 per leaf, 1.68 leaves)
+    # per thread: TwoSum accumulation of its cells (scaled conserved values of mixed sign)
+    vals = (rng.normal(size=(nwarps * 32, cells)) * 10.0 ** rng.integers(-2, 3, size=(nwarps * 32, cells))).astype(f)
+    hi = np.zeros(nwarps * 32, dtype=f)
+    lo = np.zeros(nwarps * 32, dtype=f)
+    for t in range(nwarps * 32):
+        for x in vals[t]:
+            hi[t], lo[t] = ff_add(hi[t], lo[t], x, f(0))
+    # per warp: butterfly over lane ^ o, o = 16 .. 1; both partners of an exchange compute it
+    wh, wl = [], []
+    for w in range(nwarps):
+        h = hi[32 * w:32 * w + 32].copy()
+        l = lo[32 * w:32 * w + 32].copy()
+        for o in (16, 8, 4, 2, 1):
+            nh, nl = h.copy(), l.copy()
+            for lane in range(32):
+                nh[lane], nl[lane] = ff_add(h[lane], l[lane], h[lane ^ o], l[lane ^ o])
+            h, l = nh, nl
+        assert np.all(h == h[0]) and np.all(l == l[0])  # every lane holds the same bits
+        wh.append(h[0])
+        wl.append(l[0])
+    hh, ll = wh[0], wl[0]
+    for w in range(1, nwarps):  # the warps in order
+        hh, ll = ff_add(hh, ll, wh[w], wl[w])
+    exact = float(np.sum(vals.astype(np.float64), dtype=np.float64))
+    scale = float(np.sum(np.abs(vals.astype(np.float64))))
+    assert abs((float(hh) + float(ll)) - exact) <= 2.0 ** -40 * scale
